@@ -1,0 +1,201 @@
+"""Lambda equations, damped linear-response solves and the response function (oracle).
+
+TEST INFRASTRUCTURE ONLY.
+
+  * Lambda:        lambda A = -eta  (Sec. 2.3, Eq. for t-bar^(0)), eta = dE/dt;
+  * response:      (A - z) t^Y(z) = -xi^Y, z = w + i gamma  (Eqs. LR response equation and
+                   LR response equation_cpp);
+  * Davidson:      the SI "Davidson scheme" steps 1-5, with the readings
+                   G' = b^H (sigma - z b), C' = -b^H xi, r = (sigma - z b) beta + xi,
+                   correction = -(D - z)^{-1} r with D the orbital-energy differences,
+                   modified Gram-Schmidt against the trial space, convergence on ||r||_2;
+  * response fn:   <<X;Y>>_z = f(z) + conj(f(-conj z)),
+                   f(z) = 1/2 [eta^X t^Y(z) + eta^Y t^X(-z) + (t^X(-z) F) t^Y(z)]
+                   (Eq. CC-CC response function with C^{+-w} and P(X,Y) written out; the
+                   conjugation flips the real frequency and keeps the damping, which is the
+                   reading that reproduces the exact sum over states);
+  * polarizability alpha_xy(z) = -<<mu_x; mu_y>>_z, mean alpha, anisotropy, and the absorption
+    cross section sigma(w) = 4 pi w / c Im mean-alpha (Eq. abs_cpp; Sec. 5 definitions).
+All products in the response function are bilinear (no conjugation) over unique excitations.
+"""
+from __future__ import annotations
+import numpy as np
+from . import ccsd, hbar, sigma, props
+from .deriv import pack, unpack, dot
+
+C_AU = 137.035999084
+
+
+class CCSystem:
+    """Ground state, Hbar and Lambda for one Hamiltonian (the paper's pipeline steps 1-2)."""
+
+    def __init__(self, I, tol=1e-12, t=None, lam=None):
+        self.I, self.o, self.v = I, I.o, I.v
+        if t is None:
+            t1, t2, e, it = ccsd.solve(I, tol=tol)
+            self.ground_iters = it
+        else:
+            t1, t2 = t
+            e = ccsd.energy(I, t1, t2)
+        self.t1, self.t2, self.e_corr = t1, t2, e
+        self.H = hbar.Hbar(I, t1, t2)
+        d1, d2 = ccsd.denominators(I)
+        self.D = pack(d1.astype(np.complex128), d2.astype(np.complex128))
+        if lam is None:
+            lam = self.solve_lambda(tol=tol)
+        self.l1, self.l2 = lam
+
+    # -- products on packed unique-element vectors
+    def sigma_r(self, vec):
+        r1, r2 = unpack(vec, self.o, self.v)
+        return pack(*sigma.sigma_right(self.H, self.I, r1, r2))
+
+    def sigma_l(self, vec):
+        l1, l2 = unpack(vec, self.o, self.v)
+        return pack(*sigma.sigma_left(self.H, self.I, l1, l2))
+
+    def xi(self, X):
+        return pack(*props.xi(X, self.o, self.t1, self.t2))
+
+    def eta(self, X):
+        return pack(*props.eta(X, self.o, self.t1, self.t2, self.l1, self.l2))
+
+    def eta_eom(self, X):
+        return pack(*props.eta_eom(X, self.o, self.t1, self.t2, self.l1, self.l2))
+
+    def hessian(self, u):
+        u1, u2 = unpack(u, self.o, self.v)
+        return pack(*props.hessian_product(self.H, self.I, self.l1, self.l2, u1, u2))
+
+    def bdot(self, x, y):
+        """Bilinear product over unique excitations (packed vectors carry unique elements)."""
+        return np.sum(x * y)
+
+    def eta_ground(self):
+        I = self.I
+        e1 = I.f_ov + np.einsum("mnef,nf->me", I["oovv"], self.t1)
+        return pack(e1, I["oovv"])
+
+    def solve_lambda(self, tol=1e-12, maxit=200, diis=8):
+        """lambda A = -eta by Jacobi iterations on eta + lambda A with DIIS."""
+        eta = self.eta_ground()
+        lam = -eta / self.D
+        vecs, errs = [], []
+        for it in range(maxit):
+            res = eta + self.sigma_l(lam)
+            if np.linalg.norm(res) < tol:
+                self.lambda_iters = it
+                return unpack(lam, self.o, self.v)
+            lam = lam - res / self.D
+            vecs.append(lam)
+            errs.append(res / self.D)
+            if len(vecs) > diis:
+                vecs.pop(0)
+                errs.pop(0)
+            if len(vecs) >= 2:
+                m = len(vecs)
+                E = np.array(errs)
+                B = np.zeros((m + 1, m + 1), dtype=np.complex128)
+                B[:m, :m] = E.conj() @ E.T
+                B[m, :m] = B[:m, m] = -1
+                rhs = np.zeros(m + 1, dtype=np.complex128)
+                rhs[m] = -1
+                lam = np.linalg.solve(B, rhs)[:m] @ np.array(vecs)
+        raise RuntimeError("Lambda equations did not converge")
+
+    # -- dense references (tiny systems)
+    def dense_A(self):
+        n = self.D.size
+        A = np.zeros((n, n), dtype=np.complex128)
+        for k in range(n):
+            e = np.zeros(n, dtype=np.complex128)
+            e[k] = 1.0
+            A[:, k] = self.sigma_r(e)
+        return A
+
+    # -- response solves
+    def solve_dense(self, A, xi, z):
+        return -np.linalg.solve(A - z * np.eye(A.shape[0]), xi)
+
+    def davidson(self, xi, z, tol=1e-10, maxit=200, start="pivot"):
+        """Davidson solve of (A - z) t = -xi (SI Davidson scheme, steps 1-5)."""
+        D = self.D
+        if start == "pivot":
+            b0 = np.zeros_like(xi)
+            b0[np.argmax(np.abs(xi))] = 1.0
+        else:
+            b0 = -xi / (D - z)
+        B = [b0 / np.linalg.norm(b0)]
+        S = [self.sigma_r(B[0])]
+        for it in range(1, maxit + 1):
+            Bm, Sm = np.array(B), np.array(S)
+            G = Bm.conj() @ (Sm - z * Bm).T
+            C = -(Bm.conj() @ xi)
+            beta = np.linalg.solve(G, C)
+            t = beta @ Bm
+            r = beta @ (Sm - z * Bm) + xi
+            rn = np.linalg.norm(r)
+            if rn < tol:
+                return t, it, rn
+            c = -r / (D - z)
+            for _ in range(2):
+                for b in B:
+                    c = c - np.vdot(b, c) * b
+            cn = np.linalg.norm(c)
+            if cn < 1e-14:
+                return t, it, rn
+            B.append(c / cn)
+            S.append(self.sigma_r(B[-1]))
+        raise RuntimeError(f"Davidson did not converge (|r|={rn:.3e})")
+
+    def response(self, ops, zs, solver="davidson", tol=1e-11, A=None, half=False):
+        """<<X_a; X_b>>_z for all pairs (a, b) and all z: array [len(zs), nops, nops].
+
+        With half=True return the unsymmetrized f(z) instead (2 f(0) is the second derivative
+        of the CC energy with respect to static fields).
+        """
+        nops = len(ops)
+        eta = [self.eta(X) for X in ops]
+        xis = [self.xi(X) for X in ops]
+        cache = {}
+
+        def t_of(k, w):
+            key = (k, complex(w))
+            if key not in cache:
+                if solver == "dense":
+                    cache[key] = self.solve_dense(A, xis[k], w)
+                else:
+                    cache[key] = self.davidson(xis[k], w, tol=tol)[0]
+            return cache[key]
+
+        def f(z, a, b):
+            tx = t_of(a, -z)
+            ty = t_of(b, z)
+            return 0.5 * (self.bdot(eta[a], ty) + self.bdot(eta[b], tx) + self.bdot(self.hessian(tx), ty))
+
+        out = np.zeros((len(zs), nops, nops), dtype=np.complex128)
+        for k, z in enumerate(zs):
+            for a in range(nops):
+                for b in range(nops):
+                    out[k, a, b] = f(z, a, b) if half else f(z, a, b) + np.conj(f(-np.conj(z), a, b))
+        return out
+
+
+def polarizability(resp):
+    """alpha_xy = -<<mu_x; mu_y>>."""
+    return -resp
+
+
+def mean_alpha(alpha):
+    """Isotropic mean (alpha_xx + alpha_yy + alpha_zz)/3 (Sec. 5.2)."""
+    return np.trace(alpha, axis1=-2, axis2=-1) / 3.0
+
+
+def anisotropy(alpha):
+    """Delta alpha = alpha_zz - (alpha_xx + alpha_yy)/2 (Sec. 5.2)."""
+    return alpha[..., 2, 2] - 0.5 * (alpha[..., 0, 0] + alpha[..., 1, 1])
+
+
+def cross_section(omega, alpha):
+    """sigma(w) = 4 pi w / c Im mean-alpha(w) (Eq. abs_cpp, atomic units)."""
+    return 4.0 * np.pi * np.asarray(omega) / C_AU * np.imag(mean_alpha(alpha))

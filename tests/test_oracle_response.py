@@ -1,0 +1,109 @@
+"""The response chain pinned against exact sum-over-states, finite fields and closed forms."""
+import numpy as np
+import pytest
+import synth
+from oracle import ccsd, det, deriv, response as R
+from oracle.ints import Ints
+
+ZS = [0.0, 0.077, 0.2 + 0.01j, -0.15 + 0.005j]
+
+
+@pytest.fixture(scope="module")
+def two_electron():
+    inst = synth.make_instance(2, 8, seed=11, sd=0.05)
+    s = R.CCSystem(Ints.from_instance(inst))
+    sos, w = det.fci_response(inst.fock, synth.full_eri(inst), 2, inst.ops, ZS)
+    return inst, s, sos
+
+
+def test_two_electron_sum_over_states_dense(two_electron):
+    inst, s, sos = two_electron
+    got = s.response(inst.ops, ZS, solver="dense", A=s.dense_A())
+    assert np.abs(got - sos).max() < 1e-11 * np.abs(sos).max()
+
+
+def test_two_electron_sum_over_states_davidson(two_electron):
+    inst, s, sos = two_electron
+    got = s.response(inst.ops, ZS, solver="davidson", tol=1e-12)
+    assert np.abs(got - sos).max() < 1e-10 * np.abs(sos).max()
+
+
+def test_lambda_matches_dense_left_solve():
+    inst = synth.make_instance(2, 6, seed=3, sd=0.1)
+    s = R.CCSystem(Ints.from_instance(inst))
+    A = s.dense_A()
+    lam = -np.linalg.solve(A.T, s.eta_ground())
+    assert np.abs(deriv.pack(s.l1, s.l2) - lam).max() < 1e-11
+
+
+def test_finite_field_second_derivative():
+    """2 f(0) == d^2 E_CCSD / d e_x d e_y with H -> H + e_x X + e_y Y (Richardson, h = 1e-3)."""
+    inst = synth.make_instance(4, 8, seed=3, sd=0.05)
+    I = Ints.from_instance(inst)
+    X = inst.ops[:2]
+    f0 = R.CCSystem(I).response(X, [0.0], half=True, tol=1e-12)[0]
+
+    def E(ex, ey):
+        return ccsd.solve(I.with_fock(inst.fock + ex * X[0] + ey * X[1]), tol=1e-13)[2]
+
+    def d2(h):
+        return np.array([(E(h, 0) - 2 * E(0, 0) + E(-h, 0)) / h**2,
+                         (E(h, h) - E(h, -h) - E(-h, h) + E(-h, -h)) / (4 * h * h)])
+
+    rich = (4 * d2(1e-3) - d2(2e-3)) / 3
+    assert abs(rich[0] - 2 * f0[0, 0]) < 1e-7 * abs(f0[0, 0])
+    assert abs(rich[1] - 2 * f0[0, 1]) < 1e-7 * abs(f0[0, 0])
+
+
+def test_no_interaction_closed_form():
+    """V = 0: alpha_xy(z) = sum_ia [x_ia y_ai/(D_ia - z) + y_ia x_ai/(D_ia + z)]."""
+    o, v = 3, 6
+    inst = synth.make_instance(o, v, sd=0.0)
+    s = R.CCSystem(Ints.from_instance(inst))
+    a = R.polarizability(s.response(inst.ops, ZS, tol=1e-12))
+    eps = np.diag(inst.fock).real
+    Dia = eps[None, o:] - eps[:o, None]
+    for k, z in enumerate(ZS):
+        for x in range(3):
+            for y in range(3):
+                X, Y = inst.ops[x], inst.ops[y]
+                ref = np.sum(X[:o, o:] * Y[o:, :o].T / (Dia - z) + Y[:o, o:] * X[o:, :o].T / (Dia + z))
+                assert abs(a[k, x, y] - ref) < 1e-11
+
+
+@pytest.fixture(scope="module")
+def correlated():
+    inst = synth.make_instance(4, 10, seed=5, sd=0.05)
+    return inst, R.CCSystem(Ints.from_instance(inst))
+
+
+def test_symmetries(correlated):
+    inst, s = correlated
+    w, g = 0.12, 0.01
+    a = R.polarizability(s.response(inst.ops, [w + 1j * g, -w + 1j * g, 0.0], tol=1e-12))
+    assert np.abs(a[1] - a[0].conj()).max() < 1e-10           # alpha(-w + ig) = alpha(w + ig)*
+    assert np.abs(a[2] - a[2].T).max() < 1e-10                # static alpha is symmetric
+    assert np.abs(a[2].imag).max() < 1e-10                    # real without damping at w = 0
+    assert np.all(np.diag(a[0]).imag > 0)                     # absorption: Im alpha_xx > 0
+    assert np.all(np.diag(a[2]).real > 0)
+    a2 = R.polarizability(s.response(2.5 * inst.ops[:1], [w + 1j * g], tol=1e-12))
+    assert abs(a2[0, 0, 0] - 6.25 * a[0, 0, 0]) < 1e-10 * abs(a[0, 0, 0])
+
+
+def test_real_hamiltonian_limit():
+    """Real integrals and operators: alpha is real when gamma = 0."""
+    inst = synth.make_instance(3, 6, seed=9, sd=0.05)
+    for k, b in inst.blocks.items():
+        inst.blocks[k] = b.real.astype(complex)
+    inst.ops = inst.ops.real.astype(complex)
+    s = R.CCSystem(Ints.from_instance(inst))
+    a = R.polarizability(s.response(inst.ops, [0.0, 0.1], tol=1e-12))
+    assert np.abs(a.imag).max() < 1e-12
+
+
+def test_derived_quantities():
+    alpha = np.diag([1.0, 2.0, 6.0]).astype(complex)[None]
+    assert R.mean_alpha(alpha)[0] == 3.0
+    assert R.anisotropy(alpha)[0] == 4.5
+    alpha = alpha + 1j * np.eye(3)[None]
+    assert abs(R.cross_section([0.1], alpha)[0] - 4 * np.pi * 0.1 / 137.035999084) < 1e-15
