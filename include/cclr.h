@@ -1,0 +1,165 @@
+/*
+ * libcclr: relativistic CCSD linear response on one NVIDIA B300 (sm_103a).
+ *
+ * The library implements the hot path of arXiv 2307.14296 (Yuan, Halbert, Pototschnig, Papadopoulos,
+ * Coriani, Visscher, Pereira Gomes, "Formulation and implementation of frequency-dependent linear
+ * response properties with relativistic coupled cluster theory for GPU-accelerated computer
+ * architectures"): the CCSD Jacobian-times-vector products (sigma vectors) over complex,
+ * antisymmetrized spinor integrals, the damped first-order response solve
+ *     (A - (w + i gamma)) t^X = -xi^X                   (Sec. 2.4, Eq. LR response equation_cpp)
+ * the Lambda (left) solve  t-bar A = -eta             (Sec. 2.3), and the symmetric CC-CC response
+ * function <<X;Y>>_w                                    (Sec. 2.3, Eq. CC-CC response function).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Complex numbers are interleaved (re, im) doubles: cclr_c128.
+ *  - n_occ = o, n_vir = v; spinors 0..o-1 are occupied, o..o+v-1 virtual.
+ *  - A pair index over p<q inside one index range is P(p,q) = q*(q-1)/2 + p.
+ *  - Excitation vectors ("amplitude layout") hold unique elements only:
+ *        [ singles t_i^a at i*v + a  (o*v entries) | doubles t_ij^ab at P(i,j)*Pv + P(a,b) ]
+ *    with Pv = v(v-1)/2, Po = o(o-1)/2; length N = o*v + Po*Pv.  Sums over this layout count
+ *    each unique doubles element once.  Response-function contractions are bilinear (no
+ *    conjugation); the Hermitian product b^H c is used only inside the iterative solver.
+ *  - Unless a call says otherwise, pointers are HOST pointers; the caller keeps ownership and the
+ *    library copies what it needs.  Calls are synchronous with respect to the host.
+ *  - No call throws.  Every failure returns a status other than CCLR_OK and sets a message that
+ *    cclr_last_error() returns until the next call on the same context.
+ *  - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef CCLR_H
+#define CCLR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cclr_ctx cclr_ctx;
+typedef struct { double re, im; } cclr_c128;
+
+typedef enum {
+  CCLR_OK = 0,
+  CCLR_E_ARG = 1,      /* invalid argument (size, pointer, option) */
+  CCLR_E_NOCONV = 2,   /* iteration limit reached; the best iterate is kept and readable */
+  CCLR_E_OOM = 3,      /* device allocation failed */
+  CCLR_E_CUDA = 4,     /* a CUDA runtime call failed (message carries cudaGetErrorString) */
+  CCLR_E_STATE = 5,    /* call-order violation (e.g. cc_lambda before cc_ground) */
+  CCLR_E_TIMEOUT = 6   /* a device-side bounded wait expired */
+} cclr_status;
+
+/* Arithmetic used for the sigma-vector contractions (Sec. 2.4 of the paper uses complex FP64).
+ *  CCLR_FP64      complex FP64 everywhere (DFMA).
+ *  CCLR_TC_BF16X3 ladder and ring contractions on the tensor cores from split-BF16 operands
+ *                 (hi/lo, three products, FP32 accumulation); the response solve is wrapped in
+ *                 FP64 iterative refinement so converged results keep FP64 accuracy.         */
+typedef enum { CCLR_FP64 = 0, CCLR_TC_BF16X3 = 2 } cclr_precision;
+
+typedef struct {
+  double tol;          /* residual 2-norm target of the response solves (default 1e-8)        */
+  double ground_tol;   /* residual 2-norm target of the CCSD and Lambda equations (1e-10)      */
+  int maxit;           /* iteration limit of every iterative solve (default 100)               */
+  int max_subspace;    /* Davidson trial-space limit per right-hand side (default 48)          */
+  int precision;       /* a cclr_precision value (default CCLR_FP64)                           */
+  int batch;           /* right-hand sides per batched sigma launch, 0 = automatic             */
+} cclr_options;
+
+/* Fill *opt with the defaults listed above. */
+void cclr_default_options(cclr_options *opt);
+
+/* Create a context on CUDA device `device` (its stream, workspace and all device memory).
+ * opt may be NULL (defaults).  Returns CCLR_E_ARG for a bad device, CCLR_E_CUDA otherwise. */
+cclr_status cclr_create(cclr_ctx **out, int device, const cclr_options *opt);
+
+/* Free every device allocation of the context.  NULL is ignored. */
+void cclr_destroy(cclr_ctx *ctx);
+
+/* Message of the last failed call on this context (empty string if none).  The pointer stays
+ * valid until the next call on the context.  ctx may be NULL (returns a static message). */
+const char *cclr_last_error(const cclr_ctx *ctx);
+
+/* Load the Hamiltonian (paper Sec. 3 step 1 input: Fock matrix and the six integral classes of
+ * Sec. 4, "all six two-electron integral classes").
+ *   fock    (o+v)x(o+v) row-major, <p|f|q> at p*(o+v)+q.
+ *   blocks  six host arrays, antisymmetrized integrals <pq||rs>, in this order and layout:
+ *     [0] oooo <ij||kl>  [P(i,j)][P(k,l)]      [3] ovov <ia||jb>  [i][a][j][b]
+ *     [1] ooov <ij||ka>  [P(i,j)][k][a]        [4] ovvv <ia||bc>  [i][a][P(b,c)]
+ *     [2] oovv <ij||ab>  [P(i,j)][P(a,b)]      [5] vvvv <ab||cd>  [P(a,b)][P(c,d)]
+ *   All other index classes follow from <pq||rs> = -<qp||rs> = -<pq||sr> = conj(<rs||pq>).
+ * Requires o >= 2, v >= 2.  Discards any previous ground state, Lambda and response data. */
+cclr_status cclr_set_hamiltonian(cclr_ctx *ctx, int n_occ, int n_vir, const cclr_c128 *fock,
+                                 const cclr_c128 *const blocks[6]);
+
+/* Solve the ground-state CCSD equations Omega(t) = 0 (paper Sec. 3 step 1) from t = 0 and build
+ * the Hbar intermediates of the SI (step 2).  e_corr_out (may be NULL) receives the complex
+ * correlation energy, iters_out (may be NULL) the iteration count.  CCLR_E_NOCONV keeps the
+ * last amplitudes. */
+cclr_status cc_ground(cclr_ctx *ctx, cclr_c128 *e_corr_out, int *iters_out);
+
+/* Solve the Lambda equations t-bar^(0) A = -eta (Sec. 2.3) with left sigma vectors (SI Eqs.
+ * sigma_sin-ee-left, sigma_double-ee-left).  Requires cc_ground (else CCLR_E_STATE). */
+cclr_status cc_lambda(cclr_ctx *ctx, int *iters_out);
+
+/* Damped linear response (Sec. 2.4 and SI Davidson scheme): for every operator X_k (n_ops
+ * Hermitian (o+v)x(o+v) row-major host matrices, contiguous) and every frequency omegas[f] with
+ * damping gamma >= 0, solve (A - z) t = -xi^X for the shifts z in {w+ig, -w+ig, w-ig, -w-ig}
+ * that the response function needs (duplicates removed).  iters_out (may be NULL) receives
+ * n_ops*n_freq iteration counts (max over the shifts of that pair).  The solutions stay in the
+ * context.  Requires cc_lambda. */
+cclr_status cc_lr_solve(cclr_ctx *ctx, int n_ops, const cclr_c128 *ops, int n_freq,
+                        const double *omegas, double gamma, int *iters_out);
+
+/* The symmetric CC-CC response function (Sec. 2.3 Eq. CC-CC response function with the damped
+ * frequency of Sec. 2.4): out[f][x][y] = <<X_x;X_y>>_{w_f + i gamma}, out holds
+ * n_freq*n_ops*n_ops values.  The polarizability is alpha = -<<mu;mu>>.  Requires cc_lr_solve. */
+cclr_status cc_response_function(cclr_ctx *ctx, cclr_c128 *out);
+
+/* ---------------- component entry points (parity tests, the autograd shim) ------------------ */
+
+/* Which amplitude set: ground T, Lambda, or a response solution. */
+enum { CCLR_AMP_T = 0, CCLR_AMP_LAMBDA = 1 };
+
+/* Copy amplitudes out in the amplitude layout (n must be o*v + Po*Pv). */
+cclr_status cclr_get_amplitudes(cclr_ctx *ctx, int which, cclr_c128 *dst, size_t n);
+
+/* Set T (and rebuild the Hbar intermediates) or Lambda from host data in the amplitude layout,
+ * bypassing cc_ground / cc_lambda (used to test contractions at arbitrary amplitudes). */
+cclr_status cclr_set_amplitudes(cclr_ctx *ctx, int which, const cclr_c128 *src, size_t n);
+
+/* Response solution t^X(z) for operator k, frequency f and shift s (0: w+ig, 1: -w+ig,
+ * 2: w-ig, 3: -w-ig) after cc_lr_solve, in the amplitude layout. */
+cclr_status cclr_get_response_vector(cclr_ctx *ctx, int k, int f, int s, cclr_c128 *dst, size_t n);
+
+/* Sigma vectors for nvec vectors in the amplitude layout (side 0: right, A r, SI Eqs.
+ * sigma_sin-ee / sigma_double-ee; side 1: left, l A, SI Eqs. sigma_sin-ee-left /
+ * sigma_double-ee-left).  on_device != 0 means `in` and `out` are device pointers on the
+ * context's device (e.g. from torch tensors); otherwise host pointers.  Uses the current T
+ * (and its Hbar).  precision selects the contraction arithmetic (cclr_precision). */
+cclr_status cclr_sigma(cclr_ctx *ctx, int side, int nvec, const cclr_c128 *in, cclr_c128 *out,
+                       int on_device, int precision);
+
+/* CCSD residual Omega(T) at the current T (amplitude layout, host). */
+cclr_status cclr_residual(cclr_ctx *ctx, cclr_c128 *out, cclr_c128 *e_corr_out);
+
+/* xi^X (SI Eq. xi-equation), eta^X (SI Eq. eta-equation) and, with eom != 0, the EOM eta^X of
+ * the SI, for one Hermitian operator X (host (o+v)^2).  eta needs Lambda. */
+cclr_status cclr_xi(cclr_ctx *ctx, const cclr_c128 *op, cclr_c128 *out);
+cclr_status cclr_eta(cclr_ctx *ctx, const cclr_c128 *op, int eom, cclr_c128 *out);
+
+/* CC Hessian products (u F) (SI, "(t^X F)" working equations) for nvec vectors; needs Lambda. */
+cclr_status cclr_hessian(cclr_ctx *ctx, int nvec, const cclr_c128 *u, cclr_c128 *out, int on_device);
+
+/* Per-call statistics of the last cc_* call: sigma launches and vectors, seconds spent. */
+typedef struct {
+  long sigma_calls, sigma_vectors;
+  double sigma_seconds, total_seconds;
+  long kernel_launches;
+  double max_residual;
+} cclr_stats;
+cclr_status cclr_get_stats(cclr_ctx *ctx, cclr_stats *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CCLR_H */

@@ -1,0 +1,261 @@
+"""B300-native relativistic CCSD linear response (arXiv 2307.14296), Python binding of libcclr.
+
+Thin ctypes layer over the C ABI in include/cclr.h: it converts numpy arrays (host) or torch CUDA
+tensors (device) into pointers and sizes and turns status codes into exceptions.  Every step of
+the computation runs in the CUDA library; there is no Python or CPU fallback, and importing this
+package fails if libcclr.so has not been built (python -m paper_2307_14296_b300.build).
+
+Vector layout ("amplitude layout"): [singles t_i^a at i*v + a | doubles t_ij^ab at
+P(i,j)*Pv + P(a,b)] with P(p,q) = q*(q-1)/2 + p for p < q; unique elements only.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcclr.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        "libcclr.so is missing: build the CUDA library with `python -m paper_2307_14296_b300.build` "
+        "(there is no CPU fallback)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+CCLR_OK, CCLR_E_ARG, CCLR_E_NOCONV, CCLR_E_OOM, CCLR_E_CUDA, CCLR_E_STATE, CCLR_E_TIMEOUT = range(7)
+FP64, TC_BF16X3 = 0, 2
+AMP_T, AMP_LAMBDA = 0, 1
+EXPORTS = (
+    "cclr_default_options", "cclr_create", "cclr_destroy", "cclr_last_error", "cclr_set_hamiltonian",
+    "cc_ground", "cc_lambda", "cc_lr_solve", "cc_response_function", "cclr_get_amplitudes",
+    "cclr_set_amplitudes", "cclr_get_response_vector", "cclr_sigma", "cclr_residual", "cclr_xi",
+    "cclr_eta", "cclr_hessian", "cclr_get_stats",
+)
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("ground_tol", ctypes.c_double), ("maxit", ctypes.c_int),
+                ("max_subspace", ctypes.c_int), ("precision", ctypes.c_int), ("batch", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("sigma_calls", ctypes.c_long), ("sigma_vectors", ctypes.c_long),
+                ("sigma_seconds", ctypes.c_double), ("total_seconds", ctypes.c_double),
+                ("kernel_launches", ctypes.c_long), ("max_residual", ctypes.c_double)]
+
+
+_vp, _i, _d, _sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+_sig = {
+    "cclr_default_options": (None, [ctypes.POINTER(Options)]),
+    "cclr_create": (_i, [ctypes.POINTER(_vp), _i, ctypes.POINTER(Options)]),
+    "cclr_destroy": (None, [_vp]),
+    "cclr_last_error": (ctypes.c_char_p, [_vp]),
+    "cclr_set_hamiltonian": (_i, [_vp, _i, _i, _vp, ctypes.POINTER(_vp)]),
+    "cc_ground": (_i, [_vp, _vp, ctypes.POINTER(_i)]),
+    "cc_lambda": (_i, [_vp, ctypes.POINTER(_i)]),
+    "cc_lr_solve": (_i, [_vp, _i, _vp, _i, _vp, _d, _vp]),
+    "cc_response_function": (_i, [_vp, _vp]),
+    "cclr_get_amplitudes": (_i, [_vp, _i, _vp, _sz]),
+    "cclr_set_amplitudes": (_i, [_vp, _i, _vp, _sz]),
+    "cclr_get_response_vector": (_i, [_vp, _i, _i, _i, _vp, _sz]),
+    "cclr_sigma": (_i, [_vp, _i, _i, _vp, _vp, _i, _i]),
+    "cclr_residual": (_i, [_vp, _vp, _vp]),
+    "cclr_xi": (_i, [_vp, _vp, _vp]),
+    "cclr_eta": (_i, [_vp, _vp, _i, _vp]),
+    "cclr_hessian": (_i, [_vp, _i, _vp, _vp, _i]),
+    "cclr_get_stats": (_i, [_vp, ctypes.POINTER(Stats)]),
+}
+for _name, (_res, _args) in _sig.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+class CCLRError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"libcclr status {status}: {msg}")
+        self.status = status
+
+
+def default_options(**kw) -> Options:
+    o = Options()
+    _lib.cclr_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def _c128(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.complex128)
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(_vp)
+
+
+def _is_torch_cuda(x) -> bool:
+    return hasattr(x, "is_cuda") and x.is_cuda
+
+
+class Context:
+    """One libcclr context (device memory, stream, Hamiltonian, amplitudes, response data)."""
+
+    def __init__(self, device: int = 0, **options):
+        self._h = _vp()
+        self.options = default_options(**options)
+        st = _lib.cclr_create(ctypes.byref(self._h), device, ctypes.byref(self.options))
+        if st != CCLR_OK:
+            raise CCLRError(st, "cclr_create failed (no CUDA device?)")
+        self.n_occ = self.n_vir = 0
+
+    def close(self):
+        if self._h:
+            _lib.cclr_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != CCLR_OK:
+            raise CCLRError(st, _lib.cclr_last_error(self._h).decode())
+
+    @property
+    def N(self) -> int:
+        o, v = self.n_occ, self.n_vir
+        return o * v + (o * (o - 1) // 2) * (v * (v - 1) // 2)
+
+    # ---- problem statement
+    def cclr_set_hamiltonian(self, n_occ, n_vir, fock, blocks):
+        """fock (n x n) and the six packed integral classes (oooo, ooov, oovv, ovov, ovvv, vvvv)."""
+        fock = _c128(fock)
+        bl = [_c128(b) for b in blocks]
+        arr = (_vp * 6)(*[b.ctypes.data for b in bl])
+        self._check(_lib.cclr_set_hamiltonian(self._h, n_occ, n_vir, _ptr(fock), arr))
+        self.n_occ, self.n_vir = n_occ, n_vir
+
+    def cc_ground(self):
+        e = np.zeros(1, np.complex128)
+        it = _i()
+        self._check(_lib.cc_ground(self._h, _ptr(e), ctypes.byref(it)))
+        return complex(e[0]), it.value
+
+    def cc_lambda(self):
+        it = _i()
+        self._check(_lib.cc_lambda(self._h, ctypes.byref(it)))
+        return it.value
+
+    def cc_lr_solve(self, ops, omegas, gamma):
+        ops = _c128(ops)
+        om = np.ascontiguousarray(omegas, dtype=np.float64)
+        its = np.zeros(ops.shape[0] * om.size, np.int32)
+        self._check(_lib.cc_lr_solve(self._h, ops.shape[0], _ptr(ops), om.size, _ptr(om), float(gamma), _ptr(its)))
+        self._nops, self._nfreq = ops.shape[0], om.size
+        return its.reshape(ops.shape[0], om.size)
+
+    def cc_response_function(self):
+        out = np.zeros((self._nfreq, self._nops, self._nops), np.complex128)
+        self._check(_lib.cc_response_function(self._h, _ptr(out)))
+        return out
+
+    # ---- components
+    def cclr_get_amplitudes(self, which=AMP_T):
+        out = np.zeros(self.N, np.complex128)
+        self._check(_lib.cclr_get_amplitudes(self._h, which, _ptr(out), out.size))
+        return out
+
+    def cclr_set_amplitudes(self, which, vec):
+        vec = _c128(vec)
+        self._check(_lib.cclr_set_amplitudes(self._h, which, _ptr(vec), vec.size))
+
+    def cclr_get_response_vector(self, k, f, s):
+        out = np.zeros(self.N, np.complex128)
+        self._check(_lib.cclr_get_response_vector(self._h, k, f, s, _ptr(out), out.size))
+        return out
+
+    def cclr_sigma(self, vecs, side=0, precision=FP64, out=None):
+        """Right (side 0) or left (side 1) sigma of a batch [nvec, N] (numpy or torch CUDA)."""
+        if _is_torch_cuda(vecs):
+            import torch
+            assert vecs.dtype == torch.complex128 and vecs.is_contiguous()
+            nvec = vecs.shape[0] if vecs.dim() == 2 else 1
+            if out is None:
+                out = torch.empty_like(vecs)
+            self._check(_lib.cclr_sigma(self._h, side, nvec, _vp(vecs.data_ptr()), _vp(out.data_ptr()), 1, precision))
+            return out
+        v = _c128(vecs)
+        nvec = v.shape[0] if v.ndim == 2 else 1
+        res = np.zeros_like(v)
+        self._check(_lib.cclr_sigma(self._h, side, nvec, _ptr(v), _ptr(res), 0, precision))
+        return res
+
+    def cclr_residual(self):
+        out = np.zeros(self.N, np.complex128)
+        e = np.zeros(1, np.complex128)
+        self._check(_lib.cclr_residual(self._h, _ptr(out), _ptr(e)))
+        return out, complex(e[0])
+
+    def cclr_xi(self, op):
+        op = _c128(op)
+        out = np.zeros(self.N, np.complex128)
+        self._check(_lib.cclr_xi(self._h, _ptr(op), _ptr(out)))
+        return out
+
+    def cclr_eta(self, op, eom=False):
+        op = _c128(op)
+        out = np.zeros(self.N, np.complex128)
+        self._check(_lib.cclr_eta(self._h, _ptr(op), int(eom), _ptr(out)))
+        return out
+
+    def cclr_hessian(self, vecs):
+        if _is_torch_cuda(vecs):
+            import torch
+            nvec = vecs.shape[0] if vecs.dim() == 2 else 1
+            out = torch.empty_like(vecs)
+            self._check(_lib.cclr_hessian(self._h, nvec, _vp(vecs.data_ptr()), _vp(out.data_ptr()), 1))
+            return out
+        v = _c128(vecs)
+        nvec = v.shape[0] if v.ndim == 2 else 1
+        res = np.zeros_like(v)
+        self._check(_lib.cclr_hessian(self._h, nvec, _ptr(v), _ptr(res), 0))
+        return res
+
+    def cclr_get_stats(self) -> dict:
+        s = Stats()
+        self._check(_lib.cclr_get_stats(self._h, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in Stats._fields_}
+
+
+# module-level names of the C ABI's problem-statement calls
+def cclr_create(device=0, **options) -> Context:
+    return Context(device, **options)
+
+
+def cclr_set_hamiltonian(ctx, n_occ, n_vir, fock, blocks):
+    return ctx.cclr_set_hamiltonian(n_occ, n_vir, fock, blocks)
+
+
+def cc_ground(ctx):
+    return ctx.cc_ground()
+
+
+def cc_lambda(ctx):
+    return ctx.cc_lambda()
+
+
+def cc_lr_solve(ctx, ops, omegas, gamma):
+    return ctx.cc_lr_solve(ops, omegas, gamma)
+
+
+def cc_response_function(ctx):
+    return ctx.cc_response_function()
+
+
+def library_path() -> str:
+    return LIB_PATH

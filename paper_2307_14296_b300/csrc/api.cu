@@ -1,0 +1,395 @@
+// The C ABI of libcclr (declared in include/cclr.h).  Every entry point catches all C++
+// exceptions and returns a status; the message is kept in the context for cclr_last_error().
+#include "ctx.h"
+#include <chrono>
+#include <cstdlib>
+
+using namespace cclr;
+
+struct cclr_ctx {
+  Ctx c;
+};
+
+namespace {
+
+double wall() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+template <class F>
+cclr_status guard(cclr_ctx* h, F&& fn) {
+  if (!h) return CCLR_E_ARG;
+  Ctx& c = h->c;
+  c.err.clear();
+  c.stats = cclr_stats{};
+  const long l0 = c.launches;
+  const double t0 = wall();
+  cclr_status st = CCLR_OK;
+  try {
+    CCLR_CK(cudaSetDevice(c.device));
+    fn(c);
+    CCLR_CK(cudaStreamSynchronize(c.stream));
+  } catch (const Error& e) {
+    c.err = e.what();
+    st = e.st;
+  } catch (const std::exception& e) {
+    c.err = e.what();
+    st = CCLR_E_ARG;
+  }
+  c.stats.total_seconds = wall() - t0;
+  c.stats.kernel_launches = c.launches - l0;
+  return st;
+}
+
+void free_all(Ctx& c) {
+  for (void* p : c.persistent) cudaFree(p);
+  c.persistent.clear();
+  c.named.clear();
+  c.rd = ResponseData();
+  c.fock = c.oooo = c.ooov = c.oovv = c.ovov = c.ovvv = c.vvvv_p = c.oovv_p = c.ovvv_p = nullptr;
+  c.D = nullptr;
+  c.po = c.pv = nullptr;
+  c.t = c.t2 = c.lam = c.l2 = nullptr;
+  c.Fae = c.Fmi = c.Fme = c.Wmnij = c.Wmnij_p = c.Wabef_p = c.Wmbej = c.WringR = c.WringL = nullptr;
+  c.Wmnie = c.Wamef = c.Wmbij = c.Wabei = c.tau = nullptr;
+  c.have_ham = c.have_t = c.have_lambda = c.have_hbar = false;
+  if (c.ws.base) { cudaFree(c.ws.base); c.ws = Arena(); }
+}
+
+void upload(Ctx& c, cplx* dst, const void* src, int64_t n) {
+  CCLR_CK(cudaMemcpyAsync(dst, src, sizeof(cplx) * n, cudaMemcpyHostToDevice, c.stream));
+}
+
+// copy in/out helpers for entry points that accept host or device pointers
+struct IO {
+  Ctx& c;
+  const cplx* in;
+  cplx* out;
+  cplx* dout;
+  int64_t nin, nout;
+  bool dev;
+  IO(Ctx& cc, const void* i, void* o, int64_t ni, int64_t no, bool on_device)
+      : c(cc), nin(ni), nout(no), dev(on_device) {
+    if (dev) {
+      in = (const cplx*)i;
+      out = dout = (cplx*)o;
+    } else {
+      cplx* di = c.ws.cplxs(ni);
+      if (ni) upload(c, di, i, ni);
+      in = di;
+      dout = c.ws.cplxs(no);
+      out = (cplx*)o;
+    }
+  }
+  void finish() {
+    if (!dev) {
+      CCLR_CK(cudaMemcpyAsync(out, dout, sizeof(cplx) * nout, cudaMemcpyDeviceToHost, c.stream));
+      c.sync();
+    }
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+void cclr_default_options(cclr_options* opt) {
+  if (!opt) return;
+  opt->tol = 1e-8;
+  opt->ground_tol = 1e-10;
+  opt->maxit = 100;
+  opt->max_subspace = 96;
+  opt->precision = CCLR_FP64;
+  opt->batch = 0;
+}
+
+cclr_status cclr_create(cclr_ctx** out, int device, const cclr_options* opt) {
+  if (!out) return CCLR_E_ARG;
+  *out = nullptr;
+  int nd = 0;
+  if (cudaGetDeviceCount(&nd) != cudaSuccess || device < 0 || device >= nd) return CCLR_E_ARG;
+  cclr_ctx* h = new cclr_ctx();
+  Ctx& c = h->c;
+  c.device = device;
+  if (opt) c.opt = *opt; else cclr_default_options(&c.opt);
+  if (c.opt.precision != CCLR_FP64 && c.opt.precision != CCLR_TC_BF16X3) { delete h; return CCLR_E_ARG; }
+  if (cudaSetDevice(device) != cudaSuccess || cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking) != cudaSuccess) {
+    delete h;
+    return CCLR_E_CUDA;
+  }
+  c.L.s = c.stream;
+  c.L.count = &c.launches;
+  *out = h;
+  return CCLR_OK;
+}
+
+void cclr_destroy(cclr_ctx* h) {
+  if (!h) return;
+  cudaSetDevice(h->c.device);
+  free_all(h->c);
+  if (h->c.stream) cudaStreamDestroy(h->c.stream);
+  delete h;
+}
+
+const char* cclr_last_error(const cclr_ctx* h) {
+  if (!h) return "null context";
+  return h->c.err.c_str();
+}
+
+cclr_status cclr_set_hamiltonian(cclr_ctx* h, int n_occ, int n_vir, const cclr_c128* fock,
+                                 const cclr_c128* const blocks[6]) {
+  return guard(h, [&](Ctx& c) {
+    CCLR_REQUIRE(n_occ >= 2 && n_vir >= 2, CCLR_E_ARG, "need n_occ >= 2 and n_vir >= 2");
+    CCLR_REQUIRE(fock && blocks, CCLR_E_ARG, "null Hamiltonian pointer");
+    for (int k = 0; k < 6; ++k) CCLR_REQUIRE(blocks[k], CCLR_E_ARG, "null integral block");
+    free_all(c);
+    const int64_t o = n_occ, v = n_vir, n = o + v;
+    c.o = n_occ; c.v = n_vir; c.n = (int)n;
+    c.Po = o * (o - 1) / 2; c.Pv = v * (v - 1) / 2;
+    c.Ns = o * v; c.Nd = c.Po * c.Pv; c.N = c.Ns + c.Nd;
+    // workspace: a fixed fraction of free device memory (CCLR_WORKSPACE_GB overrides)
+    size_t fr = 0, tot = 0;
+    CCLR_CK(cudaMemGetInfo(&fr, &tot));
+    size_t ws = (size_t)(0.35 * (double)fr);
+    if (const char* e = std::getenv("CCLR_WORKSPACE_GB")) ws = (size_t)(atof(e) * (1ull << 30));
+    CCLR_CK(cudaMalloc((void**)&c.ws.base, ws));
+    c.ws.cap = ws;
+    c.ws.top = 0;
+    // pair tables
+    std::vector<int2> po(c.Po), pv(c.Pv);
+    int64_t k = 0;
+    for (int q = 1; q < n_occ; ++q) for (int p = 0; p < q; ++p) po[k++] = make_int2(p, q);
+    k = 0;
+    for (int q = 1; q < n_vir; ++q) for (int p = 0; p < q; ++p) pv[k++] = make_int2(p, q);
+    CCLR_CK(cudaMalloc((void**)&c.po, sizeof(int2) * std::max<int64_t>(1, c.Po)));
+    CCLR_CK(cudaMalloc((void**)&c.pv, sizeof(int2) * std::max<int64_t>(1, c.Pv)));
+    c.persistent.push_back(c.po);
+    c.persistent.push_back(c.pv);
+    CCLR_CK(cudaMemcpy(c.po, po.data(), sizeof(int2) * c.Po, cudaMemcpyHostToDevice));
+    CCLR_CK(cudaMemcpy(c.pv, pv.data(), sizeof(int2) * c.Pv, cudaMemcpyHostToDevice));
+    // Hamiltonian
+    c.fock = c.dalloc(n * n);
+    upload(c, c.fock, fock, n * n);
+    c.oooo = c.dalloc(o * o * o * o);
+    c.ooov = c.dalloc(o * o * o * v);
+    c.oovv = c.dalloc(o * o * v * v);
+    c.ovov = c.dalloc(o * v * o * v);
+    c.ovvv = c.dalloc(o * v * v * v);
+    c.vvvv_p = c.dalloc(c.Pv * c.Pv);
+    c.oovv_p = c.dalloc(c.Po * c.Pv);
+    c.ovvv_p = c.dalloc(o * v * c.Pv);
+    {
+      Scope sc(c.ws);
+      cplx* tmp = c.ws.cplxs(c.Po * c.Po);
+      upload(c, tmp, blocks[0], c.Po * c.Po);
+      unpack_doubles(c.L, tmp, c.Po * c.Po, Tensor::make(c.oooo, {1, o, o, o, o}), n_occ, n_occ);
+    }
+    {
+      Scope sc(c.ws);
+      cplx* tmp = c.ws.cplxs(c.Po * o * v);
+      upload(c, tmp, blocks[1], c.Po * o * v);
+      cplx* tr = c.ws.cplxs(c.Po * o * v);
+      permute(c.L, Tensor::make(tmp, {c.Po, o * v}).perm({1, 0}), Tensor::make(tr, {o * v, c.Po}), cx(1), false);
+      // full[i][j][k][a] viewed as (R=(k,a), i, j)
+      Tensor dst = Tensor::make(c.ooov, {o, o, o * v}).perm({2, 0, 1});
+      unpack2(c.L, tr, c.Po, dst);
+    }
+    upload(c, c.oovv_p, blocks[2], c.Po * c.Pv);
+    unpack_doubles(c.L, c.oovv_p, c.Nd, Tensor::make(c.oovv, {1, o, o, v, v}), n_occ, n_vir);
+    upload(c, c.ovov, blocks[3], o * v * o * v);
+    upload(c, c.ovvv_p, blocks[4], o * v * c.Pv);
+    unpack2(c.L, c.ovvv_p, c.Pv, Tensor::make(c.ovvv, {o * v, v, v}));
+    upload(c, c.vvvv_p, blocks[5], c.Pv * c.Pv);
+    c.D = (double*)c.dalloc((c.N + 1) / 2 + 1);
+    c.t = c.dalloc(c.N);
+    c.t2 = c.dalloc(o * o * v * v);
+    c.lam = c.dalloc(c.N);
+    c.l2 = c.dalloc(o * o * v * v);
+    fill_zero(c.L, c.t, c.N);
+    fill_zero(c.L, c.t2, o * o * v * v);
+    c.sync();
+    build_denominators(c);
+    c.have_ham = true;
+  });
+}
+
+cclr_status cc_ground(cclr_ctx* h, cclr_c128* e_corr_out, int* iters_out) {
+  int its = 0;
+  cclr_status st = guard(h, [&](Ctx& c) {
+    CCLR_REQUIRE(c.have_ham, CCLR_E_STATE, "cc_ground before cclr_set_hamiltonian");
+    c.have_lambda = false;
+    c.rd = ResponseData();
+    try {
+      its = solve_ground(c);
+    } catch (const Error& e) {
+      if (e.st == CCLR_E_NOCONV) build_hbar(c);
+      throw;
+    }
+    build_hbar(c);
+  });
+  if (h && (st == CCLR_OK || st == CCLR_E_NOCONV)) {
+    if (e_corr_out) { e_corr_out->re = h->c.e_corr.real(); e_corr_out->im = h->c.e_corr.imag(); }
+    if (iters_out) *iters_out = its;
+  }
+  return st;
+}
+
+cclr_status cc_lambda(cclr_ctx* h, int* iters_out) {
+  int its = 0;
+  cclr_status st = guard(h, [&](Ctx& c) {
+    CCLR_REQUIRE(c.have_hbar, CCLR_E_STATE, "cc_lambda before cc_ground");
+    its = solve_lambda(c);
+  });
+  if (iters_out) *iters_out = its;
+  return st;
+}
+
+cclr_status cc_lr_solve(cclr_ctx* h, int n_ops, const cclr_c128* ops, int n_freq, const double* omegas, double gamma,
+                        int* iters_out) {
+  return guard(h, [&](Ctx& c) {
+    CCLR_REQUIRE(c.have_lambda, CCLR_E_STATE, "cc_lr_solve before cc_lambda");
+    CCLR_REQUIRE(n_ops >= 1 && n_freq >= 1 && ops && omegas && gamma >= 0.0, CCLR_E_ARG, "bad cc_lr_solve arguments");
+    lr_solve(c, n_ops, (const cplx*)ops, n_freq, omegas, gamma, iters_out);
+  });
+}
+
+cclr_status cc_response_function(cclr_ctx* h, cclr_c128* out) {
+  return guard(h, [&](Ctx& c) {
+    CCLR_REQUIRE(out, CCLR_E_ARG, "null output");
+    response_function(c, (cplx*)out);
+  });
+}
+
+cclr_status cclr_get_amplitudes(cclr_ctx* h, int which, cclr_c128* dst, size_t n) {
+  return guard(h, [&](Ctx& c) {
+    CCLR_REQUIRE(dst && (int64_t)n == c.N, CCLR_E_ARG, "amplitude buffer length must be o*v + Po*Pv");
+    const cplx* src = which == CCLR_AMP_T ? c.t : which == CCLR_AMP_LAMBDA ? c.lam : nullptr;
+    CCLR_REQUIRE(src, CCLR_E_ARG, "unknown amplitude set");
+    CCLR_REQUIRE(which == CCLR_AMP_T ? c.have_t : c.have_lambda, CCLR_E_STATE, "amplitudes not available");
+    CCLR_CK(cudaMemcpyAsync(dst, src, sizeof(cplx) * n, cudaMemcpyDeviceToHost, c.stream));
+  });
+}
+
+cclr_status cclr_set_amplitudes(cclr_ctx* h, int which, const cclr_c128* src, size_t n) {
+  return guard(h, [&](Ctx& c) {
+    CCLR_REQUIRE(c.have_ham, CCLR_E_STATE, "no Hamiltonian");
+    CCLR_REQUIRE(src && (int64_t)n == c.N, CCLR_E_ARG, "amplitude buffer length must be o*v + Po*Pv");
+    if (which == CCLR_AMP_T) {
+      upload(c, c.t, src, c.N);
+      expand_t2(c, c.t + c.Ns, c.t2, 1);
+      c.e_corr = ccsd_energy(c);
+      c.have_t = true;
+      c.have_lambda = false;
+      c.named.erase("F.ready");
+      build_hbar(c);
+    } else if (which == CCLR_AMP_LAMBDA) {
+      CCLR_REQUIRE(c.have_hbar, CCLR_E_STATE, "set T before Lambda");
+      upload(c, c.lam, src, c.N);
+      expand_t2(c, c.lam + c.Ns, c.l2, 1);
+      c.have_lambda = true;
+      c.named.erase("F.ready");
+    } else {
+      throw Error(CCLR_E_ARG, "unknown amplitude set");
+    }
+  });
+}
+
+cclr_status cclr_get_response_vector(cclr_ctx* h, int k, int f, int s, cclr_c128* dst, size_t n) {
+  return guard(h, [&](Ctx& c) {
+    ResponseData& rd = c.rd;
+    CCLR_REQUIRE(rd.solved, CCLR_E_STATE, "no response solution");
+    CCLR_REQUIRE(k >= 0 && k < rd.n_ops && f >= 0 && f < rd.n_freq && s >= 0 && s < 4 && (int64_t)n == c.N && dst,
+                 CCLR_E_ARG, "bad response-vector index");
+    const int maxL = std::max(8, c.opt.max_subspace);
+    Scope sc(c.ws);
+    cplx* b = c.ws.cplxs(maxL);
+    cplx* t = c.ws.cplxs(c.N);
+    const zc* beta = &rd.beta[k][(size_t)rd.shift_of[(size_t)f * 4 + s] * maxL];
+    CCLR_CK(cudaMemcpyAsync(b, beta, sizeof(cplx) * rd.nb[k], cudaMemcpyHostToDevice, c.stream));
+    lincomb(c.L, c.N, rd.nb[k], rd.basis[k], c.N, b, t, false);
+    CCLR_CK(cudaMemcpyAsync(dst, t, sizeof(cplx) * n, cudaMemcpyDeviceToHost, c.stream));
+    c.sync();
+  });
+}
+
+cclr_status cclr_sigma(cclr_ctx* h, int side, int nvec, const cclr_c128* in, cclr_c128* out, int on_device,
+                       int precision) {
+  return guard(h, [&](Ctx& c) {
+    CCLR_REQUIRE(c.have_hbar, CCLR_E_STATE, "sigma needs T (cc_ground or cclr_set_amplitudes)");
+    CCLR_REQUIRE(nvec >= 1 && in && out && (side == 0 || side == 1), CCLR_E_ARG, "bad sigma arguments");
+    CCLR_REQUIRE(precision == CCLR_FP64 || precision == CCLR_TC_BF16X3, CCLR_E_ARG, "unknown precision");
+    const int saved = c.opt.precision;
+    c.opt.precision = precision;
+    try {
+      Scope sc(c.ws);
+      IO io(c, in, out, (int64_t)nvec * c.N, (int64_t)nvec * c.N, on_device != 0);
+      const double t0 = wall();
+      if (side == 0) sigma_right(c, nvec, io.in, io.dout);
+      else sigma_left(c, nvec, io.in, io.dout);
+      c.sync();
+      c.stats.sigma_seconds += wall() - t0;
+      io.finish();
+    } catch (...) {
+      c.opt.precision = saved;
+      throw;
+    }
+    c.opt.precision = saved;
+  });
+}
+
+cclr_status cclr_residual(cclr_ctx* h, cclr_c128* out, cclr_c128* e_corr_out) {
+  return guard(h, [&](Ctx& c) {
+    CCLR_REQUIRE(c.have_t && out, CCLR_E_STATE, "no amplitudes");
+    Scope sc(c.ws);
+    cplx* R = c.ws.cplxs(c.N);
+    ccsd_residual(c, R);
+    CCLR_CK(cudaMemcpyAsync(out, R, sizeof(cplx) * c.N, cudaMemcpyDeviceToHost, c.stream));
+    c.sync();
+    if (e_corr_out) { zc e = ccsd_energy(c); e_corr_out->re = e.real(); e_corr_out->im = e.imag(); }
+  });
+}
+
+cclr_status cclr_xi(cclr_ctx* h, const cclr_c128* op, cclr_c128* out) {
+  return guard(h, [&](Ctx& c) {
+    CCLR_REQUIRE(c.have_t && op && out, CCLR_E_STATE, "xi needs T");
+    Scope sc(c.ws);
+    cplx* X = c.ws.cplxs((int64_t)c.n * c.n);
+    upload(c, X, op, (int64_t)c.n * c.n);
+    cplx* r = c.ws.cplxs(c.N);
+    xi_vec(c, X, r);
+    CCLR_CK(cudaMemcpyAsync(out, r, sizeof(cplx) * c.N, cudaMemcpyDeviceToHost, c.stream));
+    c.sync();
+  });
+}
+
+cclr_status cclr_eta(cclr_ctx* h, const cclr_c128* op, int eom, cclr_c128* out) {
+  return guard(h, [&](Ctx& c) {
+    CCLR_REQUIRE(c.have_lambda && op && out, CCLR_E_STATE, "eta needs Lambda");
+    Scope sc(c.ws);
+    cplx* X = c.ws.cplxs((int64_t)c.n * c.n);
+    upload(c, X, op, (int64_t)c.n * c.n);
+    cplx* r = c.ws.cplxs(c.N);
+    eta_vec(c, X, eom != 0, r);
+    CCLR_CK(cudaMemcpyAsync(out, r, sizeof(cplx) * c.N, cudaMemcpyDeviceToHost, c.stream));
+    c.sync();
+  });
+}
+
+cclr_status cclr_hessian(cclr_ctx* h, int nvec, const cclr_c128* u, cclr_c128* out, int on_device) {
+  return guard(h, [&](Ctx& c) {
+    CCLR_REQUIRE(c.have_lambda && u && out && nvec >= 1, CCLR_E_STATE, "hessian needs Lambda");
+    Scope sc(c.ws);
+    IO io(c, u, out, (int64_t)nvec * c.N, (int64_t)nvec * c.N, on_device != 0);
+    hessian_right(c, nvec, io.in, io.dout);
+    c.sync();
+    io.finish();
+  });
+}
+
+cclr_status cclr_get_stats(cclr_ctx* h, cclr_stats* out) {
+  if (!h || !out) return CCLR_E_ARG;
+  *out = h->c.stats;
+  return CCLR_OK;
+}
+
+}  // extern "C"

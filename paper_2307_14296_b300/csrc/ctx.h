@@ -1,0 +1,118 @@
+// The library context: device, stream, workspace, Hamiltonian, amplitudes, Hbar and solver state.
+#pragma once
+#include "internal.h"
+#include <complex>
+#include <map>
+
+namespace cclr {
+
+typedef std::complex<double> zc;
+
+struct ResponseData {
+  // per operator k: shared trial space (basis and sigma vectors), projected matrices and the
+  // subspace solutions of every shift.
+  int n_ops = 0, n_freq = 0;
+  double gamma = 0.0;
+  std::vector<double> omegas;
+  std::vector<zc> shifts;                 // unique shifts z
+  std::vector<int> shift_of;              // [f*4+s] -> index into shifts
+  std::vector<cplx*> ops_dev;             // property operators (n x n)
+  std::vector<cplx*> xi, eta;             // per operator, length N
+  std::vector<cplx*> basis, sig;          // per operator, max_subspace x N
+  std::vector<int> nb;                    // basis size per operator
+  std::vector<std::vector<zc>> H;         // per operator: B^H A B (nb x nb, row-major, stride maxL)
+  std::vector<std::vector<zc>> C;         // per operator: -B^H xi
+  std::vector<std::vector<zc>> beta;      // per operator: [shift][maxL] subspace solution
+  std::vector<int> iters;                 // per (op, freq)
+  bool solved = false;
+};
+
+struct Ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  Launch L;
+  long launches = 0;
+  cclr_options opt{};
+  std::string err;
+  cclr_stats stats{};
+  Arena ws;
+
+  // sizes
+  int o = 0, v = 0, n = 0;
+  int64_t Po = 0, Pv = 0, Ns = 0, Nd = 0, N = 0;
+  int2 *po = nullptr, *pv = nullptr;     // pair tables (p, q), p < q, in packed order
+
+  // Hamiltonian
+  cplx* fock = nullptr;                                   // n x n
+  cplx *oooo = nullptr, *ooov = nullptr, *oovv = nullptr, *ovov = nullptr, *ovvv = nullptr;  // full index
+  cplx *vvvv_p = nullptr, *oovv_p = nullptr, *ovvv_p = nullptr;                                 // packed
+  double* D = nullptr;                                    // orbital-energy differences, length N
+  bool have_ham = false;
+
+  // amplitudes (t and lambda), amplitude layout and full doubles
+  cplx *t = nullptr, *t2 = nullptr;                       // t: N (t1 | t2 packed); t2: o,o,v,v
+  cplx *lam = nullptr, *l2 = nullptr;
+  bool have_t = false, have_lambda = false;
+  zc e_corr = 0.0;
+
+  // Hbar (creators-first elements, see the oracle's definitions)
+  cplx *Fae = nullptr, *Fmi = nullptr, *Fme = nullptr;
+  cplx *Wmnij = nullptr, *Wmnij_p = nullptr, *Wabef_p = nullptr, *Wmbej = nullptr;
+  cplx *WringR = nullptr, *WringL = nullptr;              // (j,b) x (m,e) operands of the rings
+  cplx *Wmnie = nullptr, *Wamef = nullptr, *Wmbij = nullptr, *Wabei = nullptr;
+  cplx *tau = nullptr;                                    // o,o,v,v
+  bool have_hbar = false;
+
+  std::vector<void*> persistent;                          // all cudaMalloc'd arrays
+  std::map<std::string, void*> named;
+
+  ResponseData rd;
+
+  // helpers
+  cplx* dalloc(int64_t n_elems) {
+    void* p = nullptr;
+    CCLR_CK(cudaMalloc(&p, sizeof(cplx) * (size_t)(n_elems > 0 ? n_elems : 1)));
+    persistent.push_back(p);
+    return (cplx*)p;
+  }
+  void dfree(void* p) {
+    if (!p) return;
+    for (size_t i = 0; i < persistent.size(); ++i)
+      if (persistent[i] == p) { cudaFree(p); persistent.erase(persistent.begin() + i); return; }
+  }
+  void sync() { CCLR_CK(cudaStreamSynchronize(stream)); }
+
+  // views of the integral classes with every index explicit (Hermiticity / antisymmetry views)
+  Tensor V(const char* cls) const;
+  Tensor f(const char* blk) const;     // Fock blocks "oo", "ov", "vo", "vv" as strided views
+};
+
+// GEMM backend selection (FP64 DFMA or tensor cores), row-major, see zgemm()
+void gemm_dispatch(Ctx& c, bool ta, bool tb, int64_t M, int64_t N, int64_t K, cplx alpha, const cplx* A,
+                   int64_t lda, const cplx* B, int64_t ldb, cplx beta, cplx* C, int64_t ldc);
+
+// equations (ccsd.cu, sigma.cu, props.cu)
+void build_denominators(Ctx& c);
+zc ccsd_energy(Ctx& c);
+void ccsd_residual(Ctx& c, cplx* R);               // R: amplitude layout
+void build_hbar(Ctx& c);
+void sigma_right(Ctx& c, int nvec, const cplx* in, cplx* out);
+void sigma_left(Ctx& c, int nvec, const cplx* in, cplx* out);
+void xi_vec(Ctx& c, const cplx* X, cplx* out);
+void eta_vec(Ctx& c, const cplx* X, bool eom, cplx* out);
+void hessian_right(Ctx& c, int nvec, const cplx* in, cplx* out);
+void eta_ground(Ctx& c, cplx* out);
+void expand_t2(Ctx& c, const cplx* packed, cplx* full, int64_t nvec);   // packed doubles -> o,o,v,v
+void pack_anti(Ctx& c, const Tensor& X, cplx* D, int64_t nvec, cplx alpha, bool anti, bool acc);
+
+// solvers (solver.cu)
+int solve_ground(Ctx& c);
+int solve_lambda(Ctx& c);
+void lr_solve(Ctx& c, int n_ops, const cplx* ops_host, int n_freq, const double* omegas, double gamma,
+              int* iters_out);
+void response_function(Ctx& c, cplx* out_host);
+
+// small dense complex linear algebra on the host
+void zsolve(int n, std::vector<zc>& A, std::vector<zc>& b);   // A (n x n row-major) x = b, in place
+
+}  // namespace cclr

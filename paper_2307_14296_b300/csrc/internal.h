@@ -1,0 +1,182 @@
+// Internal declarations of libcclr (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <vector>
+#include <stdexcept>
+#include <initializer_list>
+#include "../../include/cclr.h"
+
+namespace cclr {
+
+typedef double2 cplx;   // interleaved complex FP64, same layout as cclr_c128
+
+struct Error : std::runtime_error {
+  cclr_status st;
+  Error(cclr_status s, const std::string& m) : std::runtime_error(m), st(s) {}
+};
+
+#define CCLR_CK(x)                                                                          \
+  do {                                                                                      \
+    cudaError_t e_ = (x);                                                                   \
+    if (e_ != cudaSuccess)                                                                  \
+      throw ::cclr::Error(e_ == cudaErrorMemoryAllocation ? CCLR_E_OOM : CCLR_E_CUDA,       \
+                          std::string(#x " failed: ") + cudaGetErrorString(e_));            \
+  } while (0)
+
+#define CCLR_REQUIRE(cond, st, msg) \
+  do { if (!(cond)) throw ::cclr::Error(st, msg); } while (0)
+
+constexpr int kMaxRank = 8;
+
+// A strided view of a complex tensor in device memory.  Reads apply conj (if set) and then
+// multiply by `scale` (real).  Writes ignore conj/scale.
+struct Tensor {
+  cplx* p = nullptr;
+  int rank = 0;
+  int64_t dim[kMaxRank] = {};
+  int64_t str[kMaxRank] = {};
+  bool conj = false;
+  double scale = 1.0;
+
+  int64_t numel() const {
+    int64_t n = 1;
+    for (int i = 0; i < rank; ++i) n *= dim[i];
+    return n;
+  }
+  static Tensor make(cplx* p, std::initializer_list<int64_t> dims) {
+    Tensor t;
+    t.p = p;
+    t.rank = (int)dims.size();
+    int i = 0;
+    for (int64_t d : dims) t.dim[i++] = d;
+    int64_t s = 1;
+    for (int k = t.rank - 1; k >= 0; --k) { t.str[k] = s; s *= t.dim[k]; }
+    return t;
+  }
+  static Tensor make(cplx* p, const std::vector<int64_t>& dims) {
+    Tensor t;
+    t.p = p;
+    t.rank = (int)dims.size();
+    for (int i = 0; i < t.rank; ++i) t.dim[i] = dims[i];
+    int64_t s = 1;
+    for (int k = t.rank - 1; k >= 0; --k) { t.str[k] = s; s *= t.dim[k]; }
+    return t;
+  }
+  // view with axes reordered: new axis k is old axis perm[k]
+  Tensor perm(std::initializer_list<int> pm) const {
+    Tensor t = *this;
+    int k = 0;
+    for (int a : pm) { t.dim[k] = dim[a]; t.str[k] = str[a]; ++k; }
+    return t;
+  }
+  Tensor neg() const { Tensor t = *this; t.scale = -scale; return t; }
+  Tensor scaled(double s) const { Tensor t = *this; t.scale = scale * s; return t; }
+  Tensor cj() const { Tensor t = *this; t.conj = !conj; return t; }
+  bool contiguous() const {
+    int64_t s = 1;
+    for (int k = rank - 1; k >= 0; --k) { if (dim[k] != 1 && str[k] != s) return false; s *= dim[k]; }
+    return true;
+  }
+};
+
+// Bump allocator over one device buffer; mark()/release() bracket temporaries.
+struct Arena {
+  char* base = nullptr;
+  size_t cap = 0, top = 0, peak = 0;
+  void* alloc(size_t bytes) {
+    size_t a = (top + 255) & ~size_t(255);
+    if (a + bytes > cap)
+      throw Error(CCLR_E_OOM, "workspace exhausted: need " + std::to_string((a + bytes) >> 20) +
+                                  " MiB of " + std::to_string(cap >> 20) + " MiB");
+    top = a + bytes;
+    if (top > peak) peak = top;
+    return base + a;
+  }
+  cplx* cplxs(int64_t n) { return (cplx*)alloc(sizeof(cplx) * (size_t)(n > 0 ? n : 1)); }
+  size_t mark() const { return top; }
+  void release(size_t m) { top = m; }
+};
+
+struct Scope {  // RAII release of arena temporaries
+  Arena& a;
+  size_t m;
+  explicit Scope(Arena& ar) : a(ar), m(ar.mark()) {}
+  ~Scope() { a.release(m); }
+};
+
+// ---------------------------------------------------------------- kernels (kernels.cu)
+struct Launch {  // stream + launch counter shared by all kernels of one context
+  cudaStream_t s = nullptr;
+  long* count = nullptr;
+};
+
+// dst = alpha * op(src) + (accumulate ? dst : 0), element-wise over dst's shape; src must
+// have the same rank/dims (strides arbitrary).
+void permute(const Launch& L, const Tensor& src, const Tensor& dst, cplx alpha, bool accumulate);
+void fill_zero(const Launch& L, cplx* p, int64_t n);
+
+// Row-major complex FP64 GEMM: C[MxN] = alpha op(A) op(B) + beta C; op(A)[m,k] = ta ? A[k*lda+m]
+// : A[m*lda+k]; op(B)[k,n] = tb ? B[n*ldb+k] : B[k*ldb+n].
+void zgemm(const Launch& L, bool ta, bool tb, int64_t M, int64_t N, int64_t K, cplx alpha,
+           const cplx* A, int64_t lda, const cplx* B, int64_t ldb, cplx beta, cplx* C, int64_t ldc);
+
+// Doubles packing.  X is a full antisymmetric view with axes (Z, i, j, a, b) (any strides).
+// pack:  D[z][P(i,j)][P(a,b)] = alpha * (anti ? X_ijab - X_jiab - X_ijba + X_jiba : X_ijab)
+//                              + (accumulate ? D : 0)
+void pack_doubles_impl(const Launch& L, const Tensor& X, cplx* D, int64_t nvec, int o, int v, cplx alpha,
+                       bool anti, bool accumulate, const int2* po, const int2* pv);
+// unpack: X(Z,i,j,a,b) = D[z][P(i,j)][P(a,b)] with antisymmetry signs (0 on the diagonals)
+void unpack_doubles(const Launch& L, const cplx* D, int64_t ld_vec, const Tensor& X, int o, int v);
+
+// Vector kernels over n complex elements (batched over nvec contiguous vectors of length n).
+void axpy(const Launch& L, int64_t n, cplx a, const cplx* x, cplx* y);                  // y += a x
+// out[k] = sum_i op(x_k[i]) * y_k[i] (conj x if herm) for k < nvec, x_k = x + k*ldx
+void dots(const Launch& L, int64_t n, int nvec, const cplx* x, int64_t ldx, const cplx* y,
+          int64_t ldy, bool herm, cplx* out_dev, cplx* scratch);
+// out[j] = sum_i conj(B_j[i]) y[i] for j < nb (B_j = B + j*ldb): Gram-style projections
+void proj(const Launch& L, int64_t n, int nb, const cplx* B, int64_t ldb, const cplx* y, cplx* out_dev,
+          cplx* scratch);
+// y = sum_j c[j] X_j + (accumulate ? y : 0) with coefficients on the device
+void lincomb(const Launch& L, int64_t n, int nb, const cplx* X, int64_t ldx, const cplx* c_dev, cplx* y,
+             bool accumulate);
+
+// Fused Davidson residual and preconditioner (SI Davidson step 3-4):
+//   r = sum_j beta_j (S_j - z B_j) + xi;  delta = -r / (D - z);  rnorm2 = |r|^2
+// S, B: nb vectors (stride ld); beta on device; writes r (optional) and delta; rnorm2 to
+// rnorm2_dev[0] (deterministic two-pass reduction through scratch).
+void residual_precond(const Launch& L, int64_t n, int nb, const cplx* S, const cplx* B, int64_t ld,
+                      const cplx* beta_dev, cplx z, const cplx* xi, const double* D, cplx* r_out,
+                      cplx* delta, double* rnorm2_dev, double* scratch);
+
+int reduce_blocks();
+
+// 3-D pair packing over the last two axes of X (R, m, m):
+//   pack2:   D[r*ldd + P(p,q)] = alpha (anti ? X[r,p,q] - X[r,q,p] : X[r,p,q]) (+ D)
+//   unpack2: X[r,p,q] = +-D[r*ldd + P(min,max)], 0 for p == q
+void pack2(const Launch& L, const Tensor& X, cplx* D, int64_t ldd, const int2* tab, cplx alpha, bool anti, bool acc);
+void unpack2(const Launch& L, const cplx* D, int64_t ldd, const Tensor& X);
+// Gram block out[i*ny + j] = sum_n op(X_i[n]) Y_j[n] (conj X if herm), nx, ny <= 64;
+// scratch must hold reduce_blocks() * nx * ny elements.
+void gram(const Launch& L, int64_t n, int nx, const cplx* X, int64_t ldx, int ny, const cplx* Y, int64_t ldy, bool herm,
+          cplx* out_dev, cplx* scratch, int64_t scratch_elems);
+
+// Small element-wise helpers
+void scale_vec(const Launch& L, int64_t n, cplx a, cplx* x);
+void copy_vec(const Launch& L, int64_t n, const cplx* x, cplx* y);
+// x_i <- x_i / (D_i - z) * a   (Jacobi update)
+void div_shift(const Launch& L, int64_t n, const cplx* x, const double* D, cplx z, cplx a, cplx* y);
+
+// ---------------------------------------------------------------- contraction planner
+struct Ctx;
+// C[c] = alpha * sum A[a] B[b] + beta * C  for spec "a,b->c" (letters are index names); beta
+// is 0 or 1.  Index extents come from the tensors.  Letters present only in one operand are not
+// allowed; letters present in all three operands are not allowed.
+void einsum(Ctx& c, const char* spec, cplx alpha, const Tensor& A, const Tensor& B, double beta,
+            const Tensor& C);
+
+inline cplx cx(double r, double i = 0.0) { return make_double2(r, i); }
+
+}  // namespace cclr

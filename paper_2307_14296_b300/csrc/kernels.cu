@@ -1,0 +1,627 @@
+// Complex FP64 kernels of libcclr: strided permutation, DFMA GEMM, doubles pack/unpack, and the
+// vector kernels of the iterative solvers (dots, projections, linear combinations, the fused
+// residual + orbital-energy-denominator preconditioner).  All reductions are deterministic:
+// a fixed grid writes partial sums that one block adds in a fixed order.
+#include "internal.h"
+#include <algorithm>
+
+namespace cclr {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kReduceBlocks = 296;  // 2 x 148 SMs
+
+__device__ __forceinline__ cplx cmul(cplx a, cplx b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ cplx cadd(cplx a, cplx b) { return make_double2(a.x + b.x, a.y + b.y); }
+
+inline int grid_for(int64_t n, int per = kThreads) {
+  int64_t g = (n + per - 1) / per;
+  if (g > 148 * 16) g = 148 * 16;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+inline void bump(const Launch& L) { if (L.count) ++*L.count; }
+
+struct PermArgs {
+  int rank;
+  int64_t dim[kMaxRank];
+  int64_t sstr[kMaxRank];
+  int64_t dstr[kMaxRank];
+};
+
+// alpha kinds: 0 -> +-1 real (sign only), 1 -> real, 2 -> complex
+template <int AK>
+__global__ void __launch_bounds__(kThreads) k_permute(PermArgs a, const cplx* __restrict__ src, cplx* dst,
+                                                      int64_t n, cplx alpha, bool conj, bool acc) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    int64_t r = idx, so = 0, dof = 0;
+#pragma unroll
+    for (int k = kMaxRank - 1; k >= 0; --k) {
+      if (k < a.rank) {
+        int64_t q = r / a.dim[k];
+        int64_t c = r - q * a.dim[k];
+        r = q;
+        so += c * a.sstr[k];
+        dof += c * a.dstr[k];
+      }
+    }
+    cplx x = src[so];
+    if (conj) x.y = -x.y;
+    if (AK == 0) {
+      if (alpha.x < 0) { x.x = -x.x; x.y = -x.y; }
+    } else if (AK == 1) {
+      x.x *= alpha.x;
+      x.y *= alpha.x;
+    } else {
+      x = cmul(alpha, x);
+    }
+    if (acc) x = cadd(x, dst[dof]);
+    dst[dof] = x;
+  }
+}
+
+__global__ void k_fill_zero(cplx* p, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = make_double2(0.0, 0.0);
+}
+
+// ---------------------------------------------------------------------------- DFMA GEMM
+// 64x64 output tile per 256-thread block, 4x4 complex outputs per thread, K step 8.  FP64 FMA
+// throughput on sm_103 is ~2 DFMA/clk/SM, so this simple shared-memory tiling already runs at
+// the FP64 pipe limit (the tile's shared-memory traffic is ~30x below what the pipe consumes).
+constexpr int BM = 64, BN = 64, BK = 8;
+
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(256) k_zgemm(int64_t M, int64_t N, int64_t K, cplx alpha,
+                                               const cplx* __restrict__ A, int64_t lda,
+                                               const cplx* __restrict__ B, int64_t ldb, cplx beta,
+                                               cplx* __restrict__ C, int64_t ldc) {
+  __shared__ cplx As[BK][BM + 1];
+  __shared__ cplx Bs[BK][BN + 1];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int64_t m0 = (int64_t)blockIdx.y * BM, n0 = (int64_t)blockIdx.x * BN;
+  cplx acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = make_double2(0.0, 0.0);
+
+  for (int64_t k0 = 0; k0 < K; k0 += BK) {
+#pragma unroll
+    for (int e0 = 0; e0 < BM * BK; e0 += 256) {
+      const int e = e0 + threadIdx.x;
+      int mm, kk;
+      if (!TA) { mm = e / BK; kk = e % BK; } else { kk = e / BM; mm = e % BM; }
+      const int64_t gm = m0 + mm, gk = k0 + kk;
+      cplx val = make_double2(0.0, 0.0);
+      if (gm < M && gk < K) val = TA ? A[gk * lda + gm] : A[gm * lda + gk];
+      As[kk][mm] = val;
+    }
+#pragma unroll
+    for (int e0 = 0; e0 < BN * BK; e0 += 256) {
+      const int e = e0 + threadIdx.x;
+      int nn, kk;
+      if (!TB) { kk = e / BN; nn = e % BN; } else { nn = e / BK; kk = e % BK; }
+      const int64_t gn = n0 + nn, gk = k0 + kk;
+      cplx val = make_double2(0.0, 0.0);
+      if (gn < N && gk < K) val = TB ? B[gn * ldb + gk] : B[gk * ldb + gn];
+      Bs[kk][nn] = val;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      cplx a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          acc[i][j].x = fma(a[i].x, b[j].x, acc[i][j].x);
+          acc[i][j].x = fma(-a[i].y, b[j].y, acc[i][j].x);
+          acc[i][j].y = fma(a[i].x, b[j].y, acc[i][j].y);
+          acc[i][j].y = fma(a[i].y, b[j].x, acc[i][j].y);
+        }
+    }
+    __syncthreads();
+  }
+  const bool use_beta = (beta.x != 0.0 || beta.y != 0.0);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t gm = m0 + ty + 16 * i;
+    if (gm >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t gn = n0 + tx + 16 * j;
+      if (gn >= N) continue;
+      cplx v = cmul(alpha, acc[i][j]);
+      if (use_beta) v = cadd(v, cmul(beta, C[gm * ldc + gn]));
+      C[gm * ldc + gn] = v;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------- doubles packing
+struct Pack5 {
+  int64_t str[5];  // strides of (Z, i, j, a, b) in X
+};
+
+__device__ __forceinline__ void pair_of(int64_t P, int& p, int& q) {
+  // P = q(q-1)/2 + p, p < q
+  int qq = (int)((1.0 + sqrt(1.0 + 8.0 * (double)P)) * 0.5);
+  while ((int64_t)qq * (qq - 1) / 2 > P) --qq;
+  while ((int64_t)(qq + 1) * qq / 2 <= P) ++qq;
+  q = qq;
+  p = (int)(P - (int64_t)qq * (qq - 1) / 2);
+}
+
+__global__ void k_pack(const cplx* __restrict__ X, Pack5 s, cplx* D, int64_t nvec, int64_t Po, int64_t Pv,
+                       const int2* __restrict__ po, const int2* __restrict__ pv, cplx alpha, bool anti, bool acc) {
+  const int64_t n = nvec * Po * Pv;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t ab = idx % Pv;
+    const int64_t t = idx / Pv;
+    const int64_t ij = t % Po;
+    const int64_t z = t / Po;
+    const int2 IJ = po[ij], AB = pv[ab];
+    const int64_t base = z * s.str[0];
+    const int64_t oi = IJ.x * s.str[1], oj = IJ.y * s.str[2], oa = AB.x * s.str[3], ob = AB.y * s.str[4];
+    cplx x = X[base + oi + oj + oa + ob];
+    if (anti) {
+      const int64_t oj2 = IJ.x * s.str[2], oi2 = IJ.y * s.str[1], ob2 = AB.x * s.str[4], oa2 = AB.y * s.str[3];
+      const cplx x1 = X[base + oi2 + oj2 + oa + ob];
+      const cplx x2 = X[base + oi + oj + oa2 + ob2];
+      const cplx x3 = X[base + oi2 + oj2 + oa2 + ob2];
+      x.x = x.x - x1.x - x2.x + x3.x;
+      x.y = x.y - x1.y - x2.y + x3.y;
+    }
+    if (!(alpha.x == 1.0 && alpha.y == 0.0)) x = cmul(alpha, x);
+    if (acc) x = cadd(x, D[idx]);
+    D[idx] = x;
+  }
+}
+
+struct Unpack5 {
+  int64_t mdim[5];   // extents in memory order (slowest first)
+  int64_t mstr[5];   // strides in memory order
+  int lax[5];        // logical axis (0..4 = Z,i,j,a,b) of each memory-order axis
+};
+
+__global__ void k_unpack(const cplx* __restrict__ D, int64_t ldv, int64_t Pv, Unpack5 u, cplx* X, int64_t n) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
+    int64_t r = idx, off = 0;
+    int64_t lg[5];
+#pragma unroll
+    for (int k = 4; k >= 0; --k) {
+      const int64_t q = r / u.mdim[k];
+      const int64_t c = r - q * u.mdim[k];
+      r = q;
+      off += c * u.mstr[k];
+      lg[u.lax[k]] = c;
+    }
+    const int64_t z = lg[0];
+    int i = (int)lg[1], j = (int)lg[2], a = (int)lg[3], b = (int)lg[4];
+    cplx v = make_double2(0.0, 0.0);
+    if (i != j && a != b) {
+      double sg = 1.0;
+      if (i > j) { int t = i; i = j; j = t; sg = -sg; }
+      if (a > b) { int t = a; a = b; b = t; sg = -sg; }
+      const int64_t P1 = (int64_t)j * (j - 1) / 2 + i, P2 = (int64_t)b * (b - 1) / 2 + a;
+      v = D[z * ldv + P1 * Pv + P2];
+      v.x *= sg;
+      v.y *= sg;
+    }
+    X[off] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------- vector kernels
+__global__ void k_axpy(int64_t n, cplx a, const cplx* __restrict__ x, cplx* y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = cadd(y[i], cmul(a, x[i]));
+}
+
+__global__ void k_scale(int64_t n, cplx a, cplx* x) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = cmul(a, x[i]);
+}
+
+__global__ void k_copy(int64_t n, const cplx* __restrict__ x, cplx* y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = x[i];
+}
+
+__global__ void k_div_shift(int64_t n, const cplx* __restrict__ x, const double* __restrict__ D, cplx z, cplx a,
+                            cplx* y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double dr = D[i] - z.x, di = -z.y;
+    const double inv = 1.0 / (dr * dr + di * di);
+    const cplx q = cmul(x[i], make_double2(dr * inv, -di * inv));
+    y[i] = cmul(a, q);
+  }
+}
+
+__device__ __forceinline__ cplx block_sum(cplx v) {
+  __shared__ cplx sh[kThreads / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_down_sync(0xffffffff, v.x, o);
+    v.y += __shfl_down_sync(0xffffffff, v.y, o);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  v = make_double2(0.0, 0.0);
+  if (w == 0) {
+    if (l < kThreads / 32) v = sh[l];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      v.x += __shfl_down_sync(0xffffffff, v.x, o);
+      v.y += __shfl_down_sync(0xffffffff, v.y, o);
+    }
+  }
+  __syncthreads();
+  return v;
+}
+
+// partial[k][blockIdx.x] = sum over this block's slice of op(x_k) y_k
+__global__ void __launch_bounds__(kThreads) k_dots_partial(int64_t n, const cplx* __restrict__ x, int64_t ldx,
+                                                           const cplx* __restrict__ y, int64_t ldy, bool herm,
+                                                           cplx* partial) {
+  const int k = blockIdx.y;
+  const cplx* xk = x + k * ldx;
+  const cplx* yk = y + k * ldy;
+  cplx s = make_double2(0.0, 0.0);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    cplx a = xk[i];
+    if (herm) a.y = -a.y;
+    const cplx b = yk[i];
+    s.x = fma(a.x, b.x, fma(-a.y, b.y, s.x));
+    s.y = fma(a.x, b.y, fma(a.y, b.x, s.y));
+  }
+  s = block_sum(s);
+  if (threadIdx.x == 0) partial[(int64_t)k * gridDim.x + blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(kThreads) k_sum_partials(const cplx* partial, int nb, cplx* out) {
+  const int k = blockIdx.x;
+  cplx s = make_double2(0.0, 0.0);
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) s = cadd(s, partial[(int64_t)k * nb + i]);
+  s = block_sum(s);
+  if (threadIdx.x == 0) out[k] = s;
+}
+
+__global__ void k_lincomb(int64_t n, int nb, const cplx* __restrict__ X, int64_t ldx, const cplx* __restrict__ c,
+                          cplx* y, bool acc) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    cplx s = acc ? y[i] : make_double2(0.0, 0.0);
+    for (int j = 0; j < nb; ++j) s = cadd(s, cmul(c[j], X[j * ldx + i]));
+    y[i] = s;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_resid_precond(int64_t n, int nb, const cplx* __restrict__ S,
+                                                            const cplx* __restrict__ B, int64_t ld,
+                                                            const cplx* __restrict__ beta, cplx z,
+                                                            const cplx* __restrict__ xi, const double* __restrict__ D,
+                                                            cplx* r_out, cplx* delta, double* partial) {
+  double s2 = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    cplx r = xi[i];
+    for (int j = 0; j < nb; ++j) {
+      const cplx sj = S[j * ld + i], bj = B[j * ld + i];
+      const cplx d = make_double2(sj.x - (z.x * bj.x - z.y * bj.y), sj.y - (z.x * bj.y + z.y * bj.x));
+      r = cadd(r, cmul(beta[j], d));
+    }
+    if (r_out) r_out[i] = r;
+    s2 = fma(r.x, r.x, fma(r.y, r.y, s2));
+    const double dr = D[i] - z.x, di = -z.y;
+    const double inv = 1.0 / (dr * dr + di * di);
+    // delta = -r / (D - z) = -r * conj(D - z) / |D - z|^2
+    const cplx q = cmul(r, make_double2(dr * inv, -di * inv));
+    delta[i] = make_double2(-q.x, -q.y);
+  }
+  cplx v = block_sum(make_double2(s2, 0.0));
+  if (threadIdx.x == 0) partial[blockIdx.x] = v.x;
+}
+
+__global__ void k_sum_real(const double* partial, int nb, double* out) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) s += partial[i];
+  cplx v = block_sum(make_double2(s, 0.0));
+  if (threadIdx.x == 0) out[0] = v.x;
+}
+
+// D[r][P(p,q)] = alpha (X[r,p,q] - X[r,q,p]) or alpha X[r,p,q]  (+ D), X strided (R, m, m)
+__global__ void k_pack2(const cplx* __restrict__ X, int64_t sr, int64_t sp, int64_t sq, cplx* D, int64_t ldd,
+                        int64_t R, int64_t Pm, const int2* __restrict__ tab, cplx alpha, bool anti, bool acc) {
+  const int64_t n = R * Pm;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t P = idx % Pm, r = idx / Pm;
+    const int2 pq = tab[P];
+    cplx x = X[r * sr + pq.x * sp + pq.y * sq];
+    if (anti) {
+      const cplx y = X[r * sr + pq.y * sp + pq.x * sq];
+      x.x -= y.x;
+      x.y -= y.y;
+    }
+    if (!(alpha.x == 1.0 && alpha.y == 0.0)) x = cmul(alpha, x);
+    const int64_t o = r * ldd + P;
+    if (acc) x = cadd(x, D[o]);
+    D[o] = x;
+  }
+}
+
+// X[r,p,q] = sign D[r][P(min,max)] (0 on p == q), X strided (R, m, m)
+__global__ void k_unpack2(const cplx* __restrict__ D, int64_t ldd, cplx* X, int64_t sr, int64_t sp, int64_t sq,
+                          int64_t R, int m) {
+  const int64_t n = R * m * m;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int q = (int)(idx % m);
+    const int p = (int)((idx / m) % m);
+    const int64_t r = idx / ((int64_t)m * m);
+    cplx x = make_double2(0.0, 0.0);
+    if (p != q) {
+      const int a = p < q ? p : q, b = p < q ? q : p;
+      x = D[r * ldd + (int64_t)b * (b - 1) / 2 + a];
+      if (p > q) { x.x = -x.x; x.y = -x.y; }
+    }
+    X[r * sr + p * sp + q * sq] = x;
+  }
+}
+
+// Gram block: part[blk][i][j] = sum over this block's slice of op(X_i[n]) Y_j[n]
+constexpr int kGramChunk = 16;
+__global__ void __launch_bounds__(256) k_gram_partial(int64_t n, int nx, const cplx* __restrict__ X, int64_t ldx,
+                                                      int ny, const cplx* __restrict__ Y, int64_t ldy, bool herm,
+                                                      cplx* part) {
+  extern __shared__ cplx sm[];
+  cplx* xs = sm;                         // nx x kGramChunk
+  cplx* ys = sm + nx * kGramChunk;       // ny x kGramChunk
+  const int nout = nx * ny;
+  const int per = (nout + 255) / 256;    // outputs per thread (<= 16 for 64 x 64)
+  cplx acc[16];
+  for (int q = 0; q < 16; ++q) acc[q] = make_double2(0.0, 0.0);
+  const int64_t nchunks = (n + kGramChunk - 1) / kGramChunk;
+  for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+    const int64_t base = ch * kGramChunk;
+    for (int e = threadIdx.x; e < nx * kGramChunk; e += 256) {
+      const int i = e / kGramChunk, k = e % kGramChunk;
+      cplx v = (base + k < n) ? X[i * ldx + base + k] : make_double2(0.0, 0.0);
+      if (herm) v.y = -v.y;
+      xs[e] = v;
+    }
+    for (int e = threadIdx.x; e < ny * kGramChunk; e += 256) {
+      const int j = e / kGramChunk, k = e % kGramChunk;
+      ys[e] = (base + k < n) ? Y[j * ldy + base + k] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int o = threadIdx.x + 256 * q;
+      if (q < per && o < nout) {
+        const int i = o / ny, j = o % ny;
+        cplx s = acc[q];
+        for (int k = 0; k < kGramChunk; ++k) {
+          const cplx a = xs[i * kGramChunk + k], b = ys[j * kGramChunk + k];
+          s.x = fma(a.x, b.x, fma(-a.y, b.y, s.x));
+          s.y = fma(a.x, b.y, fma(a.y, b.x, s.y));
+        }
+        acc[q] = s;
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    const int o = threadIdx.x + 256 * q;
+    if (q < per && o < nout) part[(int64_t)blockIdx.x * nout + o] = acc[q];
+  }
+}
+
+__global__ void k_gram_reduce(const cplx* __restrict__ part, int nblk, int nout, cplx* out) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= nout) return;
+  cplx s = make_double2(0.0, 0.0);
+  for (int b = 0; b < nblk; ++b) s = cadd(s, part[(int64_t)b * nout + o]);
+  out[o] = s;
+}
+
+}  // namespace
+
+int reduce_blocks() { return kReduceBlocks; }
+
+void pack2(const Launch& L, const Tensor& X, cplx* D, int64_t ldd, const int2* tab, cplx alpha, bool anti, bool acc) {
+  CCLR_REQUIRE(X.rank == 3 && X.dim[1] == X.dim[2] && !X.conj, CCLR_E_ARG, "pack2: X must be (R, m, m)");
+  const int64_t m = X.dim[1], Pm = m * (m - 1) / 2, R = X.dim[0];
+  if (R * Pm == 0) return;
+  cplx al = make_double2(alpha.x * X.scale, alpha.y * X.scale);
+  k_pack2<<<grid_for(R * Pm), kThreads, 0, L.s>>>(X.p, X.str[0], X.str[1], X.str[2], D, ldd, R, Pm, tab, al, anti, acc);
+  CCLR_CK(cudaGetLastError());
+  bump(L);
+}
+
+void unpack2(const Launch& L, const cplx* D, int64_t ldd, const Tensor& X) {
+  CCLR_REQUIRE(X.rank == 3 && X.dim[1] == X.dim[2], CCLR_E_ARG, "unpack2: X must be (R, m, m)");
+  const int64_t n = X.numel();
+  if (n == 0) return;
+  k_unpack2<<<grid_for(n), kThreads, 0, L.s>>>(D, ldd, X.p, X.str[0], X.str[1], X.str[2], X.dim[0], (int)X.dim[1]);
+  CCLR_CK(cudaGetLastError());
+  bump(L);
+}
+
+void gram(const Launch& L, int64_t n, int nx, const cplx* X, int64_t ldx, int ny, const cplx* Y, int64_t ldy, bool herm,
+          cplx* out_dev, cplx* scratch, int64_t scratch_elems) {
+  CCLR_REQUIRE(nx >= 1 && ny >= 1 && nx * ny <= 4096 && nx <= 64 && ny <= 64, CCLR_E_ARG, "gram: block too large");
+  const int nout = nx * ny;
+  int nblk = (int)std::min<int64_t>(kReduceBlocks, (n + kGramChunk - 1) / kGramChunk);
+  if (nblk < 1) nblk = 1;
+  if ((int64_t)nblk * nout > scratch_elems) nblk = (int)std::max<int64_t>(1, scratch_elems / nout);
+  const size_t shm = sizeof(cplx) * (size_t)(nx + ny) * kGramChunk;
+  k_gram_partial<<<nblk, 256, shm, L.s>>>(n, nx, X, ldx, ny, Y, ldy, herm, scratch);
+  CCLR_CK(cudaGetLastError());
+  k_gram_reduce<<<(nout + 255) / 256, 256, 0, L.s>>>(scratch, nblk, nout, out_dev);
+  CCLR_CK(cudaGetLastError());
+  bump(L);
+  bump(L);
+}
+
+void permute(const Launch& L, const Tensor& src, const Tensor& dst, cplx alpha, bool accumulate) {
+  CCLR_REQUIRE(src.rank == dst.rank, CCLR_E_ARG, "permute: rank mismatch");
+  PermArgs a{};
+  a.rank = dst.rank;
+  for (int k = 0; k < dst.rank; ++k) {
+    CCLR_REQUIRE(src.dim[k] == dst.dim[k], CCLR_E_ARG, "permute: extent mismatch");
+    a.dim[k] = dst.dim[k];
+    a.sstr[k] = src.str[k];
+    a.dstr[k] = dst.str[k];
+  }
+  const int64_t n = dst.numel();
+  if (n == 0) return;
+  cplx al = make_double2(alpha.x * src.scale, alpha.y * src.scale);
+  const int g = grid_for(n);
+  if (al.y == 0.0 && (al.x == 1.0 || al.x == -1.0))
+    k_permute<0><<<g, kThreads, 0, L.s>>>(a, src.p, dst.p, n, al, src.conj, accumulate);
+  else if (al.y == 0.0)
+    k_permute<1><<<g, kThreads, 0, L.s>>>(a, src.p, dst.p, n, al, src.conj, accumulate);
+  else
+    k_permute<2><<<g, kThreads, 0, L.s>>>(a, src.p, dst.p, n, al, src.conj, accumulate);
+  CCLR_CK(cudaGetLastError());
+  bump(L);
+}
+
+void fill_zero(const Launch& L, cplx* p, int64_t n) {
+  if (n <= 0) return;
+  k_fill_zero<<<grid_for(n), kThreads, 0, L.s>>>(p, n);
+  CCLR_CK(cudaGetLastError());
+  bump(L);
+}
+
+void zgemm(const Launch& L, bool ta, bool tb, int64_t M, int64_t N, int64_t K, cplx alpha, const cplx* A,
+           int64_t lda, const cplx* B, int64_t ldb, cplx beta, cplx* C, int64_t ldc) {
+  if (M <= 0 || N <= 0) return;
+  if (K <= 0) {  // C = beta C
+    Tensor c = Tensor::make(C, {M, N});
+    c.str[0] = ldc;
+    permute(L, c, c, beta, false);
+    return;
+  }
+  CCLR_REQUIRE((M + BM - 1) / BM <= 65535, CCLR_E_ARG, "zgemm: M too large for one launch");
+  dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM));
+  if (!ta && !tb) k_zgemm<false, false><<<grid, 256, 0, L.s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+  else if (!ta && tb) k_zgemm<false, true><<<grid, 256, 0, L.s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+  else if (ta && !tb) k_zgemm<true, false><<<grid, 256, 0, L.s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+  else k_zgemm<true, true><<<grid, 256, 0, L.s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+  CCLR_CK(cudaGetLastError());
+  bump(L);
+}
+
+// Pair tables are uploaded once per Hamiltonian; kept here as a per-process cache keyed by size.
+void pack_doubles_impl(const Launch& L, const Tensor& X, cplx* D, int64_t nvec, int o, int v, cplx alpha, bool anti,
+                       bool accumulate, const int2* po, const int2* pv) {
+  CCLR_REQUIRE(X.rank == 5, CCLR_E_ARG, "pack_doubles: X must have axes (Z,i,j,a,b)");
+  CCLR_REQUIRE(!X.conj, CCLR_E_ARG, "pack_doubles: conj view not supported");
+  Pack5 s;
+  for (int k = 0; k < 5; ++k) s.str[k] = X.str[k];
+  // o, v are the ranges of the two pairs (both may be occupied, e.g. for <mn||ij>-type tensors)
+  const int64_t Po = (int64_t)o * (o - 1) / 2, Pv = (int64_t)v * (v - 1) / 2;
+  const int64_t n = nvec * Po * Pv;
+  if (n == 0) return;
+  cplx al = make_double2(alpha.x * X.scale, alpha.y * X.scale);
+  k_pack<<<grid_for(n), kThreads, 0, L.s>>>(X.p, s, D, nvec, Po, Pv, po, pv, al, anti, accumulate);
+  CCLR_CK(cudaGetLastError());
+  bump(L);
+}
+
+void unpack_doubles(const Launch& L, const cplx* D, int64_t ld_vec, const Tensor& X, int o, int v) {
+  CCLR_REQUIRE(X.rank == 5, CCLR_E_ARG, "unpack_doubles: X must have axes (Z,i,j,a,b)");
+  Unpack5 u;
+  int order[5] = {0, 1, 2, 3, 4};
+  // memory order: sort logical axes by decreasing stride (stable)
+  for (int a = 0; a < 5; ++a)
+    for (int b = a + 1; b < 5; ++b)
+      if (X.str[order[b]] > X.str[order[a]]) { int t = order[a]; order[a] = order[b]; order[b] = t; }
+  for (int k = 0; k < 5; ++k) {
+    u.lax[k] = order[k];
+    u.mdim[k] = X.dim[order[k]];
+    u.mstr[k] = X.str[order[k]];
+  }
+  const int64_t n = X.numel();
+  if (n == 0) return;
+  const int64_t Pv = (int64_t)v * (v - 1) / 2;
+  k_unpack<<<grid_for(n), kThreads, 0, L.s>>>(D, ld_vec, Pv, u, X.p, n);
+  CCLR_CK(cudaGetLastError());
+  bump(L);
+}
+
+void axpy(const Launch& L, int64_t n, cplx a, const cplx* x, cplx* y) {
+  if (n <= 0) return;
+  k_axpy<<<grid_for(n), kThreads, 0, L.s>>>(n, a, x, y);
+  CCLR_CK(cudaGetLastError());
+  bump(L);
+}
+
+void scale_vec(const Launch& L, int64_t n, cplx a, cplx* x) {
+  if (n <= 0) return;
+  k_scale<<<grid_for(n), kThreads, 0, L.s>>>(n, a, x);
+  CCLR_CK(cudaGetLastError());
+  bump(L);
+}
+
+void copy_vec(const Launch& L, int64_t n, const cplx* x, cplx* y) {
+  if (n <= 0) return;
+  k_copy<<<grid_for(n), kThreads, 0, L.s>>>(n, x, y);
+  CCLR_CK(cudaGetLastError());
+  bump(L);
+}
+
+void div_shift(const Launch& L, int64_t n, const cplx* x, const double* D, cplx z, cplx a, cplx* y) {
+  if (n <= 0) return;
+  k_div_shift<<<grid_for(n), kThreads, 0, L.s>>>(n, x, D, z, a, y);
+  CCLR_CK(cudaGetLastError());
+  bump(L);
+}
+
+void dots(const Launch& L, int64_t n, int nvec, const cplx* x, int64_t ldx, const cplx* y, int64_t ldy, bool herm,
+          cplx* out_dev, cplx* scratch) {
+  if (nvec <= 0) return;
+  dim3 g(kReduceBlocks, nvec);
+  k_dots_partial<<<g, kThreads, 0, L.s>>>(n, x, ldx, y, ldy, herm, scratch);
+  CCLR_CK(cudaGetLastError());
+  k_sum_partials<<<nvec, kThreads, 0, L.s>>>(scratch, kReduceBlocks, out_dev);
+  CCLR_CK(cudaGetLastError());
+  bump(L);
+  bump(L);
+}
+
+void proj(const Launch& L, int64_t n, int nb, const cplx* B, int64_t ldb, const cplx* y, cplx* out_dev, cplx* scratch) {
+  dots(L, n, nb, B, ldb, y, 0, true, out_dev, scratch);
+}
+
+void lincomb(const Launch& L, int64_t n, int nb, const cplx* X, int64_t ldx, const cplx* c_dev, cplx* y,
+             bool accumulate) {
+  if (n <= 0) return;
+  k_lincomb<<<grid_for(n), kThreads, 0, L.s>>>(n, nb, X, ldx, c_dev, y, accumulate);
+  CCLR_CK(cudaGetLastError());
+  bump(L);
+}
+
+void residual_precond(const Launch& L, int64_t n, int nb, const cplx* S, const cplx* B, int64_t ld,
+                      const cplx* beta_dev, cplx z, const cplx* xi, const double* D, cplx* r_out, cplx* delta,
+                      double* rnorm2_dev, double* scratch) {
+  k_resid_precond<<<kReduceBlocks, kThreads, 0, L.s>>>(n, nb, S, B, ld, beta_dev, z, xi, D, r_out, delta, scratch);
+  CCLR_CK(cudaGetLastError());
+  k_sum_real<<<1, kThreads, 0, L.s>>>(scratch, kReduceBlocks, rnorm2_dev);
+  CCLR_CK(cudaGetLastError());
+  bump(L);
+  bump(L);
+}
+
+}  // namespace cclr

@@ -1,0 +1,137 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerance: 1e-9 relative for every FP64 result (the oracle and the GPU differ only in summation
+order; observed differences are ~1e-14).  Component tests use random, non-converged amplitudes
+of O(0.3) and a non-canonical complex Fock matrix so that every term contributes.
+"""
+import numpy as np
+import pytest
+
+import synth
+from layout import from_amp, rel, to_amp
+from oracle import ccsd, det, hbar, props, response as R, sigma
+from oracle.deriv import antisym
+from oracle.ints import Ints
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-9
+
+
+@pytest.fixture(scope="module")
+def pk():
+    import os
+    os.environ.setdefault("CCLR_WORKSPACE_GB", "4")
+    import paper_2307_14296_b300 as pk
+    return pk
+
+
+def make_ctx(pk, inst, fock=None, **opt):
+    ctx = pk.Context(0, **opt)
+    ctx.cclr_set_hamiltonian(inst.n_occ, inst.n_vir, inst.fock if fock is None else fock,
+                             [inst.blocks[k] for k in synth.CLASSES])
+    return ctx
+
+
+def rand_amp(o, v, stream, scale=0.3, seed=1):
+    return synth.random_vector((o, v), seed, stream, scale), antisym(synth.random_vector((o, o, v, v), seed, stream + 1, scale))
+
+
+SIZES = [(2, 2), (3, 5), (4, 7), (5, 9)]
+
+
+@pytest.mark.parametrize("o,v", SIZES)
+def test_components_at_random_amplitudes(pk, o, v):
+    inst = synth.make_instance(o, v, seed=7, sd=0.1)
+    F = inst.fock + synth.random_hermitian(o + v, 7, 55, 0.2)
+    I = Ints.from_instance(inst, fock=F)
+    ctx = make_ctx(pk, inst, fock=F)
+    t1, t2 = rand_amp(o, v, 1)
+    l1, l2 = rand_amp(o, v, 5)
+    ctx.cclr_set_amplitudes(pk.AMP_T, to_amp(t1, t2))
+    # residual and energy
+    res, e = ctx.cclr_residual()
+    r1, r2 = ccsd.residual(I, t1, t2)
+    assert rel(res, to_amp(r1, r2)) < TOL
+    assert abs(e - ccsd.energy(I, t1, t2)) < TOL * max(1, abs(e))
+    # right / left sigma on a batch of three vectors
+    H = hbar.Hbar(I, t1, t2)
+    vecs = [rand_amp(o, v, 11 + 2 * k) for k in range(3)]
+    batch = np.stack([to_amp(*x) for x in vecs])
+    sr = ctx.cclr_sigma(batch, side=0)
+    sl = ctx.cclr_sigma(batch, side=1)
+    for k, (a1, a2) in enumerate(vecs):
+        assert rel(sr[k], to_amp(*sigma.sigma_right(H, I, a1, a2))) < TOL
+        assert rel(sl[k], to_amp(*sigma.sigma_left(H, I, a1, a2))) < TOL
+    # xi, eta, EOM eta, Hessian
+    X = inst.ops[0]
+    assert rel(ctx.cclr_xi(X), to_amp(*props.xi(X, o, t1, t2))) < TOL
+    ctx.cclr_set_amplitudes(pk.AMP_LAMBDA, to_amp(l1, l2))
+    assert rel(ctx.cclr_eta(X), to_amp(*props.eta(X, o, t1, t2, l1, l2))) < TOL
+    assert rel(ctx.cclr_eta(X, eom=True), to_amp(*props.eta_eom(X, o, t1, t2, l1, l2))) < TOL
+    hf = ctx.cclr_hessian(batch)
+    for k, (a1, a2) in enumerate(vecs):
+        assert rel(hf[k], to_amp(*props.hessian_product(H, I, l1, l2, a1, a2))) < TOL
+    ctx.close()
+
+
+@pytest.fixture(scope="module")
+def c0_case():
+    """The 4 occupied / 20 virtual spinor system (omega 0 and 0.077, gamma 0)."""
+    inst = synth.make_instance(4, 20)
+    s = R.CCSystem(Ints.from_instance(inst))
+    return inst, s
+
+
+def test_ground_state_and_lambda(pk, c0_case):
+    inst, s = c0_case
+    ctx = make_ctx(pk, inst, ground_tol=1e-11)
+    e, it = ctx.cc_ground()
+    assert abs(e - s.e_corr) < TOL * abs(s.e_corr)
+    assert rel(ctx.cclr_get_amplitudes(pk.AMP_T), to_amp(s.t1, s.t2)) < 1e-8
+    ctx.cc_lambda()
+    assert rel(ctx.cclr_get_amplitudes(pk.AMP_LAMBDA), to_amp(s.l1, s.l2)) < 1e-8
+    ctx.close()
+
+
+def test_polarizability_static_and_dynamic(pk, c0_case):
+    inst, s = c0_case
+    omegas = [0.0, 0.077]
+    ctx = make_ctx(pk, inst, tol=1e-10, ground_tol=1e-11)
+    ctx.cc_ground()
+    ctx.cc_lambda()
+    ctx.cc_lr_solve(inst.ops, omegas, 0.0)
+    got = ctx.cc_response_function()
+    ref = s.response(inst.ops, omegas, tol=1e-11)
+    assert rel(got, ref) < TOL
+    ctx.close()
+
+
+def test_damped_response_small(pk):
+    inst = synth.make_instance(3, 8, seed=21, sd=0.05)
+    s = R.CCSystem(Ints.from_instance(inst))
+    omegas, gamma = [0.05, 0.3], 0.01
+    ctx = make_ctx(pk, inst, tol=1e-10, ground_tol=1e-11)
+    ctx.cc_ground()
+    ctx.cc_lambda()
+    ctx.cc_lr_solve(inst.ops, omegas, gamma)
+    got = ctx.cc_response_function()
+    ref = s.response(inst.ops, [w + 1j * gamma for w in omegas], tol=1e-11)
+    assert rel(got, ref) < TOL
+    # response vectors themselves
+    tvec = ctx.cclr_get_response_vector(1, 0, 0)
+    xi = s.xi(inst.ops[1])
+    tref = s.davidson(xi, omegas[0] + 1j * gamma, tol=1e-12)[0]
+    assert rel(from_amp(tvec, 3, 8)[1], __import__("oracle.deriv", fromlist=["unpack"]).unpack(tref, 3, 8)[1]) < 1e-8
+    ctx.close()
+
+
+def test_two_electron_exact_sum_over_states(pk):
+    inst = synth.make_instance(2, 10, seed=11, sd=0.05)
+    zs = [0.1 + 0.01j, 0.25 + 0.01j]
+    sos, _ = det.fci_response(inst.fock, synth.full_eri(inst), 2, inst.ops, zs)
+    ctx = make_ctx(pk, inst, tol=1e-11, ground_tol=1e-12)
+    ctx.cc_ground()
+    ctx.cc_lambda()
+    ctx.cc_lr_solve(inst.ops, [0.1, 0.25], 0.01)
+    assert rel(ctx.cc_response_function(), sos) < TOL
+    ctx.close()
