@@ -1,0 +1,306 @@
+"""Benchmark of the CC linear-response hot path (arXiv 2307.14296) on one B300 per rank.
+
+One step = the whole path on the diatomic-scale workload: ground-state CCSD (T1/T2) and its
+Hbar intermediates, the Lambda equations (left sigma), the damped response solves of three
+dipole operators at 16 frequencies (all shifts +-w +-i gamma in shared trial spaces) and the
+symmetric CC-CC response function <<mu;mu>>(w + i gamma).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cclr|reference] [--precision bf16x3|fp64]
+
+Prints one JSON line (rank 0).  `value` is the algorithmic sigma throughput of the whole step:
+8 x (packed complex multiply-adds of one sigma product) x (sigma-type products in the step:
+right and left sigma vectors, CCSD residual evaluations, Hessian products) / step time.
+Under torchrun every rank solves its own replica of the workload (independent problems, no
+data-path collective: weak scaling); rank 0 reports the sum over ranks and the max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(n_occ=30, n_vir=200, n_freq=16, w_min=0.05, w_max=0.30, gamma=0.005, n_ops=3, tol=1e-8)
+METRIC = "CC-LR sigma TFLOP/s and s per converged α(ω) at 1e-6; mixed/batched vs FP64"
+
+
+def sigma_cmac(o: int, v: int) -> float:
+    """Packed complex multiply-adds of one sigma product: ladder Po*Pv^2, ring o^3 v^3, and the
+    o^2 v^3, o^3 v^2, o^4 v^2 terms (counts of the SI sigma equations on unique pairs)."""
+    Po, Pv = o * (o - 1) / 2, v * (v - 1) / 2
+    return Po * Pv * Pv + o**3 * v**3 + 5.5 * o**2 * v**3 + 6 * o**3 * v**2 + o**4 * v**2 / 4
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p, "measured"
+    except OSError:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling (200 ms) during the timed region."""
+
+    def __init__(self, index: int):
+        self.index, self.rows, self.proc = index, [], None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if len(r) > 8 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 8 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows if len(r) > 8 for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce(x, world, op="max"):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------------------------------ CPU
+def oracle_sample(budget_s: float = 20.0):
+    """The FP64 oracle as it stands on this host: full path (CCSD, Lambda, one damped frequency
+    for the three dipole operators) on the (8 occupied, 60 virtual) member of the benchmark's
+    system family; returns (TFLOP/s by the same sigma-count rule, seconds, description)."""
+    import synth
+    from oracle.ints import Ints
+    from oracle import response as R
+    o, v = 8, 60
+    inst = synth.make_instance(o, v)
+    t0 = time.perf_counter()
+    s = R.CCSystem(Ints.from_instance(inst), tol=1e-8)
+    n_sig = s.ground_iters + s.lambda_iters
+    z = [0.1 + 1j * WORKLOAD["gamma"]]
+    calls = {"n": 0}
+    orig = s.sigma_r
+
+    def counted(vec):
+        calls["n"] += 1
+        return orig(vec)
+
+    s.sigma_r = counted
+    s.response(inst.ops, z, tol=1e-8)
+    dt = time.perf_counter() - t0
+    n_sig += calls["n"]
+    flops = 8 * sigma_cmac(o, v) * n_sig
+    return flops / dt / 1e12, dt, (f"oracle (NumPy FP64) full path at n_occ={o}, n_vir={v}: CCSD + Lambda + "
+                                    f"one damped frequency x 3 operators ({n_sig} sigma-type products, {dt:.1f} s)")
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    cores = len(os.sched_getaffinity(0))
+    times, vals = [], []
+    for i in range(args.warmup + args.steps):
+        tf, dt, desc = oracle_sample()
+        if i >= args.warmup:
+            times.append(dt)
+            vals.append(tf)
+    value = statistics.mean(vals)
+    line = dict(metric=METRIC, value=value, unit="TFLOP/s", n_gpus=0, steps=args.steps, warmup=args.warmup,
+                ms_per_step=1e3 * statistics.mean(times), higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f64", data="synthetic", impl="reference", config=config_dict(args),
+                cpu_baseline=dict(value=value, unit="TFLOP/s", cores=cores, kind="oracle", sample=desc),
+                e2e=dict(value=value, unit="TFLOP/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+
+
+def config_dict(args):
+    w = WORKLOAD
+    return {"workload": (f"diatomic-scale CC-LR: {w['n_occ']} occupied / {w['n_vir']} virtual spinors, "
+                         f"{w['n_ops']} dipole operators, {w['n_freq']} frequencies on [{w['w_min']},{w['w_max']}] au, "
+                         f"gamma {w['gamma']} au, synthetic complex antisymmetrized integrals"),
+            "n_occ": w["n_occ"], "n_vir": w["n_vir"], "n_freq": w["n_freq"], "gamma": w["gamma"],
+            "precision": args.precision, "l2": "inputs larger than L2 (vvvv block 6.3 GB)"}
+
+
+# ------------------------------------------------------------------------------------------ GPU
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="cclr", choices=["cclr", "reference"])
+    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import torch
+    import synth
+    import paper_2307_14296_b300 as pk
+    torch.cuda.set_device(local)
+    w = WORKLOAD
+    o, v = w["n_occ"], w["n_vir"]
+    inst = synth.make_instance(o, v, seed=synth.DEFAULT_SEED + rank)
+    omegas = np.linspace(w["w_min"], w["w_max"], w["n_freq"])
+    prec = pk.TC_BF16X3 if args.precision == "bf16x3" else pk.FP64
+    ctx = pk.Context(local, precision=prec, tol=w["tol"], ground_tol=1e-8, max_subspace=64, batch=8, maxit=80)
+    blocks = [inst.blocks[k] for k in synth.CLASSES]
+    # pinned host copies of the inputs (for the end-to-end measurement)
+    pinned = [torch.from_numpy(np.ascontiguousarray(b)).pin_memory() for b in [inst.fock] + blocks + [inst.ops]]
+    h2d = sum(p.numel() * p.element_size() for p in pinned)
+    host = [p.numpy() for p in pinned]
+    ctx.cclr_set_hamiltonian(o, v, host[0], host[1:7])
+
+    def step():
+        st = {}
+        e, it = ctx.cc_ground()
+        st["ground_iters"] = it
+        st["launches"] = ctx.cclr_get_stats()["kernel_launches"]
+        st["lambda_sigma"] = ctx.cc_lambda()
+        s = ctx.cclr_get_stats()
+        st["launches"] += s["kernel_launches"]
+        st["lambda_sigma"] = s["sigma_vectors"]
+        ctx.cc_lr_solve(host[7], omegas, w["gamma"])
+        s = ctx.cclr_get_stats()
+        st["lr_sigma"] = s["sigma_vectors"]
+        st["launches"] += s["kernel_launches"]
+        resp = ctx.cc_response_function()
+        s = ctx.cclr_get_stats()
+        st["launches"] += s["kernel_launches"]
+        st["hessian"] = s["sigma_vectors"]
+        st["resp"] = resp
+        return st
+
+    for _ in range(args.warmup):
+        step()
+    ctx.cclr_kernel_profile(True)
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stats = []
+    with Clocks(local) as clk:
+        ev0.record()
+        for _ in range(args.steps):
+            stats.append(step())
+        ev1.record()
+        torch.cuda.synchronize()
+    prof = ctx.cclr_kernel_profile(False)
+    barrier(world)
+    t_local = ev0.elapsed_time(ev1) / 1e3 / args.steps
+    t_step = allreduce(t_local, world, "max")
+    n_prod = statistics.mean(s["ground_iters"] + s["lambda_sigma"] + s["lr_sigma"] + s["hessian"] for s in stats)
+    flops = 8 * sigma_cmac(o, v) * n_prod
+    value = allreduce(flops / t_step / 1e12, world, "sum")
+
+    # end to end through the C ABI: pinned host inputs copied in, response function copied out
+    e2e = None
+    if not args.no_e2e:
+        barrier(world)
+        t0 = time.perf_counter()
+        ctx.cclr_set_hamiltonian(o, v, host[0], host[1:7])
+        st = step()
+        t_e2e = allreduce(time.perf_counter() - t0, world, "max")
+        n_e2e = st["ground_iters"] + st["lambda_sigma"] + st["lr_sigma"] + st["hessian"]
+        e2e = dict(value=allreduce(8 * sigma_cmac(o, v) * n_e2e / t_e2e / 1e12, world, "sum"), unit="TFLOP/s",
+                   h2d_bytes_per_step=int(h2d), d2h_bytes_per_step=int(st["resp"].nbytes), seconds=t_e2e)
+
+    # plain-FP64 comparison: one FP64 right sigma vector, timed alone (outside the timed region)
+    fp64 = None
+    if rank == 0:
+        x = synth.random_vector((1, ctx.N), 5, 5, 1e-3)
+        ctx.cclr_sigma(x, side=0, precision=pk.FP64)
+        t0 = time.perf_counter()
+        ctx.cclr_sigma(x, side=0, precision=pk.FP64)
+        fp64_sigma = time.perf_counter() - t0
+        fp64 = dict(sigma_seconds=fp64_sigma, step_seconds_extrapolated=fp64_sigma * n_prod,
+                    note="FP64 step extrapolated: sigma-type products of the mixed step x one FP64 sigma")
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        tf, dt, desc = oracle_sample()
+        cpu = dict(value=tf, unit="TFLOP/s", cores=len(os.sched_getaffinity(0)), kind="oracle", sample=desc)
+
+    if rank != 0:
+        return
+    pk_, src = peaks()
+    peak = pk_.get("bf16_tflops_sustained", pk_["bf16_tflops"])
+    achieved = prof["flops_exec"] / (prof["ms"] / 1e3) / 1e12 if prof["ms"] > 0 else None
+    alpha = -stats[-1]["resp"]
+    line = dict(
+        metric=METRIC, value=value, unit="TFLOP/s", n_gpus=world, steps=args.steps, warmup=args.warmup,
+        ms_per_step=1e3 * t_step, higher_is_better=True, scaling="weak", vs_baseline=None,
+        dtype="bf16x3+f64" if prec != pk.FP64 else "f64", data="synthetic", config=config_dict(args),
+        s_per_alpha=t_step / w["n_freq"],
+        sigma_products_per_step=n_prod,
+        roofline=dict(bound="tensor", kernel="k_tc_zgemm (tcgen05 split-BF16 complex GEMM)", achieved=achieved,
+                      peak=peak, unit="TFLOP/s", frac=(achieved / peak if achieved else None), traffic=None,
+                      peak_source=f"bf16_tflops_sustained of {src} MEASURED_PEAKS",
+                      launches=prof["launches"], kernel_ms_per_step=prof["ms"] / args.steps,
+                      useful_complex_tflops=(prof["flops_useful"] / (prof["ms"] / 1e3) / 1e12 if prof["ms"] else None)),
+        cpu_baseline=cpu, e2e=e2e, fp64=fp64,
+        gpu_launches=int(sum(s["launches"] for s in stats)),
+        clocks=clk.summary(),
+        alpha_mean_last_freq=[float(np.trace(alpha[-1]).real / 3), float(np.trace(alpha[-1]).imag / 3)],
+    )
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -49,12 +49,15 @@ typedef enum {
   CCLR_E_TIMEOUT = 6   /* a device-side bounded wait expired */
 } cclr_status;
 
-/* Arithmetic used for the sigma-vector contractions (Sec. 2.4 of the paper uses complex FP64).
- *  CCLR_FP64      complex FP64 everywhere (DFMA).
- *  CCLR_TC_BF16X3 ladder and ring contractions on the tensor cores from split-BF16 operands
- *                 (hi/lo, three products, FP32 accumulation); the response solve is wrapped in
- *                 FP64 iterative refinement so converged results keep FP64 accuracy.         */
-typedef enum { CCLR_FP64 = 0, CCLR_TC_BF16X3 = 2 } cclr_precision;
+/* Arithmetic used for the large contractions (the paper computes in complex FP64, Sec. 2.4).
+ *  CCLR_FP64      complex FP64 everywhere (DFMA on the CUDA cores).
+ *  CCLR_TC_BF16X3 the ladder and ring contractions (and every other large K-major GEMM) run on
+ *                 the tensor cores from split-BF16 operands x = x0 + x1 (products x0y0 + x0y1 +
+ *                 x1y0, FP32 accumulation; ~1e-5 relative per contraction).
+ *  CCLR_TC_BF16X6 as above with three slices and six products (FP32-class, ~1e-6).
+ *  Small solves, inner products, the preconditioner and the response-function contraction stay
+ *  in FP64 in every mode. */
+typedef enum { CCLR_FP64 = 0, CCLR_TC_BF16X3 = 2, CCLR_TC_BF16X6 = 3 } cclr_precision;
 
 typedef struct {
   double tol;          /* residual 2-norm target of the response solves (default 1e-8)        */
@@ -149,6 +152,19 @@ cclr_status cclr_eta(cclr_ctx *ctx, const cclr_c128 *op, int eom, cclr_c128 *out
 
 /* CC Hessian products (u F) (SI, "(t^X F)" working equations) for nvec vectors; needs Lambda. */
 cclr_status cclr_hessian(cclr_ctx *ctx, int nvec, const cclr_c128 *u, cclr_c128 *out, int on_device);
+
+/* The contraction engine's GEMM on its own (used to test the tensor-core kernels):
+ *   C[m][n] = sum_k A[m][k] B[n][k]  (complex, row-major, both operands K-major, host pointers,
+ *   A: M x K, B: N x K, C: M x N), in the given precision.  Needs a Hamiltonian (for the
+ *   context's device workspace). */
+cclr_status cclr_zgemm_nt(cclr_ctx *ctx, int precision, int M, int N, int K, const cclr_c128 *A,
+                          const cclr_c128 *B, cclr_c128 *C);
+
+/* Timing of the tensor-core GEMM kernel with CUDA events recorded on the context's stream around
+ * every launch.  enable != 0 switches recording on.  out4 (may be NULL) receives, accumulated
+ * since the previous call: {launches, milliseconds, executed BF16 flops (8 M N K per slice
+ * product), useful complex flops (8 M N K)}; the counters are then reset. */
+cclr_status cclr_kernel_profile(cclr_ctx *ctx, int enable, double *out4);
 
 /* Per-call statistics of the last cc_* call: sigma launches and vectors, seconds spent. */
 typedef struct {

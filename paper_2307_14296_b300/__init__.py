@@ -26,13 +26,13 @@ if not os.path.exists(LIB_PATH):
 _lib = ctypes.CDLL(LIB_PATH)
 
 CCLR_OK, CCLR_E_ARG, CCLR_E_NOCONV, CCLR_E_OOM, CCLR_E_CUDA, CCLR_E_STATE, CCLR_E_TIMEOUT = range(7)
-FP64, TC_BF16X3 = 0, 2
+FP64, TC_BF16X3, TC_BF16X6 = 0, 2, 3
 AMP_T, AMP_LAMBDA = 0, 1
 EXPORTS = (
     "cclr_default_options", "cclr_create", "cclr_destroy", "cclr_last_error", "cclr_set_hamiltonian",
     "cc_ground", "cc_lambda", "cc_lr_solve", "cc_response_function", "cclr_get_amplitudes",
     "cclr_set_amplitudes", "cclr_get_response_vector", "cclr_sigma", "cclr_residual", "cclr_xi",
-    "cclr_eta", "cclr_hessian", "cclr_get_stats",
+    "cclr_eta", "cclr_hessian", "cclr_zgemm_nt", "cclr_kernel_profile", "cclr_get_stats",
 )
 
 
@@ -66,6 +66,8 @@ _sig = {
     "cclr_xi": (_i, [_vp, _vp, _vp]),
     "cclr_eta": (_i, [_vp, _vp, _i, _vp]),
     "cclr_hessian": (_i, [_vp, _i, _vp, _vp, _i]),
+    "cclr_zgemm_nt": (_i, [_vp, _i, _i, _i, _i, _vp, _vp, _vp]),
+    "cclr_kernel_profile": (_i, [_vp, _i, _vp]),
     "cclr_get_stats": (_i, [_vp, ctypes.POINTER(Stats)]),
 }
 for _name, (_res, _args) in _sig.items():
@@ -225,6 +227,19 @@ class Context:
         res = np.zeros_like(v)
         self._check(_lib.cclr_hessian(self._h, nvec, _ptr(v), _ptr(res), 0))
         return res
+
+    def cclr_zgemm_nt(self, A, B, precision=FP64):
+        """C = A B^T for complex A (M x K) and B (N x K) through the contraction engine."""
+        A, B = _c128(A), _c128(B)
+        C = np.zeros((A.shape[0], B.shape[0]), np.complex128)
+        self._check(_lib.cclr_zgemm_nt(self._h, precision, A.shape[0], B.shape[0], A.shape[1], _ptr(A), _ptr(B), _ptr(C)))
+        return C
+
+    def cclr_kernel_profile(self, enable=True) -> dict:
+        """Tensor-core kernel timing (CUDA events on the library's stream) since the last call."""
+        out = np.zeros(4, np.float64)
+        self._check(_lib.cclr_kernel_profile(self._h, int(enable), _ptr(out)))
+        return dict(launches=int(out[0]), ms=float(out[1]), flops_exec=float(out[2]), flops_useful=float(out[3]))
 
     def cclr_get_stats(self) -> dict:
         s = Stats()

@@ -49,7 +49,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if verbose and out:
             print(out.decode())
     tmp = LIB + ".tmp"
-    cmd = ["nvcc", *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lcuda"]
+    cmd = ["nvcc", *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + r.stdout + r.stderr)

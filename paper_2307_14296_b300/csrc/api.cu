@@ -29,7 +29,17 @@ cclr_status guard(cclr_ctx* h, F&& fn) {
     CCLR_CK(cudaSetDevice(c.device));
     fn(c);
     CCLR_CK(cudaStreamSynchronize(c.stream));
+    if (c.prof) c.prof_collect();
+    if (c.tc_err) {
+      int h = 0;
+      CCLR_CK(cudaMemcpy(&h, c.tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+      if (h) {
+        CCLR_CK(cudaMemset(c.tc_err, 0, sizeof(int)));
+        throw Error(CCLR_E_TIMEOUT, "tensor-core GEMM: a bounded wait expired (code " + std::to_string(h) + ")");
+      }
+    }
   } catch (const Error& e) {
+    c.ev_used = 0;
     c.err = e.what();
     st = e.st;
   } catch (const std::exception& e) {
@@ -42,6 +52,8 @@ cclr_status guard(cclr_ctx* h, F&& fn) {
 }
 
 void free_all(Ctx& c) {
+  tc_release_cache();
+  ++hbar_generation();
   for (void* p : c.persistent) cudaFree(p);
   c.persistent.clear();
   c.named.clear();
@@ -112,7 +124,10 @@ cclr_status cclr_create(cclr_ctx** out, int device, const cclr_options* opt) {
   Ctx& c = h->c;
   c.device = device;
   if (opt) c.opt = *opt; else cclr_default_options(&c.opt);
-  if (c.opt.precision != CCLR_FP64 && c.opt.precision != CCLR_TC_BF16X3) { delete h; return CCLR_E_ARG; }
+  if (c.opt.precision != CCLR_FP64 && c.opt.precision != CCLR_TC_BF16X3 && c.opt.precision != CCLR_TC_BF16X6) {
+    delete h;
+    return CCLR_E_ARG;
+  }
   if (cudaSetDevice(device) != cudaSuccess || cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking) != cudaSuccess) {
     delete h;
     return CCLR_E_CUDA;
@@ -127,6 +142,8 @@ void cclr_destroy(cclr_ctx* h) {
   if (!h) return;
   cudaSetDevice(h->c.device);
   free_all(h->c);
+  if (h->c.tc_err) cudaFree(h->c.tc_err);
+  for (auto& e : h->c.ev_pool) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
   if (h->c.stream) cudaStreamDestroy(h->c.stream);
   delete h;
 }
@@ -317,7 +334,8 @@ cclr_status cclr_sigma(cclr_ctx* h, int side, int nvec, const cclr_c128* in, ccl
   return guard(h, [&](Ctx& c) {
     CCLR_REQUIRE(c.have_hbar, CCLR_E_STATE, "sigma needs T (cc_ground or cclr_set_amplitudes)");
     CCLR_REQUIRE(nvec >= 1 && in && out && (side == 0 || side == 1), CCLR_E_ARG, "bad sigma arguments");
-    CCLR_REQUIRE(precision == CCLR_FP64 || precision == CCLR_TC_BF16X3, CCLR_E_ARG, "unknown precision");
+    CCLR_REQUIRE(precision == CCLR_FP64 || precision == CCLR_TC_BF16X3 || precision == CCLR_TC_BF16X6, CCLR_E_ARG,
+                 "unknown precision");
     const int saved = c.opt.precision;
     c.opt.precision = precision;
     try {
@@ -384,6 +402,46 @@ cclr_status cclr_hessian(cclr_ctx* h, int nvec, const cclr_c128* u, cclr_c128* o
     c.sync();
     io.finish();
   });
+}
+
+cclr_status cclr_zgemm_nt(cclr_ctx* h, int precision, int M, int N, int K, const cclr_c128* A, const cclr_c128* B,
+                          cclr_c128* C) {
+  return guard(h, [&](Ctx& c) {
+    CCLR_REQUIRE(c.have_ham, CCLR_E_STATE, "cclr_zgemm_nt needs a Hamiltonian (device workspace)");
+    CCLR_REQUIRE(M > 0 && N > 0 && K > 0 && A && B && C, CCLR_E_ARG, "bad GEMM arguments");
+    CCLR_REQUIRE(precision == CCLR_FP64 || precision == CCLR_TC_BF16X3 || precision == CCLR_TC_BF16X6, CCLR_E_ARG,
+                 "unknown precision");
+    const int saved = c.opt.precision;
+    c.opt.precision = precision;
+    try {
+      Scope sc(c.ws);
+      cplx *a = c.ws.cplxs((int64_t)M * K), *b = c.ws.cplxs((int64_t)N * K), *d = c.ws.cplxs((int64_t)M * N);
+      upload(c, a, A, (int64_t)M * K);
+      upload(c, b, B, (int64_t)N * K);
+      gemm_dispatch(c, false, true, M, N, K, cx(1), a, K, b, K, cx(0), d, N);
+      CCLR_CK(cudaMemcpyAsync(C, d, sizeof(cplx) * (size_t)M * N, cudaMemcpyDeviceToHost, c.stream));
+      c.sync();
+    } catch (...) {
+      c.opt.precision = saved;
+      throw;
+    }
+    c.opt.precision = saved;
+  });
+}
+
+cclr_status cclr_kernel_profile(cclr_ctx* h, int enable, double* out4) {
+  if (!h) return CCLR_E_ARG;
+  Ctx& c = h->c;
+  if (out4) {
+    out4[0] = (double)c.prof_launches;
+    out4[1] = c.prof_ms;
+    out4[2] = c.prof_flops_exec;
+    out4[3] = c.prof_flops_useful;
+  }
+  c.prof_launches = 0;
+  c.prof_ms = c.prof_flops_exec = c.prof_flops_useful = 0.0;
+  c.prof = enable != 0;
+  return CCLR_OK;
 }
 
 cclr_status cclr_get_stats(cclr_ctx* h, cclr_stats* out) {

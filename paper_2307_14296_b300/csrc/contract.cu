@@ -4,6 +4,9 @@
 // The GEMM backend is chosen per call by gemm_dispatch (FP64 DFMA or the tensor-core path).
 #include "ctx.h"
 #include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
 
 namespace cclr {
 
@@ -49,7 +52,23 @@ int64_t prod(const Tensor& t, const std::string& have, const std::string& letter
 
 }  // namespace
 
+void einsum_impl(Ctx& c, const char* spec, cplx alpha, const Tensor& A, const Tensor& B, double beta, const Tensor& C);
+
+// CCLR_TRACE=1 prints every contraction with its GEMM shape and device time (debug aid; it
+// synchronizes the stream around each call).
 void einsum(Ctx& c, const char* spec, cplx alpha, const Tensor& A, const Tensor& B, double beta, const Tensor& C) {
+  static const bool trace = std::getenv("CCLR_TRACE") != nullptr;
+  if (!trace) return einsum_impl(c, spec, alpha, A, B, beta, C);
+  CCLR_CK(cudaStreamSynchronize(c.stream));
+  auto t0 = std::chrono::steady_clock::now();
+  einsum_impl(c, spec, alpha, A, B, beta, C);
+  CCLR_CK(cudaStreamSynchronize(c.stream));
+  const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  std::fprintf(stderr, "[cclr] %-28s A%s B%s C%s %9.3f ms\n", spec, std::to_string(A.numel()).c_str(),
+               std::to_string(B.numel()).c_str(), std::to_string(C.numel()).c_str(), ms);
+}
+
+void einsum_impl(Ctx& c, const char* spec, cplx alpha, const Tensor& A, const Tensor& B, double beta, const Tensor& C) {
   Spec s = parse(spec);
   CCLR_REQUIRE((int)s.a.size() == A.rank && (int)s.b.size() == B.rank && (int)s.c.size() == C.rank, CCLR_E_ARG,
                std::string("einsum: rank mismatch in ") + spec);
@@ -100,6 +119,28 @@ void einsum(Ctx& c, const char* spec, cplx alpha, const Tensor& A, const Tensor&
   }
 
   cplx al = make_double2(alpha.x, alpha.y);
+  // Tensor-core route: both operands K-major ([M][K] and [N][K]); the GEMM then computes
+  // C = A' B'^T (or C^T = B' A'^T when the target is laid out [N][M]).
+  if (c.opt.precision != CCLR_FP64 && tc_eligible(M, N, K)) {
+    // operands go straight from their strided views into BF16 slices (no FP64 copy)
+    Tensor va = reorder(A, s.a, fa + korder), vb = reorder(B, s.b, fb + korder);
+    al.x *= A.scale * B.scale;
+    al.y *= A.scale * B.scale;
+    const int nra = (int)fa.size(), nrb = (int)fb.size();
+    Tensor cAB = reorder(C, s.c, fa + fb), cBA = reorder(C, s.c, fb + fa);
+    if (cAB.contiguous()) {
+      tc_gemm_views(c, va, nra, vb, nrb, al, cx(beta), C.p, N);
+    } else if (cBA.contiguous()) {
+      tc_gemm_views(c, vb, nrb, va, nra, al, cx(beta), C.p, M);
+    } else {
+      cplx* tmp = c.ws.cplxs(M * N);
+      tc_gemm_views(c, va, nra, vb, nrb, al, cx(0.0), tmp, N);
+      std::vector<int64_t> d;
+      for (char ch : fa + fb) d.push_back(ext[ch]);
+      permute(c.L, reorder(Tensor::make(tmp, d), fa + fb, s.c), C, cx(1.0), beta != 0.0);
+    }
+    return;
+  }
   // ---- operand A as op(A) = [M x K]
   bool ta = false;
   const cplx* pa;

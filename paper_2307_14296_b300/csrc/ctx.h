@@ -68,6 +68,35 @@ struct Ctx {
 
   ResponseData rd;
 
+  // tensor-core status word (bounded-wait expiry) and optional per-launch timing of the
+  // tensor-core kernel with CUDA events on the context's stream
+  int* tc_err = nullptr;
+  bool prof = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
+  size_t ev_used = 0;
+  double prof_ms = 0.0, prof_flops_exec = 0.0, prof_flops_useful = 0.0;
+  long prof_launches = 0;
+  void prof_events(cudaEvent_t& a, cudaEvent_t& b) {
+    if (ev_used == ev_pool.size()) {
+      cudaEvent_t x, y;
+      CCLR_CK(cudaEventCreate(&x));
+      CCLR_CK(cudaEventCreate(&y));
+      ev_pool.push_back({x, y});
+    }
+    a = ev_pool[ev_used].first;
+    b = ev_pool[ev_used].second;
+    ++ev_used;
+  }
+  void prof_collect() {  // after a stream synchronize
+    for (size_t i = 0; i < ev_used; ++i) {
+      float ms = 0.f;
+      CCLR_CK(cudaEventElapsedTime(&ms, ev_pool[i].first, ev_pool[i].second));
+      prof_ms += ms;
+      ++prof_launches;
+    }
+    ev_used = 0;
+  }
+
   // helpers
   cplx* dalloc(int64_t n_elems) {
     void* p = nullptr;
@@ -90,6 +119,17 @@ struct Ctx {
 // GEMM backend selection (FP64 DFMA or tensor cores), row-major, see zgemm()
 void gemm_dispatch(Ctx& c, bool ta, bool tb, int64_t M, int64_t N, int64_t K, cplx alpha, const cplx* A,
                    int64_t lda, const cplx* B, int64_t ldb, cplx beta, cplx* C, int64_t ldc);
+
+// tensor-core backend state (tc_gemm.cu): cached BF16 slices of static operands are valid for one
+// Hbar generation
+uint64_t& hbar_generation();
+uint64_t& data_generation();   // bumped whenever integrals, T, Lambda or Hbar change
+void tc_release_cache();
+bool tc_eligible(int64_t M, int64_t N, int64_t K);
+// C[m*ldc + n] = alpha sum_k vm[m,k] vn[n,k] + beta C on the tensor cores; the first nrm / nrn
+// axes of the views are the rows, the remaining axes K (in the same order in both views)
+void tc_gemm_views(Ctx& c, const Tensor& vm, int nrm, const Tensor& vn, int nrn, cplx alpha, cplx beta, cplx* C,
+                   int64_t ldc);
 
 // equations (ccsd.cu, sigma.cu, props.cu)
 void build_denominators(Ctx& c);

@@ -1,6 +1,9 @@
 // GEMM backend selection.  CCLR_FP64 runs every contraction on the FP64 DFMA kernel; the
-// tensor-core modes route large contractions to the tcgen05 kernels (tc_gemm.cu).
+// tensor-core modes route K-major contractions to the tcgen05 kernel (tc_gemm.cu).
+// Skinny shapes (few output tiles, long K: e.g. the singles projections of o^2 v^3 terms) are
+// split along K so that every SM works; the partial tiles are summed in a fixed order.
 #include "ctx.h"
+#include <algorithm>
 
 namespace cclr {
 
@@ -10,13 +13,21 @@ bool tc_gemm_try(Ctx& c, bool ta, bool tb, int64_t M, int64_t N, int64_t K, cplx
 void gemm_dispatch(Ctx& c, bool ta, bool tb, int64_t M, int64_t N, int64_t K, cplx alpha, const cplx* A,
                    int64_t lda, const cplx* B, int64_t ldb, cplx beta, cplx* C, int64_t ldc) {
   if (c.opt.precision != CCLR_FP64 && tc_gemm_try(c, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc)) return;
+  const int64_t tiles = ((M + 63) / 64) * ((N + 63) / 64);
+  if (tiles < 2 * 148 && K >= 4096) {
+    // FP64 split-K: enough slices for ~2 blocks per SM, each slice at least 1024 deep
+    int64_t S = std::min<int64_t>({(2 * 148 + tiles - 1) / tiles, K / 1024, 256});
+    if (S >= 2) {
+      int64_t kchunk = ((K + S - 1) / S + 7) / 8 * 8;
+      S = (K + kchunk - 1) / kchunk;
+      Scope sc(c.ws);
+      cplx* P = c.ws.cplxs(S * M * N);
+      zgemm_splitk(c.L, ta, tb, M, N, K, A, lda, B, ldb, P, (int)S, kchunk);
+      splitk_reduce(c.L, P, (int)S, M, N, alpha, beta, C, ldc);
+      return;
+    }
+  }
   zgemm(c.L, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
-}
-
-// Until the tensor-core kernels are enabled every call falls back to FP64.
-__attribute__((weak)) bool tc_gemm_try(Ctx&, bool, bool, int64_t, int64_t, int64_t, cplx, const cplx*, int64_t,
-                                       const cplx*, int64_t, cplx, cplx*, int64_t) {
-  return false;
 }
 
 }  // namespace cclr

@@ -23,7 +23,8 @@ struct Error : std::runtime_error {
     cudaError_t e_ = (x);                                                                   \
     if (e_ != cudaSuccess)                                                                  \
       throw ::cclr::Error(e_ == cudaErrorMemoryAllocation ? CCLR_E_OOM : CCLR_E_CUDA,       \
-                          std::string(#x " failed: ") + cudaGetErrorString(e_));            \
+                          std::string(#x " failed: ") + cudaGetErrorString(e_) + " at " +  \
+                              __FILE__ + ":" + std::to_string(__LINE__));                   \
   } while (0)
 
 #define CCLR_REQUIRE(cond, st, msg) \
@@ -152,6 +153,13 @@ void residual_precond(const Launch& L, int64_t n, int nb, const cplx* S, const c
                       cplx* delta, double* rnorm2_dev, double* scratch);
 
 int reduce_blocks();
+
+// Split-K GEMM for skinny shapes: partials P[z] = op(A) op(B) over k in [z*kchunk, (z+1)*kchunk)
+// (S slices, each M x N with ld N), then C = alpha * sum_z P[z] + beta * C in a fixed order.
+void zgemm_splitk(const Launch& L, bool ta, bool tb, int64_t M, int64_t N, int64_t K, const cplx* A, int64_t lda,
+                  const cplx* B, int64_t ldb, cplx* P, int S, int64_t kchunk);
+void splitk_reduce(const Launch& L, const cplx* P, int S, int64_t M, int64_t N, cplx alpha, cplx beta, cplx* C,
+                   int64_t ldc);
 
 // 3-D pair packing over the last two axes of X (R, m, m):
 //   pack2:   D[r*ldd + P(p,q)] = alpha (anti ? X[r,p,q] - X[r,q,p] : X[r,p,q]) (+ D)

@@ -80,18 +80,22 @@ template <bool TA, bool TB>
 __global__ void __launch_bounds__(256) k_zgemm(int64_t M, int64_t N, int64_t K, cplx alpha,
                                                const cplx* __restrict__ A, int64_t lda,
                                                const cplx* __restrict__ B, int64_t ldb, cplx beta,
-                                               cplx* __restrict__ C, int64_t ldc) {
+                                               cplx* __restrict__ C, int64_t ldc, int64_t kchunk, int64_t cz) {
+  // split-K: blockIdx.z owns k in [z*kchunk, min(K, (z+1)*kchunk)) and writes C + z*cz
   __shared__ cplx As[BK][BM + 1];
   __shared__ cplx Bs[BK][BN + 1];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int64_t m0 = (int64_t)blockIdx.y * BM, n0 = (int64_t)blockIdx.x * BN;
+  const int64_t kbeg = (int64_t)blockIdx.z * kchunk;
+  const int64_t kend = kbeg + kchunk < K ? kbeg + kchunk : K;
+  C += (int64_t)blockIdx.z * cz;
   cplx acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = make_double2(0.0, 0.0);
 
-  for (int64_t k0 = 0; k0 < K; k0 += BK) {
+  for (int64_t k0 = kbeg; k0 < kend; k0 += BK) {
 #pragma unroll
     for (int e0 = 0; e0 < BM * BK; e0 += 256) {
       const int e = e0 + threadIdx.x;
@@ -99,7 +103,7 @@ __global__ void __launch_bounds__(256) k_zgemm(int64_t M, int64_t N, int64_t K, 
       if (!TA) { mm = e / BK; kk = e % BK; } else { kk = e / BM; mm = e % BM; }
       const int64_t gm = m0 + mm, gk = k0 + kk;
       cplx val = make_double2(0.0, 0.0);
-      if (gm < M && gk < K) val = TA ? A[gk * lda + gm] : A[gm * lda + gk];
+      if (gm < M && gk < kend) val = TA ? A[gk * lda + gm] : A[gm * lda + gk];
       As[kk][mm] = val;
     }
 #pragma unroll
@@ -109,7 +113,7 @@ __global__ void __launch_bounds__(256) k_zgemm(int64_t M, int64_t N, int64_t K, 
       if (!TB) { kk = e / BN; nn = e % BN; } else { nn = e / BK; kk = e % BK; }
       const int64_t gn = n0 + nn, gk = k0 + kk;
       cplx val = make_double2(0.0, 0.0);
-      if (gn < N && gk < K) val = TB ? B[gn * ldb + gk] : B[gk * ldb + gn];
+      if (gn < N && gk < kend) val = TB ? B[gn * ldb + gk] : B[gk * ldb + gn];
       Bs[kk][nn] = val;
     }
     __syncthreads();
@@ -434,9 +438,45 @@ __global__ void k_gram_reduce(const cplx* __restrict__ part, int nblk, int nout,
   out[o] = s;
 }
 
+// split-K epilogue: C[m*ldc + n] = alpha * sum_z P[z][m][n] + beta * C (fixed summation order)
+__global__ void k_splitk_reduce(const cplx* __restrict__ P, int S, int64_t M, int64_t N, cplx alpha, cplx beta, cplx* C,
+                                int64_t ldc) {
+  const int64_t n_el = M * N;
+  const bool use_beta = (beta.x != 0.0 || beta.y != 0.0);
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n_el; idx += (int64_t)gridDim.x * blockDim.x) {
+    cplx s = make_double2(0.0, 0.0);
+    for (int z = 0; z < S; ++z) s = cadd(s, P[(int64_t)z * n_el + idx]);
+    const int64_t m = idx / N, n = idx - m * N;
+    cplx v = cmul(alpha, s);
+    if (use_beta) v = cadd(v, cmul(beta, C[m * ldc + n]));
+    C[m * ldc + n] = v;
+  }
+}
+
 }  // namespace
 
 int reduce_blocks() { return kReduceBlocks; }
+
+void splitk_reduce(const Launch& L, const cplx* P, int S, int64_t M, int64_t N, cplx alpha, cplx beta, cplx* C,
+                   int64_t ldc) {
+  k_splitk_reduce<<<grid_for(M * N), kThreads, 0, L.s>>>(P, S, M, N, alpha, beta, C, ldc);
+  CCLR_CK(cudaGetLastError());
+  bump(L);
+}
+
+void zgemm_splitk(const Launch& L, bool ta, bool tb, int64_t M, int64_t N, int64_t K, const cplx* A, int64_t lda,
+                  const cplx* B, int64_t ldb, cplx* P, int S, int64_t kchunk) {
+  // partials P[z] (M x N, ld N) over k in [z*kchunk, (z+1)*kchunk); kchunk a multiple of 8
+  CCLR_REQUIRE((M + BM - 1) / BM <= 65535 && S <= 65535, CCLR_E_ARG, "zgemm_splitk: grid too large");
+  dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM), (unsigned)S);
+  const cplx one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
+  if (!ta && !tb) k_zgemm<false, false><<<grid, 256, 0, L.s>>>(M, N, K, one, A, lda, B, ldb, zero, P, N, kchunk, M * N);
+  else if (!ta && tb) k_zgemm<false, true><<<grid, 256, 0, L.s>>>(M, N, K, one, A, lda, B, ldb, zero, P, N, kchunk, M * N);
+  else if (ta && !tb) k_zgemm<true, false><<<grid, 256, 0, L.s>>>(M, N, K, one, A, lda, B, ldb, zero, P, N, kchunk, M * N);
+  else k_zgemm<true, true><<<grid, 256, 0, L.s>>>(M, N, K, one, A, lda, B, ldb, zero, P, N, kchunk, M * N);
+  CCLR_CK(cudaGetLastError());
+  bump(L);
+}
 
 void pack2(const Launch& L, const Tensor& X, cplx* D, int64_t ldd, const int2* tab, cplx alpha, bool anti, bool acc) {
   CCLR_REQUIRE(X.rank == 3 && X.dim[1] == X.dim[2] && !X.conj, CCLR_E_ARG, "pack2: X must be (R, m, m)");
@@ -513,12 +553,19 @@ void zgemm(const Launch& L, bool ta, bool tb, int64_t M, int64_t N, int64_t K, c
     permute(L, c, c, beta, false);
     return;
   }
-  CCLR_REQUIRE((M + BM - 1) / BM <= 65535, CCLR_E_ARG, "zgemm: M too large for one launch");
+  const int64_t max_rows = (int64_t)65535 * BM;   // grid.y limit: split the rows into launches
+  if (M > max_rows) {
+    for (int64_t m0 = 0; m0 < M; m0 += max_rows) {
+      const int64_t mm = std::min(max_rows, M - m0);
+      zgemm(L, ta, tb, mm, N, K, alpha, ta ? A + m0 : A + m0 * lda, lda, B, ldb, beta, C + m0 * ldc, ldc);
+    }
+    return;
+  }
   dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM));
-  if (!ta && !tb) k_zgemm<false, false><<<grid, 256, 0, L.s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
-  else if (!ta && tb) k_zgemm<false, true><<<grid, 256, 0, L.s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
-  else if (ta && !tb) k_zgemm<true, false><<<grid, 256, 0, L.s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
-  else k_zgemm<true, true><<<grid, 256, 0, L.s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+  if (!ta && !tb) k_zgemm<false, false><<<grid, 256, 0, L.s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, K, 0);
+  else if (!ta && tb) k_zgemm<false, true><<<grid, 256, 0, L.s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, K, 0);
+  else if (ta && !tb) k_zgemm<true, false><<<grid, 256, 0, L.s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, K, 0);
+  else k_zgemm<true, true><<<grid, 256, 0, L.s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, K, 0);
   CCLR_CK(cudaGetLastError());
   bump(L);
 }

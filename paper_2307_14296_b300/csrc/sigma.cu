@@ -402,6 +402,8 @@ void hessian_right(Ctx& c, int nvec, const cplx* in, cplx* out) {
   cplx* s2 = c.ws.cplxs(Z * c.Nd);
   pack_anti(c, X4, s2, Z, cx(1), true, false);
   scatter(c, Z, s1, s2, out);
+  c.stats.sigma_calls++;
+  c.stats.sigma_vectors += Z;
 }
 
 }  // namespace cclr

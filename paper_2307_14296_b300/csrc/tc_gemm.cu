@@ -1,0 +1,515 @@
+// Tensor-core complex GEMM for sm_103a (tcgen05 + TMA + TMEM), used by the mixed-precision
+// modes for the two contractions that carry ~90% of the sigma-vector work: the packed
+// particle-particle ladder (SI Eq. sigma_double-ee, 1/2 W_abef r_ij^ef) and the ring
+// P(ij)P(ab) W_mbej r_im^ae.
+//
+// C[m*ldc + n] = alpha * sum_k A[m,k] B[n,k] + beta * C     (complex, both operands K-major)
+//
+// Each complex FP64 operand is split into BF16 slices, x = x_0 + x_1 (+ x_2): x_0 = bf16(x),
+// x_1 = bf16(x - x_0), ...; slice products (s,t) with s + t below the slice count are summed in
+// FP32 accumulators in tensor memory.  Real and imaginary parts are separate planes; the complex
+// product uses four real MMAs per k-step into two accumulators, the minus sign of Ai*Bi coming
+// from the instruction descriptor's negate-A bit, so no operand is duplicated in memory.
+//
+// CTA tile: 128 rows of the "A-side" MMA operand (= 128 consecutive n, one TMEM lane each) x BN
+// rows of the "B-side" operand (= BN consecutive m, TMEM columns).  Warp 0 issues TMA loads into
+// a STAGES-deep shared-memory ring, warp 1 issues tcgen05.mma, then all four warps drain TMEM
+// and write C with stores that are contiguous along n.  Every mbarrier wait is bounded: on
+// expiry the kernel records an error code, stops issuing work, releases TMEM and returns.
+#include "ctx.h"
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <algorithm>
+#include <cstdlib>
+#include <map>
+
+namespace cclr {
+
+namespace tc {
+
+constexpr int BM = 128;         // MMA M (TMEM lanes) = n-rows per CTA
+constexpr int BN = 128;         // MMA N = m-rows per CTA
+constexpr int BK = 64;          // K per stage (one 128-byte swizzle row of BF16)
+constexpr int STAGES = 3;
+constexpr int A_PLANE = BM * BK * 2;           // bytes of one BF16 plane tile
+constexpr int B_PLANE = BN * BK * 2;
+constexpr int STAGE_BYTES = 2 * A_PLANE + 2 * B_PLANE;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+constexpr int TMEM_COLS = 2 * BN;              // Cr | Ci
+constexpr int MAX_PAIRS = 6;
+
+struct Pairs {
+  int n;
+  int sa[MAX_PAIRS], sb[MAX_PAIRS];
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait: ~2^22 polls with back-off (about a second); false on expiry
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
+  for (uint32_t i = 0; i < (1u << 22); ++i) {
+    if (mbar_try_wait(b, parity)) return true;
+    if (i > 64) __nanosleep(256);
+  }
+  return false;
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, int x, int y, int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+          smem_u32(dst)),
+      "l"(tm), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);  // start address
+  d |= (uint64_t)1 << 16;                   // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;         // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                   // descriptor version (sm_100 family)
+  d |= (uint64_t)2 << 61;                   // 128-byte swizzle
+  return d;
+}
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, bool negA) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((negA ? 1u : 0u) << 13) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,"
+      "%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(128, 1)
+    k_tc_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int n_rows, int m_rows,
+               int kblocks, int kb_per, Pairs pairs, double2 alpha, double2 beta, double2* __restrict__ C, int64_t ldc,
+               int64_t cz, int* __restrict__ err, int ytile0) {
+  // split-K: blockIdx.z owns k-blocks [z*kb_per, min(kblocks, (z+1)*kb_per)) and writes C + z*cz;
+  // ytile0 offsets the n-tiles of this launch (tall operands are launched in row chunks)
+  const int kb0 = blockIdx.z * kb_per;
+  const int kb1 = min(kblocks, kb0 + kb_per);
+  C += (int64_t)blockIdx.z * cz;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* done = empty + STAGES;
+  uint32_t* tmem_slot = (uint32_t*)(done + 1);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 2) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int n0 = (ytile0 + (int)blockIdx.y) * BM;  // rows of the A-side operand (C columns)
+  const int m0 = blockIdx.x * BN;  // rows of the B-side operand (C rows)
+  const int iters = (kb1 - kb0) * pairs.n;   // >= 1: the host never creates an empty slice
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer
+    for (int it = 0; it < iters; ++it) {
+      const int s = it % STAGES;
+      const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+      if (!mbar_wait(&empty[s], ph ^ 1u)) { atomicExch(err, 1); *abort_flag = 1; break; }
+      if (*abort_flag) break;
+      const int kb = kb0 + it / pairs.n, p = it % pairs.n;
+      uint8_t* st = smem + s * STAGE_BYTES;
+      mbar_expect_tx(&full[s], STAGE_BYTES);
+      tma_load_3d(st, &tmA, kb * BK, n0, 2 * pairs.sa[p] + 0, &full[s]);
+      tma_load_3d(st + A_PLANE, &tmA, kb * BK, n0, 2 * pairs.sa[p] + 1, &full[s]);
+      tma_load_3d(st + 2 * A_PLANE, &tmB, kb * BK, m0, 2 * pairs.sb[p] + 0, &full[s]);
+      tma_load_3d(st + 2 * A_PLANE + B_PLANE, &tmB, kb * BK, m0, 2 * pairs.sb[p] + 1, &full[s]);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer (single thread)
+    constexpr uint32_t ID = idesc_bf16(BM, BN, false), IDN = idesc_bf16(BM, BN, true);
+    const uint32_t cr = tmem, ci = tmem + BN;
+    for (int it = 0; it < iters; ++it) {
+      const int s = it % STAGES;
+      const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+      if (!mbar_wait(&full[s], ph)) { atomicExch(err, 2); *abort_flag = 1; break; }
+      fence_after();
+      const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
+      const uint32_t ar = base, ai = base + A_PLANE, br = base + 2 * A_PLANE, bi = br + B_PLANE;
+#pragma unroll
+      for (int ks = 0; ks < BK / 16; ++ks) {
+        const uint32_t off = ks * 32;  // 16 BF16 = 32 bytes along K inside the swizzle row
+        const uint64_t dar = desc_sw128(ar + off), dai = desc_sw128(ai + off);
+        const uint64_t dbr = desc_sw128(br + off), dbi = desc_sw128(bi + off);
+        const uint32_t first = (it == 0 && ks == 0) ? 0u : 1u;
+        mma_bf16(cr, dar, dbr, ID, first);
+        mma_bf16(cr, dai, dbi, IDN, 1u);
+        mma_bf16(ci, dar, dbi, ID, first);
+        mma_bf16(ci, dai, dbr, ID, 1u);
+      }
+      mma_commit(&empty[s]);
+    }
+    mma_commit(done);
+  }
+  __syncwarp();
+  // ---------------- epilogue: TMEM -> registers -> C (contiguous along n across lanes)
+  const bool ok = mbar_wait(done, 0);
+  if (!ok && lane == 0) atomicExch(err, 3);
+  fence_after();
+  const int n = n0 + warp * 32 + lane;
+  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+  const bool use_beta = (beta.x != 0.0 || beta.y != 0.0);
+  if (ok) {
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 32) {
+      uint32_t rr[32], ri[32];
+      tmem_ld32(tmem + lane_base + c0, rr);
+      tmem_ld32(tmem + lane_base + BN + c0, ri);
+      if (n < n_rows) {
+#pragma unroll 4
+        for (int j = 0; j < 32; ++j) {
+          const int m = m0 + c0 + j;
+          if (m >= m_rows) break;
+          const double xr = (double)__uint_as_float(rr[j]), xi = (double)__uint_as_float(ri[j]);
+          double2 v = make_double2(alpha.x * xr - alpha.y * xi, alpha.x * xi + alpha.y * xr);
+          double2* cp = C + (int64_t)m * ldc + n;
+          if (use_beta) {
+            const double2 o = *cp;
+            v.x += beta.x * o.x - beta.y * o.y;
+            v.y += beta.x * o.y + beta.y * o.x;
+          }
+          *cp = v;
+        }
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 2) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+  }
+}
+
+// Strided complex FP64 view -> BF16 slice planes [slice][re|im][rows][Kpad].  The view is given
+// as up to 8 axes, the first nr of which form the row index and the rest the K index (row-major
+// order within each group), so any permutation of a tensor is split in one pass.
+struct ViewArgs {
+  int rank, nr;
+  int64_t dim[kMaxRank];
+  int64_t str[kMaxRank];
+};
+
+__global__ void k_split_view(const double2* __restrict__ X, ViewArgs v, int64_t rows, int64_t K, bool conj, int nsl,
+                             __nv_bfloat16* __restrict__ out, int64_t Kpad) {
+  const int64_t n = rows * Kpad;
+  const int64_t plane = rows * Kpad;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = idx / Kpad, k = idx - r * Kpad;
+    double2 x = make_double2(0.0, 0.0);
+    if (k < K) {
+      int64_t off = 0, rr = r, kk = k;
+#pragma unroll
+      for (int a = kMaxRank - 1; a >= 0; --a) {
+        if (a >= v.rank) continue;
+        if (a >= v.nr) {
+          const int64_t q = kk / v.dim[a];
+          off += (kk - q * v.dim[a]) * v.str[a];
+          kk = q;
+        } else {
+          const int64_t q = rr / v.dim[a];
+          off += (rr - q * v.dim[a]) * v.str[a];
+          rr = q;
+        }
+      }
+      x = X[off];
+      if (conj) x.y = -x.y;
+    }
+    double re = x.x, im = x.y;
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+      if (s >= nsl) break;
+      const __nv_bfloat16 hr = __float2bfloat16_rn((float)re), hi = __float2bfloat16_rn((float)im);
+      out[(2 * s + 0) * plane + idx] = hr;
+      out[(2 * s + 1) * plane + idx] = hi;
+      re -= (double)__bfloat162float(hr);
+      im -= (double)__bfloat162float(hi);
+    }
+  }
+}
+
+}  // namespace tc
+
+namespace {
+
+// The tensor-map encoder lives in the driver library; resolve it through the runtime so that
+// libcclr loads (and its CPU-side checks run) on machines without a GPU driver.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    CCLR_CK(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+    CCLR_REQUIRE(p && q == cudaDriverEntryPointSuccess, CCLR_E_CUDA, "cuTensorMapEncodeTiled not available");
+    fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+CUtensorMap make_map(const __nv_bfloat16* p, int64_t rows, int64_t Kpad, int nplanes, int box_rows) {
+  CUtensorMap tm;
+  cuuint64_t dims[3] = {(cuuint64_t)Kpad, (cuuint64_t)rows, (cuuint64_t)nplanes};
+  cuuint64_t strides[2] = {(cuuint64_t)(Kpad * 2), (cuuint64_t)(rows * Kpad * 2)};
+  cuuint32_t box[3] = {(cuuint32_t)tc::BK, (cuuint32_t)box_rows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = encode_tiled()(&tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)p, dims, strides, box, estr,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CCLR_REQUIRE(r == CUDA_SUCCESS, CCLR_E_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+  return tm;
+}
+
+// BF16 slices of one GEMM operand (rows x K, zero-padded to Kpad) with its TMA descriptor
+struct Slices {
+  __nv_bfloat16* p = nullptr;
+  int64_t rows = 0, K = 0, Kpad = 0;
+  int nsl = 0;
+  CUtensorMap tm;
+};
+
+// Slices of persistent operands (integrals, Hbar, amplitudes) are kept for one generation of
+// the context's data (bumped whenever any of them changes) keyed by pointer and view layout.
+struct CacheEntry {
+  Slices s;
+  uint64_t gen = 0;
+};
+std::map<std::string, CacheEntry>& cache() {
+  static std::map<std::string, CacheEntry> m;
+  return m;
+}
+uint64_t g_cache_gen = 0;
+
+void make_slices(Ctx& c, const Tensor& v, int nr, int nsl, Slices& s, __nv_bfloat16* dst) {
+  tc::ViewArgs a{};
+  a.rank = v.rank;
+  a.nr = nr;
+  int64_t rows = 1, K = 1;
+  for (int i = 0; i < v.rank; ++i) {
+    a.dim[i] = v.dim[i];
+    a.str[i] = v.str[i];
+    (i < nr ? rows : K) *= v.dim[i];
+  }
+  s.rows = rows;
+  s.K = K;
+  s.Kpad = (K + tc::BK - 1) / tc::BK * tc::BK;
+  s.nsl = nsl;
+  s.p = dst;
+  const int64_t n = rows * s.Kpad;
+  const int g = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 148 * 16));
+  tc::k_split_view<<<g, 256, 0, c.stream>>>(v.p, a, rows, K, v.conj, nsl, dst, s.Kpad);
+  CCLR_CK(cudaGetLastError());
+  ++c.launches;
+  s.tm = make_map(dst, rows, s.Kpad, 2 * nsl, 128);
+}
+
+bool is_persistent(const Ctx& c, const void* p) {
+  const void* arr[] = {c.Fae, c.Fmi, c.Fme, c.Wmnij, c.Wmnij_p, c.Wabef_p, c.Wmbej, c.WringR, c.WringL, c.Wmnie,
+                       c.Wamef, c.Wmbij, c.Wabei, c.tau, c.t2, c.l2, c.oooo, c.ooov, c.oovv, c.ovov, c.ovvv,
+                       c.vvvv_p, c.oovv_p, c.ovvv_p, c.t, c.lam};
+  for (const void* q : arr)
+    if (q && q == p) return true;
+  for (auto& kv : c.named)
+    if (kv.second == p && kv.first.rfind("F.", 0) == 0 && kv.first != "F.ready") return true;
+  return false;
+}
+
+// Slices of view v (first nr axes = rows): from the cache for persistent operands, else into
+// the workspace.
+Slices get_slices(Ctx& c, const Tensor& v, int nr, int nsl) {
+  if (g_cache_gen != data_generation()) {
+    for (auto& kv : cache()) cudaFree(kv.second.s.p);
+    cache().clear();
+    g_cache_gen = data_generation();
+  }
+  int64_t elems = 1;
+  for (int i = 0; i < v.rank; ++i) elems *= v.dim[i];
+  int64_t K = 1;
+  for (int i = nr; i < v.rank; ++i) K *= v.dim[i];
+  const int64_t Kpad = (K + tc::BK - 1) / tc::BK * tc::BK;
+  const size_t bytes = sizeof(__nv_bfloat16) * 2 * nsl * (size_t)(elems / K) * (size_t)Kpad;
+  Slices s;
+  static const double cap_gb = std::getenv("CCLR_TC_CACHE_GB") ? atof(std::getenv("CCLR_TC_CACHE_GB")) : 16.0;
+  size_t cached = 0;
+  for (auto& kv : cache()) cached += sizeof(__nv_bfloat16) * 2 * kv.second.s.nsl * kv.second.s.rows * kv.second.s.Kpad;
+  if (is_persistent(c, v.p) && (double)(cached + bytes) <= cap_gb * (double)(1ull << 30)) {
+    std::string key = std::to_string((uintptr_t)v.p) + "|" + std::to_string(nr) + "|" + std::to_string(nsl) + "|" +
+                      std::to_string((int)v.conj);
+    for (int i = 0; i < v.rank; ++i) key += "|" + std::to_string(v.dim[i]) + ":" + std::to_string(v.str[i]);
+    auto it = cache().find(key);
+    if (it != cache().end()) return it->second.s;
+    __nv_bfloat16* dst = nullptr;
+    if (cudaMalloc((void**)&dst, bytes) == cudaSuccess) {
+      make_slices(c, v, nr, nsl, s, dst);
+      cache()[key] = CacheEntry{s, data_generation()};
+      return s;
+    }
+    cudaGetLastError();  // out of memory for the cache: fall through to a workspace copy
+  }
+  make_slices(c, v, nr, nsl, s, (__nv_bfloat16*)c.ws.alloc(bytes));
+  return s;
+}
+
+tc::Pairs pairs_for(int nsl) {
+  tc::Pairs pairs{};
+  if (nsl == 2) {
+    pairs.n = 3;
+    const int sa[3] = {0, 0, 1}, sb[3] = {0, 1, 0};
+    for (int i = 0; i < 3; ++i) { pairs.sa[i] = sa[i]; pairs.sb[i] = sb[i]; }
+  } else {
+    pairs.n = 6;
+    const int sa[6] = {0, 0, 1, 0, 1, 2}, sb[6] = {0, 1, 0, 2, 1, 0};
+    for (int i = 0; i < 6; ++i) { pairs.sa[i] = sa[i]; pairs.sb[i] = sb[i]; }
+  }
+  return pairs;
+}
+
+}  // namespace
+
+uint64_t& data_generation() {
+  static uint64_t g = 1;
+  return g;
+}
+
+uint64_t& hbar_generation() { return data_generation(); }
+
+void tc_release_cache() {
+  for (auto& kv : cache()) cudaFree(kv.second.s.p);
+  cache().clear();
+}
+
+int tc_slices(int precision) { return precision == CCLR_TC_BF16X3 ? 2 : 3; }
+
+bool tc_eligible(int64_t M, int64_t N, int64_t K) {
+  // below ~2^24 complex multiply-adds the FP64 kernel finishes in ~0.1 ms and keeps full accuracy;
+  // short K is zero-padded to 64 (the tensor cores stay far ahead of the FP64 pipe even so)
+  return K >= 1 && M >= 1 && N >= 1 && M <= INT32_MAX && N <= INT32_MAX &&
+         (double)M * (double)N * (double)K >= 16777216.0;
+}
+
+// C[m*ldc + n] = alpha sum_k vm[m,k] vn[n,k] + beta C, vm / vn views whose first nr axes are the
+// rows (m resp. n) and whose remaining axes are K (same order in both).
+void tc_gemm_views(Ctx& c, const Tensor& vm, int nrm, const Tensor& vn, int nrn, cplx alpha, cplx beta, cplx* C,
+                   int64_t ldc) {
+  const int nsl = tc_slices(c.opt.precision);
+  const tc::Pairs pairs = pairs_for(nsl);
+  Scope sc(c.ws);
+  const Slices sn = get_slices(c, vn, nrn, nsl);   // MMA A-side: rows = n (TMEM lanes)
+  const Slices sm = get_slices(c, vm, nrm, nsl);   // MMA B-side: rows = m
+  CCLR_REQUIRE(sn.K == sm.K, CCLR_E_ARG, "tc_gemm: K mismatch");
+  const int64_t M = sm.rows, N = sn.rows;
+  static bool attr = false;
+  if (!attr) {
+    CCLR_CK(cudaFuncSetAttribute(tc::k_tc_zgemm, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES));
+    attr = true;
+  }
+  if (!c.tc_err) {  // device status word, checked by the API layer at the end of every call
+    CCLR_CK(cudaMalloc((void**)&c.tc_err, sizeof(int)));
+    CCLR_CK(cudaMemsetAsync(c.tc_err, 0, sizeof(int), c.stream));
+  }
+  const int kblocks = (int)(sn.Kpad / tc::BK);
+  const int64_t tiles = ((M + tc::BN - 1) / tc::BN) * ((N + tc::BM - 1) / tc::BM);
+  // split-K when the output has fewer tiles than SMs: each slice >= 4 k-blocks
+  int S = 1, kb_per = kblocks;
+  if (tiles < 148 && kblocks >= 8) {
+    S = (int)std::min<int64_t>((148 + tiles - 1) / tiles, kblocks / 4);
+    kb_per = (kblocks + S - 1) / S;
+    S = (kblocks + kb_per - 1) / kb_per;   // no empty slice
+  }
+  cplx* P = nullptr;
+  if (S > 1) P = c.ws.cplxs((int64_t)S * M * N);
+  const int64_t ytiles = (N + tc::BM - 1) / tc::BM, xtiles = (M + tc::BN - 1) / tc::BN;
+  CCLR_REQUIRE(xtiles < (int64_t)INT32_MAX, CCLR_E_ARG, "tc_gemm: M too large");
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (c.prof) c.prof_events(e0, e1);
+  if (e0) CCLR_CK(cudaEventRecord(e0, c.stream));
+  for (int64_t y0 = 0; y0 < ytiles; y0 += 65535) {   // grid.y limit: chunks of n-tiles
+    dim3 grid((unsigned)xtiles, (unsigned)std::min<int64_t>(65535, ytiles - y0), (unsigned)S);
+    if (S > 1)
+      tc::k_tc_zgemm<<<grid, 128, tc::SMEM_BYTES, c.stream>>>(sn.tm, sm.tm, (int)N, (int)M, kblocks, kb_per, pairs,
+                                                              make_double2(1.0, 0.0), make_double2(0.0, 0.0), P, N,
+                                                              M * N, c.tc_err, (int)y0);
+    else
+      tc::k_tc_zgemm<<<grid, 128, tc::SMEM_BYTES, c.stream>>>(sn.tm, sm.tm, (int)N, (int)M, kblocks, kb_per, pairs,
+                                                              alpha, beta, C, ldc, 0, c.tc_err, (int)y0);
+    const cudaError_t le = cudaGetLastError();
+    CCLR_REQUIRE(le == cudaSuccess, CCLR_E_CUDA,
+                 std::string("tensor-core GEMM launch failed (") + cudaGetErrorString(le) + ") M=" + std::to_string(M) +
+                     " N=" + std::to_string(N) + " K=" + std::to_string(sn.K) + " S=" + std::to_string(S));
+  }
+  if (e1) {
+    CCLR_CK(cudaEventRecord(e1, c.stream));
+    c.prof_flops_exec += 8.0 * (double)M * N * sn.K * pairs.n;
+    c.prof_flops_useful += 8.0 * (double)M * N * sn.K;
+  }
+  ++c.launches;
+  if (S > 1) splitk_reduce(c.L, P, S, M, N, alpha, beta, C, ldc);
+}
+
+bool tc_gemm_try(Ctx& c, bool ta, bool tb, int64_t M, int64_t N, int64_t K, cplx alpha, const cplx* A, int64_t lda,
+                 const cplx* B, int64_t ldb, cplx beta, cplx* C, int64_t ldc) {
+  if (!tc_eligible(M, N, K)) return false;
+  // 2-axis views (rows, K) of op(A) and op(B)^T; transposed storage is read with swapped strides
+  Tensor vm = Tensor::make((cplx*)A, {M, K}), vn = Tensor::make((cplx*)B, {N, K});
+  if (ta) { vm.str[0] = 1; vm.str[1] = lda; } else { vm.str[0] = lda; vm.str[1] = 1; }
+  if (tb) { vn.str[0] = ldb; vn.str[1] = 1; } else { vn.str[0] = 1; vn.str[1] = ldb; }
+  tc_gemm_views(c, vm, 1, vn, 1, alpha, beta, C, ldc);
+  return true;
+}
+
+}  // namespace cclr

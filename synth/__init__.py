@@ -98,10 +98,26 @@ class Instance:
         return self.n_occ + self.n_vir
 
 
-def make_instance(n_occ: int, n_vir: int, seed: int = DEFAULT_SEED, sd: float = 0.02,
+def integral_sd(n_occ: int, n_vir: int, sd0: float = 0.02) -> float:
+    """Integral standard deviation with the coupling-to-gap ratio of the 4-occupied/20-virtual
+    reference system.  A block of random antisymmetrized integrals over P pair (or
+    particle-hole) states is a random Hermitian P x P matrix with spectral radius ~2 sd sqrt(2P);
+    with sd fixed the ladder block grows past the orbital-energy gaps as n_vir grows (about 8 au
+    at 200 virtuals against a smallest doubles gap of 1.6 au) and the CC equations lose their
+    solution.  sd0 applies up to the reference size; beyond it sd shrinks as 1/sqrt of the
+    largest block dimension, which keeps that spectral radius at the reference value."""
+    ref = 20 * 19 // 2                                   # vv pair count of 20 virtuals
+    big = max(n_vir * (n_vir - 1) // 2, n_occ * n_vir, n_occ * (n_occ - 1) // 2)
+    return sd0 * min(1.0, float(np.sqrt(ref / max(big, 1))))
+
+
+def make_instance(n_occ: int, n_vir: int, seed: int = DEFAULT_SEED, sd: float | None = None,
                   dip_sd: float = 0.1, n_ops: int = 3, occ_range=(-2.0, -0.5),
                   vir_range=(0.3, 4.0)) -> Instance:
+    """sd: integral standard deviation per real component; None -> integral_sd(n_occ, n_vir)."""
     o, v = n_occ, n_vir
+    if sd is None:
+        sd = integral_sd(o, v)
     g = _rng(seed, 0)
     eo = np.sort(g.uniform(occ_range[0], occ_range[1], size=o))
     ev = np.sort(g.uniform(vir_range[0], vir_range[1], size=v))

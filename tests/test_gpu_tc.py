@@ -1,0 +1,63 @@
+"""Tensor-core (tcgen05) complex GEMM and mixed-precision sigma vectors against FP64.
+
+Bounds: split-BF16 with two slices (three products) keeps ~16 significant bits per operand, so a
+contraction is accurate to ~2^-16 relative (1e-4 bound below); three slices (six products) are
+limited by FP32 accumulation (1e-5 bound).  The errors must also be clearly nonzero, which shows
+that the tensor-core path (not the FP64 one) produced the result.
+"""
+import numpy as np
+import pytest
+
+import synth
+from layout import rel, to_amp
+from oracle.deriv import antisym
+
+pytestmark = pytest.mark.gpu
+BOUND = {2: 1e-4, 3: 1e-5}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import os
+    os.environ.setdefault("CCLR_WORKSPACE_GB", "4")
+    import paper_2307_14296_b300 as pk
+    inst = synth.make_instance(4, 10)
+    c = pk.Context(0)
+    c.cclr_set_hamiltonian(4, 10, inst.fock, [inst.blocks[k] for k in synth.CLASSES])
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("M,N,K", [(256, 256, 512), (300, 500, 250), (64, 129, 4000), (513, 640, 77), (40, 30, 20000)])
+@pytest.mark.parametrize("prec", [2, 3])
+def test_tc_zgemm_matches_fp64(ctx, M, N, K, prec):
+    A = synth.random_vector((M, K), 3, 1)
+    B = synth.random_vector((N, K), 3, 2)
+    ref = A @ B.T
+    got = ctx.cclr_zgemm_nt(A, B, precision=prec)
+    err = rel(got, ref)
+    assert err < BOUND[prec], err
+    assert err > 1e-12  # the BF16 path really ran
+    f64 = ctx.cclr_zgemm_nt(A, B, precision=0)
+    assert rel(f64, ref) < 1e-13
+
+
+@pytest.mark.parametrize("prec", [2, 3])
+def test_tc_sigma_matches_fp64(prec):
+    import paper_2307_14296_b300 as pk
+    o, v = 6, 40
+    inst = synth.make_instance(o, v, seed=5)
+    c = pk.Context(0)
+    c.cclr_set_hamiltonian(o, v, inst.fock, [inst.blocks[k] for k in synth.CLASSES])
+    t1 = synth.random_vector((o, v), 1, 1, 0.05)
+    t2 = antisym(synth.random_vector((o, o, v, v), 1, 2, 0.05))
+    c.cclr_set_amplitudes(pk.AMP_T, to_amp(t1, t2))
+    vecs = np.stack([to_amp(synth.random_vector((o, v), 2, 2 * k, 1.0),
+                            antisym(synth.random_vector((o, o, v, v), 2, 2 * k + 1, 1.0))) for k in range(8)])
+    for side in (0, 1):
+        ref = c.cclr_sigma(vecs, side=side, precision=pk.FP64)
+        got = c.cclr_sigma(vecs, side=side, precision=prec)
+        err = rel(got, ref)
+        assert err < BOUND[prec], (side, err)
+        assert err > 1e-12
+    c.close()
