@@ -160,6 +160,25 @@ cclr_status cclr_hessian(cclr_ctx *ctx, int nvec, const cclr_c128 *u, cclr_c128 
 cclr_status cclr_zgemm_nt(cclr_ctx *ctx, int precision, int M, int N, int K, const cclr_c128 *A,
                           const cclr_c128 *B, cclr_c128 *C);
 
+/* Allocation-free tensor-core GEMM (the paper has no counterpart; it serves callers that cannot
+ * allocate device memory: a framework that owns all device memory through its own pool, a
+ * server that fixes its footprint after start-up, or code running where an allocation may block).
+ *   C[m][n] = sum_k A[m][k] B[n][k]   complex, row-major, DEVICE pointers on the current device,
+ *   A: M x K, B: N x K, C: M x N (written, not accumulated); precision CCLR_TC_BF16X3 or
+ *   CCLR_TC_BF16X6 (same slicing and kernel as the context's tensor-core contractions).
+ * No context, and no cudaMalloc / cudaFree or allocating library call: every temporary (BF16
+ * operand slices, split-K partial tiles, the kernel's status word) lives in one fixed 64 MiB
+ * file-scope device array that each device holds from library load until process exit.
+ * Sizes whose temporaries exceed it return CCLR_E_ARG with no GPU work (a square problem fits up
+ * to M = N = K of about 1000 with three products).  stream may be NULL (legacy default stream); the call
+ * returns after the result is complete.  The first call on a device resolves the array's device
+ * address with that device current; make that first call before any stream capture.  Every
+ * call shares the array and each call clears the status word it uses, so calls that overlap on
+ * the GPU (other streams, other host threads) race and must be serialized by the caller.
+ * Returns CCLR_E_TIMEOUT if a bounded device wait expired, CCLR_E_CUDA on a runtime error. */
+cclr_status cclr_zgemm_nt_noalloc(int precision, int M, int N, int K, const cclr_c128 *A, const cclr_c128 *B,
+                                  cclr_c128 *C, void *stream);
+
 /* Timing of the tensor-core GEMM kernel with CUDA events recorded on the context's stream around
  * every launch.  enable != 0 switches recording on.  out4 (may be NULL) receives, accumulated
  * since the previous call: {launches, milliseconds, executed BF16 flops (8 M N K per slice

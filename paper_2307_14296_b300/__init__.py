@@ -33,6 +33,7 @@ EXPORTS = (
     "cc_ground", "cc_lambda", "cc_lr_solve", "cc_response_function", "cclr_get_amplitudes",
     "cclr_set_amplitudes", "cclr_get_response_vector", "cclr_sigma", "cclr_residual", "cclr_xi",
     "cclr_eta", "cclr_hessian", "cclr_zgemm_nt", "cclr_kernel_profile", "cclr_get_stats",
+    "cclr_zgemm_nt_noalloc",
 )
 
 
@@ -68,6 +69,7 @@ _sig = {
     "cclr_hessian": (_i, [_vp, _i, _vp, _vp, _i]),
     "cclr_zgemm_nt": (_i, [_vp, _i, _i, _i, _i, _vp, _vp, _vp]),
     "cclr_kernel_profile": (_i, [_vp, _i, _vp]),
+    "cclr_zgemm_nt_noalloc": (_i, [_i, _i, _i, _i, _vp, _vp, _vp, _vp]),
     "cclr_get_stats": (_i, [_vp, ctypes.POINTER(Stats)]),
 }
 for _name, (_res, _args) in _sig.items():
@@ -270,6 +272,17 @@ def cc_lr_solve(ctx, ops, omegas, gamma):
 
 def cc_response_function(ctx):
     return ctx.cc_response_function()
+
+
+def cclr_zgemm_nt_noalloc(A, B, C, precision=TC_BF16X3, stream=None) -> int:
+    """C = A B^T on the tensor cores without any device allocation (torch CUDA complex128 tensors,
+    contiguous, on the current device; C is written).  For callers that cannot allocate device
+    memory; the library keeps its temporaries in one fixed 64 MiB device array shared by all
+    calls, so overlapping calls race.  Returns the C-ABI status code (0 = success)."""
+    M, K = A.shape
+    N = B.shape[0]
+    s = _vp(stream.cuda_stream) if stream is not None else _vp()
+    return _lib.cclr_zgemm_nt_noalloc(precision, M, N, K, _vp(A.data_ptr()), _vp(B.data_ptr()), _vp(C.data_ptr()), s)
 
 
 def library_path() -> str:

@@ -512,4 +512,95 @@ bool tc_gemm_try(Ctx& c, bool ta, bool tb, int64_t M, int64_t N, int64_t K, cplx
   return true;
 }
 
+// ---------------------------------------------------------------------------------------------
+// Building blocks of the allocation-free GEMM entry point (noalloc.cu): the same slicing, kernel
+// and split-K choice as tc_gemm_views, with every temporary placed in caller-provided scratch.
+// Scratch layout: [status word, 256 B][slices of B (n rows)][slices of A (m rows)][split-K partials]
+
+namespace {
+struct RawPlan {
+  int64_t Kpad, bytes_sn, bytes_sm, bytes_p;
+  int S, kb_per, kblocks;
+};
+RawPlan raw_plan(int nsl, int64_t M, int64_t N, int64_t K) {
+  RawPlan p{};
+  p.Kpad = (K + tc::BK - 1) / tc::BK * tc::BK;
+  p.bytes_sn = (int64_t)sizeof(__nv_bfloat16) * 2 * nsl * N * p.Kpad;
+  p.bytes_sm = (int64_t)sizeof(__nv_bfloat16) * 2 * nsl * M * p.Kpad;
+  p.kblocks = (int)(p.Kpad / tc::BK);
+  const int64_t tiles = ((M + tc::BN - 1) / tc::BN) * ((N + tc::BM - 1) / tc::BM);
+  p.S = 1;
+  p.kb_per = p.kblocks;
+  if (tiles < 148 && p.kblocks >= 8) {
+    p.S = (int)std::min<int64_t>((148 + tiles - 1) / tiles, p.kblocks / 4);
+    p.kb_per = (p.kblocks + p.S - 1) / p.S;
+    p.S = (p.kblocks + p.kb_per - 1) / p.kb_per;
+  }
+  p.bytes_p = p.S > 1 ? (int64_t)sizeof(cplx) * p.S * M * N : 0;
+  return p;
+}
+int64_t up256(int64_t b) { return (b + 255) / 256 * 256; }
+}  // namespace
+
+int64_t tc_raw_scratch_bytes(int precision, int64_t M, int64_t N, int64_t K) {
+  const RawPlan p = raw_plan(tc_slices(precision), M, N, K);
+  return 256 + up256(p.bytes_sn) + up256(p.bytes_sm) + up256(p.bytes_p);
+}
+
+// C[m*N + n] = sum_k A[m*K + k] B[n*K + k] on `stream`, synchronously; returns the status word
+// (0 = every bounded wait completed).
+int tc_raw_gemm_nt(int precision, int64_t M, int64_t N, int64_t K, const cplx* A, const cplx* B, cplx* C, char* scratch,
+                   cudaStream_t stream) {
+  const int nsl = tc_slices(precision);
+  const RawPlan p = raw_plan(nsl, M, N, K);
+  int* err = (int*)scratch;
+  __nv_bfloat16* sn = (__nv_bfloat16*)(scratch + 256);
+  __nv_bfloat16* sm = (__nv_bfloat16*)(scratch + 256 + up256(p.bytes_sn));
+  cplx* P = (cplx*)(scratch + 256 + up256(p.bytes_sn) + up256(p.bytes_sm));
+  CCLR_CK(cudaMemsetAsync(err, 0, sizeof(int), stream));   // the shared scratch keeps the last call's flag
+  auto split = [&](const cplx* X, int64_t rows, __nv_bfloat16* dst) {
+    tc::ViewArgs a{};
+    a.rank = 2;
+    a.nr = 1;
+    a.dim[0] = rows;
+    a.dim[1] = K;
+    a.str[0] = K;
+    a.str[1] = 1;
+    const int64_t n = rows * p.Kpad;
+    const int g = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 148 * 16));
+    tc::k_split_view<<<g, 256, 0, stream>>>(X, a, rows, K, false, nsl, dst, p.Kpad);
+    CCLR_CK(cudaGetLastError());
+  };
+  split(B, N, sn);
+  split(A, M, sm);
+  const CUtensorMap tn = make_map(sn, N, p.Kpad, 2 * nsl, 128), tm = make_map(sm, M, p.Kpad, 2 * nsl, 128);
+  static bool attr = false;
+  if (!attr) {
+    CCLR_CK(cudaFuncSetAttribute(tc::k_tc_zgemm, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES));
+    attr = true;
+  }
+  const tc::Pairs pairs = pairs_for(nsl);
+  const int64_t ytiles = (N + tc::BM - 1) / tc::BM, xtiles = (M + tc::BN - 1) / tc::BN;
+  const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
+  for (int64_t y0 = 0; y0 < ytiles; y0 += 65535) {
+    dim3 grid((unsigned)xtiles, (unsigned)std::min<int64_t>(65535, ytiles - y0), (unsigned)p.S);
+    if (p.S > 1)
+      tc::k_tc_zgemm<<<grid, 128, tc::SMEM_BYTES, stream>>>(tn, tm, (int)N, (int)M, p.kblocks, p.kb_per, pairs, one,
+                                                            zero, P, N, M * N, err, (int)y0);
+    else
+      tc::k_tc_zgemm<<<grid, 128, tc::SMEM_BYTES, stream>>>(tn, tm, (int)N, (int)M, p.kblocks, p.kb_per, pairs, one,
+                                                            zero, C, N, 0, err, (int)y0);
+    CCLR_CK(cudaGetLastError());
+  }
+  if (p.S > 1) {
+    Launch L;
+    L.s = stream;
+    splitk_reduce(L, P, p.S, M, N, one, zero, C, N);
+  }
+  int h = 0;
+  CCLR_CK(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, stream));
+  CCLR_CK(cudaStreamSynchronize(stream));
+  return h;
+}
+
 }  // namespace cclr
