@@ -29,7 +29,13 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = dict(n_occ=30, n_vir=200, n_freq=16, w_min=0.05, w_max=0.30, gamma=0.005, n_ops=3, tol=1e-8)
+WORKLOADS = {
+    # diatomic scale (the benchmark workload)
+    "30x200": dict(n_occ=30, n_vir=200, n_freq=16, w_min=0.05, w_max=0.30, gamma=0.005, n_ops=3, tol=1e-8),
+    # smaller replica of the same path (profiling captures that must stay small)
+    "12x90": dict(n_occ=12, n_vir=90, n_freq=4, w_min=0.05, w_max=0.30, gamma=0.005, n_ops=3, tol=1e-8),
+}
+WORKLOAD = WORKLOADS["30x200"]
 METRIC = "CC-LR sigma TFLOP/s and s per converged α(ω) at 1e-6; mixed/batched vs FP64"
 
 
@@ -173,7 +179,8 @@ def config_dict(args):
                          f"{w['n_ops']} dipole operators, {w['n_freq']} frequencies on [{w['w_min']},{w['w_max']}] au, "
                          f"gamma {w['gamma']} au, synthetic complex antisymmetrized integrals"),
             "n_occ": w["n_occ"], "n_vir": w["n_vir"], "n_freq": w["n_freq"], "gamma": w["gamma"],
-            "precision": args.precision, "l2": "inputs larger than L2 (vvvv block 6.3 GB)"}
+            "precision": args.precision,
+            "l2": "inputs larger than L2 (packed vvvv block %.2f GB)" % (16 * (w["n_vir"] * (w["n_vir"] - 1) / 2) ** 2 / 1e9)}
 
 
 # ------------------------------------------------------------------------------------------ GPU
@@ -186,7 +193,10 @@ def main():
     ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="30x200", choices=sorted(WORKLOADS))
     args = ap.parse_args()
+    global WORKLOAD
+    WORKLOAD = WORKLOADS[args.workload]
     world, rank, local = dist_init()
     if args.impl == "reference":
         run_reference(args, world, rank)
