@@ -222,20 +222,26 @@ def main():
     def step():
         st = {}
         e, it = ctx.cc_ground()
+        s = ctx.cclr_get_stats()
         st["ground_iters"] = it
-        st["launches"] = ctx.cclr_get_stats()["kernel_launches"]
-        st["lambda_sigma"] = ctx.cc_lambda()
+        st["launches"] = s["kernel_launches"]
+        st["phase"] = {"ground": s["total_seconds"]}
+        ctx.cc_lambda()
         s = ctx.cclr_get_stats()
         st["launches"] += s["kernel_launches"]
         st["lambda_sigma"] = s["sigma_vectors"]
+        st["phase"]["lambda"] = s["total_seconds"]
         ctx.cc_lr_solve(host[7], omegas, w["gamma"])
         s = ctx.cclr_get_stats()
         st["lr_sigma"] = s["sigma_vectors"]
         st["launches"] += s["kernel_launches"]
+        st["phase"]["lr_solve"] = s["total_seconds"]
+        st["phase"]["lr_sigma"] = s["sigma_seconds"]
         resp = ctx.cc_response_function()
         s = ctx.cclr_get_stats()
         st["launches"] += s["kernel_launches"]
         st["hessian"] = s["sigma_vectors"]
+        st["phase"]["response_function"] = s["total_seconds"]
         st["resp"] = resp
         return st
 
@@ -299,6 +305,8 @@ def main():
         dtype="bf16x3+f64" if prec != pk.FP64 else "f64", data="synthetic", config=config_dict(args),
         s_per_alpha=t_step / w["n_freq"],
         sigma_products_per_step=n_prod,
+        phase_seconds={k: statistics.mean(s["phase"][k] for s in stats) for k in stats[0]["phase"]},
+        counts={k: statistics.mean(s[k] for s in stats) for k in ("ground_iters", "lambda_sigma", "lr_sigma", "hessian")},
         roofline=dict(bound="tensor", kernel="k_tc_zgemm (tcgen05 split-BF16 complex GEMM)", achieved=achieved,
                       peak=peak, unit="TFLOP/s", frac=(achieved / peak if achieved else None), traffic=None,
                       peak_source=f"bf16_tflops_sustained of {src} MEASURED_PEAKS",

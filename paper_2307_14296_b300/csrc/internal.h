@@ -112,6 +112,10 @@ struct Scope {  // RAII release of arena temporaries
 struct Launch {  // stream + launch counter shared by all kernels of one context
   cudaStream_t s = nullptr;
   long* count = nullptr;
+  // FP32 arithmetic (FP64 storage, FP64 accumulation across 16-element runs) in the solver's
+  // search-direction kernels (dots, lincomb, residual/preconditioner); Gram blocks stay FP64.
+  // Set by the iterative solvers in the tensor-core modes only.
+  bool fast32 = false;
 };
 
 // dst = alpha * op(src) + (accumulate ? dst : 0), element-wise over dst's shape; src must

@@ -336,6 +336,90 @@ __global__ void __launch_bounds__(kThreads) k_resid_precond(int64_t n, int nb, c
   if (threadIdx.x == 0) partial[blockIdx.x] = v.x;
 }
 
+// ---- FP32-arithmetic variants of the solver's vector kernels (FP64 storage).  FP64 on sm_103 runs
+// at ~1/64 of FP32, and these kernels do 4-8 L flops per element (L = trial-space size), so in
+// FP64 they are ALU-bound by a wide margin.  Products are formed and summed in FP32 over runs of
+// 16 elements; the runs are added in FP64, which keeps ~1e-7 relative accuracy.
+__device__ __forceinline__ float2 f2(cplx a) { return make_float2((float)a.x, (float)a.y); }
+constexpr int kMaxVec32 = 256;   // largest coefficient count of the FP32 lincomb / residual kernels
+
+__global__ void __launch_bounds__(kThreads) k_dots_partial32(int64_t n, const cplx* __restrict__ x, int64_t ldx,
+                                                             const cplx* __restrict__ y, int64_t ldy, bool herm,
+                                                             cplx* partial) {
+  const int k = blockIdx.y;
+  const cplx* xk = x + k * ldx;
+  const cplx* yk = y + k * ldy;
+  cplx s = make_double2(0.0, 0.0);
+  float2 f = make_float2(0.f, 0.f);
+  int run = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    float2 a = f2(xk[i]);
+    if (herm) a.y = -a.y;
+    const float2 b = f2(yk[i]);
+    f.x = fmaf(a.x, b.x, fmaf(-a.y, b.y, f.x));
+    f.y = fmaf(a.x, b.y, fmaf(a.y, b.x, f.y));
+    if (++run == 16) { s.x += f.x; s.y += f.y; f = make_float2(0.f, 0.f); run = 0; }
+  }
+  s.x += f.x;
+  s.y += f.y;
+  s = block_sum(s);
+  if (threadIdx.x == 0) partial[(int64_t)k * gridDim.x + blockIdx.x] = s;
+}
+
+__global__ void k_lincomb32(int64_t n, int nb, const cplx* __restrict__ X, int64_t ldx, const cplx* __restrict__ c,
+                            cplx* y, bool acc) {
+  __shared__ float2 cs[kMaxVec32];   // the host guarantees nb <= kMaxVec32
+  for (int j = threadIdx.x; j < nb; j += blockDim.x) cs[j] = f2(c[j]);
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    float2 s = make_float2(0.f, 0.f);
+    for (int j = 0; j < nb; ++j) {
+      const float2 a = cs[j], b = f2(X[j * ldx + i]);
+      s.x = fmaf(a.x, b.x, fmaf(-a.y, b.y, s.x));
+      s.y = fmaf(a.x, b.y, fmaf(a.y, b.x, s.y));
+    }
+    cplx out = make_double2((double)s.x, (double)s.y);
+    if (acc) out = cadd(out, y[i]);
+    y[i] = out;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_resid_precond32(int64_t n, int nb, const cplx* __restrict__ S,
+                                                              const cplx* __restrict__ B, int64_t ld,
+                                                              const cplx* __restrict__ beta, cplx z,
+                                                              const cplx* __restrict__ xi,
+                                                              const double* __restrict__ D, cplx* r_out, cplx* delta,
+                                                              double* partial) {
+  __shared__ float2 bs[kMaxVec32], bz[kMaxVec32];   // beta_j and -z beta_j (nb <= kMaxVec32)
+  for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+    const cplx b = beta[j];
+    bs[j] = f2(b);
+    bz[j] = make_float2((float)(-(z.x * b.x - z.y * b.y)), (float)(-(z.x * b.y + z.y * b.x)));
+  }
+  __syncthreads();
+  double s2 = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    float2 acc = make_float2(0.f, 0.f);
+    for (int j = 0; j < nb; ++j) {
+      const float2 sj = f2(S[j * ld + i]), bj = f2(B[j * ld + i]);
+      acc.x = fmaf(bs[j].x, sj.x, fmaf(-bs[j].y, sj.y, acc.x));
+      acc.y = fmaf(bs[j].x, sj.y, fmaf(bs[j].y, sj.x, acc.y));
+      acc.x = fmaf(bz[j].x, bj.x, fmaf(-bz[j].y, bj.y, acc.x));
+      acc.y = fmaf(bz[j].x, bj.y, fmaf(bz[j].y, bj.x, acc.y));
+    }
+    const cplx x0 = xi[i];
+    const cplx r = make_double2(x0.x + (double)acc.x, x0.y + (double)acc.y);
+    if (r_out) r_out[i] = r;
+    s2 = fma(r.x, r.x, fma(r.y, r.y, s2));
+    const double dr = D[i] - z.x, di = -z.y;
+    const double inv = 1.0 / (dr * dr + di * di);
+    const cplx q = cmul(r, make_double2(dr * inv, -di * inv));
+    delta[i] = make_double2(-q.x, -q.y);
+  }
+  cplx v = block_sum(make_double2(s2, 0.0));
+  if (threadIdx.x == 0) partial[blockIdx.x] = v.x;
+}
+
 __global__ void k_sum_real(const double* partial, int nb, double* out) {
   double s = 0.0;
   for (int i = threadIdx.x; i < nb; i += blockDim.x) s += partial[i];
@@ -504,8 +588,8 @@ void gram(const Launch& L, int64_t n, int nx, const cplx* X, int64_t ldx, int ny
   int nblk = (int)std::min<int64_t>(kReduceBlocks, (n + kGramChunk - 1) / kGramChunk);
   if (nblk < 1) nblk = 1;
   if ((int64_t)nblk * nout > scratch_elems) nblk = (int)std::max<int64_t>(1, scratch_elems / nout);
-  const size_t shm = sizeof(cplx) * (size_t)(nx + ny) * kGramChunk;
-  k_gram_partial<<<nblk, 256, shm, L.s>>>(n, nx, X, ldx, ny, Y, ldy, herm, scratch);
+  k_gram_partial<<<nblk, 256, sizeof(cplx) * (size_t)(nx + ny) * kGramChunk, L.s>>>(n, nx, X, ldx, ny, Y, ldy, herm,
+                                                                                   scratch);
   CCLR_CK(cudaGetLastError());
   k_gram_reduce<<<(nout + 255) / 256, 256, 0, L.s>>>(scratch, nblk, nout, out_dev);
   CCLR_CK(cudaGetLastError());
@@ -640,7 +724,8 @@ void dots(const Launch& L, int64_t n, int nvec, const cplx* x, int64_t ldx, cons
           cplx* out_dev, cplx* scratch) {
   if (nvec <= 0) return;
   dim3 g(kReduceBlocks, nvec);
-  k_dots_partial<<<g, kThreads, 0, L.s>>>(n, x, ldx, y, ldy, herm, scratch);
+  if (L.fast32) k_dots_partial32<<<g, kThreads, 0, L.s>>>(n, x, ldx, y, ldy, herm, scratch);
+  else k_dots_partial<<<g, kThreads, 0, L.s>>>(n, x, ldx, y, ldy, herm, scratch);
   CCLR_CK(cudaGetLastError());
   k_sum_partials<<<nvec, kThreads, 0, L.s>>>(scratch, kReduceBlocks, out_dev);
   CCLR_CK(cudaGetLastError());
@@ -655,7 +740,8 @@ void proj(const Launch& L, int64_t n, int nb, const cplx* B, int64_t ldb, const 
 void lincomb(const Launch& L, int64_t n, int nb, const cplx* X, int64_t ldx, const cplx* c_dev, cplx* y,
              bool accumulate) {
   if (n <= 0) return;
-  k_lincomb<<<grid_for(n), kThreads, 0, L.s>>>(n, nb, X, ldx, c_dev, y, accumulate);
+  if (L.fast32 && nb <= kMaxVec32) k_lincomb32<<<grid_for(n), kThreads, 0, L.s>>>(n, nb, X, ldx, c_dev, y, accumulate);
+  else k_lincomb<<<grid_for(n), kThreads, 0, L.s>>>(n, nb, X, ldx, c_dev, y, accumulate);
   CCLR_CK(cudaGetLastError());
   bump(L);
 }
@@ -663,7 +749,10 @@ void lincomb(const Launch& L, int64_t n, int nb, const cplx* X, int64_t ldx, con
 void residual_precond(const Launch& L, int64_t n, int nb, const cplx* S, const cplx* B, int64_t ld,
                       const cplx* beta_dev, cplx z, const cplx* xi, const double* D, cplx* r_out, cplx* delta,
                       double* rnorm2_dev, double* scratch) {
-  k_resid_precond<<<kReduceBlocks, kThreads, 0, L.s>>>(n, nb, S, B, ld, beta_dev, z, xi, D, r_out, delta, scratch);
+  if (L.fast32 && nb <= kMaxVec32)
+    k_resid_precond32<<<kReduceBlocks, kThreads, 0, L.s>>>(n, nb, S, B, ld, beta_dev, z, xi, D, r_out, delta, scratch);
+  else
+    k_resid_precond<<<kReduceBlocks, kThreads, 0, L.s>>>(n, nb, S, B, ld, beta_dev, z, xi, D, r_out, delta, scratch);
   CCLR_CK(cudaGetLastError());
   k_sum_real<<<1, kThreads, 0, L.s>>>(scratch, kReduceBlocks, rnorm2_dev);
   CCLR_CK(cudaGetLastError());

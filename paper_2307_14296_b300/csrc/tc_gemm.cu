@@ -436,10 +436,11 @@ void tc_release_cache() {
 int tc_slices(int precision) { return precision == CCLR_TC_BF16X3 ? 2 : 3; }
 
 bool tc_eligible(int64_t M, int64_t N, int64_t K) {
-  // below ~2^24 complex multiply-adds the FP64 kernel finishes in ~0.1 ms and keeps full accuracy;
-  // short K is zero-padded to 64 (the tensor cores stay far ahead of the FP64 pipe even so)
+  // below ~2^18 complex multiply-adds the FP64 kernel is as fast as a tensor-core launch (a few
+  // us) and keeps full accuracy; above it the FP64 pipe (~7.6 GFLOP/s per SM on sm_103) loses by
+  // orders of magnitude.  Short K is zero-padded to 64.
   return K >= 1 && M >= 1 && N >= 1 && M <= INT32_MAX && N <= INT32_MAX &&
-         (double)M * (double)N * (double)K >= 16777216.0;
+         (double)M * (double)N * (double)K >= 262144.0;
 }
 
 // C[m*ldc + n] = alpha sum_k vm[m,k] vn[n,k] + beta C, vm / vn views whose first nr axes are the
