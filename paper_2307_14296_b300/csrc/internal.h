@@ -7,6 +7,7 @@
 #include <vector>
 #include <stdexcept>
 #include <initializer_list>
+#include <algorithm>
 #include "../../include/cclr.h"
 
 namespace cclr {
@@ -112,9 +113,8 @@ struct Scope {  // RAII release of arena temporaries
 struct Launch {  // stream + launch counter shared by all kernels of one context
   cudaStream_t s = nullptr;
   long* count = nullptr;
-  // FP32 arithmetic (FP64 storage, FP64 accumulation across 16-element runs) in the solver's
-  // search-direction kernels (dots, lincomb, residual/preconditioner); Gram blocks stay FP64.
-  // Set by the iterative solvers in the tensor-core modes only.
+  // FP32 arithmetic (FP64 storage) in the solvers' vector kernels (dots, vecmat, Gram blocks);
+  // set by the iterative solvers in the tensor-core modes only.
   bool fast32 = false;
 };
 
@@ -136,6 +136,61 @@ void pack_doubles_impl(const Launch& L, const Tensor& X, cplx* D, int64_t nvec, 
 // unpack: X(Z,i,j,a,b) = D[z][P(i,j)][P(a,b)] with antisymmetry signs (0 on the diagonals)
 void unpack_doubles(const Launch& L, const cplx* D, int64_t ld_vec, const Tensor& X, int o, int v);
 
+// Up to four segments of equally strided device vectors, read as one list of rows
+// (row j of segment s is p[s] + j * ld[s]).
+struct Rows {
+  const cplx* p[4] = {};
+  int64_t ld[4] = {};
+  int cnt[4] = {};
+  int ns = 0;
+  __host__ __device__ int total() const {
+    int t = 0;
+    for (int s = 0; s < ns; ++s) t += cnt[s];
+    return t;
+  }
+  Rows& add(const cplx* ptr, int count, int64_t stride) {
+    if (count > 0) {
+      if (ns == 4) throw Error(CCLR_E_ARG, "Rows: more than four segments");
+      p[ns] = ptr; cnt[ns] = count; ld[ns] = stride; ++ns;
+    }
+    return *this;
+  }
+  Rows slice(int j0, int n) const {   // rows [j0, j0 + n)
+    Rows r;
+    for (int s = 0; s < ns && n > 0; ++s) {
+      if (j0 >= cnt[s]) { j0 -= cnt[s]; continue; }
+      const int take = std::min(cnt[s] - j0, n);
+      r.add(p[s] + (int64_t)j0 * ld[s], take, ld[s]);
+      n -= take;
+      j0 = 0;
+    }
+    return r;
+  }
+};
+
+// Multi-output linear combination over n elements, one pass over the inputs:
+//   r_q = sum_j X_j C[j*m + q] + add,  q < m <= 16
+//   Y_q = (D ? -r_q / (D - z_q) : r_q) + (acc ? Y_q : 0)
+// with optional |r_q|^2 and |Y_q|^2.  Products and sums in FP32 when Launch::fast32 (FP64
+// storage), otherwise FP64.  All device pointers; C has X.total() x m entries.
+struct VecMat {
+  Rows X;
+  int m = 0;
+  const cplx* C = nullptr;
+  const cplx* add = nullptr;
+  cplx* Y = nullptr;
+  int64_t ldy = 0;
+  bool acc = false;
+  const double* D = nullptr;
+  const cplx* z = nullptr;
+  double* rnorm2 = nullptr;
+  double* ynorm2 = nullptr;
+};
+constexpr int kVecMatOut = 16;        // outputs per pass
+constexpr int kVecMatMaxRows = 512;   // inputs per pass
+int64_t vecmat_scratch_doubles();
+void vecmat(const Launch& L, int64_t n, const VecMat& a, double* scratch);
+
 // Vector kernels over n complex elements (batched over nvec contiguous vectors of length n).
 void axpy(const Launch& L, int64_t n, cplx a, const cplx* x, cplx* y);                  // y += a x
 // out[k] = sum_i op(x_k[i]) * y_k[i] (conj x if herm) for k < nvec, x_k = x + k*ldx
@@ -147,14 +202,6 @@ void proj(const Launch& L, int64_t n, int nb, const cplx* B, int64_t ldb, const 
 // y = sum_j c[j] X_j + (accumulate ? y : 0) with coefficients on the device
 void lincomb(const Launch& L, int64_t n, int nb, const cplx* X, int64_t ldx, const cplx* c_dev, cplx* y,
              bool accumulate);
-
-// Fused Davidson residual and preconditioner (SI Davidson step 3-4):
-//   r = sum_j beta_j (S_j - z B_j) + xi;  delta = -r / (D - z);  rnorm2 = |r|^2
-// S, B: nb vectors (stride ld); beta on device; writes r (optional) and delta; rnorm2 to
-// rnorm2_dev[0] (deterministic two-pass reduction through scratch).
-void residual_precond(const Launch& L, int64_t n, int nb, const cplx* S, const cplx* B, int64_t ld,
-                      const cplx* beta_dev, cplx z, const cplx* xi, const double* D, cplx* r_out,
-                      cplx* delta, double* rnorm2_dev, double* scratch);
 
 int reduce_blocks();
 
@@ -170,10 +217,11 @@ void splitk_reduce(const Launch& L, const cplx* P, int S, int64_t M, int64_t N, 
 //   unpack2: X[r,p,q] = +-D[r*ldd + P(min,max)], 0 for p == q
 void pack2(const Launch& L, const Tensor& X, cplx* D, int64_t ldd, const int2* tab, cplx alpha, bool anti, bool acc);
 void unpack2(const Launch& L, const cplx* D, int64_t ldd, const Tensor& X);
-// Gram block out[i*ny + j] = sum_n op(X_i[n]) Y_j[n] (conj X if herm), nx, ny <= 64;
-// scratch must hold reduce_blocks() * nx * ny elements.
-void gram(const Launch& L, int64_t n, int nx, const cplx* X, int64_t ldx, int ny, const cplx* Y, int64_t ldy, bool herm,
-          cplx* out_dev, cplx* scratch, int64_t scratch_elems);
+// Gram block out[i*ny + j] = sum_n op(X_i[n]) Y_j[n] (conj X if herm) over row lists with
+// nx * ny <= 4096 and nx + ny <= 256; FP32 products summed in FP64 per 16 elements when
+// Launch::fast32, FP64 otherwise.  scratch must hold reduce_blocks() * nx * ny elements.
+void gram(const Launch& L, int64_t n, const Rows& X, const Rows& Y, bool herm, cplx* out_dev, cplx* scratch,
+          int64_t scratch_elems);
 
 // Small element-wise helpers
 void scale_vec(const Launch& L, int64_t n, cplx a, cplx* x);

@@ -302,46 +302,11 @@ __global__ void __launch_bounds__(kThreads) k_sum_partials(const cplx* partial, 
   if (threadIdx.x == 0) out[k] = s;
 }
 
-__global__ void k_lincomb(int64_t n, int nb, const cplx* __restrict__ X, int64_t ldx, const cplx* __restrict__ c,
-                          cplx* y, bool acc) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    cplx s = acc ? y[i] : make_double2(0.0, 0.0);
-    for (int j = 0; j < nb; ++j) s = cadd(s, cmul(c[j], X[j * ldx + i]));
-    y[i] = s;
-  }
-}
-
-__global__ void __launch_bounds__(kThreads) k_resid_precond(int64_t n, int nb, const cplx* __restrict__ S,
-                                                            const cplx* __restrict__ B, int64_t ld,
-                                                            const cplx* __restrict__ beta, cplx z,
-                                                            const cplx* __restrict__ xi, const double* __restrict__ D,
-                                                            cplx* r_out, cplx* delta, double* partial) {
-  double s2 = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    cplx r = xi[i];
-    for (int j = 0; j < nb; ++j) {
-      const cplx sj = S[j * ld + i], bj = B[j * ld + i];
-      const cplx d = make_double2(sj.x - (z.x * bj.x - z.y * bj.y), sj.y - (z.x * bj.y + z.y * bj.x));
-      r = cadd(r, cmul(beta[j], d));
-    }
-    if (r_out) r_out[i] = r;
-    s2 = fma(r.x, r.x, fma(r.y, r.y, s2));
-    const double dr = D[i] - z.x, di = -z.y;
-    const double inv = 1.0 / (dr * dr + di * di);
-    // delta = -r / (D - z) = -r * conj(D - z) / |D - z|^2
-    const cplx q = cmul(r, make_double2(dr * inv, -di * inv));
-    delta[i] = make_double2(-q.x, -q.y);
-  }
-  cplx v = block_sum(make_double2(s2, 0.0));
-  if (threadIdx.x == 0) partial[blockIdx.x] = v.x;
-}
-
 // ---- FP32-arithmetic variants of the solver's vector kernels (FP64 storage).  FP64 on sm_103 runs
-// at ~1/64 of FP32, and these kernels do 4-8 L flops per element (L = trial-space size), so in
-// FP64 they are ALU-bound by a wide margin.  Products are formed and summed in FP32 over runs of
-// 16 elements; the runs are added in FP64, which keeps ~1e-7 relative accuracy.
+// at ~1/64 of FP32, and the solver's multi-vector kernels do 8 L m flops per element (L inputs,
+// m outputs), so in FP64 they are ALU-bound by a wide margin; in FP32 they stay near the HBM
+// roofline.  The inputs are rounded to FP32 (relative 6e-8) and products summed in FP32.
 __device__ __forceinline__ float2 f2(cplx a) { return make_float2((float)a.x, (float)a.y); }
-constexpr int kMaxVec32 = 256;   // largest coefficient count of the FP32 lincomb / residual kernels
 
 __global__ void __launch_bounds__(kThreads) k_dots_partial32(int64_t n, const cplx* __restrict__ x, int64_t ldx,
                                                              const cplx* __restrict__ y, int64_t ldy, bool herm,
@@ -366,58 +331,120 @@ __global__ void __launch_bounds__(kThreads) k_dots_partial32(int64_t n, const cp
   if (threadIdx.x == 0) partial[(int64_t)k * gridDim.x + blockIdx.x] = s;
 }
 
-__global__ void k_lincomb32(int64_t n, int nb, const cplx* __restrict__ X, int64_t ldx, const cplx* __restrict__ c,
-                            cplx* y, bool acc) {
-  __shared__ float2 cs[kMaxVec32];   // the host guarantees nb <= kMaxVec32
-  for (int j = threadIdx.x; j < nb; j += blockDim.x) cs[j] = f2(c[j]);
-  __syncthreads();
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    float2 s = make_float2(0.f, 0.f);
-    for (int j = 0; j < nb; ++j) {
-      const float2 a = cs[j], b = f2(X[j * ldx + i]);
-      s.x = fmaf(a.x, b.x, fmaf(-a.y, b.y, s.x));
-      s.y = fmaf(a.x, b.y, fmaf(a.y, b.x, s.y));
+// Row j of a Rows list (the host guarantees j < X.total()).
+__device__ __forceinline__ const cplx* row_of(const Rows& r, int j) {
+  const cplx* p = nullptr;
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    if (p == nullptr && s < r.ns) {
+      if (j < r.cnt[s]) p = r.p[s] + (int64_t)j * r.ld[s];
+      else j -= r.cnt[s];
     }
-    cplx out = make_double2((double)s.x, (double)s.y);
-    if (acc) out = cadd(out, y[i]);
-    y[i] = out;
+  }
+  return p;
+}
+
+template <bool F32> struct Arith;
+template <> struct Arith<true> {
+  typedef float2 T;
+  typedef float R;
+  __device__ static T cvt(cplx a) { return make_float2((float)a.x, (float)a.y); }
+  __device__ static void mac(T& acc, T c, T x) {
+    acc.x = fmaf(c.x, x.x, fmaf(-c.y, x.y, acc.x));
+    acc.y = fmaf(c.x, x.y, fmaf(c.y, x.x, acc.y));
+  }
+};
+template <> struct Arith<false> {
+  typedef double2 T;
+  typedef double R;
+  __device__ static T cvt(cplx a) { return a; }
+  __device__ static void mac(T& acc, T c, T x) {
+    acc.x = fma(c.x, x.x, fma(-c.y, x.y, acc.x));
+    acc.y = fma(c.x, x.y, fma(c.y, x.x, acc.y));
+  }
+};
+
+constexpr int kVecMatBlocks = 4 * 148;
+
+// r_q = sum_j X_j C[j][q] + add; Y_q = (D ? -r_q / (D - z_q) : r_q) (+ Y_q); partial norms per
+// block.  Q >= m outputs are computed (coefficients of q >= m are zero and never stored).
+template <bool F32, int Q>
+__global__ void __launch_bounds__(kThreads) k_vecmat(int64_t n, Rows X, int m, const cplx* __restrict__ C,
+                                                     const cplx* __restrict__ add, cplx* Y, int64_t ldy, bool acc,
+                                                     const double* __restrict__ D, const cplx* __restrict__ z,
+                                                     double* part_r, double* part_y) {
+  typedef Arith<F32> A;
+  typedef typename A::T T;
+  typedef typename A::R R;
+  extern __shared__ __align__(16) unsigned char vm_smem[];
+  const int nx = X.total();
+  T* cs = reinterpret_cast<T*>(vm_smem);                                          // nx x Q
+  const cplx** rows = reinterpret_cast<const cplx**>(vm_smem + sizeof(T) * (size_t)nx * Q);
+  for (int e = threadIdx.x; e < nx * Q; e += blockDim.x) {
+    const int j = e / Q, q = e % Q;
+    cs[e] = A::cvt(q < m ? C[(int64_t)j * m + q] : make_double2(0.0, 0.0));
+  }
+  for (int j = threadIdx.x; j < nx; j += blockDim.x) rows[j] = row_of(X, j);
+  __syncthreads();
+  R nr[Q], ny[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) { nr[q] = 0; ny[q] = 0; }
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    T a[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) a[q].x = a[q].y = 0;
+#pragma unroll 4
+    for (int j = 0; j < nx; ++j) {
+      const T x = A::cvt(__ldg(rows[j] + i));
+#pragma unroll
+      for (int q = 0; q < Q; ++q) A::mac(a[q], cs[j * Q + q], x);
+    }
+    const cplx b = add ? add[i] : make_double2(0.0, 0.0);
+    const double di = D ? D[i] : 0.0;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      if (q < m) {
+        cplx r = make_double2((double)a[q].x + b.x, (double)a[q].y + b.y);
+        nr[q] += (R)(r.x * r.x + r.y * r.y);
+        if (D) {
+          const cplx zq = z[q];
+          const double dr = di - zq.x, dm = -zq.y;
+          const double inv = 1.0 / (dr * dr + dm * dm);
+          // -r / (D - z) = -r conj(D - z) / |D - z|^2
+          r = make_double2(-(r.x * dr + r.y * dm) * inv, -(r.y * dr - r.x * dm) * inv);
+        }
+        if (Y) {
+          cplx* yq = Y + q * ldy + i;
+          if (acc) r = cadd(r, *yq);
+          *yq = r;
+        }
+        ny[q] += (R)(r.x * r.x + r.y * r.y);
+      }
+    }
+  }
+  if (part_r || part_y) {
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      if (q < m) {   // uniform across the block
+        if (part_r) {
+          const cplx v = block_sum(make_double2((double)nr[q], 0.0));
+          if (threadIdx.x == 0) part_r[q * gridDim.x + blockIdx.x] = v.x;
+        }
+        if (part_y) {
+          const cplx v = block_sum(make_double2((double)ny[q], 0.0));
+          if (threadIdx.x == 0) part_y[q * gridDim.x + blockIdx.x] = v.x;
+        }
+      }
+    }
   }
 }
 
-__global__ void __launch_bounds__(kThreads) k_resid_precond32(int64_t n, int nb, const cplx* __restrict__ S,
-                                                              const cplx* __restrict__ B, int64_t ld,
-                                                              const cplx* __restrict__ beta, cplx z,
-                                                              const cplx* __restrict__ xi,
-                                                              const double* __restrict__ D, cplx* r_out, cplx* delta,
-                                                              double* partial) {
-  __shared__ float2 bs[kMaxVec32], bz[kMaxVec32];   // beta_j and -z beta_j (nb <= kMaxVec32)
-  for (int j = threadIdx.x; j < nb; j += blockDim.x) {
-    const cplx b = beta[j];
-    bs[j] = f2(b);
-    bz[j] = make_float2((float)(-(z.x * b.x - z.y * b.y)), (float)(-(z.x * b.y + z.y * b.x)));
-  }
-  __syncthreads();
-  double s2 = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    float2 acc = make_float2(0.f, 0.f);
-    for (int j = 0; j < nb; ++j) {
-      const float2 sj = f2(S[j * ld + i]), bj = f2(B[j * ld + i]);
-      acc.x = fmaf(bs[j].x, sj.x, fmaf(-bs[j].y, sj.y, acc.x));
-      acc.y = fmaf(bs[j].x, sj.y, fmaf(bs[j].y, sj.x, acc.y));
-      acc.x = fmaf(bz[j].x, bj.x, fmaf(-bz[j].y, bj.y, acc.x));
-      acc.y = fmaf(bz[j].x, bj.y, fmaf(bz[j].y, bj.x, acc.y));
-    }
-    const cplx x0 = xi[i];
-    const cplx r = make_double2(x0.x + (double)acc.x, x0.y + (double)acc.y);
-    if (r_out) r_out[i] = r;
-    s2 = fma(r.x, r.x, fma(r.y, r.y, s2));
-    const double dr = D[i] - z.x, di = -z.y;
-    const double inv = 1.0 / (dr * dr + di * di);
-    const cplx q = cmul(r, make_double2(dr * inv, -di * inv));
-    delta[i] = make_double2(-q.x, -q.y);
-  }
-  cplx v = block_sum(make_double2(s2, 0.0));
-  if (threadIdx.x == 0) partial[blockIdx.x] = v.x;
+// out[q] = sum_b part[q * nb + b]   (one block per q, fixed order)
+__global__ void k_sum_rows(const double* part, int nb, double* out) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) s += part[(int64_t)blockIdx.x * nb + i];
+  cplx v = block_sum(make_double2(s, 0.0));
+  if (threadIdx.x == 0) out[blockIdx.x] = v.x;
 }
 
 __global__ void k_sum_real(const double* partial, int nb, double* out) {
@@ -465,16 +492,25 @@ __global__ void k_unpack2(const cplx* __restrict__ D, int64_t ldd, cplx* X, int6
   }
 }
 
-// Gram block: part[blk][i][j] = sum over this block's slice of op(X_i[n]) Y_j[n]
+// Gram block: part[blk][i][j] = sum over this block's slice of op(X_i[n]) Y_j[n].  Chunks of 16
+// elements are staged in shared memory; with F32 the chunk's products are summed in FP32 and
+// the chunk sums in FP64.
 constexpr int kGramChunk = 16;
-__global__ void __launch_bounds__(256) k_gram_partial(int64_t n, int nx, const cplx* __restrict__ X, int64_t ldx,
-                                                      int ny, const cplx* __restrict__ Y, int64_t ldy, bool herm,
-                                                      cplx* part) {
-  extern __shared__ cplx sm[];
-  cplx* xs = sm;                         // nx x kGramChunk
-  cplx* ys = sm + nx * kGramChunk;       // ny x kGramChunk
+template <bool F32>
+__global__ void __launch_bounds__(256) k_gram_partial(int64_t n, Rows X, Rows Y, bool herm, cplx* part) {
+  typedef Arith<F32> A;
+  typedef typename A::T T;
+  extern __shared__ __align__(16) unsigned char gr_smem[];
+  const int nx = X.total(), ny = Y.total();
+  T* xs = reinterpret_cast<T*>(gr_smem);   // nx x kGramChunk
+  T* ys = xs + nx * kGramChunk;            // ny x kGramChunk
+  const cplx** xrow = reinterpret_cast<const cplx**>(ys + ny * kGramChunk);
+  const cplx** yrow = xrow + nx;
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) xrow[i] = row_of(X, i);
+  for (int j = threadIdx.x; j < ny; j += blockDim.x) yrow[j] = row_of(Y, j);
+  __syncthreads();
   const int nout = nx * ny;
-  const int per = (nout + 255) / 256;    // outputs per thread (<= 16 for 64 x 64)
+  const int per = (nout + 255) / 256;      // outputs per thread (<= 16)
   cplx acc[16];
   for (int q = 0; q < 16; ++q) acc[q] = make_double2(0.0, 0.0);
   const int64_t nchunks = (n + kGramChunk - 1) / kGramChunk;
@@ -482,13 +518,13 @@ __global__ void __launch_bounds__(256) k_gram_partial(int64_t n, int nx, const c
     const int64_t base = ch * kGramChunk;
     for (int e = threadIdx.x; e < nx * kGramChunk; e += 256) {
       const int i = e / kGramChunk, k = e % kGramChunk;
-      cplx v = (base + k < n) ? X[i * ldx + base + k] : make_double2(0.0, 0.0);
+      cplx v = (base + k < n) ? xrow[i][base + k] : make_double2(0.0, 0.0);
       if (herm) v.y = -v.y;
-      xs[e] = v;
+      xs[e] = A::cvt(v);
     }
     for (int e = threadIdx.x; e < ny * kGramChunk; e += 256) {
       const int j = e / kGramChunk, k = e % kGramChunk;
-      ys[e] = (base + k < n) ? Y[j * ldy + base + k] : make_double2(0.0, 0.0);
+      ys[e] = A::cvt((base + k < n) ? yrow[j][base + k] : make_double2(0.0, 0.0));
     }
     __syncthreads();
 #pragma unroll
@@ -496,13 +532,12 @@ __global__ void __launch_bounds__(256) k_gram_partial(int64_t n, int nx, const c
       const int o = threadIdx.x + 256 * q;
       if (q < per && o < nout) {
         const int i = o / ny, j = o % ny;
-        cplx s = acc[q];
-        for (int k = 0; k < kGramChunk; ++k) {
-          const cplx a = xs[i * kGramChunk + k], b = ys[j * kGramChunk + k];
-          s.x = fma(a.x, b.x, fma(-a.y, b.y, s.x));
-          s.y = fma(a.x, b.y, fma(a.y, b.x, s.y));
-        }
-        acc[q] = s;
+        T s;
+        s.x = s.y = 0;
+#pragma unroll
+        for (int k = 0; k < kGramChunk; ++k) A::mac(s, xs[i * kGramChunk + k], ys[j * kGramChunk + k]);
+        acc[q].x += (double)s.x;
+        acc[q].y += (double)s.y;
       }
     }
     __syncthreads();
@@ -581,20 +616,76 @@ void unpack2(const Launch& L, const cplx* D, int64_t ldd, const Tensor& X) {
   bump(L);
 }
 
-void gram(const Launch& L, int64_t n, int nx, const cplx* X, int64_t ldx, int ny, const cplx* Y, int64_t ldy, bool herm,
-          cplx* out_dev, cplx* scratch, int64_t scratch_elems) {
-  CCLR_REQUIRE(nx >= 1 && ny >= 1 && nx * ny <= 4096 && nx <= 64 && ny <= 64, CCLR_E_ARG, "gram: block too large");
+void gram(const Launch& L, int64_t n, const Rows& X, const Rows& Y, bool herm, cplx* out_dev, cplx* scratch,
+          int64_t scratch_elems) {
+  const int nx = X.total(), ny = Y.total();
+  CCLR_REQUIRE(nx >= 1 && ny >= 1 && nx * ny <= 4096 && nx + ny <= 256, CCLR_E_ARG, "gram: block too large");
   const int nout = nx * ny;
   int nblk = (int)std::min<int64_t>(kReduceBlocks, (n + kGramChunk - 1) / kGramChunk);
   if (nblk < 1) nblk = 1;
   if ((int64_t)nblk * nout > scratch_elems) nblk = (int)std::max<int64_t>(1, scratch_elems / nout);
-  k_gram_partial<<<nblk, 256, sizeof(cplx) * (size_t)(nx + ny) * kGramChunk, L.s>>>(n, nx, X, ldx, ny, Y, ldy, herm,
-                                                                                   scratch);
+  const size_t smem = ((L.fast32 ? sizeof(float2) : sizeof(cplx)) * kGramChunk + sizeof(void*)) * (size_t)(nx + ny);
+  static bool attr = false;
+  if (!attr) {   // up to 256 staged rows of FP64 plus their row pointers: 66 KiB
+    CCLR_CK(cudaFuncSetAttribute(k_gram_partial<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 72 << 10));
+    CCLR_CK(cudaFuncSetAttribute(k_gram_partial<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 72 << 10));
+    attr = true;
+  }
+  if (L.fast32) k_gram_partial<true><<<nblk, 256, smem, L.s>>>(n, X, Y, herm, scratch);
+  else k_gram_partial<false><<<nblk, 256, smem, L.s>>>(n, X, Y, herm, scratch);
   CCLR_CK(cudaGetLastError());
   k_gram_reduce<<<(nout + 255) / 256, 256, 0, L.s>>>(scratch, nblk, nout, out_dev);
   CCLR_CK(cudaGetLastError());
   bump(L);
   bump(L);
+}
+
+int64_t vecmat_scratch_doubles() { return 2 * (int64_t)kVecMatOut * kVecMatBlocks; }
+
+namespace {
+template <bool F32, int Q>
+void launch_vecmat(const Launch& L, int64_t n, const VecMat& a, double* pr, double* py) {
+  const int nx = a.X.total();
+  const size_t smem = sizeof(typename Arith<F32>::T) * (size_t)nx * Q + sizeof(void*) * (size_t)nx;
+  static bool attr = false;
+  if (!attr) {   // kVecMatMaxRows x 16 FP64 coefficients + row table: 132 KiB
+    CCLR_CK(cudaFuncSetAttribute(k_vecmat<F32, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, 136 << 10));
+    attr = true;
+  }
+  k_vecmat<F32, Q><<<kVecMatBlocks, kThreads, smem, L.s>>>(n, a.X, a.m, a.C, a.add, a.Y, a.ldy, a.acc, a.D, a.z, pr,
+                                                           py);
+}
+}  // namespace
+
+void vecmat(const Launch& L, int64_t n, const VecMat& a, double* scratch) {
+  const int nx = a.X.total();
+  CCLR_REQUIRE(a.m >= 1 && a.m <= kVecMatOut && nx >= 1 && nx <= kVecMatMaxRows && a.C, CCLR_E_ARG,
+               "vecmat: bad shape");
+  CCLR_REQUIRE(!a.D || a.z, CCLR_E_ARG, "vecmat: preconditioner without shifts");
+  if (n <= 0) return;
+  double* pr = a.rnorm2 ? scratch : nullptr;
+  double* py = a.ynorm2 ? scratch + (int64_t)kVecMatOut * kVecMatBlocks : nullptr;
+  if (L.fast32) {
+    if (a.m == 1) launch_vecmat<true, 1>(L, n, a, pr, py);
+    else if (a.m <= 4) launch_vecmat<true, 4>(L, n, a, pr, py);
+    else launch_vecmat<true, 16>(L, n, a, pr, py);
+  } else {
+    if (a.m == 1) launch_vecmat<false, 1>(L, n, a, pr, py);
+    else if (a.m <= 4) launch_vecmat<false, 4>(L, n, a, pr, py);
+    else launch_vecmat<false, 16>(L, n, a, pr, py);
+  }
+  CCLR_CK(cudaGetLastError());
+  bump(L);
+  if (a.rnorm2) {
+    k_sum_rows<<<a.m, kThreads, 0, L.s>>>(pr, kVecMatBlocks, a.rnorm2);
+    CCLR_CK(cudaGetLastError());
+    bump(L);
+  }
+  if (a.ynorm2) {
+    k_sum_rows<<<a.m, kThreads, 0, L.s>>>(py, kVecMatBlocks, a.ynorm2);
+    CCLR_CK(cudaGetLastError());
+    bump(L);
+  }
 }
 
 void permute(const Launch& L, const Tensor& src, const Tensor& dst, cplx alpha, bool accumulate) {
@@ -739,25 +830,17 @@ void proj(const Launch& L, int64_t n, int nb, const cplx* B, int64_t ldb, const 
 
 void lincomb(const Launch& L, int64_t n, int nb, const cplx* X, int64_t ldx, const cplx* c_dev, cplx* y,
              bool accumulate) {
-  if (n <= 0) return;
-  if (L.fast32 && nb <= kMaxVec32) k_lincomb32<<<grid_for(n), kThreads, 0, L.s>>>(n, nb, X, ldx, c_dev, y, accumulate);
-  else k_lincomb<<<grid_for(n), kThreads, 0, L.s>>>(n, nb, X, ldx, c_dev, y, accumulate);
-  CCLR_CK(cudaGetLastError());
-  bump(L);
-}
-
-void residual_precond(const Launch& L, int64_t n, int nb, const cplx* S, const cplx* B, int64_t ld,
-                      const cplx* beta_dev, cplx z, const cplx* xi, const double* D, cplx* r_out, cplx* delta,
-                      double* rnorm2_dev, double* scratch) {
-  if (L.fast32 && nb <= kMaxVec32)
-    k_resid_precond32<<<kReduceBlocks, kThreads, 0, L.s>>>(n, nb, S, B, ld, beta_dev, z, xi, D, r_out, delta, scratch);
-  else
-    k_resid_precond<<<kReduceBlocks, kThreads, 0, L.s>>>(n, nb, S, B, ld, beta_dev, z, xi, D, r_out, delta, scratch);
-  CCLR_CK(cudaGetLastError());
-  k_sum_real<<<1, kThreads, 0, L.s>>>(scratch, kReduceBlocks, rnorm2_dev);
-  CCLR_CK(cudaGetLastError());
-  bump(L);
-  bump(L);
+  if (n <= 0 || nb <= 0) return;
+  Rows r;
+  r.add(X, nb, ldx);
+  VecMat a;
+  a.X = r;
+  a.m = 1;
+  a.C = c_dev;
+  a.Y = y;
+  a.ldy = n;
+  a.acc = accumulate;
+  vecmat(L, n, a, nullptr);
 }
 
 }  // namespace cclr

@@ -6,10 +6,10 @@
 //    a Davidson solver whose trial space is shared by every shift z of one right-hand side.
 //    Per iteration and right-hand side: project (G' = B^H (S - z B), C' = -B^H b), solve the small
 //    systems in FP64 on the host, form residuals r = (S - z B) beta + b fused with the
-//    orbital-energy-denominator preconditioner delta = -(D - z)^{-1} r, orthogonalize the
-//    corrections against the trial space (classical Gram-Schmidt, two passes), and add those
-//    that bring a new direction.  Sigma vectors of all new trial vectors of all right-hand sides
-//    are evaluated in one batched call.  With one shift this is the paper's per-system scheme.
+//    orbital-energy-denominator preconditioner delta = -(D - z)^{-1} r, project the corrections
+//    against the trial space, and add those that bring a new direction.  Sigma vectors of all
+//    new trial vectors of all right-hand sides are evaluated in one batched call.  With one
+//    shift this is the paper's per-system scheme.
 //  * Response function: t^X(z) = B^X beta^X(z) for every shift, so the CC-CC response function
 //    reduces to small bilinear forms: eta^X . B^Y, and (B^X F) . B^Y built from one Hessian
 //    product per trial vector.
@@ -73,53 +73,60 @@ void to_dev(Ctx& c, const zc* h, cplx* d, int64_t n) {
   c.sync();
 }
 
-// out[i*ny + j] = sum op(X_i) Y_j for arbitrary nx, ny (tiles of 64), always in FP64: the
-// Galerkin matrices and the response-function forms carry their errors into the results, and the
-// residual-norm estimates cancel O(|b|^2) terms.
-void gram_host(Ctx& c, int nx, const cplx* X, int ny, const cplx* Y, bool herm, std::vector<zc>& out,
-               bool = true) {
+// out[i*ny + j] = sum op(X_i) Y_j over row lists of any length, in tiles that the Gram kernel
+// takes (FP32 products when the solver's vector kernels run in FP32, FP64 otherwise)
+void gram_host(Ctx& c, const Rows& X, const Rows& Y, bool herm, std::vector<zc>& out) {
+  const int nx = X.total(), ny = Y.total();
   out.assign((size_t)nx * ny, zc(0));
   if (nx == 0 || ny == 0) return;
-  Launch L = c.L;
-  L.fast32 = false;
   Scope sc(c.ws);
-  const int64_t scr_n = (int64_t)reduce_blocks() * 64 * 64;
+  const int64_t scr_n = (int64_t)reduce_blocks() * 4096;
   cplx* scr = c.ws.cplxs(scr_n);
-  cplx* dout = c.ws.cplxs(64 * 64);
-  std::vector<zc> blk(64 * 64);
-  for (int i0 = 0; i0 < nx; i0 += 64)
-    for (int j0 = 0; j0 < ny; j0 += 64) {
-      const int bx = std::min(64, nx - i0), by = std::min(64, ny - j0);
-      gram(L, c.N, bx, X + (int64_t)i0 * c.N, c.N, by, Y + (int64_t)j0 * c.N, c.N, herm, dout, scr, scr_n);
+  cplx* dout = c.ws.cplxs(4096);
+  std::vector<zc> blk(4096);
+  const int by_max = std::min(ny, 64);
+  const int bx_max = std::max(1, std::min({nx, 4096 / by_max, 256 - by_max}));
+  for (int i0 = 0; i0 < nx; i0 += bx_max)
+    for (int j0 = 0; j0 < ny; j0 += by_max) {
+      const int bx = std::min(bx_max, nx - i0), by = std::min(by_max, ny - j0);
+      gram(c.L, c.N, X.slice(i0, bx), Y.slice(j0, by), herm, dout, scr, scr_n);
       to_host(c, dout, blk.data(), (int64_t)bx * by);
       for (int i = 0; i < bx; ++i)
         for (int j = 0; j < by; ++j) out[(size_t)(i0 + i) * ny + j0 + j] = blk[(size_t)i * by + j];
     }
 }
 
-// y -= sum_j (B_j^H y) B_j over the nb vectors of B, twice; returns |y| after and before
-std::pair<double, double> orthogonalize(Ctx& c, int nb, const cplx* B, cplx* y) {
+Rows rows(const Ctx& c, const cplx* p, int n) {
+  Rows r;
+  r.add(p, n, c.N);
+  return r;
+}
+
+double norm2(Ctx& c, const cplx* x) {
+  std::vector<zc> g;
+  gram_host(c, rows(c, x, 1), rows(c, x, 1), true, g);
+  return std::max(0.0, g[0].real());
+}
+
+// Y_q = sum_j X_j W[j*m + q] for m outputs in passes of kVecMatOut (W on the host, nx x m)
+void combine(Ctx& c, const Rows& X, int m, const std::vector<zc>& W, cplx* Y) {
+  const int nx = X.total();
   Scope sc(c.ws);
-  cplx* scr = c.ws.cplxs((int64_t)reduce_blocks() * 64);
-  cplx* coef = c.ws.cplxs(64);
-  cplx* nrm = c.ws.cplxs(1);
-  zc h;
-  dots(c.L, c.N, 1, y, 0, y, 0, true, nrm, scr);
-  to_host(c, nrm, &h, 1);
-  const double before = std::sqrt(std::max(0.0, h.real()));
-  for (int pass = 0; pass < 2; ++pass)
-    for (int j0 = 0; j0 < nb; j0 += 64) {
-      const int bj = std::min(64, nb - j0);
-      proj(c.L, c.N, bj, B + (int64_t)j0 * c.N, c.N, y, coef, scr);
-      std::vector<zc> cf(bj);
-      to_host(c, coef, cf.data(), bj);
-      for (auto& x : cf) x = -x;
-      to_dev(c, cf.data(), coef, bj);
-      lincomb(c.L, c.N, bj, B + (int64_t)j0 * c.N, c.N, coef, y, true);
-    }
-  dots(c.L, c.N, 1, y, 0, y, 0, true, nrm, scr);
-  to_host(c, nrm, &h, 1);
-  return {std::sqrt(std::max(0.0, h.real())), before};
+  cplx* cdev = c.ws.cplxs((int64_t)nx * kVecMatOut);
+  for (int q0 = 0; q0 < m; q0 += kVecMatOut) {
+    const int mq = std::min(kVecMatOut, m - q0);
+    std::vector<zc> Cq((size_t)nx * mq);
+    for (int j = 0; j < nx; ++j)
+      for (int q = 0; q < mq; ++q) Cq[(size_t)j * mq + q] = W[(size_t)j * m + q0 + q];
+    to_dev(c, Cq.data(), cdev, (int64_t)nx * mq);
+    VecMat a;
+    a.X = X;
+    a.m = mq;
+    a.C = cdev;
+    a.Y = Y + (int64_t)q0 * c.N;
+    a.ldy = c.N;
+    vecmat(c.L, c.N, a, nullptr);
+  }
 }
 
 }  // namespace
@@ -218,13 +225,13 @@ struct System {            // one right-hand side with its shared trial space
   std::vector<zc> z;       // shifts
   cplx *B = nullptr, *S = nullptr;
   int L = 0;
-  std::vector<zc> BS, Cp;  // maxL x maxL (B^H S), -B^H b
-  std::vector<zc> SS, BB;  // maxL x maxL: S^H S, B^H B
-  std::vector<zc> Sx;      // S^H b
+  std::vector<zc> BS, BB;  // maxL x maxL: B^H S, B^H B
+  std::vector<zc> Cp;      // -B^H b
   double xx = 0.0;         // b^H b
   std::vector<std::vector<zc>> beta;
   std::vector<double> rnorm;
   std::vector<char> conv;
+  bool done = false;
   int iters = 0;
   double best = 1e300;     // best max-residual so far and its iteration (stagnation test)
   int best_it = 0;
@@ -269,14 +276,14 @@ void restart(Ctx& c, System& s, int maxL, int kmax) {
   const int kk = (int)Q.size();
   CCLR_REQUIRE(kk >= 1, CCLR_E_NOCONV, "Davidson restart: empty solution space");
   {
+    // B' = B Q and S' = S Q, kVecMatOut columns per pass over the old vectors
     Scope sc(c.ws);
     cplx* tmp = c.ws.cplxs((int64_t)kk * N);
-    cplx* coef = c.ws.cplxs(L);
+    std::vector<zc> W((size_t)L * kk);
+    for (int j = 0; j < L; ++j)
+      for (int a = 0; a < kk; ++a) W[(size_t)j * kk + a] = Q[a][j];
     for (cplx* X : {s.B, s.S}) {
-      for (int j = 0; j < kk; ++j) {
-        to_dev(c, Q[j].data(), coef, L);
-        lincomb(c.L, N, L, X, N, coef, tmp + (int64_t)j * N, false);
-      }
+      combine(c, rows(c, X, L), kk, W, tmp);
       copy_vec(c.L, (int64_t)kk * N, tmp, X);
     }
   }
@@ -295,7 +302,6 @@ void restart(Ctx& c, System& s, int maxL, int kmax) {
     M.swap(out);
   };
   congr(s.BS);
-  congr(s.SS);
   congr(s.BB);
   auto vec = [&](std::vector<zc>& v) {     // v' = Q^H v
     std::vector<zc> out(maxL, zc(0));
@@ -304,50 +310,79 @@ void restart(Ctx& c, System& s, int maxL, int kmax) {
     v.swap(out);
   };
   vec(s.Cp);
-  vec(s.Sx);
-  for (int q = 0; q < ns; ++q) {           // beta in the new basis (re-solved next iteration)
-    std::vector<zc> nb(maxL, zc(0));
-    for (int a = 0; a < kk; ++a)
-      for (int i = 0; i < L; ++i) nb[a] += std::conj(Q[a][i]) * s.beta[q][i];
-    s.beta[q].swap(nb);
-  }
+  for (int q = 0; q < ns; ++q) vec(s.beta[q]);   // beta in the new basis (re-solved next iteration)
   s.L = kk;
-  c.stats.sigma_calls += 0;
 }
 
 // Solve (Op - z) x = -b for every system and shift.  Op(nvec, in, out) acts on N-vectors.
+//
+// Per iteration and right-hand side, every pass over the N-vectors is one multi-output kernel:
+//   Gram:      B^H [S_new | B_new | b] and S_old^H B_new (the Galerkin matrices B^H S, B^H B)
+//   residuals: r_q = (S - z_q B) beta_q + b for up to 16 open shifts per pass (norms only)
+//   candidates: delta_q = -(D - z_q)^{-1} r_q for the worst shifts, one pass
+//   projection: delta -= B (B^H delta), one classical Gram-Schmidt pass; the basis need not be
+//              orthonormal to working precision because B^H B enters the Galerkin matrices
+//   selection: Gram-Schmidt among the candidates in their own Gram metric, worst first
 void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, const cplx*, cplx*)>& Op,
               int maxL, double tol) {
   static const bool verbose = std::getenv("CCLR_VERBOSE") != nullptr;
   Fast32 f32(c);
   const int64_t N = c.N;
   const int kMaxNew = 4;   // new trial vectors per right-hand side and iteration (worst shifts first)
+  const int kTry = 8;      // candidate corrections formed per right-hand side and iteration
+  CCLR_REQUIRE(2 * maxL <= kVecMatMaxRows, CCLR_E_ARG, "max_subspace too large");
   Scope sc(c.ws);
-  cplx* scr = c.ws.cplxs((int64_t)reduce_blocks() * 64);
-  cplx* bdev = c.ws.cplxs(maxL);
-  double* r2dev = (double*)c.ws.alloc(sizeof(double) * 2);
-  double* rscr = (double*)c.ws.alloc(sizeof(double) * reduce_blocks());
-  cplx* delta = c.ws.cplxs(N);
+  double* vscr = (double*)c.ws.alloc(sizeof(double) * vecmat_scratch_doubles());
+  cplx* cdev = c.ws.cplxs((int64_t)2 * maxL * kVecMatOut);
+  cplx* zdev = c.ws.cplxs(kVecMatOut);
+  double* n2dev = (double*)c.ws.alloc(sizeof(double) * kVecMatOut);
+  cplx* R = c.ws.cplxs((int64_t)kTry * N);
+  // coefficients of r_q = S beta_q - z_q B beta_q over the rows [S | B]
+  auto resid_coef = [&](const System& s, const std::vector<int>& qs, size_t g0, int m) {
+    const int L = s.L;
+    std::vector<zc> C((size_t)2 * L * m);
+    for (int t = 0; t < m; ++t) {
+      const int q = qs[g0 + t];
+      for (int j = 0; j < L; ++j) {
+        C[(size_t)j * m + t] = s.beta[q][j];
+        C[(size_t)(L + j) * m + t] = -s.z[q] * s.beta[q][j];
+      }
+    }
+    to_dev(c, C.data(), cdev, (int64_t)2 * L * m);
+  };
+  auto SB = [&](const System& s) { return Rows().add(s.S, s.L, N).add(s.B, s.L, N); };
+  auto residual_norms = [&](System& s, const std::vector<int>& qs) {
+    for (size_t g0 = 0; g0 < qs.size(); g0 += kVecMatOut) {
+      const int m = (int)std::min<size_t>(kVecMatOut, qs.size() - g0);
+      resid_coef(s, qs, g0, m);
+      VecMat a;
+      a.X = SB(s);
+      a.m = m;
+      a.C = cdev;
+      a.add = s.rhs;
+      a.rnorm2 = n2dev;
+      vecmat(c.L, N, a, vscr);
+      double h[kVecMatOut];
+      CCLR_CK(cudaMemcpyAsync(h, n2dev, sizeof(double) * m, cudaMemcpyDeviceToHost, c.stream));
+      c.sync();
+      for (int t = 0; t < m; ++t) s.rnorm[qs[g0 + t]] = std::sqrt(std::max(0.0, h[t]));
+    }
+  };
   for (auto& s : sys) {
     s.BS.assign((size_t)maxL * maxL, zc(0));
-    s.SS.assign((size_t)maxL * maxL, zc(0));
     s.BB.assign((size_t)maxL * maxL, zc(0));
     s.Cp.assign(maxL, zc(0));
-    s.Sx.assign(maxL, zc(0));
-    {
-      std::vector<zc> g;
-      gram_host(c, 1, s.rhs, 1, s.rhs, true, g, true);
-      s.xx = g[0].real();
-    }
+    s.xx = norm2(c, s.rhs);
     s.beta.assign(s.z.size(), std::vector<zc>(maxL, zc(0)));
     s.rnorm.assign(s.z.size(), 1e300);
     s.conv.assign(s.z.size(), 0);
+    s.done = false;
     s.L = 0;
     // start: b / D, normalized (preconditioned right-hand side at z = 0)
     div_shift(c.L, N, s.rhs, c.D, cx(0), cx(1), s.B);
-    auto nr = orthogonalize(c, 0, s.B, s.B);
-    CCLR_REQUIRE(nr.second > 0.0, CCLR_E_ARG, "zero right-hand side");
-    scale_vec(c.L, N, cx(1.0 / nr.second), s.B);
+    const double nb = std::sqrt(norm2(c, s.B));
+    CCLR_REQUIRE(nb > 0.0, CCLR_E_ARG, "zero right-hand side");
+    scale_vec(c.L, N, cx(1.0 / nb), s.B);
     s.L = 1;
   }
   std::vector<int> fresh(sys.size(), 1);   // new vectors at the end of each basis
@@ -377,45 +412,39 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
         for (int j = 0; j < fresh[k]; ++j, ++q)
           copy_vec(c.L, N, out + (int64_t)q * N, sys[k].S + (int64_t)(sys[k].L - fresh[k] + j) * N);
     }
-    bool all_conv = true;
+    bool all_done = true;
     for (size_t k = 0; k < sys.size(); ++k) {
       System& s = sys[k];
+      if (s.done) continue;
       const int L0 = s.L - fresh[k], f = fresh[k];
-      // ---- Gram blocks of the new vectors: B^H S, S^H S, B^H B and S^H b (FP64, host)
+      // ---- Galerkin matrices: new columns of B^H S and B^H B, new rows of B^H S, B^H b
       if (f > 0) {
         std::vector<zc> g;
         const cplx* Bn = s.B + (int64_t)L0 * N;
         const cplx* Sn = s.S + (int64_t)L0 * N;
-        auto put = [&](std::vector<zc>& M, const std::vector<zc>& blk, int r0, int nr, int c0, int nc, bool herm_fill) {
-          for (int i = 0; i < nr; ++i)
-            for (int j = 0; j < nc; ++j) {
-              M[(size_t)(r0 + i) * maxL + c0 + j] = blk[(size_t)i * nc + j];
-              if (herm_fill) M[(size_t)(c0 + j) * maxL + r0 + i] = std::conj(blk[(size_t)i * nc + j]);
-            }
-        };
-        gram_host(c, s.L, s.B, f, Sn, true, g, true);     // B^H S_new: new columns of BS
-        put(s.BS, g, 0, s.L, L0, f, false);
-        if (L0 > 0) {
-          gram_host(c, f, Bn, L0, s.S, true, g, true);    // B_new^H S_old: new rows of BS
-          put(s.BS, g, L0, f, 0, L0, false);
+        const int ny = 2 * f + 1;
+        gram_host(c, rows(c, s.B, s.L), Rows().add(Sn, f, N).add(Bn, f, N).add(s.rhs, 1, N), true, g);
+        for (int i = 0; i < s.L; ++i) {
+          for (int j = 0; j < f; ++j) {
+            s.BS[(size_t)i * maxL + L0 + j] = g[(size_t)i * ny + j];
+            const zc bb = g[(size_t)i * ny + f + j];
+            s.BB[(size_t)i * maxL + L0 + j] = bb;
+            s.BB[(size_t)(L0 + j) * maxL + i] = std::conj(bb);
+          }
+          s.Cp[i] = -g[(size_t)i * ny + 2 * f];
         }
-        gram_host(c, s.L, s.S, f, Sn, true, g);           // S^H S_new (Hermitian)
-        put(s.SS, g, 0, s.L, L0, f, true);
-        gram_host(c, s.L, s.B, f, Bn, true, g, true);     // B^H B_new (Hermitian)
-        put(s.BB, g, 0, s.L, L0, f, true);
-        gram_host(c, f, Bn, 1, s.rhs, true, g, true);     // B_new^H b
-        for (int i = 0; i < f; ++i) s.Cp[L0 + i] = -g[i];
-        gram_host(c, f, Sn, 1, s.rhs, true, g);           // S_new^H b
-        for (int i = 0; i < f; ++i) s.Sx[L0 + i] = g[i];
+        if (L0 > 0) {
+          gram_host(c, rows(c, s.S, L0), rows(c, Bn, f), true, g);   // S_old^H B_new
+          for (int i = 0; i < L0; ++i)
+            for (int j = 0; j < f; ++j) s.BS[(size_t)(L0 + j) * maxL + i] = std::conj(g[(size_t)i * f + j]);
+        }
       }
       fresh[k] = 0;
-      // ---- subspace solves; residual norms from the Gram matrices:
-      //   |r|^2 = beta^H (S - zB)^H (S - zB) beta + 2 Re beta^H (S^H b - z* B^H b) + b^H b
       const int L = s.L;
       // tensor-core modes: sigma carries ~1e-5 relative error at long K (FP32 accumulation), so
       // the reachable residual is ~1e-5 of |b|; the target is raised to that floor
       const double tol_s = c.opt.precision == CCLR_FP64 ? tol : std::max(tol, 1e-5 * std::sqrt(s.xx));
-      std::vector<std::pair<double, int>> order;
+      // ---- subspace solves (B^H S - z B^H B) beta = -B^H b for every shift
       for (size_t q = 0; q < s.z.size(); ++q) {
         const zc z = s.z[q];
         std::vector<zc> G((size_t)L * L), rhs(s.Cp.begin(), s.Cp.begin() + L);
@@ -423,36 +452,25 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
           for (int j = 0; j < L; ++j) G[(size_t)i * L + j] = s.BS[(size_t)i * maxL + j] - z * s.BB[(size_t)i * maxL + j];
         zsolve(L, G, rhs);
         for (int i = 0; i < L; ++i) s.beta[q][i] = rhs[i];
-        const zc* b = rhs.data();
-        zc quad(0), lin(0);
-        for (int i = 0; i < L; ++i) {
-          zc row(0);
-          for (int j = 0; j < L; ++j) {
-            const size_t ij = (size_t)i * maxL + j, ji = (size_t)j * maxL + i;
-            const zc Gij = s.SS[ij] - z * std::conj(s.BS[ji]) - std::conj(z) * s.BS[ij] + std::norm(z) * s.BB[ij];
-            row += Gij * b[j];
-          }
-          quad += std::conj(b[i]) * row;
-          lin += std::conj(b[i]) * (s.Sx[i] + std::conj(z) * s.Cp[i]);   // Cp = -B^H b
-        }
-        const double r2 = quad.real() + 2.0 * lin.real() + s.xx;
-        s.rnorm[q] = std::sqrt(std::max(0.0, r2));
-        // the Gram estimate cancels O(|b|^2) terms: with FP64 Gram blocks it resolves |r| down to
-        // ~1e-7 |b|; below that, confirm on the vectors
-        const double floor = 1e-7 * std::sqrt(s.xx);
-        if (s.rnorm[q] < std::max(tol_s, floor) * 4.0) {
-          to_dev(c, rhs.data(), bdev, L);
-          residual_precond(c.L, N, L, s.S, s.B, N, bdev, cx(z.real(), z.imag()), s.rhs, c.D, nullptr, delta, r2dev,
-                           rscr);
-          double e2;
-          CCLR_CK(cudaMemcpyAsync(&e2, r2dev, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
-          c.sync();
-          s.rnorm[q] = std::sqrt(e2);
-        }
-        s.conv[q] = s.rnorm[q] < tol_s;
-        if (!s.conv[q]) order.push_back({s.rnorm[q], (int)q});
-        c.stats.max_residual = std::max(c.stats.max_residual, s.rnorm[q]);
       }
+      // ---- residual norms of the open shifts; once all are below the target, the shifts
+      // locked earlier are checked again at the final trial space
+      std::vector<int> open, locked;
+      for (size_t q = 0; q < s.z.size(); ++q) (s.conv[q] ? locked : open).push_back((int)q);
+      std::vector<std::pair<double, int>> order;
+      residual_norms(s, open);
+      for (int q : open) {
+        s.conv[q] = s.rnorm[q] < tol_s;
+        if (!s.conv[q]) order.push_back({s.rnorm[q], q});
+      }
+      if (order.empty() && !locked.empty()) {
+        residual_norms(s, locked);
+        for (int q : locked) {
+          s.conv[q] = s.rnorm[q] < tol_s;
+          if (!s.conv[q]) order.push_back({s.rnorm[q], q});
+        }
+      }
+      for (size_t q = 0; q < s.z.size(); ++q) c.stats.max_residual = std::max(c.stats.max_residual, s.rnorm[q]);
       s.iters = it;
       if (verbose)
         std::fprintf(stderr, "[cclr] davidson it %d rhs %zu L %d unconverged %zu/%zu max|r| %.3e tol %.1e\n", it, k, L,
@@ -465,34 +483,92 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
         if (mx < 0.8 * s.best) { s.best = mx; s.best_it = it; }
         if (it - s.best_it >= 4 && mx < 5.0 * tol_s) order.clear();
       }
-      if (order.empty()) continue;
-      all_conv = false;
+      if (order.empty()) {
+        s.done = true;
+        continue;
+      }
+      all_done = false;
       std::sort(order.begin(), order.end(), [](auto& a, auto& b) { return a.first > b.first; });
       if (s.L + kMaxNew > maxL) restart(c, s, maxL, maxL - 2 * kMaxNew);
-      int added = 0, tried = 0;
-      for (auto& pr : order) {
-        // corrections of neighbouring shifts are nearly collinear: try a few, worst first
-        if (added >= kMaxNew || s.L >= maxL || tried >= 2 * kMaxNew) break;
-        ++tried;
-        const int q = pr.second;
-        std::vector<zc> bq(s.beta[q].begin(), s.beta[q].begin() + s.L);
-        to_dev(c, bq.data(), bdev, s.L);
-        cplx* nb = s.B + (int64_t)s.L * N;
-        residual_precond(c.L, N, s.L, s.S, s.B, N, bdev, cx(s.z[q].real(), s.z[q].imag()), s.rhs, c.D, nullptr, nb,
-                         r2dev, rscr);
-        auto nr = orthogonalize(c, s.L, s.B, nb);
-        // accept a correction only if at least 1% of it lies outside the trial space
-        if (nr.first <= 1e-2 * nr.second || nr.first < 1e-300) continue;
-        scale_vec(c.L, N, cx(1.0 / nr.first), nb);
-        s.L++;
-        fresh[k]++;
-        added++;
+      // ---- preconditioned residuals of the worst shifts, one pass
+      const int nt = std::min<int>(kTry, (int)order.size());
+      std::vector<int> qs(nt);
+      std::vector<zc> zq(nt);
+      for (int t = 0; t < nt; ++t) { qs[t] = order[t].second; zq[t] = s.z[qs[t]]; }
+      resid_coef(s, qs, 0, nt);
+      to_dev(c, zq.data(), zdev, nt);
+      double pre2[kVecMatOut];
+      {
+        VecMat a;
+        a.X = SB(s);
+        a.m = nt;
+        a.C = cdev;
+        a.add = s.rhs;
+        a.Y = R;
+        a.ldy = N;
+        a.D = c.D;
+        a.z = zdev;
+        a.ynorm2 = n2dev;
+        vecmat(c.L, N, a, vscr);
+        CCLR_CK(cudaMemcpyAsync(pre2, n2dev, sizeof(double) * nt, cudaMemcpyDeviceToHost, c.stream));
+        c.sync();
       }
-      if (added == 0)
+      // ---- project out the trial space: R -= B (B^H R)
+      {
+        std::vector<zc> g;
+        gram_host(c, rows(c, s.B, s.L), rows(c, R, nt), true, g);
+        for (auto& x : g) x = -x;
+        to_dev(c, g.data(), cdev, (int64_t)s.L * nt);
+        VecMat a;
+        a.X = rows(c, s.B, s.L);
+        a.m = nt;
+        a.C = cdev;
+        a.Y = R;
+        a.ldy = N;
+        a.acc = true;
+        vecmat(c.L, N, a, vscr);
+      }
+      // ---- selection: Gram-Schmidt in the candidates' Gram metric, worst first; a direction is
+      // kept only if at least 1% of the preconditioned residual lies outside the trial space and
+      // the directions kept before it
+      std::vector<zc> RR;
+      gram_host(c, rows(c, R, nt), rows(c, R, nt), true, RR);
+      auto ip = [&](const std::vector<zc>& u, const std::vector<zc>& v) {   // u^H RR v
+        zc acc(0);
+        for (int i = 0; i < nt; ++i) {
+          zc r(0);
+          for (int j = 0; j < nt; ++j) r += RR[(size_t)i * nt + j] * v[j];
+          acc += std::conj(u[i]) * r;
+        }
+        return acc;
+      };
+      std::vector<std::vector<zc>> T;
+      for (int t = 0; t < nt; ++t) {
+        if ((int)T.size() >= kMaxNew || s.L + (int)T.size() >= maxL) break;
+        std::vector<zc> v(nt, zc(0));
+        v[t] = 1.0;
+        for (int pass = 0; pass < 2; ++pass)
+          for (auto& u : T) {
+            const zc d = ip(u, v);
+            for (int i = 0; i < nt; ++i) v[i] -= d * u[i];
+          }
+        const double n2 = ip(v, v).real();
+        if (!(n2 > 0.0) || std::sqrt(n2) < 1e-2 * std::sqrt(std::max(0.0, pre2[t]))) continue;
+        for (auto& x : v) x /= std::sqrt(n2);
+        T.push_back(v);
+      }
+      if (T.empty())
         throw Error(CCLR_E_NOCONV, "Davidson stagnated: residual " + std::to_string(order.front().first) +
                                        " above tolerance " + std::to_string(tol_s) + " with no new direction");
+      const int kk = (int)T.size();
+      std::vector<zc> W((size_t)nt * kk);
+      for (int j = 0; j < nt; ++j)
+        for (int a = 0; a < kk; ++a) W[(size_t)j * kk + a] = T[a][j];
+      combine(c, rows(c, R, nt), kk, W, s.B + (int64_t)s.L * N);
+      s.L += kk;
+      fresh[k] = kk;
     }
-    if (all_conv) return;
+    if (all_done) return;
   }
   throw Error(CCLR_E_NOCONV, "Davidson did not converge within maxit iterations");
 }
@@ -604,7 +680,8 @@ void response_function(Ctx& c, cplx* out_host) {
   // products of the trial vectors are formed in batches and contracted at once (never stored).
   std::vector<std::vector<zc>> M((size_t)nop * nop), E((size_t)nop * nop);
   for (int x = 0; x < nop; ++x)
-    for (int y = 0; y < nop; ++y) gram_host(c, 1, rd.eta[x], rd.nb[y], rd.basis[y], false, E[(size_t)x * nop + y], true);
+    for (int y = 0; y < nop; ++y)
+      gram_host(c, rows(c, rd.eta[x], 1), rows(c, rd.basis[y], rd.nb[y]), false, E[(size_t)x * nop + y]);
   auto beta = [&](int k, int f, int s) { return &rd.beta[k][(size_t)rd.shift_of[(size_t)f * 4 + s] * maxL]; };
   // The Hessian acts only on the solutions t^X(-z) and t^X(z*) of every frequency.  Their
   // coefficient vectors span few directions: compress them (QR with column pivoting, 1e-12
@@ -650,15 +727,14 @@ void response_function(Ctx& c, cplx* out_host) {
       Scope sc(c.ws);
       cplx* yv = c.ws.cplxs((int64_t)nb * N);
       cplx* fb = c.ws.cplxs((int64_t)nb * N);
-      cplx* coef = c.ws.cplxs(Lx);
-      for (int j = 0; j < nb; ++j) {
-        to_dev(c, Q[x][q0 + j].data(), coef, Lx);
-        lincomb(c.L, N, Lx, rd.basis[x], N, coef, yv + (int64_t)j * N, false);
-      }
+      std::vector<zc> W((size_t)Lx * nb);
+      for (int l = 0; l < Lx; ++l)
+        for (int j = 0; j < nb; ++j) W[(size_t)l * nb + j] = Q[x][q0 + j][l];
+      combine(c, rows(c, rd.basis[x], Lx), nb, W, yv);
       hessian_right(c, nb, yv, fb);
       for (int y = 0; y < nop; ++y) {
         std::vector<zc> g;
-        gram_host(c, nb, fb, rd.nb[y], rd.basis[y], false, g, true);
+        gram_host(c, rows(c, fb, nb), rows(c, rd.basis[y], rd.nb[y]), false, g);
         auto& Mxy = M[(size_t)x * nop + y];
         for (int i = 0; i < nb; ++i)
           for (int j = 0; j < rd.nb[y]; ++j) Mxy[(size_t)(q0 + i) * rd.nb[y] + j] = g[(size_t)i * rd.nb[y] + j];
