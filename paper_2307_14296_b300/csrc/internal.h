@@ -171,8 +171,9 @@ struct Rows {
 // Multi-output linear combination over n elements, one pass over the inputs:
 //   r_q = sum_j X_j C[j*m + q] + add,  q < m <= 16
 //   Y_q = (D ? -r_q / (D - z_q) : r_q) + (acc ? Y_q : 0)
-// with optional |r_q|^2 and |Y_q|^2.  Products and sums in FP32 when Launch::fast32 (FP64
-// storage), otherwise FP64.  All device pointers; C has X.total() x m entries.
+// with optional norm2[q] = |r_q|^2 (or |Y_q|^2 if norm_y).  Products and sums in FP32 pairs
+// when Launch::fast32 (FP64 storage), otherwise FP64.  All device pointers; C has X.total() x m
+// entries; scratch holds vecmat_scratch_doubles() when norms are requested.
 struct VecMat {
   Rows X;
   int m = 0;
@@ -183,8 +184,8 @@ struct VecMat {
   bool acc = false;
   const double* D = nullptr;
   const cplx* z = nullptr;
-  double* rnorm2 = nullptr;
-  double* ynorm2 = nullptr;
+  double* norm2 = nullptr;
+  bool norm_y = false;
 };
 constexpr int kVecMatOut = 16;        // outputs per pass
 constexpr int kVecMatMaxRows = 512;   // inputs per pass
@@ -217,11 +218,13 @@ void splitk_reduce(const Launch& L, const cplx* P, int S, int64_t M, int64_t N, 
 //   unpack2: X[r,p,q] = +-D[r*ldd + P(min,max)], 0 for p == q
 void pack2(const Launch& L, const Tensor& X, cplx* D, int64_t ldd, const int2* tab, cplx alpha, bool anti, bool acc);
 void unpack2(const Launch& L, const cplx* D, int64_t ldd, const Tensor& X);
-// Gram block out[i*ny + j] = sum_n op(X_i[n]) Y_j[n] (conj X if herm) over row lists with
-// nx * ny <= 4096 and nx + ny <= 256; FP32 products summed in FP64 per 16 elements when
-// Launch::fast32, FP64 otherwise.  scratch must hold reduce_blocks() * nx * ny elements.
+// Gram block out[i*ny + j] = sum_n op(X_i[n]) Y_j[n] (conj X if herm) over row lists of any
+// length (tiles of 64 x 8 rows, longer list first), out_dev holding nx * ny.  FP32 products
+// summed in FP32 over runs of 32 elements and in FP64 across runs when Launch::fast32, FP64
+// otherwise.  Row starts must be 16-byte aligned; scratch holds gram_scratch_elems().
 void gram(const Launch& L, int64_t n, const Rows& X, const Rows& Y, bool herm, cplx* out_dev, cplx* scratch,
           int64_t scratch_elems);
+inline int64_t gram_scratch_elems() { return 148 * 64 * 8; }
 
 // Small element-wise helpers
 void scale_vec(const Launch& L, int64_t n, cplx a, cplx* x);

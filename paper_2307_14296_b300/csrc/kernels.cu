@@ -4,6 +4,7 @@
 // a fixed grid writes partial sums that one block adds in a fixed order.
 #include "internal.h"
 #include <algorithm>
+#include <type_traits>
 
 namespace cclr {
 
@@ -302,11 +303,38 @@ __global__ void __launch_bounds__(kThreads) k_sum_partials(const cplx* partial, 
   if (threadIdx.x == 0) out[k] = s;
 }
 
+// ---- FP64 <-> FP32 by bit manipulation of the IEEE 754 binary64 and binary32 layouts.  On sm_103
+// the cvt instructions between the two formats issue on the FP64 pipe (about 1/64 of the FP32
+// rate), which would bound every FP32 kernel that reads or writes FP64 storage; these run on the
+// integer pipe.  d2f rounds to nearest (ties away from zero), flushes results below the binary32
+// normal range to signed zero and overflows to signed infinity (NaN stays NaN); f2d is exact for
+// normal inputs and flushes binary32 subnormals to zero.
+__device__ __forceinline__ float d2f(double x) {
+  const uint64_t b = (uint64_t)__double_as_longlong(x);
+  const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
+  const uint32_t sign = hi & 0x80000000u, e = (hi >> 20) & 0x7ffu;
+  // low 9 exponent bits and the top 23 mantissa bits, rounded on the 24th; the exponent bias
+  // changes by 1023 - 127 = 896, whose low 9 bits are 0x180
+  const uint32_t t = __funnelshift_l(lo, hi, 3) + ((lo >> 28) & 1u);
+  uint32_t f = (t - 0xC0000000u) | sign;
+  if (e < 897u) f = sign;
+  if (e > 1150u) f = sign | ((e == 0x7ffu && ((hi & 0xfffffu) | lo)) ? 0x7fc00000u : 0x7f800000u);
+  return __uint_as_float(f);
+}
+__device__ __forceinline__ double f2d(float x) {
+  const uint32_t u = __float_as_uint(x), sign = u & 0x80000000u, e = (u >> 23) & 0xffu;
+  uint32_t hi = (((u & 0x7fffffffu) >> 3) + 0x38000000u) | sign, lo = u << 29;
+  if (e == 0u) { hi = sign; lo = 0u; }
+  if (e == 0xffu) { hi = sign | 0x7ff00000u | ((u & 0x7fffffu) ? 0x80000u : 0u); lo = 0u; }
+  return __longlong_as_double((long long)(((uint64_t)hi << 32) | lo));
+}
+__device__ __forceinline__ float2 d2f2(cplx a) { return make_float2(d2f(a.x), d2f(a.y)); }
+__device__ __forceinline__ cplx f2d2(float2 a) { return make_double2(f2d(a.x), f2d(a.y)); }
+
 // ---- FP32-arithmetic variants of the solver's vector kernels (FP64 storage).  FP64 on sm_103 runs
 // at ~1/64 of FP32, and the solver's multi-vector kernels do 8 L m flops per element (L inputs,
 // m outputs), so in FP64 they are ALU-bound by a wide margin; in FP32 they stay near the HBM
 // roofline.  The inputs are rounded to FP32 (relative 6e-8) and products summed in FP32.
-__device__ __forceinline__ float2 f2(cplx a) { return make_float2((float)a.x, (float)a.y); }
 
 __global__ void __launch_bounds__(kThreads) k_dots_partial32(int64_t n, const cplx* __restrict__ x, int64_t ldx,
                                                              const cplx* __restrict__ y, int64_t ldy, bool herm,
@@ -318,9 +346,9 @@ __global__ void __launch_bounds__(kThreads) k_dots_partial32(int64_t n, const cp
   float2 f = make_float2(0.f, 0.f);
   int run = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    float2 a = f2(xk[i]);
+    float2 a = d2f2(xk[i]);
     if (herm) a.y = -a.y;
-    const float2 b = f2(yk[i]);
+    const float2 b = d2f2(yk[i]);
     f.x = fmaf(a.x, b.x, fmaf(-a.y, b.y, f.x));
     f.y = fmaf(a.x, b.y, fmaf(a.y, b.x, f.y));
     if (++run == 16) { s.x += f.x; s.y += f.y; f = make_float2(0.f, 0.f); run = 0; }
@@ -344,21 +372,59 @@ __device__ __forceinline__ const cplx* row_of(const Rows& r, int j) {
   return p;
 }
 
+// Packed FP32 pairs (sm_100+ f32x2 FMA): a complex multiply-accumulate acc += c x is two
+// packed FMAs with c held as (c.re, c.re), (-c.im, c.im) and x as (x.re, x.im), (x.im, x.re).
+__device__ __forceinline__ uint64_t pk2(float a, float b) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ float2 upk2(uint64_t v) {
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+  return r;
+}
+__device__ __forceinline__ uint64_t ffma2(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
+// Arithmetic of the solver's multi-vector kernels: FP32 pairs (F32) or FP64.
+//   C: a coefficient, X: an operand, Acc: an accumulator; mac(acc, c, x): acc += c x
 template <bool F32> struct Arith;
 template <> struct Arith<true> {
-  typedef float2 T;
-  typedef float R;
-  __device__ static T cvt(cplx a) { return make_float2((float)a.x, (float)a.y); }
-  __device__ static void mac(T& acc, T c, T x) {
-    acc.x = fmaf(c.x, x.x, fmaf(-c.y, x.y, acc.x));
-    acc.y = fmaf(c.x, x.y, fmaf(c.y, x.x, acc.y));
+  struct __align__(16) C { uint64_t re, im; };
+  struct X { uint64_t a, b; };
+  typedef uint64_t Acc;
+  __device__ static C coef(float2 c) {
+    C r;
+    r.re = pk2(c.x, c.x);
+    r.im = pk2(-c.y, c.y);
+    return r;
+  }
+  __device__ static C coef(cplx c) { return coef(d2f2(c)); }
+  __device__ static X opnd(float2 v) {
+    X r;
+    r.a = pk2(v.x, v.y);
+    r.b = pk2(v.y, v.x);
+    return r;
+  }
+  __device__ static X opnd(cplx v) { return opnd(d2f2(v)); }
+  __device__ static Acc zero() { return 0ull; }
+  __device__ static void mac(Acc& acc, const C& c, const X& x) {
+    acc = ffma2(c.re, x.a, acc);
+    acc = ffma2(c.im, x.b, acc);
   }
 };
 template <> struct Arith<false> {
-  typedef double2 T;
-  typedef double R;
-  __device__ static T cvt(cplx a) { return a; }
-  __device__ static void mac(T& acc, T c, T x) {
+  typedef cplx C;
+  typedef cplx X;
+  typedef cplx Acc;
+  __device__ static C coef(cplx c) { return c; }
+  __device__ static X opnd(cplx v) { return v; }
+  __device__ static Acc zero() { return make_double2(0.0, 0.0); }
+  __device__ static void mac(Acc& acc, const C& c, const X& x) {
     acc.x = fma(c.x, x.x, fma(-c.y, x.y, acc.x));
     acc.y = fma(c.x, x.y, fma(c.y, x.x, acc.y));
   }
@@ -366,74 +432,117 @@ template <> struct Arith<false> {
 
 constexpr int kVecMatBlocks = 4 * 148;
 
-// r_q = sum_j X_j C[j][q] + add; Y_q = (D ? -r_q / (D - z_q) : r_q) (+ Y_q); partial norms per
-// block.  Q >= m outputs are computed (coefficients of q >= m are zero and never stored).
-template <bool F32, int Q>
-__global__ void __launch_bounds__(kThreads) k_vecmat(int64_t n, Rows X, int m, const cplx* __restrict__ C,
-                                                     const cplx* __restrict__ add, cplx* Y, int64_t ldy, bool acc,
-                                                     const double* __restrict__ D, const cplx* __restrict__ z,
-                                                     double* part_r, double* part_y) {
+// r_q = sum_j X_j C[j][q] + add; Y_q = (D ? -r_q / (D - z_q) : r_q) (+ Y_q); per-block partial
+// norms of r_q (or of Y_q if norm_y).  Q >= m outputs are computed (coefficients of q >= m are
+// zero and never stored); each thread takes E elements per step so that every coefficient read
+// from shared memory serves E elements.  With F32 the whole element pipeline (products, sums,
+// preconditioner, accumulation into Y) runs in FP32 and only loads and stores touch FP64.
+template <bool F32, int Q, int E>
+__global__ void __launch_bounds__(kThreads, F32 ? 2 : 1)
+    k_vecmat(int64_t n, Rows X, int m, const cplx* __restrict__ C, const cplx* __restrict__ add, cplx* Y, int64_t ldy,
+             bool acc, const double* __restrict__ D, const cplx* __restrict__ z, bool norm_y, double* part) {
   typedef Arith<F32> A;
-  typedef typename A::T T;
-  typedef typename A::R R;
+  typedef typename A::C Cf;
+  typedef typename std::conditional<F32, float, double>::type R;
+  typedef typename std::conditional<F32, float2, double2>::type V;
   extern __shared__ __align__(16) unsigned char vm_smem[];
+  __shared__ V zs[Q];
   const int nx = X.total();
-  T* cs = reinterpret_cast<T*>(vm_smem);                                          // nx x Q
-  const cplx** rows = reinterpret_cast<const cplx**>(vm_smem + sizeof(T) * (size_t)nx * Q);
+  Cf* cs = reinterpret_cast<Cf*>(vm_smem);                                        // nx x Q
+  const cplx** rows = reinterpret_cast<const cplx**>(vm_smem + sizeof(Cf) * (size_t)nx * Q);
   for (int e = threadIdx.x; e < nx * Q; e += blockDim.x) {
     const int j = e / Q, q = e % Q;
-    cs[e] = A::cvt(q < m ? C[(int64_t)j * m + q] : make_double2(0.0, 0.0));
+    cs[e] = A::coef(q < m ? C[(int64_t)j * m + q] : make_double2(0.0, 0.0));
   }
   for (int j = threadIdx.x; j < nx; j += blockDim.x) rows[j] = row_of(X, j);
+  if (threadIdx.x < Q) {
+    const cplx zq = (D && (int)threadIdx.x < m) ? z[threadIdx.x] : make_double2(0.0, 0.0);
+    if constexpr (F32) zs[threadIdx.x] = d2f2(zq);
+    else zs[threadIdx.x] = zq;
+  }
   __syncthreads();
-  R nr[Q], ny[Q];
+  R nn[Q];
 #pragma unroll
-  for (int q = 0; q < Q; ++q) { nr[q] = 0; ny[q] = 0; }
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    T a[Q];
+  for (int q = 0; q < Q; ++q) nn[q] = 0;
+  const int64_t tile = (int64_t)E * blockDim.x;
+  for (int64_t i0 = blockIdx.x * tile + threadIdx.x; i0 < n; i0 += (int64_t)gridDim.x * tile) {
+    typename A::Acc a[E][Q];
 #pragma unroll
-    for (int q = 0; q < Q; ++q) a[q].x = a[q].y = 0;
+    for (int e = 0; e < E; ++e)
+#pragma unroll
+      for (int q = 0; q < Q; ++q) a[e][q] = A::zero();
 #pragma unroll 4
     for (int j = 0; j < nx; ++j) {
-      const T x = A::cvt(__ldg(rows[j] + i));
+      const cplx* rp = rows[j];
+      typename A::X xv[E];
 #pragma unroll
-      for (int q = 0; q < Q; ++q) A::mac(a[q], cs[j * Q + q], x);
+      for (int e = 0; e < E; ++e) {
+        const int64_t i = i0 + (int64_t)e * blockDim.x;
+        xv[e] = A::opnd(i < n ? __ldg(rp + i) : make_double2(0.0, 0.0));
+      }
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const Cf cq = cs[j * Q + q];
+#pragma unroll
+        for (int e = 0; e < E; ++e) A::mac(a[e][q], cq, xv[e]);
+      }
     }
-    const cplx b = add ? add[i] : make_double2(0.0, 0.0);
-    const double di = D ? D[i] : 0.0;
 #pragma unroll
-    for (int q = 0; q < Q; ++q) {
-      if (q < m) {
-        cplx r = make_double2((double)a[q].x + b.x, (double)a[q].y + b.y);
-        nr[q] += (R)(r.x * r.x + r.y * r.y);
-        if (D) {
-          const cplx zq = z[q];
-          const double dr = di - zq.x, dm = -zq.y;
-          const double inv = 1.0 / (dr * dr + dm * dm);
-          // -r / (D - z) = -r conj(D - z) / |D - z|^2
-          r = make_double2(-(r.x * dr + r.y * dm) * inv, -(r.y * dr - r.x * dm) * inv);
+    for (int e = 0; e < E; ++e) {
+      const int64_t i = i0 + (int64_t)e * blockDim.x;
+      if (i >= n) continue;
+      V b, dz;
+      if constexpr (F32) {
+        b = add ? d2f2(add[i]) : make_float2(0.f, 0.f);
+        dz.x = D ? d2f(D[i]) : 0.f;
+      } else {
+        b = add ? add[i] : make_double2(0.0, 0.0);
+        dz.x = D ? D[i] : 0.0;
+      }
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        if (q < m) {
+          V r;
+          if constexpr (F32) {
+            const float2 v = upk2(a[e][q]);
+            r = make_float2(v.x + b.x, v.y + b.y);
+          } else {
+            r = make_double2(a[e][q].x + b.x, a[e][q].y + b.y);
+          }
+          if (!norm_y) nn[q] += r.x * r.x + r.y * r.y;
+          if (D) {
+            // -r / (D - z) = -r conj(D - z) / |D - z|^2
+            const R dr = dz.x - zs[q].x, dm = -zs[q].y;
+            const R inv = R(1) / (dr * dr + dm * dm);
+            const R rx = r.x, ry = r.y;
+            r.x = -(rx * dr + ry * dm) * inv;
+            r.y = -(ry * dr - rx * dm) * inv;
+          }
+          if (Y) {
+            cplx* yq = Y + q * ldy + i;
+            if constexpr (F32) {
+              if (acc) {
+                const float2 y0 = d2f2(*yq);
+                r.x += y0.x;
+                r.y += y0.y;
+              }
+              *yq = f2d2(r);
+            } else {
+              if (acc) r = cadd(r, *yq);
+              *yq = r;
+            }
+          }
+          if (norm_y) nn[q] += r.x * r.x + r.y * r.y;
         }
-        if (Y) {
-          cplx* yq = Y + q * ldy + i;
-          if (acc) r = cadd(r, *yq);
-          *yq = r;
-        }
-        ny[q] += (R)(r.x * r.x + r.y * r.y);
       }
     }
   }
-  if (part_r || part_y) {
+  if (part) {
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
       if (q < m) {   // uniform across the block
-        if (part_r) {
-          const cplx v = block_sum(make_double2((double)nr[q], 0.0));
-          if (threadIdx.x == 0) part_r[q * gridDim.x + blockIdx.x] = v.x;
-        }
-        if (part_y) {
-          const cplx v = block_sum(make_double2((double)ny[q], 0.0));
-          if (threadIdx.x == 0) part_y[q * gridDim.x + blockIdx.x] = v.x;
-        }
+        const cplx v = block_sum(make_double2((double)nn[q], 0.0));
+        if (threadIdx.x == 0) part[q * gridDim.x + blockIdx.x] = v.x;
       }
     }
   }
@@ -447,12 +556,6 @@ __global__ void k_sum_rows(const double* part, int nb, double* out) {
   if (threadIdx.x == 0) out[blockIdx.x] = v.x;
 }
 
-__global__ void k_sum_real(const double* partial, int nb, double* out) {
-  double s = 0.0;
-  for (int i = threadIdx.x; i < nb; i += blockDim.x) s += partial[i];
-  cplx v = block_sum(make_double2(s, 0.0));
-  if (threadIdx.x == 0) out[0] = v.x;
-}
 
 // D[r][P(p,q)] = alpha (X[r,p,q] - X[r,q,p]) or alpha X[r,p,q]  (+ D), X strided (R, m, m)
 __global__ void k_pack2(const cplx* __restrict__ X, int64_t sr, int64_t sp, int64_t sq, cplx* D, int64_t ldd,
@@ -492,69 +595,175 @@ __global__ void k_unpack2(const cplx* __restrict__ D, int64_t ldd, cplx* X, int6
   }
 }
 
-// Gram block: part[blk][i][j] = sum over this block's slice of op(X_i[n]) Y_j[n].  Chunks of 16
-// elements are staged in shared memory; with F32 the chunk's products are summed in FP32 and
-// the chunk sums in FP64.
-constexpr int kGramChunk = 16;
-template <bool F32>
-__global__ void __launch_bounds__(256) k_gram_partial(int64_t n, Rows X, Rows Y, bool herm, cplx* part) {
+// Gram tile for tall-skinny operands: part[blk][i][j] = sum over this block's share of the
+// elements of op(X_i[k]) Y_j[k], nx <= 32 RL, ny <= NY.  Chunks of 64 elements of all rows are
+// copied to shared memory with cp.async, double-buffered; lane l owns rows l, l+32, ... of X and
+// all rows of Y (read as shared-memory broadcasts); the 8 warps split each chunk's elements and
+// are summed at the end.  F32: each chunk is converted to FP32 once in shared memory; products
+// are summed in FP32 pairs over runs of kGramRun chunks and the runs added with a compensated
+// (two-sum) FP32 accumulator.
+constexpr int kGramChunk = 64;
+constexpr int kGramPitch = kGramChunk + 1;   // padded row pitch: lanes reading distinct rows hit distinct banks
+constexpr int kGramRun = 4;                  // chunks per FP32 run (32 elements per warp)
+constexpr int kGramMaxX = 64, kGramMaxY = 8; // tile of one launch
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// hi + lo += v with the rounding error of the addition kept in lo (Knuth's two-sum)
+__device__ __forceinline__ void two_sum(float& hi, float& lo, float v) {
+  const float s = hi + v;
+  const float bb = s - hi;
+  lo += (hi - (s - bb)) + (v - bb);
+  hi = s;
+}
+
+template <bool F32, int RL, int NY>
+__global__ void __launch_bounds__(256, 1) k_gram_skinny(int64_t n, Rows X, Rows Y, bool herm, cplx* part) {
   typedef Arith<F32> A;
-  typedef typename A::T T;
-  extern __shared__ __align__(16) unsigned char gr_smem[];
-  const int nx = X.total(), ny = Y.total();
-  T* xs = reinterpret_cast<T*>(gr_smem);   // nx x kGramChunk
-  T* ys = xs + nx * kGramChunk;            // ny x kGramChunk
-  const cplx** xrow = reinterpret_cast<const cplx**>(ys + ny * kGramChunk);
-  const cplx** yrow = xrow + nx;
-  for (int i = threadIdx.x; i < nx; i += blockDim.x) xrow[i] = row_of(X, i);
-  for (int j = threadIdx.x; j < ny; j += blockDim.x) yrow[j] = row_of(Y, j);
+  extern __shared__ __align__(16) unsigned char gs_smem[];
+  const int nx = X.total(), ny = Y.total(), nr = nx + ny;
+  cplx* stage[2];
+  stage[0] = reinterpret_cast<cplx*>(gs_smem);
+  stage[1] = stage[0] + (size_t)nr * kGramPitch;
+  float2* cv = reinterpret_cast<float2*>(stage[1] + (size_t)nr * kGramPitch);   // F32 copy of a chunk
+  const cplx** rowp = reinterpret_cast<const cplx**>(cv + (F32 ? (size_t)nr * kGramPitch : 0));
+  for (int r = threadIdx.x; r < nr; r += blockDim.x) rowp[r] = r < nx ? row_of(X, r) : row_of(Y, r - nx);
   __syncthreads();
-  const int nout = nx * ny;
-  const int per = (nout + 255) / 256;      // outputs per thread (<= 16)
-  cplx acc[16];
-  for (int q = 0; q < 16; ++q) acc[q] = make_double2(0.0, 0.0);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t nchunks = (n + kGramChunk - 1) / kGramChunk;
-  for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+  auto issue = [&](int s, int64_t ch) {
     const int64_t base = ch * kGramChunk;
-    for (int e = threadIdx.x; e < nx * kGramChunk; e += 256) {
-      const int i = e / kGramChunk, k = e % kGramChunk;
-      cplx v = (base + k < n) ? xrow[i][base + k] : make_double2(0.0, 0.0);
-      if (herm) v.y = -v.y;
-      xs[e] = A::cvt(v);
+    for (int e = threadIdx.x; e < nr * kGramChunk; e += blockDim.x) {
+      const int r = e / kGramChunk, k = e % kGramChunk;
+      if (base + k < n) cp_async16(stage[s] + r * kGramPitch + k, rowp[r] + base + k);
     }
-    for (int e = threadIdx.x; e < ny * kGramChunk; e += 256) {
-      const int j = e / kGramChunk, k = e % kGramChunk;
-      ys[e] = A::cvt((base + k < n) ? yrow[j][base + k] : make_double2(0.0, 0.0));
+    cp_async_commit();
+  };
+  typename A::Acc acc[RL][NY];
+  float hi[RL][NY][2], lo[RL][NY][2];   // F32 run totals (two-sum)
+#pragma unroll
+  for (int a = 0; a < RL; ++a)
+#pragma unroll
+    for (int j = 0; j < NY; ++j) {
+      acc[a][j] = A::zero();
+      hi[a][j][0] = hi[a][j][1] = lo[a][j][0] = lo[a][j][1] = 0.f;
+    }
+  auto flush = [&]() {
+#pragma unroll
+    for (int a = 0; a < RL; ++a)
+#pragma unroll
+      for (int j = 0; j < NY; ++j) {
+        if constexpr (F32) {
+          const float2 v = upk2(acc[a][j]);
+          two_sum(hi[a][j][0], lo[a][j][0], v.x);
+          two_sum(hi[a][j][1], lo[a][j][1], v.y);
+          acc[a][j] = A::zero();
+        }
+      }
+  };
+  int s = 0, run = 0;
+  if ((int64_t)blockIdx.x < nchunks) issue(0, blockIdx.x);
+  for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+    const bool more = ch + gridDim.x < nchunks;
+    if (more) {
+      issue(s ^ 1, ch + gridDim.x);
+      cp_async_wait1();
+    } else {
+      cp_async_wait0();
     }
     __syncthreads();
+    const cplx* st = stage[s];
+    const int64_t base = ch * kGramChunk;
+    if constexpr (F32) {
+      for (int e = threadIdx.x; e < nr * kGramChunk; e += blockDim.x) {
+        const int r = e / kGramChunk, k = e % kGramChunk;
+        if (base + k < n) {
+          float2 v = d2f2(st[r * kGramPitch + k]);
+          if (herm && r < nx) v.y = -v.y;
+          cv[r * kGramPitch + k] = v;
+        }
+      }
+      __syncthreads();
+    }
+#pragma unroll 2
+    for (int kk = 0; kk < kGramChunk / 8; ++kk) {
+      const int k = warp * (kGramChunk / 8) + kk;
+      if (base + k < n) {
+        typename A::X yv[NY];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      const int o = threadIdx.x + 256 * q;
-      if (q < per && o < nout) {
-        const int i = o / ny, j = o % ny;
-        T s;
-        s.x = s.y = 0;
+        for (int j = 0; j < NY; ++j) {
+          if constexpr (F32) yv[j] = A::opnd(j < ny ? cv[(nx + j) * kGramPitch + k] : make_float2(0.f, 0.f));
+          else yv[j] = A::opnd(j < ny ? st[(nx + j) * kGramPitch + k] : make_double2(0.0, 0.0));
+        }
 #pragma unroll
-        for (int k = 0; k < kGramChunk; ++k) A::mac(s, xs[i * kGramChunk + k], ys[j * kGramChunk + k]);
-        acc[q].x += (double)s.x;
-        acc[q].y += (double)s.y;
+        for (int a = 0; a < RL; ++a) {
+          const int r = lane + 32 * a;
+          typename A::C xc;
+          if constexpr (F32) {
+            xc = A::coef(r < nx ? cv[r * kGramPitch + k] : make_float2(0.f, 0.f));
+          } else {
+            cplx xv = r < nx ? st[r * kGramPitch + k] : make_double2(0.0, 0.0);
+            if (herm) xv.y = -xv.y;
+            xc = A::coef(xv);
+          }
+#pragma unroll
+          for (int j = 0; j < NY; ++j) A::mac(acc[a][j], xc, yv[j]);
+        }
       }
     }
-    __syncthreads();
+    if (++run == kGramRun) {
+      run = 0;
+      flush();
+    }
+    __syncthreads();   // the stage (and the FP32 copy) are overwritten next
+    s ^= 1;
   }
+  flush();
+  // sum the 8 warps' shares in shared memory (the staging buffers are free now)
+  cplx* red = reinterpret_cast<cplx*>(gs_smem);   // [warp][a][j][lane]
 #pragma unroll
-  for (int q = 0; q < 16; ++q) {
-    const int o = threadIdx.x + 256 * q;
-    if (q < per && o < nout) part[(int64_t)blockIdx.x * nout + o] = acc[q];
+  for (int a = 0; a < RL; ++a)
+#pragma unroll
+    for (int j = 0; j < NY; ++j) {
+      cplx v;
+      if constexpr (F32) {
+        v = make_double2((double)hi[a][j][0] + (double)lo[a][j][0], (double)hi[a][j][1] + (double)lo[a][j][1]);
+      } else {
+        v = acc[a][j];
+      }
+      red[((warp * RL + a) * NY + j) * 32 + lane] = v;
+    }
+  __syncthreads();
+  for (int o = threadIdx.x; o < nx * ny; o += blockDim.x) {
+    const int i = o / ny, j = o % ny;
+    const int a = i / 32, l = i % 32;
+    cplx v = make_double2(0.0, 0.0);
+    for (int w = 0; w < 8; ++w) v = cadd(v, red[((w * RL + a) * NY + j) * 32 + l]);
+    part[(int64_t)blockIdx.x * nx * ny + o] = v;
   }
 }
 
-__global__ void k_gram_reduce(const cplx* __restrict__ part, int nblk, int nout, cplx* out) {
+// out[(swap ? j * ldo + i : i * ldo + j)] = (swap && herm ? conj : id)(sum_b part[b][i][j]) for the
+// a x b tile, i < a, j < b
+__global__ void k_gram_reduce(const cplx* __restrict__ part, int nblk, int a, int b, cplx* out, int64_t ldo, bool swap,
+                              bool herm) {
   const int o = blockIdx.x * blockDim.x + threadIdx.x;
-  if (o >= nout) return;
+  if (o >= a * b) return;
   cplx s = make_double2(0.0, 0.0);
-  for (int b = 0; b < nblk; ++b) s = cadd(s, part[(int64_t)b * nout + o]);
-  out[o] = s;
+  for (int k = 0; k < nblk; ++k) s = cadd(s, part[(int64_t)k * a * b + o]);
+  const int i = o / b, j = o % b;
+  if (swap) {
+    if (herm) s.y = -s.y;
+    out[(int64_t)j * ldo + i] = s;
+  } else {
+    out[(int64_t)i * ldo + j] = s;
+  }
 }
 
 // split-K epilogue: C[m*ldc + n] = alpha * sum_z P[z][m][n] + beta * C (fixed summation order)
@@ -616,44 +825,79 @@ void unpack2(const Launch& L, const cplx* D, int64_t ldd, const Tensor& X) {
   bump(L);
 }
 
+namespace {
+template <bool F32, int RL, int NY>
+void launch_gram(const Launch& L, int nblk, size_t smem, int64_t n, const Rows& X, const Rows& Y, bool herm,
+                 cplx* part) {
+  static bool attr = false;
+  if (!attr) {
+    CCLR_CK(cudaFuncSetAttribute(k_gram_skinny<F32, RL, NY>, cudaFuncAttributeMaxDynamicSharedMemorySize, 192 << 10));
+    attr = true;
+  }
+  k_gram_skinny<F32, RL, NY><<<nblk, 256, smem, L.s>>>(n, X, Y, herm, part);
+}
+template <bool F32>
+void launch_gram_tile(const Launch& L, int nblk, size_t smem, int64_t n, const Rows& X, const Rows& Y, bool herm,
+                      cplx* part) {
+  const int a = X.total(), b = Y.total();
+  if (a <= 32) {
+    if (b == 1) launch_gram<F32, 1, 1>(L, nblk, smem, n, X, Y, herm, part);
+    else if (b <= 4) launch_gram<F32, 1, 4>(L, nblk, smem, n, X, Y, herm, part);
+    else launch_gram<F32, 1, 8>(L, nblk, smem, n, X, Y, herm, part);
+  } else {
+    if (b == 1) launch_gram<F32, 2, 1>(L, nblk, smem, n, X, Y, herm, part);
+    else if (b <= 4) launch_gram<F32, 2, 4>(L, nblk, smem, n, X, Y, herm, part);
+    else launch_gram<F32, 2, 8>(L, nblk, smem, n, X, Y, herm, part);
+  }
+}
+}  // namespace
+
 void gram(const Launch& L, int64_t n, const Rows& X, const Rows& Y, bool herm, cplx* out_dev, cplx* scratch,
           int64_t scratch_elems) {
   const int nx = X.total(), ny = Y.total();
-  CCLR_REQUIRE(nx >= 1 && ny >= 1 && nx * ny <= 4096 && nx + ny <= 256, CCLR_E_ARG, "gram: block too large");
-  const int nout = nx * ny;
-  int nblk = (int)std::min<int64_t>(kReduceBlocks, (n + kGramChunk - 1) / kGramChunk);
-  if (nblk < 1) nblk = 1;
-  if ((int64_t)nblk * nout > scratch_elems) nblk = (int)std::max<int64_t>(1, scratch_elems / nout);
-  const size_t smem = ((L.fast32 ? sizeof(float2) : sizeof(cplx)) * kGramChunk + sizeof(void*)) * (size_t)(nx + ny);
-  static bool attr = false;
-  if (!attr) {   // up to 256 staged rows of FP64 plus their row pointers: 66 KiB
-    CCLR_CK(cudaFuncSetAttribute(k_gram_partial<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 72 << 10));
-    CCLR_CK(cudaFuncSetAttribute(k_gram_partial<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 72 << 10));
-    attr = true;
-  }
-  if (L.fast32) k_gram_partial<true><<<nblk, 256, smem, L.s>>>(n, X, Y, herm, scratch);
-  else k_gram_partial<false><<<nblk, 256, smem, L.s>>>(n, X, Y, herm, scratch);
-  CCLR_CK(cudaGetLastError());
-  k_gram_reduce<<<(nout + 255) / 256, 256, 0, L.s>>>(scratch, nblk, nout, out_dev);
-  CCLR_CK(cudaGetLastError());
-  bump(L);
-  bump(L);
+  CCLR_REQUIRE(nx >= 1 && ny >= 1 && n >= 1, CCLR_E_ARG, "gram: empty operand");
+  // the kernel takes the longer list as its X side; the transpose is undone when the tile is stored
+  const bool swap = ny > nx;
+  const Rows& P = swap ? Y : X;
+  const Rows& Q = swap ? X : Y;
+  const int np = P.total(), nq = Q.total();
+  const int64_t nchunks = (n + kGramChunk - 1) / kGramChunk;
+  for (int i0 = 0; i0 < np; i0 += kGramMaxX)
+    for (int j0 = 0; j0 < nq; j0 += kGramMaxY) {
+      const int a = std::min(kGramMaxX, np - i0), b = std::min(kGramMaxY, nq - j0);
+      int nblk = (int)std::min<int64_t>(148, nchunks);
+      if ((int64_t)nblk * a * b > scratch_elems) nblk = (int)std::max<int64_t>(1, scratch_elems / ((int64_t)a * b));
+      const int RL = a <= 32 ? 1 : 2, NYt = b == 1 ? 1 : (b <= 4 ? 4 : 8);
+      const size_t stage = (2 * sizeof(cplx) + (L.fast32 ? sizeof(float2) : 0)) * (size_t)(a + b) * kGramPitch +
+                           sizeof(void*) * (size_t)(a + b);
+      const size_t red = sizeof(cplx) * 8 * RL * NYt * 32;
+      const size_t smem = std::max(stage, red);
+      if (L.fast32) launch_gram_tile<true>(L, nblk, smem, n, P.slice(i0, a), Q.slice(j0, b), herm, scratch);
+      else launch_gram_tile<false>(L, nblk, smem, n, P.slice(i0, a), Q.slice(j0, b), herm, scratch);
+      CCLR_CK(cudaGetLastError());
+      cplx* o = swap ? out_dev + (int64_t)j0 * ny + i0 : out_dev + (int64_t)i0 * ny + j0;
+      k_gram_reduce<<<(a * b + 255) / 256, 256, 0, L.s>>>(scratch, nblk, a, b, o, ny, swap, herm);
+      CCLR_CK(cudaGetLastError());
+      bump(L);
+      bump(L);
+    }
 }
 
-int64_t vecmat_scratch_doubles() { return 2 * (int64_t)kVecMatOut * kVecMatBlocks; }
+int64_t vecmat_scratch_doubles() { return (int64_t)kVecMatOut * kVecMatBlocks; }
 
 namespace {
 template <bool F32, int Q>
-void launch_vecmat(const Launch& L, int64_t n, const VecMat& a, double* pr, double* py) {
+void launch_vecmat(const Launch& L, int64_t n, const VecMat& a, double* part) {
+  constexpr int E = (F32 && Q <= 4) ? 2 : 1;   // 16 outputs x 2 elements would not fit 128 registers
   const int nx = a.X.total();
-  const size_t smem = sizeof(typename Arith<F32>::T) * (size_t)nx * Q + sizeof(void*) * (size_t)nx;
+  const size_t smem = sizeof(typename Arith<F32>::C) * (size_t)nx * Q + sizeof(void*) * (size_t)nx;
   static bool attr = false;
-  if (!attr) {   // kVecMatMaxRows x 16 FP64 coefficients + row table: 132 KiB
-    CCLR_CK(cudaFuncSetAttribute(k_vecmat<F32, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, 136 << 10));
+  if (!attr) {   // kVecMatMaxRows x 16 coefficients (16 B each) + row table: 132 KiB
+    CCLR_CK(cudaFuncSetAttribute(k_vecmat<F32, Q, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, 136 << 10));
     attr = true;
   }
-  k_vecmat<F32, Q><<<kVecMatBlocks, kThreads, smem, L.s>>>(n, a.X, a.m, a.C, a.add, a.Y, a.ldy, a.acc, a.D, a.z, pr,
-                                                           py);
+  k_vecmat<F32, Q, E><<<kVecMatBlocks, kThreads, smem, L.s>>>(n, a.X, a.m, a.C, a.add, a.Y, a.ldy, a.acc, a.D, a.z,
+                                                              a.norm_y, part);
 }
 }  // namespace
 
@@ -662,27 +906,22 @@ void vecmat(const Launch& L, int64_t n, const VecMat& a, double* scratch) {
   CCLR_REQUIRE(a.m >= 1 && a.m <= kVecMatOut && nx >= 1 && nx <= kVecMatMaxRows && a.C, CCLR_E_ARG,
                "vecmat: bad shape");
   CCLR_REQUIRE(!a.D || a.z, CCLR_E_ARG, "vecmat: preconditioner without shifts");
+  CCLR_REQUIRE(!a.norm2 || scratch, CCLR_E_ARG, "vecmat: norms without scratch");
   if (n <= 0) return;
-  double* pr = a.rnorm2 ? scratch : nullptr;
-  double* py = a.ynorm2 ? scratch + (int64_t)kVecMatOut * kVecMatBlocks : nullptr;
+  double* part = a.norm2 ? scratch : nullptr;
   if (L.fast32) {
-    if (a.m == 1) launch_vecmat<true, 1>(L, n, a, pr, py);
-    else if (a.m <= 4) launch_vecmat<true, 4>(L, n, a, pr, py);
-    else launch_vecmat<true, 16>(L, n, a, pr, py);
+    if (a.m == 1) launch_vecmat<true, 1>(L, n, a, part);
+    else if (a.m <= 4) launch_vecmat<true, 4>(L, n, a, part);
+    else launch_vecmat<true, 16>(L, n, a, part);
   } else {
-    if (a.m == 1) launch_vecmat<false, 1>(L, n, a, pr, py);
-    else if (a.m <= 4) launch_vecmat<false, 4>(L, n, a, pr, py);
-    else launch_vecmat<false, 16>(L, n, a, pr, py);
+    if (a.m == 1) launch_vecmat<false, 1>(L, n, a, part);
+    else if (a.m <= 4) launch_vecmat<false, 4>(L, n, a, part);
+    else launch_vecmat<false, 16>(L, n, a, part);
   }
   CCLR_CK(cudaGetLastError());
   bump(L);
-  if (a.rnorm2) {
-    k_sum_rows<<<a.m, kThreads, 0, L.s>>>(pr, kVecMatBlocks, a.rnorm2);
-    CCLR_CK(cudaGetLastError());
-    bump(L);
-  }
-  if (a.ynorm2) {
-    k_sum_rows<<<a.m, kThreads, 0, L.s>>>(py, kVecMatBlocks, a.ynorm2);
+  if (a.norm2) {
+    k_sum_rows<<<a.m, kThreads, 0, L.s>>>(part, kVecMatBlocks, a.norm2);
     CCLR_CK(cudaGetLastError());
     bump(L);
   }

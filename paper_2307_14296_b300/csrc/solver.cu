@@ -64,6 +64,35 @@ double now() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
+// Wall time per solver phase, printed when CCLR_VERBOSE is set (the stream is synchronized at
+// every phase boundary then, so those runs are slower)
+struct Phases {
+  const char* what;
+  bool on;
+  std::vector<std::pair<std::string, double>> t;
+  std::string cur;
+  double t0 = 0.0;
+  explicit Phases(const char* w) : what(w), on(std::getenv("CCLR_VERBOSE") != nullptr) {}
+  void mark(Ctx& c, const char* name) {
+    if (!on) return;
+    c.sync();
+    const double n = now();
+    if (!cur.empty()) {
+      auto it = std::find_if(t.begin(), t.end(), [&](auto& p) { return p.first == cur; });
+      if (it == t.end()) t.push_back({cur, n - t0});
+      else it->second += n - t0;
+    }
+    cur = name;
+    t0 = n;
+  }
+  ~Phases() {
+    if (!on || t.empty()) return;
+    std::fprintf(stderr, "[cclr] %s phases:", what);
+    for (auto& p : t) std::fprintf(stderr, " %s %.3fs", p.first.c_str(), p.second);
+    std::fprintf(stderr, "\n");
+  }
+};
+
 void to_host(Ctx& c, const cplx* d, zc* h, int64_t n) {
   CCLR_CK(cudaMemcpyAsync(h, d, sizeof(cplx) * n, cudaMemcpyDeviceToHost, c.stream));
   c.sync();
@@ -80,20 +109,10 @@ void gram_host(Ctx& c, const Rows& X, const Rows& Y, bool herm, std::vector<zc>&
   out.assign((size_t)nx * ny, zc(0));
   if (nx == 0 || ny == 0) return;
   Scope sc(c.ws);
-  const int64_t scr_n = (int64_t)reduce_blocks() * 4096;
-  cplx* scr = c.ws.cplxs(scr_n);
-  cplx* dout = c.ws.cplxs(4096);
-  std::vector<zc> blk(4096);
-  const int by_max = std::min(ny, 64);
-  const int bx_max = std::max(1, std::min({nx, 4096 / by_max, 256 - by_max}));
-  for (int i0 = 0; i0 < nx; i0 += bx_max)
-    for (int j0 = 0; j0 < ny; j0 += by_max) {
-      const int bx = std::min(bx_max, nx - i0), by = std::min(by_max, ny - j0);
-      gram(c.L, c.N, X.slice(i0, bx), Y.slice(j0, by), herm, dout, scr, scr_n);
-      to_host(c, dout, blk.data(), (int64_t)bx * by);
-      for (int i = 0; i < bx; ++i)
-        for (int j = 0; j < by; ++j) out[(size_t)(i0 + i) * ny + j0 + j] = blk[(size_t)i * by + j];
-    }
+  cplx* scr = c.ws.cplxs(gram_scratch_elems());
+  cplx* dout = c.ws.cplxs((int64_t)nx * ny);
+  gram(c.L, c.N, X, Y, herm, dout, scr, gram_scratch_elems());
+  to_host(c, dout, out.data(), (int64_t)nx * ny);
 }
 
 Rows rows(const Ctx& c, const cplx* p, int n) {
@@ -152,9 +171,12 @@ int solve_ground(Ctx& c) {
   bool ok = false;
   double rn = 0.0, tol_eff = c.opt.ground_tol, rn0 = 0.0, best = 1e300;
   int best_it = 0;
+  Phases ph("ground");
   try {
     for (it = 1; it <= c.opt.maxit * 2; ++it) {
+      ph.mark(c, "residual");
       ccsd_residual(c, R);
+      ph.mark(c, "diis");
       zc h;
       dots(c.L, N, 1, R, 0, R, 0, true, dd, scr);
       to_host(c, dd, &h, 1);
@@ -208,6 +230,7 @@ int solve_ground(Ctx& c) {
       }
       expand_t2(c, c.t + c.Ns, c.t2, 1);
     }
+    ph.mark(c, "");
   } catch (...) {
     c.dfree(R); c.dfree(hist_t); c.dfree(hist_e);
     throw;
@@ -360,7 +383,7 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
       a.m = m;
       a.C = cdev;
       a.add = s.rhs;
-      a.rnorm2 = n2dev;
+      a.norm2 = n2dev;
       vecmat(c.L, N, a, vscr);
       double h[kVecMatOut];
       CCLR_CK(cudaMemcpyAsync(h, n2dev, sizeof(double) * m, cudaMemcpyDeviceToHost, c.stream));
@@ -386,7 +409,9 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
     s.L = 1;
   }
   std::vector<int> fresh(sys.size(), 1);   // new vectors at the end of each basis
+  Phases ph("davidson");
   for (int it = 1; it <= c.opt.maxit; ++it) {
+    ph.mark(c, "sigma");
     // ---- sigma of all new vectors (one batched call; vectors are gathered contiguously)
     int total = 0;
     for (size_t k = 0; k < sys.size(); ++k) total += fresh[k];
@@ -418,6 +443,7 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
       if (s.done) continue;
       const int L0 = s.L - fresh[k], f = fresh[k];
       // ---- Galerkin matrices: new columns of B^H S and B^H B, new rows of B^H S, B^H b
+      ph.mark(c, "gram");
       if (f > 0) {
         std::vector<zc> g;
         const cplx* Bn = s.B + (int64_t)L0 * N;
@@ -445,6 +471,7 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
       // the reachable residual is ~1e-5 of |b|; the target is raised to that floor
       const double tol_s = c.opt.precision == CCLR_FP64 ? tol : std::max(tol, 1e-5 * std::sqrt(s.xx));
       // ---- subspace solves (B^H S - z B^H B) beta = -B^H b for every shift
+      ph.mark(c, "subspace");
       for (size_t q = 0; q < s.z.size(); ++q) {
         const zc z = s.z[q];
         std::vector<zc> G((size_t)L * L), rhs(s.Cp.begin(), s.Cp.begin() + L);
@@ -458,6 +485,7 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
       std::vector<int> open, locked;
       for (size_t q = 0; q < s.z.size(); ++q) (s.conv[q] ? locked : open).push_back((int)q);
       std::vector<std::pair<double, int>> order;
+      ph.mark(c, "norms");
       residual_norms(s, open);
       for (int q : open) {
         s.conv[q] = s.rnorm[q] < tol_s;
@@ -489,8 +517,10 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
       }
       all_done = false;
       std::sort(order.begin(), order.end(), [](auto& a, auto& b) { return a.first > b.first; });
+      ph.mark(c, "restart");
       if (s.L + kMaxNew > maxL) restart(c, s, maxL, maxL - 2 * kMaxNew);
       // ---- preconditioned residuals of the worst shifts, one pass
+      ph.mark(c, "candidates");
       const int nt = std::min<int>(kTry, (int)order.size());
       std::vector<int> qs(nt);
       std::vector<zc> zq(nt);
@@ -508,12 +538,14 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
         a.ldy = N;
         a.D = c.D;
         a.z = zdev;
-        a.ynorm2 = n2dev;
+        a.norm2 = n2dev;
+        a.norm_y = true;
         vecmat(c.L, N, a, vscr);
         CCLR_CK(cudaMemcpyAsync(pre2, n2dev, sizeof(double) * nt, cudaMemcpyDeviceToHost, c.stream));
         c.sync();
       }
       // ---- project out the trial space: R -= B (B^H R)
+      ph.mark(c, "project");
       {
         std::vector<zc> g;
         gram_host(c, rows(c, s.B, s.L), rows(c, R, nt), true, g);
@@ -531,6 +563,7 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
       // ---- selection: Gram-Schmidt in the candidates' Gram metric, worst first; a direction is
       // kept only if at least 1% of the preconditioned residual lies outside the trial space and
       // the directions kept before it
+      ph.mark(c, "select");
       std::vector<zc> RR;
       gram_host(c, rows(c, R, nt), rows(c, R, nt), true, RR);
       auto ip = [&](const std::vector<zc>& u, const std::vector<zc>& v) {   // u^H RR v
@@ -568,6 +601,7 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
       s.L += kk;
       fresh[k] = kk;
     }
+    ph.mark(c, "other");
     if (all_done) return;
   }
   throw Error(CCLR_E_NOCONV, "Davidson did not converge within maxit iterations");
@@ -617,6 +651,8 @@ void lr_solve(Ctx& c, int n_ops, const cplx* ops_host, int n_freq, const double*
   rd = ResponseData();
   const int64_t N = c.N, n = c.n;
   const int maxL = std::max(8, c.opt.max_subspace);
+  Phases ph("lr_solve");
+  ph.mark(c, "setup");
   rd.n_ops = n_ops;
   rd.n_freq = n_freq;
   rd.gamma = gamma;
@@ -651,7 +687,9 @@ void lr_solve(Ctx& c, int n_ops, const cplx* ops_host, int n_freq, const double*
     sys[k].B = rd.basis[k];
     sys[k].S = rd.sig[k];
   }
+  ph.mark(c, "davidson");
   davidson(c, sys, [&](int nv, const cplx* in, cplx* out) { sigma_right(c, nv, in, out); }, maxL, c.opt.tol);
+  ph.mark(c, "finish");
   rd.nb.resize(n_ops);
   rd.beta.resize(n_ops);
   rd.iters.assign((size_t)n_ops * n_freq, 0);
@@ -668,6 +706,7 @@ void lr_solve(Ctx& c, int n_ops, const cplx* ops_host, int n_freq, const double*
   for (auto& p : rd.sig) c.dfree(p);
   rd.sig.clear();
   rd.solved = true;
+  ph.mark(c, "");
 }
 
 void response_function(Ctx& c, cplx* out_host) {
@@ -676,6 +715,8 @@ void response_function(Ctx& c, cplx* out_host) {
   Fast32 f32(c);
   const int64_t N = c.N;
   const int nop = rd.n_ops, maxL = std::max(8, c.opt.max_subspace);
+  Phases ph("response_function");
+  ph.mark(c, "eta.B");
   // Bilinear forms M^{xy}_{kl} = (b^x_k F) . b^y_l and E^{xy}_l = eta^x . b^y_l.  The Hessian
   // products of the trial vectors are formed in batches and contracted at once (never stored).
   std::vector<std::vector<zc>> M((size_t)nop * nop), E((size_t)nop * nop);
@@ -730,8 +771,11 @@ void response_function(Ctx& c, cplx* out_host) {
       std::vector<zc> W((size_t)Lx * nb);
       for (int l = 0; l < Lx; ++l)
         for (int j = 0; j < nb; ++j) W[(size_t)l * nb + j] = Q[x][q0 + j][l];
+      ph.mark(c, "combine");
       combine(c, rows(c, rd.basis[x], Lx), nb, W, yv);
+      ph.mark(c, "hessian");
       hessian_right(c, nb, yv, fb);
+      ph.mark(c, "gram");
       for (int y = 0; y < nop; ++y) {
         std::vector<zc> g;
         gram_host(c, rows(c, fb, nb), rows(c, rd.basis[y], rd.nb[y]), false, g);
@@ -741,6 +785,7 @@ void response_function(Ctx& c, cplx* out_host) {
       }
     }
   }
+  ph.mark(c, "forms");
   // f(z) = 1/2 [eta^X t^Y(z) + eta^Y t^X(-z) + (t^X(-z) F) t^Y(z)]
   auto half = [&](int f, int x, int y, int sz, int smz) {
     const zc* by = beta(y, f, sz);
