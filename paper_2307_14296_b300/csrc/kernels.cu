@@ -32,37 +32,123 @@ struct PermArgs {
   int64_t dim[kMaxRank];
   int64_t sstr[kMaxRank];
   int64_t dstr[kMaxRank];
+  uint32_t mul[kMaxRank];   // Granlund-Montgomery multipliers of dim (32-bit quotients)
+  int shr[kMaxRank];
 };
 
-// alpha kinds: 0 -> +-1 real (sign only), 1 -> real, 2 -> complex
+// q = n / d for 32-bit n with the multiplier m and shift l of d: q = (umulhi(n, m) + n) >> l
+__device__ __forceinline__ uint32_t gm_div(uint32_t n, uint32_t m, int l) {
+  return (uint32_t)(((uint64_t)__umulhi(n, m) + n) >> l);
+}
+
 template <int AK>
+__device__ __forceinline__ cplx scale_alpha(cplx x, cplx alpha, bool conj) {
+  if (conj) x.y = -x.y;
+  if (AK == 0) {
+    if (alpha.x < 0) { x.x = -x.x; x.y = -x.y; }
+  } else if (AK == 1) {
+    x.x *= alpha.x;
+    x.y *= alpha.x;
+  } else {
+    x = cmul(alpha, x);
+  }
+  return x;
+}
+
+// alpha kinds: 0 -> +-1 real (sign only), 1 -> real, 2 -> complex.  Element-wise in the
+// destination's index order; W32: every index is below 2^31 and the multipliers are used.
+template <int AK, bool W32>
 __global__ void __launch_bounds__(kThreads) k_permute(PermArgs a, const cplx* __restrict__ src, cplx* dst,
                                                       int64_t n, cplx alpha, bool conj, bool acc) {
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
        idx += (int64_t)gridDim.x * blockDim.x) {
-    int64_t r = idx, so = 0, dof = 0;
+    int64_t so = 0, dof = 0;
+    if (W32) {
+      uint32_t r = (uint32_t)idx;
 #pragma unroll
-    for (int k = kMaxRank - 1; k >= 0; --k) {
-      if (k < a.rank) {
-        int64_t q = r / a.dim[k];
-        int64_t c = r - q * a.dim[k];
-        r = q;
-        so += c * a.sstr[k];
-        dof += c * a.dstr[k];
+      for (int k = kMaxRank - 1; k >= 0; --k) {
+        if (k < a.rank) {
+          const uint32_t q = gm_div(r, a.mul[k], a.shr[k]);
+          const int64_t c = (int64_t)(r - q * (uint32_t)a.dim[k]);
+          r = q;
+          so += c * a.sstr[k];
+          dof += c * a.dstr[k];
+        }
+      }
+    } else {
+      int64_t r = idx;
+#pragma unroll
+      for (int k = kMaxRank - 1; k >= 0; --k) {
+        if (k < a.rank) {
+          const int64_t q = r / a.dim[k];
+          const int64_t c = r - q * a.dim[k];
+          r = q;
+          so += c * a.sstr[k];
+          dof += c * a.dstr[k];
+        }
       }
     }
-    cplx x = src[so];
-    if (conj) x.y = -x.y;
-    if (AK == 0) {
-      if (alpha.x < 0) { x.x = -x.x; x.y = -x.y; }
-    } else if (AK == 1) {
-      x.x *= alpha.x;
-      x.y *= alpha.x;
-    } else {
-      x = cmul(alpha, x);
-    }
+    cplx x = scale_alpha<AK>(src[so], alpha, conj);
     if (acc) x = cadd(x, dst[dof]);
     dst[dof] = x;
+  }
+}
+
+// Transposing permutation through shared memory: axis S has unit source stride, axis T unit
+// destination stride (S != T).  One 32 x 32 tile of (S, T) per step, the other axes ("batch")
+// decoded from the tile index; reads are coalesced along S and writes along T.
+struct TileArgs {
+  int nb;                      // batch axes
+  int64_t bdim[kMaxRank], bsstr[kMaxRank], bdstr[kMaxRank];
+  uint32_t bmul[kMaxRank];
+  int bshr[kMaxRank];
+  int64_t dimS, dimT, sstrT, dstrS;   // extents of S and T, source stride of T, destination stride of S
+  uint32_t ntS, ntT;                  // tiles along S and T
+  uint32_t mulS, mulT;                // multipliers of ntS, ntT
+  int shrS, shrT;
+};
+
+template <int AK>
+__global__ void __launch_bounds__(256) k_permute_tiled(TileArgs a, const cplx* __restrict__ src, cplx* dst,
+                                                       int64_t ntiles, cplx alpha, bool conj, bool acc) {
+  __shared__ cplx tile[32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    uint32_t r = (uint32_t)t;
+    const uint32_t qS = gm_div(r, a.mulS, a.shrS);
+    const int64_t s0 = (int64_t)(r - qS * a.ntS) * 32;
+    r = qS;
+    const uint32_t qT = gm_div(r, a.mulT, a.shrT);
+    const int64_t t0 = (int64_t)(r - qT * a.ntT) * 32;
+    r = qT;
+    int64_t sb = 0, db = 0;
+#pragma unroll
+    for (int k = kMaxRank - 1; k >= 0; --k) {
+      if (k < a.nb) {
+        const uint32_t q = gm_div(r, a.bmul[k], a.bshr[k]);
+        const int64_t c = (int64_t)(r - q * (uint32_t)a.bdim[k]);
+        r = q;
+        sb += c * a.bsstr[k];
+        db += c * a.bdstr[k];
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {   // read: tx along S (unit source stride), rows along T
+      const int64_t s = s0 + tx, tt = t0 + ty + 8 * i;
+      if (s < a.dimS && tt < a.dimT) tile[ty + 8 * i][tx] = src[sb + s + tt * a.sstrT];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {   // write: tx along T (unit destination stride), rows along S
+      const int64_t tt = t0 + tx, s = s0 + ty + 8 * i;
+      if (s < a.dimS && tt < a.dimT) {
+        cplx x = scale_alpha<AK>(tile[tx][ty + 8 * i], alpha, conj);
+        cplx* d = dst + db + tt + s * a.dstrS;
+        if (acc) x = cadd(x, *d);
+        *d = x;
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -927,26 +1013,83 @@ void vecmat(const Launch& L, int64_t n, const VecMat& a, double* scratch) {
   }
 }
 
+namespace {
+void gm_magic(int64_t d, uint32_t& mul, int& shr) {   // Granlund-Montgomery multiplier of d < 2^31
+  int l = 0;
+  while ((int64_t(1) << l) < d) ++l;
+  shr = l;
+  mul = (uint32_t)(((unsigned __int128)1 << 32) * (((uint64_t)1 << l) - (uint64_t)d) / (uint64_t)d + 1);
+}
+template <int AK>
+void launch_permute(const Launch& L, const PermArgs& a, const cplx* src, cplx* dst, int64_t n, cplx al, bool conj,
+                    bool acc) {
+  // transposing case: the unit-stride source axis is not the unit-stride destination axis
+  int S = -1, T = -1;
+  for (int k = 0; k < a.rank; ++k) {
+    if (a.sstr[k] == 1) S = k;
+    if (a.dstr[k] == 1) T = k;
+  }
+  if (S >= 0 && T >= 0 && S != T && a.dim[S] >= 8 && a.dim[T] >= 8 && n < (int64_t(1) << 31)) {
+    TileArgs t{};
+    t.dimS = a.dim[S];
+    t.dimT = a.dim[T];
+    t.sstrT = a.sstr[T];
+    t.dstrS = a.dstr[S];
+    t.ntS = (uint32_t)((t.dimS + 31) / 32);
+    t.ntT = (uint32_t)((t.dimT + 31) / 32);
+    gm_magic(t.ntS, t.mulS, t.shrS);
+    gm_magic(t.ntT, t.mulT, t.shrT);
+    int64_t batch = 1;
+    for (int k = 0; k < a.rank; ++k) {
+      if (k == S || k == T) continue;
+      t.bdim[t.nb] = a.dim[k];
+      t.bsstr[t.nb] = a.sstr[k];
+      t.bdstr[t.nb] = a.dstr[k];
+      gm_magic(a.dim[k], t.bmul[t.nb], t.bshr[t.nb]);
+      ++t.nb;
+      batch *= a.dim[k];
+    }
+    const int64_t ntiles = batch * t.ntS * t.ntT;
+    const int g = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, 148 * 16));
+    k_permute_tiled<AK><<<g, 256, 0, L.s>>>(t, src, dst, ntiles, al, conj, acc);
+    return;
+  }
+  const int g = grid_for(n);
+  if (n < (int64_t(1) << 31)) k_permute<AK, true><<<g, kThreads, 0, L.s>>>(a, src, dst, n, al, conj, acc);
+  else k_permute<AK, false><<<g, kThreads, 0, L.s>>>(a, src, dst, n, al, conj, acc);
+}
+}  // namespace
+
 void permute(const Launch& L, const Tensor& src, const Tensor& dst, cplx alpha, bool accumulate) {
   CCLR_REQUIRE(src.rank == dst.rank, CCLR_E_ARG, "permute: rank mismatch");
+  // drop extent-1 axes and merge neighbours that are contiguous in both source and destination
   PermArgs a{};
-  a.rank = dst.rank;
   for (int k = 0; k < dst.rank; ++k) {
     CCLR_REQUIRE(src.dim[k] == dst.dim[k], CCLR_E_ARG, "permute: extent mismatch");
-    a.dim[k] = dst.dim[k];
-    a.sstr[k] = src.str[k];
-    a.dstr[k] = dst.str[k];
+    if (dst.dim[k] == 1) continue;
+    if (a.rank > 0 && a.sstr[a.rank - 1] == dst.dim[k] * src.str[k] && a.dstr[a.rank - 1] == dst.dim[k] * dst.str[k]) {
+      a.dim[a.rank - 1] *= dst.dim[k];
+      a.sstr[a.rank - 1] = src.str[k];
+      a.dstr[a.rank - 1] = dst.str[k];
+    } else {
+      a.dim[a.rank] = dst.dim[k];
+      a.sstr[a.rank] = src.str[k];
+      a.dstr[a.rank] = dst.str[k];
+      ++a.rank;
+    }
+  }
+  if (a.rank == 0) {
+    a.rank = 1;
+    a.dim[0] = 1;
   }
   const int64_t n = dst.numel();
   if (n == 0) return;
+  for (int k = 0; k < a.rank; ++k)
+    if (a.dim[k] < (int64_t(1) << 31)) gm_magic(a.dim[k], a.mul[k], a.shr[k]);
   cplx al = make_double2(alpha.x * src.scale, alpha.y * src.scale);
-  const int g = grid_for(n);
-  if (al.y == 0.0 && (al.x == 1.0 || al.x == -1.0))
-    k_permute<0><<<g, kThreads, 0, L.s>>>(a, src.p, dst.p, n, al, src.conj, accumulate);
-  else if (al.y == 0.0)
-    k_permute<1><<<g, kThreads, 0, L.s>>>(a, src.p, dst.p, n, al, src.conj, accumulate);
-  else
-    k_permute<2><<<g, kThreads, 0, L.s>>>(a, src.p, dst.p, n, al, src.conj, accumulate);
+  if (al.y == 0.0 && (al.x == 1.0 || al.x == -1.0)) launch_permute<0>(L, a, src.p, dst.p, n, al, src.conj, accumulate);
+  else if (al.y == 0.0) launch_permute<1>(L, a, src.p, dst.p, n, al, src.conj, accumulate);
+  else launch_permute<2>(L, a, src.p, dst.p, n, al, src.conj, accumulate);
   CCLR_CK(cudaGetLastError());
   bump(L);
 }

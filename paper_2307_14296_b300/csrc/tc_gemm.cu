@@ -235,47 +235,96 @@ __global__ void __launch_bounds__(128, 1)
 
 // Strided complex FP64 view -> BF16 slice planes [slice][re|im][rows][Kpad].  The view is given
 // as up to 8 axes, the first nr of which form the row index and the rest the K index (row-major
-// order within each group), so any permutation of a tensor is split in one pass.
+// order within each group), so any permutation of a tensor is split in one pass.  Index decoding
+// divides by the axis extents with Granlund-Montgomery multipliers (q = (umulhi(n, m) + n) >> l,
+// exact for 32-bit n).
 struct ViewArgs {
   int rank, nr;
   int64_t dim[kMaxRank];
   int64_t str[kMaxRank];
+  uint32_t mul[kMaxRank];
+  int shr[kMaxRank];
 };
 
-__global__ void k_split_view(const double2* __restrict__ X, ViewArgs v, int64_t rows, int64_t K, bool conj, int nsl,
-                             __nv_bfloat16* __restrict__ out, int64_t Kpad) {
-  const int64_t n = rows * Kpad;
+__device__ __forceinline__ int64_t view_off(const ViewArgs& v, int a0, int a1, uint32_t i) {
+  int64_t off = 0;
+#pragma unroll
+  for (int a = kMaxRank - 1; a >= 0; --a) {
+    if (a < a0 || a >= a1) continue;
+    const uint32_t q = (uint32_t)(((uint64_t)__umulhi(i, v.mul[a]) + i) >> v.shr[a]);
+    off += (int64_t)(i - q * (uint32_t)v.dim[a]) * v.str[a];
+    i = q;
+  }
+  return off;
+}
+
+// IEEE 754 binary64 -> binary32 on the integer pipe (round to nearest, ties away from zero;
+// results below the binary32 normal range flush to zero).  The FP64 <-> FP32 cvt instructions
+// issue on the FP64 pipe, about 1/64 of the FP32 rate on sm_103.
+__device__ __forceinline__ float split_d2f(double x) {
+  const uint64_t b = (uint64_t)__double_as_longlong(x);
+  const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
+  const uint32_t sign = hi & 0x80000000u, e = (hi >> 20) & 0x7ffu;
+  const uint32_t t = __funnelshift_l(lo, hi, 3) + ((lo >> 28) & 1u);
+  uint32_t f = (t - 0xC0000000u) | sign;   // rebias 1023 -> 127 (896; low 9 bits 0x180)
+  if (e < 897u) f = sign;
+  if (e > 1150u) f = sign | ((e == 0x7ffu && ((hi & 0xfffffu) | lo)) ? 0x7fc00000u : 0x7f800000u);
+  return __uint_as_float(f);
+}
+// bfloat16 = the top 16 bits of a binary32, rounded to nearest even
+__device__ __forceinline__ uint32_t bf16_bits(float f) {
+  const uint32_t u = __float_as_uint(f);
+  return (u + 0x7fffu + ((u >> 16) & 1u)) >> 16;
+}
+
+// Work items are (row, chunk of 64 element pairs), strided over all warps of the grid, so that
+// operands with few long rows and with many short rows both fill the GPU; each lane converts
+// pairs of consecutive K elements and stores them as packed bf16x2.  x is rounded to FP32
+// (24 bits) and cut into slices s_0 + s_1 + s_2 in FP32 arithmetic (each difference is exact).
+constexpr int kSplitPairs = 64;
+__global__ void __launch_bounds__(256) k_split_view(const double2* __restrict__ X, ViewArgs v, int64_t rows, int64_t K,
+                                                    bool conj, int nsl, __nv_bfloat16* __restrict__ out, int64_t Kpad,
+                                                    uint32_t nchunk, uint32_t chunk_mul, int chunk_shr) {
   const int64_t plane = rows * Kpad;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = idx / Kpad, k = idx - r * Kpad;
-    double2 x = make_double2(0.0, 0.0);
-    if (k < K) {
-      int64_t off = 0, rr = r, kk = k;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  uint32_t* o32 = reinterpret_cast<uint32_t*>(out);
+  const int64_t pairs = Kpad / 2;
+  const int64_t items = rows * (int64_t)nchunk;
+  for (int64_t w = warp0; w < items; w += nwarps) {
+    const uint32_t wi = (uint32_t)w;
+    const uint32_t r = (uint32_t)(((uint64_t)__umulhi(wi, chunk_mul) + wi) >> chunk_shr);
+    const uint32_t c = wi - r * nchunk;
+    const int64_t roff = view_off(v, 0, v.nr, r);
 #pragma unroll
-      for (int a = kMaxRank - 1; a >= 0; --a) {
-        if (a >= v.rank) continue;
-        if (a >= v.nr) {
-          const int64_t q = kk / v.dim[a];
-          off += (kk - q * v.dim[a]) * v.str[a];
-          kk = q;
-        } else {
-          const int64_t q = rr / v.dim[a];
-          off += (rr - q * v.dim[a]) * v.str[a];
-          rr = q;
-        }
+    for (int h = 0; h < kSplitPairs / 32; ++h) {
+      const int64_t p = (int64_t)c * kSplitPairs + h * 32 + lane;
+      if (p >= pairs) break;
+      float re[2], im[2];
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        const int64_t k = 2 * p + t;
+        double2 x = make_double2(0.0, 0.0);
+        if (k < K) x = X[roff + view_off(v, v.nr, v.rank, (uint32_t)k)];
+        re[t] = split_d2f(x.x);
+        im[t] = split_d2f(conj ? -x.y : x.y);
       }
-      x = X[off];
-      if (conj) x.y = -x.y;
-    }
-    double re = x.x, im = x.y;
+      const int64_t e2 = (int64_t)r * (Kpad / 2) + p;   // index of the bf16 pair within a plane
 #pragma unroll
-    for (int s = 0; s < 3; ++s) {
-      if (s >= nsl) break;
-      const __nv_bfloat16 hr = __float2bfloat16_rn((float)re), hi = __float2bfloat16_rn((float)im);
-      out[(2 * s + 0) * plane + idx] = hr;
-      out[(2 * s + 1) * plane + idx] = hi;
-      re -= (double)__bfloat162float(hr);
-      im -= (double)__bfloat162float(hi);
+      for (int s = 0; s < 3; ++s) {
+        if (s >= nsl) break;
+        uint32_t br[2], bi[2];
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+          br[t] = bf16_bits(re[t]);
+          bi[t] = bf16_bits(im[t]);
+          re[t] -= __uint_as_float(br[t] << 16);
+          im[t] -= __uint_as_float(bi[t] << 16);
+        }
+        o32[((2 * s + 0) * plane) / 2 + e2] = br[0] | (br[1] << 16);
+        o32[((2 * s + 1) * plane) / 2 + e2] = bi[0] | (bi[1] << 16);
+      }
     }
   }
 }
@@ -335,24 +384,62 @@ std::map<std::string, CacheEntry>& cache() {
 }
 uint64_t g_cache_gen = 0;
 
-void make_slices(Ctx& c, const Tensor& v, int nr, int nsl, Slices& s, __nv_bfloat16* dst) {
-  tc::ViewArgs a{};
-  a.rank = v.rank;
-  a.nr = nr;
-  int64_t rows = 1, K = 1;
+// View arguments of the split kernel: axes of extent 1 dropped, neighbours that are contiguous
+// in memory merged (within the row group and within the K group), division multipliers set.
+tc::ViewArgs view_args(const Tensor& v, int nr) {
+  std::vector<int64_t> d[2], st[2];
   for (int i = 0; i < v.rank; ++i) {
-    a.dim[i] = v.dim[i];
-    a.str[i] = v.str[i];
-    (i < nr ? rows : K) *= v.dim[i];
+    const int g = i < nr ? 0 : 1;
+    if (v.dim[i] == 1) continue;
+    if (!d[g].empty() && st[g].back() == v.dim[i] * v.str[i]) {
+      d[g].back() *= v.dim[i];
+      st[g].back() = v.str[i];
+    } else {
+      d[g].push_back(v.dim[i]);
+      st[g].push_back(v.str[i]);
+    }
   }
+  for (int g = 0; g < 2; ++g)
+    if (d[g].empty()) { d[g].push_back(1); st[g].push_back(0); }
+  tc::ViewArgs a{};
+  a.nr = (int)d[0].size();
+  a.rank = a.nr + (int)d[1].size();
+  for (int i = 0; i < a.rank; ++i) {
+    const int g = i < a.nr ? 0 : 1, j = i < a.nr ? i : i - a.nr;
+    const int64_t dim = d[g][j];
+    CCLR_REQUIRE(dim >= 1 && dim < (int64_t(1) << 31), CCLR_E_ARG, "tensor-core split: axis extent too large");
+    int l = 0;
+    while ((int64_t(1) << l) < dim) ++l;
+    a.dim[i] = dim;
+    a.str[i] = st[g][j];
+    a.shr[i] = l;
+    a.mul[i] = (uint32_t)(((unsigned __int128)1 << 32) * (((uint64_t)1 << l) - (uint64_t)dim) / (uint64_t)dim + 1);
+  }
+  return a;
+}
+
+void launch_split(const Tensor& v, int nr, int64_t rows, int64_t K, int64_t Kpad, int nsl, __nv_bfloat16* dst,
+                  cudaStream_t stream) {
+  CCLR_REQUIRE(rows < (int64_t(1) << 31) && K < (int64_t(1) << 31), CCLR_E_ARG, "tensor-core split: operand too large");
+  const tc::ViewArgs a = view_args(v, nr);
+  const int64_t nchunk = (Kpad / 2 + tc::kSplitPairs - 1) / tc::kSplitPairs;
+  CCLR_REQUIRE(rows * nchunk < (int64_t(1) << 32), CCLR_E_ARG, "tensor-core split: operand too large");
+  int l = 0;
+  while ((int64_t(1) << l) < nchunk) ++l;
+  const uint32_t mul = (uint32_t)(((unsigned __int128)1 << 32) * (((uint64_t)1 << l) - (uint64_t)nchunk) / (uint64_t)nchunk + 1);
+  const int g = (int)std::max<int64_t>(1, std::min<int64_t>((rows * nchunk + 7) / 8, 148 * 16));
+  tc::k_split_view<<<g, 256, 0, stream>>>(v.p, a, rows, K, v.conj, nsl, dst, Kpad, (uint32_t)nchunk, mul, l);
+}
+
+void make_slices(Ctx& c, const Tensor& v, int nr, int nsl, Slices& s, __nv_bfloat16* dst) {
+  int64_t rows = 1, K = 1;
+  for (int i = 0; i < v.rank; ++i) (i < nr ? rows : K) *= v.dim[i];
   s.rows = rows;
   s.K = K;
   s.Kpad = (K + tc::BK - 1) / tc::BK * tc::BK;
   s.nsl = nsl;
   s.p = dst;
-  const int64_t n = rows * s.Kpad;
-  const int g = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 148 * 16));
-  tc::k_split_view<<<g, 256, 0, c.stream>>>(v.p, a, rows, K, v.conj, nsl, dst, s.Kpad);
+  launch_split(v, nr, rows, K, s.Kpad, nsl, dst, c.stream);
   CCLR_CK(cudaGetLastError());
   ++c.launches;
   s.tm = make_map(dst, rows, s.Kpad, 2 * nsl, 128);
@@ -560,16 +647,7 @@ int tc_raw_gemm_nt(int precision, int64_t M, int64_t N, int64_t K, const cplx* A
   cplx* P = (cplx*)(scratch + 256 + up256(p.bytes_sn) + up256(p.bytes_sm));
   CCLR_CK(cudaMemsetAsync(err, 0, sizeof(int), stream));   // the shared scratch keeps the last call's flag
   auto split = [&](const cplx* X, int64_t rows, __nv_bfloat16* dst) {
-    tc::ViewArgs a{};
-    a.rank = 2;
-    a.nr = 1;
-    a.dim[0] = rows;
-    a.dim[1] = K;
-    a.str[0] = K;
-    a.str[1] = 1;
-    const int64_t n = rows * p.Kpad;
-    const int g = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 148 * 16));
-    tc::k_split_view<<<g, 256, 0, stream>>>(X, a, rows, K, false, nsl, dst, p.Kpad);
+    launch_split(Tensor::make(const_cast<cplx*>(X), {rows, K}), 1, rows, K, p.Kpad, nsl, dst, stream);
     CCLR_CK(cudaGetLastError());
   };
   split(B, N, sn);
