@@ -184,6 +184,36 @@ def config_dict(args):
 
 
 # ------------------------------------------------------------------------------------------ GPU
+def run_gemm(args):
+    """Tensor-core GEMM alone on one shape (A: M x K, B: N x K, complex), e.g. the packed ladder
+    contraction of eight trial vectors (M = 8 Po, K = Pv): a small case for kernel captures."""
+    import paper_2307_14296_b300 as pk
+    import synth
+    M, N, K = (int(x) for x in args.gemm.split(","))
+    rng = np.random.default_rng(2307)
+    A = rng.standard_normal((M, K)) + 1j * rng.standard_normal((M, K))
+    B = rng.standard_normal((N, K)) + 1j * rng.standard_normal((N, K))
+    prec = pk.TC_BF16X3 if args.precision == "bf16x3" else pk.FP64
+    ctx = pk.Context(0, precision=prec)
+    tiny = synth.make_instance(2, 4)   # a Hamiltonian gives the context its device workspace
+    ctx.cclr_set_hamiltonian(2, 4, tiny.fock, [tiny.blocks[k] for k in synth.CLASSES])
+    ctx.cclr_kernel_profile(True)
+    for _ in range(max(1, args.warmup)):
+        ctx.cclr_zgemm_nt(A, B, prec)
+    ctx.cclr_kernel_profile(True)
+    for _ in range(max(1, args.steps)):
+        C = ctx.cclr_zgemm_nt(A, B, prec)
+    prof = ctx.cclr_kernel_profile(False)
+    part = A[:4] @ B[:4].T
+    rel = float(np.abs(C[:4, :4] - part).max() / np.abs(part).max())
+    per = prof["ms"] / max(1, args.steps)
+    print(json.dumps({"mode": "gemm", "M": M, "N": N, "K": K, "precision": args.precision,
+                      "kernel_ms": per, "launches_per_call": prof["launches"] / max(1, args.steps),
+                      "exec_tflops": prof["flops_exec"] / max(1, args.steps) / (per * 1e-3) / 1e12 if per > 0 else None,
+                      "useful_tflops": prof["flops_useful"] / max(1, args.steps) / (per * 1e-3) / 1e12 if per > 0 else None,
+                      "sample_rel_err": rel}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -193,10 +223,16 @@ def main():
     ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-breakdown", action="store_true", help="skip the per-kernel timing step")
     ap.add_argument("--workload", default="30x200", choices=sorted(WORKLOADS))
+    ap.add_argument("--gemm", default=None, metavar="M,N,K",
+                    help="time only the tensor-core complex GEMM C = A B^T on one shape (kernel profiling)")
     args = ap.parse_args()
     global WORKLOAD
     WORKLOAD = WORKLOADS[args.workload]
+    if args.gemm:
+        run_gemm(args)
+        return
     world, rank, local = dist_init()
     if args.impl == "reference":
         run_reference(args, world, rank)
@@ -288,6 +324,18 @@ def main():
         fp64_sigma = time.perf_counter() - t0
         fp64 = dict(sigma_seconds=fp64_sigma, step_seconds_extrapolated=fp64_sigma * n_prod,
                     note="FP64 step extrapolated: sigma-type products of the mixed step x one FP64 sigma")
+    # per-kernel shares: one extra untimed step with CUDA events around every launch
+    breakdown = None
+    if rank == 0 and not args.no_breakdown:
+        ctx.cclr_kernel_profile(True)
+        ctx.cclr_kernel_breakdown()
+        step()
+        ctx.cclr_kernel_profile(False)
+        bd = ctx.cclr_kernel_breakdown()
+        tot = sum(ms for _, ms in bd.values())
+        top = sorted(bd.items(), key=lambda kv: -kv[1][1])[:12]
+        breakdown = dict(note="one untimed step, CUDA events around every launch", total_ms=tot,
+                         kernels=[dict(name=k, launches=n, ms=ms, share=ms / tot) for k, (n, ms) in top])
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         tf, dt, desc = oracle_sample()
@@ -312,7 +360,7 @@ def main():
                       peak_source=f"bf16_tflops_sustained of {src} MEASURED_PEAKS",
                       launches=prof["launches"], kernel_ms_per_step=prof["ms"] / args.steps,
                       useful_complex_tflops=(prof["flops_useful"] / (prof["ms"] / 1e3) / 1e12 if prof["ms"] else None)),
-        cpu_baseline=cpu, e2e=e2e, fp64=fp64,
+        cpu_baseline=cpu, e2e=e2e, fp64=fp64, kernel_breakdown=breakdown,
         gpu_launches=int(sum(s["launches"] for s in stats)),
         clocks=clk.summary(),
         alpha_mean_last_freq=[float(np.trace(alpha[-1]).real / 3), float(np.trace(alpha[-1]).imag / 3)],

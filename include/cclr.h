@@ -185,6 +185,13 @@ cclr_status cclr_zgemm_nt_noalloc(int precision, int M, int N, int K, const cclr
  * product), useful complex flops (8 M N K)}; the counters are then reset. */
 cclr_status cclr_kernel_profile(cclr_ctx *ctx, int enable, double *out4);
 
+/* Per-kernel timing switched on by cclr_kernel_profile: a pair of CUDA events on the context's
+ * stream around every launch of the library, summed per kernel name.  Writes one text line per
+ * kernel, "name launches milliseconds\n", most expensive first, into buf (cap bytes including
+ * the terminating NUL; longer text is truncated) and resets the totals.  The library's own
+ * measurement aid, not an operation of the paper.  CCLR_E_ARG if buf is NULL or cap < 1. */
+cclr_status cclr_kernel_breakdown(cclr_ctx *ctx, char *buf, int cap);
+
 /* Per-call statistics of the last cc_* call: sigma launches and vectors, seconds spent. */
 typedef struct {
   long sigma_calls, sigma_vectors;

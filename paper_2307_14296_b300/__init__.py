@@ -33,7 +33,7 @@ EXPORTS = (
     "cc_ground", "cc_lambda", "cc_lr_solve", "cc_response_function", "cclr_get_amplitudes",
     "cclr_set_amplitudes", "cclr_get_response_vector", "cclr_sigma", "cclr_residual", "cclr_xi",
     "cclr_eta", "cclr_hessian", "cclr_zgemm_nt", "cclr_kernel_profile", "cclr_get_stats",
-    "cclr_zgemm_nt_noalloc",
+    "cclr_zgemm_nt_noalloc", "cclr_kernel_breakdown",
 )
 
 
@@ -69,6 +69,7 @@ _sig = {
     "cclr_hessian": (_i, [_vp, _i, _vp, _vp, _i]),
     "cclr_zgemm_nt": (_i, [_vp, _i, _i, _i, _i, _vp, _vp, _vp]),
     "cclr_kernel_profile": (_i, [_vp, _i, _vp]),
+    "cclr_kernel_breakdown": (_i, [_vp, ctypes.c_char_p, _i]),
     "cclr_zgemm_nt_noalloc": (_i, [_i, _i, _i, _i, _vp, _vp, _vp, _vp]),
     "cclr_get_stats": (_i, [_vp, ctypes.POINTER(Stats)]),
 }
@@ -242,6 +243,17 @@ class Context:
         out = np.zeros(4, np.float64)
         self._check(_lib.cclr_kernel_profile(self._h, int(enable), _ptr(out)))
         return dict(launches=int(out[0]), ms=float(out[1]), flops_exec=float(out[2]), flops_useful=float(out[3]))
+
+    def cclr_kernel_breakdown(self) -> dict:
+        """Per-kernel {name: (launches, milliseconds)} since the last call (timing switched on by
+        cclr_kernel_profile)."""
+        buf = ctypes.create_string_buffer(1 << 16)
+        self._check(_lib.cclr_kernel_breakdown(self._h, buf, len(buf)))
+        out = {}
+        for line in buf.value.decode().splitlines():
+            name, n, ms = line.rsplit(" ", 2)
+            out[name] = (int(n), float(ms))
+        return out
 
     def cclr_get_stats(self) -> dict:
         s = Stats()

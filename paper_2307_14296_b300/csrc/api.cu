@@ -1,6 +1,7 @@
 // The C ABI of libcclr (declared in include/cclr.h).  Every entry point catches all C++
 // exceptions and returns a status; the message is kept in the context for cclr_last_error().
 #include "ctx.h"
+#include <cstdio>
 #include <chrono>
 #include <cstdlib>
 
@@ -30,6 +31,7 @@ cclr_status guard(cclr_ctx* h, F&& fn) {
     fn(c);
     CCLR_CK(cudaStreamSynchronize(c.stream));
     if (c.prof) c.prof_collect();
+    if (c.kt.on) c.kt.collect();
     if (c.tc_err) {
       int h = 0;
       CCLR_CK(cudaMemcpy(&h, c.tc_err, sizeof(int), cudaMemcpyDeviceToHost));
@@ -134,6 +136,7 @@ cclr_status cclr_create(cclr_ctx** out, int device, const cclr_options* opt) {
   }
   c.L.s = c.stream;
   c.L.count = &c.launches;
+  c.L.kt = &c.kt;
   *out = h;
   return CCLR_OK;
 }
@@ -441,6 +444,25 @@ cclr_status cclr_kernel_profile(cclr_ctx* h, int enable, double* out4) {
   c.prof_launches = 0;
   c.prof_ms = c.prof_flops_exec = c.prof_flops_useful = 0.0;
   c.prof = enable != 0;
+  c.kt.on = enable != 0;
+  return CCLR_OK;
+}
+
+cclr_status cclr_kernel_breakdown(cclr_ctx* h, char* buf, int cap) {
+  if (!h || !buf || cap < 1) return CCLR_E_ARG;
+  Ctx& c = h->c;
+  auto t = c.kt.totals;
+  std::sort(t.begin(), t.end(), [](auto& a, auto& b) { return a.second.second > b.second.second; });
+  std::string out;
+  for (auto& e : t) {
+    char line[256];
+    std::snprintf(line, sizeof(line), "%s %ld %.6f\n", e.first.c_str(), e.second.first, e.second.second);
+    out += line;
+  }
+  const size_t n = std::min<size_t>(out.size(), (size_t)cap - 1);
+  std::memcpy(buf, out.data(), n);
+  buf[n] = 0;
+  c.kt.totals.clear();
   return CCLR_OK;
 }
 

@@ -58,6 +58,13 @@ void einsum_impl(Ctx& c, const char* spec, cplx alpha, const Tensor& A, const Te
 // synchronizes the stream around each call).
 void einsum(Ctx& c, const char* spec, cplx alpha, const Tensor& A, const Tensor& B, double beta, const Tensor& C) {
   static const bool trace = std::getenv("CCLR_TRACE") != nullptr;
+  // per-contraction kernel timing: launches are labelled with the spec when asked for
+  static const bool detail = std::getenv("CCLR_PROFILE_DETAIL") != nullptr;
+  struct Label {
+    KernelTimer& k;
+    Label(KernelTimer& kt, const char* l, bool on) : k(kt) { if (on) k.label = l; }
+    ~Label() { k.label = nullptr; }
+  } lab(c.kt, spec, detail);
   if (!trace) return einsum_impl(c, spec, alpha, A, B, beta, C);
   CCLR_CK(cudaStreamSynchronize(c.stream));
   auto t0 = std::chrono::steady_clock::now();
@@ -133,11 +140,40 @@ void einsum_impl(Ctx& c, const char* spec, cplx alpha, const Tensor& A, const Te
     } else if (cBA.contiguous()) {
       tc_gemm_views(c, vb, nrb, va, nra, al, cx(beta), C.p, M);
     } else {
-      cplx* tmp = c.ws.cplxs(M * N);
-      tc_gemm_views(c, va, nra, vb, nrb, al, cx(0.0), tmp, N);
-      std::vector<int64_t> d;
-      for (char ch : fa + fb) d.push_back(ext[ch]);
-      permute(c.L, reorder(Tensor::make(tmp, d), fa + fb, s.c), C, cx(1.0), beta != 0.0);
+      // Strided target: the epilogue writes C through a row-offset map.  The lane side (TMEM
+      // rows, stored contiguously across a warp) is the operand holding C's unit-stride index,
+      // which is made its fastest row index.
+      char unit = 0;
+      for (size_t k = 0; k < s.c.size(); ++k)
+        if (C.str[k] == 1 && C.dim[k] > 1) unit = s.c[k];
+      const bool lane_b = unit == 0 || fb.find(unit) != std::string::npos;
+      std::string fl = lane_b ? fb : fa, fr = lane_b ? fa : fb;
+      if (unit) {
+        fl.erase(fl.find(unit), 1);
+        fl += unit;
+      }
+      if (tc_splits(M, N, K) == 1 && !fl.empty() && !fr.empty() && fl.size() <= 4 && fr.size() <= 4) {
+        const Tensor vl = lane_b ? reorder(B, s.b, fl + korder) : reorder(A, s.a, fl + korder);
+        const Tensor vr = lane_b ? reorder(A, s.a, fr + korder) : reorder(B, s.b, fr + korder);
+        OutAxes oa;
+        oa.nm = (int)fr.size();
+        oa.nn = (int)fl.size();
+        for (int i = 0; i < oa.nm; ++i) {
+          oa.mdim[i] = ext[fr[i]];
+          oa.mstr[i] = C.str[s.c.find(fr[i])];
+        }
+        for (int i = 0; i < oa.nn; ++i) {
+          oa.ndim[i] = ext[fl[i]];
+          oa.nstr[i] = C.str[s.c.find(fl[i])];
+        }
+        tc_gemm_views(c, vr, (int)fr.size(), vl, (int)fl.size(), al, cx(beta), C.p, 0, &oa);
+      } else {
+        cplx* tmp = c.ws.cplxs(M * N);
+        tc_gemm_views(c, va, nra, vb, nrb, al, cx(0.0), tmp, N);
+        std::vector<int64_t> d;
+        for (char ch : fa + fb) d.push_back(ext[ch]);
+        permute(c.L, reorder(Tensor::make(tmp, d), fa + fb, s.c), C, cx(1.0), beta != 0.0);
+      }
     }
     return;
   }

@@ -27,6 +27,9 @@ struct ResponseData {
   bool solved = false;
 };
 
+struct Ctx;
+void tc_release_cache_for(Ctx& c);   // frees the cached BF16 slices of persistent operands
+
 struct Ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -71,6 +74,7 @@ struct Ctx {
   // tensor-core status word (bounded-wait expiry) and optional per-launch timing of the
   // tensor-core kernel with CUDA events on the context's stream
   int* tc_err = nullptr;
+  KernelTimer kt;   // per-kernel timing (switched on with the tensor-core timing)
   bool prof = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
   size_t ev_used = 0;
@@ -100,7 +104,12 @@ struct Ctx {
   // helpers
   cplx* dalloc(int64_t n_elems) {
     void* p = nullptr;
-    CCLR_CK(cudaMalloc(&p, sizeof(cplx) * (size_t)(n_elems > 0 ? n_elems : 1)));
+    const size_t bytes = sizeof(cplx) * (size_t)(n_elems > 0 ? n_elems : 1);
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {   // the tensor-core slice cache yields its memory first
+      cudaGetLastError();
+      tc_release_cache_for(*this);
+      CCLR_CK(cudaMalloc(&p, bytes));
+    }
     persistent.push_back(p);
     return (cplx*)p;
   }
@@ -128,8 +137,15 @@ void tc_release_cache();
 bool tc_eligible(int64_t M, int64_t N, int64_t K);
 // C[m*ldc + n] = alpha sum_k vm[m,k] vn[n,k] + beta C on the tensor cores; the first nrm / nrn
 // axes of the views are the rows, the remaining axes K (in the same order in both views)
+// Output map of a strided GEMM result: element (m, n) at C + moff(m) + noff(n), each a row-major
+// decomposition over up to four axes.
+struct OutAxes {
+  int nm = 0, nn = 0;
+  int64_t mdim[4] = {}, mstr[4] = {}, ndim[4] = {}, nstr[4] = {};
+};
 void tc_gemm_views(Ctx& c, const Tensor& vm, int nrm, const Tensor& vn, int nrn, cplx alpha, cplx beta, cplx* C,
-                   int64_t ldc);
+                   int64_t ldc, const OutAxes* oa = nullptr);
+int tc_splits(int64_t M, int64_t N, int64_t K);   // split-K slices the tensor-core GEMM would use
 
 // equations (ccsd.cu, sigma.cu, props.cu)
 void build_denominators(Ctx& c);

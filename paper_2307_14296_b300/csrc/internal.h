@@ -110,9 +110,52 @@ struct Scope {  // RAII release of arena temporaries
 };
 
 // ---------------------------------------------------------------- kernels (kernels.cu)
+// Per-kernel timing: when on, a pair of CUDA events is recorded on the stream around every
+// launch (begin() before, end() after); collect() (after a stream synchronize) adds the
+// durations to per-name totals.
+struct KernelTimer {
+  bool on = false;
+  const char* label = nullptr;   // contraction being executed (kept in the names when set)
+  std::vector<cudaEvent_t> pool;
+  std::vector<std::string> names;
+  size_t used = 0;
+  std::vector<std::pair<std::string, std::pair<long, double>>> totals;   // name -> (launches, ms)
+  cudaEvent_t next(cudaStream_t s) {
+    if (used == pool.size()) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) throw Error(CCLR_E_CUDA, "cudaEventCreate failed");
+      pool.push_back(e);
+    }
+    cudaEvent_t e = pool[used++];
+    if (cudaEventRecord(e, s) != cudaSuccess) throw Error(CCLR_E_CUDA, "cudaEventRecord failed");
+    return e;
+  }
+  void begin(cudaStream_t s) {
+    if (on) next(s);
+  }
+  void end(cudaStream_t s, const char* name) {
+    if (!on || used % 2 == 0) return;   // no begin() recorded for this launch
+    next(s);
+    names.push_back(label ? std::string(label) + " | " + name : std::string(name));
+  }
+  void collect() {
+    for (size_t i = 0; i + 1 < used; i += 2) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, pool[i], pool[i + 1]) != cudaSuccess) continue;
+      const std::string& nm = names[i / 2];
+      auto it = std::find_if(totals.begin(), totals.end(), [&](auto& t) { return t.first == nm; });
+      if (it == totals.end()) totals.push_back({nm, {1, ms}});
+      else { it->second.first += 1; it->second.second += ms; }
+    }
+    used = 0;
+    names.clear();
+  }
+};
+
 struct Launch {  // stream + launch counter shared by all kernels of one context
   cudaStream_t s = nullptr;
   long* count = nullptr;
+  KernelTimer* kt = nullptr;
   // FP32 arithmetic (FP64 storage) in the solvers' vector kernels (dots, vecmat, Gram blocks);
   // set by the iterative solvers in the tensor-core modes only.
   bool fast32 = false;

@@ -25,7 +25,13 @@ inline int grid_for(int64_t n, int per = kThreads) {
   return (int)g;
 }
 
-inline void bump(const Launch& L) { if (L.count) ++*L.count; }
+inline void kbeg(const Launch& L) {   // before a launch: timer start (when per-kernel timing is on)
+  if (L.kt) L.kt->begin(L.s);
+}
+inline void bump(const Launch& L, const char* name) {   // after a launch: count it, timer stop
+  if (L.count) ++*L.count;
+  if (L.kt) L.kt->end(L.s, name);
+}
 
 struct PermArgs {
   int rank;
@@ -873,9 +879,10 @@ int reduce_blocks() { return kReduceBlocks; }
 
 void splitk_reduce(const Launch& L, const cplx* P, int S, int64_t M, int64_t N, cplx alpha, cplx beta, cplx* C,
                    int64_t ldc) {
+  kbeg(L);
   k_splitk_reduce<<<grid_for(M * N), kThreads, 0, L.s>>>(P, S, M, N, alpha, beta, C, ldc);
   CCLR_CK(cudaGetLastError());
-  bump(L);
+  bump(L, "k_splitk_reduce");
 }
 
 void zgemm_splitk(const Launch& L, bool ta, bool tb, int64_t M, int64_t N, int64_t K, const cplx* A, int64_t lda,
@@ -884,12 +891,13 @@ void zgemm_splitk(const Launch& L, bool ta, bool tb, int64_t M, int64_t N, int64
   CCLR_REQUIRE((M + BM - 1) / BM <= 65535 && S <= 65535, CCLR_E_ARG, "zgemm_splitk: grid too large");
   dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM), (unsigned)S);
   const cplx one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
+  kbeg(L);
   if (!ta && !tb) k_zgemm<false, false><<<grid, 256, 0, L.s>>>(M, N, K, one, A, lda, B, ldb, zero, P, N, kchunk, M * N);
   else if (!ta && tb) k_zgemm<false, true><<<grid, 256, 0, L.s>>>(M, N, K, one, A, lda, B, ldb, zero, P, N, kchunk, M * N);
   else if (ta && !tb) k_zgemm<true, false><<<grid, 256, 0, L.s>>>(M, N, K, one, A, lda, B, ldb, zero, P, N, kchunk, M * N);
   else k_zgemm<true, true><<<grid, 256, 0, L.s>>>(M, N, K, one, A, lda, B, ldb, zero, P, N, kchunk, M * N);
   CCLR_CK(cudaGetLastError());
-  bump(L);
+  bump(L, "k_zgemm_splitk");
 }
 
 void pack2(const Launch& L, const Tensor& X, cplx* D, int64_t ldd, const int2* tab, cplx alpha, bool anti, bool acc) {
@@ -897,18 +905,20 @@ void pack2(const Launch& L, const Tensor& X, cplx* D, int64_t ldd, const int2* t
   const int64_t m = X.dim[1], Pm = m * (m - 1) / 2, R = X.dim[0];
   if (R * Pm == 0) return;
   cplx al = make_double2(alpha.x * X.scale, alpha.y * X.scale);
+  kbeg(L);
   k_pack2<<<grid_for(R * Pm), kThreads, 0, L.s>>>(X.p, X.str[0], X.str[1], X.str[2], D, ldd, R, Pm, tab, al, anti, acc);
   CCLR_CK(cudaGetLastError());
-  bump(L);
+  bump(L, "k_pack2");
 }
 
 void unpack2(const Launch& L, const cplx* D, int64_t ldd, const Tensor& X) {
   CCLR_REQUIRE(X.rank == 3 && X.dim[1] == X.dim[2], CCLR_E_ARG, "unpack2: X must be (R, m, m)");
   const int64_t n = X.numel();
   if (n == 0) return;
+  kbeg(L);
   k_unpack2<<<grid_for(n), kThreads, 0, L.s>>>(D, ldd, X.p, X.str[0], X.str[1], X.str[2], X.dim[0], (int)X.dim[1]);
   CCLR_CK(cudaGetLastError());
-  bump(L);
+  bump(L, "k_unpack2");
 }
 
 namespace {
@@ -958,14 +968,16 @@ void gram(const Launch& L, int64_t n, const Rows& X, const Rows& Y, bool herm, c
                            sizeof(void*) * (size_t)(a + b);
       const size_t red = sizeof(cplx) * 8 * RL * NYt * 32;
       const size_t smem = std::max(stage, red);
+      kbeg(L);
       if (L.fast32) launch_gram_tile<true>(L, nblk, smem, n, P.slice(i0, a), Q.slice(j0, b), herm, scratch);
       else launch_gram_tile<false>(L, nblk, smem, n, P.slice(i0, a), Q.slice(j0, b), herm, scratch);
       CCLR_CK(cudaGetLastError());
+      bump(L, "k_gram_skinny");
       cplx* o = swap ? out_dev + (int64_t)j0 * ny + i0 : out_dev + (int64_t)i0 * ny + j0;
+      kbeg(L);
       k_gram_reduce<<<(a * b + 255) / 256, 256, 0, L.s>>>(scratch, nblk, a, b, o, ny, swap, herm);
       CCLR_CK(cudaGetLastError());
-      bump(L);
-      bump(L);
+      bump(L, "k_gram_reduce");
     }
 }
 
@@ -995,6 +1007,7 @@ void vecmat(const Launch& L, int64_t n, const VecMat& a, double* scratch) {
   CCLR_REQUIRE(!a.norm2 || scratch, CCLR_E_ARG, "vecmat: norms without scratch");
   if (n <= 0) return;
   double* part = a.norm2 ? scratch : nullptr;
+  kbeg(L);
   if (L.fast32) {
     if (a.m == 1) launch_vecmat<true, 1>(L, n, a, part);
     else if (a.m <= 4) launch_vecmat<true, 4>(L, n, a, part);
@@ -1005,11 +1018,12 @@ void vecmat(const Launch& L, int64_t n, const VecMat& a, double* scratch) {
     else launch_vecmat<false, 16>(L, n, a, part);
   }
   CCLR_CK(cudaGetLastError());
-  bump(L);
+  bump(L, "k_vecmat");
   if (a.norm2) {
+    kbeg(L);
     k_sum_rows<<<a.m, kThreads, 0, L.s>>>(part, kVecMatBlocks, a.norm2);
     CCLR_CK(cudaGetLastError());
-    bump(L);
+    bump(L, "k_sum_rows");
   }
 }
 
@@ -1087,18 +1101,20 @@ void permute(const Launch& L, const Tensor& src, const Tensor& dst, cplx alpha, 
   for (int k = 0; k < a.rank; ++k)
     if (a.dim[k] < (int64_t(1) << 31)) gm_magic(a.dim[k], a.mul[k], a.shr[k]);
   cplx al = make_double2(alpha.x * src.scale, alpha.y * src.scale);
+  kbeg(L);
   if (al.y == 0.0 && (al.x == 1.0 || al.x == -1.0)) launch_permute<0>(L, a, src.p, dst.p, n, al, src.conj, accumulate);
   else if (al.y == 0.0) launch_permute<1>(L, a, src.p, dst.p, n, al, src.conj, accumulate);
   else launch_permute<2>(L, a, src.p, dst.p, n, al, src.conj, accumulate);
   CCLR_CK(cudaGetLastError());
-  bump(L);
+  bump(L, "k_permute");
 }
 
 void fill_zero(const Launch& L, cplx* p, int64_t n) {
   if (n <= 0) return;
+  kbeg(L);
   k_fill_zero<<<grid_for(n), kThreads, 0, L.s>>>(p, n);
   CCLR_CK(cudaGetLastError());
-  bump(L);
+  bump(L, "k_fill_zero");
 }
 
 void zgemm(const Launch& L, bool ta, bool tb, int64_t M, int64_t N, int64_t K, cplx alpha, const cplx* A,
@@ -1119,12 +1135,13 @@ void zgemm(const Launch& L, bool ta, bool tb, int64_t M, int64_t N, int64_t K, c
     return;
   }
   dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM));
+  kbeg(L);
   if (!ta && !tb) k_zgemm<false, false><<<grid, 256, 0, L.s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, K, 0);
   else if (!ta && tb) k_zgemm<false, true><<<grid, 256, 0, L.s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, K, 0);
   else if (ta && !tb) k_zgemm<true, false><<<grid, 256, 0, L.s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, K, 0);
   else k_zgemm<true, true><<<grid, 256, 0, L.s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, K, 0);
   CCLR_CK(cudaGetLastError());
-  bump(L);
+  bump(L, "k_zgemm");
 }
 
 // Pair tables are uploaded once per Hamiltonian; kept here as a per-process cache keyed by size.
@@ -1139,9 +1156,10 @@ void pack_doubles_impl(const Launch& L, const Tensor& X, cplx* D, int64_t nvec, 
   const int64_t n = nvec * Po * Pv;
   if (n == 0) return;
   cplx al = make_double2(alpha.x * X.scale, alpha.y * X.scale);
+  kbeg(L);
   k_pack<<<grid_for(n), kThreads, 0, L.s>>>(X.p, s, D, nvec, Po, Pv, po, pv, al, anti, accumulate);
   CCLR_CK(cudaGetLastError());
-  bump(L);
+  bump(L, "k_pack");
 }
 
 void unpack_doubles(const Launch& L, const cplx* D, int64_t ld_vec, const Tensor& X, int o, int v) {
@@ -1160,50 +1178,57 @@ void unpack_doubles(const Launch& L, const cplx* D, int64_t ld_vec, const Tensor
   const int64_t n = X.numel();
   if (n == 0) return;
   const int64_t Pv = (int64_t)v * (v - 1) / 2;
+  kbeg(L);
   k_unpack<<<grid_for(n), kThreads, 0, L.s>>>(D, ld_vec, Pv, u, X.p, n);
   CCLR_CK(cudaGetLastError());
-  bump(L);
+  bump(L, "k_unpack");
 }
 
 void axpy(const Launch& L, int64_t n, cplx a, const cplx* x, cplx* y) {
   if (n <= 0) return;
+  kbeg(L);
   k_axpy<<<grid_for(n), kThreads, 0, L.s>>>(n, a, x, y);
   CCLR_CK(cudaGetLastError());
-  bump(L);
+  bump(L, "k_axpy");
 }
 
 void scale_vec(const Launch& L, int64_t n, cplx a, cplx* x) {
   if (n <= 0) return;
+  kbeg(L);
   k_scale<<<grid_for(n), kThreads, 0, L.s>>>(n, a, x);
   CCLR_CK(cudaGetLastError());
-  bump(L);
+  bump(L, "k_scale");
 }
 
 void copy_vec(const Launch& L, int64_t n, const cplx* x, cplx* y) {
   if (n <= 0) return;
+  kbeg(L);
   k_copy<<<grid_for(n), kThreads, 0, L.s>>>(n, x, y);
   CCLR_CK(cudaGetLastError());
-  bump(L);
+  bump(L, "k_copy");
 }
 
 void div_shift(const Launch& L, int64_t n, const cplx* x, const double* D, cplx z, cplx a, cplx* y) {
   if (n <= 0) return;
+  kbeg(L);
   k_div_shift<<<grid_for(n), kThreads, 0, L.s>>>(n, x, D, z, a, y);
   CCLR_CK(cudaGetLastError());
-  bump(L);
+  bump(L, "k_div_shift");
 }
 
 void dots(const Launch& L, int64_t n, int nvec, const cplx* x, int64_t ldx, const cplx* y, int64_t ldy, bool herm,
           cplx* out_dev, cplx* scratch) {
   if (nvec <= 0) return;
   dim3 g(kReduceBlocks, nvec);
+  kbeg(L);
   if (L.fast32) k_dots_partial32<<<g, kThreads, 0, L.s>>>(n, x, ldx, y, ldy, herm, scratch);
   else k_dots_partial<<<g, kThreads, 0, L.s>>>(n, x, ldx, y, ldy, herm, scratch);
   CCLR_CK(cudaGetLastError());
+  bump(L, "k_dots");
+  kbeg(L);
   k_sum_partials<<<nvec, kThreads, 0, L.s>>>(scratch, kReduceBlocks, out_dev);
   CCLR_CK(cudaGetLastError());
-  bump(L);
-  bump(L);
+  bump(L, "k_sum_partials");
 }
 
 void proj(const Launch& L, int64_t n, int nb, const cplx* B, int64_t ldb, const cplx* y, cplx* out_dev, cplx* scratch) {

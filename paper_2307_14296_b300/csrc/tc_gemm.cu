@@ -34,7 +34,7 @@ constexpr int STAGES = 3;
 constexpr int A_PLANE = BM * BK * 2;           // bytes of one BF16 plane tile
 constexpr int B_PLANE = BN * BK * 2;
 constexpr int STAGE_BYTES = 2 * A_PLANE + 2 * B_PLANE;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/ + BN * 8 /*row offsets*/;
 constexpr int TMEM_COLS = 2 * BN;              // Cr | Ci
 constexpr int MAX_PAIRS = 6;
 
@@ -42,6 +42,28 @@ struct Pairs {
   int n;
   int sa[MAX_PAIRS], sb[MAX_PAIRS];
 };
+
+// Strided output: the element (m, n) of the product lives at C + moff(m) + noff(n), each offset a
+// row-major decomposition of the index over up to four axes (extents, strides, and the
+// Granlund-Montgomery multipliers of the extents: q = (umulhi(i, mul) + i) >> shr).
+struct OutMap {
+  int nm = 0, nn = 0;
+  int64_t mdim[4] = {}, mstr[4] = {}, ndim[4] = {}, nstr[4] = {};
+  uint32_t mmul[4] = {}, nmul[4] = {};
+  int mshr[4] = {}, nshr[4] = {};
+};
+__device__ __forceinline__ int64_t out_off(uint32_t i, int na, const int64_t* dim, const int64_t* str,
+                                           const uint32_t* mul, const int* shr) {
+  int64_t off = 0;
+#pragma unroll
+  for (int a = 3; a >= 0; --a) {
+    if (a >= na) continue;
+    const uint32_t q = (uint32_t)(((uint64_t)__umulhi(i, mul[a]) + i) >> shr[a]);
+    off += (int64_t)(i - q * (uint32_t)dim[a]) * str[a];
+    i = q;
+  }
+  return off;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -113,10 +135,20 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// IEEE 754 binary32 -> binary64 on the integer pipe (exact for normal inputs; binary32
+// subnormals flush to zero; infinities and NaN are kept)
+__device__ __forceinline__ double epi_f2d(float x) {
+  const uint32_t u = __float_as_uint(x), sign = u & 0x80000000u, e = (u >> 23) & 0xffu;
+  uint32_t hi = (((u & 0x7fffffffu) >> 3) + 0x38000000u) | sign, lo = u << 29;
+  if (e == 0u) { hi = sign; lo = 0u; }
+  if (e == 0xffu) { hi = sign | 0x7ff00000u | ((u & 0x7fffffu) ? 0x80000u : 0u); lo = 0u; }
+  return __longlong_as_double((long long)(((uint64_t)hi << 32) | lo));
+}
+
 __global__ void __launch_bounds__(128, 1)
     k_tc_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int n_rows, int m_rows,
                int kblocks, int kb_per, Pairs pairs, double2 alpha, double2 beta, double2* __restrict__ C, int64_t ldc,
-               int64_t cz, int* __restrict__ err, int ytile0) {
+               int64_t cz, int* __restrict__ err, int ytile0, const OutMap om, bool strided) {
   // split-K: blockIdx.z owns k-blocks [z*kb_per, min(kblocks, (z+1)*kb_per)) and writes C + z*cz;
   // ytile0 offsets the n-tiles of this launch (tall operands are launched in row chunks)
   const int kb0 = blockIdx.z * kb_per;
@@ -129,6 +161,7 @@ __global__ void __launch_bounds__(128, 1)
   uint64_t* done = empty + STAGES;
   uint32_t* tmem_slot = (uint32_t*)(done + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+  int64_t* moff = (int64_t*)(smem + STAGES * STAGE_BYTES + 256);   // strided output: offsets of this tile's m
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -138,6 +171,10 @@ __global__ void __launch_bounds__(128, 1)
     mbar_init(done, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (strided) {   // offsets of this tile's 128 output rows (read by every thread in the epilogue)
+    const int m = blockIdx.x * BN + threadIdx.x;
+    moff[threadIdx.x] = m < m_rows ? out_off((uint32_t)m, om.nm, om.mdim, om.mstr, om.mmul, om.mshr) : 0;
   }
   if (warp == 2) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
@@ -199,8 +236,14 @@ __global__ void __launch_bounds__(128, 1)
   if (!ok && lane == 0) atomicExch(err, 3);
   fence_after();
   const int n = n0 + warp * 32 + lane;
+  const int64_t noff = (strided && n < n_rows) ? out_off((uint32_t)n, om.nn, om.ndim, om.nstr, om.nmul, om.nshr) : 0;
   const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+  // The accumulators are FP32: alpha is applied in FP32 and the result widened on the integer
+  // pipe (FP64 arithmetic and FP32 <-> FP64 cvt issue on the FP64 pipe, ~1/64 of the FP32 rate on
+  // sm_103); only the beta term (1 or 0 in every caller but the general entry) uses FP64.
   const bool use_beta = (beta.x != 0.0 || beta.y != 0.0);
+  const bool beta_one = (beta.x == 1.0 && beta.y == 0.0);
+  const float ar = (float)alpha.x, ai = (float)alpha.y;
   if (ok) {
 #pragma unroll 1
     for (int c0 = 0; c0 < BN; c0 += 32) {
@@ -208,19 +251,37 @@ __global__ void __launch_bounds__(128, 1)
       tmem_ld32(tmem + lane_base + c0, rr);
       tmem_ld32(tmem + lane_base + BN + c0, ri);
       if (n < n_rows) {
-#pragma unroll 4
-        for (int j = 0; j < 32; ++j) {
-          const int m = m0 + c0 + j;
-          if (m >= m_rows) break;
-          const double xr = (double)__uint_as_float(rr[j]), xi = (double)__uint_as_float(ri[j]);
-          double2 v = make_double2(alpha.x * xr - alpha.y * xi, alpha.x * xi + alpha.y * xr);
-          double2* cp = C + (int64_t)m * ldc + n;
+        // 16 columns at a time: the beta operands are all loaded before any is used, so that a
+        // warp has 16 loads in flight instead of one
+#pragma unroll 1
+        for (int h = 0; h < 32; h += 16) {
+          double2 old[16];
           if (use_beta) {
-            const double2 o = *cp;
-            v.x += beta.x * o.x - beta.y * o.y;
-            v.y += beta.x * o.y + beta.y * o.x;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const int m = m0 + c0 + h + j;
+              if (m < m_rows) old[j] = *(strided ? C + moff[c0 + h + j] + noff : C + (int64_t)m * ldc + n);
+            }
           }
-          *cp = v;
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int m = m0 + c0 + h + j;
+            if (m < m_rows) {
+              const float xr = __uint_as_float(rr[h + j]), xi = __uint_as_float(ri[h + j]);
+              double2 v = make_double2(epi_f2d(ar * xr - ai * xi), epi_f2d(ar * xi + ai * xr));
+              if (use_beta) {
+                const double2 o = old[j];
+                if (beta_one) {
+                  v.x += o.x;
+                  v.y += o.y;
+                } else {
+                  v.x += beta.x * o.x - beta.y * o.y;
+                  v.y += beta.x * o.y + beta.y * o.x;
+                }
+              }
+              *(strided ? C + moff[c0 + h + j] + noff : C + (int64_t)m * ldc + n) = v;
+            }
+          }
         }
       }
     }
@@ -439,8 +500,10 @@ void make_slices(Ctx& c, const Tensor& v, int nr, int nsl, Slices& s, __nv_bfloa
   s.Kpad = (K + tc::BK - 1) / tc::BK * tc::BK;
   s.nsl = nsl;
   s.p = dst;
+  c.kt.begin(c.stream);
   launch_split(v, nr, rows, K, s.Kpad, nsl, dst, c.stream);
   CCLR_CK(cudaGetLastError());
+  c.kt.end(c.stream, "k_split_view");
   ++c.launches;
   s.tm = make_map(dst, rows, s.Kpad, 2 * nsl, 128);
 }
@@ -471,17 +534,17 @@ Slices get_slices(Ctx& c, const Tensor& v, int nr, int nsl) {
   const int64_t Kpad = (K + tc::BK - 1) / tc::BK * tc::BK;
   const size_t bytes = sizeof(__nv_bfloat16) * 2 * nsl * (size_t)(elems / K) * (size_t)Kpad;
   Slices s;
-  static const double cap_gb = std::getenv("CCLR_TC_CACHE_GB") ? atof(std::getenv("CCLR_TC_CACHE_GB")) : 16.0;
-  size_t cached = 0;
-  for (auto& kv : cache()) cached += sizeof(__nv_bfloat16) * 2 * kv.second.s.nsl * kv.second.s.rows * kv.second.s.Kpad;
-  if (is_persistent(c, v.p) && (double)(cached + bytes) <= cap_gb * (double)(1ull << 30)) {
+  static const double cap_gb = std::getenv("CCLR_TC_CACHE_GB") ? atof(std::getenv("CCLR_TC_CACHE_GB")) : 32.0;
+  if (is_persistent(c, v.p)) {
     std::string key = std::to_string((uintptr_t)v.p) + "|" + std::to_string(nr) + "|" + std::to_string(nsl) + "|" +
                       std::to_string((int)v.conj);
     for (int i = 0; i < v.rank; ++i) key += "|" + std::to_string(v.dim[i]) + ":" + std::to_string(v.str[i]);
     auto it = cache().find(key);
     if (it != cache().end()) return it->second.s;
+    size_t cached = 0;
+    for (auto& kv : cache()) cached += sizeof(__nv_bfloat16) * 2 * kv.second.s.nsl * kv.second.s.rows * kv.second.s.Kpad;
     __nv_bfloat16* dst = nullptr;
-    if (cudaMalloc((void**)&dst, bytes) == cudaSuccess) {
+    if ((double)(cached + bytes) <= cap_gb * (double)(1ull << 30) && cudaMalloc((void**)&dst, bytes) == cudaSuccess) {
       make_slices(c, v, nr, nsl, s, dst);
       cache()[key] = CacheEntry{s, data_generation()};
       return s;
@@ -515,10 +578,11 @@ uint64_t& data_generation() {
 
 uint64_t& hbar_generation() { return data_generation(); }
 
-void tc_release_cache() {
+void tc_release_cache() {   // cudaFree waits for the kernels still reading the slices
   for (auto& kv : cache()) cudaFree(kv.second.s.p);
   cache().clear();
 }
+void tc_release_cache_for(Ctx&) { tc_release_cache(); }
 
 int tc_slices(int precision) { return precision == CCLR_TC_BF16X3 ? 2 : 3; }
 
@@ -532,8 +596,50 @@ bool tc_eligible(int64_t M, int64_t N, int64_t K) {
 
 // C[m*ldc + n] = alpha sum_k vm[m,k] vn[n,k] + beta C, vm / vn views whose first nr axes are the
 // rows (m resp. n) and whose remaining axes are K (same order in both).
+// split-K slices for an output of M x N with K (1 = none): when the output has fewer tiles than
+// SMs, each slice >= 4 k-blocks
+void tc_split_plan(int64_t M, int64_t N, int64_t K, int& S, int& kb_per) {
+  const int kblocks = (int)((K + tc::BK - 1) / tc::BK);
+  const int64_t tiles = ((M + tc::BN - 1) / tc::BN) * ((N + tc::BM - 1) / tc::BM);
+  S = 1;
+  kb_per = kblocks;
+  if (tiles < 148 && kblocks >= 8) {
+    S = (int)std::min<int64_t>((148 + tiles - 1) / tiles, kblocks / 4);
+    kb_per = (kblocks + S - 1) / S;
+    S = (kblocks + kb_per - 1) / kb_per;   // no empty slice
+  }
+}
+int tc_splits(int64_t M, int64_t N, int64_t K) {
+  int S, kb;
+  tc_split_plan(M, N, K, S, kb);
+  return S;
+}
+
+namespace {
+tc::OutMap out_map(const OutAxes& a) {
+  tc::OutMap m;
+  auto fill = [](int n, const int64_t* dim, const int64_t* str, int64_t* d, int64_t* st, uint32_t* mul, int* shr) {
+    for (int i = 0; i < n; ++i) {
+      CCLR_REQUIRE(dim[i] >= 1 && dim[i] < (int64_t(1) << 31), CCLR_E_ARG, "tc_gemm: output axis too large");
+      d[i] = dim[i];
+      st[i] = str[i];
+      int l = 0;
+      while ((int64_t(1) << l) < dim[i]) ++l;
+      shr[i] = l;
+      mul[i] = (uint32_t)(((unsigned __int128)1 << 32) * (((uint64_t)1 << l) - (uint64_t)dim[i]) / (uint64_t)dim[i] + 1);
+    }
+  };
+  CCLR_REQUIRE(a.nm >= 1 && a.nm <= 4 && a.nn >= 1 && a.nn <= 4, CCLR_E_ARG, "tc_gemm: output map rank");
+  m.nm = a.nm;
+  m.nn = a.nn;
+  fill(a.nm, a.mdim, a.mstr, m.mdim, m.mstr, m.mmul, m.mshr);
+  fill(a.nn, a.ndim, a.nstr, m.ndim, m.nstr, m.nmul, m.nshr);
+  return m;
+}
+}  // namespace
+
 void tc_gemm_views(Ctx& c, const Tensor& vm, int nrm, const Tensor& vn, int nrn, cplx alpha, cplx beta, cplx* C,
-                   int64_t ldc) {
+                   int64_t ldc, const OutAxes* oa) {
   const int nsl = tc_slices(c.opt.precision);
   const tc::Pairs pairs = pairs_for(nsl);
   Scope sc(c.ws);
@@ -551,14 +657,11 @@ void tc_gemm_views(Ctx& c, const Tensor& vm, int nrm, const Tensor& vn, int nrn,
     CCLR_CK(cudaMemsetAsync(c.tc_err, 0, sizeof(int), c.stream));
   }
   const int kblocks = (int)(sn.Kpad / tc::BK);
-  const int64_t tiles = ((M + tc::BN - 1) / tc::BN) * ((N + tc::BM - 1) / tc::BM);
-  // split-K when the output has fewer tiles than SMs: each slice >= 4 k-blocks
   int S = 1, kb_per = kblocks;
-  if (tiles < 148 && kblocks >= 8) {
-    S = (int)std::min<int64_t>((148 + tiles - 1) / tiles, kblocks / 4);
-    kb_per = (kblocks + S - 1) / S;
-    S = (kblocks + kb_per - 1) / kb_per;   // no empty slice
-  }
+  tc_split_plan(M, N, sn.Kpad, S, kb_per);
+  CCLR_REQUIRE(!oa || S == 1, CCLR_E_ARG, "tc_gemm: strided output with split-K");
+  const tc::OutMap om = oa ? out_map(*oa) : tc::OutMap();
+  const bool strided = oa != nullptr;
   cplx* P = nullptr;
   if (S > 1) P = c.ws.cplxs((int64_t)S * M * N);
   const int64_t ytiles = (N + tc::BM - 1) / tc::BM, xtiles = (M + tc::BN - 1) / tc::BN;
@@ -568,17 +671,19 @@ void tc_gemm_views(Ctx& c, const Tensor& vm, int nrm, const Tensor& vn, int nrn,
   if (e0) CCLR_CK(cudaEventRecord(e0, c.stream));
   for (int64_t y0 = 0; y0 < ytiles; y0 += 65535) {   // grid.y limit: chunks of n-tiles
     dim3 grid((unsigned)xtiles, (unsigned)std::min<int64_t>(65535, ytiles - y0), (unsigned)S);
+    c.kt.begin(c.stream);
     if (S > 1)
       tc::k_tc_zgemm<<<grid, 128, tc::SMEM_BYTES, c.stream>>>(sn.tm, sm.tm, (int)N, (int)M, kblocks, kb_per, pairs,
                                                               make_double2(1.0, 0.0), make_double2(0.0, 0.0), P, N,
-                                                              M * N, c.tc_err, (int)y0);
+                                                              M * N, c.tc_err, (int)y0, om, false);
     else
       tc::k_tc_zgemm<<<grid, 128, tc::SMEM_BYTES, c.stream>>>(sn.tm, sm.tm, (int)N, (int)M, kblocks, kb_per, pairs,
-                                                              alpha, beta, C, ldc, 0, c.tc_err, (int)y0);
+                                                              alpha, beta, C, ldc, 0, c.tc_err, (int)y0, om, strided);
     const cudaError_t le = cudaGetLastError();
     CCLR_REQUIRE(le == cudaSuccess, CCLR_E_CUDA,
                  std::string("tensor-core GEMM launch failed (") + cudaGetErrorString(le) + ") M=" + std::to_string(M) +
                      " N=" + std::to_string(N) + " K=" + std::to_string(sn.K) + " S=" + std::to_string(S));
+    c.kt.end(c.stream, "k_tc_zgemm");
   }
   if (e1) {
     CCLR_CK(cudaEventRecord(e1, c.stream));
@@ -665,10 +770,10 @@ int tc_raw_gemm_nt(int precision, int64_t M, int64_t N, int64_t K, const cplx* A
     dim3 grid((unsigned)xtiles, (unsigned)std::min<int64_t>(65535, ytiles - y0), (unsigned)p.S);
     if (p.S > 1)
       tc::k_tc_zgemm<<<grid, 128, tc::SMEM_BYTES, stream>>>(tn, tm, (int)N, (int)M, p.kblocks, p.kb_per, pairs, one,
-                                                            zero, P, N, M * N, err, (int)y0);
+                                                            zero, P, N, M * N, err, (int)y0, tc::OutMap(), false);
     else
       tc::k_tc_zgemm<<<grid, 128, tc::SMEM_BYTES, stream>>>(tn, tm, (int)N, (int)M, p.kblocks, p.kb_per, pairs, one,
-                                                            zero, C, N, 0, err, (int)y0);
+                                                            zero, C, N, 0, err, (int)y0, tc::OutMap(), false);
     CCLR_CK(cudaGetLastError());
   }
   if (p.S > 1) {
