@@ -11,11 +11,12 @@
 // product uses four real MMAs per k-step into two accumulators, the minus sign of Ai*Bi coming
 // from the instruction descriptor's negate-A bit, so no operand is duplicated in memory.
 //
-// CTA tile: 128 rows of the "A-side" MMA operand (= 128 consecutive n, one TMEM lane each) x BN
-// rows of the "B-side" operand (= BN consecutive m, TMEM columns).  Warp 0 issues TMA loads into
-// a STAGES-deep shared-memory ring, warp 1 issues tcgen05.mma, then all four warps drain TMEM
-// and write C with stores that are contiguous along n.  Every mbarrier wait is bounded: on
-// expiry the kernel records an error code, stops issuing work, releases TMEM and returns.
+// Tile: 128 rows of the "A-side" MMA operand (= 128 consecutive n, one TMEM lane each) x BN rows
+// of the "B-side" operand (= BN consecutive m, TMEM columns).  The kernel is persistent (one CTA
+// per SM) and warp-specialised: a TMA producer, a single-thread MMA issuer and four epilogue warps
+// that drain one of two TMEM accumulators while the next tile accumulates in the other; stores
+// are contiguous along n.  Every mbarrier wait is bounded: on expiry the kernel records an error
+// code, stops issuing work, releases TMEM and returns.
 #include "ctx.h"
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -34,7 +35,7 @@ constexpr int STAGES = 3;
 constexpr int A_PLANE = BM * BK * 2;           // bytes of one BF16 plane tile
 constexpr int B_PLANE = BN * BK * 2;
 constexpr int STAGE_BYTES = 2 * A_PLANE + 2 * B_PLANE;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/ + BN * 8 /*row offsets*/;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/ + 2 * BN * 8 /*row offsets*/;
 constexpr int TMEM_COLS = 2 * BN;              // Cr | Ci
 constexpr int MAX_PAIRS = 6;
 
@@ -145,152 +146,216 @@ __device__ __forceinline__ double epi_f2d(float x) {
   return __longlong_as_double((long long)(((uint64_t)hi << 32) | lo));
 }
 
-__global__ void __launch_bounds__(128, 1)
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+// OR of q over the 128 epilogue threads (named barrier 1; all of them must call it)
+__device__ __forceinline__ bool group_any(bool q) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 q, %1, 0;\n bar.red.or.pred p, 1, 128, q;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)q)
+      : "memory");
+  return r != 0;
+}
+
+// Persistent, warp-specialised kernel: one CTA per SM walks the tiles t = blockIdx.x + i gridDim.x
+// (tile = (m-tile fastest, n-tile, split-K slice z)).  Warp 0 lane 0 streams operand tiles into a
+// STAGES-deep shared-memory ring with TMA, warp 1 lane 0 issues tcgen05.mma into one of two TMEM
+// accumulators (Cr | Ci, 2 x 256 columns), and warps 2..5 drain the other accumulator to C, so a
+// tile's epilogue overlaps the next tile's MMAs.  Every mbarrier wait is bounded; on expiry the
+// kernel records an error code, stops issuing work, waits (bounded) for its MMAs, frees TMEM and
+// returns.
+__global__ void __launch_bounds__(192, 1)
     k_tc_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int n_rows, int m_rows,
                int kblocks, int kb_per, Pairs pairs, double2 alpha, double2 beta, double2* __restrict__ C, int64_t ldc,
-               int64_t cz, int* __restrict__ err, int ytile0, const OutMap om, bool strided) {
-  // split-K: blockIdx.z owns k-blocks [z*kb_per, min(kblocks, (z+1)*kb_per)) and writes C + z*cz;
-  // ytile0 offsets the n-tiles of this launch (tall operands are launched in row chunks)
-  const int kb0 = blockIdx.z * kb_per;
-  const int kb1 = min(kblocks, kb0 + kb_per);
-  C += (int64_t)blockIdx.z * cz;
+               int64_t cz, int* __restrict__ err, int xtiles, int ytiles, int nsplit, const OutMap om, bool strided) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
   uint64_t* empty = full + STAGES;
-  uint64_t* done = empty + STAGES;
+  uint64_t* tfull = empty + STAGES;    // accumulator b holds a finished tile (MMA commit)
+  uint64_t* tempty = tfull + 2;        // accumulator b drained (128 epilogue threads)
+  uint64_t* done = tempty + 2;         // every MMA of this CTA has completed
   uint32_t* tmem_slot = (uint32_t*)(done + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
-  int64_t* moff = (int64_t*)(smem + STAGES * STAGE_BYTES + 256);   // strided output: offsets of this tile's m
+  int64_t* moff = (int64_t*)(smem + STAGES * STAGE_BYTES + 256);   // [2][BN] strided row offsets
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 128);
+    }
     mbar_init(done, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (strided) {   // offsets of this tile's 128 output rows (read by every thread in the epilogue)
-    const int m = blockIdx.x * BN + threadIdx.x;
-    moff[threadIdx.x] = m < m_rows ? out_off((uint32_t)m, om.nm, om.mdim, om.mstr, om.mmul, om.mshr) : 0;
-  }
   if (warp == 2) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(TMEM_COLS));
+                 "r"(2 * TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   fence_before();
   __syncthreads();
   fence_after();
   const uint32_t tmem = *tmem_slot;
-  const int n0 = (ytile0 + (int)blockIdx.y) * BM;  // rows of the A-side operand (C columns)
-  const int m0 = blockIdx.x * BN;  // rows of the B-side operand (C rows)
-  const int iters = (kb1 - kb0) * pairs.n;   // >= 1: the host never creates an empty slice
+  const int xy = xtiles * ytiles;
+  const int ntiles = xy * nsplit;
 
-  if (warp == 0 && lane == 0) {
-    // ---------------- TMA producer
-    for (int it = 0; it < iters; ++it) {
-      const int s = it % STAGES;
-      const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-      if (!mbar_wait(&empty[s], ph ^ 1u)) { atomicExch(err, 1); *abort_flag = 1; break; }
-      if (*abort_flag) break;
-      const int kb = kb0 + it / pairs.n, p = it % pairs.n;
-      uint8_t* st = smem + s * STAGE_BYTES;
-      mbar_expect_tx(&full[s], STAGE_BYTES);
-      tma_load_3d(st, &tmA, kb * BK, n0, 2 * pairs.sa[p] + 0, &full[s]);
-      tma_load_3d(st + A_PLANE, &tmA, kb * BK, n0, 2 * pairs.sa[p] + 1, &full[s]);
-      tma_load_3d(st + 2 * A_PLANE, &tmB, kb * BK, m0, 2 * pairs.sb[p] + 0, &full[s]);
-      tma_load_3d(st + 2 * A_PLANE + B_PLANE, &tmB, kb * BK, m0, 2 * pairs.sb[p] + 1, &full[s]);
-    }
-  } else if (warp == 1 && lane == 0) {
-    // ---------------- MMA issuer (single thread)
-    constexpr uint32_t ID = idesc_bf16(BM, BN, false), IDN = idesc_bf16(BM, BN, true);
-    const uint32_t cr = tmem, ci = tmem + BN;
-    for (int it = 0; it < iters; ++it) {
-      const int s = it % STAGES;
-      const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-      if (!mbar_wait(&full[s], ph)) { atomicExch(err, 2); *abort_flag = 1; break; }
-      fence_after();
-      const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
-      const uint32_t ar = base, ai = base + A_PLANE, br = base + 2 * A_PLANE, bi = br + B_PLANE;
-#pragma unroll
-      for (int ks = 0; ks < BK / 16; ++ks) {
-        const uint32_t off = ks * 32;  // 16 BF16 = 32 bytes along K inside the swizzle row
-        const uint64_t dar = desc_sw128(ar + off), dai = desc_sw128(ai + off);
-        const uint64_t dbr = desc_sw128(br + off), dbi = desc_sw128(bi + off);
-        const uint32_t first = (it == 0 && ks == 0) ? 0u : 1u;
-        mma_bf16(cr, dar, dbr, ID, first);
-        mma_bf16(cr, dai, dbi, IDN, 1u);
-        mma_bf16(ci, dar, dbi, ID, first);
-        mma_bf16(ci, dai, dbr, ID, 1u);
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer: the ring runs on across tile boundaries
+      int g = 0;
+      for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
+        const int z = t / xy, r = t - z * xy, y = r / xtiles, x = r - y * xtiles;
+        const int kb0 = z * kb_per, kb1 = min(kblocks, kb0 + kb_per);
+        const int n0 = y * BM, m0 = x * BN;
+        const int iters = (kb1 - kb0) * pairs.n;
+        for (int it = 0; it < iters; ++it, ++g) {
+          const int s = g % STAGES;
+          const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
+          if (!mbar_wait(&empty[s], ph ^ 1u)) { atomicExch(err, 1); *abort_flag = 1; break; }
+          if (*abort_flag) break;
+          const int kb = kb0 + it / pairs.n, p = it % pairs.n;
+          uint8_t* st = smem + s * STAGE_BYTES;
+          mbar_expect_tx(&full[s], STAGE_BYTES);
+          tma_load_3d(st, &tmA, kb * BK, n0, 2 * pairs.sa[p] + 0, &full[s]);
+          tma_load_3d(st + A_PLANE, &tmA, kb * BK, n0, 2 * pairs.sa[p] + 1, &full[s]);
+          tma_load_3d(st + 2 * A_PLANE, &tmB, kb * BK, m0, 2 * pairs.sb[p] + 0, &full[s]);
+          tma_load_3d(st + 2 * A_PLANE + B_PLANE, &tmB, kb * BK, m0, 2 * pairs.sb[p] + 1, &full[s]);
+        }
       }
-      mma_commit(&empty[s]);
     }
-    mma_commit(done);
-  }
-  __syncwarp();
-  // ---------------- epilogue: TMEM -> registers -> C (contiguous along n across lanes)
-  const bool ok = mbar_wait(done, 0);
-  if (!ok && lane == 0) atomicExch(err, 3);
-  fence_after();
-  const int n = n0 + warp * 32 + lane;
-  const int64_t noff = (strided && n < n_rows) ? out_off((uint32_t)n, om.nn, om.ndim, om.nstr, om.nmul, om.nshr) : 0;
-  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-  // The accumulators are FP32: alpha is applied in FP32 and the result widened on the integer
-  // pipe (FP64 arithmetic and FP32 <-> FP64 cvt issue on the FP64 pipe, ~1/64 of the FP32 rate on
-  // sm_103); only the beta term (1 or 0 in every caller but the general entry) uses FP64.
-  const bool use_beta = (beta.x != 0.0 || beta.y != 0.0);
-  const bool beta_one = (beta.x == 1.0 && beta.y == 0.0);
-  const float ar = (float)alpha.x, ai = (float)alpha.y;
-  if (ok) {
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer (single thread)
+      constexpr uint32_t ID = idesc_bf16(BM, BN, false), IDN = idesc_bf16(BM, BN, true);
+      int g = 0, tl = 0;
+      for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x, ++tl) {
+        const int z = t / xy;
+        const int kb0 = z * kb_per, kb1 = min(kblocks, kb0 + kb_per);
+        const int iters = (kb1 - kb0) * pairs.n;
+        const int b = tl & 1;
+        if (!mbar_wait(&tempty[b], (((uint32_t)tl >> 1) & 1u) ^ 1u)) { atomicExch(err, 4); *abort_flag = 1; break; }
+        fence_after();
+        const uint32_t cr = tmem + b * TMEM_COLS, ci = cr + BN;
+        bool ok = true;
+        for (int it = 0; it < iters; ++it, ++g) {
+          const int s = g % STAGES;
+          const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
+          if (!mbar_wait(&full[s], ph)) { atomicExch(err, 2); *abort_flag = 1; ok = false; break; }
+          fence_after();
+          const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
+          const uint32_t ar = base, ai = base + A_PLANE, br = base + 2 * A_PLANE, bi = br + B_PLANE;
+#pragma unroll
+          for (int ks = 0; ks < BK / 16; ++ks) {
+            const uint32_t off = ks * 32;  // 16 BF16 = 32 bytes along K inside the swizzle row
+            const uint64_t dar = desc_sw128(ar + off), dai = desc_sw128(ai + off);
+            const uint64_t dbr = desc_sw128(br + off), dbi = desc_sw128(bi + off);
+            const uint32_t first = (it == 0 && ks == 0) ? 0u : 1u;
+            mma_bf16(cr, dar, dbr, ID, first);
+            mma_bf16(cr, dai, dbi, IDN, 1u);
+            mma_bf16(ci, dar, dbi, ID, first);
+            mma_bf16(ci, dai, dbr, ID, 1u);
+          }
+          mma_commit(&empty[s]);
+        }
+        if (!ok) break;
+        mma_commit(&tfull[b]);
+      }
+      mma_commit(done);
+    }
+  } else {
+    // ---------------- epilogue warps 2..5: TMEM lanes 32 (warp % 4) .. +32
+    const int et = threadIdx.x - 64;                 // 0..127
+    const int lg = warp & 3;                         // TMEM lane quarter of this warp
+    const uint32_t lane_base = (uint32_t)(lg * 32) << 16;
+    // The accumulators are FP32: alpha is applied in FP32 and the result widened on the integer
+    // pipe (FP64 arithmetic and FP32 <-> FP64 cvt issue on the FP64 pipe, ~1/64 of the FP32 rate
+    // on sm_103); only the beta term uses FP64.
+    const bool use_beta = (beta.x != 0.0 || beta.y != 0.0);
+    const bool beta_one = (beta.x == 1.0 && beta.y == 0.0);
+    const float ar = (float)alpha.x, ai = (float)alpha.y;
+    // Control flow stays uniform across the 128 epilogue threads: every exit decision is taken
+    // through a barrier reduction over named barrier 1, so no thread is left waiting in it.
+    int tl = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++tl) {
+      const int z = t / xy, r = t - z * xy, y = r / xtiles, x = r - y * xtiles;
+      const int n0 = y * BM, m0 = x * BN;
+      const int b = tl & 1;
+      double2* Cz = C + (int64_t)z * cz;
+      int64_t* mo = moff + b * BN;
+      if (strided) {
+        const int m = m0 + et;
+        mo[et] = m < m_rows ? out_off((uint32_t)m, om.nm, om.mdim, om.mstr, om.mmul, om.mshr) : 0;
+      }
+      if (group_any(*abort_flag != 0)) break;   // also publishes this tile's offsets to the group
+      const int n = n0 + lg * 32 + lane;
+      const int64_t noff = (strided && n < n_rows) ? out_off((uint32_t)n, om.nn, om.ndim, om.nstr, om.nmul, om.nshr) : 0;
+      const bool ready = mbar_wait(&tfull[b], ((uint32_t)tl >> 1) & 1u);
+      if (group_any(!ready)) {
+        if (et == 0) atomicExch(err, 3);
+        *abort_flag = 1;
+        break;
+      }
+      fence_after();
+      const uint32_t acc = tmem + b * TMEM_COLS + lane_base;
 #pragma unroll 1
-    for (int c0 = 0; c0 < BN; c0 += 32) {
-      uint32_t rr[32], ri[32];
-      tmem_ld32(tmem + lane_base + c0, rr);
-      tmem_ld32(tmem + lane_base + BN + c0, ri);
-      if (n < n_rows) {
-        // 16 columns at a time: the beta operands are all loaded before any is used, so that a
-        // warp has 16 loads in flight instead of one
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        uint32_t rr[32], ri[32];
+        tmem_ld32(acc + c0, rr);
+        tmem_ld32(acc + BN + c0, ri);
+        if (n < n_rows) {
+          // 16 columns at a time: the beta operands are all loaded before any is used
 #pragma unroll 1
-        for (int h = 0; h < 32; h += 16) {
-          double2 old[16];
-          if (use_beta) {
+          for (int h = 0; h < 32; h += 16) {
+            double2 old[16];
+            if (use_beta) {
+#pragma unroll
+              for (int j = 0; j < 16; ++j) {
+                const int m = m0 + c0 + h + j;
+                if (m < m_rows) old[j] = *(strided ? Cz + mo[c0 + h + j] + noff : Cz + (int64_t)m * ldc + n);
+              }
+            }
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
               const int m = m0 + c0 + h + j;
-              if (m < m_rows) old[j] = *(strided ? C + moff[c0 + h + j] + noff : C + (int64_t)m * ldc + n);
-            }
-          }
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int m = m0 + c0 + h + j;
-            if (m < m_rows) {
-              const float xr = __uint_as_float(rr[h + j]), xi = __uint_as_float(ri[h + j]);
-              double2 v = make_double2(epi_f2d(ar * xr - ai * xi), epi_f2d(ar * xi + ai * xr));
-              if (use_beta) {
-                const double2 o = old[j];
-                if (beta_one) {
-                  v.x += o.x;
-                  v.y += o.y;
-                } else {
-                  v.x += beta.x * o.x - beta.y * o.y;
-                  v.y += beta.x * o.y + beta.y * o.x;
+              if (m < m_rows) {
+                const float xr = __uint_as_float(rr[h + j]), xi = __uint_as_float(ri[h + j]);
+                double2 v = make_double2(epi_f2d(ar * xr - ai * xi), epi_f2d(ar * xi + ai * xr));
+                if (use_beta) {
+                  const double2 o = old[j];
+                  if (beta_one) {
+                    v.x += o.x;
+                    v.y += o.y;
+                  } else {
+                    v.x += beta.x * o.x - beta.y * o.y;
+                    v.y += beta.x * o.y + beta.y * o.x;
+                  }
                 }
+                *(strided ? Cz + mo[c0 + h + j] + noff : Cz + (int64_t)m * ldc + n) = v;
               }
-              *(strided ? C + moff[c0 + h + j] + noff : C + (int64_t)m * ldc + n) = v;
             }
           }
         }
       }
+      fence_before();
+      mbar_arrive(&tempty[b]);   // this thread's part of accumulator b has been read
     }
   }
+  __syncwarp();
   fence_before();
   __syncthreads();
   if (warp == 2) {
     fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+    // the MMAs may still run if a role gave up early: wait (bounded) for all of them first
+    if (!mbar_wait(done, 0) && lane == 0) atomicExch(err, 5);
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TMEM_COLS));
   }
 }
 
@@ -665,20 +730,22 @@ void tc_gemm_views(Ctx& c, const Tensor& vm, int nrm, const Tensor& vn, int nrn,
   cplx* P = nullptr;
   if (S > 1) P = c.ws.cplxs((int64_t)S * M * N);
   const int64_t ytiles = (N + tc::BM - 1) / tc::BM, xtiles = (M + tc::BN - 1) / tc::BN;
-  CCLR_REQUIRE(xtiles < (int64_t)INT32_MAX, CCLR_E_ARG, "tc_gemm: M too large");
+  CCLR_REQUIRE(xtiles * ytiles * S < (int64_t)INT32_MAX, CCLR_E_ARG, "tc_gemm: too many tiles");
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (c.prof) c.prof_events(e0, e1);
   if (e0) CCLR_CK(cudaEventRecord(e0, c.stream));
-  for (int64_t y0 = 0; y0 < ytiles; y0 += 65535) {   // grid.y limit: chunks of n-tiles
-    dim3 grid((unsigned)xtiles, (unsigned)std::min<int64_t>(65535, ytiles - y0), (unsigned)S);
+  {
+    // persistent: one CTA per SM (or per tile when there are fewer)
+    const int grid = (int)std::min<int64_t>(xtiles * ytiles * S, 148);
     c.kt.begin(c.stream);
     if (S > 1)
-      tc::k_tc_zgemm<<<grid, 128, tc::SMEM_BYTES, c.stream>>>(sn.tm, sm.tm, (int)N, (int)M, kblocks, kb_per, pairs,
+      tc::k_tc_zgemm<<<grid, 192, tc::SMEM_BYTES, c.stream>>>(sn.tm, sm.tm, (int)N, (int)M, kblocks, kb_per, pairs,
                                                               make_double2(1.0, 0.0), make_double2(0.0, 0.0), P, N,
-                                                              M * N, c.tc_err, (int)y0, om, false);
+                                                              M * N, c.tc_err, (int)xtiles, (int)ytiles, S, om, false);
     else
-      tc::k_tc_zgemm<<<grid, 128, tc::SMEM_BYTES, c.stream>>>(sn.tm, sm.tm, (int)N, (int)M, kblocks, kb_per, pairs,
-                                                              alpha, beta, C, ldc, 0, c.tc_err, (int)y0, om, strided);
+      tc::k_tc_zgemm<<<grid, 192, tc::SMEM_BYTES, c.stream>>>(sn.tm, sm.tm, (int)N, (int)M, kblocks, kb_per, pairs,
+                                                              alpha, beta, C, ldc, 0, c.tc_err, (int)xtiles, (int)ytiles,
+                                                              1, om, strided);
     const cudaError_t le = cudaGetLastError();
     CCLR_REQUIRE(le == cudaSuccess, CCLR_E_CUDA,
                  std::string("tensor-core GEMM launch failed (") + cudaGetErrorString(le) + ") M=" + std::to_string(M) +
@@ -766,14 +833,17 @@ int tc_raw_gemm_nt(int precision, int64_t M, int64_t N, int64_t K, const cplx* A
   const tc::Pairs pairs = pairs_for(nsl);
   const int64_t ytiles = (N + tc::BM - 1) / tc::BM, xtiles = (M + tc::BN - 1) / tc::BN;
   const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
-  for (int64_t y0 = 0; y0 < ytiles; y0 += 65535) {
-    dim3 grid((unsigned)xtiles, (unsigned)std::min<int64_t>(65535, ytiles - y0), (unsigned)p.S);
+  CCLR_REQUIRE(xtiles * ytiles * p.S < (int64_t)INT32_MAX, CCLR_E_ARG, "tc_gemm: too many tiles");
+  {
+    const int grid = (int)std::min<int64_t>(xtiles * ytiles * p.S, 148);
     if (p.S > 1)
-      tc::k_tc_zgemm<<<grid, 128, tc::SMEM_BYTES, stream>>>(tn, tm, (int)N, (int)M, p.kblocks, p.kb_per, pairs, one,
-                                                            zero, P, N, M * N, err, (int)y0, tc::OutMap(), false);
+      tc::k_tc_zgemm<<<grid, 192, tc::SMEM_BYTES, stream>>>(tn, tm, (int)N, (int)M, p.kblocks, p.kb_per, pairs, one,
+                                                            zero, P, N, M * N, err, (int)xtiles, (int)ytiles, p.S,
+                                                            tc::OutMap(), false);
     else
-      tc::k_tc_zgemm<<<grid, 128, tc::SMEM_BYTES, stream>>>(tn, tm, (int)N, (int)M, p.kblocks, p.kb_per, pairs, one,
-                                                            zero, C, N, 0, err, (int)y0, tc::OutMap(), false);
+      tc::k_tc_zgemm<<<grid, 192, tc::SMEM_BYTES, stream>>>(tn, tm, (int)N, (int)M, p.kblocks, p.kb_per, pairs, one,
+                                                            zero, C, N, 0, err, (int)xtiles, (int)ytiles, 1,
+                                                            tc::OutMap(), false);
     CCLR_CK(cudaGetLastError());
   }
   if (p.S > 1) {
