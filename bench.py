@@ -165,7 +165,7 @@ def run_reference(args, world, rank):
             times.append(dt)
             vals.append(tf)
     value = statistics.mean(vals)
-    line = dict(metric=METRIC, value=value, unit="TFLOP/s", n_gpus=0, steps=args.steps, warmup=args.warmup,
+    line = dict(metric=METRIC, value=value, unit="TFLOP/s", n_gpus=world, steps=args.steps, warmup=args.warmup,
                 ms_per_step=1e3 * statistics.mean(times), higher_is_better=True, scaling="weak", vs_baseline=None,
                 dtype="f64", data="synthetic", impl="reference", config=config_dict(args),
                 cpu_baseline=dict(value=value, unit="TFLOP/s", cores=cores, kind="oracle", sample=desc),

@@ -32,6 +32,14 @@ cclr_status guard(cclr_ctx* h, F&& fn) {
     CCLR_CK(cudaStreamSynchronize(c.stream));
     if (c.prof) c.prof_collect();
     if (c.kt.on) c.kt.collect();
+    static const bool verbose = std::getenv("CCLR_VERBOSE") != nullptr;
+    if (verbose) {
+      size_t fr = 0, tot = 0;
+      cudaMemGetInfo(&fr, &tot);
+      std::fprintf(stderr, "[cclr] memory: arrays %.2f GiB (%zu), slice cache %.2f GiB, workspace peak %.2f of %.2f GiB, free %.2f GiB\n",
+                   c.persistent_total() / 1073741824.0, c.persistent.size(), tc_cache_bytes() / 1073741824.0,
+                   c.ws.peak / 1073741824.0, c.ws.cap / 1073741824.0, fr / 1073741824.0);
+    }
     if (c.tc_err) {
       int h = 0;
       CCLR_CK(cudaMemcpy(&h, c.tc_err, sizeof(int), cudaMemcpyDeviceToHost));
@@ -58,6 +66,7 @@ void free_all(Ctx& c) {
   ++hbar_generation();
   for (void* p : c.persistent) cudaFree(p);
   c.persistent.clear();
+  c.persistent_bytes.clear();
   c.named.clear();
   c.rd = ResponseData();
   c.fock = c.oooo = c.ooov = c.oovv = c.ovov = c.ovvv = c.vvvv_p = c.oovv_p = c.ovvv_p = nullptr;
@@ -238,7 +247,7 @@ cclr_status cc_ground(cclr_ctx* h, cclr_c128* e_corr_out, int* iters_out) {
   cclr_status st = guard(h, [&](Ctx& c) {
     CCLR_REQUIRE(c.have_ham, CCLR_E_STATE, "cc_ground before cclr_set_hamiltonian");
     c.have_lambda = false;
-    c.rd = ResponseData();
+    release_response(c);
     try {
       its = solve_ground(c);
     } catch (const Error& e) {

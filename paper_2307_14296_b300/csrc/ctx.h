@@ -29,6 +29,7 @@ struct ResponseData {
 
 struct Ctx;
 void tc_release_cache_for(Ctx& c);   // frees the cached BF16 slices of persistent operands
+size_t tc_cache_bytes();             // bytes held by that cache
 
 struct Ctx {
   int device = 0;
@@ -67,6 +68,7 @@ struct Ctx {
   bool have_hbar = false;
 
   std::vector<void*> persistent;                          // all cudaMalloc'd arrays
+  std::vector<size_t> persistent_bytes;
   std::map<std::string, void*> named;
 
   ResponseData rd;
@@ -111,12 +113,23 @@ struct Ctx {
       CCLR_CK(cudaMalloc(&p, bytes));
     }
     persistent.push_back(p);
+    persistent_bytes.push_back(bytes);
     return (cplx*)p;
   }
   void dfree(void* p) {
     if (!p) return;
     for (size_t i = 0; i < persistent.size(); ++i)
-      if (persistent[i] == p) { cudaFree(p); persistent.erase(persistent.begin() + i); return; }
+      if (persistent[i] == p) {
+        cudaFree(p);
+        persistent.erase(persistent.begin() + i);
+        persistent_bytes.erase(persistent_bytes.begin() + i);
+        return;
+      }
+  }
+  size_t persistent_total() const {
+    size_t t = 0;
+    for (size_t b : persistent_bytes) t += b;
+    return t;
   }
   void sync() { CCLR_CK(cudaStreamSynchronize(stream)); }
 
@@ -164,6 +177,7 @@ void pack_anti(Ctx& c, const Tensor& X, cplx* D, int64_t nvec, cplx alpha, bool 
 // solvers (solver.cu)
 int solve_ground(Ctx& c);
 int solve_lambda(Ctx& c);
+void release_response(Ctx& c);   // frees the arrays of the last linear-response solve
 void lr_solve(Ctx& c, int n_ops, const cplx* ops_host, int n_freq, const double* omegas, double gamma,
               int* iters_out);
 void response_function(Ctx& c, cplx* out_host);

@@ -640,8 +640,8 @@ int solve_lambda(Ctx& c) {
 }
 
 // ------------------------------------------------------------------------------ response
-void lr_solve(Ctx& c, int n_ops, const cplx* ops_host, int n_freq, const double* omegas, double gamma,
-              int* iters_out) {
+// Frees the device arrays of the last linear-response solve.
+void release_response(Ctx& c) {
   ResponseData& rd = c.rd;
   for (auto p : rd.ops_dev) c.dfree(p);
   for (auto p : rd.xi) c.dfree(p);
@@ -649,6 +649,12 @@ void lr_solve(Ctx& c, int n_ops, const cplx* ops_host, int n_freq, const double*
   for (auto p : rd.basis) c.dfree(p);
   for (auto p : rd.sig) c.dfree(p);
   rd = ResponseData();
+}
+
+void lr_solve(Ctx& c, int n_ops, const cplx* ops_host, int n_freq, const double* omegas, double gamma,
+              int* iters_out) {
+  release_response(c);
+  ResponseData& rd = c.rd;
   const int64_t N = c.N, n = c.n;
   const int maxL = std::max(8, c.opt.max_subspace);
   Phases ph("lr_solve");

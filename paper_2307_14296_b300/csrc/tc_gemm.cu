@@ -648,6 +648,11 @@ void tc_release_cache() {   // cudaFree waits for the kernels still reading the 
   cache().clear();
 }
 void tc_release_cache_for(Ctx&) { tc_release_cache(); }
+size_t tc_cache_bytes() {
+  size_t t = 0;
+  for (auto& kv : cache()) t += sizeof(__nv_bfloat16) * 2 * kv.second.s.nsl * kv.second.s.rows * kv.second.s.Kpad;
+  return t;
+}
 
 int tc_slices(int precision) { return precision == CCLR_TC_BF16X3 ? 2 : 3; }
 
