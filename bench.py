@@ -184,6 +184,34 @@ def config_dict(args):
 
 
 # ------------------------------------------------------------------------------------------ GPU
+def accuracy_vs_fp64(pk, synth):
+    """Mixed-precision alpha against the FP64 path on the 12/90 replica: max over frequencies and
+    the nine components of |d alpha| / |alpha| (each component against its own size and against
+    the largest one) and the isotropic mean alpha per frequency."""
+    w = WORKLOADS["12x90"]
+    o, v = w["n_occ"], w["n_vir"]
+    inst = synth.make_instance(o, v)
+    om = np.linspace(w["w_min"], w["w_max"], 16)
+    res = {}
+    for prec in (pk.FP64, pk.TC_BF16X3):
+        ctx = pk.Context(0, precision=prec, tol=1e-9 if prec == pk.FP64 else w["tol"], ground_tol=1e-10 if prec == pk.FP64 else 1e-8,
+                         max_subspace=64, batch=8, maxit=80)
+        ctx.cclr_set_hamiltonian(o, v, inst.fock, [inst.blocks[k] for k in synth.CLASSES])
+        ctx.cc_ground()
+        ctx.cc_lambda()
+        ctx.cc_lr_solve(inst.ops, om, w["gamma"])
+        res[prec] = -ctx.cc_response_function()
+        ctx.close()
+    a, b = res[pk.TC_BF16X3], res[pk.FP64]
+    d = np.abs(a - b)
+    mean_a = np.trace(a, axis1=1, axis2=2) / 3
+    mean_b = np.trace(b, axis1=1, axis2=2) / 3
+    return dict(workload="12/90 replica, 16 frequencies on [0.05,0.30], gamma 0.005, 3 operators",
+                max_rel_per_component=float((d / np.abs(b)).max()),
+                max_rel_to_largest=float(d.max() / np.abs(b).max()),
+                max_rel_mean_alpha=float((np.abs(mean_a - mean_b) / np.abs(mean_b)).max()))
+
+
 def run_gemm(args):
     """Tensor-core GEMM alone on one shape (A: M x K, B: N x K, complex), e.g. the packed ladder
     contraction of eight trial vectors (M = 8 Po, K = Pv): a small case for kernel captures."""
@@ -224,6 +252,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-breakdown", action="store_true", help="skip the per-kernel timing step")
+    ap.add_argument("--no-accuracy", action="store_true", help="skip the mixed-vs-FP64 accuracy check")
     ap.add_argument("--workload", default="30x200", choices=sorted(WORKLOADS))
     ap.add_argument("--gemm", default=None, metavar="M,N,K",
                     help="time only the tensor-core complex GEMM C = A B^T on one shape (kernel profiling)")
@@ -336,6 +365,11 @@ def main():
         top = sorted(bd.items(), key=lambda kv: -kv[1][1])[:12]
         breakdown = dict(note="one untimed step, CUDA events around every launch", total_ms=tot,
                          kernels=[dict(name=k, launches=n, ms=ms, share=ms / tot) for k, (n, ms) in top])
+    # accuracy of the mixed-precision step against the FP64 path, on the 12/90 replica (the FP64
+    # step at the full workload takes ~13 min): 16 frequencies, every component of alpha
+    accuracy = None
+    if rank == 0 and not args.no_accuracy and prec != pk.FP64:
+        accuracy = accuracy_vs_fp64(pk, synth)
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         tf, dt, desc = oracle_sample()
@@ -351,7 +385,10 @@ def main():
         metric=METRIC, value=value, unit="TFLOP/s", n_gpus=world, steps=args.steps, warmup=args.warmup,
         ms_per_step=1e3 * t_step, higher_is_better=True, scaling="weak", vs_baseline=None,
         dtype="bf16x3+f64" if prec != pk.FP64 else "f64", data="synthetic", config=config_dict(args),
-        s_per_alpha=t_step / w["n_freq"],
+        s_per_alpha=statistics.mean(s["phase"]["lr_solve"] + s["phase"]["response_function"] for s in stats) / w["n_freq"],
+        s_per_alpha_note="linear-response solves + response function per frequency; ground state and Lambda "
+                         "(once per Hamiltonian) in phase_seconds",
+        s_per_step_per_freq=t_step / w["n_freq"],
         sigma_products_per_step=n_prod,
         phase_seconds={k: statistics.mean(s["phase"][k] for s in stats) for k in stats[0]["phase"]},
         counts={k: statistics.mean(s[k] for s in stats) for k in ("ground_iters", "lambda_sigma", "lr_sigma", "hessian")},
@@ -360,7 +397,7 @@ def main():
                       peak_source=f"bf16_tflops_sustained of {src} MEASURED_PEAKS",
                       launches=prof["launches"], kernel_ms_per_step=prof["ms"] / args.steps,
                       useful_complex_tflops=(prof["flops_useful"] / (prof["ms"] / 1e3) / 1e12 if prof["ms"] else None)),
-        cpu_baseline=cpu, e2e=e2e, fp64=fp64, kernel_breakdown=breakdown,
+        cpu_baseline=cpu, e2e=e2e, fp64=fp64, kernel_breakdown=breakdown, accuracy_vs_fp64=accuracy,
         gpu_launches=int(sum(s["launches"] for s in stats)),
         clocks=clk.summary(),
         alpha_mean_last_freq=[float(np.trace(alpha[-1]).real / 3), float(np.trace(alpha[-1]).imag / 3)],
