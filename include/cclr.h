@@ -118,6 +118,12 @@ cclr_status cc_lr_solve(cclr_ctx *ctx, int n_ops, const cclr_c128 *ops, int n_fr
  * n_freq*n_ops*n_ops values.  The polarizability is alpha = -<<mu;mu>>.  Requires cc_lr_solve. */
 cclr_status cc_response_function(cclr_ctx *ctx, cclr_c128 *out);
 
+/* The CC-CI response function (Sec. 2.3 Eq. CC-CI response function; EOM-eta of the SI "Linear
+ * response" section): the same symmetrization and layout as cc_response_function, from the
+ * solutions of the last cc_lr_solve, without the Hessian term.  Requires cc_lr_solve (after
+ * cc_lambda); CCLR_E_STATE otherwise. */
+cclr_status cc_response_function_ci(cclr_ctx *ctx, cclr_c128 *out);
+
 /* ---------------- component entry points (parity tests, the autograd shim) ------------------ */
 
 /* Which amplitude set: ground T, Lambda, or a response solution. */

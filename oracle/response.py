@@ -148,15 +148,26 @@ class CCSystem:
             S.append(self.sigma_r(B[-1]))
         raise RuntimeError(f"Davidson did not converge (|r|={rn:.3e})")
 
-    def response(self, ops, zs, solver="davidson", tol=1e-11, A=None, half=False):
+    def response(self, ops, zs, solver="davidson", tol=1e-11, A=None, half=False, form="cc"):
         """<<X_a; X_b>>_z for all pairs (a, b) and all z: array [len(zs), nops, nops].
 
-        With half=True return the unsymmetrized f(z) instead (2 f(0) is the second derivative
-        of the CC energy with respect to static fields).
+        form="cc": the CC-CC response function (Sec. 2.3, Eq. CC-CC response function),
+            f(z) = 1/2 [eta^a t^b(z) + eta^b t^a(-z) + (t^a(-z) F) t^b(z)].
+        form="ci": the CC-CI response function (Eq. CC-CI response function; EOM-eta of the SI
+            "Linear response" section, no Hessian term),
+            f(z) = 1/2 [eometa^a t^b(z) - (lam.t^a(-z))(lam.xi^b)
+                        + eometa^b t^a(-z) - (lam.t^b(z))(lam.xi^a)],
+            lam the ground-state multipliers; P swaps (a, -z) with (b, z).
+        Both are symmetrized as f(z) + conj(f(-z*)).  With half=True return the unsymmetrized
+        f(z) instead (2 f(0) of the CC-CC form is the second derivative of the CC energy with
+        respect to static fields).
         """
+        assert form in ("cc", "ci")
         nops = len(ops)
-        eta = [self.eta(X) for X in ops]
+        eta = [self.eta(X) if form == "cc" else self.eta_eom(X) for X in ops]
         xis = [self.xi(X) for X in ops]
+        lam = pack(self.l1, self.l2)
+        lam_xi = [self.bdot(lam, x) for x in xis]
         cache = {}
 
         def t_of(k, w):
@@ -171,6 +182,9 @@ class CCSystem:
         def f(z, a, b):
             tx = t_of(a, -z)
             ty = t_of(b, z)
+            if form == "ci":
+                return 0.5 * (self.bdot(eta[a], ty) - self.bdot(lam, tx) * lam_xi[b]
+                              + self.bdot(eta[b], tx) - self.bdot(lam, ty) * lam_xi[a])
             return 0.5 * (self.bdot(eta[a], ty) + self.bdot(eta[b], tx) + self.bdot(self.hessian(tx), ty))
 
         out = np.zeros((len(zs), nops, nops), dtype=np.complex128)

@@ -30,7 +30,8 @@ FP64, TC_BF16X3, TC_BF16X6 = 0, 2, 3
 AMP_T, AMP_LAMBDA = 0, 1
 EXPORTS = (
     "cclr_default_options", "cclr_create", "cclr_destroy", "cclr_last_error", "cclr_set_hamiltonian",
-    "cc_ground", "cc_lambda", "cc_lr_solve", "cc_response_function", "cclr_get_amplitudes",
+    "cc_ground", "cc_lambda", "cc_lr_solve", "cc_response_function", "cc_response_function_ci",
+    "cclr_get_amplitudes",
     "cclr_set_amplitudes", "cclr_get_response_vector", "cclr_sigma", "cclr_residual", "cclr_xi",
     "cclr_eta", "cclr_hessian", "cclr_zgemm_nt", "cclr_kernel_profile", "cclr_get_stats",
     "cclr_zgemm_nt_noalloc", "cclr_kernel_breakdown",
@@ -59,6 +60,7 @@ _sig = {
     "cc_lambda": (_i, [_vp, ctypes.POINTER(_i)]),
     "cc_lr_solve": (_i, [_vp, _i, _vp, _i, _vp, _d, _vp]),
     "cc_response_function": (_i, [_vp, _vp]),
+    "cc_response_function_ci": (_i, [_vp, _vp]),
     "cclr_get_amplitudes": (_i, [_vp, _i, _vp, _sz]),
     "cclr_set_amplitudes": (_i, [_vp, _i, _vp, _sz]),
     "cclr_get_response_vector": (_i, [_vp, _i, _i, _i, _vp, _sz]),
@@ -167,6 +169,12 @@ class Context:
     def cc_response_function(self):
         out = np.zeros((self._nfreq, self._nops, self._nops), np.complex128)
         self._check(_lib.cc_response_function(self._h, _ptr(out)))
+        return out
+
+    def cc_response_function_ci(self):
+        """The CC-CI form (no Hessian term) from the same solutions."""
+        out = np.zeros((self._nfreq, self._nops, self._nops), np.complex128)
+        self._check(_lib.cc_response_function_ci(self._h, _ptr(out)))
         return out
 
     # ---- components
@@ -284,6 +292,10 @@ def cc_lr_solve(ctx, ops, omegas, gamma):
 
 def cc_response_function(ctx):
     return ctx.cc_response_function()
+
+
+def cc_response_function_ci(ctx):
+    return ctx.cc_response_function_ci()
 
 
 def cclr_zgemm_nt_noalloc(A, B, C, precision=TC_BF16X3, stream=None) -> int:

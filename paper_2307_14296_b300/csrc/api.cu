@@ -289,6 +289,13 @@ cclr_status cc_response_function(cclr_ctx* h, cclr_c128* out) {
   });
 }
 
+cclr_status cc_response_function_ci(cclr_ctx* h, cclr_c128* out) {
+  return guard(h, [&](Ctx& c) {
+    CCLR_REQUIRE(out, CCLR_E_ARG, "null output");
+    response_function_ci(c, (cplx*)out);
+  });
+}
+
 cclr_status cclr_get_amplitudes(cclr_ctx* h, int which, cclr_c128* dst, size_t n) {
   return guard(h, [&](Ctx& c) {
     CCLR_REQUIRE(dst && (int64_t)n == c.N, CCLR_E_ARG, "amplitude buffer length must be o*v + Po*Pv");

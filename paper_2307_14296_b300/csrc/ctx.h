@@ -181,6 +181,7 @@ void release_response(Ctx& c);   // frees the arrays of the last linear-response
 void lr_solve(Ctx& c, int n_ops, const cplx* ops_host, int n_freq, const double* omegas, double gamma,
               int* iters_out);
 void response_function(Ctx& c, cplx* out_host);
+void response_function_ci(Ctx& c, cplx* out_host);
 
 // small dense complex linear algebra on the host
 void zsolve(int n, std::vector<zc>& A, std::vector<zc>& b);   // A (n x n row-major) x = b, in place

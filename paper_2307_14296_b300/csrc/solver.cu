@@ -818,4 +818,54 @@ void response_function(Ctx& c, cplx* out_host) {
       }
 }
 
+// CC-CI response function (Eq. CC-CI response function): no Hessian term; EOM-eta of the SI
+// "Linear response" section and the ground-state multipliers lambda,
+//   f(z) = 1/2 [eometa^X t^Y(z) - (lam.t^X(-z))(lam.xi^Y) + eometa^Y t^X(-z) - (lam.t^Y(z))(lam.xi^X)],
+//   <<X;Y>>_z = f(z) + conj(f(-z*)),
+// evaluated in the trial spaces of cc_lr_solve: t^X(w) = B^X beta^X(w).
+void response_function_ci(Ctx& c, cplx* out_host) {
+  ResponseData& rd = c.rd;
+  CCLR_REQUIRE(rd.solved, CCLR_E_STATE, "cc_response_function_ci before cc_lr_solve");
+  CCLR_REQUIRE(c.have_lambda, CCLR_E_STATE, "cc_response_function_ci needs Lambda");
+  Fast32 f32(c);
+  const int64_t N = c.N;
+  const int nop = rd.n_ops, maxL = std::max(8, c.opt.max_subspace);
+  std::vector<std::vector<zc>> E((size_t)nop * nop), Lb(nop);
+  std::vector<zc> lam_xi(nop);
+  {
+    Scope sc(c.ws);
+    cplx* eom = c.ws.cplxs(N);
+    for (int x = 0; x < nop; ++x) {
+      eta_vec(c, rd.ops_dev[x], true, eom);
+      for (int y = 0; y < nop; ++y)
+        gram_host(c, rows(c, eom, 1), rows(c, rd.basis[y], rd.nb[y]), false, E[(size_t)x * nop + y]);
+      gram_host(c, rows(c, c.lam, 1), rows(c, rd.basis[x], rd.nb[x]), false, Lb[x]);
+      std::vector<zc> g;
+      gram_host(c, rows(c, c.lam, 1), rows(c, rd.xi[x], 1), false, g);
+      lam_xi[x] = g[0];
+    }
+  }
+  auto beta = [&](int k, int f, int s) { return &rd.beta[k][(size_t)rd.shift_of[(size_t)f * 4 + s] * maxL]; };
+  auto dotL = [&](const std::vector<zc>& a, const zc* b, int L) {
+    zc acc(0);
+    for (int i = 0; i < L; ++i) acc += a[i] * b[i];
+    return acc;
+  };
+  // shifts: 0: w+ig (z), 1: -w+ig (-z*), 2: w-ig (z*), 3: -w-ig (-z)
+  auto half = [&](int f, int x, int y, int sz, int smz) {
+    const zc* by = beta(y, f, sz);
+    const zc* bx = beta(x, f, smz);
+    const int Lx = rd.nb[x], Ly = rd.nb[y];
+    const zc a = dotL(E[(size_t)x * nop + y], by, Ly), b = dotL(E[(size_t)y * nop + x], bx, Lx);
+    const zc lx = dotL(Lb[x], bx, Lx), ly = dotL(Lb[y], by, Ly);
+    return 0.5 * (a - lx * lam_xi[y] + b - ly * lam_xi[x]);
+  };
+  for (int f = 0; f < rd.n_freq; ++f)
+    for (int x = 0; x < nop; ++x)
+      for (int y = 0; y < nop; ++y) {
+        const zc val = half(f, x, y, 0, 3) + std::conj(half(f, x, y, 1, 2));
+        out_host[((size_t)f * nop + x) * nop + y] = make_double2(val.real(), val.imag());
+      }
+}
+
 }  // namespace cclr

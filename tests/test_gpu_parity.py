@@ -134,4 +134,20 @@ def test_two_electron_exact_sum_over_states(pk):
     ctx.cc_lambda()
     ctx.cc_lr_solve(inst.ops, [0.1, 0.25], 0.01)
     assert rel(ctx.cc_response_function(), sos) < TOL
+    assert rel(ctx.cc_response_function_ci(), sos) < TOL   # both forms are exact for two electrons
+    ctx.close()
+
+
+def test_cc_ci_response_function(pk):
+    """CC-CI form (EOM-eta, no Hessian term) against the oracle at (3,8), damped frequencies."""
+    inst = synth.make_instance(3, 8, seed=21, sd=0.05)
+    s = R.CCSystem(Ints.from_instance(inst))
+    omegas, gamma = [0.05, 0.3], 0.01
+    ctx = make_ctx(pk, inst, tol=1e-10, ground_tol=1e-11)
+    ctx.cc_ground()
+    ctx.cc_lambda()
+    ctx.cc_lr_solve(inst.ops, omegas, gamma)
+    got = ctx.cc_response_function_ci()
+    ref = s.response(inst.ops, [w + 1j * gamma for w in omegas], tol=1e-11, form="ci")
+    assert rel(got, ref) < TOL
     ctx.close()

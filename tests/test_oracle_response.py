@@ -28,6 +28,26 @@ def test_two_electron_sum_over_states_davidson(two_electron):
     assert np.abs(got - sos).max() < 1e-10 * np.abs(sos).max()
 
 
+def test_two_electron_sum_over_states_cc_ci(two_electron):
+    """The CC-CI form is exact for two electrons as well (CCSD = FCI)."""
+    inst, s, sos = two_electron
+    got = s.response(inst.ops, ZS, solver="dense", A=s.dense_A(), form="ci")
+    assert np.abs(got - sos).max() < 1e-11 * np.abs(sos).max()
+
+
+def test_cc_ci_differs_from_cc_cc_beyond_two_electrons():
+    """With four electrons the two forms differ (the CC-CI form drops the Hessian term and is
+    not the derivative of the CC quasienergy); both keep alpha(-w+ig) = alpha(w+ig)*."""
+    inst = synth.make_instance(4, 8, seed=5, sd=0.05)
+    s = R.CCSystem(Ints.from_instance(inst))
+    A = s.dense_A()
+    zs = [0.1 + 0.01j, -0.1 + 0.01j]
+    cc = s.response(inst.ops, zs, solver="dense", A=A)
+    ci = s.response(inst.ops, zs, solver="dense", A=A, form="ci")
+    assert np.abs(ci - cc).max() > 1e-6 * np.abs(cc).max()
+    assert np.abs(ci[1] - np.conj(ci[0])).max() < 1e-11 * np.abs(ci).max()
+
+
 def test_lambda_matches_dense_left_solve():
     inst = synth.make_instance(2, 6, seed=3, sd=0.1)
     s = R.CCSystem(Ints.from_instance(inst))
