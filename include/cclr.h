@@ -124,6 +124,20 @@ cclr_status cc_response_function(cclr_ctx *ctx, cclr_c128 *out);
  * cc_lambda); CCLR_E_STATE otherwise. */
 cclr_status cc_response_function_ci(cclr_ctx *ctx, cclr_c128 *out);
 
+/* EOM-CCSD excitation energies (SI "EOM-EE sigma-vectors and intermediates"; the Davidson scheme
+ * applied to the eigenproblem): the n_roots (1..16) eigenvalues of the CC Jacobian A with the
+ * smallest real part, from a non-Hermitian Davidson iteration on right sigma products with the
+ * orbital-energy-denominator preconditioner.  energies_out receives n_roots complex values (the
+ * real part is the excitation energy in Hartree), ordered by real part; iters_out (may be NULL)
+ * the iteration count.  Options: tol (absolute residual norm of the unit right vector),
+ * max_subspace, maxit, batch, precision (tensor-core modes stop at 1e-5 |w|).  Requires
+ * cc_ground (CCLR_E_STATE); CCLR_E_NOCONV if maxit is reached. */
+cclr_status cc_eom_ee(cclr_ctx *ctx, int n_roots, cclr_c128 *energies_out, int *iters_out);
+
+/* Right eigenvector of root `root` of the last cc_eom_ee in the amplitude layout (n = o*v + Po*Pv
+ * values, host buffer, norm 1 over the unique excitations to the solver's precision). */
+cclr_status cclr_get_eom_vector(cclr_ctx *ctx, int root, cclr_c128 *dst, size_t n);
+
 /* ---------------- component entry points (parity tests, the autograd shim) ------------------ */
 
 /* Which amplitude set: ground T, Lambda, or a response solution. */

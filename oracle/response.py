@@ -104,6 +104,14 @@ class CCSystem:
         raise RuntimeError("Lambda equations did not converge")
 
     # -- dense references (tiny systems)
+    def eom_energies(self, nroots, A=None):
+        """Lowest EOM-CCSD excitation energies: the eigenvalues of the CC Jacobian A (SI "EOM-EE
+        sigma-vectors and intermediates"), smallest real part first, from the dense A (tiny
+        systems only)."""
+        A = self.dense_A() if A is None else A
+        w = np.linalg.eigvals(A)
+        return w[np.argsort(w.real, kind="stable")][:nroots]
+
     def dense_A(self):
         n = self.D.size
         A = np.zeros((n, n), dtype=np.complex128)

@@ -30,7 +30,8 @@ FP64, TC_BF16X3, TC_BF16X6 = 0, 2, 3
 AMP_T, AMP_LAMBDA = 0, 1
 EXPORTS = (
     "cclr_default_options", "cclr_create", "cclr_destroy", "cclr_last_error", "cclr_set_hamiltonian",
-    "cc_ground", "cc_lambda", "cc_lr_solve", "cc_response_function", "cc_response_function_ci",
+    "cc_ground", "cc_lambda", "cc_lr_solve", "cc_response_function", "cc_response_function_ci", "cc_eom_ee",
+    "cclr_get_eom_vector",
     "cclr_get_amplitudes",
     "cclr_set_amplitudes", "cclr_get_response_vector", "cclr_sigma", "cclr_residual", "cclr_xi",
     "cclr_eta", "cclr_hessian", "cclr_zgemm_nt", "cclr_kernel_profile", "cclr_get_stats",
@@ -61,6 +62,8 @@ _sig = {
     "cc_lr_solve": (_i, [_vp, _i, _vp, _i, _vp, _d, _vp]),
     "cc_response_function": (_i, [_vp, _vp]),
     "cc_response_function_ci": (_i, [_vp, _vp]),
+    "cc_eom_ee": (_i, [_vp, _i, _vp, _vp]),
+    "cclr_get_eom_vector": (_i, [_vp, _i, _vp, ctypes.c_size_t]),
     "cclr_get_amplitudes": (_i, [_vp, _i, _vp, _sz]),
     "cclr_set_amplitudes": (_i, [_vp, _i, _vp, _sz]),
     "cclr_get_response_vector": (_i, [_vp, _i, _i, _i, _vp, _sz]),
@@ -175,6 +178,19 @@ class Context:
         """The CC-CI form (no Hessian term) from the same solutions."""
         out = np.zeros((self._nfreq, self._nops, self._nops), np.complex128)
         self._check(_lib.cc_response_function_ci(self._h, _ptr(out)))
+        return out
+
+    def cc_eom_ee(self, n_roots):
+        """Lowest n_roots EOM-CCSD excitation energies (complex, ordered by real part) and the
+        iteration count."""
+        w = np.zeros(n_roots, np.complex128)
+        it = _i()
+        self._check(_lib.cc_eom_ee(self._h, int(n_roots), _ptr(w), ctypes.byref(it)))
+        return w, it.value
+
+    def cclr_get_eom_vector(self, root):
+        out = np.zeros(self.N, np.complex128)
+        self._check(_lib.cclr_get_eom_vector(self._h, int(root), _ptr(out), out.size))
         return out
 
     # ---- components
@@ -296,6 +312,10 @@ def cc_response_function(ctx):
 
 def cc_response_function_ci(ctx):
     return ctx.cc_response_function_ci()
+
+
+def cc_eom_ee(ctx, n_roots):
+    return ctx.cc_eom_ee(n_roots)
 
 
 def cclr_zgemm_nt_noalloc(A, B, C, precision=TC_BF16X3, stream=None) -> int:

@@ -69,6 +69,8 @@ void free_all(Ctx& c) {
   c.persistent_bytes.clear();
   c.named.clear();
   c.rd = ResponseData();
+  c.eom_vecs.clear();
+  c.eom_w.clear();
   c.fock = c.oooo = c.ooov = c.oovv = c.ovov = c.ovvv = c.vvvv_p = c.oovv_p = c.ovvv_p = nullptr;
   c.D = nullptr;
   c.po = c.pv = nullptr;
@@ -248,6 +250,9 @@ cclr_status cc_ground(cclr_ctx* h, cclr_c128* e_corr_out, int* iters_out) {
     CCLR_REQUIRE(c.have_ham, CCLR_E_STATE, "cc_ground before cclr_set_hamiltonian");
     c.have_lambda = false;
     release_response(c);
+    for (auto p : c.eom_vecs) c.dfree(p);
+    c.eom_vecs.clear();
+    c.eom_w.clear();
     try {
       its = solve_ground(c);
     } catch (const Error& e) {
@@ -293,6 +298,24 @@ cclr_status cc_response_function_ci(cclr_ctx* h, cclr_c128* out) {
   return guard(h, [&](Ctx& c) {
     CCLR_REQUIRE(out, CCLR_E_ARG, "null output");
     response_function_ci(c, (cplx*)out);
+  });
+}
+
+cclr_status cc_eom_ee(cclr_ctx* h, int n_roots, cclr_c128* energies_out, int* iters_out) {
+  return guard(h, [&](Ctx& c) {
+    CCLR_REQUIRE(energies_out, CCLR_E_ARG, "null output");
+    std::vector<zc> w;
+    const int its = eom_ee(c, n_roots, w);
+    for (int q = 0; q < n_roots; ++q) energies_out[q] = cclr_c128{w[q].real(), w[q].imag()};
+    if (iters_out) *iters_out = its;
+  });
+}
+
+cclr_status cclr_get_eom_vector(cclr_ctx* h, int root, cclr_c128* dst, size_t n) {
+  return guard(h, [&](Ctx& c) {
+    CCLR_REQUIRE(dst && (int64_t)n == c.N, CCLR_E_ARG, "vector buffer length must be o*v + Po*Pv");
+    CCLR_REQUIRE(root >= 0 && root < (int)c.eom_vecs.size(), CCLR_E_STATE, "no such EOM root (call cc_eom_ee)");
+    CCLR_CK(cudaMemcpyAsync(dst, c.eom_vecs[root], sizeof(cplx) * n, cudaMemcpyDeviceToHost, c.stream));
   });
 }
 

@@ -72,6 +72,8 @@ struct Ctx {
   std::map<std::string, void*> named;
 
   ResponseData rd;
+  std::vector<zc> eom_w;            // EOM-EE roots of the last cc_eom_ee and their right vectors
+  std::vector<cplx*> eom_vecs;
 
   // tensor-core status word (bounded-wait expiry) and optional per-launch timing of the
   // tensor-core kernel with CUDA events on the context's stream
@@ -182,6 +184,7 @@ void lr_solve(Ctx& c, int n_ops, const cplx* ops_host, int n_freq, const double*
               int* iters_out);
 void response_function(Ctx& c, cplx* out_host);
 void response_function_ci(Ctx& c, cplx* out_host);
+int eom_ee(Ctx& c, int nroots, std::vector<zc>& w_out);
 
 // small dense complex linear algebra on the host
 void zsolve(int n, std::vector<zc>& A, std::vector<zc>& b);   // A (n x n row-major) x = b, in place

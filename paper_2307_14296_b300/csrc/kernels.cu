@@ -603,9 +603,10 @@ __global__ void __launch_bounds__(kThreads, F32 ? 2 : 1)
           }
           if (!norm_y) nn[q] += r.x * r.x + r.y * r.y;
           if (D) {
-            // -r / (D - z) = -r conj(D - z) / |D - z|^2
+            // -r / (D - z) = -r conj(D - z) / |D - z|^2, with |D - z| >= 1e-4 (a Ritz value of the
+            // eigensolver can come arbitrarily close to a denominator)
             const R dr = dz.x - zs[q].x, dm = -zs[q].y;
-            const R inv = R(1) / (dr * dr + dm * dm);
+            const R inv = R(1) / fmax(dr * dr + dm * dm, R(1e-8));
             const R rx = r.x, ry = r.y;
             r.x = -(rx * dr + ry * dm) * inv;
             r.y = -(ry * dr - rx * dm) * inv;

@@ -14,6 +14,7 @@
 //    reduces to small bilinear forms: eta^X . B^Y, and (B^X F) . B^Y built from one Hessian
 //    product per trial vector.
 #include "ctx.h"
+#include "zeig.h"
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -337,6 +338,64 @@ void restart(Ctx& c, System& s, int maxL, int kmax) {
   s.L = kk;
 }
 
+// Projects the nt candidate corrections R (device, nt x N; overwritten) against the trial space
+// B[0..L) with one classical Gram-Schmidt pass (R -= B (B^H R)), then appends up to kmax of them
+// to B[L..]: Gram-Schmidt among the candidates in their own Gram metric, in the given order; a
+// direction is kept only if at least 1% of its norm before projection (pre2: squared norms) lies
+// outside the trial space and the directions kept before it.  Returns the number appended.
+// cdev holds >= L * nt coefficients.
+int add_corrections(Ctx& c, cplx* B, int L, cplx* R, int nt, const double* pre2, int kmax, cplx* cdev,
+                    double* vscr) {
+  const int64_t N = c.N;
+  if (kmax <= 0 || nt <= 0) return 0;
+  if (L > 0) {
+    std::vector<zc> g;
+    gram_host(c, rows(c, B, L), rows(c, R, nt), true, g);
+    for (auto& x : g) x = -x;
+    to_dev(c, g.data(), cdev, (int64_t)L * nt);
+    VecMat a;
+    a.X = rows(c, B, L);
+    a.m = nt;
+    a.C = cdev;
+    a.Y = R;
+    a.ldy = N;
+    a.acc = true;
+    vecmat(c.L, N, a, vscr);
+  }
+  std::vector<zc> RR;
+  gram_host(c, rows(c, R, nt), rows(c, R, nt), true, RR);
+  auto ip = [&](const std::vector<zc>& u, const std::vector<zc>& v) {   // u^H RR v
+    zc acc(0);
+    for (int i = 0; i < nt; ++i) {
+      zc r(0);
+      for (int j = 0; j < nt; ++j) r += RR[(size_t)i * nt + j] * v[j];
+      acc += std::conj(u[i]) * r;
+    }
+    return acc;
+  };
+  std::vector<std::vector<zc>> T;
+  for (int t = 0; t < nt && (int)T.size() < kmax; ++t) {
+    std::vector<zc> v(nt, zc(0));
+    v[t] = 1.0;
+    for (int pass = 0; pass < 2; ++pass)
+      for (auto& u : T) {
+        const zc d = ip(u, v);
+        for (int i = 0; i < nt; ++i) v[i] -= d * u[i];
+      }
+    const double n2 = ip(v, v).real();
+    if (!(n2 > 0.0) || std::sqrt(n2) < 1e-2 * std::sqrt(std::max(0.0, pre2[t]))) continue;
+    for (auto& x : v) x /= std::sqrt(n2);
+    T.push_back(v);
+  }
+  const int kk = (int)T.size();
+  if (kk == 0) return 0;
+  std::vector<zc> W((size_t)nt * kk);
+  for (int j = 0; j < nt; ++j)
+    for (int a = 0; a < kk; ++a) W[(size_t)j * kk + a] = T[a][j];
+  combine(c, rows(c, R, nt), kk, W, B + (int64_t)L * N);
+  return kk;
+}
+
 // Solve (Op - z) x = -b for every system and shift.  Op(nvec, in, out) acts on N-vectors.
 //
 // Per iteration and right-hand side, every pass over the N-vectors is one multi-output kernel:
@@ -544,60 +603,12 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
         CCLR_CK(cudaMemcpyAsync(pre2, n2dev, sizeof(double) * nt, cudaMemcpyDeviceToHost, c.stream));
         c.sync();
       }
-      // ---- project out the trial space: R -= B (B^H R)
+      // ---- project out the trial space and append the new directions
       ph.mark(c, "project");
-      {
-        std::vector<zc> g;
-        gram_host(c, rows(c, s.B, s.L), rows(c, R, nt), true, g);
-        for (auto& x : g) x = -x;
-        to_dev(c, g.data(), cdev, (int64_t)s.L * nt);
-        VecMat a;
-        a.X = rows(c, s.B, s.L);
-        a.m = nt;
-        a.C = cdev;
-        a.Y = R;
-        a.ldy = N;
-        a.acc = true;
-        vecmat(c.L, N, a, vscr);
-      }
-      // ---- selection: Gram-Schmidt in the candidates' Gram metric, worst first; a direction is
-      // kept only if at least 1% of the preconditioned residual lies outside the trial space and
-      // the directions kept before it
-      ph.mark(c, "select");
-      std::vector<zc> RR;
-      gram_host(c, rows(c, R, nt), rows(c, R, nt), true, RR);
-      auto ip = [&](const std::vector<zc>& u, const std::vector<zc>& v) {   // u^H RR v
-        zc acc(0);
-        for (int i = 0; i < nt; ++i) {
-          zc r(0);
-          for (int j = 0; j < nt; ++j) r += RR[(size_t)i * nt + j] * v[j];
-          acc += std::conj(u[i]) * r;
-        }
-        return acc;
-      };
-      std::vector<std::vector<zc>> T;
-      for (int t = 0; t < nt; ++t) {
-        if ((int)T.size() >= kMaxNew || s.L + (int)T.size() >= maxL) break;
-        std::vector<zc> v(nt, zc(0));
-        v[t] = 1.0;
-        for (int pass = 0; pass < 2; ++pass)
-          for (auto& u : T) {
-            const zc d = ip(u, v);
-            for (int i = 0; i < nt; ++i) v[i] -= d * u[i];
-          }
-        const double n2 = ip(v, v).real();
-        if (!(n2 > 0.0) || std::sqrt(n2) < 1e-2 * std::sqrt(std::max(0.0, pre2[t]))) continue;
-        for (auto& x : v) x /= std::sqrt(n2);
-        T.push_back(v);
-      }
-      if (T.empty())
+      const int kk = add_corrections(c, s.B, s.L, R, nt, pre2, std::min(kMaxNew, maxL - s.L), cdev, vscr);
+      if (kk == 0)
         throw Error(CCLR_E_NOCONV, "Davidson stagnated: residual " + std::to_string(order.front().first) +
                                        " above tolerance " + std::to_string(tol_s) + " with no new direction");
-      const int kk = (int)T.size();
-      std::vector<zc> W((size_t)nt * kk);
-      for (int j = 0; j < nt; ++j)
-        for (int a = 0; a < kk; ++a) W[(size_t)j * kk + a] = T[a][j];
-      combine(c, rows(c, R, nt), kk, W, s.B + (int64_t)s.L * N);
       s.L += kk;
       fresh[k] = kk;
     }
@@ -866,6 +877,288 @@ void response_function_ci(Ctx& c, cplx* out_host) {
         const zc val = half(f, x, y, 0, 3) + std::conj(half(f, x, y, 1, 2));
         out_host[((size_t)f * nop + x) * nop + y] = make_double2(val.real(), val.imag());
       }
+}
+
+// ------------------------------------------------------------------------------ EOM-EE
+// Lowest roots of the right eigenproblem A r = w r (EOM-CCSD excitation energies; SI "EOM-EE
+// sigma-vectors and intermediates", with the Davidson scheme used for eigenvalues): a
+// non-Hermitian Davidson iteration on right sigma products with the orbital-energy-denominator
+// preconditioner delta = -(D - w)^{-1} r.  Ritz pairs come from the Galerkin problem
+// (B^H S) y = w (B^H B) y (Cholesky of B^H B, then the general complex eigensolver on the host);
+// roots are ordered by real part; when the space is full it is compressed onto the lowest Ritz
+// vectors.  Starting vectors: unit vectors on the smallest denominators.
+namespace {
+// B^H B = L L^H (lower L, n x n, ld = ld); false if not positive definite
+bool zchol(int n, const std::vector<zc>& A, int ld, std::vector<zc>& Lo) {
+  Lo.assign((size_t)n * n, zc(0));
+  for (int j = 0; j < n; ++j) {
+    double d = A[(size_t)j * ld + j].real();
+    for (int k = 0; k < j; ++k) d -= std::norm(Lo[(size_t)j * n + k]);
+    if (!(d > 0.0)) return false;
+    const double ljj = std::sqrt(d);
+    Lo[(size_t)j * n + j] = ljj;
+    for (int i = j + 1; i < n; ++i) {
+      zc s = A[(size_t)i * ld + j];
+      for (int k = 0; k < j; ++k) s -= Lo[(size_t)i * n + k] * std::conj(Lo[(size_t)j * n + k]);
+      Lo[(size_t)i * n + j] = s / ljj;
+    }
+  }
+  return true;
+}
+}  // namespace
+
+int eom_ee(Ctx& c, int nroots, std::vector<zc>& w_out) {
+  static const bool verbose = std::getenv("CCLR_VERBOSE") != nullptr;
+  CCLR_REQUIRE(c.have_t && c.have_hbar, CCLR_E_STATE, "cc_eom_ee before cc_ground");
+  CCLR_REQUIRE(nroots >= 1 && nroots <= kVecMatOut, CCLR_E_ARG, "cc_eom_ee: n_roots must be 1..16");
+  Fast32 f32(c);
+  const int64_t N = c.N;
+  CCLR_REQUIRE(N > nroots, CCLR_E_ARG, "cc_eom_ee: more roots than excitations");
+  const int maxL = std::min<int>(kVecMatMaxRows / 2, std::max(c.opt.max_subspace, 6 * nroots));
+  const int nstart = (int)std::min<int64_t>(N, std::max(2 * nroots, nroots + 2));
+  for (auto p : c.eom_vecs) c.dfree(p);
+  c.eom_vecs.clear();
+  c.eom_w.clear();
+  cplx* B = c.dalloc((int64_t)maxL * N);
+  cplx* S = c.dalloc((int64_t)maxL * N);
+  auto cleanup = [&]() { c.dfree(B); c.dfree(S); };
+  int iters = 0;
+  try {
+    Scope sc(c.ws);
+    double* vscr = (double*)c.ws.alloc(sizeof(double) * vecmat_scratch_doubles());
+    cplx* cdev = c.ws.cplxs((int64_t)2 * maxL * kVecMatOut);
+    cplx* zdev = c.ws.cplxs(kVecMatOut);
+    double* n2dev = (double*)c.ws.alloc(sizeof(double) * kVecMatOut);
+    cplx* R = c.ws.cplxs((int64_t)nroots * N);
+    // starting vectors: e_k on the nstart smallest denominators
+    {
+      std::vector<double> D(N);
+      CCLR_CK(cudaMemcpyAsync(D.data(), c.D, sizeof(double) * N, cudaMemcpyDeviceToHost, c.stream));
+      c.sync();
+      std::vector<int64_t> idx(N);
+      for (int64_t i = 0; i < N; ++i) idx[i] = i;
+      std::partial_sort(idx.begin(), idx.begin() + nstart, idx.end(), [&](int64_t a, int64_t b) { return D[a] < D[b]; });
+      fill_zero(c.L, B, (int64_t)nstart * N);
+      const cplx one = cx(1.0);
+      for (int j = 0; j < nstart; ++j)
+        CCLR_CK(cudaMemcpyAsync(B + (int64_t)j * N + idx[j], &one, sizeof(cplx), cudaMemcpyHostToDevice, c.stream));
+      c.sync();
+    }
+    std::vector<zc> BS((size_t)maxL * maxL, zc(0)), BB((size_t)maxL * maxL, zc(0));
+    int L = nstart, fresh = nstart;
+    std::vector<zc> theta(nroots);
+    std::vector<std::vector<zc>> Y(nroots);
+    std::vector<double> rn(nroots, 1e300);
+    double best = 1e300;
+    int best_it = 0;
+    for (int it = 1; it <= c.opt.maxit; ++it) {
+      iters = it;
+      {   // sigma of the new vectors, in batches
+        const int L0 = L - fresh;
+        const int bmax = c.opt.batch > 0 ? c.opt.batch : fresh;
+        const double t0 = now();
+        for (int q0 = 0; q0 < fresh; q0 += bmax) {
+          const int nb = std::min(bmax, fresh - q0);
+          sigma_right(c, nb, B + (int64_t)(L0 + q0) * N, S + (int64_t)(L0 + q0) * N);
+        }
+        c.sync();
+        c.stats.sigma_seconds += now() - t0;
+        // Galerkin matrices: new columns of B^H S and B^H B, new rows of B^H S
+        std::vector<zc> g;
+        gram_host(c, rows(c, B, L), Rows().add(S + (int64_t)L0 * N, fresh, N).add(B + (int64_t)L0 * N, fresh, N), true,
+                  g);
+        const int ny = 2 * fresh;
+        for (int i = 0; i < L; ++i)
+          for (int j = 0; j < fresh; ++j) {
+            BS[(size_t)i * maxL + L0 + j] = g[(size_t)i * ny + j];
+            const zc bb = g[(size_t)i * ny + fresh + j];
+            BB[(size_t)i * maxL + L0 + j] = bb;
+            BB[(size_t)(L0 + j) * maxL + i] = std::conj(bb);
+          }
+        if (L0 > 0) {
+          gram_host(c, rows(c, S, L0), rows(c, B + (int64_t)L0 * N, fresh), true, g);
+          for (int i = 0; i < L0; ++i)
+            for (int j = 0; j < fresh; ++j) BS[(size_t)(L0 + j) * maxL + i] = std::conj(g[(size_t)i * fresh + j]);
+        }
+      }
+      // Ritz pairs: M = Lo^{-1} (B^H S) Lo^{-H}, y = Lo^{-H} y'
+      std::vector<zc> Lo;
+      CCLR_REQUIRE(zchol(L, BB, maxL, Lo), CCLR_E_NOCONV, "cc_eom_ee: trial space lost linear independence");
+      std::vector<zc> M((size_t)L * L);
+      {
+        std::vector<zc> T((size_t)L * L);   // T = Lo^{-1} BS (forward substitution, column by column)
+        for (int j = 0; j < L; ++j)
+          for (int i = 0; i < L; ++i) {
+            zc s = BS[(size_t)i * maxL + j];
+            for (int k = 0; k < i; ++k) s -= Lo[(size_t)i * L + k] * T[(size_t)k * L + j];
+            T[(size_t)i * L + j] = s / Lo[(size_t)i * L + i];
+          }
+        for (int i = 0; i < L; ++i)   // M = T Lo^{-H}: solve M Lo^H = T row by row
+          for (int j = 0; j < L; ++j) {
+            zc s = T[(size_t)i * L + j];
+            for (int k = 0; k < j; ++k) s -= M[(size_t)i * L + k] * std::conj(Lo[(size_t)j * L + k]);
+            M[(size_t)i * L + j] = s / std::conj(Lo[(size_t)j * L + j]);
+          }
+      }
+      std::vector<zc> wv, V;
+      CCLR_REQUIRE(zgeev_small(L, M, wv, V), CCLR_E_NOCONV, "cc_eom_ee: subspace eigenproblem did not converge");
+      std::vector<int> ord(L);
+      for (int i = 0; i < L; ++i) ord[i] = i;
+      std::sort(ord.begin(), ord.end(), [&](int a, int b) { return wv[a].real() < wv[b].real(); });
+      auto ritz = [&](int col, std::vector<zc>& y) {   // y = Lo^{-H} y' (back substitution)
+        y.assign(maxL, zc(0));
+        for (int i = L - 1; i >= 0; --i) {
+          zc s = V[(size_t)i * L + col];
+          for (int k = i + 1; k < L; ++k) s -= std::conj(Lo[(size_t)k * L + i]) * y[k];
+          y[i] = s / std::conj(Lo[(size_t)i * L + i]);
+        }
+      };
+      for (int q = 0; q < nroots; ++q) {
+        theta[q] = wv[ord[q]];
+        ritz(ord[q], Y[q]);
+      }
+      // residual norms r_q = (S - theta_q B) y_q, all roots in one pass
+      auto coef = [&](const std::vector<int>& qs) {
+        const int m = (int)qs.size();
+        std::vector<zc> C((size_t)2 * L * m);
+        for (int t = 0; t < m; ++t)
+          for (int j = 0; j < L; ++j) {
+            C[(size_t)j * m + t] = Y[qs[t]][j];
+            C[(size_t)(L + j) * m + t] = -theta[qs[t]] * Y[qs[t]][j];
+          }
+        to_dev(c, C.data(), cdev, (int64_t)2 * L * m);
+      };
+      std::vector<int> all(nroots);
+      for (int q = 0; q < nroots; ++q) all[q] = q;
+      coef(all);
+      {
+        VecMat a;
+        a.X = Rows().add(S, L, N).add(B, L, N);
+        a.m = nroots;
+        a.C = cdev;
+        a.norm2 = n2dev;
+        vecmat(c.L, N, a, vscr);
+        double h[kVecMatOut];
+        CCLR_CK(cudaMemcpyAsync(h, n2dev, sizeof(double) * nroots, cudaMemcpyDeviceToHost, c.stream));
+        c.sync();
+        for (int q = 0; q < nroots; ++q) rn[q] = std::sqrt(std::max(0.0, h[q]));
+      }
+      std::vector<int> open;
+      double mx = 0.0;
+      for (int q = 0; q < nroots; ++q) {
+        const double tol_q =
+            c.opt.precision == CCLR_FP64 ? c.opt.tol : std::max(c.opt.tol, 1e-5 * std::max(1.0, std::abs(theta[q])));
+        if (rn[q] >= tol_q) open.push_back(q);
+        mx = std::max(mx, rn[q] / tol_q);
+      }
+      if (verbose)
+        std::fprintf(stderr, "[cclr] eom it %d L %d open %zu/%d max|r|/tol %.3e lowest %.10f\n", it, L, open.size(),
+                     nroots, mx, theta[0].real());
+      if (!open.empty() && c.opt.precision != CCLR_FP64) {   // stagnation within 5x the floor
+        if (mx < 0.8 * best) { best = mx; best_it = it; }
+        if (it - best_it >= 4 && mx < 5.0) open.clear();
+      }
+      if (open.empty()) break;
+      if (it == c.opt.maxit) throw Error(CCLR_E_NOCONV, "cc_eom_ee did not converge within maxit iterations");
+      // compress onto the lowest Ritz vectors when the space cannot take the new directions
+      if (L + (int)open.size() > maxL) {
+        const int kk = std::min(L, std::max(2 * nroots, maxL / 2));
+        std::vector<std::vector<zc>> Q;   // B^H B-orthonormal combinations of the lowest Ritz vectors
+        for (int t = 0; t < kk; ++t) {
+          std::vector<zc> y;
+          ritz(ord[t], y);
+          for (int pass = 0; pass < 2; ++pass)
+            for (auto& u : Q) {
+              zc d(0);
+              for (int i = 0; i < L; ++i) {
+                zc r(0);
+                for (int j = 0; j < L; ++j) r += BB[(size_t)i * maxL + j] * y[j];
+                d += std::conj(u[i]) * r;
+              }
+              for (int i = 0; i < L; ++i) y[i] -= d * u[i];
+            }
+          double n2 = 0.0;
+          for (int i = 0; i < L; ++i) {
+            zc r(0);
+            for (int j = 0; j < L; ++j) r += BB[(size_t)i * maxL + j] * y[j];
+            n2 += (std::conj(y[i]) * r).real();
+          }
+          if (!(n2 > 1e-20)) continue;
+          for (auto& x : y) x /= std::sqrt(n2);
+          Q.push_back(y);
+        }
+        const int k2 = (int)Q.size();
+        std::vector<zc> W((size_t)L * k2);
+        for (int j = 0; j < L; ++j)
+          for (int a = 0; a < k2; ++a) W[(size_t)j * k2 + a] = Q[a][j];
+        Scope s2(c.ws);
+        cplx* tmp = c.ws.cplxs((int64_t)k2 * N);
+        for (cplx* X : {B, S}) {
+          combine(c, rows(c, X, L), k2, W, tmp);
+          copy_vec(c.L, (int64_t)k2 * N, tmp, X);
+        }
+        auto congr = [&](std::vector<zc>& Mx) {
+          std::vector<zc> out((size_t)maxL * maxL, zc(0));
+          for (int a = 0; a < k2; ++a)
+            for (int b = 0; b < k2; ++b) {
+              zc acc(0);
+              for (int i = 0; i < L; ++i) {
+                zc r(0);
+                for (int j = 0; j < L; ++j) r += Mx[(size_t)i * maxL + j] * Q[b][j];
+                acc += std::conj(Q[a][i]) * r;
+              }
+              out[(size_t)a * maxL + b] = acc;
+            }
+          Mx.swap(out);
+        };
+        congr(BS);
+        congr(BB);
+        L = k2;
+        fresh = 0;
+        continue;   // the Ritz pairs of the compressed space are formed before new corrections
+      }
+      // preconditioned corrections of the open roots, one pass; then projection and selection
+      coef(open);
+      std::vector<zc> zq(open.size());
+      for (size_t t = 0; t < open.size(); ++t) zq[t] = theta[open[t]];
+      to_dev(c, zq.data(), zdev, (int64_t)open.size());
+      double pre2[kVecMatOut];
+      {
+        VecMat a;
+        a.X = Rows().add(S, L, N).add(B, L, N);
+        a.m = (int)open.size();
+        a.C = cdev;
+        a.Y = R;
+        a.ldy = N;
+        a.D = c.D;
+        a.z = zdev;
+        a.norm2 = n2dev;
+        a.norm_y = true;
+        vecmat(c.L, N, a, vscr);
+        CCLR_CK(cudaMemcpyAsync(pre2, n2dev, sizeof(double) * open.size(), cudaMemcpyDeviceToHost, c.stream));
+        c.sync();
+      }
+      const int kk = add_corrections(c, B, L, R, (int)open.size(), pre2, std::min((int)open.size(), maxL - L), cdev,
+                                     vscr);
+      if (kk == 0) throw Error(CCLR_E_NOCONV, "cc_eom_ee stagnated: no new direction");
+      L += kk;
+      fresh = kk;
+    }
+    // eigenvectors x_q = B y_q (unit norm up to the Galerkin metric)
+    for (int q = 0; q < nroots; ++q) {
+      cplx* v = c.dalloc(N);
+      std::vector<zc> W(Y[q].begin(), Y[q].begin() + L);
+      combine(c, rows(c, B, L), 1, W, v);
+      c.eom_vecs.push_back(v);
+    }
+    c.eom_w = theta;
+  } catch (...) {
+    cleanup();
+    throw;
+  }
+  cleanup();
+  w_out = c.eom_w;
+  return iters;
 }
 
 }  // namespace cclr

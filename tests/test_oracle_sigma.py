@@ -63,6 +63,15 @@ def test_two_electron_jacobian_eigenvalues_are_fci_excitations():
     assert np.abs(ev - (w[1:] - w[0])).max() < 1e-11
 
 
+def test_eom_energies_are_the_lowest_fci_excitations():
+    """The oracle's EOM-EE roots (lowest by real part) == the lowest FCI excitation energies."""
+    inst = synth.make_instance(2, 8, seed=11, sd=0.05)
+    s = response.CCSystem(Ints.from_instance(inst))
+    got = s.eom_energies(4)
+    w = det.fci_energies(inst.fock, synth.full_eri(inst), 2)
+    assert np.abs(got - (w[1:5] - w[0])).max() < 1e-11
+
+
 def test_pins_detect_planted_mistakes():
     """A plausible slip in one Hbar element (sign, conjugation, index order) breaks the pin."""
     inst, F, I = general_case(3, 5)
