@@ -253,6 +253,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-breakdown", action="store_true", help="skip the per-kernel timing step")
     ap.add_argument("--no-accuracy", action="store_true", help="skip the mixed-vs-FP64 accuracy check")
+    ap.add_argument("--no-extra", action="store_true", help="skip the CC-CI and EOM-EE measurements")
     ap.add_argument("--workload", default="30x200", choices=sorted(WORKLOADS))
     ap.add_argument("--gemm", default=None, metavar="M,N,K",
                     help="time only the tensor-core complex GEMM C = A B^T on one shape (kernel profiling)")
@@ -365,6 +366,23 @@ def main():
         top = sorted(bd.items(), key=lambda kv: -kv[1][1])[:12]
         breakdown = dict(note="one untimed step, CUDA events around every launch", total_ms=tot,
                          kernels=[dict(name=k, launches=n, ms=ms, share=ms / tot) for k, (n, ms) in top])
+    # the next rows on the same converged state: CC-CI response function (no Hessian products)
+    # and the four lowest EOM-EE roots (right sigma Davidson)
+    extra = None
+    if rank == 0 and not args.no_extra:
+        t0 = time.perf_counter()
+        ci = ctx.cc_response_function_ci()
+        t_ci = time.perf_counter() - t0
+        alpha_ci = -ci
+        t0 = time.perf_counter()
+        roots, eom_its = ctx.cc_eom_ee(4)
+        t_eom = time.perf_counter() - t0
+        s1 = ctx.cclr_get_stats()
+        extra = dict(cc_ci_seconds=t_ci,
+                     cc_ci_alpha_mean_last_freq=[float(np.trace(alpha_ci[-1]).real / 3),
+                                                 float(np.trace(alpha_ci[-1]).imag / 3)],
+                     eom_ee_roots=[[float(r.real), float(r.imag)] for r in roots], eom_ee_iterations=eom_its,
+                     eom_ee_sigma_products=s1["sigma_vectors"], eom_ee_seconds=t_eom)
     # accuracy of the mixed-precision step against the FP64 path, on the 12/90 replica (the FP64
     # step at the full workload takes ~13 min): 16 frequencies, every component of alpha
     accuracy = None
@@ -398,6 +416,7 @@ def main():
                       launches=prof["launches"], kernel_ms_per_step=prof["ms"] / args.steps,
                       useful_complex_tflops=(prof["flops_useful"] / (prof["ms"] / 1e3) / 1e12 if prof["ms"] else None)),
         cpu_baseline=cpu, e2e=e2e, fp64=fp64, kernel_breakdown=breakdown, accuracy_vs_fp64=accuracy,
+        next_rows=extra,
         gpu_launches=int(sum(s["launches"] for s in stats)),
         clocks=clk.summary(),
         alpha_mean_last_freq=[float(np.trace(alpha[-1]).real / 3), float(np.trace(alpha[-1]).imag / 3)],

@@ -191,3 +191,21 @@ def test_eom_ee_tensor_cores_match_fp64(pk):
         w[prec], _ = ctx.cc_eom_ee(3)
         ctx.close()
     assert np.abs(w[pk.TC_BF16X3] - w[pk.FP64]).max() < 2e-5 * np.abs(w[pk.FP64]).max()
+
+
+def test_mixed_electric_magnetic_operators(pk):
+    """Optical-rotation operator pair (real symmetric mu, imaginary antisymmetric m) through the
+    same path: both response forms against the oracle at (3,8), damped frequencies."""
+    from test_oracle_response import mixed_operators
+    inst = synth.make_instance(3, 8, seed=21, sd=0.05)
+    ops = mixed_operators(inst.n_occ + inst.n_vir, 4)
+    s = R.CCSystem(Ints.from_instance(inst))
+    omegas, gamma = [0.05, 0.3], 0.01
+    zs = [w + 1j * gamma for w in omegas]
+    ctx = make_ctx(pk, inst, tol=1e-10, ground_tol=1e-11)
+    ctx.cc_ground()
+    ctx.cc_lambda()
+    ctx.cc_lr_solve(ops, omegas, gamma)
+    assert rel(ctx.cc_response_function(), s.response(ops, zs, tol=1e-11)) < TOL
+    assert rel(ctx.cc_response_function_ci(), s.response(ops, zs, tol=1e-11, form="ci")) < TOL
+    ctx.close()

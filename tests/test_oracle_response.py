@@ -48,6 +48,30 @@ def test_cc_ci_differs_from_cc_cc_beyond_two_electrons():
     assert np.abs(ci[1] - np.conj(ci[0])).max() < 1e-11 * np.abs(ci).max()
 
 
+def mixed_operators(n, seed):
+    """An electric-dipole-like real symmetric matrix and a magnetic-dipole-like Hermitian matrix
+    that is purely imaginary (i times a real antisymmetric one): the operator pair of optical
+    rotation, G'(w) = -Im <<mu; m>>."""
+    rng = np.random.default_rng(seed)
+    a = rng.normal(0, 0.1, (n, n))
+    b = rng.normal(0, 0.1, (n, n))
+    return np.stack([(a + a.T) / 2 + 0j, 1j * (b - b.T) / 2])
+
+
+def test_two_electron_mixed_electric_magnetic_operators():
+    """<<mu; m>> for an electric and a magnetic-type operator equals the exact sum over states,
+    both response forms."""
+    inst = synth.make_instance(2, 8, seed=11, sd=0.05)
+    ops = mixed_operators(inst.n_occ + inst.n_vir, 4)
+    s = R.CCSystem(Ints.from_instance(inst))
+    sos, _ = det.fci_response(inst.fock, synth.full_eri(inst), 2, ops, ZS)
+    A = s.dense_A()
+    for form in ("cc", "ci"):
+        got = s.response(ops, ZS, solver="dense", A=A, form=form)
+        assert np.abs(got - sos).max() < 1e-11 * np.abs(sos).max()
+    assert np.abs(sos[1, 0, 1]) > 1e-6   # the mixed element is not trivially zero
+
+
 def test_lambda_matches_dense_left_solve():
     inst = synth.make_instance(2, 6, seed=3, sd=0.1)
     s = R.CCSystem(Ints.from_instance(inst))
