@@ -209,3 +209,54 @@ def test_mixed_electric_magnetic_operators(pk):
     assert rel(ctx.cc_response_function(), s.response(ops, zs, tol=1e-11)) < TOL
     assert rel(ctx.cc_response_function_ci(), s.response(ops, zs, tol=1e-11, form="ci")) < TOL
     ctx.close()
+
+
+def test_autograd_residual_backward_is_the_left_sigma(pk):
+    """d Re(w^H Omega(t)) along random complex directions d: the autograd gradient (backward =
+    conj(left sigma(conj g))) against a 5-point central difference (exact for the quartic Omega)."""
+    import torch
+    from paper_2307_14296_b300 import autograd as ag
+    inst = synth.make_instance(3, 8, seed=21, sd=0.05)
+    ctx = make_ctx(pk, inst)
+    n = ctx.N
+    rng = np.random.default_rng(5)
+    t0 = 0.05 * (rng.standard_normal(n) + 1j * rng.standard_normal(n))
+    w = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    t = torch.tensor(t0, requires_grad=True)
+    loss = (torch.tensor(w).conj() * ag.ccsd_residual(t, ctx)).sum().real
+    loss.backward()
+    grad = t.grad.numpy()
+
+    def L(x):
+        ctx.cclr_set_amplitudes(pk.AMP_T, x)
+        return float((np.conj(w) * ctx.cclr_residual()[0]).sum().real)
+    for k in range(3):
+        d = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+        h = 1e-3
+        fd = (L(t0 - 2 * h * d) - 8 * L(t0 - h * d) + 8 * L(t0 + h * d) - L(t0 + 2 * h * d)) / (12 * h)
+        assert abs(fd - float(np.real(np.vdot(grad, d)))) < 1e-8 * abs(fd)
+    ctx.close()
+
+
+def test_alpha_directional_derivative_is_exact(pk):
+    """alpha is quadratic in the operator, so the central difference along dX is exact: the
+    derivative from the bilinear response function matches it to the solver tolerance."""
+    from paper_2307_14296_b300 import autograd as ag
+    inst = synth.make_instance(3, 8, seed=21, sd=0.05)
+    X = inst.ops[0]
+    rng = np.random.default_rng(9)
+    a = rng.normal(0, 0.1, X.shape) + 1j * rng.normal(0, 0.1, X.shape)
+    dX = (a + a.conj().T) / 2
+    omegas, gamma = [0.05, 0.3], 0.01
+    ctx = make_ctx(pk, inst, tol=1e-11, ground_tol=1e-12)
+    ctx.cc_ground()
+    ctx.cc_lambda()
+    got = ag.alpha_directional_derivative(ctx, X, dX, omegas, gamma)
+
+    def alpha(op):
+        ctx.cc_lr_solve(op[None], omegas, gamma)
+        return -ctx.cc_response_function()[:, 0, 0]
+    h = 0.1
+    fd = (alpha(X + h * dX) - alpha(X - h * dX)) / (2 * h)
+    assert np.abs(got - fd).max() < 1e-8 * np.abs(fd).max()
+    ctx.close()
