@@ -915,7 +915,7 @@ int eom_ee(Ctx& c, int nroots, std::vector<zc>& w_out) {
   const int64_t N = c.N;
   CCLR_REQUIRE(N > nroots, CCLR_E_ARG, "cc_eom_ee: more roots than excitations");
   const int maxL = std::min<int>(kVecMatMaxRows / 2, std::max(c.opt.max_subspace, 6 * nroots));
-  const int nstart = (int)std::min<int64_t>(N, std::max(2 * nroots, nroots + 2));
+  const int nstart = (int)std::min<int64_t>(N, std::max(3 * nroots, 8));
   for (auto p : c.eom_vecs) c.dfree(p);
   c.eom_vecs.clear();
   c.eom_w.clear();
