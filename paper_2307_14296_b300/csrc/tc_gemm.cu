@@ -149,11 +149,11 @@ __device__ __forceinline__ double epi_f2d(float x) {
 __device__ __forceinline__ void mbar_arrive(uint64_t* b) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
 }
-// OR of q over the 128 epilogue threads (named barrier 1; all of them must call it)
+// OR of q over the 256 epilogue threads (named barrier 1; all of them must call it)
 __device__ __forceinline__ bool group_any(bool q) {
   uint32_t r;
   asm volatile(
-      "{\n .reg .pred p, q;\n setp.ne.u32 q, %1, 0;\n bar.red.or.pred p, 1, 128, q;\n selp.u32 %0, 1, 0, p;\n}\n"
+      "{\n .reg .pred p, q;\n setp.ne.u32 q, %1, 0;\n bar.red.or.pred p, 1, 256, q;\n selp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(r)
       : "r"((uint32_t)q)
       : "memory");
@@ -163,11 +163,16 @@ __device__ __forceinline__ bool group_any(bool q) {
 // Persistent, warp-specialised kernel: one CTA per SM walks the tiles t = blockIdx.x + i gridDim.x
 // (tile = (m-tile fastest, n-tile, split-K slice z)).  Warp 0 lane 0 streams operand tiles into a
 // STAGES-deep shared-memory ring with TMA, warp 1 lane 0 issues tcgen05.mma into one of two TMEM
-// accumulators (Cr | Ci, 2 x 256 columns), and warps 2..5 drain the other accumulator to C, so a
-// tile's epilogue overlaps the next tile's MMAs.  Every mbarrier wait is bounded; on expiry the
+// accumulators (Cr | Ci, 2 x 256 columns), and warps 2..9 drain the other accumulator to C (two
+// warps per TMEM lane quarter, alternate 32-column chunks: short-K contractions are bound by this
+// read-modify-write of C), so a tile's epilogue overlaps the next tile's MMAs.  Every mbarrier wait is bounded; on expiry the
 // kernel records an error code, stops issuing work, waits (bounded) for its MMAs, frees TMEM and
 // returns.
-__global__ void __launch_bounds__(192, 1)
+constexpr int EPI_WARPS = 8;
+constexpr int EPI_THREADS = 32 * EPI_WARPS;
+constexpr int TC_THREADS = 64 + EPI_THREADS;
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
     k_tc_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int n_rows, int m_rows,
                int kblocks, int kb_per, Pairs pairs, double2 alpha, double2 beta, double2* __restrict__ C, int64_t ldc,
                int64_t cz, int* __restrict__ err, int xtiles, int ytiles, int nsplit, const OutMap om, bool strided) {
@@ -176,7 +181,7 @@ __global__ void __launch_bounds__(192, 1)
   uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
   uint64_t* empty = full + STAGES;
   uint64_t* tfull = empty + STAGES;    // accumulator b holds a finished tile (MMA commit)
-  uint64_t* tempty = tfull + 2;        // accumulator b drained (128 epilogue threads)
+  uint64_t* tempty = tfull + 2;        // accumulator b drained (all epilogue threads)
   uint64_t* done = tempty + 2;         // every MMA of this CTA has completed
   uint32_t* tmem_slot = (uint32_t*)(done + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
@@ -189,7 +194,7 @@ __global__ void __launch_bounds__(192, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], 128);
+      mbar_init(&tempty[b], EPI_THREADS);
     }
     mbar_init(done, 1);
     *abort_flag = 0;
@@ -271,9 +276,11 @@ __global__ void __launch_bounds__(192, 1)
       mma_commit(done);
     }
   } else {
-    // ---------------- epilogue warps 2..5: TMEM lanes 32 (warp % 4) .. +32
-    const int et = threadIdx.x - 64;                 // 0..127
+    // ---------------- epilogue warps 2..9: TMEM lanes 32 (warp % 4) .. +32, column chunks
+    // starting at 32 ch, ch = (warp - 2) / 4, in steps of 64
+    const int et = threadIdx.x - 64;                 // 0..EPI_THREADS-1
     const int lg = warp & 3;                         // TMEM lane quarter of this warp
+    const int ch = (warp - 2) >> 2;
     const uint32_t lane_base = (uint32_t)(lg * 32) << 16;
     // The accumulators are FP32: alpha is applied in FP32 and the result widened on the integer
     // pipe (FP64 arithmetic and FP32 <-> FP64 cvt issue on the FP64 pipe, ~1/64 of the FP32 rate
@@ -281,7 +288,7 @@ __global__ void __launch_bounds__(192, 1)
     const bool use_beta = (beta.x != 0.0 || beta.y != 0.0);
     const bool beta_one = (beta.x == 1.0 && beta.y == 0.0);
     const float ar = (float)alpha.x, ai = (float)alpha.y;
-    // Control flow stays uniform across the 128 epilogue threads: every exit decision is taken
+    // Control flow stays uniform across the epilogue threads: every exit decision is taken
     // through a barrier reduction over named barrier 1, so no thread is left waiting in it.
     int tl = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++tl) {
@@ -290,7 +297,7 @@ __global__ void __launch_bounds__(192, 1)
       const int b = tl & 1;
       double2* Cz = C + (int64_t)z * cz;
       int64_t* mo = moff + b * BN;
-      if (strided) {
+      if (strided && et < BN) {
         const int m = m0 + et;
         mo[et] = m < m_rows ? out_off((uint32_t)m, om.nm, om.mdim, om.mstr, om.mmul, om.mshr) : 0;
       }
@@ -306,7 +313,7 @@ __global__ void __launch_bounds__(192, 1)
       fence_after();
       const uint32_t acc = tmem + b * TMEM_COLS + lane_base;
 #pragma unroll 1
-      for (int c0 = 0; c0 < BN; c0 += 32) {
+      for (int c0 = 32 * ch; c0 < BN; c0 += 64) {
         uint32_t rr[32], ri[32];
         tmem_ld32(acc + c0, rr);
         tmem_ld32(acc + BN + c0, ri);
@@ -744,11 +751,11 @@ void tc_gemm_views(Ctx& c, const Tensor& vm, int nrm, const Tensor& vn, int nrn,
     const int grid = (int)std::min<int64_t>(xtiles * ytiles * S, 148);
     c.kt.begin(c.stream);
     if (S > 1)
-      tc::k_tc_zgemm<<<grid, 192, tc::SMEM_BYTES, c.stream>>>(sn.tm, sm.tm, (int)N, (int)M, kblocks, kb_per, pairs,
+      tc::k_tc_zgemm<<<grid, tc::TC_THREADS, tc::SMEM_BYTES, c.stream>>>(sn.tm, sm.tm, (int)N, (int)M, kblocks, kb_per, pairs,
                                                               make_double2(1.0, 0.0), make_double2(0.0, 0.0), P, N,
                                                               M * N, c.tc_err, (int)xtiles, (int)ytiles, S, om, false);
     else
-      tc::k_tc_zgemm<<<grid, 192, tc::SMEM_BYTES, c.stream>>>(sn.tm, sm.tm, (int)N, (int)M, kblocks, kb_per, pairs,
+      tc::k_tc_zgemm<<<grid, tc::TC_THREADS, tc::SMEM_BYTES, c.stream>>>(sn.tm, sm.tm, (int)N, (int)M, kblocks, kb_per, pairs,
                                                               alpha, beta, C, ldc, 0, c.tc_err, (int)xtiles, (int)ytiles,
                                                               1, om, strided);
     const cudaError_t le = cudaGetLastError();
@@ -842,11 +849,11 @@ int tc_raw_gemm_nt(int precision, int64_t M, int64_t N, int64_t K, const cplx* A
   {
     const int grid = (int)std::min<int64_t>(xtiles * ytiles * p.S, 148);
     if (p.S > 1)
-      tc::k_tc_zgemm<<<grid, 192, tc::SMEM_BYTES, stream>>>(tn, tm, (int)N, (int)M, p.kblocks, p.kb_per, pairs, one,
+      tc::k_tc_zgemm<<<grid, tc::TC_THREADS, tc::SMEM_BYTES, stream>>>(tn, tm, (int)N, (int)M, p.kblocks, p.kb_per, pairs, one,
                                                             zero, P, N, M * N, err, (int)xtiles, (int)ytiles, p.S,
                                                             tc::OutMap(), false);
     else
-      tc::k_tc_zgemm<<<grid, 192, tc::SMEM_BYTES, stream>>>(tn, tm, (int)N, (int)M, p.kblocks, p.kb_per, pairs, one,
+      tc::k_tc_zgemm<<<grid, tc::TC_THREADS, tc::SMEM_BYTES, stream>>>(tn, tm, (int)N, (int)M, p.kblocks, p.kb_per, pairs, one,
                                                             zero, C, N, 0, err, (int)xtiles, (int)ytiles, 1,
                                                             tc::OutMap(), false);
     CCLR_CK(cudaGetLastError());
