@@ -462,6 +462,84 @@ __global__ void __launch_bounds__(256) k_split_view(const double2* __restrict__ 
   }
 }
 
+// Transposing split, for views whose unit-stride index is a row index while the K index runs
+// with a large stride (e.g. the ring-layout doubles contracted over (m, n, e)): a tile of 32
+// consecutive values of the unit-stride row axis U x 64 K values is read into shared memory with
+// loads contiguous along U, then written as BF16 slices contiguous along K.  Tiles are
+// (other row indices, U chunk, K chunk), K chunk fastest.
+struct SplitT {
+  int u;                         // the unit-stride row axis of the view
+  int64_t rstride[kMaxRank];     // row-index stride of every row axis in the [rows][Kpad] output
+  uint32_t n_cu, n_ck;           // U chunks of 32, K chunks of 64
+  uint32_t mul_cu, mul_ck;       // Granlund-Montgomery multipliers of n_cu, n_ck
+  int shr_cu, shr_ck;
+};
+
+__global__ void __launch_bounds__(256) k_split_view_t(const double2* __restrict__ X, ViewArgs v, SplitT s,
+                                                      int64_t rows, int64_t K, bool conj, int nsl,
+                                                      __nv_bfloat16* __restrict__ out, int64_t Kpad, int64_t ntiles) {
+  __shared__ double2 tile[64][33];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t plane = rows * Kpad;
+  uint32_t* o32 = reinterpret_cast<uint32_t*>(out);
+  const int64_t dimU = v.dim[s.u];
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    uint32_t r = (uint32_t)t;
+    const uint32_t q1 = (uint32_t)(((uint64_t)__umulhi(r, s.mul_ck) + r) >> s.shr_ck);
+    const uint32_t ck = r - q1 * s.n_ck;
+    const uint32_t q2 = (uint32_t)(((uint64_t)__umulhi(q1, s.mul_cu) + q1) >> s.shr_cu);
+    const uint32_t cu = q1 - q2 * s.n_cu;
+    uint32_t o = q2;   // index over the row axes other than U (row-major)
+    int64_t soff = 0, rbase = 0;
+#pragma unroll
+    for (int a = kMaxRank - 1; a >= 0; --a) {
+      if (a >= v.nr || a == s.u) continue;
+      const uint32_t q = (uint32_t)(((uint64_t)__umulhi(o, v.mul[a]) + o) >> v.shr[a]);
+      const int64_t idx = (int64_t)(o - q * (uint32_t)v.dim[a]);
+      soff += idx * v.str[a];
+      rbase += idx * s.rstride[a];
+      o = q;
+    }
+    const int64_t u0 = (int64_t)cu * 32, k0 = (int64_t)ck * 64;
+    // read: lanes along U (unit stride), warps over K
+    for (int kk = warp; kk < 64; kk += 8) {
+      const int64_t k = k0 + kk;
+      double2 x = make_double2(0.0, 0.0);
+      if (k < K && u0 + lane < dimU) x = X[soff + (u0 + lane) + view_off(v, v.nr, v.rank, (uint32_t)k)];
+      tile[kk][lane] = x;
+    }
+    __syncthreads();
+    // write: warp w takes rows w, w+8, w+16, w+24 of the tile; lane p the K pair (2p, 2p+1)
+    for (int j = warp; j < 32; j += 8) {
+      if (u0 + j >= dimU) continue;
+      const int64_t row = rbase + (u0 + j) * s.rstride[s.u];
+      float re[2], im[2];
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const double2 x = tile[2 * lane + e][j];
+        re[e] = split_d2f(x.x);
+        im[e] = split_d2f(conj ? -x.y : x.y);
+      }
+      const int64_t e2 = row * (Kpad / 2) + (k0 / 2) + lane;
+#pragma unroll
+      for (int sl = 0; sl < 3; ++sl) {
+        if (sl >= nsl) break;
+        uint32_t br[2], bi[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          br[e] = bf16_bits(re[e]);
+          bi[e] = bf16_bits(im[e]);
+          re[e] -= __uint_as_float(br[e] << 16);
+          im[e] -= __uint_as_float(bi[e] << 16);
+        }
+        o32[((2 * sl + 0) * plane) / 2 + e2] = br[0] | (br[1] << 16);
+        o32[((2 * sl + 1) * plane) / 2 + e2] = bi[0] | (bi[1] << 16);
+      }
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace tc
 
 namespace {
@@ -555,6 +633,36 @@ void launch_split(const Tensor& v, int nr, int64_t rows, int64_t K, int64_t Kpad
                   cudaStream_t stream) {
   CCLR_REQUIRE(rows < (int64_t(1) << 31) && K < (int64_t(1) << 31), CCLR_E_ARG, "tensor-core split: operand too large");
   const tc::ViewArgs a = view_args(v, nr);
+  // transposing variant: a row axis has unit stride while the innermost K axis does not
+  int u = -1;
+  for (int i = 0; i < a.nr; ++i)
+    if (a.str[i] == 1 && a.dim[i] >= 16) u = i;
+  if (u >= 0 && a.str[a.rank - 1] != 1) {
+    tc::SplitT st{};
+    st.u = u;
+    int64_t rs = 1;
+    for (int i = a.nr - 1; i >= 0; --i) {
+      st.rstride[i] = rs;
+      rs *= a.dim[i];
+    }
+    const int64_t n_other = rows / a.dim[u];
+    const int64_t n_cu = (a.dim[u] + 31) / 32, n_ck = Kpad / 64;
+    const int64_t ntiles = n_other * n_cu * n_ck;
+    CCLR_REQUIRE(ntiles < (int64_t(1) << 32), CCLR_E_ARG, "tensor-core split: operand too large");
+    auto magic = [](int64_t d, uint32_t& mul, int& shr) {
+      int l = 0;
+      while ((int64_t(1) << l) < d) ++l;
+      shr = l;
+      mul = (uint32_t)(((unsigned __int128)1 << 32) * (((uint64_t)1 << l) - (uint64_t)d) / (uint64_t)d + 1);
+    };
+    st.n_cu = (uint32_t)n_cu;
+    st.n_ck = (uint32_t)n_ck;
+    magic(n_cu, st.mul_cu, st.shr_cu);
+    magic(n_ck, st.mul_ck, st.shr_ck);
+    const int g = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, 148 * 8));
+    tc::k_split_view_t<<<g, 256, 0, stream>>>(v.p, a, st, rows, K, v.conj, nsl, dst, Kpad, ntiles);
+    return;
+  }
   const int64_t nchunk = (Kpad / 2 + tc::kSplitPairs - 1) / tc::kSplitPairs;
   CCLR_REQUIRE(rows * nchunk < (int64_t(1) << 32), CCLR_E_ARG, "tensor-core split: operand too large");
   int l = 0;
