@@ -124,14 +124,11 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,"
-      "%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
@@ -149,11 +146,11 @@ __device__ __forceinline__ double epi_f2d(float x) {
 __device__ __forceinline__ void mbar_arrive(uint64_t* b) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
 }
-// OR of q over the 256 epilogue threads (named barrier 1; all of them must call it)
+// OR of q over the 384 epilogue threads (named barrier 1; all of them must call it)
 __device__ __forceinline__ bool group_any(bool q) {
   uint32_t r;
   asm volatile(
-      "{\n .reg .pred p, q;\n setp.ne.u32 q, %1, 0;\n bar.red.or.pred p, 1, 256, q;\n selp.u32 %0, 1, 0, p;\n}\n"
+      "{\n .reg .pred p, q;\n setp.ne.u32 q, %1, 0;\n bar.red.or.pred p, 1, 384, q;\n selp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(r)
       : "r"((uint32_t)q)
       : "memory");
@@ -163,12 +160,12 @@ __device__ __forceinline__ bool group_any(bool q) {
 // Persistent, warp-specialised kernel: one CTA per SM walks the tiles t = blockIdx.x + i gridDim.x
 // (tile = (m-tile fastest, n-tile, split-K slice z)).  Warp 0 lane 0 streams operand tiles into a
 // STAGES-deep shared-memory ring with TMA, warp 1 lane 0 issues tcgen05.mma into one of two TMEM
-// accumulators (Cr | Ci, 2 x 256 columns), and warps 2..9 drain the other accumulator to C (two
-// warps per TMEM lane quarter, alternate 32-column chunks: short-K contractions are bound by this
-// read-modify-write of C), so a tile's epilogue overlaps the next tile's MMAs.  Every mbarrier wait is bounded; on expiry the
+// accumulators (Cr | Ci, 2 x 256 columns), and warps 2..13 drain the other accumulator to C
+// (three warps per TMEM lane quarter, 16-column chunks in turn: short-K contractions are bound by
+// this read-modify-write of C), so a tile's epilogue overlaps the next tile's MMAs.  Every mbarrier wait is bounded; on expiry the
 // kernel records an error code, stops issuing work, waits (bounded) for its MMAs, frees TMEM and
 // returns.
-constexpr int EPI_WARPS = 8;
+constexpr int EPI_WARPS = 12;
 constexpr int EPI_THREADS = 32 * EPI_WARPS;
 constexpr int TC_THREADS = 64 + EPI_THREADS;
 
@@ -276,8 +273,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       mma_commit(done);
     }
   } else {
-    // ---------------- epilogue warps 2..9: TMEM lanes 32 (warp % 4) .. +32, column chunks
-    // starting at 32 ch, ch = (warp - 2) / 4, in steps of 64
+    // ---------------- epilogue warps 2..13: TMEM lanes 32 (warp % 4) .. +32, 16-column chunks
+    // starting at 16 ch, ch = (warp - 2) / 4, in steps of 48
     const int et = threadIdx.x - 64;                 // 0..EPI_THREADS-1
     const int lg = warp & 3;                         // TMEM lane quarter of this warp
     const int ch = (warp - 2) >> 2;
@@ -313,40 +310,37 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       fence_after();
       const uint32_t acc = tmem + b * TMEM_COLS + lane_base;
 #pragma unroll 1
-      for (int c0 = 32 * ch; c0 < BN; c0 += 64) {
-        uint32_t rr[32], ri[32];
-        tmem_ld32(acc + c0, rr);
-        tmem_ld32(acc + BN + c0, ri);
+      for (int c0 = 16 * ch; c0 < BN; c0 += 16 * (EPI_WARPS / 4)) {
+        uint32_t rr[16], ri[16];
+        tmem_ld16(acc + c0, rr);
+        tmem_ld16(acc + BN + c0, ri);
         if (n < n_rows) {
-          // 16 columns at a time: the beta operands are all loaded before any is used
-#pragma unroll 1
-          for (int h = 0; h < 32; h += 16) {
-            double2 old[16];
-            if (use_beta) {
-#pragma unroll
-              for (int j = 0; j < 16; ++j) {
-                const int m = m0 + c0 + h + j;
-                if (m < m_rows) old[j] = *(strided ? Cz + mo[c0 + h + j] + noff : Cz + (int64_t)m * ldc + n);
-              }
-            }
+          // the beta operands of the chunk are all loaded before any is used
+          double2 old[16];
+          if (use_beta) {
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
-              const int m = m0 + c0 + h + j;
-              if (m < m_rows) {
-                const float xr = __uint_as_float(rr[h + j]), xi = __uint_as_float(ri[h + j]);
-                double2 v = make_double2(epi_f2d(ar * xr - ai * xi), epi_f2d(ar * xi + ai * xr));
-                if (use_beta) {
-                  const double2 o = old[j];
-                  if (beta_one) {
-                    v.x += o.x;
-                    v.y += o.y;
-                  } else {
-                    v.x += beta.x * o.x - beta.y * o.y;
-                    v.y += beta.x * o.y + beta.y * o.x;
-                  }
+              const int m = m0 + c0 + j;
+              if (m < m_rows) old[j] = *(strided ? Cz + mo[c0 + j] + noff : Cz + (int64_t)m * ldc + n);
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int m = m0 + c0 + j;
+            if (m < m_rows) {
+              const float xr = __uint_as_float(rr[j]), xi = __uint_as_float(ri[j]);
+              double2 v = make_double2(epi_f2d(ar * xr - ai * xi), epi_f2d(ar * xi + ai * xr));
+              if (use_beta) {
+                const double2 o = old[j];
+                if (beta_one) {
+                  v.x += o.x;
+                  v.y += o.y;
+                } else {
+                  v.x += beta.x * o.x - beta.y * o.y;
+                  v.y += beta.x * o.y + beta.y * o.x;
                 }
-                *(strided ? Cz + mo[c0 + h + j] + noff : Cz + (int64_t)m * ldc + n) = v;
               }
+              *(strided ? Cz + mo[c0 + j] + noff : Cz + (int64_t)m * ldc + n) = v;
             }
           }
         }
