@@ -742,8 +742,9 @@ void response_function(Ctx& c, cplx* out_host) {
       gram_host(c, rows(c, rd.eta[x], 1), rows(c, rd.basis[y], rd.nb[y]), false, E[(size_t)x * nop + y]);
   auto beta = [&](int k, int f, int s) { return &rd.beta[k][(size_t)rd.shift_of[(size_t)f * 4 + s] * maxL]; };
   // The Hessian acts only on the solutions t^X(-z) and t^X(z*) of every frequency.  Their
-  // coefficient vectors span few directions: compress them (QR with column pivoting, 1e-12
-  // cutoff) to Q_x, form the products F (B^x Q_x) in batches and contract them at once:
+  // coefficient vectors span few directions: compress them (QR with column pivoting, cutoff
+  // 1e-12 of the largest in FP64 mode; 1e-9 in the tensor-core modes, whose sigma products carry
+  // ~1e-5 relative error) to Q_x, form the products F (B^x Q_x) in batches and contract them at once:
   //   M^{xy} = (B^x Q_x F) . B^y,  (t^X F) . t^Y = gamma^T M^{xy} beta^Y,  gamma = Q_x^H beta^X.
   std::vector<std::vector<std::vector<zc>>> Q(nop);
   for (int x = 0; x < nop; ++x) {
@@ -765,7 +766,7 @@ void response_function(Ctx& c, cplx* out_host) {
       if (best < 0) break;
       const double nrm = std::sqrt(bn);
       if (first < 0) first = nrm;
-      if (nrm <= 1e-12 * first) break;
+      if (nrm <= (c.opt.precision == CCLR_FP64 ? 1e-12 : 1e-9) * first) break;
       used[best] = 1;
       std::vector<zc> qv(Lx);
       for (int i = 0; i < Lx; ++i) qv[i] = cols[best][i] / nrm;
