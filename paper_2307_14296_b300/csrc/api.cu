@@ -76,6 +76,7 @@ void free_all(Ctx& c) {
   c.po = c.pv = nullptr;
   c.t = c.t2 = c.lam = c.l2 = nullptr;
   c.Fae = c.Fmi = c.Fme = c.Wmnij = c.Wmnij_p = c.Wabef_p = c.Wmbej = c.WringR = c.WringL = nullptr;
+  c.Fae_od = c.Fmi_od = nullptr;
   c.Wmnie = c.Wamef = c.Wmbij = c.Wabei = c.tau = nullptr;
   c.have_ham = c.have_t = c.have_lambda = c.have_hbar = false;
   if (c.ws.base) { cudaFree(c.ws.base); c.ws = Arena(); }

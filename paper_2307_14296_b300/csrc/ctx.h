@@ -61,6 +61,7 @@ struct Ctx {
 
   // Hbar (creators-first elements, see the oracle's definitions)
   cplx *Fae = nullptr, *Fmi = nullptr, *Fme = nullptr;
+  cplx *Fae_od = nullptr, *Fmi_od = nullptr;             // Fae, Fmi minus the bare Fock diagonal
   cplx *Wmnij = nullptr, *Wmnij_p = nullptr, *Wabef_p = nullptr, *Wmbej = nullptr;
   cplx *WringR = nullptr, *WringL = nullptr;              // (j,b) x (m,e) operands of the rings
   cplx *Wmnie = nullptr, *Wamef = nullptr, *Wmbij = nullptr, *Wabei = nullptr;

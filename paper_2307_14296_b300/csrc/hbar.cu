@@ -15,6 +15,8 @@ void build_hbar(Ctx& c) {
   auto ensure = [&](cplx*& p, int64_t n) { if (!p) p = c.dalloc(n); };
   ensure(c.Fae, v * v);
   ensure(c.Fmi, o * o);
+  ensure(c.Fae_od, v * v);
+  ensure(c.Fmi_od, o * o);
   ensure(c.Fme, o * v);
   ensure(c.Wmnij, o * o * o * o);
   ensure(c.Wmnij_p, Po * Po);
@@ -92,6 +94,53 @@ void build_hbar(Ctx& c) {
   // right ring operand [(j,b)][(m,e)] = W_mbej[m,b,e,j]; left ring operand = W_mbej[j,e,b,m]
   permute(c.L, Wmbej.perm({3, 1, 0, 2}), T(c.WringR, {o, v, o, v}), cx(1), false);
   permute(c.L, Wmbej.perm({0, 2, 3, 1}), T(c.WringL, {o, v, o, v}), cx(1), false);
+  // Fae, Fmi without the bare Fock diagonal: sigma adds that part exactly as D r (D the
+  // orbital-energy differences), so the tensor-core products carry only the rest
+  copy_vec(c.L, v * v, c.Fae, c.Fae_od);
+  copy_vec(c.L, o * o, c.Fmi, c.Fmi_od);
+  {
+    Tensor fv = c.f("vv"), fo = c.f("oo");
+    fv.rank = fo.rank = 1;
+    fv.str[0] = c.n + 1;
+    fo.str[0] = c.n + 1;
+    Tensor dv = Tensor::make(c.Fae_od, {v}), dov = Tensor::make(c.Fmi_od, {o});
+    dv.str[0] = v + 1;
+    dov.str[0] = o + 1;
+    permute(c.L, fv, dv, cx(-1), true);
+    permute(c.L, fo, dov, cx(-1), true);
+  }
+  // The one-index F terms of the doubles sigma are ring terms with a Kronecker delta: the ring
+  // contracts the amplitudes over (m, e), so (weights as the terms enter the accumulator packed
+  // with P(ij)P(ab))
+  //   right: 1/2 F_be r_ij^ae - 1/2 F_mj r_im^ab  ->  W[j,b,m,e] += 1/2 d_jm F_be - 1/2 d_be F_mj
+  //   left:  1/2 l_ij^ae F_eb - 1/2 l_im^ab F_jm  ->  W[j,b,m,e] += 1/2 d_jm F_eb - 1/2 d_be F_jm
+  // and ride in the ring GEMM instead of two read-modify-write passes over the accumulator.
+  {
+    auto view = [](cplx* p, std::initializer_list<int64_t> d, std::initializer_list<int64_t> st) {
+      Tensor t;
+      t.p = p;
+      t.rank = (int)d.size();
+      int i = 0;
+      for (int64_t x : d) t.dim[i++] = x;
+      i = 0;
+      for (int64_t x : st) t.str[i++] = x;
+      return t;
+    };
+    const int64_t sj = v * o * v, sb = o * v, sm = v;   // strides of W[j][b][m][e]
+    for (int side = 0; side < 2; ++side) {
+      cplx* W = side == 0 ? c.WringR : c.WringL;
+      // d_jm: (j, b, e) -> W[j][b][j][e]
+      const Tensor djm = view(W, {o, v, v}, {sj + sm, sb, 1});
+      const Tensor fae = side == 0 ? view(c.Fae_od, {o, v, v}, {0, v, 1})    // F_be
+                                   : view(c.Fae_od, {o, v, v}, {0, 1, v});   // F_eb
+      permute(c.L, fae, djm, cx(0.5), true);
+      // d_be: (j, b, m) -> W[j][b][m][b]
+      const Tensor dbe = view(W, {o, v, o}, {sj, sb + 1, sm});
+      const Tensor fmi = side == 0 ? view(c.Fmi_od, {o, v, o}, {1, 0, o})    // F_mj
+                                   : view(c.Fmi_od, {o, v, o}, {o, 0, 1});   // F_jm
+      permute(c.L, fmi, dbe, cx(-0.5), true);
+    }
+  }
 
   // W_mnie (Eq. W_mnie), W_amef (Eq. W_amef)
   Tensor Wmnie = T(c.Wmnie, {o, o, o, v});

@@ -272,6 +272,8 @@ inline int64_t gram_scratch_elems() { return 148 * 64 * 8; }
 // Small element-wise helpers
 void scale_vec(const Launch& L, int64_t n, cplx a, cplx* x);
 void copy_vec(const Launch& L, int64_t n, const cplx* x, cplx* y);
+// y[z*n + i] += D[i] * x[z*n + i] for z < nvec (FP64): the diagonal part of a sigma product
+void diag_axpy(const Launch& L, int64_t n, int64_t nvec, const double* D, const cplx* x, cplx* y);
 // x_i <- x_i / (D_i - z) * a   (Jacobi update)
 void div_shift(const Launch& L, int64_t n, const cplx* x, const double* D, cplx z, cplx a, cplx* y);
 

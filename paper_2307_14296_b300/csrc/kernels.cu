@@ -335,6 +335,18 @@ __global__ void k_copy(int64_t n, const cplx* __restrict__ x, cplx* y) {
     y[i] = x[i];
 }
 
+__global__ void k_diag_axpy(int64_t n, int64_t total, const double* __restrict__ D, const cplx* __restrict__ x,
+                            cplx* y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const double d = D[i % n];
+    const cplx a = x[i];
+    cplx b = y[i];
+    b.x = fma(d, a.x, b.x);
+    b.y = fma(d, a.y, b.y);
+    y[i] = b;
+  }
+}
+
 __global__ void k_div_shift(int64_t n, const cplx* __restrict__ x, const double* __restrict__ D, cplx z, cplx a,
                             cplx* y) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -1207,6 +1219,15 @@ void copy_vec(const Launch& L, int64_t n, const cplx* x, cplx* y) {
   k_copy<<<grid_for(n), kThreads, 0, L.s>>>(n, x, y);
   CCLR_CK(cudaGetLastError());
   bump(L, "k_copy");
+}
+
+void diag_axpy(const Launch& L, int64_t n, int64_t nvec, const double* D, const cplx* x, cplx* y) {
+  const int64_t total = n * nvec;
+  if (total <= 0) return;
+  kbeg(L);
+  k_diag_axpy<<<grid_for(total), kThreads, 0, L.s>>>(n, total, D, x, y);
+  CCLR_CK(cudaGetLastError());
+  bump(L, "k_diag_axpy");
 }
 
 void div_shift(const Launch& L, int64_t n, const cplx* x, const double* D, cplx z, cplx a, cplx* y) {

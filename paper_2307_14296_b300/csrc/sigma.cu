@@ -76,8 +76,9 @@ void sigma_right(Ctx& c, int nvec, const cplx* in, cplx* out) {
   // ---- singles
   cplx* s1 = c.ws.cplxs(Z * o * v);
   Tensor S1 = T(s1, {Z, o, v});
-  einsum(c, "ae,zie->zia", cx(1), Fae, r.t1, 0.0, S1);
-  einsum(c, "mi,zma->zia", cx(-1), Fmi, r.t1, 1.0, S1);
+  // the Fock-diagonal part of F_ae, F_mi enters exactly as D r at the end
+  einsum(c, "ae,zie->zia", cx(1), T(c.Fae_od, {v, v}), r.t1, 0.0, S1);
+  einsum(c, "mi,zma->zia", cx(-1), T(c.Fmi_od, {o, o}), r.t1, 1.0, S1);
   einsum(c, "me,zimae->zia", cx(1), Fme, r.t2, 1.0, S1);
   einsum(c, "maei,zme->zia", cx(1), Wmbej, r.t1, 1.0, S1);
   einsum(c, "amef,zimef->zia", cx(0.5), Wamef, r.t2, 1.0, S1);
@@ -85,7 +86,7 @@ void sigma_right(Ctx& c, int nvec, const cplx* in, cplx* out) {
   // ---- doubles
   cplx* x4 = c.ws.cplxs(Z * o * o * v * v);
   Tensor X4 = ring_layout(x4, Z, o, v);
-  // ring first (beta = 0 initializes X4)
+  // ring first (beta = 0 initializes X4); its operand carries the one-index F terms as well
   einsum(c, "zimae,jbme->zijab", cx(1), r.t2, T(c.WringR, {o, v, o, v}), 0.0, X4);
   einsum(c, "mbij,zma->zijab", cx(-0.5), T(c.Wmbij, {o, v, o, o}), r.t1, 1.0, X4);
   einsum(c, "abej,zie->zijab", cx(0.5), T(c.Wabei, {v, v, v, o}), r.t1, 1.0, X4);
@@ -104,8 +105,7 @@ void sigma_right(Ctx& c, int nvec, const cplx* in, cplx* out) {
     einsum(c, "nmfe,zimfe->zni", cx(1), c.V("oovv"), r.t2, 0.0, T(ni, {Z, o, o}));
     einsum(c, "zni,jnba->zijab", cx(-0.25), T(ni, {Z, o, o}), t2, 1.0, X4);
   }
-  einsum(c, "be,zijae->zijab", cx(0.5), Fae, r.t2, 1.0, X4);
-  einsum(c, "mj,zimab->zijab", cx(-0.5), Fmi, r.t2, 1.0, X4);
+  // 1/2 P(ab) F_be r_ij^ae and -1/2 P(ij) F_mj r_im^ab are folded into the ring operand (H-bar)
   cplx* s2 = c.ws.cplxs(Z * c.Nd);
   pack_anti(c, X4, s2, Z, cx(1), true, false);
   // ladder 1/2 W_abef r_ij^ef over packed pairs: s2[(z,Pij)][Pab] += r[(z,Pij)][Pef] W[Pab][Pef]
@@ -114,6 +114,7 @@ void sigma_right(Ctx& c, int nvec, const cplx* in, cplx* out) {
   for (int64_t z = 0; z < Z; ++z)
     gemm_dispatch(c, true, false, Po, Pv, Po, cx(1), c.Wmnij_p, Po, r.d2 + z * c.Nd, Pv, cx(1), s2 + z * c.Nd, Pv);
   scatter(c, Z, s1, s2, out);
+  diag_axpy(c.L, c.N, Z, c.D, in, out);
   c.stats.sigma_calls++;
   c.stats.sigma_vectors += Z;
 }
@@ -135,8 +136,9 @@ void sigma_left(Ctx& c, int nvec, const cplx* in, cplx* out) {
   // ---- singles
   cplx* s1 = c.ws.cplxs(Z * o * v);
   Tensor S1 = T(s1, {Z, o, v});
-  einsum(c, "zie,ea->zia", cx(1), l.t1, Fae, 0.0, S1);
-  einsum(c, "zma,im->zia", cx(-1), l.t1, Fmi, 1.0, S1);
+  // the Fock-diagonal part of F_ae, F_mi enters exactly as D l at the end
+  einsum(c, "zie,ea->zia", cx(1), l.t1, T(c.Fae_od, {v, v}), 0.0, S1);
+  einsum(c, "zma,im->zia", cx(-1), l.t1, T(c.Fmi_od, {o, o}), 1.0, S1);
   einsum(c, "zimef,efam->zia", cx(0.5), l.t2, T(c.Wabei, {v, v, v, o}), 1.0, S1);
   einsum(c, "zmnae,iemn->zia", cx(-0.5), l.t2, T(c.Wmbij, {o, v, o, o}), 1.0, S1);
   einsum(c, "zef,eifa->zia", cx(-1), Gae, Wamef, 1.0, S1);
@@ -146,8 +148,7 @@ void sigma_left(Ctx& c, int nvec, const cplx* in, cplx* out) {
   cplx* x4 = c.ws.cplxs(Z * o * o * v * v);
   Tensor X4 = ring_layout(x4, Z, o, v);
   einsum(c, "zimae,jbme->zijab", cx(1), l.t2, T(c.WringL, {o, v, o, v}), 0.0, X4);
-  einsum(c, "zijae,eb->zijab", cx(0.5), l.t2, Fae, 1.0, X4);
-  einsum(c, "zimab,jm->zijab", cx(-0.5), l.t2, Fmi, 1.0, X4);
+  // 1/2 P(ab) l_ij^ae F_eb and -1/2 P(ij) l_im^ab F_jm are folded into the ring operand (H-bar)
   einsum(c, "ijae,zbe->zijab", cx(0.5), c.V("oovv"), Gae, 1.0, X4);
   einsum(c, "zma,ijmb->zijab", cx(-0.5), l.t1, Wmnie, 1.0, X4);
   einsum(c, "imab,zmj->zijab", cx(-0.5), c.V("oovv"), Gmi, 1.0, X4);
@@ -161,6 +162,7 @@ void sigma_left(Ctx& c, int nvec, const cplx* in, cplx* out) {
   for (int64_t z = 0; z < Z; ++z)
     gemm_dispatch(c, false, false, Po, Pv, Po, cx(1), c.Wmnij_p, Po, l.d2 + z * c.Nd, Pv, cx(1), s2 + z * c.Nd, Pv);
   scatter(c, Z, s1, s2, out);
+  diag_axpy(c.L, c.N, Z, c.D, in, out);
   c.stats.sigma_calls++;
   c.stats.sigma_vectors += Z;
 }

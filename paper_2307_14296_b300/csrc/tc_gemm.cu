@@ -683,7 +683,7 @@ void make_slices(Ctx& c, const Tensor& v, int nr, int nsl, Slices& s, __nv_bfloa
 }
 
 bool is_persistent(const Ctx& c, const void* p) {
-  const void* arr[] = {c.Fae, c.Fmi, c.Fme, c.Wmnij, c.Wmnij_p, c.Wabef_p, c.Wmbej, c.WringR, c.WringL, c.Wmnie,
+  const void* arr[] = {c.Fae, c.Fmi, c.Fae_od, c.Fmi_od, c.Fme, c.Wmnij, c.Wmnij_p, c.Wabef_p, c.Wmbej, c.WringR, c.WringL, c.Wmnie,
                        c.Wamef, c.Wmbij, c.Wabei, c.tau, c.t2, c.l2, c.oooo, c.ooov, c.oovv, c.ovov, c.ovvv,
                        c.vvvv_p, c.oovv_p, c.ovvv_p, c.t, c.lam};
   for (const void* q : arr)
