@@ -744,7 +744,7 @@ void response_function(Ctx& c, cplx* out_host) {
   auto beta = [&](int k, int f, int s) { return &rd.beta[k][(size_t)rd.shift_of[(size_t)f * 4 + s] * maxL]; };
   // The Hessian acts only on the solutions t^X(-z) and t^X(z*) of every frequency.  Their
   // coefficient vectors span few directions: compress them (QR with column pivoting, cutoff
-  // 1e-12 of the largest in FP64 mode; 1e-9 in the tensor-core modes, whose sigma products carry
+  // 1e-12 of the largest in FP64 mode; 1e-7 in the tensor-core modes, whose sigma products carry
   // ~1e-5 relative error) to Q_x, form the products F (B^x Q_x) in batches and contract them at once:
   //   M^{xy} = (B^x Q_x F) . B^y,  (t^X F) . t^Y = gamma^T M^{xy} beta^Y,  gamma = Q_x^H beta^X.
   std::vector<std::vector<std::vector<zc>>> Q(nop);
@@ -767,7 +767,7 @@ void response_function(Ctx& c, cplx* out_host) {
       if (best < 0) break;
       const double nrm = std::sqrt(bn);
       if (first < 0) first = nrm;
-      if (nrm <= (c.opt.precision == CCLR_FP64 ? 1e-12 : 1e-9) * first) break;
+      if (nrm <= (c.opt.precision == CCLR_FP64 ? 1e-12 : 1e-7) * first) break;
       used[best] = 1;
       std::vector<zc> qv(Lx);
       for (int i = 0; i < Lx; ++i) qv[i] = cols[best][i] / nrm;
