@@ -73,6 +73,7 @@ void free_all(Ctx& c) {
   c.eom_w.clear();
   c.fock = c.oooo = c.ooov = c.oovv = c.ovov = c.ovvv = c.vvvv_p = c.oovv_p = c.ovvv_p = nullptr;
   c.D = nullptr;
+  c.Dpre = nullptr;
   c.po = c.pv = nullptr;
   c.t = c.t2 = c.lam = c.l2 = nullptr;
   c.Fae = c.Fmi = c.Fme = c.Wmnij = c.Wmnij_p = c.Wabef_p = c.Wmbej = c.WringR = c.WringL = nullptr;

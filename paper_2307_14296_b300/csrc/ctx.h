@@ -51,6 +51,7 @@ struct Ctx {
   cplx *oooo = nullptr, *ooov = nullptr, *oovv = nullptr, *ovov = nullptr, *ovvv = nullptr;  // full index
   cplx *vvvv_p = nullptr, *oovv_p = nullptr, *ovvv_p = nullptr;                                 // packed
   double* D = nullptr;                                    // orbital-energy differences, length N
+  double* Dpre = nullptr;   // Davidson preconditioner: differences of the dressed one-body diagonal (Re F_aa, Re F_ii)
   bool have_ham = false;
 
   // amplitudes (t and lambda), amplitude layout and full doubles

@@ -94,6 +94,30 @@ void build_hbar(Ctx& c) {
   // right ring operand [(j,b)][(m,e)] = W_mbej[m,b,e,j]; left ring operand = W_mbej[j,e,b,m]
   permute(c.L, Wmbej.perm({3, 1, 0, 2}), T(c.WringR, {o, v, o, v}), cx(1), false);
   permute(c.L, Wmbej.perm({0, 2, 3, 1}), T(c.WringL, {o, v, o, v}), cx(1), false);
+  // Davidson preconditioner from the dressed one-body diagonal: Re F_aa - Re F_ii (singles),
+  // Re (F_aa + F_bb - F_ii - F_jj) (doubles)
+  {
+    if (!c.Dpre) c.Dpre = (double*)c.dalloc((c.N + 1) / 2 + 1);
+    std::vector<cplx> fa((size_t)v * v), fi((size_t)o * o);
+    CCLR_CK(cudaMemcpyAsync(fa.data(), c.Fae, sizeof(cplx) * fa.size(), cudaMemcpyDeviceToHost, c.stream));
+    CCLR_CK(cudaMemcpyAsync(fi.data(), c.Fmi, sizeof(cplx) * fi.size(), cudaMemcpyDeviceToHost, c.stream));
+    c.sync();
+    std::vector<double> ea(v), ei(o), D((size_t)c.N);
+    for (int a = 0; a < v; ++a) ea[a] = fa[(size_t)a * v + a].x;
+    for (int i = 0; i < o; ++i) ei[i] = fi[(size_t)i * o + i].x;
+    for (int i = 0; i < o; ++i)
+      for (int a = 0; a < v; ++a) D[(size_t)i * v + a] = ea[a] - ei[i];
+    int64_t ij = 0;
+    for (int q = 1; q < o; ++q)
+      for (int p = 0; p < q; ++p, ++ij) {
+        int64_t ab = 0;
+        for (int bq = 1; bq < v; ++bq)
+          for (int bp = 0; bp < bq; ++bp, ++ab)
+            D[(size_t)(c.Ns + ij * c.Pv + ab)] = ea[bp] + ea[bq] - ei[p] - ei[q];
+      }
+    CCLR_CK(cudaMemcpyAsync(c.Dpre, D.data(), sizeof(double) * D.size(), cudaMemcpyHostToDevice, c.stream));
+    c.sync();
+  }
   // Fae, Fmi without the bare Fock diagonal: sigma adds that part exactly as D r (D the
   // orbital-energy differences), so the tensor-core products carry only the rest
   copy_vec(c.L, v * v, c.Fae, c.Fae_od);

@@ -462,7 +462,7 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
     s.done = false;
     s.L = 0;
     // start: b / D, normalized (preconditioned right-hand side at z = 0)
-    div_shift(c.L, N, s.rhs, c.D, cx(0), cx(1), s.B);
+    div_shift(c.L, N, s.rhs, c.Dpre ? c.Dpre : c.D, cx(0), cx(1), s.B);
     const double nb = std::sqrt(norm2(c, s.B));
     CCLR_REQUIRE(nb > 0.0, CCLR_E_ARG, "zero right-hand side");
     scale_vec(c.L, N, cx(1.0 / nb), s.B);
@@ -596,7 +596,7 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
         a.add = s.rhs;
         a.Y = R;
         a.ldy = N;
-        a.D = c.D;
+        a.D = c.Dpre ? c.Dpre : c.D;
         a.z = zdev;
         a.norm2 = n2dev;
         a.norm_y = true;
@@ -1132,7 +1132,7 @@ int eom_ee(Ctx& c, int nroots, std::vector<zc>& w_out) {
         a.C = cdev;
         a.Y = R;
         a.ldy = N;
-        a.D = c.D;
+        a.D = c.Dpre ? c.Dpre : c.D;
         a.z = zdev;
         a.norm2 = n2dev;
         a.norm_y = true;
