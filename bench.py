@@ -267,6 +267,41 @@ def run_gemm(args):
                       "sample_rel_err": rel}))
 
 
+def run_sigma(args):
+    """One batched sigma product (8 trial vectors) alone, on a system of O occupied / V virtual
+    spinors (right sigma, or left with SIDE = 1): a small case for kernel captures.  Prints the
+    number of tensor-core GEMM launches before the timed calls (the ncu launch-skip of the first
+    timed launch) and the per-kernel times of the last call."""
+    import paper_2307_14296_b300 as pk
+    import synth
+    parts = [int(x) for x in args.sigma.split(",")]
+    o, v, side = parts[0], parts[1], (parts[2] if len(parts) > 2 else 0)
+    inst = synth.make_instance(o, v)
+    prec = pk.TC_BF16X3 if args.precision == "bf16x3" else pk.FP64
+    ctx = pk.Context(0, precision=prec, tol=1e-6, ground_tol=1e-8, max_subspace=32, batch=8, maxit=60)
+    ctx.cclr_set_hamiltonian(o, v, inst.fock, [inst.blocks[k] for k in synth.CLASSES])
+    ctx.cclr_kernel_profile(True)
+    ctx.cc_ground()
+    if side:
+        ctx.cc_lambda()
+    x = synth.random_vector((8, ctx.N), 5, 5, 1e-3)
+    for _ in range(max(1, args.warmup)):
+        ctx.cclr_sigma(x, side=side, precision=prec)
+    warm = ctx.cclr_kernel_breakdown()
+    before = sum(n for k, (n, ms) in warm.items() if k.split(" | ")[-1] == "k_tc_zgemm")
+    before_split = sum(n for k, (n, ms) in warm.items() if k.split(" | ")[-1].startswith("k_split_view"))
+    t_ms = []
+    for _ in range(max(1, args.steps)):
+        ctx.cclr_sigma(x, side=side, precision=prec)
+        bd = ctx.cclr_kernel_breakdown()
+        t_ms.append(sum(ms for _, ms in bd.values()))
+    ctx.cclr_kernel_profile(False)
+    print(json.dumps({"mode": "sigma", "o": o, "v": v, "side": side, "vectors": 8, "precision": args.precision,
+                      "tc_launches_before_timed": before,
+                      "tc_and_split_launches_before_timed": before + before_split, "kernel_ms_per_call": t_ms,
+                      "kernels": {k: [n, ms] for k, (n, ms) in sorted(bd.items(), key=lambda kv: -kv[1][1])}}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -282,11 +317,16 @@ def main():
     ap.add_argument("--workload", default="30x200", choices=sorted(WORKLOADS))
     ap.add_argument("--gemm", default=None, metavar="M,N,K",
                     help="time only the tensor-core complex GEMM C = A B^T on one shape (kernel profiling)")
+    ap.add_argument("--sigma", default=None, metavar="O,V[,SIDE]",
+                    help="time only one batched sigma product of 8 vectors on an O/V system (kernel profiling)")
     args = ap.parse_args()
     global WORKLOAD
     WORKLOAD = WORKLOADS[args.workload]
     if args.gemm:
         run_gemm(args)
+        return
+    if args.sigma:
+        run_sigma(args)
         return
     world, rank, local = dist_init()
     if args.impl == "reference":
@@ -399,16 +439,17 @@ def main():
         ci = ctx.cc_response_function_ci()
         t_ci = time.perf_counter() - t0
         alpha_ci = -ci
+        n0 = ctx.cclr_get_stats()["sigma_vectors"]
         t0 = time.perf_counter()
         roots, eom_its = ctx.cc_eom_ee(4)
         t_eom = time.perf_counter() - t0
-        st = ctx.cclr_get_stats()
+        n_eom = ctx.cclr_get_stats()["sigma_vectors"] - n0
         extra = dict(cc_ci_seconds=t_ci,
                      cc_ci_alpha_mean_last_freq=[float(np.trace(alpha_ci[-1]).real / 3),
                                                  float(np.trace(alpha_ci[-1]).imag / 3)],
                      eom_ee=dict(workload="4 lowest roots of the benchmark system (split-BF16)",
                                  roots=[[float(r.real), float(r.imag)] for r in roots], iterations=eom_its,
-                                 sigma_products=st["sigma_vectors"], seconds=t_eom),
+                                 sigma_products=n_eom, seconds=t_eom),
                      eom_ee_accuracy=eom_replica(pk, synth))
     # accuracy of the mixed-precision step against the FP64 path, on the 12/90 replica (the FP64
     # step at the full workload takes ~13 min): 16 frequencies, every component of alpha

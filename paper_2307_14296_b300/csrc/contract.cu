@@ -109,7 +109,7 @@ void einsum_impl(Ctx& c, const char* spec, cplx alpha, const Tensor& A, const Te
   if (M == 0 || N == 0) return;
   Scope scope(c.ws);
 
-  // candidate K orders: as in A, as in B
+  // candidate K orders: as in A, as in B (the one that lets more operands be used in place)
   std::string kB;
   for (char ch : s.b)
     if (kk.find(ch) != std::string::npos) kB += ch;
@@ -121,8 +121,10 @@ void einsum_impl(Ctx& c, const char* spec, cplx alpha, const Tensor& A, const Te
     auto directB = [&](const std::string& ko) {
       return !B.conj && (reorder(B, s.b, ko + fb).contiguous() || reorder(B, s.b, fb + ko).contiguous());
     };
+    // on a tie the larger operand keeps its own order: its view (and BF16 slices) are then the
+    // same for every contraction that reads it over the same indices
     int sa = (int)directA(kk) + (int)directB(kk), sb = (int)directA(kB) + (int)directB(kB);
-    if (sb > sa) korder = kB;
+    if (sb > sa || (sb == sa && B.numel() > A.numel())) korder = kB;
   }
 
   cplx al = make_double2(alpha.x, alpha.y);

@@ -28,6 +28,18 @@ struct ResponseData {
 };
 
 struct Ctx;
+int tc_slices(int precision);        // BF16 slices per operand in a tensor-core precision mode
+// While alive, the BF16 slices of the transient operand src (elems complex values, unchanged
+// meanwhile) are made once per view and reused by later contractions; workspace for `views`
+// views is reserved from the context's arena at construction (declare it after the Scope that
+// should release that space).  No effect in the FP64 mode.
+struct SliceMemo {
+  bool active = false;
+  SliceMemo(Ctx& c, const void* src, int64_t elems, int views);
+  ~SliceMemo();
+  SliceMemo(const SliceMemo&) = delete;
+  SliceMemo& operator=(const SliceMemo&) = delete;
+};
 void tc_release_cache_for(Ctx& c);   // frees the cached BF16 slices of persistent operands
 size_t tc_cache_bytes();             // bytes held by that cache
 

@@ -2,6 +2,8 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -139,10 +141,16 @@ struct KernelTimer {
     names.push_back(label ? std::string(label) + " | " + name : std::string(name));
   }
   void collect() {
+    // CCLR_PROFILE_DETAIL=2: also print every timed launch, in launch order
+    static const bool trace = [] {
+      const char* e = std::getenv("CCLR_PROFILE_DETAIL");
+      return e != nullptr && e[0] == '2';
+    }();
     for (size_t i = 0; i + 1 < used; i += 2) {
       float ms = 0.f;
       if (cudaEventElapsedTime(&ms, pool[i], pool[i + 1]) != cudaSuccess) continue;
       const std::string& nm = names[i / 2];
+      if (trace) std::fprintf(stderr, "[cclr] launch %s %.4f ms\n", nm.c_str(), ms);
       auto it = std::find_if(totals.begin(), totals.end(), [&](auto& t) { return t.first == nm; });
       if (it == totals.end()) totals.push_back({nm, {1, ms}});
       else { it->second.first += 1; it->second.second += ms; }

@@ -32,6 +32,17 @@ inline void bump(const Launch& L, const char* name) {   // after a launch: count
   if (L.count) ++*L.count;
   if (L.kt) L.kt->end(L.s, name);
 }
+// kernel name with its shape when every launch is traced (CCLR_PROFILE_DETAIL=2)
+inline const char* shaped(const char* name, int a, int b, int c) {
+  static const bool on = [] {
+    const char* e = std::getenv("CCLR_PROFILE_DETAIL");
+    return e != nullptr && e[0] == '2';
+  }();
+  if (!on) return name;
+  static thread_local char buf[96];
+  std::snprintf(buf, sizeof buf, "%s[%d,%d,%d]", name, a, b, c);
+  return buf;
+}
 
 struct PermArgs {
   int rank;
@@ -541,7 +552,7 @@ constexpr int kVecMatBlocks = 4 * 148;
 // zero and never stored); each thread takes E elements per step so that every coefficient read
 // from shared memory serves E elements.  With F32 the whole element pipeline (products, sums,
 // preconditioner, accumulation into Y) runs in FP32 and only loads and stores touch FP64.
-template <bool F32, int Q, int E>
+template <bool F32, int Q, int E, int U>
 __global__ void __launch_bounds__(kThreads, F32 ? 2 : 1)
     k_vecmat(int64_t n, Rows X, int m, const cplx* __restrict__ C, const cplx* __restrict__ add, cplx* Y, int64_t ldy,
              bool acc, const double* __restrict__ D, const cplx* __restrict__ z, bool norm_y, double* part) {
@@ -575,20 +586,33 @@ __global__ void __launch_bounds__(kThreads, F32 ? 2 : 1)
     for (int e = 0; e < E; ++e)
 #pragma unroll
       for (int q = 0; q < Q; ++q) a[e][q] = A::zero();
-#pragma unroll 4
-    for (int j = 0; j < nx; ++j) {
-      const cplx* rp = rows[j];
-      typename A::X xv[E];
+    // rows in groups of U: all loads of a group are issued before any is used, so that each
+    // thread keeps U * E loads in flight
+    for (int j0 = 0; j0 < nx; j0 += U) {
+      cplx raw[U][E];
 #pragma unroll
-      for (int e = 0; e < E; ++e) {
-        const int64_t i = i0 + (int64_t)e * blockDim.x;
-        xv[e] = A::opnd(i < n ? __ldg(rp + i) : make_double2(0.0, 0.0));
+      for (int u = 0; u < U; ++u) {
+        const int j = j0 + u;
+        const cplx* rp = rows[j < nx ? j : 0];
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int64_t i = i0 + (int64_t)e * blockDim.x;
+          raw[u][e] = (j < nx && i < n) ? __ldg(rp + i) : make_double2(0.0, 0.0);
+        }
       }
 #pragma unroll
-      for (int q = 0; q < Q; ++q) {
-        const Cf cq = cs[j * Q + q];
+      for (int u = 0; u < U; ++u) {
+        const int j = j0 + u;
+        if (j >= nx) break;
+        typename A::X xv[E];
 #pragma unroll
-        for (int e = 0; e < E; ++e) A::mac(a[e][q], cq, xv[e]);
+        for (int e = 0; e < E; ++e) xv[e] = A::opnd(raw[u][e]);
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+          const Cf cq = cs[j * Q + q];
+#pragma unroll
+          for (int e = 0; e < E; ++e) A::mac(a[e][q], cq, xv[e]);
+        }
       }
     }
 #pragma unroll
@@ -701,16 +725,16 @@ __global__ void k_unpack2(const cplx* __restrict__ D, int64_t ldd, cplx* X, int6
 }
 
 // Gram tile for tall-skinny operands: part[blk][i][j] = sum over this block's share of the
-// elements of op(X_i[k]) Y_j[k], nx <= 32 RL, ny <= NY.  Chunks of 64 elements of all rows are
-// copied to shared memory with cp.async, double-buffered; lane l owns rows l, l+32, ... of X and
-// all rows of Y (read as shared-memory broadcasts); the 8 warps split each chunk's elements and
-// are summed at the end.  F32: each chunk is converted to FP32 once in shared memory; products
-// are summed in FP32 pairs over runs of kGramRun chunks and the runs added with a compensated
-// (two-sum) FP32 accumulator.
-constexpr int kGramChunk = 64;
-constexpr int kGramPitch = kGramChunk + 1;   // padded row pitch: lanes reading distinct rows hit distinct banks
-constexpr int kGramRun = 4;                  // chunks per FP32 run (32 elements per warp)
+// elements of op(X_i[k]) Y_j[k], nx <= 32 RL, ny <= NY.  Chunks of 2^lc elements of all rows are
+// copied to shared memory with cp.async, double-buffered (the chunk grows as the row count falls,
+// so that about 64 KiB per SM are in flight whatever the tile); lane l owns rows l, l+32, ... of X
+// and all rows of Y (read as shared-memory broadcasts); the 8 warps split each chunk's elements
+// and are summed at the end.  F32: each chunk is converted to FP32 once in shared memory;
+// products are summed in FP32 pairs over runs of 32 elements per warp and the runs added with a
+// compensated (two-sum) FP32 accumulator.
+constexpr int kGramRunElems = 32;            // elements per warp in one FP32 run
 constexpr int kGramMaxX = 64, kGramMaxY = 8; // tile of one launch
+constexpr int kGramMinLog = 6, kGramMaxLog = 11;   // chunk of 64 .. 2048 elements
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -729,24 +753,27 @@ __device__ __forceinline__ void two_sum(float& hi, float& lo, float v) {
 }
 
 template <bool F32, int RL, int NY>
-__global__ void __launch_bounds__(256, 1) k_gram_skinny(int64_t n, Rows X, Rows Y, bool herm, cplx* part) {
+__global__ void __launch_bounds__(256, 1) k_gram_skinny(int64_t n, Rows X, Rows Y, bool herm, cplx* part, int lc) {
   typedef Arith<F32> A;
   extern __shared__ __align__(16) unsigned char gs_smem[];
   const int nx = X.total(), ny = Y.total(), nr = nx + ny;
+  const int CH = 1 << lc, pitch = CH + 1;   // padded row pitch: lanes reading distinct rows hit distinct banks
   cplx* stage[2];
   stage[0] = reinterpret_cast<cplx*>(gs_smem);
-  stage[1] = stage[0] + (size_t)nr * kGramPitch;
-  float2* cv = reinterpret_cast<float2*>(stage[1] + (size_t)nr * kGramPitch);   // F32 copy of a chunk
-  const cplx** rowp = reinterpret_cast<const cplx**>(cv + (F32 ? (size_t)nr * kGramPitch : 0));
+  stage[1] = stage[0] + (size_t)nr * pitch;
+  float2* cv = reinterpret_cast<float2*>(stage[1] + (size_t)nr * pitch);   // F32 copy of a chunk
+  const cplx** rowp = reinterpret_cast<const cplx**>(cv + (F32 ? (size_t)nr * pitch : 0));
   for (int r = threadIdx.x; r < nr; r += blockDim.x) rowp[r] = r < nx ? row_of(X, r) : row_of(Y, r - nx);
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t nchunks = (n + kGramChunk - 1) / kGramChunk;
+  const int64_t nchunks = (n + CH - 1) >> lc;
+  const int per_warp = CH >> 3;
+  const int flush_every = per_warp >= kGramRunElems ? 1 : kGramRunElems / per_warp;   // chunks per run
   auto issue = [&](int s, int64_t ch) {
-    const int64_t base = ch * kGramChunk;
-    for (int e = threadIdx.x; e < nr * kGramChunk; e += blockDim.x) {
-      const int r = e / kGramChunk, k = e % kGramChunk;
-      if (base + k < n) cp_async16(stage[s] + r * kGramPitch + k, rowp[r] + base + k);
+    const int64_t base = ch << lc;
+    for (int e = threadIdx.x; e < nr * CH; e += blockDim.x) {
+      const int r = e >> lc, k = e & (CH - 1);
+      if (base + k < n) cp_async16(stage[s] + r * pitch + k, rowp[r] + base + k);
     }
     cp_async_commit();
   };
@@ -772,6 +799,28 @@ __global__ void __launch_bounds__(256, 1) k_gram_skinny(int64_t n, Rows X, Rows 
         }
       }
   };
+  auto mac_elem = [&](const cplx* st, int k) {
+    typename A::X yv[NY];
+#pragma unroll
+    for (int j = 0; j < NY; ++j) {
+      if constexpr (F32) yv[j] = A::opnd(j < ny ? cv[(nx + j) * pitch + k] : make_float2(0.f, 0.f));
+      else yv[j] = A::opnd(j < ny ? st[(nx + j) * pitch + k] : make_double2(0.0, 0.0));
+    }
+#pragma unroll
+    for (int a = 0; a < RL; ++a) {
+      const int r = lane + 32 * a;
+      typename A::C xc;
+      if constexpr (F32) {
+        xc = A::coef(r < nx ? cv[r * pitch + k] : make_float2(0.f, 0.f));
+      } else {
+        cplx xv = r < nx ? st[r * pitch + k] : make_double2(0.0, 0.0);
+        if (herm) xv.y = -xv.y;
+        xc = A::coef(xv);
+      }
+#pragma unroll
+      for (int j = 0; j < NY; ++j) A::mac(acc[a][j], xc, yv[j]);
+    }
+  };
   int s = 0, run = 0;
   if ((int64_t)blockIdx.x < nchunks) issue(0, blockIdx.x);
   for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
@@ -784,45 +833,29 @@ __global__ void __launch_bounds__(256, 1) k_gram_skinny(int64_t n, Rows X, Rows 
     }
     __syncthreads();
     const cplx* st = stage[s];
-    const int64_t base = ch * kGramChunk;
+    const int64_t base = ch << lc;
     if constexpr (F32) {
-      for (int e = threadIdx.x; e < nr * kGramChunk; e += blockDim.x) {
-        const int r = e / kGramChunk, k = e % kGramChunk;
+      for (int e = threadIdx.x; e < nr * CH; e += blockDim.x) {
+        const int r = e >> lc, k = e & (CH - 1);
         if (base + k < n) {
-          float2 v = d2f2(st[r * kGramPitch + k]);
+          float2 v = d2f2(st[r * pitch + k]);
           if (herm && r < nx) v.y = -v.y;
-          cv[r * kGramPitch + k] = v;
+          cv[r * pitch + k] = v;
         }
       }
       __syncthreads();
     }
+    const int k0 = warp * per_warp;
+    for (int kk = 0; kk < per_warp; kk += kGramRunElems) {
+      const int len = min(kGramRunElems, per_warp - kk);
 #pragma unroll 2
-    for (int kk = 0; kk < kGramChunk / 8; ++kk) {
-      const int k = warp * (kGramChunk / 8) + kk;
-      if (base + k < n) {
-        typename A::X yv[NY];
-#pragma unroll
-        for (int j = 0; j < NY; ++j) {
-          if constexpr (F32) yv[j] = A::opnd(j < ny ? cv[(nx + j) * kGramPitch + k] : make_float2(0.f, 0.f));
-          else yv[j] = A::opnd(j < ny ? st[(nx + j) * kGramPitch + k] : make_double2(0.0, 0.0));
-        }
-#pragma unroll
-        for (int a = 0; a < RL; ++a) {
-          const int r = lane + 32 * a;
-          typename A::C xc;
-          if constexpr (F32) {
-            xc = A::coef(r < nx ? cv[r * kGramPitch + k] : make_float2(0.f, 0.f));
-          } else {
-            cplx xv = r < nx ? st[r * kGramPitch + k] : make_double2(0.0, 0.0);
-            if (herm) xv.y = -xv.y;
-            xc = A::coef(xv);
-          }
-#pragma unroll
-          for (int j = 0; j < NY; ++j) A::mac(acc[a][j], xc, yv[j]);
-        }
+      for (int t = 0; t < len; ++t) {
+        const int k = k0 + kk + t;
+        if (base + k < n) mac_elem(st, k);
       }
+      if (per_warp >= kGramRunElems) flush();
     }
-    if (++run == kGramRun) {
+    if (per_warp < kGramRunElems && ++run == flush_every) {
       run = 0;
       flush();
     }
@@ -935,28 +968,30 @@ void unpack2(const Launch& L, const cplx* D, int64_t ldd, const Tensor& X) {
 }
 
 namespace {
+constexpr size_t kGramSmemMax = 200 << 10;
 template <bool F32, int RL, int NY>
 void launch_gram(const Launch& L, int nblk, size_t smem, int64_t n, const Rows& X, const Rows& Y, bool herm,
-                 cplx* part) {
+                 cplx* part, int lc) {
   static bool attr = false;
   if (!attr) {
-    CCLR_CK(cudaFuncSetAttribute(k_gram_skinny<F32, RL, NY>, cudaFuncAttributeMaxDynamicSharedMemorySize, 192 << 10));
+    CCLR_CK(cudaFuncSetAttribute(k_gram_skinny<F32, RL, NY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kGramSmemMax));
     attr = true;
   }
-  k_gram_skinny<F32, RL, NY><<<nblk, 256, smem, L.s>>>(n, X, Y, herm, part);
+  k_gram_skinny<F32, RL, NY><<<nblk, 256, smem, L.s>>>(n, X, Y, herm, part, lc);
 }
 template <bool F32>
 void launch_gram_tile(const Launch& L, int nblk, size_t smem, int64_t n, const Rows& X, const Rows& Y, bool herm,
-                      cplx* part) {
+                      cplx* part, int lc) {
   const int a = X.total(), b = Y.total();
   if (a <= 32) {
-    if (b == 1) launch_gram<F32, 1, 1>(L, nblk, smem, n, X, Y, herm, part);
-    else if (b <= 4) launch_gram<F32, 1, 4>(L, nblk, smem, n, X, Y, herm, part);
-    else launch_gram<F32, 1, 8>(L, nblk, smem, n, X, Y, herm, part);
+    if (b == 1) launch_gram<F32, 1, 1>(L, nblk, smem, n, X, Y, herm, part, lc);
+    else if (b <= 4) launch_gram<F32, 1, 4>(L, nblk, smem, n, X, Y, herm, part, lc);
+    else launch_gram<F32, 1, 8>(L, nblk, smem, n, X, Y, herm, part, lc);
   } else {
-    if (b == 1) launch_gram<F32, 2, 1>(L, nblk, smem, n, X, Y, herm, part);
-    else if (b <= 4) launch_gram<F32, 2, 4>(L, nblk, smem, n, X, Y, herm, part);
-    else launch_gram<F32, 2, 8>(L, nblk, smem, n, X, Y, herm, part);
+    if (b == 1) launch_gram<F32, 2, 1>(L, nblk, smem, n, X, Y, herm, part, lc);
+    else if (b <= 4) launch_gram<F32, 2, 4>(L, nblk, smem, n, X, Y, herm, part, lc);
+    else launch_gram<F32, 2, 8>(L, nblk, smem, n, X, Y, herm, part, lc);
   }
 }
 }  // namespace
@@ -970,22 +1005,31 @@ void gram(const Launch& L, int64_t n, const Rows& X, const Rows& Y, bool herm, c
   const Rows& P = swap ? Y : X;
   const Rows& Q = swap ? X : Y;
   const int np = P.total(), nq = Q.total();
-  const int64_t nchunks = (n + kGramChunk - 1) / kGramChunk;
   for (int i0 = 0; i0 < np; i0 += kGramMaxX)
     for (int j0 = 0; j0 < nq; j0 += kGramMaxY) {
       const int a = std::min(kGramMaxX, np - i0), b = std::min(kGramMaxY, nq - j0);
+      // chunk: at least 64 KiB of rows per stage (the bytes each SM keeps in flight), within the
+      // shared-memory budget of two stages plus the FP32 copy
+      auto stage_bytes = [&](int lc) {
+        return (2 * sizeof(cplx) + (L.fast32 ? sizeof(float2) : 0)) * (size_t)(a + b) * ((size_t(1) << lc) + 1) +
+               sizeof(void*) * (size_t)(a + b);
+      };
+      int lc = kGramMinLog;
+      while (lc < kGramMaxLog && ((size_t)(a + b) * sizeof(cplx) << lc) < (size_t(64) << 10) &&
+             stage_bytes(lc + 1) <= kGramSmemMax)
+        ++lc;
+      const int64_t nchunks = (n + (int64_t(1) << lc) - 1) >> lc;
       int nblk = (int)std::min<int64_t>(148, nchunks);
       if ((int64_t)nblk * a * b > scratch_elems) nblk = (int)std::max<int64_t>(1, scratch_elems / ((int64_t)a * b));
       const int RL = a <= 32 ? 1 : 2, NYt = b == 1 ? 1 : (b <= 4 ? 4 : 8);
-      const size_t stage = (2 * sizeof(cplx) + (L.fast32 ? sizeof(float2) : 0)) * (size_t)(a + b) * kGramPitch +
-                           sizeof(void*) * (size_t)(a + b);
       const size_t red = sizeof(cplx) * 8 * RL * NYt * 32;
-      const size_t smem = std::max(stage, red);
+      const size_t smem = std::max(stage_bytes(lc), red);
+      CCLR_REQUIRE(smem <= kGramSmemMax, CCLR_E_ARG, "gram: tile too large");
       kbeg(L);
-      if (L.fast32) launch_gram_tile<true>(L, nblk, smem, n, P.slice(i0, a), Q.slice(j0, b), herm, scratch);
-      else launch_gram_tile<false>(L, nblk, smem, n, P.slice(i0, a), Q.slice(j0, b), herm, scratch);
+      if (L.fast32) launch_gram_tile<true>(L, nblk, smem, n, P.slice(i0, a), Q.slice(j0, b), herm, scratch, lc);
+      else launch_gram_tile<false>(L, nblk, smem, n, P.slice(i0, a), Q.slice(j0, b), herm, scratch, lc);
       CCLR_CK(cudaGetLastError());
-      bump(L, "k_gram_skinny");
+      bump(L, shaped("k_gram_skinny", a, b, lc));
       cplx* o = swap ? out_dev + (int64_t)j0 * ny + i0 : out_dev + (int64_t)i0 * ny + j0;
       kbeg(L);
       k_gram_reduce<<<(a * b + 255) / 256, 256, 0, L.s>>>(scratch, nblk, a, b, o, ny, swap, herm);
@@ -999,15 +1043,18 @@ int64_t vecmat_scratch_doubles() { return (int64_t)kVecMatOut * kVecMatBlocks; }
 namespace {
 template <bool F32, int Q>
 void launch_vecmat(const Launch& L, int64_t n, const VecMat& a, double* part) {
-  constexpr int E = (F32 && Q <= 4) ? 2 : 1;   // 16 outputs x 2 elements would not fit 128 registers
+  // E elements per thread (each shared-memory coefficient serves E elements), U rows of loads in
+  // flight; the FP32 variants stay within 128 registers (two blocks per SM)
+  constexpr int E = F32 ? 2 : 1;
+  constexpr int U = (F32 && Q == 16) ? 4 : 8;
   const int nx = a.X.total();
   const size_t smem = sizeof(typename Arith<F32>::C) * (size_t)nx * Q + sizeof(void*) * (size_t)nx;
   static bool attr = false;
   if (!attr) {   // kVecMatMaxRows x 16 coefficients (16 B each) + row table: 132 KiB
-    CCLR_CK(cudaFuncSetAttribute(k_vecmat<F32, Q, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, 136 << 10));
+    CCLR_CK(cudaFuncSetAttribute(k_vecmat<F32, Q, E, U>, cudaFuncAttributeMaxDynamicSharedMemorySize, 136 << 10));
     attr = true;
   }
-  k_vecmat<F32, Q, E><<<kVecMatBlocks, kThreads, smem, L.s>>>(n, a.X, a.m, a.C, a.add, a.Y, a.ldy, a.acc, a.D, a.z,
+  k_vecmat<F32, Q, E, U><<<kVecMatBlocks, kThreads, smem, L.s>>>(n, a.X, a.m, a.C, a.add, a.Y, a.ldy, a.acc, a.D, a.z,
                                                               a.norm_y, part);
 }
 }  // namespace
@@ -1024,14 +1071,16 @@ void vecmat(const Launch& L, int64_t n, const VecMat& a, double* scratch) {
   if (L.fast32) {
     if (a.m == 1) launch_vecmat<true, 1>(L, n, a, part);
     else if (a.m <= 4) launch_vecmat<true, 4>(L, n, a, part);
+    else if (a.m <= 8) launch_vecmat<true, 8>(L, n, a, part);
     else launch_vecmat<true, 16>(L, n, a, part);
   } else {
     if (a.m == 1) launch_vecmat<false, 1>(L, n, a, part);
     else if (a.m <= 4) launch_vecmat<false, 4>(L, n, a, part);
+    else if (a.m <= 8) launch_vecmat<false, 8>(L, n, a, part);
     else launch_vecmat<false, 16>(L, n, a, part);
   }
   CCLR_CK(cudaGetLastError());
-  bump(L, "k_vecmat");
+  bump(L, shaped("k_vecmat", nx, a.m, a.D ? 1 : 0));
   if (a.norm2) {
     kbeg(L);
     k_sum_rows<<<a.m, kThreads, 0, L.s>>>(part, kVecMatBlocks, a.norm2);

@@ -70,6 +70,7 @@ void sigma_right(Ctx& c, int nvec, const cplx* in, cplx* out) {
   Scope sc(c.ws);
   const int64_t Z = nvec, o = c.o, v = c.v, Po = c.Po, Pv = c.Pv;
   Batch r = gather(c, Z, in, true);
+  SliceMemo memo(c, r.full, Z * o * o * v * v, 3);   // r_ij^ab is read in three layouts
   Tensor t2 = T(c.t2, {o, o, v, v});
   Tensor Fae = T(c.Fae, {v, v}), Fmi = T(c.Fmi, {o, o}), Fme = T(c.Fme, {o, v});
   Tensor Wmbej = T(c.Wmbej, {o, v, v, o}), Wamef = T(c.Wamef, {v, o, v, v}), Wmnie = T(c.Wmnie, {o, o, o, v});
@@ -91,19 +92,19 @@ void sigma_right(Ctx& c, int nvec, const cplx* in, cplx* out) {
   einsum(c, "mbij,zma->zijab", cx(-0.5), T(c.Wmbij, {o, v, o, o}), r.t1, 1.0, X4);
   einsum(c, "abej,zie->zijab", cx(0.5), T(c.Wabei, {v, v, v, o}), r.t1, 1.0, X4);
   {
+    // Terms of the form (W r) t: the packing antisymmetrizer A = (1 - P(ij))(1 - P(ab)) obeys
+    // A P(ab) = A P(ij) = -A, so -1/4 Z_af t_ij^fb enters as -1/4 Z_bf t_ij^af (t antisymmetric)
+    // and -1/4 Z_ni t_jn^ba as -1/4 Z_nj t_in^ab: the two (W r) intermediates that multiply t the
+    // same way are summed first and each pair costs one pass over X4.
     Scope s2(c.ws);
     cplx* bf = c.ws.cplxs(Z * v * v);
-    einsum(c, "bmfe,zme->zbf", cx(1), Wamef, r.t1, 0.0, T(bf, {Z, v, v}));
-    einsum(c, "zbf,ijaf->zijab", cx(0.5), T(bf, {Z, v, v}), t2, 1.0, X4);
+    einsum(c, "bmfe,zme->zbf", cx(0.5), Wamef, r.t1, 0.0, T(bf, {Z, v, v}));
+    einsum(c, "nmfe,zmnea->zaf", cx(-0.25), c.V("oovv"), r.t2, 1.0, T(bf, {Z, v, v}));
+    einsum(c, "zbf,ijaf->zijab", cx(1), T(bf, {Z, v, v}), t2, 1.0, X4);
     cplx* nj = c.ws.cplxs(Z * o * o);
-    einsum(c, "nmje,zme->znj", cx(1), Wmnie, r.t1, 0.0, T(nj, {Z, o, o}));
-    einsum(c, "znj,inab->zijab", cx(-0.5), T(nj, {Z, o, o}), t2, 1.0, X4);
-    cplx* af = c.ws.cplxs(Z * v * v);
-    einsum(c, "nmfe,zmnea->zaf", cx(1), c.V("oovv"), r.t2, 0.0, T(af, {Z, v, v}));
-    einsum(c, "zaf,ijfb->zijab", cx(-0.25), T(af, {Z, v, v}), t2, 1.0, X4);
-    cplx* ni = c.ws.cplxs(Z * o * o);
-    einsum(c, "nmfe,zimfe->zni", cx(1), c.V("oovv"), r.t2, 0.0, T(ni, {Z, o, o}));
-    einsum(c, "zni,jnba->zijab", cx(-0.25), T(ni, {Z, o, o}), t2, 1.0, X4);
+    einsum(c, "nmje,zme->znj", cx(-0.5), Wmnie, r.t1, 0.0, T(nj, {Z, o, o}));
+    einsum(c, "nmfe,zimfe->zni", cx(-0.25), c.V("oovv"), r.t2, 1.0, T(nj, {Z, o, o}));
+    einsum(c, "znj,inab->zijab", cx(1), T(nj, {Z, o, o}), t2, 1.0, X4);
   }
   // 1/2 P(ab) F_be r_ij^ae and -1/2 P(ij) F_mj r_im^ab are folded into the ring operand (H-bar)
   cplx* s2 = c.ws.cplxs(Z * c.Nd);
@@ -124,6 +125,7 @@ void sigma_left(Ctx& c, int nvec, const cplx* in, cplx* out) {
   Scope sc(c.ws);
   const int64_t Z = nvec, o = c.o, v = c.v, Po = c.Po, Pv = c.Pv;
   Batch l = gather(c, Z, in, true);
+  SliceMemo memo(c, l.full, Z * o * o * v * v, 3);   // l_ij^ab is read in three layouts
   Tensor t2 = T(c.t2, {o, o, v, v});
   Tensor Fae = T(c.Fae, {v, v}), Fmi = T(c.Fmi, {o, o}), Fme = T(c.Fme, {o, v});
   Tensor Wmbej = T(c.Wmbej, {o, v, v, o}), Wamef = T(c.Wamef, {v, o, v, v}), Wmnie = T(c.Wmnie, {o, o, o, v});
@@ -302,6 +304,7 @@ void hessian_right(Ctx& c, int nvec, const cplx* in, cplx* out) {
 
   Scope sc(c.ws);
   Batch u = gather(c, Z, in, true);
+  SliceMemo memo(c, u.full, Z * o * o * v * v, 7);   // u_ij^ab is read in seven layouts
   Tensor u1 = u.t1, u2 = u.t2;
   cplx* s1 = c.ws.cplxs(Z * o * v);
   Tensor S = T(s1, {Z, o, v});
@@ -367,40 +370,48 @@ void hessian_right(Ctx& c, int nvec, const cplx* in, cplx* out) {
   fill_zero(c.L, x4, Z * o * o * v * v);
   { Tensor t = tmp({Z, o, v}); einsum(c, "lida,zia->zld", cx(1), oovv, u1, 0.0, t);
     einsum(c, "kc,zld->zklcd", cx(1), l1, t, 1.0, X4); }
-  { Tensor t = tmp({Z, o, o}); einsum(c, "ka,zia->zki", cx(1), l1, u1, 0.0, t);
-    einsum(c, "zki,ilcd->zklcd", cx(-0.5), t, oovv, 1.0, X4); }
-  { Tensor t = tmp({Z, v, v}); einsum(c, "ic,zia->zca", cx(1), l1, u1, 0.0, t);
-    einsum(c, "zca,klad->zklcd", cx(-0.5), t, oovv, 1.0, X4); }
-  { Tensor t = tmp({Z, o, o}); einsum(c, "la,zia->zli", cx(1), Fme, u1, 0.0, t);
-    einsum(c, "kicd,zli->zklcd", cx(-0.5), l2, t, 1.0, X4); }
-  { Tensor t = tmp({Z, v, v}); einsum(c, "id,zia->zda", cx(1), Fme, u1, 0.0, t);
-    einsum(c, "klca,zda->zklcd", cx(-0.5), l2, t, 1.0, X4); }
-  { Tensor t = tmp({Z, v, v}); einsum(c, "eida,zia->zed", cx(1), Wamef, u1, 0.0, t);
-    einsum(c, "klce,zed->zklcd", cx(0.5), l2, t, 1.0, X4); }
-  { Tensor t = tmp({Z, o, o}); einsum(c, "lima,zia->zlm", cx(1), Wmnie, u1, 0.0, t);
-    einsum(c, "kmcd,zlm->zklcd", cx(-0.5), l2, t, 1.0, X4); }
-  { Tensor t = tmp({Z, o, o, v, v}); einsum(c, "kimd,zia->zkmda", cx(1), Wmnie, u1, 0.0, t);
+  // The remaining terms share their outer operand in groups.  With the packing antisymmetrizer
+  // A = (1 - P(kl))(1 - P(cd)) (A P(kl) = A P(cd) = -A, A P(kl) P(cd) = A) every group is rewritten
+  // onto one index pattern, its (u-dependent) intermediates are summed, and the group costs one
+  // product and one pass over X4.
+  { // <il||cd> (-1/2 l_ka u_ia - 1/4 l_ik^ab u_ij^ab)
+    Tensor t = tmp({Z, o, o});
+    einsum(c, "ka,zia->zki", cx(-0.5), l1, u1, 0.0, t);
+    einsum(c, "ikab,zijab->zkj", cx(-0.25), l2, u2, 1.0, t);
+    einsum(c, "zki,ilcd->zklcd", cx(1), t, oovv, 1.0, X4); }
+  { // <kl||ad> (-1/2 l_ic u_ia - 1/4 l_ij^ac u_ij^ab)
+    Tensor t = tmp({Z, v, v});
+    einsum(c, "ic,zia->zca", cx(-0.5), l1, u1, 0.0, t);
+    einsum(c, "ijac,zijab->zcb", cx(-0.25), l2, u2, 1.0, t);
+    einsum(c, "zca,klad->zklcd", cx(1), t, oovv, 1.0, X4); }
+  { // l_ki^cd (-1/2 F_la u_ia - 1/2 W_lima u_ia - 1/4 <lj||ab> u_ij^ab)
+    Tensor t = tmp({Z, o, o});
+    einsum(c, "la,zia->zli", cx(-0.5), Fme, u1, 0.0, t);
+    einsum(c, "lima,zia->zlm", cx(-0.5), Wmnie, u1, 1.0, t);
+    einsum(c, "ljab,zijab->zli", cx(-0.25), oovv, u2, 1.0, t);
+    einsum(c, "kicd,zli->zklcd", cx(1), l2, t, 1.0, X4); }
+  { // l_kl^ca (-1/2 F_id u_ia + 1/2 W_eida u_ia (as its transpose) - 1/4 <ij||db> u_ij^ab)
+    Tensor t = tmp({Z, v, v});
+    einsum(c, "id,zia->zda", cx(-0.5), Fme, u1, 0.0, t);
+    einsum(c, "eida,zia->zde", cx(0.5), Wamef, u1, 1.0, t);
+    einsum(c, "ijdb,zijab->zda", cx(-0.25), oovv, u2, 1.0, t);
+    einsum(c, "klca,zda->zklcd", cx(1), l2, t, 1.0, X4); }
+  { // l_mi^cd (1/4 W_klma u_ia + 1/16 <kl||ab> u_mi^ab)
+    Tensor t = tmp({Z, o, o, o, o});
+    einsum(c, "klma,zia->zklmi", cx(0.25), Wmnie, u1, 0.0, t);
+    einsum(c, "klab,zijab->zklij", cx(0.0625), oovv, u2, 1.0, t);
+    einsum(c, "micd,zklmi->zklcd", cx(1), l2, t, 1.0, X4); }
+  { // ring-shaped terms on l_ml^ca: W_kimd u_ia, <li||da> u_ij^ab (under P(kl)) and
+    // -l_ki^ed W_elca u_ia (under P(kl)P(cd), i.e. -W_ekdf u_if at (k,i,d,e))
+    Tensor t = tmp({Z, o, o, v, v});
+    einsum(c, "kimd,zia->zkmda", cx(1), Wmnie, u1, 0.0, t);
+    einsum(c, "lida,zijab->zljdb", cx(1), oovv, u2, 1.0, t);
+    einsum(c, "ekdf,zif->zkide", cx(-1), Wamef, u1, 1.0, t);
     einsum(c, "mlca,zkmda->zklcd", cx(1), l2, t, 1.0, X4); }
-  { Tensor t = tmp({Z, o, o, o, o}); einsum(c, "klma,zia->zklmi", cx(1), Wmnie, u1, 0.0, t);
-    einsum(c, "micd,zklmi->zklcd", cx(0.25), l2, t, 1.0, X4); }
-  { Tensor t = tmp({Z, v, o, v, o}); einsum(c, "elca,zia->zelci", cx(1), Wamef, u1, 0.0, t);
-    einsum(c, "kied,zelci->zklcd", cx(-1), l2, t, 1.0, X4); }
   { Tensor t = tmp({Z, o, o, v, o}); einsum(c, "klea,zia->zklei", cx(1), l2, u1, 0.0, t);
     einsum(c, "zklei,eicd->zklcd", cx(-0.25), t, Wamef, 1.0, X4); }
-  { Tensor t = tmp({Z, v, v}); einsum(c, "ijdb,zijab->zda", cx(1), oovv, u2, 0.0, t);
-    einsum(c, "klca,zda->zklcd", cx(-0.25), l2, t, 1.0, X4); }
-  { Tensor t = tmp({Z, o, o}); einsum(c, "ljab,zijab->zli", cx(1), oovv, u2, 0.0, t);
-    einsum(c, "kicd,zli->zklcd", cx(-0.25), l2, t, 1.0, X4); }
-  { Tensor t = tmp({Z, o, o, o, o}); einsum(c, "klab,zijab->zklij", cx(1), oovv, u2, 0.0, t);
-    einsum(c, "ijcd,zklij->zklcd", cx(0.0625), l2, t, 1.0, X4); }
   { Tensor t = tmp({Z, o, o, o, o}); einsum(c, "klab,zijab->zklij", cx(1), l2, u2, 0.0, t);
     einsum(c, "zklij,ijcd->zklcd", cx(0.0625), t, oovv, 1.0, X4); }
-  { Tensor t = tmp({Z, o, o, v, v}); einsum(c, "lida,zijab->zljdb", cx(1), oovv, u2, 0.0, t);
-    einsum(c, "kjcb,zljdb->zklcd", cx(1), l2, t, 1.0, X4); }
-  { Tensor t = tmp({Z, o, o}); einsum(c, "ikab,zijab->zkj", cx(1), l2, u2, 0.0, t);
-    einsum(c, "zkj,jlcd->zklcd", cx(-0.25), t, oovv, 1.0, X4); }
-  { Tensor t = tmp({Z, v, v}); einsum(c, "ijac,zijab->zcb", cx(1), l2, u2, 0.0, t);
-    einsum(c, "zcb,klbd->zklcd", cx(-0.25), t, oovv, 1.0, X4); }
   cplx* s2 = c.ws.cplxs(Z * c.Nd);
   pack_anti(c, X4, s2, Z, cx(1), true, false);
   scatter(c, Z, s1, s2, out);

@@ -508,8 +508,8 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
         std::vector<zc> g;
         const cplx* Bn = s.B + (int64_t)L0 * N;
         const cplx* Sn = s.S + (int64_t)L0 * N;
-        const int ny = 2 * f + 1;
-        gram_host(c, rows(c, s.B, s.L), Rows().add(Sn, f, N).add(Bn, f, N).add(s.rhs, 1, N), true, g);
+        const int ny = 2 * f;
+        gram_host(c, rows(c, s.B, s.L), Rows().add(Sn, f, N).add(Bn, f, N), true, g);
         for (int i = 0; i < s.L; ++i) {
           for (int j = 0; j < f; ++j) {
             s.BS[(size_t)i * maxL + L0 + j] = g[(size_t)i * ny + j];
@@ -517,13 +517,16 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
             s.BB[(size_t)i * maxL + L0 + j] = bb;
             s.BB[(size_t)(L0 + j) * maxL + i] = std::conj(bb);
           }
-          s.Cp[i] = -g[(size_t)i * ny + 2 * f];
         }
-        if (L0 > 0) {
-          gram_host(c, rows(c, s.S, L0), rows(c, Bn, f), true, g);   // S_old^H B_new
-          for (int i = 0; i < L0; ++i)
-            for (int j = 0; j < f; ++j) s.BS[(size_t)(L0 + j) * maxL + i] = std::conj(g[(size_t)i * f + j]);
-        }
+        // S_old^H B_new and b^H B_new in one pass (the old rows of B^H b are unchanged: b is fixed
+        // and a restart transforms them with the basis)
+        Rows sb;
+        if (L0 > 0) sb.add(s.S, L0, N);
+        sb.add(s.rhs, 1, N);
+        gram_host(c, sb, rows(c, Bn, f), true, g);
+        for (int i = 0; i < L0; ++i)
+          for (int j = 0; j < f; ++j) s.BS[(size_t)(L0 + j) * maxL + i] = std::conj(g[(size_t)i * f + j]);
+        for (int j = 0; j < f; ++j) s.Cp[L0 + j] = -std::conj(g[(size_t)L0 * f + j]);
       }
       fresh[k] = 0;
       const int L = s.L;

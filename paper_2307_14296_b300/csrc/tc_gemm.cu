@@ -693,8 +693,23 @@ bool is_persistent(const Ctx& c, const void* p) {
   return false;
 }
 
-// Slices of view v (first nr axes = rows): from the cache for persistent operands, else into
-// the workspace.
+// Slices of a transient operand that several contractions of one call read in the same view
+// (the unpacked trial vectors of a sigma product: e.g. r_mn^ea over (m, n, e) for two singles
+// terms) are split once.  A SliceMemo names the operand, which must not change while it is
+// alive, and reserves workspace for its slices; memos nest.
+struct Memo {
+  const void* src = nullptr;
+  char* base = nullptr;
+  size_t cap = 0, used = 0;
+  std::vector<std::pair<std::string, Slices>> entries;
+};
+std::vector<Memo>& memos() {
+  static std::vector<Memo> m;
+  return m;
+}
+
+// Slices of view v (first nr axes = rows): from the cache for persistent operands, from the memo
+// of a transient operand named by a SliceMemo, else into the workspace.
 Slices get_slices(Ctx& c, const Tensor& v, int nr, int nsl) {
   if (g_cache_gen != data_generation()) {
     for (auto& kv : cache()) cudaFree(kv.second.s.p);
@@ -725,9 +740,47 @@ Slices get_slices(Ctx& c, const Tensor& v, int nr, int nsl) {
     }
     cudaGetLastError();  // out of memory for the cache: fall through to a workspace copy
   }
+  for (auto it = memos().rbegin(); it != memos().rend(); ++it) {
+    if (it->src != v.p) continue;
+    std::string key = std::to_string(nr) + "|" + std::to_string(nsl) + "|" + std::to_string((int)v.conj);
+    for (int i = 0; i < v.rank; ++i) key += "|" + std::to_string(v.dim[i]) + ":" + std::to_string(v.str[i]);
+    for (auto& e : it->entries)
+      if (e.first == key) return e.second;
+    const size_t at = (it->used + 255) & ~size_t(255);
+    if (at + bytes <= it->cap) {
+      make_slices(c, v, nr, nsl, s, (__nv_bfloat16*)(it->base + at));
+      it->used = at + bytes;
+      it->entries.push_back({key, s});
+      return s;
+    }
+    break;
+  }
   make_slices(c, v, nr, nsl, s, (__nv_bfloat16*)c.ws.alloc(bytes));
   return s;
 }
+
+}  // namespace
+
+SliceMemo::SliceMemo(Ctx& c, const void* src, int64_t elems, int views) {
+  if (c.opt.precision == CCLR_FP64 || src == nullptr) return;
+  // each view: nsl slices x (re, im) BF16 planes, K padded to a multiple of BK per row
+  const size_t want = (size_t)views * 2 * sizeof(__nv_bfloat16) * (size_t)tc_slices(c.opt.precision) *
+                      (size_t)((double)elems * 1.05 + 65536.0);
+  const size_t avail = c.ws.cap > c.ws.top ? (c.ws.cap - c.ws.top) / 2 : 0;   // leave half for the call
+  const size_t cap = std::min(want, avail);
+  if (cap < ((size_t)1 << 20)) return;
+  Memo m;
+  m.src = src;
+  m.base = (char*)c.ws.alloc(cap);
+  m.cap = cap;
+  memos().push_back(std::move(m));
+  active = true;
+}
+SliceMemo::~SliceMemo() {
+  if (active) memos().pop_back();
+}
+
+namespace {
 
 tc::Pairs pairs_for(int nsl) {
   tc::Pairs pairs{};
