@@ -302,6 +302,23 @@ def run_sigma(args):
                       "kernels": {k: [n, ms] for k, (n, ms) in sorted(bd.items(), key=lambda kv: -kv[1][1])}}))
 
 
+def run_vector_kernels(args):
+    """The Davidson solver's multi-vector kernels alone on synthetic device vectors of length N:
+    a Gram block (NX x NY) and the NX-row, M-output vecmat passes (norms only; outputs stored).
+    Reports milliseconds per call and the bandwidth of the bytes each pass must move."""
+    import paper_2307_14296_b300 as pk
+    import synth
+    n, nx, ny, m = (int(x) for x in args.vector_kernels.split(","))
+    prec = pk.TC_BF16X3 if args.precision == "bf16x3" else pk.FP64
+    ctx = pk.Context(0, precision=prec)
+    tiny = synth.make_instance(2, 4)   # a Hamiltonian gives the context its device workspace
+    ctx.cclr_set_hamiltonian(2, 4, tiny.fock, [tiny.blocks[k] for k in synth.CLASSES])
+    r = ctx.cclr_bench_vector_kernels(n, nx, ny, m, reps=max(1, args.steps), precision=prec)
+    gb = dict(gram=16.0 * n * (nx + ny) / 1e9, norms=16.0 * n * nx / 1e9, write=16.0 * n * (nx + m) / 1e9)
+    print(json.dumps({"mode": "vector_kernels", "n": n, "nx": nx, "ny": ny, "m": m, "precision": args.precision,
+                      **r, **{f"{k}_gbs": gb[k] / (r[f"{k}_ms"] * 1e-3) for k in gb}}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -317,6 +334,8 @@ def main():
     ap.add_argument("--workload", default="30x200", choices=sorted(WORKLOADS))
     ap.add_argument("--gemm", default=None, metavar="M,N,K",
                     help="time only the tensor-core complex GEMM C = A B^T on one shape (kernel profiling)")
+    ap.add_argument("--vector-kernels", default=None, metavar="N,NX,NY,M",
+                    help="time only the solver's Gram and vecmat kernels on synthetic vectors (kernel profiling)")
     ap.add_argument("--sigma", default=None, metavar="O,V[,SIDE]",
                     help="time only one batched sigma product of 8 vectors on an O/V system (kernel profiling)")
     args = ap.parse_args()
@@ -327,6 +346,9 @@ def main():
         return
     if args.sigma:
         run_sigma(args)
+        return
+    if args.vector_kernels:
+        run_vector_kernels(args)
         return
     world, rank, local = dist_init()
     if args.impl == "reference":

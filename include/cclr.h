@@ -180,6 +180,19 @@ cclr_status cclr_hessian(cclr_ctx *ctx, int nvec, const cclr_c128 *u, cclr_c128 
 cclr_status cclr_zgemm_nt(cclr_ctx *ctx, int precision, int M, int N, int K, const cclr_c128 *A,
                           const cclr_c128 *B, cclr_c128 *C);
 
+/* The Davidson solver's multi-vector kernels on their own (measurement; the paper's Davidson
+ * scheme, SI "Davidson scheme", does these passes over the trial vectors every iteration).
+ * On nx + max(ny, m) synthetic device vectors of length n (deterministic values, allocated and
+ * freed here), after one warm-up call each, times `reps` calls of
+ *   ms3[0]  the Gram block X^H Y (nx x ny),
+ *   ms3[1]  Y_q = sum_j X_j C_jq for m outputs, squared norms only (the residual-norm pass),
+ *   ms3[2]  the same with the m outputs stored (the correction pass),
+ * and returns milliseconds per call (CUDA events on the context's stream).  precision
+ * CCLR_FP64 runs the FP64 kernels, the tensor-core modes the FP32-arithmetic ones the solver
+ * uses there.  1 <= m <= 16, nx <= 512.  Needs a Hamiltonian (for the context's workspace). */
+cclr_status cclr_bench_vector_kernels(cclr_ctx *ctx, int precision, int64_t n, int nx, int ny, int m, int reps,
+                                      double *ms3);
+
 /* Allocation-free tensor-core GEMM (the paper has no counterpart; it serves callers that cannot
  * allocate device memory: a framework that owns all device memory through its own pool, a
  * server that fixes its footprint after start-up, or code running where an allocation may block).

@@ -35,7 +35,7 @@ EXPORTS = (
     "cclr_get_amplitudes",
     "cclr_set_amplitudes", "cclr_get_response_vector", "cclr_sigma", "cclr_residual", "cclr_xi",
     "cclr_eta", "cclr_hessian", "cclr_zgemm_nt", "cclr_kernel_profile", "cclr_get_stats",
-    "cclr_zgemm_nt_noalloc", "cclr_kernel_breakdown",
+    "cclr_zgemm_nt_noalloc", "cclr_kernel_breakdown", "cclr_bench_vector_kernels",
 )
 
 
@@ -77,6 +77,7 @@ _sig = {
     "cclr_kernel_breakdown": (_i, [_vp, ctypes.c_char_p, _i]),
     "cclr_zgemm_nt_noalloc": (_i, [_i, _i, _i, _i, _vp, _vp, _vp, _vp]),
     "cclr_get_stats": (_i, [_vp, ctypes.POINTER(Stats)]),
+    "cclr_bench_vector_kernels": (_i, [_vp, _i, ctypes.c_int64, _i, _i, _i, _i, _vp]),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(_lib, _name)
@@ -261,6 +262,13 @@ class Context:
         C = np.zeros((A.shape[0], B.shape[0]), np.complex128)
         self._check(_lib.cclr_zgemm_nt(self._h, precision, A.shape[0], B.shape[0], A.shape[1], _ptr(A), _ptr(B), _ptr(C)))
         return C
+
+    def cclr_bench_vector_kernels(self, n, nx, ny, m, reps=5, precision=TC_BF16X3) -> dict:
+        """Milliseconds per call of the solver's Gram block (nx x ny), residual-norm pass and
+        correction pass (m outputs from nx rows) on synthetic device vectors of length n."""
+        out = np.zeros(3, np.float64)
+        self._check(_lib.cclr_bench_vector_kernels(self._h, precision, int(n), nx, ny, m, reps, _ptr(out)))
+        return dict(gram_ms=float(out[0]), norms_ms=float(out[1]), write_ms=float(out[2]))
 
     def cclr_kernel_profile(self, enable=True) -> dict:
         """Tensor-core kernel timing (CUDA events on the library's stream) since the last call."""

@@ -45,7 +45,7 @@ cclr_status guard(cclr_ctx* h, F&& fn) {
       CCLR_CK(cudaMemcpy(&h, c.tc_err, sizeof(int), cudaMemcpyDeviceToHost));
       if (h) {
         CCLR_CK(cudaMemset(c.tc_err, 0, sizeof(int)));
-        throw Error(CCLR_E_TIMEOUT, "tensor-core GEMM: a bounded wait expired (code " + std::to_string(h) + ")");
+        throw Error(CCLR_E_TIMEOUT, "a bounded device wait expired (code " + std::to_string(h) + ")");
       }
     }
   } catch (const Error& e) {
@@ -150,6 +150,12 @@ cclr_status cclr_create(cclr_ctx** out, int device, const cclr_options* opt) {
   c.L.s = c.stream;
   c.L.count = &c.launches;
   c.L.kt = &c.kt;
+  if (cudaMalloc((void**)&c.tc_err, sizeof(int)) != cudaSuccess || cudaMemset(c.tc_err, 0, sizeof(int)) != cudaSuccess) {
+    cudaStreamDestroy(c.stream);
+    delete h;
+    return CCLR_E_CUDA;
+  }
+  c.L.err = c.tc_err;
   *out = h;
   return CCLR_OK;
 }
@@ -470,6 +476,75 @@ cclr_status cclr_zgemm_nt(cclr_ctx* h, int precision, int M, int N, int K, const
       throw;
     }
     c.opt.precision = saved;
+  });
+}
+
+cclr_status cclr_bench_vector_kernels(cclr_ctx* h, int precision, int64_t n, int nx, int ny, int m, int reps,
+                                      double* ms3) {
+  return guard(h, [&](Ctx& c) {
+    CCLR_REQUIRE(c.have_ham, CCLR_E_STATE, "cclr_bench_vector_kernels needs a Hamiltonian (device workspace)");
+    CCLR_REQUIRE(n >= 1 && nx >= 1 && ny >= 1 && m >= 1 && m <= kVecMatOut && nx <= kVecMatMaxRows && reps >= 1 && ms3,
+                 CCLR_E_ARG, "bad vector-kernel benchmark arguments");
+    CCLR_REQUIRE(precision == CCLR_FP64 || precision == CCLR_TC_BF16X3 || precision == CCLR_TC_BF16X6, CCLR_E_ARG,
+                 "unknown precision");
+    const bool saved = c.L.fast32;
+    c.L.fast32 = precision != CCLR_FP64;
+    cplx *X = nullptr, *Y = nullptr, *C = nullptr, *G = nullptr, *scr = nullptr;
+    double *vs = nullptr, *n2 = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto cleanup = [&]() {
+      c.L.fast32 = saved;
+      for (cplx* p : {X, Y, C, G, scr}) c.dfree(p);
+      c.dfree((cplx*)vs);
+      c.dfree((cplx*)n2);
+      if (e0) cudaEventDestroy(e0);
+      if (e1) cudaEventDestroy(e1);
+    };
+    try {
+      X = c.dalloc((int64_t)nx * n);
+      Y = c.dalloc((int64_t)std::max(ny, m) * n);   // Gram operand (ny rows) and vecmat outputs (m rows)
+      C = c.dalloc((int64_t)nx * m);
+      G = c.dalloc((int64_t)nx * ny);
+      scr = c.dalloc(gram_scratch_elems());
+      vs = (double*)c.dalloc((vecmat_scratch_doubles() + 1) / 2);
+      n2 = (double*)c.dalloc(kVecMatOut);
+      fill_hash(c.L, X, (int64_t)nx * n, 1);
+      fill_hash(c.L, Y, (int64_t)ny * n, 2);
+      fill_hash(c.L, C, (int64_t)nx * m, 3);
+      CCLR_CK(cudaEventCreate(&e0));
+      CCLR_CK(cudaEventCreate(&e1));
+      Rows rx, ry;
+      rx.add(X, nx, n);
+      ry.add(Y, ny, n);
+      VecMat norms;   // Y_q = sum_j X_j C_jq, norms only (the solver's residual-norm pass)
+      norms.X = rx;
+      norms.m = m;
+      norms.C = C;
+      norms.norm2 = n2;
+      VecMat write = norms;   // the same with the outputs stored (candidate corrections)
+      write.Y = Y;
+      write.ldy = n;
+      const int calls = 3;
+      for (int k = 0; k < calls; ++k) {
+        auto run = [&]() {
+          if (k == 0) gram(c.L, n, rx, ry, true, G, scr, gram_scratch_elems());
+          else vecmat(c.L, n, k == 1 ? norms : write, vs);
+        };
+        run();   // warm-up
+        CCLR_CK(cudaEventRecord(e0, c.stream));
+        for (int r = 0; r < reps; ++r) run();
+        CCLR_CK(cudaEventRecord(e1, c.stream));
+        CCLR_CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CCLR_CK(cudaEventElapsedTime(&ms, e0, e1));
+        ms3[k] = ms / reps;
+      }
+      c.sync();
+    } catch (...) {
+      cleanup();
+      throw;
+    }
+    cleanup();
   });
 }
 

@@ -167,12 +167,16 @@ struct Launch {  // stream + launch counter shared by all kernels of one context
   // FP32 arithmetic (FP64 storage) in the solvers' vector kernels (dots, vecmat, Gram blocks);
   // set by the iterative solvers in the tensor-core modes only.
   bool fast32 = false;
+  // device status word of the context: kernels with bounded waits record an expiry here (the
+  // API layer checks it at the end of every call)
+  int* err = nullptr;
 };
 
 // dst = alpha * op(src) + (accumulate ? dst : 0), element-wise over dst's shape; src must
 // have the same rank/dims (strides arbitrary).
 void permute(const Launch& L, const Tensor& src, const Tensor& dst, cplx alpha, bool accumulate);
 void fill_zero(const Launch& L, cplx* p, int64_t n);
+void fill_hash(const Launch& L, cplx* p, int64_t n, uint64_t seed);   // deterministic values in [-1, 1)^2
 
 // Row-major complex FP64 GEMM: C[MxN] = alpha op(A) op(B) + beta C; op(A)[m,k] = ta ? A[k*lda+m]
 // : A[m*lda+k]; op(B)[k,n] = tb ? B[n*ldb+k] : B[k*ldb+n].

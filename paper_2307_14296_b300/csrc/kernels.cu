@@ -169,6 +169,19 @@ __global__ void __launch_bounds__(256) k_permute_tiled(TileArgs a, const cplx* _
   }
 }
 
+// p[i] = deterministic values in [-1, 1) + i [-1, 1) from a 64-bit mix of (seed, i) (test and
+// benchmark operands)
+__global__ void k_fill_hash(cplx* p, int64_t n, uint64_t seed) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t h = (uint64_t)i * 0x9E3779B97F4A7C15ull + seed;
+    h ^= h >> 31;
+    h *= 0xBF58476D1CE4E5B9ull;
+    h ^= h >> 29;
+    const uint32_t a = (uint32_t)h, b = (uint32_t)(h >> 32);
+    p[i] = make_double2((double)a * 0x1p-31 - 1.0, (double)b * 0x1p-31 - 1.0);
+  }
+}
+
 __global__ void k_fill_zero(cplx* p, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     p[i] = make_double2(0.0, 0.0);
@@ -510,7 +523,7 @@ __device__ __forceinline__ uint64_t ffma2(uint64_t a, uint64_t b, uint64_t c) {
 template <bool F32> struct Arith;
 template <> struct Arith<true> {
   struct __align__(16) C { uint64_t re, im; };
-  struct X { uint64_t a, b; };
+  struct __align__(16) X { uint64_t a, b; };
   typedef uint64_t Acc;
   __device__ static C coef(float2 c) {
     C r;
@@ -726,23 +739,38 @@ __global__ void k_unpack2(const cplx* __restrict__ D, int64_t ldd, cplx* X, int6
 
 // Gram tile for tall-skinny operands: part[blk][i][j] = sum over this block's share of the
 // elements of op(X_i[k]) Y_j[k], nx <= 32 RL, ny <= NY.  Chunks of 2^lc elements of all rows are
-// copied to shared memory with cp.async, double-buffered (the chunk grows as the row count falls,
-// so that about 64 KiB per SM are in flight whatever the tile); lane l owns rows l, l+32, ... of X
-// and all rows of Y (read as shared-memory broadcasts); the 8 warps split each chunk's elements
-// and are summed at the end.  F32: each chunk is converted to FP32 once in shared memory;
-// products are summed in FP32 pairs over runs of 32 elements per warp and the runs added with a
-// compensated (two-sum) FP32 accumulator.
+// brought into shared memory by bulk asynchronous copies (one per row, completion counted on an
+// mbarrier), double-buffered; the chunk grows as the row count falls, so that about 64 KiB per SM
+// are in flight whatever the tile.  Lane l owns rows l, l+32, ... of X and all rows of Y (read as
+// shared-memory broadcasts); the 16 warps split each chunk's elements and are summed at the end.
+// F32: each chunk is converted to FP32 once, in place in shared memory, into
+// the packed forms the paired FMAs take; products are summed in FP32 pairs over runs of 32
+// elements per warp and the runs added with a compensated (two-sum) FP32 accumulator.  The mbarrier waits are bounded: on expiry the block records code
+// 11 in the context's status word, waits (bounded) for its copies in flight and returns.
 constexpr int kGramRunElems = 32;            // elements per warp in one FP32 run
-constexpr int kGramMaxX = 64, kGramMaxY = 8; // tile of one launch
+constexpr int kGramMaxX = 32, kGramMaxY = 8; // tile of one launch (one X row per lane)
+constexpr int kGramWarps = 16;               // 512 threads: enough warps per SM to hide latencies
 constexpr int kGramMinLog = 6, kGramMaxLog = 11;   // chunk of 64 .. 2048 elements
+constexpr int kGramHead = 128;               // bytes before the staging buffers (two mbarriers)
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ bool bar_try_wait(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+// bounded wait (about a second): false if the phase did not complete
+__device__ __forceinline__ bool bar_wait(uint64_t* b, uint32_t parity) {
+  for (uint32_t i = 0; i < (1u << 22); ++i) {
+    if (bar_try_wait(b, parity)) return true;
+    if (i > 64) __nanosleep(256);
+  }
+  return false;
+}
 
 // hi + lo += v with the rounding error of the addition kept in lo (Knuth's two-sum)
 __device__ __forceinline__ void two_sum(float& hi, float& lo, float v) {
@@ -753,29 +781,43 @@ __device__ __forceinline__ void two_sum(float& hi, float& lo, float v) {
 }
 
 template <bool F32, int RL, int NY>
-__global__ void __launch_bounds__(256, 1) k_gram_skinny(int64_t n, Rows X, Rows Y, bool herm, cplx* part, int lc) {
+__global__ void __launch_bounds__(kGramWarps * 32, 1)
+    k_gram_skinny(int64_t n, Rows X, Rows Y, bool herm, cplx* part, int lc, int* __restrict__ err) {
   typedef Arith<F32> A;
-  extern __shared__ __align__(16) unsigned char gs_smem[];
+  extern __shared__ __align__(128) unsigned char gs_smem[];
   const int nx = X.total(), ny = Y.total(), nr = nx + ny;
   const int CH = 1 << lc, pitch = CH + 1;   // padded row pitch: lanes reading distinct rows hit distinct banks
-  cplx* stage[2];
-  stage[0] = reinterpret_cast<cplx*>(gs_smem);
-  stage[1] = stage[0] + (size_t)nr * pitch;
-  float2* cv = reinterpret_cast<float2*>(stage[1] + (size_t)nr * pitch);   // F32 copy of a chunk
-  const cplx** rowp = reinterpret_cast<const cplx**>(cv + (F32 ? (size_t)nr * pitch : 0));
+  uint64_t* bar = reinterpret_cast<uint64_t*>(gs_smem);
+  cplx* st0 = reinterpret_cast<cplx*>(gs_smem + kGramHead);
+  cplx* st1 = st0 + (size_t)nr * pitch;
+  const cplx** rowp = reinterpret_cast<const cplx**>(st1 + (size_t)nr * pitch);
   for (int r = threadIdx.x; r < nr; r += blockDim.x) rowp[r] = r < nx ? row_of(X, r) : row_of(Y, r - nx);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar[0])) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar[1])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t nchunks = (n + CH - 1) >> lc;
-  const int per_warp = CH >> 3;
+  const int per_warp = CH / kGramWarps;
   const int flush_every = per_warp >= kGramRunElems ? 1 : kGramRunElems / per_warp;   // chunks per run
+  // warp 0: bulk copies of chunk ch (all rows) into stage s
   auto issue = [&](int s, int64_t ch) {
     const int64_t base = ch << lc;
-    for (int e = threadIdx.x; e < nr * CH; e += blockDim.x) {
-      const int r = e >> lc, k = e & (CH - 1);
-      if (base + k < n) cp_async16(stage[s] + r * pitch + k, rowp[r] + base + k);
-    }
-    cp_async_commit();
+    const uint32_t bytes = (uint32_t)(min((int64_t)CH, n - base) * (int64_t)sizeof(cplx));
+    cplx* dst = s ? st1 : st0;
+    if (lane == 0)
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(&bar[s])),
+                   "r"(bytes * (uint32_t)nr)
+                   : "memory");
+    __syncwarp();
+    for (int r = lane; r < nr; r += 32)
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+              smem_addr(dst + (size_t)r * pitch)),
+          "l"(rowp[r] + base), "r"(bytes), "r"(smem_addr(&bar[s]))
+          : "memory");
   };
   typename A::Acc acc[RL][NY];
   float hi[RL][NY][2], lo[RL][NY][2];   // F32 run totals (two-sum)
@@ -799,11 +841,15 @@ __global__ void __launch_bounds__(256, 1) k_gram_skinny(int64_t n, Rows X, Rows 
         }
       }
   };
+  // F32: the staged chunk holds every element already in its packed operand form (Y rows) or
+  // coefficient form (X rows), 16 bytes each, so the products need no register moves
+  typedef typename A::X PX;
+  typedef typename A::C PC;
   auto mac_elem = [&](const cplx* st, int k) {
     typename A::X yv[NY];
 #pragma unroll
     for (int j = 0; j < NY; ++j) {
-      if constexpr (F32) yv[j] = A::opnd(j < ny ? cv[(nx + j) * pitch + k] : make_float2(0.f, 0.f));
+      if constexpr (F32) yv[j] = j < ny ? reinterpret_cast<const PX*>(st)[(nx + j) * pitch + k] : PX{0ull, 0ull};
       else yv[j] = A::opnd(j < ny ? st[(nx + j) * pitch + k] : make_double2(0.0, 0.0));
     }
 #pragma unroll
@@ -811,7 +857,7 @@ __global__ void __launch_bounds__(256, 1) k_gram_skinny(int64_t n, Rows X, Rows 
       const int r = lane + 32 * a;
       typename A::C xc;
       if constexpr (F32) {
-        xc = A::coef(r < nx ? cv[r * pitch + k] : make_float2(0.f, 0.f));
+        xc = r < nx ? reinterpret_cast<const PC*>(st)[r * pitch + k] : PC{0ull, 0ull};
       } else {
         cplx xv = r < nx ? st[r * pitch + k] : make_double2(0.0, 0.0);
         if (herm) xv.y = -xv.y;
@@ -821,26 +867,47 @@ __global__ void __launch_bounds__(256, 1) k_gram_skinny(int64_t n, Rows X, Rows 
       for (int j = 0; j < NY; ++j) A::mac(acc[a][j], xc, yv[j]);
     }
   };
+  uint32_t uses0 = 0, uses1 = 0;   // completed phases per stage (the wait parity)
   int s = 0, run = 0;
-  if ((int64_t)blockIdx.x < nchunks) issue(0, blockIdx.x);
+  if (warp == 0 && (int64_t)blockIdx.x < nchunks) issue(0, blockIdx.x);
   for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
     const bool more = ch + gridDim.x < nchunks;
-    if (more) {
-      issue(s ^ 1, ch + gridDim.x);
-      cp_async_wait1();
-    } else {
-      cp_async_wait0();
+    if (more && warp == 0) issue(s ^ 1, ch + gridDim.x);
+    const bool ok = bar_wait(&bar[s], (s ? uses1 : uses0) & 1u);
+    if (__syncthreads_or(!ok)) {
+      // give up: record the expiry, let the copies in flight land (bounded), return
+      if (threadIdx.x == 0) {
+        atomicExch(err, 11);
+        bar_wait(&bar[s], (s ? uses1 : uses0) & 1u);
+        if (more) bar_wait(&bar[s ^ 1], (s ? uses0 : uses1) & 1u);
+      }
+      __syncthreads();
+      return;
     }
-    __syncthreads();
-    const cplx* st = stage[s];
+    if (s) ++uses1; else ++uses0;
+    cplx* st = s ? st1 : st0;
     const int64_t base = ch << lc;
+    const int lim = (int)min((int64_t)CH, n - base);
     if constexpr (F32) {
-      for (int e = threadIdx.x; e < nr * CH; e += blockDim.x) {
-        const int r = e >> lc, k = e & (CH - 1);
-        if (base + k < n) {
-          float2 v = d2f2(st[r * pitch + k]);
-          if (herm && r < nx) v.y = -v.y;
-          cv[r * pitch + k] = v;
+      // in place: each FP64 element becomes its 16-byte FP32 packed form; a warp per row when
+      // there are enough rows, else all threads over the rows x chunk elements
+      const float sg = herm ? -1.f : 1.f;   // coefficient of conj(x) for the Hermitian product
+      auto pack = [&](cplx* p, bool xrow) {
+        const float2 v = d2f2(*p);
+        if (xrow) {
+          const float ci = sg * v.y;
+          *reinterpret_cast<PC*>(p) = PC{pk2(v.x, v.x), pk2(-ci, ci)};
+        } else {
+          *reinterpret_cast<PX*>(p) = PX{pk2(v.x, v.y), pk2(v.y, v.x)};
+        }
+      };
+      if (nr >= kGramWarps) {
+        for (int r = warp; r < nr; r += kGramWarps)
+          for (int k = lane; k < lim; k += 32) pack(st + (size_t)r * pitch + k, r < nx);
+      } else {
+        for (int e = threadIdx.x; e < nr * CH; e += blockDim.x) {
+          const int r = e >> lc, k = e & (CH - 1);
+          if (k < lim) pack(st + (size_t)r * pitch + k, r < nx);
         }
       }
       __syncthreads();
@@ -851,7 +918,7 @@ __global__ void __launch_bounds__(256, 1) k_gram_skinny(int64_t n, Rows X, Rows 
 #pragma unroll 2
       for (int t = 0; t < len; ++t) {
         const int k = k0 + kk + t;
-        if (base + k < n) mac_elem(st, k);
+        if (k < lim) mac_elem(st, k);
       }
       if (per_warp >= kGramRunElems) flush();
     }
@@ -863,8 +930,9 @@ __global__ void __launch_bounds__(256, 1) k_gram_skinny(int64_t n, Rows X, Rows 
     s ^= 1;
   }
   flush();
-  // sum the 8 warps' shares in shared memory (the staging buffers are free now)
-  cplx* red = reinterpret_cast<cplx*>(gs_smem);   // [warp][a][j][lane]
+  // sum the 8 warps' shares in shared memory (the staging buffers are free now; the mbarriers
+  // in the head are left alone)
+  cplx* red = reinterpret_cast<cplx*>(gs_smem + kGramHead);   // [warp][a][j][lane]
 #pragma unroll
   for (int a = 0; a < RL; ++a)
 #pragma unroll
@@ -882,7 +950,7 @@ __global__ void __launch_bounds__(256, 1) k_gram_skinny(int64_t n, Rows X, Rows 
     const int i = o / ny, j = o % ny;
     const int a = i / 32, l = i % 32;
     cplx v = make_double2(0.0, 0.0);
-    for (int w = 0; w < 8; ++w) v = cadd(v, red[((w * RL + a) * NY + j) * 32 + l]);
+    for (int w = 0; w < kGramWarps; ++w) v = cadd(v, red[((w * RL + a) * NY + j) * 32 + l]);
     part[(int64_t)blockIdx.x * nx * ny + o] = v;
   }
 }
@@ -972,27 +1040,22 @@ constexpr size_t kGramSmemMax = 200 << 10;
 template <bool F32, int RL, int NY>
 void launch_gram(const Launch& L, int nblk, size_t smem, int64_t n, const Rows& X, const Rows& Y, bool herm,
                  cplx* part, int lc) {
+  CCLR_REQUIRE(L.err, CCLR_E_STATE, "gram: no device status word");
   static bool attr = false;
   if (!attr) {
     CCLR_CK(cudaFuncSetAttribute(k_gram_skinny<F32, RL, NY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kGramSmemMax));
     attr = true;
   }
-  k_gram_skinny<F32, RL, NY><<<nblk, 256, smem, L.s>>>(n, X, Y, herm, part, lc);
+  k_gram_skinny<F32, RL, NY><<<nblk, kGramWarps * 32, smem, L.s>>>(n, X, Y, herm, part, lc, L.err);
 }
 template <bool F32>
 void launch_gram_tile(const Launch& L, int nblk, size_t smem, int64_t n, const Rows& X, const Rows& Y, bool herm,
                       cplx* part, int lc) {
-  const int a = X.total(), b = Y.total();
-  if (a <= 32) {
-    if (b == 1) launch_gram<F32, 1, 1>(L, nblk, smem, n, X, Y, herm, part, lc);
-    else if (b <= 4) launch_gram<F32, 1, 4>(L, nblk, smem, n, X, Y, herm, part, lc);
-    else launch_gram<F32, 1, 8>(L, nblk, smem, n, X, Y, herm, part, lc);
-  } else {
-    if (b == 1) launch_gram<F32, 2, 1>(L, nblk, smem, n, X, Y, herm, part, lc);
-    else if (b <= 4) launch_gram<F32, 2, 4>(L, nblk, smem, n, X, Y, herm, part, lc);
-    else launch_gram<F32, 2, 8>(L, nblk, smem, n, X, Y, herm, part, lc);
-  }
+  const int b = Y.total();   // X.total() <= kGramMaxX = 32: one row per lane
+  if (b == 1) launch_gram<F32, 1, 1>(L, nblk, smem, n, X, Y, herm, part, lc);
+  else if (b <= 4) launch_gram<F32, 1, 4>(L, nblk, smem, n, X, Y, herm, part, lc);
+  else launch_gram<F32, 1, 8>(L, nblk, smem, n, X, Y, herm, part, lc);
 }
 }  // namespace
 
@@ -1011,8 +1074,7 @@ void gram(const Launch& L, int64_t n, const Rows& X, const Rows& Y, bool herm, c
       // chunk: at least 64 KiB of rows per stage (the bytes each SM keeps in flight), within the
       // shared-memory budget of two stages plus the FP32 copy
       auto stage_bytes = [&](int lc) {
-        return (2 * sizeof(cplx) + (L.fast32 ? sizeof(float2) : 0)) * (size_t)(a + b) * ((size_t(1) << lc) + 1) +
-               sizeof(void*) * (size_t)(a + b);
+        return kGramHead + 2 * sizeof(cplx) * (size_t)(a + b) * ((size_t(1) << lc) + 1) + sizeof(void*) * (size_t)(a + b);
       };
       int lc = kGramMinLog;
       while (lc < kGramMaxLog && ((size_t)(a + b) * sizeof(cplx) << lc) < (size_t(64) << 10) &&
@@ -1021,8 +1083,8 @@ void gram(const Launch& L, int64_t n, const Rows& X, const Rows& Y, bool herm, c
       const int64_t nchunks = (n + (int64_t(1) << lc) - 1) >> lc;
       int nblk = (int)std::min<int64_t>(148, nchunks);
       if ((int64_t)nblk * a * b > scratch_elems) nblk = (int)std::max<int64_t>(1, scratch_elems / ((int64_t)a * b));
-      const int RL = a <= 32 ? 1 : 2, NYt = b == 1 ? 1 : (b <= 4 ? 4 : 8);
-      const size_t red = sizeof(cplx) * 8 * RL * NYt * 32;
+      const int NYt = b == 1 ? 1 : (b <= 4 ? 4 : 8);
+      const size_t red = kGramHead + sizeof(cplx) * kGramWarps * NYt * 32;
       const size_t smem = std::max(stage_bytes(lc), red);
       CCLR_REQUIRE(smem <= kGramSmemMax, CCLR_E_ARG, "gram: tile too large");
       kbeg(L);
@@ -1169,6 +1231,14 @@ void permute(const Launch& L, const Tensor& src, const Tensor& dst, cplx alpha, 
   else launch_permute<2>(L, a, src.p, dst.p, n, al, src.conj, accumulate);
   CCLR_CK(cudaGetLastError());
   bump(L, "k_permute");
+}
+
+void fill_hash(const Launch& L, cplx* p, int64_t n, uint64_t seed) {
+  if (n <= 0) return;
+  kbeg(L);
+  k_fill_hash<<<grid_for(n), kThreads, 0, L.s>>>(p, n, seed);
+  CCLR_CK(cudaGetLastError());
+  bump(L, "k_fill_hash");
 }
 
 void fill_zero(const Launch& L, cplx* p, int64_t n) {

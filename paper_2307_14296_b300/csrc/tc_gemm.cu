@@ -577,12 +577,16 @@ struct Slices {
   CUtensorMap tm;
 };
 
-// Slices of persistent operands (integrals, Hbar, amplitudes) are kept for one generation of
-// the context's data (bumped whenever any of them changes) keyed by pointer and view layout.
+// Slices of persistent operands (integrals, Hbar, amplitudes) are kept keyed by pointer and view
+// layout.  Those of the integrals live until the Hamiltonian changes; the others for one
+// generation of the context's data (bumped whenever amplitudes, Lambda or Hbar change).  When the
+// cache is full, integral slices not read in the current generation are evicted, largest first.
 struct CacheEntry {
   Slices s;
-  uint64_t gen = 0;
+  uint64_t gen = 0;    // data generation of the last use
+  bool integral = false;
 };
+size_t entry_bytes(const CacheEntry& e) { return sizeof(__nv_bfloat16) * 2 * e.s.nsl * e.s.rows * e.s.Kpad; }
 std::map<std::string, CacheEntry>& cache() {
   static std::map<std::string, CacheEntry> m;
   return m;
@@ -682,6 +686,13 @@ void make_slices(Ctx& c, const Tensor& v, int nr, int nsl, Slices& s, __nv_bfloa
   s.tm = make_map(dst, rows, s.Kpad, 2 * nsl, 128);
 }
 
+bool is_integral(const Ctx& c, const void* p) {
+  const void* arr[] = {c.oooo, c.ooov, c.oovv, c.ovov, c.ovvv, c.vvvv_p, c.oovv_p, c.ovvv_p};
+  for (const void* q : arr)
+    if (q && q == p) return true;
+  return false;
+}
+
 bool is_persistent(const Ctx& c, const void* p) {
   const void* arr[] = {c.Fae, c.Fmi, c.Fae_od, c.Fmi_od, c.Fme, c.Wmnij, c.Wmnij_p, c.Wabef_p, c.Wmbej, c.WringR, c.WringL, c.Wmnie,
                        c.Wamef, c.Wmbij, c.Wabei, c.tau, c.t2, c.l2, c.oooo, c.ooov, c.oovv, c.ovov, c.ovvv,
@@ -712,8 +723,14 @@ std::vector<Memo>& memos() {
 // of a transient operand named by a SliceMemo, else into the workspace.
 Slices get_slices(Ctx& c, const Tensor& v, int nr, int nsl) {
   if (g_cache_gen != data_generation()) {
-    for (auto& kv : cache()) cudaFree(kv.second.s.p);
-    cache().clear();
+    for (auto it = cache().begin(); it != cache().end();) {
+      if (it->second.integral) {
+        ++it;
+        continue;
+      }
+      cudaFree(it->second.s.p);
+      it = cache().erase(it);
+    }
     g_cache_gen = data_generation();
   }
   int64_t elems = 1;
@@ -729,13 +746,27 @@ Slices get_slices(Ctx& c, const Tensor& v, int nr, int nsl) {
                       std::to_string((int)v.conj);
     for (int i = 0; i < v.rank; ++i) key += "|" + std::to_string(v.dim[i]) + ":" + std::to_string(v.str[i]);
     auto it = cache().find(key);
-    if (it != cache().end()) return it->second.s;
-    size_t cached = 0;
-    for (auto& kv : cache()) cached += sizeof(__nv_bfloat16) * 2 * kv.second.s.nsl * kv.second.s.rows * kv.second.s.Kpad;
+    if (it != cache().end()) {
+      it->second.gen = data_generation();
+      return it->second.s;
+    }
+    const double cap = cap_gb * (double)(1ull << 30);
+    size_t cached = tc_cache_bytes();
+    while ((double)(cached + bytes) > cap) {   // evict the largest integral entry idle this generation
+      auto victim = cache().end();
+      for (auto e = cache().begin(); e != cache().end(); ++e)
+        if (e->second.integral && e->second.gen != data_generation() &&
+            (victim == cache().end() || entry_bytes(e->second) > entry_bytes(victim->second)))
+          victim = e;
+      if (victim == cache().end()) break;
+      cached -= entry_bytes(victim->second);
+      cudaFree(victim->second.s.p);
+      cache().erase(victim);
+    }
     __nv_bfloat16* dst = nullptr;
-    if ((double)(cached + bytes) <= cap_gb * (double)(1ull << 30) && cudaMalloc((void**)&dst, bytes) == cudaSuccess) {
+    if ((double)(cached + bytes) <= cap && cudaMalloc((void**)&dst, bytes) == cudaSuccess) {
       make_slices(c, v, nr, nsl, s, dst);
-      cache()[key] = CacheEntry{s, data_generation()};
+      cache()[key] = CacheEntry{s, data_generation(), is_integral(c, v.p)};
       return s;
     }
     cudaGetLastError();  // out of memory for the cache: fall through to a workspace copy
@@ -812,7 +843,7 @@ void tc_release_cache() {   // cudaFree waits for the kernels still reading the 
 void tc_release_cache_for(Ctx&) { tc_release_cache(); }
 size_t tc_cache_bytes() {
   size_t t = 0;
-  for (auto& kv : cache()) t += sizeof(__nv_bfloat16) * 2 * kv.second.s.nsl * kv.second.s.rows * kv.second.s.Kpad;
+  for (auto& kv : cache()) t += entry_bytes(kv.second);
   return t;
 }
 
