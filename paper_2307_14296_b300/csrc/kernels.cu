@@ -700,22 +700,23 @@ __global__ void k_sum_rows(const double* part, int nb, double* out) {
 
 
 // D[r][P(p,q)] = alpha (X[r,p,q] - X[r,q,p]) or alpha X[r,p,q]  (+ D), X strided (R, m, m)
+// grid: x over the pairs, y over the rows r (no index division)
 __global__ void k_pack2(const cplx* __restrict__ X, int64_t sr, int64_t sp, int64_t sq, cplx* D, int64_t ldd,
                         int64_t R, int64_t Pm, const int2* __restrict__ tab, cplx alpha, bool anti, bool acc) {
-  const int64_t n = R * Pm;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t P = idx % Pm, r = idx / Pm;
-    const int2 pq = tab[P];
-    cplx x = X[r * sr + pq.x * sp + pq.y * sq];
-    if (anti) {
-      const cplx y = X[r * sr + pq.y * sp + pq.x * sq];
-      x.x -= y.x;
-      x.y -= y.y;
+  for (int64_t r = blockIdx.y; r < R; r += gridDim.y) {
+    for (int64_t P = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; P < Pm; P += (int64_t)gridDim.x * blockDim.x) {
+      const int2 pq = tab[P];
+      cplx x = X[r * sr + pq.x * sp + pq.y * sq];
+      if (anti) {
+        const cplx y = X[r * sr + pq.y * sp + pq.x * sq];
+        x.x -= y.x;
+        x.y -= y.y;
+      }
+      if (!(alpha.x == 1.0 && alpha.y == 0.0)) x = cmul(alpha, x);
+      const int64_t o = r * ldd + P;
+      if (acc) x = cadd(x, D[o]);
+      D[o] = x;
     }
-    if (!(alpha.x == 1.0 && alpha.y == 0.0)) x = cmul(alpha, x);
-    const int64_t o = r * ldd + P;
-    if (acc) x = cadd(x, D[o]);
-    D[o] = x;
   }
 }
 
@@ -1020,7 +1021,9 @@ void pack2(const Launch& L, const Tensor& X, cplx* D, int64_t ldd, const int2* t
   if (R * Pm == 0) return;
   cplx al = make_double2(alpha.x * X.scale, alpha.y * X.scale);
   kbeg(L);
-  k_pack2<<<grid_for(R * Pm), kThreads, 0, L.s>>>(X.p, X.str[0], X.str[1], X.str[2], D, ldd, R, Pm, tab, al, anti, acc);
+  const dim3 grid((unsigned)std::min<int64_t>((Pm + kThreads - 1) / kThreads, 1024),
+                  (unsigned)std::min<int64_t>(R, 65535));
+  k_pack2<<<grid, kThreads, 0, L.s>>>(X.p, X.str[0], X.str[1], X.str[2], D, ldd, R, Pm, tab, al, anti, acc);
   CCLR_CK(cudaGetLastError());
   bump(L, "k_pack2");
 }
