@@ -241,7 +241,12 @@ struct VecMat {
   const cplx* z = nullptr;
   double* norm2 = nullptr;
   bool norm_y = false;
+  // X rows hold FP32 complex values (float2; row pointers cast to cplx*, strides in float2
+  // elements): the FP32 mirrors of the solver's trial vectors.  Needs Launch::fast32.
+  bool x32 = false;
 };
+// y[i] = x[i] rounded to FP32 (float2), n complex values (the solver's FP32 mirrors)
+void to_f32(const Launch& L, const cplx* x, void* y, int64_t n);
 constexpr int kVecMatOut = 16;        // outputs per pass
 constexpr int kVecMatMaxRows = 512;   // inputs per pass
 int64_t vecmat_scratch_doubles();

@@ -459,6 +459,11 @@ __device__ __forceinline__ double f2d(float x) {
 __device__ __forceinline__ float2 d2f2(cplx a) { return make_float2(d2f(a.x), d2f(a.y)); }
 __device__ __forceinline__ cplx f2d2(float2 a) { return make_double2(f2d(a.x), f2d(a.y)); }
 
+__global__ void k_to_f32(const cplx* __restrict__ x, float2* __restrict__ y, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = d2f2(x[i]);
+}
+
 // ---- FP32-arithmetic variants of the solver's vector kernels (FP64 storage).  FP64 on sm_103 runs
 // at ~1/64 of FP32, and the solver's multi-vector kernels do 8 L m flops per element (L inputs,
 // m outputs), so in FP64 they are ALU-bound by a wide margin; in FP32 they stay near the HBM
@@ -494,6 +499,20 @@ __device__ __forceinline__ const cplx* row_of(const Rows& r, int j) {
   for (int s = 0; s < 4; ++s) {
     if (p == nullptr && s < r.ns) {
       if (j < r.cnt[s]) p = r.p[s] + (int64_t)j * r.ld[s];
+      else j -= r.cnt[s];
+    }
+  }
+  return p;
+}
+
+// Row j of a Rows list of FP32 mirrors: base pointers are float2 arrays cast to cplx*, strides
+// counted in float2 elements.
+__device__ __forceinline__ const float2* row_of32(const Rows& r, int j) {
+  const float2* p = nullptr;
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    if (p == nullptr && s < r.ns) {
+      if (j < r.cnt[s]) p = reinterpret_cast<const float2*>(r.p[s]) + (int64_t)j * r.ld[s];
       else j -= r.cnt[s];
     }
   }
@@ -565,7 +584,7 @@ constexpr int kVecMatBlocks = 4 * 148;
 // zero and never stored); each thread takes E elements per step so that every coefficient read
 // from shared memory serves E elements.  With F32 the whole element pipeline (products, sums,
 // preconditioner, accumulation into Y) runs in FP32 and only loads and stores touch FP64.
-template <bool F32, int Q, int E, int U>
+template <bool F32, int Q, int E, int U, bool X32>
 __global__ void __launch_bounds__(kThreads, F32 ? 2 : 1)
     k_vecmat(int64_t n, Rows X, int m, const cplx* __restrict__ C, const cplx* __restrict__ add, cplx* Y, int64_t ldy,
              bool acc, const double* __restrict__ D, const cplx* __restrict__ z, bool norm_y, double* part) {
@@ -582,7 +601,8 @@ __global__ void __launch_bounds__(kThreads, F32 ? 2 : 1)
     const int j = e / Q, q = e % Q;
     cs[e] = A::coef(q < m ? C[(int64_t)j * m + q] : make_double2(0.0, 0.0));
   }
-  for (int j = threadIdx.x; j < nx; j += blockDim.x) rows[j] = row_of(X, j);
+  for (int j = threadIdx.x; j < nx; j += blockDim.x)
+    rows[j] = X32 ? reinterpret_cast<const cplx*>(row_of32(X, j)) : row_of(X, j);
   if (threadIdx.x < Q) {
     const cplx zq = (D && (int)threadIdx.x < m) ? z[threadIdx.x] : make_double2(0.0, 0.0);
     if constexpr (F32) zs[threadIdx.x] = d2f2(zq);
@@ -602,15 +622,17 @@ __global__ void __launch_bounds__(kThreads, F32 ? 2 : 1)
     // rows in groups of U: all loads of a group are issued before any is used, so that each
     // thread keeps U * E loads in flight
     for (int j0 = 0; j0 < nx; j0 += U) {
-      cplx raw[U][E];
+      typedef typename std::conditional<X32, float2, cplx>::type XV;
+      XV raw[U][E];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int j = j0 + u;
-        const cplx* rp = rows[j < nx ? j : 0];
+        const XV* rp = reinterpret_cast<const XV*>(rows[j < nx ? j : 0]);
 #pragma unroll
         for (int e = 0; e < E; ++e) {
           const int64_t i = i0 + (int64_t)e * blockDim.x;
-          raw[u][e] = (j < nx && i < n) ? __ldg(rp + i) : make_double2(0.0, 0.0);
+          if constexpr (X32) raw[u][e] = (j < nx && i < n) ? __ldg(rp + i) : make_float2(0.f, 0.f);
+          else raw[u][e] = (j < nx && i < n) ? __ldg(rp + i) : make_double2(0.0, 0.0);
         }
       }
 #pragma unroll
@@ -1106,7 +1128,7 @@ void gram(const Launch& L, int64_t n, const Rows& X, const Rows& Y, bool herm, c
 int64_t vecmat_scratch_doubles() { return (int64_t)kVecMatOut * kVecMatBlocks; }
 
 namespace {
-template <bool F32, int Q>
+template <bool F32, int Q, bool X32>
 void launch_vecmat(const Launch& L, int64_t n, const VecMat& a, double* part) {
   // E elements per thread (each shared-memory coefficient serves E elements), U rows of loads in
   // flight; the FP32 variants stay within 128 registers (two blocks per SM)
@@ -1116,10 +1138,10 @@ void launch_vecmat(const Launch& L, int64_t n, const VecMat& a, double* part) {
   const size_t smem = sizeof(typename Arith<F32>::C) * (size_t)nx * Q + sizeof(void*) * (size_t)nx;
   static bool attr = false;
   if (!attr) {   // kVecMatMaxRows x 16 coefficients (16 B each) + row table: 132 KiB
-    CCLR_CK(cudaFuncSetAttribute(k_vecmat<F32, Q, E, U>, cudaFuncAttributeMaxDynamicSharedMemorySize, 136 << 10));
+    CCLR_CK(cudaFuncSetAttribute(k_vecmat<F32, Q, E, U, X32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 136 << 10));
     attr = true;
   }
-  k_vecmat<F32, Q, E, U><<<kVecMatBlocks, kThreads, smem, L.s>>>(n, a.X, a.m, a.C, a.add, a.Y, a.ldy, a.acc, a.D, a.z,
+  k_vecmat<F32, Q, E, U, X32><<<kVecMatBlocks, kThreads, smem, L.s>>>(n, a.X, a.m, a.C, a.add, a.Y, a.ldy, a.acc, a.D, a.z,
                                                               a.norm_y, part);
 }
 }  // namespace
@@ -1133,16 +1155,22 @@ void vecmat(const Launch& L, int64_t n, const VecMat& a, double* scratch) {
   if (n <= 0) return;
   double* part = a.norm2 ? scratch : nullptr;
   kbeg(L);
-  if (L.fast32) {
-    if (a.m == 1) launch_vecmat<true, 1>(L, n, a, part);
-    else if (a.m <= 4) launch_vecmat<true, 4>(L, n, a, part);
-    else if (a.m <= 8) launch_vecmat<true, 8>(L, n, a, part);
-    else launch_vecmat<true, 16>(L, n, a, part);
+  CCLR_REQUIRE(!a.x32 || L.fast32, CCLR_E_ARG, "vecmat: FP32 rows need the FP32 arithmetic");
+  if (a.x32) {
+    if (a.m == 1) launch_vecmat<true, 1, true>(L, n, a, part);
+    else if (a.m <= 4) launch_vecmat<true, 4, true>(L, n, a, part);
+    else if (a.m <= 8) launch_vecmat<true, 8, true>(L, n, a, part);
+    else launch_vecmat<true, 16, true>(L, n, a, part);
+  } else if (L.fast32) {
+    if (a.m == 1) launch_vecmat<true, 1, false>(L, n, a, part);
+    else if (a.m <= 4) launch_vecmat<true, 4, false>(L, n, a, part);
+    else if (a.m <= 8) launch_vecmat<true, 8, false>(L, n, a, part);
+    else launch_vecmat<true, 16, false>(L, n, a, part);
   } else {
-    if (a.m == 1) launch_vecmat<false, 1>(L, n, a, part);
-    else if (a.m <= 4) launch_vecmat<false, 4>(L, n, a, part);
-    else if (a.m <= 8) launch_vecmat<false, 8>(L, n, a, part);
-    else launch_vecmat<false, 16>(L, n, a, part);
+    if (a.m == 1) launch_vecmat<false, 1, false>(L, n, a, part);
+    else if (a.m <= 4) launch_vecmat<false, 4, false>(L, n, a, part);
+    else if (a.m <= 8) launch_vecmat<false, 8, false>(L, n, a, part);
+    else launch_vecmat<false, 16, false>(L, n, a, part);
   }
   CCLR_CK(cudaGetLastError());
   bump(L, shaped("k_vecmat", nx, a.m, a.D ? 1 : 0));
@@ -1234,6 +1262,14 @@ void permute(const Launch& L, const Tensor& src, const Tensor& dst, cplx alpha, 
   else launch_permute<2>(L, a, src.p, dst.p, n, al, src.conj, accumulate);
   CCLR_CK(cudaGetLastError());
   bump(L, "k_permute");
+}
+
+void to_f32(const Launch& L, const cplx* x, void* y, int64_t n) {
+  if (n <= 0) return;
+  kbeg(L);
+  k_to_f32<<<grid_for(n), kThreads, 0, L.s>>>(x, (float2*)y, n);
+  CCLR_CK(cudaGetLastError());
+  bump(L, "k_to_f32");
 }
 
 void fill_hash(const Launch& L, cplx* p, int64_t n, uint64_t seed) {

@@ -249,6 +249,9 @@ struct System {            // one right-hand side with its shared trial space
   const cplx* rhs;         // b (device, N)
   std::vector<zc> z;       // shifts
   cplx *B = nullptr, *S = nullptr;
+  // FP32 mirrors of B and S (tensor-core modes): the passes whose arithmetic is FP32 anyway
+  // (residual norms, candidates, projections) read 8 instead of 16 bytes per element
+  void *Bf = nullptr, *Sf = nullptr;
   int L = 0;
   std::vector<zc> BS, BB;  // maxL x maxL: B^H S, B^H B
   std::vector<zc> Cp;      // -B^H b
@@ -346,7 +349,7 @@ void restart(Ctx& c, System& s, int maxL, int kmax) {
 // outside the trial space and the directions kept before it.  Returns the number appended.
 // cdev holds >= L * nt coefficients.
 int add_corrections(Ctx& c, cplx* B, int L, cplx* R, int nt, const double* pre2, int kmax, cplx* cdev,
-                    double* vscr) {
+                    double* vscr, const void* Bf = nullptr) {
   const int64_t N = c.N;
   if (kmax <= 0 || nt <= 0) return 0;
   if (L > 0) {
@@ -355,7 +358,8 @@ int add_corrections(Ctx& c, cplx* B, int L, cplx* R, int nt, const double* pre2,
     for (auto& x : g) x = -x;
     to_dev(c, g.data(), cdev, (int64_t)L * nt);
     VecMat a;
-    a.X = rows(c, B, L);
+    a.X = Bf ? rows(c, (const cplx*)Bf, L) : rows(c, B, L);
+    a.x32 = Bf != nullptr;
     a.m = nt;
     a.C = cdev;
     a.Y = R;
@@ -433,13 +437,26 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
     }
     to_dev(c, C.data(), cdev, (int64_t)2 * L * m);
   };
-  auto SB = [&](const System& s) { return Rows().add(s.S, s.L, N).add(s.B, s.L, N); };
+  auto SB = [&](const System& s) {
+    return s.Sf ? Rows().add((const cplx*)s.Sf, s.L, N).add((const cplx*)s.Bf, s.L, N)
+                : Rows().add(s.S, s.L, N).add(s.B, s.L, N);
+  };
+  // FP32 mirrors of the trial space in the tensor-core modes (rows [r0, r0 + nr) of B or S)
+  const bool mirrors = c.L.fast32;
+  for (auto& s : sys) {
+    s.Bf = mirrors ? c.ws.alloc(sizeof(float2) * (size_t)maxL * (size_t)N) : nullptr;
+    s.Sf = mirrors ? c.ws.alloc(sizeof(float2) * (size_t)maxL * (size_t)N) : nullptr;
+  }
+  auto mirror = [&](const cplx* X, void* Xf, int r0, int nr) {
+    if (Xf && nr > 0) to_f32(c.L, X + (int64_t)r0 * N, (float2*)Xf + (int64_t)r0 * N, (int64_t)nr * N);
+  };
   auto residual_norms = [&](System& s, const std::vector<int>& qs) {
     for (size_t g0 = 0; g0 < qs.size(); g0 += kVecMatOut) {
       const int m = (int)std::min<size_t>(kVecMatOut, qs.size() - g0);
       resid_coef(s, qs, g0, m);
       VecMat a;
       a.X = SB(s);
+      a.x32 = s.Sf != nullptr;
       a.m = m;
       a.C = cdev;
       a.add = s.rhs;
@@ -466,6 +483,7 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
     const double nb = std::sqrt(norm2(c, s.B));
     CCLR_REQUIRE(nb > 0.0, CCLR_E_ARG, "zero right-hand side");
     scale_vec(c.L, N, cx(1.0 / nb), s.B);
+    mirror(s.B, s.Bf, 0, 1);
     s.L = 1;
   }
   std::vector<int> fresh(sys.size(), 1);   // new vectors at the end of each basis
@@ -493,9 +511,11 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
       c.sync();
       c.stats.sigma_seconds += now() - t0;
       q = 0;
-      for (size_t k = 0; k < sys.size(); ++k)
+      for (size_t k = 0; k < sys.size(); ++k) {
         for (int j = 0; j < fresh[k]; ++j, ++q)
           copy_vec(c.L, N, out + (int64_t)q * N, sys[k].S + (int64_t)(sys[k].L - fresh[k] + j) * N);
+        mirror(sys[k].S, sys[k].Sf, sys[k].L - fresh[k], fresh[k]);
+      }
     }
     bool all_done = true;
     for (size_t k = 0; k < sys.size(); ++k) {
@@ -581,7 +601,11 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
       all_done = false;
       std::sort(order.begin(), order.end(), [](auto& a, auto& b) { return a.first > b.first; });
       ph.mark(c, "restart");
-      if (s.L + kMaxNew > maxL) restart(c, s, maxL, maxL - 2 * kMaxNew);
+      if (s.L + kMaxNew > maxL) {
+        restart(c, s, maxL, maxL - 2 * kMaxNew);
+        mirror(s.B, s.Bf, 0, s.L);
+        mirror(s.S, s.Sf, 0, s.L);
+      }
       // ---- preconditioned residuals of the worst shifts, one pass
       ph.mark(c, "candidates");
       const int nt = std::min<int>(kTry, (int)order.size());
@@ -594,6 +618,7 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
       {
         VecMat a;
         a.X = SB(s);
+        a.x32 = s.Sf != nullptr;
         a.m = nt;
         a.C = cdev;
         a.add = s.rhs;
@@ -609,7 +634,8 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
       }
       // ---- project out the trial space and append the new directions
       ph.mark(c, "project");
-      const int kk = add_corrections(c, s.B, s.L, R, nt, pre2, std::min(kMaxNew, maxL - s.L), cdev, vscr);
+      const int kk = add_corrections(c, s.B, s.L, R, nt, pre2, std::min(kMaxNew, maxL - s.L), cdev, vscr, s.Bf);
+      mirror(s.B, s.Bf, s.L, kk);
       if (kk == 0)
         throw Error(CCLR_E_NOCONV, "Davidson stagnated: residual " + std::to_string(order.front().first) +
                                        " above tolerance " + std::to_string(tol_s) + " with no new direction");
