@@ -237,6 +237,11 @@ def eom_replica(pk, synth):
     return out
 
 
+# DRAM bytes per k_tc_zgemm launch from an ncu capture of the default step (the launch-list window
+# summarised in profiles/launch_list_30x200_step.md); valid while the kernel is unchanged
+K_TC_ZGEMM_DRAM_BYTES_PER_LAUNCH = 7.97e9
+
+
 def run_gemm(args):
     """Tensor-core GEMM alone on one shape (A: M x K, B: N x K, complex), e.g. the packed ladder
     contraction of eight trial vectors (M = 8 Po, K = Pv): a small case for kernel captures."""
@@ -501,7 +506,10 @@ def main():
         phase_seconds={k: statistics.mean(s["phase"][k] for s in stats) for k in stats[0]["phase"]},
         counts={k: statistics.mean(s[k] for s in stats) for k in ("ground_iters", "lambda_sigma", "lr_sigma", "hessian")},
         roofline=dict(bound="tensor", kernel="k_tc_zgemm (tcgen05 split-BF16 complex GEMM)", achieved=achieved,
-                      peak=peak, unit="TFLOP/s", frac=(achieved / peak if achieved else None), traffic=None,
+                      peak=peak, unit="TFLOP/s", frac=(achieved / peak if achieved else None),
+                      traffic=K_TC_ZGEMM_DRAM_BYTES_PER_LAUNCH, traffic_unit="bytes per launch",
+                      traffic_source="ncu dram__bytes_read.sum + dram__bytes_write.sum, mean over the 209 k_tc_zgemm "
+                                     "launches of a 1000-launch window of this step (profiles/launch_list_30x200_step.md)",
                       peak_source=f"bf16_tflops_sustained of {src} MEASURED_PEAKS",
                       launches=prof["launches"], kernel_ms_per_step=prof["ms"] / args.steps,
                       useful_complex_tflops=(prof["flops_useful"] / (prof["ms"] / 1e3) / 1e12 if prof["ms"] else None)),
