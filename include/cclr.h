@@ -180,6 +180,13 @@ cclr_status cclr_hessian(cclr_ctx *ctx, int nvec, const cclr_c128 *u, cclr_c128 
 cclr_status cclr_zgemm_nt(cclr_ctx *ctx, int precision, int M, int N, int K, const cclr_c128 *A,
                           const cclr_c128 *B, cclr_c128 *C);
 
+/* The Davidson solver's Gram block on its own (parity tests): out[i*ny + j] = sum_k conj(X_i[k]) Y_j[k]
+ * for host row-major X (nx x n) and Y (ny x n), computed by the FP32-arithmetic kernel the
+ * tensor-core modes use, from FP64 rows (mirror = 0) or from FP32 copies with even row strides
+ * (mirror = 1, the solver's trial-vector mirrors).  Needs a Hamiltonian (device workspace). */
+cclr_status cclr_gram(cclr_ctx *ctx, int mirror, int64_t n, int nx, int ny, const cclr_c128 *X, const cclr_c128 *Y,
+                      cclr_c128 *out);
+
 /* The Davidson solver's multi-vector kernels on their own (measurement; the paper's Davidson
  * scheme, SI "Davidson scheme", does these passes over the trial vectors every iteration).
  * On nx + max(ny, m) synthetic device vectors of length n (deterministic values, allocated and

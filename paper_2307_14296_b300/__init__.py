@@ -35,7 +35,7 @@ EXPORTS = (
     "cclr_get_amplitudes",
     "cclr_set_amplitudes", "cclr_get_response_vector", "cclr_sigma", "cclr_residual", "cclr_xi",
     "cclr_eta", "cclr_hessian", "cclr_zgemm_nt", "cclr_kernel_profile", "cclr_get_stats",
-    "cclr_zgemm_nt_noalloc", "cclr_kernel_breakdown", "cclr_bench_vector_kernels",
+    "cclr_zgemm_nt_noalloc", "cclr_kernel_breakdown", "cclr_bench_vector_kernels", "cclr_gram",
 )
 
 
@@ -78,6 +78,7 @@ _sig = {
     "cclr_zgemm_nt_noalloc": (_i, [_i, _i, _i, _i, _vp, _vp, _vp, _vp]),
     "cclr_get_stats": (_i, [_vp, ctypes.POINTER(Stats)]),
     "cclr_bench_vector_kernels": (_i, [_vp, _i, ctypes.c_int64, _i, _i, _i, _i, _vp]),
+    "cclr_gram": (_i, [_vp, _i, ctypes.c_int64, _i, _i, _vp, _vp, _vp]),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(_lib, _name)
@@ -262,6 +263,15 @@ class Context:
         C = np.zeros((A.shape[0], B.shape[0]), np.complex128)
         self._check(_lib.cclr_zgemm_nt(self._h, precision, A.shape[0], B.shape[0], A.shape[1], _ptr(A), _ptr(B), _ptr(C)))
         return C
+
+    def cclr_gram(self, X, Y, mirror=False):
+        """X^H Y (nx x ny) by the solver's FP32-arithmetic Gram kernel, from FP64 rows or from FP32
+        mirrors of them."""
+        X, Y = _c128(X), _c128(Y)
+        out = np.zeros((X.shape[0], Y.shape[0]), np.complex128)
+        self._check(_lib.cclr_gram(self._h, int(bool(mirror)), X.shape[1], X.shape[0], Y.shape[0], _ptr(X), _ptr(Y),
+                                   _ptr(out)))
+        return out
 
     def cclr_bench_vector_kernels(self, n, nx, ny, m, reps=5, precision=TC_BF16X3) -> dict:
         """Milliseconds per call of the solver's Gram block (nx x ny), residual-norm pass and

@@ -479,6 +479,43 @@ cclr_status cclr_zgemm_nt(cclr_ctx* h, int precision, int M, int N, int K, const
   });
 }
 
+cclr_status cclr_gram(cclr_ctx* h, int mirror, int64_t n, int nx, int ny, const cclr_c128* X, const cclr_c128* Y,
+                      cclr_c128* out) {
+  return guard(h, [&](Ctx& c) {
+    CCLR_REQUIRE(c.have_ham, CCLR_E_STATE, "cclr_gram needs a Hamiltonian (device workspace)");
+    CCLR_REQUIRE(n >= 1 && nx >= 1 && ny >= 1 && X && Y && out, CCLR_E_ARG, "bad Gram arguments");
+    const bool saved = c.L.fast32;
+    c.L.fast32 = true;
+    try {
+      Scope sc(c.ws);
+      const int64_t np = n + (n & 1);   // mirror row stride (even)
+      cplx *x = c.ws.cplxs((int64_t)nx * n), *y = c.ws.cplxs((int64_t)ny * n), *g = c.ws.cplxs((int64_t)nx * ny);
+      cplx* scr = c.ws.cplxs(gram_scratch_elems());
+      upload(c, x, X, (int64_t)nx * n);
+      upload(c, y, Y, (int64_t)ny * n);
+      Rows rx, ry;
+      if (mirror) {
+        float2* xf = (float2*)c.ws.alloc(sizeof(float2) * (size_t)nx * (size_t)np);
+        float2* yf = (float2*)c.ws.alloc(sizeof(float2) * (size_t)ny * (size_t)np);
+        for (int r = 0; r < nx; ++r) to_f32(c.L, x + (int64_t)r * n, xf + (int64_t)r * np, n);
+        for (int r = 0; r < ny; ++r) to_f32(c.L, y + (int64_t)r * n, yf + (int64_t)r * np, n);
+        rx.add(reinterpret_cast<const cplx*>(xf), nx, np);
+        ry.add(reinterpret_cast<const cplx*>(yf), ny, np);
+      } else {
+        rx.add(x, nx, n);
+        ry.add(y, ny, n);
+      }
+      gram(c.L, n, rx, ry, true, g, scr, gram_scratch_elems(), mirror != 0);
+      CCLR_CK(cudaMemcpyAsync(out, g, sizeof(cplx) * (size_t)nx * ny, cudaMemcpyDeviceToHost, c.stream));
+      c.sync();
+    } catch (...) {
+      c.L.fast32 = saved;
+      throw;
+    }
+    c.L.fast32 = saved;
+  });
+}
+
 cclr_status cclr_bench_vector_kernels(cclr_ctx* h, int precision, int64_t n, int nx, int ny, int m, int reps,
                                       double* ms3) {
   return guard(h, [&](Ctx& c) {

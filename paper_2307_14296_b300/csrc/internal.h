@@ -210,12 +210,14 @@ struct Rows {
     }
     return *this;
   }
-  Rows slice(int j0, int n) const {   // rows [j0, j0 + n)
+  // rows [j0, j0 + n); f32: the rows are FP32 mirrors (strides count float2 elements)
+  Rows slice(int j0, int n, bool f32 = false) const {
     Rows r;
     for (int s = 0; s < ns && n > 0; ++s) {
       if (j0 >= cnt[s]) { j0 -= cnt[s]; continue; }
       const int take = std::min(cnt[s] - j0, n);
-      r.add(p[s] + (int64_t)j0 * ld[s], take, ld[s]);
+      const int64_t bytes = (int64_t)j0 * ld[s] * (f32 ? 8 : 16);
+      r.add(reinterpret_cast<const cplx*>(reinterpret_cast<const char*>(p[s]) + bytes), take, ld[s]);
       n -= take;
       j0 = 0;
     }
@@ -283,7 +285,7 @@ void unpack2(const Launch& L, const cplx* D, int64_t ldd, const Tensor& X);
 // summed in FP32 over runs of 32 elements and in FP64 across runs when Launch::fast32, FP64
 // otherwise.  Row starts must be 16-byte aligned; scratch holds gram_scratch_elems().
 void gram(const Launch& L, int64_t n, const Rows& X, const Rows& Y, bool herm, cplx* out_dev, cplx* scratch,
-          int64_t scratch_elems);
+          int64_t scratch_elems, bool x32 = false);   // x32: all rows FP32 mirrors (even strides)
 inline int64_t gram_scratch_elems() { return 148 * 64 * 8; }
 
 // Small element-wise helpers

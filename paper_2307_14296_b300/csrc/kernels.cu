@@ -803,18 +803,26 @@ __device__ __forceinline__ void two_sum(float& hi, float& lo, float v) {
   hi = s;
 }
 
-template <bool F32, int RL, int NY>
+template <bool F32, int RL, int NY, bool X32>
 __global__ void __launch_bounds__(kGramWarps * 32, 1)
     k_gram_skinny(int64_t n, Rows X, Rows Y, bool herm, cplx* part, int lc, int* __restrict__ err) {
   typedef Arith<F32> A;
+  // staged element: FP64 complex, or FP32 complex for rows that are the solver's FP32 mirrors
+  // (even row strides, so a chunk's byte count rounded up to 16 stays inside its row)
+  typedef typename std::conditional<X32, float2, cplx>::type SE;
   extern __shared__ __align__(128) unsigned char gs_smem[];
   const int nx = X.total(), ny = Y.total(), nr = nx + ny;
-  const int CH = 1 << lc, pitch = CH + 1;   // padded row pitch: lanes reading distinct rows hit distinct banks
+  // padded row pitch (FP64: odd, so lanes reading distinct rows hit distinct banks; FP32: even,
+  // for 16-byte aligned rows)
+  const int CH = 1 << lc, pitch = X32 ? CH + 2 : CH + 1;
   uint64_t* bar = reinterpret_cast<uint64_t*>(gs_smem);
-  cplx* st0 = reinterpret_cast<cplx*>(gs_smem + kGramHead);
-  cplx* st1 = st0 + (size_t)nr * pitch;
-  const cplx** rowp = reinterpret_cast<const cplx**>(st1 + (size_t)nr * pitch);
-  for (int r = threadIdx.x; r < nr; r += blockDim.x) rowp[r] = r < nx ? row_of(X, r) : row_of(Y, r - nx);
+  SE* st0 = reinterpret_cast<SE*>(gs_smem + kGramHead);
+  SE* st1 = st0 + (size_t)nr * pitch;
+  const SE** rowp = reinterpret_cast<const SE**>(st1 + (size_t)nr * pitch);
+  for (int r = threadIdx.x; r < nr; r += blockDim.x) {
+    if constexpr (X32) rowp[r] = r < nx ? row_of32(X, r) : row_of32(Y, r - nx);
+    else rowp[r] = r < nx ? row_of(X, r) : row_of(Y, r - nx);
+  }
   if (threadIdx.x == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar[0])) : "memory");
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar[1])) : "memory");
@@ -828,8 +836,10 @@ __global__ void __launch_bounds__(kGramWarps * 32, 1)
   // warp 0: bulk copies of chunk ch (all rows) into stage s
   auto issue = [&](int s, int64_t ch) {
     const int64_t base = ch << lc;
-    const uint32_t bytes = (uint32_t)(min((int64_t)CH, n - base) * (int64_t)sizeof(cplx));
-    cplx* dst = s ? st1 : st0;
+    int64_t cnt = min((int64_t)CH, n - base);
+    if (X32) cnt += cnt & 1;   // 16-byte multiple; the even row stride keeps it inside the row
+    const uint32_t bytes = (uint32_t)(cnt * (int64_t)sizeof(SE));
+    SE* dst = s ? st1 : st0;
     if (lane == 0)
       asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(&bar[s])),
                    "r"(bytes * (uint32_t)nr)
@@ -868,18 +878,23 @@ __global__ void __launch_bounds__(kGramWarps * 32, 1)
   // coefficient form (X rows), 16 bytes each, so the products need no register moves
   typedef typename A::X PX;
   typedef typename A::C PC;
-  auto mac_elem = [&](const cplx* st, int k) {
+  auto mac_elem = [&](const SE* st, int k) {
     typename A::X yv[NY];
 #pragma unroll
     for (int j = 0; j < NY; ++j) {
-      if constexpr (F32) yv[j] = j < ny ? reinterpret_cast<const PX*>(st)[(nx + j) * pitch + k] : PX{0ull, 0ull};
+      if constexpr (X32) yv[j] = A::opnd(j < ny ? st[(nx + j) * pitch + k] : make_float2(0.f, 0.f));
+      else if constexpr (F32) yv[j] = j < ny ? reinterpret_cast<const PX*>(st)[(nx + j) * pitch + k] : PX{0ull, 0ull};
       else yv[j] = A::opnd(j < ny ? st[(nx + j) * pitch + k] : make_double2(0.0, 0.0));
     }
 #pragma unroll
     for (int a = 0; a < RL; ++a) {
       const int r = lane + 32 * a;
       typename A::C xc;
-      if constexpr (F32) {
+      if constexpr (X32) {
+        float2 xv = r < nx ? st[r * pitch + k] : make_float2(0.f, 0.f);
+        if (herm) xv.y = -xv.y;
+        xc = A::coef(xv);
+      } else if constexpr (F32) {
         xc = r < nx ? reinterpret_cast<const PC*>(st)[r * pitch + k] : PC{0ull, 0ull};
       } else {
         cplx xv = r < nx ? st[r * pitch + k] : make_double2(0.0, 0.0);
@@ -908,10 +923,10 @@ __global__ void __launch_bounds__(kGramWarps * 32, 1)
       return;
     }
     if (s) ++uses1; else ++uses0;
-    cplx* st = s ? st1 : st0;
+    SE* st = s ? st1 : st0;
     const int64_t base = ch << lc;
     const int lim = (int)min((int64_t)CH, n - base);
-    if constexpr (F32) {
+    if constexpr (F32 && !X32) {
       // in place: each FP64 element becomes its 16-byte FP32 packed form; a warp per row when
       // there are enough rows, else all threads over the rows x chunk elements
       const float sg = herm ? -1.f : 1.f;   // coefficient of conj(x) for the Hermitian product
@@ -1062,32 +1077,38 @@ void unpack2(const Launch& L, const cplx* D, int64_t ldd, const Tensor& X) {
 
 namespace {
 constexpr size_t kGramSmemMax = 200 << 10;
-template <bool F32, int RL, int NY>
+template <bool F32, int RL, int NY, bool X32>
 void launch_gram(const Launch& L, int nblk, size_t smem, int64_t n, const Rows& X, const Rows& Y, bool herm,
                  cplx* part, int lc) {
   CCLR_REQUIRE(L.err, CCLR_E_STATE, "gram: no device status word");
   static bool attr = false;
   if (!attr) {
-    CCLR_CK(cudaFuncSetAttribute(k_gram_skinny<F32, RL, NY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    CCLR_CK(cudaFuncSetAttribute(k_gram_skinny<F32, RL, NY, X32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kGramSmemMax));
     attr = true;
   }
-  k_gram_skinny<F32, RL, NY><<<nblk, kGramWarps * 32, smem, L.s>>>(n, X, Y, herm, part, lc, L.err);
+  k_gram_skinny<F32, RL, NY, X32><<<nblk, kGramWarps * 32, smem, L.s>>>(n, X, Y, herm, part, lc, L.err);
 }
-template <bool F32>
+template <bool F32, bool X32>
 void launch_gram_tile(const Launch& L, int nblk, size_t smem, int64_t n, const Rows& X, const Rows& Y, bool herm,
                       cplx* part, int lc) {
   const int b = Y.total();   // X.total() <= kGramMaxX = 32: one row per lane
-  if (b == 1) launch_gram<F32, 1, 1>(L, nblk, smem, n, X, Y, herm, part, lc);
-  else if (b <= 4) launch_gram<F32, 1, 4>(L, nblk, smem, n, X, Y, herm, part, lc);
-  else launch_gram<F32, 1, 8>(L, nblk, smem, n, X, Y, herm, part, lc);
+  if (b == 1) launch_gram<F32, 1, 1, X32>(L, nblk, smem, n, X, Y, herm, part, lc);
+  else if (b <= 4) launch_gram<F32, 1, 4, X32>(L, nblk, smem, n, X, Y, herm, part, lc);
+  else launch_gram<F32, 1, 8, X32>(L, nblk, smem, n, X, Y, herm, part, lc);
 }
 }  // namespace
 
 void gram(const Launch& L, int64_t n, const Rows& X, const Rows& Y, bool herm, cplx* out_dev, cplx* scratch,
-          int64_t scratch_elems) {
+          int64_t scratch_elems, bool x32) {
   const int nx = X.total(), ny = Y.total();
   CCLR_REQUIRE(nx >= 1 && ny >= 1 && n >= 1, CCLR_E_ARG, "gram: empty operand");
+  CCLR_REQUIRE(!x32 || L.fast32, CCLR_E_ARG, "gram: FP32 rows need the FP32 arithmetic");
+  if (x32)   // chunk copies are rounded up to 16 bytes: rows need even strides covering n + 1
+    for (const Rows* R : {&X, &Y})
+      for (int g = 0; g < R->ns; ++g)
+        CCLR_REQUIRE(R->ld[g] % 2 == 0 && R->ld[g] >= n + (n & 1), CCLR_E_ARG, "gram: FP32 row stride");
+  const size_t esz = x32 ? sizeof(float2) : sizeof(cplx);
   // the kernel takes the longer list as its X side; the transpose is undone when the tile is stored
   const bool swap = ny > nx;
   const Rows& P = swap ? Y : X;
@@ -1099,11 +1120,10 @@ void gram(const Launch& L, int64_t n, const Rows& X, const Rows& Y, bool herm, c
       // chunk: at least 64 KiB of rows per stage (the bytes each SM keeps in flight), within the
       // shared-memory budget of two stages plus the FP32 copy
       auto stage_bytes = [&](int lc) {
-        return kGramHead + 2 * sizeof(cplx) * (size_t)(a + b) * ((size_t(1) << lc) + 1) + sizeof(void*) * (size_t)(a + b);
+        return kGramHead + 2 * esz * (size_t)(a + b) * ((size_t(1) << lc) + 2) + sizeof(void*) * (size_t)(a + b);
       };
       int lc = kGramMinLog;
-      while (lc < kGramMaxLog && ((size_t)(a + b) * sizeof(cplx) << lc) < (size_t(64) << 10) &&
-             stage_bytes(lc + 1) <= kGramSmemMax)
+      while (lc < kGramMaxLog && ((size_t)(a + b) * esz << lc) < (size_t(64) << 10) && stage_bytes(lc + 1) <= kGramSmemMax)
         ++lc;
       const int64_t nchunks = (n + (int64_t(1) << lc) - 1) >> lc;
       int nblk = (int)std::min<int64_t>(148, nchunks);
@@ -1113,10 +1133,12 @@ void gram(const Launch& L, int64_t n, const Rows& X, const Rows& Y, bool herm, c
       const size_t smem = std::max(stage_bytes(lc), red);
       CCLR_REQUIRE(smem <= kGramSmemMax, CCLR_E_ARG, "gram: tile too large");
       kbeg(L);
-      if (L.fast32) launch_gram_tile<true>(L, nblk, smem, n, P.slice(i0, a), Q.slice(j0, b), herm, scratch, lc);
-      else launch_gram_tile<false>(L, nblk, smem, n, P.slice(i0, a), Q.slice(j0, b), herm, scratch, lc);
+      if (x32)
+        launch_gram_tile<true, true>(L, nblk, smem, n, P.slice(i0, a, true), Q.slice(j0, b, true), herm, scratch, lc);
+      else if (L.fast32) launch_gram_tile<true, false>(L, nblk, smem, n, P.slice(i0, a), Q.slice(j0, b), herm, scratch, lc);
+      else launch_gram_tile<false, false>(L, nblk, smem, n, P.slice(i0, a), Q.slice(j0, b), herm, scratch, lc);
       CCLR_CK(cudaGetLastError());
-      bump(L, shaped("k_gram_skinny", a, b, lc));
+      bump(L, shaped(x32 ? "k_gram_skinny32" : "k_gram_skinny", a, b, lc));
       cplx* o = swap ? out_dev + (int64_t)j0 * ny + i0 : out_dev + (int64_t)i0 * ny + j0;
       kbeg(L);
       k_gram_reduce<<<(a * b + 255) / 256, 256, 0, L.s>>>(scratch, nblk, a, b, o, ny, swap, herm);

@@ -105,14 +105,14 @@ void to_dev(Ctx& c, const zc* h, cplx* d, int64_t n) {
 
 // out[i*ny + j] = sum op(X_i) Y_j over row lists of any length, in tiles that the Gram kernel
 // takes (FP32 products when the solver's vector kernels run in FP32, FP64 otherwise)
-void gram_host(Ctx& c, const Rows& X, const Rows& Y, bool herm, std::vector<zc>& out) {
+void gram_host(Ctx& c, const Rows& X, const Rows& Y, bool herm, std::vector<zc>& out, bool x32 = false) {
   const int nx = X.total(), ny = Y.total();
   out.assign((size_t)nx * ny, zc(0));
   if (nx == 0 || ny == 0) return;
   Scope sc(c.ws);
   cplx* scr = c.ws.cplxs(gram_scratch_elems());
   cplx* dout = c.ws.cplxs((int64_t)nx * ny);
-  gram(c.L, c.N, X, Y, herm, dout, scr, gram_scratch_elems());
+  gram(c.L, c.N, X, Y, herm, dout, scr, gram_scratch_elems(), x32);
   to_host(c, dout, out.data(), (int64_t)nx * ny);
 }
 
@@ -251,7 +251,7 @@ struct System {            // one right-hand side with its shared trial space
   cplx *B = nullptr, *S = nullptr;
   // FP32 mirrors of B and S (tensor-core modes): the passes whose arithmetic is FP32 anyway
   // (residual norms, candidates, projections) read 8 instead of 16 bytes per element
-  void *Bf = nullptr, *Sf = nullptr;
+  void *Bf = nullptr, *Sf = nullptr, *bf = nullptr;   // rows of Np = N rounded up to even elements
   int L = 0;
   std::vector<zc> BS, BB;  // maxL x maxL: B^H S, B^H B
   std::vector<zc> Cp;      // -B^H b
@@ -349,16 +349,25 @@ void restart(Ctx& c, System& s, int maxL, int kmax) {
 // outside the trial space and the directions kept before it.  Returns the number appended.
 // cdev holds >= L * nt coefficients.
 int add_corrections(Ctx& c, cplx* B, int L, cplx* R, int nt, const double* pre2, int kmax, cplx* cdev,
-                    double* vscr, const void* Bf = nullptr) {
-  const int64_t N = c.N;
+                    double* vscr, const void* Bf = nullptr, void* Rf = nullptr) {
+  const int64_t N = c.N, Np = N + (N & 1);
   if (kmax <= 0 || nt <= 0) return 0;
   if (L > 0) {
     std::vector<zc> g;
-    gram_host(c, rows(c, B, L), rows(c, R, nt), true, g);
+    if (Bf && Rf) {   // B^H R from the FP32 mirrors (R mirrored here)
+      for (int t = 0; t < nt; ++t) to_f32(c.L, R + (int64_t)t * N, (float2*)Rf + (int64_t)t * Np, N);
+      Rows b, r;
+      b.add(reinterpret_cast<const cplx*>(Bf), L, Np);
+      r.add(reinterpret_cast<const cplx*>(Rf), nt, Np);
+      gram_host(c, b, r, true, g, true);
+    } else {
+      gram_host(c, rows(c, B, L), rows(c, R, nt), true, g);
+    }
     for (auto& x : g) x = -x;
     to_dev(c, g.data(), cdev, (int64_t)L * nt);
     VecMat a;
-    a.X = Bf ? rows(c, (const cplx*)Bf, L) : rows(c, B, L);
+    if (Bf) a.X.add(reinterpret_cast<const cplx*>(Bf), L, Np);
+    else a.X = rows(c, B, L);
     a.x32 = Bf != nullptr;
     a.m = nt;
     a.C = cdev;
@@ -437,18 +446,29 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
     }
     to_dev(c, C.data(), cdev, (int64_t)2 * L * m);
   };
+  // FP32 mirrors of the trial space in the tensor-core modes; row stride Np (even, as the Gram
+  // kernel's 16-byte chunk copies need)
+  const int64_t Np = N + (N & 1);
+  auto m32 = [&](const void* p, int r0, int nr) {   // rows [r0, r0 + nr) of a mirror
+    Rows r;
+    r.add(reinterpret_cast<const cplx*>((const float2*)p + (int64_t)r0 * Np), nr, Np);
+    return r;
+  };
   auto SB = [&](const System& s) {
-    return s.Sf ? Rows().add((const cplx*)s.Sf, s.L, N).add((const cplx*)s.Bf, s.L, N)
+    return s.Sf ? m32(s.Sf, 0, s.L).add(reinterpret_cast<const cplx*>(s.Bf), s.L, Np)
                 : Rows().add(s.S, s.L, N).add(s.B, s.L, N);
   };
-  // FP32 mirrors of the trial space in the tensor-core modes (rows [r0, r0 + nr) of B or S)
   const bool mirrors = c.L.fast32;
   for (auto& s : sys) {
-    s.Bf = mirrors ? c.ws.alloc(sizeof(float2) * (size_t)maxL * (size_t)N) : nullptr;
-    s.Sf = mirrors ? c.ws.alloc(sizeof(float2) * (size_t)maxL * (size_t)N) : nullptr;
+    s.Bf = mirrors ? c.ws.alloc(sizeof(float2) * (size_t)maxL * (size_t)Np) : nullptr;
+    s.Sf = mirrors ? c.ws.alloc(sizeof(float2) * (size_t)maxL * (size_t)Np) : nullptr;
+    s.bf = mirrors ? c.ws.alloc(sizeof(float2) * (size_t)Np) : nullptr;
+    if (s.bf) to_f32(c.L, s.rhs, s.bf, N);
   }
-  auto mirror = [&](const cplx* X, void* Xf, int r0, int nr) {
-    if (Xf && nr > 0) to_f32(c.L, X + (int64_t)r0 * N, (float2*)Xf + (int64_t)r0 * N, (int64_t)nr * N);
+  void* Rf = mirrors ? c.ws.alloc(sizeof(float2) * (size_t)kTry * (size_t)Np) : nullptr;
+  auto mirror = [&](const cplx* X, void* Xf, int r0, int nr) {   // rows [r0, r0 + nr) of B or S
+    if (Xf)
+      for (int r = r0; r < r0 + nr; ++r) to_f32(c.L, X + (int64_t)r * N, (float2*)Xf + (int64_t)r * Np, N);
   };
   auto residual_norms = [&](System& s, const std::vector<int>& qs) {
     for (size_t g0 = 0; g0 < qs.size(); g0 += kVecMatOut) {
@@ -529,7 +549,11 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
         const cplx* Bn = s.B + (int64_t)L0 * N;
         const cplx* Sn = s.S + (int64_t)L0 * N;
         const int ny = 2 * f;
-        gram_host(c, rows(c, s.B, s.L), Rows().add(Sn, f, N).add(Bn, f, N), true, g);
+        if (s.Sf)
+          gram_host(c, m32(s.Bf, 0, s.L), m32(s.Sf, L0, f).add(reinterpret_cast<const cplx*>((const float2*)s.Bf + (int64_t)L0 * Np), f, Np),
+                    true, g, true);
+        else
+          gram_host(c, rows(c, s.B, s.L), Rows().add(Sn, f, N).add(Bn, f, N), true, g);
         for (int i = 0; i < s.L; ++i) {
           for (int j = 0; j < f; ++j) {
             s.BS[(size_t)i * maxL + L0 + j] = g[(size_t)i * ny + j];
@@ -541,9 +565,15 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
         // S_old^H B_new and b^H B_new in one pass (the old rows of B^H b are unchanged: b is fixed
         // and a restart transforms them with the basis)
         Rows sb;
-        if (L0 > 0) sb.add(s.S, L0, N);
-        sb.add(s.rhs, 1, N);
-        gram_host(c, sb, rows(c, Bn, f), true, g);
+        if (s.Sf) {
+          if (L0 > 0) sb = m32(s.Sf, 0, L0);
+          sb.add(reinterpret_cast<const cplx*>(s.bf), 1, Np);
+          gram_host(c, sb, m32(s.Bf, L0, f), true, g, true);
+        } else {
+          if (L0 > 0) sb.add(s.S, L0, N);
+          sb.add(s.rhs, 1, N);
+          gram_host(c, sb, rows(c, Bn, f), true, g);
+        }
         for (int i = 0; i < L0; ++i)
           for (int j = 0; j < f; ++j) s.BS[(size_t)(L0 + j) * maxL + i] = std::conj(g[(size_t)i * f + j]);
         for (int j = 0; j < f; ++j) s.Cp[L0 + j] = -std::conj(g[(size_t)L0 * f + j]);
@@ -634,7 +664,7 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
       }
       // ---- project out the trial space and append the new directions
       ph.mark(c, "project");
-      const int kk = add_corrections(c, s.B, s.L, R, nt, pre2, std::min(kMaxNew, maxL - s.L), cdev, vscr, s.Bf);
+      const int kk = add_corrections(c, s.B, s.L, R, nt, pre2, std::min(kMaxNew, maxL - s.L), cdev, vscr, s.Bf, Rf);
       mirror(s.B, s.Bf, s.L, kk);
       if (kk == 0)
         throw Error(CCLR_E_NOCONV, "Davidson stagnated: residual " + std::to_string(order.front().first) +

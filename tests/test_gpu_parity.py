@@ -260,3 +260,21 @@ def test_alpha_directional_derivative_is_exact(pk):
     fd = (alpha(X + h * dX) - alpha(X - h * dX)) / (2 * h)
     assert np.abs(got - fd).max() < 1e-8 * np.abs(fd).max()
     ctx.close()
+
+
+def test_tensor_core_response_matches_fp64(pk):
+    """(8,40), 16 damped frequencies x 3 operators: the split-BF16 path (tensor-core sigma, FP32
+    solver passes over FP32 mirrors of the trial vectors) gives alpha within 2e-5 of the largest
+    component of the FP64 result."""
+    inst = synth.make_instance(8, 40)
+    omegas, gamma = list(np.linspace(0.05, 0.3, 16)), 0.005
+    alpha = {}
+    for prec in (pk.FP64, pk.TC_BF16X3):
+        ctx = make_ctx(pk, inst, precision=prec, tol=1e-7, ground_tol=1e-9, max_subspace=64, batch=8)
+        ctx.cc_ground()
+        ctx.cc_lambda()
+        ctx.cc_lr_solve(inst.ops, omegas, gamma)
+        alpha[prec] = -ctx.cc_response_function()
+        ctx.close()
+    ref = alpha[pk.FP64]
+    assert np.abs(alpha[pk.TC_BF16X3] - ref).max() < 2e-5 * np.abs(ref).max()

@@ -61,3 +61,17 @@ def test_tc_sigma_matches_fp64(prec):
         assert err < BOUND[prec], (side, err)
         assert err > 1e-12
     c.close()
+
+
+@pytest.mark.parametrize("n,nx,ny", [(1, 1, 1), (1001, 3, 5), (70001, 40, 9), (130003, 33, 17), (4097, 8, 8)])
+@pytest.mark.parametrize("mirror", [False, True])
+def test_solver_gram_block(ctx, n, nx, ny, mirror):
+    """The Davidson Gram kernel (FP32 arithmetic, compensated sums) against NumPy's X^H Y: ragged
+    lengths (odd n exercises the 16-byte rounding of the mirrored chunk copies), tiles split over
+    more than 32 X rows and 8 Y rows.  Bound: FP32 inputs (2^-24 relative) summed with
+    compensation, 1e-6 of the largest entry."""
+    X = synth.random_vector((nx, n), 5, 1)
+    Y = synth.random_vector((ny, n), 5, 2)
+    got = ctx.cclr_gram(X, Y, mirror=mirror)
+    ref = np.conj(X) @ Y.T
+    assert np.abs(got - ref).max() < 1e-6 * np.abs(ref).max()
