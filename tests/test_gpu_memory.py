@@ -2,7 +2,7 @@
 
 Each cycle (ground state, Lambda, linear response, response function) must release what the
 previous cycle allocated: the second and third cycles end with the same free device memory
-(within 4 MiB, two of the driver's 2 MiB pages; one leaked set of response arrays at this size
+(within 4 MiB, two of the CUDA driver's 2 MiB pages; one leaked set of response arrays at this size
 is ~20 MB).
 """
 import numpy as np
