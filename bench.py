@@ -46,6 +46,10 @@ def sigma_cmac(o: int, v: int) -> float:
     return Po * Pv * Pv + o**3 * v**3 + 5.5 * o**2 * v**3 + 6 * o**3 * v**2 + o**4 * v**2 / 4
 
 
+def prec_of(pk, name: str) -> int:
+    return {"bf16x3": pk.TC_BF16X3, "bf16x6": pk.TC_BF16X6, "f64tc": pk.TC_F64, "fp64": pk.FP64}[name]
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -185,31 +189,48 @@ def config_dict(args):
 
 # ------------------------------------------------------------------------------------------ GPU
 def accuracy_vs_fp64(pk, synth):
-    """Mixed-precision alpha against the FP64 path on the 12/90 replica: max over frequencies and
-    the nine components of |d alpha| / |alpha| (each component against its own size and against
-    the largest one) and the isotropic mean alpha per frequency."""
+    """The mixed-precision path against the GPU's plain FP64 path on the 12/90 replica (16
+    frequencies, 3 operators, the full path from the Hamiltonian to alpha), both timed: alpha
+    error per component (against its own size and against the largest component), of the mean
+    alpha, and the end-to-end seconds of each run.  Runs: FP64 (DFMA) to 1e-11 / 1e-11 (residual
+    of the response / ground-state equations), split BF16 with FP64 refinement to 1e-10 / 1e-10,
+    and split BF16 without refinement (stopped at its floor) for contrast."""
     w = WORKLOADS["12x90"]
     o, v = w["n_occ"], w["n_vir"]
     inst = synth.make_instance(o, v)
     om = np.linspace(w["w_min"], w["w_max"], 16)
-    res = {}
-    for prec in (pk.FP64, pk.TC_BF16X3):
-        ctx = pk.Context(0, precision=prec, tol=1e-9 if prec == pk.FP64 else w["tol"], ground_tol=1e-10 if prec == pk.FP64 else 1e-8,
-                         max_subspace=64, batch=8, maxit=80)
+    runs = {"fp64": dict(precision=pk.FP64, tol=1e-11, ground_tol=1e-11),
+            "bf16x3_refined": dict(precision=pk.TC_BF16X3, tol=1e-10, ground_tol=1e-10),
+            "bf16x3_unrefined": dict(precision=pk.TC_BF16X3, tol=1e-10, ground_tol=1e-10, refine=0)}
+    res, secs, refine = {}, {}, {}
+    for name, opt in runs.items():
+        ctx = pk.Context(0, max_subspace=64, batch=8, maxit=100, **opt)
+        t0 = time.perf_counter()
         ctx.cclr_set_hamiltonian(o, v, inst.fock, [inst.blocks[k] for k in synth.CLASSES])
         ctx.cc_ground()
+        rv = ctx.cclr_get_stats()["refine_vectors"]
         ctx.cc_lambda()
+        rv += ctx.cclr_get_stats()["refine_vectors"]
         ctx.cc_lr_solve(inst.ops, om, w["gamma"])
-        res[prec] = -ctx.cc_response_function()
+        st = ctx.cclr_get_stats()
+        rv += st["refine_vectors"]
+        res[name] = -ctx.cc_response_function()
+        secs[name] = time.perf_counter() - t0
+        refine[name] = dict(refine_sigma_products=rv, final_response_residual=st["max_residual"])
         ctx.close()
-    a, b = res[pk.TC_BF16X3], res[pk.FP64]
-    d = np.abs(a - b)
-    mean_a = np.trace(a, axis1=1, axis2=2) / 3
-    mean_b = np.trace(b, axis1=1, axis2=2) / 3
-    return dict(workload="12/90 replica, 16 frequencies on [0.05,0.30], gamma 0.005, 3 operators",
-                max_rel_per_component=float((d / np.abs(b)).max()),
-                max_rel_to_largest=float(d.max() / np.abs(b).max()),
-                max_rel_mean_alpha=float((np.abs(mean_a - mean_b) / np.abs(mean_b)).max()))
+    b = res["fp64"]
+    out = dict(workload="12/90 replica, 16 frequencies on [0.05,0.30], gamma 0.005, 3 operators, "
+                        "Hamiltonian to alpha", smallest_component=float(np.abs(b).min()),
+               largest_component=float(np.abs(b).max()), fp64_seconds=secs["fp64"])
+    for name in ("bf16x3_refined", "bf16x3_unrefined"):
+        a = res[name]
+        d = np.abs(a - b)
+        mean_a, mean_b = np.trace(a, axis1=1, axis2=2) / 3, np.trace(b, axis1=1, axis2=2) / 3
+        out[name] = dict(max_rel_per_component=float((d / np.abs(b)).max()),
+                         max_rel_to_largest=float(d.max() / np.abs(b).max()),
+                         max_rel_mean_alpha=float((np.abs(mean_a - mean_b) / np.abs(mean_b)).max()),
+                         seconds=secs[name], speedup_vs_fp64=secs["fp64"] / secs[name], **refine[name])
+    return out
 
 
 def eom_replica(pk, synth):
@@ -237,11 +258,6 @@ def eom_replica(pk, synth):
     return out
 
 
-# DRAM bytes per k_tc_zgemm launch from an ncu capture of the default step (the launch-list window
-# summarised in profiles/launch_list_30x200_step.md); valid while the kernel is unchanged
-K_TC_ZGEMM_DRAM_BYTES_PER_LAUNCH = 7.97e9
-
-
 def run_gemm(args):
     """Tensor-core GEMM alone on one shape (A: M x K, B: N x K, complex), e.g. the packed ladder
     contraction of eight trial vectors (M = 8 Po, K = Pv): a small case for kernel captures."""
@@ -251,7 +267,7 @@ def run_gemm(args):
     rng = np.random.default_rng(2307)
     A = rng.standard_normal((M, K)) + 1j * rng.standard_normal((M, K))
     B = rng.standard_normal((N, K)) + 1j * rng.standard_normal((N, K))
-    prec = pk.TC_BF16X3 if args.precision == "bf16x3" else pk.FP64
+    prec = prec_of(pk, args.precision)
     ctx = pk.Context(0, precision=prec)
     tiny = synth.make_instance(2, 4)   # a Hamiltonian gives the context its device workspace
     ctx.cclr_set_hamiltonian(2, 4, tiny.fock, [tiny.blocks[k] for k in synth.CLASSES])
@@ -262,6 +278,8 @@ def run_gemm(args):
     for _ in range(max(1, args.steps)):
         C = ctx.cclr_zgemm_nt(A, B, prec)
     prof = ctx.cclr_kernel_profile(False)
+    if prec == pk.TC_F64:
+        prof = prof["f64"]
     part = A[:4] @ B[:4].T
     rel = float(np.abs(C[:4, :4] - part).max() / np.abs(part).max())
     per = prof["ms"] / max(1, args.steps)
@@ -282,7 +300,7 @@ def run_sigma(args):
     parts = [int(x) for x in args.sigma.split(",")]
     o, v, side = parts[0], parts[1], (parts[2] if len(parts) > 2 else 0)
     inst = synth.make_instance(o, v)
-    prec = pk.TC_BF16X3 if args.precision == "bf16x3" else pk.FP64
+    prec = prec_of(pk, args.precision)
     ctx = pk.Context(0, precision=prec, tol=1e-6, ground_tol=1e-8, max_subspace=32, batch=8, maxit=60)
     ctx.cclr_set_hamiltonian(o, v, inst.fock, [inst.blocks[k] for k in synth.CLASSES])
     ctx.cclr_kernel_profile(True)
@@ -314,7 +332,7 @@ def run_vector_kernels(args):
     import paper_2307_14296_b300 as pk
     import synth
     n, nx, ny, m = (int(x) for x in args.vector_kernels.split(","))
-    prec = pk.TC_BF16X3 if args.precision == "bf16x3" else pk.FP64
+    prec = prec_of(pk, args.precision)
     ctx = pk.Context(0, precision=prec)
     tiny = synth.make_instance(2, 4)   # a Hamiltonian gives the context its device workspace
     ctx.cclr_set_hamiltonian(2, 4, tiny.fock, [tiny.blocks[k] for k in synth.CLASSES])
@@ -330,7 +348,7 @@ def main():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cclr", choices=["cclr", "reference"])
-    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp64"])
+    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "bf16x6", "f64tc", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-breakdown", action="store_true", help="skip the per-kernel timing step")
@@ -368,7 +386,7 @@ def main():
     o, v = w["n_occ"], w["n_vir"]
     inst = synth.make_instance(o, v, seed=synth.DEFAULT_SEED + rank)
     omegas = np.linspace(w["w_min"], w["w_max"], w["n_freq"])
-    prec = pk.TC_BF16X3 if args.precision == "bf16x3" else pk.FP64
+    prec = prec_of(pk, args.precision)
     ctx = pk.Context(local, precision=prec, tol=w["tol"], ground_tol=1e-8, max_subspace=64, batch=8, maxit=80)
     blocks = [inst.blocks[k] for k in synth.CLASSES]
     # pinned host copies of the inputs (for the end-to-end measurement)
@@ -383,18 +401,24 @@ def main():
         s = ctx.cclr_get_stats()
         st["ground_iters"] = it
         st["launches"] = s["kernel_launches"]
-        st["phase"] = {"ground": s["total_seconds"]}
+        st["phase"] = {"ground": s["total_seconds"], "ground_refine": s["refine_seconds"]}
+        st["refine_products"] = s["refine_vectors"]
         ctx.cc_lambda()
         s = ctx.cclr_get_stats()
         st["launches"] += s["kernel_launches"]
         st["lambda_sigma"] = s["sigma_vectors"]
+        st["refine_products"] += s["refine_vectors"]
         st["phase"]["lambda"] = s["total_seconds"]
+        st["phase"]["lambda_refine"] = s["refine_seconds"]
         ctx.cc_lr_solve(host[7], omegas, w["gamma"])
         s = ctx.cclr_get_stats()
         st["lr_sigma"] = s["sigma_vectors"]
+        st["refine_products"] += s["refine_vectors"]
         st["launches"] += s["kernel_launches"]
         st["phase"]["lr_solve"] = s["total_seconds"]
         st["phase"]["lr_sigma"] = s["sigma_seconds"]
+        st["phase"]["lr_refine"] = s["refine_seconds"]
+        st["final_residual"] = s["max_residual"]
         resp = ctx.cc_response_function()
         s = ctx.cclr_get_stats()
         st["launches"] += s["kernel_launches"]
@@ -436,7 +460,9 @@ def main():
         e2e = dict(value=allreduce(8 * sigma_cmac(o, v) * n_e2e / t_e2e / 1e12, world, "sum"), unit="TFLOP/s",
                    h2d_bytes_per_step=int(h2d), d2h_bytes_per_step=int(st["resp"].nbytes), seconds=t_e2e)
 
-    # plain-FP64 comparison: one FP64 right sigma vector, timed alone (outside the timed region)
+    # plain-FP64 comparison at full size: one FP64 right sigma vector timed alone (outside the
+    # timed region); the measured FP64-vs-mixed comparison of whole solves is the 12/90 replica
+    # in accuracy_vs_fp64
     fp64 = None
     if rank == 0:
         x = synth.random_vector((1, ctx.N), 5, 5, 1e-3)
@@ -445,7 +471,7 @@ def main():
         ctx.cclr_sigma(x, side=0, precision=pk.FP64)
         fp64_sigma = time.perf_counter() - t0
         fp64 = dict(sigma_seconds=fp64_sigma, step_seconds_extrapolated=fp64_sigma * n_prod,
-                    note="FP64 step extrapolated: sigma-type products of the mixed step x one FP64 sigma")
+                    note="extrapolated, not measured: sigma-type products of this step x one FP64 sigma")
     # per-kernel shares: one extra untimed step with CUDA events around every launch
     breakdown = None
     if rank == 0 and not args.no_breakdown:
@@ -492,27 +518,40 @@ def main():
         return
     pk_, src = peaks()
     peak = pk_.get("bf16_tflops_sustained", pk_["bf16_tflops"])
-    achieved = prof["flops_exec"] / (prof["ms"] / 1e3) / 1e12 if prof["ms"] > 0 else None
     alpha = -stats[-1]["resp"]
+    # Roofline of the tensor-core kernels on their algorithmic work: every sigma-type product
+    # counts sigma_cmac complex MACs; the split-BF16 kernel executes 3 slice products x 8 BF16
+    # flops per complex MAC, the FP64-class kernel 15 digit products x 8.  The products of the
+    # refinement (and, when refining, the Hessian products) run on the FP64-class kernel.
+    n_ref = statistics.mean(s["refine_products"] + (s["hessian"] if s["refine_products"] else 0) for s in stats)
+    per_kernel = {}
+    for name, key, mult, n_algo in (("k_tc_zgemm", None, 24.0, n_prod - n_ref), ("k_tc_zgemm_x", "f64", 120.0, n_ref)):
+        pr = prof if key is None else prof[key]
+        ms = pr["ms"] / args.steps
+        algo = mult * sigma_cmac(o, v) * n_algo
+        per_kernel[name] = dict(kernel_ms_per_step=ms, launches_per_step=pr["launches"] / args.steps,
+                                algorithmic_tflops=(algo / (ms * 1e-3) / 1e12 if ms > 0 else None),
+                                executed_tflops=(pr["flops_exec"] / args.steps / (ms * 1e-3) / 1e12 if ms > 0 else None))
+    dom = max(per_kernel, key=lambda k: per_kernel[k]["kernel_ms_per_step"])
+    achieved = per_kernel[dom]["algorithmic_tflops"]
     line = dict(
         metric=METRIC, value=value, unit="TFLOP/s", n_gpus=world, steps=args.steps, warmup=args.warmup,
         ms_per_step=1e3 * t_step, higher_is_better=True, scaling="weak", vs_baseline=None,
         dtype="bf16x3+f64" if prec != pk.FP64 else "f64", data="synthetic", config=config_dict(args),
         s_per_alpha=statistics.mean(s["phase"]["lr_solve"] + s["phase"]["response_function"] for s in stats) / w["n_freq"],
-        s_per_alpha_note="linear-response solves + response function per frequency; ground state and Lambda "
-                         "(once per Hamiltonian) in phase_seconds",
+        s_per_alpha_note="linear-response solves (with their FP64 refinement) + response function per frequency; "
+                         "ground state and Lambda (once per Hamiltonian) in phase_seconds",
         s_per_step_per_freq=t_step / w["n_freq"],
         sigma_products_per_step=n_prod,
+        final_response_residual=max(s["final_residual"] for s in stats),
         phase_seconds={k: statistics.mean(s["phase"][k] for s in stats) for k in stats[0]["phase"]},
-        counts={k: statistics.mean(s[k] for s in stats) for k in ("ground_iters", "lambda_sigma", "lr_sigma", "hessian")},
-        roofline=dict(bound="tensor", kernel="k_tc_zgemm (tcgen05 split-BF16 complex GEMM)", achieved=achieved,
-                      peak=peak, unit="TFLOP/s", frac=(achieved / peak if achieved else None),
-                      traffic=K_TC_ZGEMM_DRAM_BYTES_PER_LAUNCH, traffic_unit="bytes per launch",
-                      traffic_source="ncu dram__bytes_read.sum + dram__bytes_write.sum, mean over the 209 k_tc_zgemm "
-                                     "launches of a 1000-launch window of this step (profiles/launch_list_30x200_step.md)",
+        counts={k: statistics.mean(s[k] for s in stats)
+                for k in ("ground_iters", "lambda_sigma", "lr_sigma", "hessian", "refine_products")},
+        roofline=dict(bound="tensor", kernel=dom, achieved=achieved, peak=peak, unit="TFLOP/s",
+                      frac=(achieved / peak if achieved else None), traffic=None,
+                      traffic_note="DRAM bytes of this kernel are measured with ncu on a small case, outside this run",
                       peak_source=f"bf16_tflops_sustained of {src} MEASURED_PEAKS",
-                      launches=prof["launches"], kernel_ms_per_step=prof["ms"] / args.steps,
-                      useful_complex_tflops=(prof["flops_useful"] / (prof["ms"] / 1e3) / 1e12 if prof["ms"] else None)),
+                      kernels=per_kernel),
         cpu_baseline=cpu, e2e=e2e, fp64=fp64, kernel_breakdown=breakdown, accuracy_vs_fp64=accuracy,
         next_rows=extra,
         gpu_launches=int(sum(s["launches"] for s in stats)),

@@ -54,18 +54,39 @@ typedef enum {
  *  CCLR_TC_BF16X3 the ladder and ring contractions (and every other large K-major GEMM) run on
  *                 the tensor cores from split-BF16 operands x = x0 + x1 (products x0y0 + x0y1 +
  *                 x1y0, FP32 accumulation; ~1e-5 relative per contraction).
- *  CCLR_TC_BF16X6 as above with three slices and six products (FP32-class, ~1e-6).
- *  Small solves, inner products, the preconditioner and the response-function contraction stay
- *  in FP64 in every mode. */
-typedef enum { CCLR_FP64 = 0, CCLR_TC_BF16X3 = 2, CCLR_TC_BF16X6 = 3 } cclr_precision;
+ *  CCLR_TC_BF16X6 as above with three slices and six products: the FP32-class tensor-core mode
+ *                 (FP32 complex accuracy, ~1e-6 relative per contraction, limited by the FP32
+ *                 accumulation over long K).
+ *  CCLR_TC_F64    FP64-class tensor-core mode: every operand row is cut into five fixed-point
+ *                 BF16 digits on a per-row exponent grid (Ozaki splitting), the 15 digit products
+ *                 above 2^-40 are summed on the tensor cores, the two leading digit groups exactly
+ *                 in 256-deep chunks, and the chunk sums in float-float; ~1e-11 relative to the
+ *                 product of the row maxima.  Operand magnitudes must lie within the binary32
+ *                 range.  The solvers treat this mode like CCLR_FP64 (FP64 vector arithmetic, no
+ *                 convergence floors).
+ *  In the BF16X3/BF16X6 modes the solvers' vector passes run in FP32 arithmetic and the iterations
+ *  stop at floors relative to the right-hand side (see cclr_options.refine); small solves and the
+ *  response-function contraction stay in FP64 in every mode. */
+typedef enum { CCLR_FP64 = 0, CCLR_TC_BF16X3 = 2, CCLR_TC_BF16X6 = 3, CCLR_TC_F64 = 4 } cclr_precision;
 
 typedef struct {
   double tol;          /* residual 2-norm target of the response solves (default 1e-8)        */
   double ground_tol;   /* residual 2-norm target of the CCSD and Lambda equations (1e-10)      */
   int maxit;           /* iteration limit of every iterative solve (default 100)               */
-  int max_subspace;    /* Davidson trial-space limit per right-hand side (default 48)          */
+  int max_subspace;    /* Davidson trial-space limit per right-hand side (default 96)          */
   int precision;       /* a cclr_precision value (default CCLR_FP64)                           */
   int batch;           /* right-hand sides per batched sigma launch, 0 = automatic             */
+  /* FP64 iterative refinement in the CCLR_TC_BF16X3 / CCLR_TC_BF16X6 modes (default 1).  With
+   * refine = 1, the Hbar intermediates, xi, eta and the Hessian products are formed in the
+   * FP64-class mode (CCLR_TC_F64), and every iterative solve (CCSD, Lambda, response) first runs
+   * in the mixed mode until its residual reaches refine_tol times the norm of its right-hand side
+   * (CCSD: of its first residual), then continues from the compressed solutions with FP64-class
+   * sigma products and FP64 residuals, norms and orthogonalisation until tol / ground_tol is met.
+   * CCLR_E_NOCONV is returned if it is not met within maxit.  With refine = 0 the mixed solve
+   * stops at that floor (or when it stagnates within 5x of it) and returns CCLR_OK; the residual
+   * reached is in cclr_stats.max_residual. */
+  int refine;
+  double refine_tol;   /* mixed-phase floor relative to the right-hand side, 0 = 2e-5         */
 } cclr_options;
 
 /* Fill *opt with the defaults listed above. */
@@ -211,19 +232,21 @@ cclr_status cclr_bench_vector_kernels(cclr_ctx *ctx, int precision, int64_t n, i
  * file-scope device array that each device holds from library load until process exit.
  * Sizes whose temporaries exceed it return CCLR_E_ARG with no GPU work (a square problem fits up
  * to M = N = K of about 1000 with three products).  stream may be NULL (legacy default stream); the call
- * returns after the result is complete.  The first call on a device resolves the array's device
- * address with that device current; make that first call before any stream capture.  Every
+ * is synchronous: it reads the status word back and synchronizes the stream before it returns.
+ * The first call on a device resolves the array's device address with that device current; make
+ * that first call before any stream capture.  Every
  * call shares the array and each call clears the status word it uses, so calls that overlap on
  * the GPU (other streams, other host threads) race and must be serialized by the caller.
  * Returns CCLR_E_TIMEOUT if a bounded device wait expired, CCLR_E_CUDA on a runtime error. */
 cclr_status cclr_zgemm_nt_noalloc(int precision, int M, int N, int K, const cclr_c128 *A, const cclr_c128 *B,
                                   cclr_c128 *C, void *stream);
 
-/* Timing of the tensor-core GEMM kernel with CUDA events recorded on the context's stream around
- * every launch.  enable != 0 switches recording on.  out4 (may be NULL) receives, accumulated
- * since the previous call: {launches, milliseconds, executed BF16 flops (8 M N K per slice
+/* Timing of the tensor-core GEMM kernels with CUDA events recorded on the context's stream around
+ * every launch.  enable != 0 switches recording on.  out8 (may be NULL) receives, accumulated
+ * since the previous call, for the split-BF16 kernel (out8[0..3]) and the FP64-class kernel
+ * (out8[4..7]): {launches, milliseconds, executed BF16 flops (8 M N K per slice or digit
  * product), useful complex flops (8 M N K)}; the counters are then reset. */
-cclr_status cclr_kernel_profile(cclr_ctx *ctx, int enable, double *out4);
+cclr_status cclr_kernel_profile(cclr_ctx *ctx, int enable, double *out8);
 
 /* Per-kernel timing switched on by cclr_kernel_profile: a pair of CUDA events on the context's
  * stream around every launch of the library, summed per kernel name.  Writes one text line per
@@ -232,12 +255,24 @@ cclr_status cclr_kernel_profile(cclr_ctx *ctx, int enable, double *out4);
  * measurement aid, not an operation of the paper.  CCLR_E_ARG if buf is NULL or cap < 1. */
 cclr_status cclr_kernel_breakdown(cclr_ctx *ctx, char *buf, int cap);
 
-/* Per-call statistics of the last cc_* call: sigma launches and vectors, seconds spent. */
+/* Test of the failure path of the tensor-core GEMM's bounded waits (not an operation of the
+ * paper): the next launch of the split-BF16 GEMM kernel on this context waits first for a
+ * barrier phase that nothing completes, with a limit of `polls` polls (about 256 ns each) on
+ * every wait, so the wait runs out before any copy or MMA is issued; the kernel records the
+ * expiry, every role exits, TMEM is freed, and the call that launched it returns CCLR_E_TIMEOUT.
+ * The context stays usable.  CCLR_E_ARG for polls = 0. */
+cclr_status cclr_debug_expire_next_wait(cclr_ctx *ctx, unsigned polls);
+
+/* Per-call statistics of the last cc_* call: sigma launches and vectors, seconds spent;
+ * refine_vectors / refine_seconds: the FP64-class sigma products (CCSD residuals) and the
+ * seconds of the refinement phase; max_residual: the largest final residual norm. */
 typedef struct {
   long sigma_calls, sigma_vectors;
   double sigma_seconds, total_seconds;
   long kernel_launches;
   double max_residual;
+  long refine_vectors;
+  double refine_seconds;
 } cclr_stats;
 cclr_status cclr_get_stats(cclr_ctx *ctx, cclr_stats *out);
 

@@ -26,7 +26,8 @@ if not os.path.exists(LIB_PATH):
 _lib = ctypes.CDLL(LIB_PATH)
 
 CCLR_OK, CCLR_E_ARG, CCLR_E_NOCONV, CCLR_E_OOM, CCLR_E_CUDA, CCLR_E_STATE, CCLR_E_TIMEOUT = range(7)
-FP64, TC_BF16X3, TC_BF16X6 = 0, 2, 3
+FP64, TC_BF16X3, TC_BF16X6, TC_F64 = 0, 2, 3, 4
+TC_FP32 = TC_BF16X6   # the FP32-class tensor-core mode
 AMP_T, AMP_LAMBDA = 0, 1
 EXPORTS = (
     "cclr_default_options", "cclr_create", "cclr_destroy", "cclr_last_error", "cclr_set_hamiltonian",
@@ -36,18 +37,21 @@ EXPORTS = (
     "cclr_set_amplitudes", "cclr_get_response_vector", "cclr_sigma", "cclr_residual", "cclr_xi",
     "cclr_eta", "cclr_hessian", "cclr_zgemm_nt", "cclr_kernel_profile", "cclr_get_stats",
     "cclr_zgemm_nt_noalloc", "cclr_kernel_breakdown", "cclr_bench_vector_kernels", "cclr_gram",
+    "cclr_debug_expire_next_wait",
 )
 
 
 class Options(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("ground_tol", ctypes.c_double), ("maxit", ctypes.c_int),
-                ("max_subspace", ctypes.c_int), ("precision", ctypes.c_int), ("batch", ctypes.c_int)]
+                ("max_subspace", ctypes.c_int), ("precision", ctypes.c_int), ("batch", ctypes.c_int),
+                ("refine", ctypes.c_int), ("refine_tol", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [("sigma_calls", ctypes.c_long), ("sigma_vectors", ctypes.c_long),
                 ("sigma_seconds", ctypes.c_double), ("total_seconds", ctypes.c_double),
-                ("kernel_launches", ctypes.c_long), ("max_residual", ctypes.c_double)]
+                ("kernel_launches", ctypes.c_long), ("max_residual", ctypes.c_double),
+                ("refine_vectors", ctypes.c_long), ("refine_seconds", ctypes.c_double)]
 
 
 _vp, _i, _d, _sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
@@ -79,6 +83,7 @@ _sig = {
     "cclr_get_stats": (_i, [_vp, ctypes.POINTER(Stats)]),
     "cclr_bench_vector_kernels": (_i, [_vp, _i, ctypes.c_int64, _i, _i, _i, _i, _vp]),
     "cclr_gram": (_i, [_vp, _i, ctypes.c_int64, _i, _i, _vp, _vp, _vp]),
+    "cclr_debug_expire_next_wait": (_i, [_vp, ctypes.c_uint]),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(_lib, _name)
@@ -281,10 +286,14 @@ class Context:
         return dict(gram_ms=float(out[0]), norms_ms=float(out[1]), write_ms=float(out[2]))
 
     def cclr_kernel_profile(self, enable=True) -> dict:
-        """Tensor-core kernel timing (CUDA events on the library's stream) since the last call."""
-        out = np.zeros(4, np.float64)
+        """Tensor-core kernel timing (CUDA events on the library's stream) since the last call: the
+        split-BF16 kernel's launches, ms, executed and useful flops, and under "f64" the same for
+        the FP64-class kernel."""
+        out = np.zeros(8, np.float64)
         self._check(_lib.cclr_kernel_profile(self._h, int(enable), _ptr(out)))
-        return dict(launches=int(out[0]), ms=float(out[1]), flops_exec=float(out[2]), flops_useful=float(out[3]))
+        d = lambda k: dict(launches=int(out[4 * k]), ms=float(out[4 * k + 1]), flops_exec=float(out[4 * k + 2]),
+                           flops_useful=float(out[4 * k + 3]))
+        return dict(d(0), f64=d(1))
 
     def cclr_kernel_breakdown(self) -> dict:
         """Per-kernel {name: (launches, milliseconds)} since the last call (timing switched on by
@@ -296,6 +305,11 @@ class Context:
             name, n, ms = line.rsplit(" ", 2)
             out[name] = (int(n), float(ms))
         return out
+
+    def cclr_debug_expire_next_wait(self, polls: int):
+        """Make the next split-BF16 GEMM launch of this context wait first for a barrier phase that
+        nothing completes, with `polls` polls per wait (test of the CCLR_E_TIMEOUT path)."""
+        self._check(_lib.cclr_debug_expire_next_wait(self._h, int(polls)))
 
     def cclr_get_stats(self) -> dict:
         s = Stats()
@@ -336,11 +350,37 @@ def cc_eom_ee(ctx, n_roots):
     return ctx.cc_eom_ee(n_roots)
 
 
+def _check_noalloc_operands(A, B, C):
+    """Argument checks of cclr_zgemm_nt_noalloc, all before any GPU work: complex128 CUDA tensors,
+    contiguous, 2-D, A: M x K, B: N x K, C: M x N, on the current device.  Raises ValueError."""
+    import torch
+    for name, t in (("A", A), ("B", B), ("C", C)):
+        if not _is_torch_cuda(t):
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if t.dtype != torch.complex128:
+            raise ValueError(f"{name} must be complex128, not {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        if t.dim() != 2:
+            raise ValueError(f"{name} must be a matrix")
+    M, K = A.shape
+    if tuple(B.shape)[1] != K:
+        raise ValueError(f"B has {tuple(B.shape)[1]} columns, A has {K}")
+    if tuple(C.shape) != (M, B.shape[0]):
+        raise ValueError(f"C must be {M} x {B.shape[0]}, not {tuple(C.shape)[0]} x {tuple(C.shape)[1]}")
+    dev = torch.cuda.current_device()
+    for name, t in (("A", A), ("B", B), ("C", C)):
+        if t.device.index != dev:
+            raise ValueError(f"{name} is on cuda:{t.device.index}, the current device is cuda:{dev}")
+
+
 def cclr_zgemm_nt_noalloc(A, B, C, precision=TC_BF16X3, stream=None) -> int:
     """C = A B^T on the tensor cores without any device allocation (torch CUDA complex128 tensors,
     contiguous, on the current device; C is written).  For callers that cannot allocate device
     memory; the library keeps its temporaries in one fixed 64 MiB device array shared by all
-    calls, so overlapping calls race.  Returns the C-ABI status code (0 = success)."""
+    calls, so overlapping calls race.  The call synchronizes the stream before it returns.
+    Returns the C-ABI status code (0 = success); bad tensors raise ValueError before any GPU work."""
+    _check_noalloc_operands(A, B, C)
     M, K = A.shape
     N = B.shape[0]
     s = _vp(stream.cuda_stream) if stream is not None else _vp()

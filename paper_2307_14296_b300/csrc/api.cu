@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <chrono>
 #include <cstdlib>
+#include <cmath>
 
 using namespace cclr;
 
@@ -12,6 +13,10 @@ struct cclr_ctx {
 };
 
 namespace {
+
+bool valid_precision(int p) {
+  return p == CCLR_FP64 || p == CCLR_TC_BF16X3 || p == CCLR_TC_BF16X6 || p == CCLR_TC_F64;
+}
 
 double wall() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
@@ -128,6 +133,8 @@ void cclr_default_options(cclr_options* opt) {
   opt->max_subspace = 96;
   opt->precision = CCLR_FP64;
   opt->batch = 0;
+  opt->refine = 1;
+  opt->refine_tol = 0.0;
 }
 
 cclr_status cclr_create(cclr_ctx** out, int device, const cclr_options* opt) {
@@ -139,7 +146,7 @@ cclr_status cclr_create(cclr_ctx** out, int device, const cclr_options* opt) {
   Ctx& c = h->c;
   c.device = device;
   if (opt) c.opt = *opt; else cclr_default_options(&c.opt);
-  if (c.opt.precision != CCLR_FP64 && c.opt.precision != CCLR_TC_BF16X3 && c.opt.precision != CCLR_TC_BF16X6) {
+  if (!valid_precision(c.opt.precision)) {
     delete h;
     return CCLR_E_ARG;
   }
@@ -194,6 +201,10 @@ cclr_status cclr_set_hamiltonian(cclr_ctx* h, int n_occ, int n_vir, const cclr_c
     CCLR_CK(cudaMalloc((void**)&c.ws.base, ws));
     c.ws.cap = ws;
     c.ws.top = 0;
+    // every uploaded value is checked for infinities and NaN (one flag, read at the end)
+    const size_t ws_base = c.ws.mark();
+    int* bad = (int*)c.ws.alloc(sizeof(int));
+    CCLR_CK(cudaMemsetAsync(bad, 0, sizeof(int), c.stream));
     // pair tables
     std::vector<int2> po(c.Po), pv(c.Pv);
     int64_t k = 0;
@@ -209,6 +220,7 @@ cclr_status cclr_set_hamiltonian(cclr_ctx* h, int n_occ, int n_vir, const cclr_c
     // Hamiltonian
     c.fock = c.dalloc(n * n);
     upload(c, c.fock, fock, n * n);
+    flag_nonfinite(c.L, c.fock, n * n, bad);
     c.oooo = c.dalloc(o * o * o * o);
     c.ooov = c.dalloc(o * o * o * v);
     c.oovv = c.dalloc(o * o * v * v);
@@ -221,12 +233,14 @@ cclr_status cclr_set_hamiltonian(cclr_ctx* h, int n_occ, int n_vir, const cclr_c
       Scope sc(c.ws);
       cplx* tmp = c.ws.cplxs(c.Po * c.Po);
       upload(c, tmp, blocks[0], c.Po * c.Po);
+      flag_nonfinite(c.L, tmp, c.Po * c.Po, bad);
       unpack_doubles(c.L, tmp, c.Po * c.Po, Tensor::make(c.oooo, {1, o, o, o, o}), n_occ, n_occ);
     }
     {
       Scope sc(c.ws);
       cplx* tmp = c.ws.cplxs(c.Po * o * v);
       upload(c, tmp, blocks[1], c.Po * o * v);
+      flag_nonfinite(c.L, tmp, c.Po * o * v, bad);
       cplx* tr = c.ws.cplxs(c.Po * o * v);
       permute(c.L, Tensor::make(tmp, {c.Po, o * v}).perm({1, 0}), Tensor::make(tr, {o * v, c.Po}), cx(1), false);
       // full[i][j][k][a] viewed as (R=(k,a), i, j)
@@ -234,11 +248,25 @@ cclr_status cclr_set_hamiltonian(cclr_ctx* h, int n_occ, int n_vir, const cclr_c
       unpack2(c.L, tr, c.Po, dst);
     }
     upload(c, c.oovv_p, blocks[2], c.Po * c.Pv);
+    flag_nonfinite(c.L, c.oovv_p, c.Po * c.Pv, bad);
     unpack_doubles(c.L, c.oovv_p, c.Nd, Tensor::make(c.oovv, {1, o, o, v, v}), n_occ, n_vir);
     upload(c, c.ovov, blocks[3], o * v * o * v);
+    flag_nonfinite(c.L, c.ovov, o * v * o * v, bad);
     upload(c, c.ovvv_p, blocks[4], o * v * c.Pv);
+    flag_nonfinite(c.L, c.ovvv_p, o * v * c.Pv, bad);
     unpack2(c.L, c.ovvv_p, c.Pv, Tensor::make(c.ovvv, {o * v, v, v}));
     upload(c, c.vvvv_p, blocks[5], c.Pv * c.Pv);
+    flag_nonfinite(c.L, c.vvvv_p, c.Pv * c.Pv, bad);
+    {
+      int h = 0;
+      CCLR_CK(cudaMemcpyAsync(&h, bad, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+      c.sync();
+      if (h) {
+        free_all(c);
+        throw Error(CCLR_E_ARG, "cclr_set_hamiltonian: an infinity or NaN in the Fock matrix or the integrals");
+      }
+    }
+    c.ws.release(ws_base);
     c.D = (double*)c.dalloc((c.N + 1) / 2 + 1);
     c.t = c.dalloc(c.N);
     c.t2 = c.dalloc(o * o * v * v);
@@ -261,12 +289,17 @@ cclr_status cc_ground(cclr_ctx* h, cclr_c128* e_corr_out, int* iters_out) {
     for (auto p : c.eom_vecs) c.dfree(p);
     c.eom_vecs.clear();
     c.eom_w.clear();
+    // Hbar defines the sigma products of every later solve: FP64-class when refining
     try {
       its = solve_ground(c);
     } catch (const Error& e) {
-      if (e.st == CCLR_E_NOCONV) build_hbar(c);
+      if (e.st == CCLR_E_NOCONV) {
+        PrecisionScope exact(c, exact_precision(c));
+        build_hbar(c);
+      }
       throw;
     }
+    PrecisionScope exact(c, exact_precision(c));
     build_hbar(c);
   });
   if (h && (st == CCLR_OK || st == CCLR_E_NOCONV)) {
@@ -291,6 +324,12 @@ cclr_status cc_lr_solve(cclr_ctx* h, int n_ops, const cclr_c128* ops, int n_freq
   return guard(h, [&](Ctx& c) {
     CCLR_REQUIRE(c.have_lambda, CCLR_E_STATE, "cc_lr_solve before cc_lambda");
     CCLR_REQUIRE(n_ops >= 1 && n_freq >= 1 && ops && omegas && gamma >= 0.0, CCLR_E_ARG, "bad cc_lr_solve arguments");
+    CCLR_REQUIRE(std::isfinite(gamma), CCLR_E_ARG, "cc_lr_solve: gamma must be finite");
+    for (int f = 0; f < n_freq; ++f)
+      CCLR_REQUIRE(std::isfinite(omegas[f]), CCLR_E_ARG, "cc_lr_solve: a frequency is an infinity or NaN");
+    for (int64_t i = 0; i < (int64_t)n_ops * c.n * c.n; ++i)
+      CCLR_REQUIRE(std::isfinite(ops[i].re) && std::isfinite(ops[i].im), CCLR_E_ARG,
+                   "cc_lr_solve: an operator element is an infinity or NaN");
     lr_solve(c, n_ops, (const cplx*)ops, n_freq, omegas, gamma, iters_out);
   });
 }
@@ -348,6 +387,7 @@ cclr_status cclr_set_amplitudes(cclr_ctx* h, int which, const cclr_c128* src, si
       c.have_t = true;
       c.have_lambda = false;
       c.named.erase("F.ready");
+      PrecisionScope exact(c, exact_precision(c));
       build_hbar(c);
     } else if (which == CCLR_AMP_LAMBDA) {
       CCLR_REQUIRE(c.have_hbar, CCLR_E_STATE, "set T before Lambda");
@@ -384,8 +424,7 @@ cclr_status cclr_sigma(cclr_ctx* h, int side, int nvec, const cclr_c128* in, ccl
   return guard(h, [&](Ctx& c) {
     CCLR_REQUIRE(c.have_hbar, CCLR_E_STATE, "sigma needs T (cc_ground or cclr_set_amplitudes)");
     CCLR_REQUIRE(nvec >= 1 && in && out && (side == 0 || side == 1), CCLR_E_ARG, "bad sigma arguments");
-    CCLR_REQUIRE(precision == CCLR_FP64 || precision == CCLR_TC_BF16X3 || precision == CCLR_TC_BF16X6, CCLR_E_ARG,
-                 "unknown precision");
+    CCLR_REQUIRE(valid_precision(precision), CCLR_E_ARG, "unknown precision");
     const int saved = c.opt.precision;
     c.opt.precision = precision;
     try {
@@ -459,8 +498,7 @@ cclr_status cclr_zgemm_nt(cclr_ctx* h, int precision, int M, int N, int K, const
   return guard(h, [&](Ctx& c) {
     CCLR_REQUIRE(c.have_ham, CCLR_E_STATE, "cclr_zgemm_nt needs a Hamiltonian (device workspace)");
     CCLR_REQUIRE(M > 0 && N > 0 && K > 0 && A && B && C, CCLR_E_ARG, "bad GEMM arguments");
-    CCLR_REQUIRE(precision == CCLR_FP64 || precision == CCLR_TC_BF16X3 || precision == CCLR_TC_BF16X6, CCLR_E_ARG,
-                 "unknown precision");
+    CCLR_REQUIRE(valid_precision(precision), CCLR_E_ARG, "unknown precision");
     const int saved = c.opt.precision;
     c.opt.precision = precision;
     try {
@@ -522,8 +560,7 @@ cclr_status cclr_bench_vector_kernels(cclr_ctx* h, int precision, int64_t n, int
     CCLR_REQUIRE(c.have_ham, CCLR_E_STATE, "cclr_bench_vector_kernels needs a Hamiltonian (device workspace)");
     CCLR_REQUIRE(n >= 1 && nx >= 1 && ny >= 1 && m >= 1 && m <= kVecMatOut && nx <= kVecMatMaxRows && reps >= 1 && ms3,
                  CCLR_E_ARG, "bad vector-kernel benchmark arguments");
-    CCLR_REQUIRE(precision == CCLR_FP64 || precision == CCLR_TC_BF16X3 || precision == CCLR_TC_BF16X6, CCLR_E_ARG,
-                 "unknown precision");
+    CCLR_REQUIRE(valid_precision(precision), CCLR_E_ARG, "unknown precision");
     const bool saved = c.L.fast32;
     c.L.fast32 = precision != CCLR_FP64;
     cplx *X = nullptr, *Y = nullptr, *C = nullptr, *G = nullptr, *scr = nullptr;
@@ -585,17 +622,20 @@ cclr_status cclr_bench_vector_kernels(cclr_ctx* h, int precision, int64_t n, int
   });
 }
 
-cclr_status cclr_kernel_profile(cclr_ctx* h, int enable, double* out4) {
+cclr_status cclr_kernel_profile(cclr_ctx* h, int enable, double* out8) {
   if (!h) return CCLR_E_ARG;
   Ctx& c = h->c;
-  if (out4) {
-    out4[0] = (double)c.prof_launches;
-    out4[1] = c.prof_ms;
-    out4[2] = c.prof_flops_exec;
-    out4[3] = c.prof_flops_useful;
+  if (out8)
+    for (int k = 0; k < 2; ++k) {
+      out8[4 * k + 0] = (double)c.prof_launches[k];
+      out8[4 * k + 1] = c.prof_ms[k];
+      out8[4 * k + 2] = c.prof_flops_exec[k];
+      out8[4 * k + 3] = c.prof_flops_useful[k];
+    }
+  for (int k = 0; k < 2; ++k) {
+    c.prof_launches[k] = 0;
+    c.prof_ms[k] = c.prof_flops_exec[k] = c.prof_flops_useful[k] = 0.0;
   }
-  c.prof_launches = 0;
-  c.prof_ms = c.prof_flops_exec = c.prof_flops_useful = 0.0;
   c.prof = enable != 0;
   c.kt.on = enable != 0;
   return CCLR_OK;
@@ -616,6 +656,12 @@ cclr_status cclr_kernel_breakdown(cclr_ctx* h, char* buf, int cap) {
   std::memcpy(buf, out.data(), n);
   buf[n] = 0;
   c.kt.totals.clear();
+  return CCLR_OK;
+}
+
+cclr_status cclr_debug_expire_next_wait(cclr_ctx* h, unsigned polls) {
+  if (!h || polls == 0) return CCLR_E_ARG;
+  h->c.dbg_wait_polls = polls;
   return CCLR_OK;
 }
 

@@ -25,9 +25,12 @@ struct ResponseData {
   std::vector<std::vector<zc>> beta;      // per operator: [shift][maxL] subspace solution
   std::vector<int> iters;                 // per (op, freq)
   bool solved = false;
+  bool refined = false;                   // solutions from the FP64-class refinement
 };
 
 struct Ctx;
+// BF16X3 / BF16X6: the modes whose vector passes run in FP32 and whose solves stop at floors
+inline bool mixed_precision(int p) { return p == CCLR_TC_BF16X3 || p == CCLR_TC_BF16X6; }
 int tc_slices(int precision);        // BF16 slices per operand in a tensor-core precision mode
 // While alive, the BF16 slices of the transient operand src (elems complex values, unchanged
 // meanwhile) are made once per view and reused by later contractions; workspace for `views`
@@ -92,29 +95,36 @@ struct Ctx {
   // tensor-core status word (bounded-wait expiry) and optional per-launch timing of the
   // tensor-core kernel with CUDA events on the context's stream
   int* tc_err = nullptr;
+  // test of the expiry path: the next tensor-core GEMM launch gets this poll limit and a first
+  // wait that nothing completes (0 = no test pending)
+  uint32_t dbg_wait_polls = 0;
   KernelTimer kt;   // per-kernel timing (switched on with the tensor-core timing)
   bool prof = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
+  std::vector<int> ev_kind;   // per used pair: 0 split-BF16 kernel, 1 FP64-class kernel
   size_t ev_used = 0;
-  double prof_ms = 0.0, prof_flops_exec = 0.0, prof_flops_useful = 0.0;
-  long prof_launches = 0;
-  void prof_events(cudaEvent_t& a, cudaEvent_t& b) {
+  // per kernel kind: launches, milliseconds, executed BF16 flops, useful complex flops (8 M N K)
+  double prof_ms[2] = {}, prof_flops_exec[2] = {}, prof_flops_useful[2] = {};
+  long prof_launches[2] = {};
+  void prof_events(cudaEvent_t& a, cudaEvent_t& b, int kind) {
     if (ev_used == ev_pool.size()) {
       cudaEvent_t x, y;
       CCLR_CK(cudaEventCreate(&x));
       CCLR_CK(cudaEventCreate(&y));
       ev_pool.push_back({x, y});
+      ev_kind.push_back(0);
     }
     a = ev_pool[ev_used].first;
     b = ev_pool[ev_used].second;
+    ev_kind[ev_used] = kind;
     ++ev_used;
   }
   void prof_collect() {  // after a stream synchronize
     for (size_t i = 0; i < ev_used; ++i) {
       float ms = 0.f;
       CCLR_CK(cudaEventElapsedTime(&ms, ev_pool[i].first, ev_pool[i].second));
-      prof_ms += ms;
-      ++prof_launches;
+      prof_ms[ev_kind[i]] += ms;
+      ++prof_launches[ev_kind[i]];
     }
     ev_used = 0;
   }
@@ -154,6 +164,20 @@ struct Ctx {
   Tensor f(const char* blk) const;     // Fock blocks "oo", "ov", "vo", "vv" as strided views
 };
 
+// The contraction arithmetic of c switched for the lifetime of the object
+struct PrecisionScope {
+  Ctx& c;
+  int old;
+  PrecisionScope(Ctx& cc, int p) : c(cc), old(cc.opt.precision) { c.opt.precision = p; }
+  ~PrecisionScope() { c.opt.precision = old; }
+};
+// mixed-precision mode with FP64 refinement (cclr_options.refine)
+inline bool refining(const Ctx& c) { return mixed_precision(c.opt.precision) && c.opt.refine != 0; }
+// the arithmetic of the quantities that define the answer (Hbar, xi, eta, Hessian products)
+inline int exact_precision(const Ctx& c) { return refining(c) ? CCLR_TC_F64 : c.opt.precision; }
+// floor of the mixed-precision phase relative to the right-hand side
+inline double mixed_floor(const Ctx& c) { return c.opt.refine_tol > 0.0 ? c.opt.refine_tol : 2e-5; }
+
 // GEMM backend selection (FP64 DFMA or tensor cores), row-major, see zgemm()
 void gemm_dispatch(Ctx& c, bool ta, bool tb, int64_t M, int64_t N, int64_t K, cplx alpha, const cplx* A,
                    int64_t lda, const cplx* B, int64_t ldb, cplx beta, cplx* C, int64_t ldc);
@@ -174,7 +198,7 @@ struct OutAxes {
 };
 void tc_gemm_views(Ctx& c, const Tensor& vm, int nrm, const Tensor& vn, int nrn, cplx alpha, cplx beta, cplx* C,
                    int64_t ldc, const OutAxes* oa = nullptr);
-int tc_splits(int64_t M, int64_t N, int64_t K);   // split-K slices the tensor-core GEMM would use
+int tc_splits(int64_t M, int64_t N, int64_t K, int precision);   // split-K slices the tensor-core GEMM would use
 
 // equations (ccsd.cu, sigma.cu, props.cu)
 void build_denominators(Ctx& c);

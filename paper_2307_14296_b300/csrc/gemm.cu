@@ -14,10 +14,11 @@ void gemm_dispatch(Ctx& c, bool ta, bool tb, int64_t M, int64_t N, int64_t K, cp
                    int64_t lda, const cplx* B, int64_t ldb, cplx beta, cplx* C, int64_t ldc) {
   if (c.opt.precision != CCLR_FP64 && tc_gemm_try(c, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc)) return;
   const int64_t tiles = ((M + 63) / 64) * ((N + 63) / 64);
-  if (tiles < 2 * 148 && K >= 32) {
+  const int64_t sms = num_sms();
+  if (tiles < 2 * sms && K >= 32) {
     // FP64 split-K: enough slices for ~2 blocks per SM, each slice at least 16 deep (FP64 runs at
     // a few GFLOP/s per SM, so even a 30 x 30 x 200 product wants more than one SM)
-    int64_t S = std::min<int64_t>({(2 * 148 + tiles - 1) / tiles, K / 16, 256});
+    int64_t S = std::min<int64_t>({(2 * sms + tiles - 1) / tiles, K / 16, 256});
     if (S >= 2) {
       int64_t kchunk = ((K + S - 1) / S + 7) / 8 * 8;
       S = (K + kchunk - 1) / kchunk;

@@ -176,6 +176,7 @@ struct Launch {  // stream + launch counter shared by all kernels of one context
 // have the same rank/dims (strides arbitrary).
 void permute(const Launch& L, const Tensor& src, const Tensor& dst, cplx alpha, bool accumulate);
 void fill_zero(const Launch& L, cplx* p, int64_t n);
+void flag_nonfinite(const Launch& L, const cplx* p, int64_t n, int* flag);   // *flag = 1 on inf / NaN
 void fill_hash(const Launch& L, cplx* p, int64_t n, uint64_t seed);   // deterministic values in [-1, 1)^2
 
 // Row-major complex FP64 GEMM: C[MxN] = alpha op(A) op(B) + beta C; op(A)[m,k] = ta ? A[k*lda+m]
@@ -267,6 +268,11 @@ void lincomb(const Launch& L, int64_t n, int nb, const cplx* X, int64_t ldx, con
              bool accumulate);
 
 int reduce_blocks();
+// streaming multiprocessors of the current device (queried once per device)
+int num_sms();
+// true on the first call for the current device (done: 64 per-device flags), e.g. for per-device
+// kernel attributes
+bool once_per_device(bool* done);
 
 // Split-K GEMM for skinny shapes: partials P[z] = op(A) op(B) over k in [z*kchunk, (z+1)*kchunk)
 // (S slices, each M x N with ld N), then C = alpha * sum_z P[z] + beta * C in a fixed order.
@@ -286,7 +292,7 @@ void unpack2(const Launch& L, const cplx* D, int64_t ldd, const Tensor& X);
 // otherwise.  Row starts must be 16-byte aligned; scratch holds gram_scratch_elems().
 void gram(const Launch& L, int64_t n, const Rows& X, const Rows& Y, bool herm, cplx* out_dev, cplx* scratch,
           int64_t scratch_elems, bool x32 = false);   // x32: all rows FP32 mirrors (even strides)
-inline int64_t gram_scratch_elems() { return 148 * 64 * 8; }
+inline int64_t gram_scratch_elems() { return (int64_t)num_sms() * 64 * 8; }
 
 // Small element-wise helpers
 void scale_vec(const Launch& L, int64_t n, cplx a, cplx* x);

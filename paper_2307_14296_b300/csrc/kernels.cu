@@ -11,7 +11,6 @@ namespace cclr {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kReduceBlocks = 296;  // 2 x 148 SMs
 
 __device__ __forceinline__ cplx cmul(cplx a, cplx b) {
   return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
@@ -20,7 +19,8 @@ __device__ __forceinline__ cplx cadd(cplx a, cplx b) { return make_double2(a.x +
 
 inline int grid_for(int64_t n, int per = kThreads) {
   int64_t g = (n + per - 1) / per;
-  if (g > 148 * 16) g = 148 * 16;
+  const int64_t cap = (int64_t)num_sms() * 16;
+  if (g > cap) g = cap;
   if (g < 1) g = 1;
   return (int)g;
 }
@@ -180,6 +180,16 @@ __global__ void k_fill_hash(cplx* p, int64_t n, uint64_t seed) {
     const uint32_t a = (uint32_t)h, b = (uint32_t)(h >> 32);
     p[i] = make_double2((double)a * 0x1p-31 - 1.0, (double)b * 0x1p-31 - 1.0);
   }
+}
+
+// *flag = 1 if any real or imaginary part is an infinity or a NaN
+__global__ void k_nonfinite(const cplx* __restrict__ p, int64_t n, int* flag) {
+  bool bad = false;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const cplx x = p[i];
+    bad |= !isfinite(x.x) || !isfinite(x.y);
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch(flag, 1);
 }
 
 __global__ void k_fill_zero(cplx* p, int64_t n) {
@@ -577,7 +587,7 @@ template <> struct Arith<false> {
   }
 };
 
-constexpr int kVecMatBlocks = 4 * 148;
+inline int vecmat_blocks() { return 4 * num_sms(); }
 
 // r_q = sum_j X_j C[j][q] + add; Y_q = (D ? -r_q / (D - z_q) : r_q) (+ Y_q); per-block partial
 // norms of r_q (or of Y_q if norm_y).  Q >= m outputs are computed (coefficients of q >= m are
@@ -1027,7 +1037,27 @@ __global__ void k_splitk_reduce(const cplx* __restrict__ P, int S, int64_t M, in
 
 }  // namespace
 
-int reduce_blocks() { return kReduceBlocks; }
+int num_sms() {
+  static int cache[64] = {};
+  int d = 0;
+  if (cudaGetDevice(&d) != cudaSuccess) d = 0;
+  const int slot = d >= 0 && d < 64 ? d : -1;
+  if (slot >= 0 && cache[slot]) return cache[slot];
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, d) != cudaSuccess || n <= 0) n = 1;
+  if (slot >= 0) cache[slot] = n;
+  return n;
+}
+
+bool once_per_device(bool* done) {
+  int d = 0;
+  if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= 64) return true;
+  if (done[d]) return false;
+  done[d] = true;
+  return true;
+}
+
+int reduce_blocks() { return 2 * num_sms(); }
 
 void splitk_reduce(const Launch& L, const cplx* P, int S, int64_t M, int64_t N, cplx alpha, cplx beta, cplx* C,
                    int64_t ldc) {
@@ -1126,7 +1156,7 @@ void gram(const Launch& L, int64_t n, const Rows& X, const Rows& Y, bool herm, c
       while (lc < kGramMaxLog && ((size_t)(a + b) * esz << lc) < (size_t(64) << 10) && stage_bytes(lc + 1) <= kGramSmemMax)
         ++lc;
       const int64_t nchunks = (n + (int64_t(1) << lc) - 1) >> lc;
-      int nblk = (int)std::min<int64_t>(148, nchunks);
+      int nblk = (int)std::min<int64_t>(num_sms(), nchunks);
       if ((int64_t)nblk * a * b > scratch_elems) nblk = (int)std::max<int64_t>(1, scratch_elems / ((int64_t)a * b));
       const int NYt = b == 1 ? 1 : (b <= 4 ? 4 : 8);
       const size_t red = kGramHead + sizeof(cplx) * kGramWarps * NYt * 32;
@@ -1147,7 +1177,7 @@ void gram(const Launch& L, int64_t n, const Rows& X, const Rows& Y, bool herm, c
     }
 }
 
-int64_t vecmat_scratch_doubles() { return (int64_t)kVecMatOut * kVecMatBlocks; }
+int64_t vecmat_scratch_doubles() { return (int64_t)kVecMatOut * vecmat_blocks(); }
 
 namespace {
 template <bool F32, int Q, bool X32>
@@ -1158,12 +1188,10 @@ void launch_vecmat(const Launch& L, int64_t n, const VecMat& a, double* part) {
   constexpr int U = (F32 && Q == 16) ? 4 : 8;
   const int nx = a.X.total();
   const size_t smem = sizeof(typename Arith<F32>::C) * (size_t)nx * Q + sizeof(void*) * (size_t)nx;
-  static bool attr = false;
-  if (!attr) {   // kVecMatMaxRows x 16 coefficients (16 B each) + row table: 132 KiB
+  static bool attr[64] = {};
+  if (once_per_device(attr))   // kVecMatMaxRows x 16 coefficients (16 B each) + row table: 132 KiB
     CCLR_CK(cudaFuncSetAttribute(k_vecmat<F32, Q, E, U, X32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 136 << 10));
-    attr = true;
-  }
-  k_vecmat<F32, Q, E, U, X32><<<kVecMatBlocks, kThreads, smem, L.s>>>(n, a.X, a.m, a.C, a.add, a.Y, a.ldy, a.acc, a.D, a.z,
+  k_vecmat<F32, Q, E, U, X32><<<vecmat_blocks(), kThreads, smem, L.s>>>(n, a.X, a.m, a.C, a.add, a.Y, a.ldy, a.acc, a.D, a.z,
                                                               a.norm_y, part);
 }
 }  // namespace
@@ -1198,7 +1226,7 @@ void vecmat(const Launch& L, int64_t n, const VecMat& a, double* scratch) {
   bump(L, shaped("k_vecmat", nx, a.m, a.D ? 1 : 0));
   if (a.norm2) {
     kbeg(L);
-    k_sum_rows<<<a.m, kThreads, 0, L.s>>>(part, kVecMatBlocks, a.norm2);
+    k_sum_rows<<<a.m, kThreads, 0, L.s>>>(part, vecmat_blocks(), a.norm2);
     CCLR_CK(cudaGetLastError());
     bump(L, "k_sum_rows");
   }
@@ -1241,7 +1269,7 @@ void launch_permute(const Launch& L, const PermArgs& a, const cplx* src, cplx* d
       batch *= a.dim[k];
     }
     const int64_t ntiles = batch * t.ntS * t.ntT;
-    const int g = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, 148 * 16));
+    const int g = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)num_sms() * 16));
     k_permute_tiled<AK><<<g, 256, 0, L.s>>>(t, src, dst, ntiles, al, conj, acc);
     return;
   }
@@ -1300,6 +1328,14 @@ void fill_hash(const Launch& L, cplx* p, int64_t n, uint64_t seed) {
   k_fill_hash<<<grid_for(n), kThreads, 0, L.s>>>(p, n, seed);
   CCLR_CK(cudaGetLastError());
   bump(L, "k_fill_hash");
+}
+
+void flag_nonfinite(const Launch& L, const cplx* p, int64_t n, int* flag) {
+  if (n <= 0) return;
+  kbeg(L);
+  k_nonfinite<<<grid_for(n), kThreads, 0, L.s>>>(p, n, flag);
+  CCLR_CK(cudaGetLastError());
+  bump(L, "k_nonfinite");
 }
 
 void fill_zero(const Launch& L, cplx* p, int64_t n) {
@@ -1421,14 +1457,14 @@ void div_shift(const Launch& L, int64_t n, const cplx* x, const double* D, cplx 
 void dots(const Launch& L, int64_t n, int nvec, const cplx* x, int64_t ldx, const cplx* y, int64_t ldy, bool herm,
           cplx* out_dev, cplx* scratch) {
   if (nvec <= 0) return;
-  dim3 g(kReduceBlocks, nvec);
+  dim3 g(reduce_blocks(), nvec);
   kbeg(L);
   if (L.fast32) k_dots_partial32<<<g, kThreads, 0, L.s>>>(n, x, ldx, y, ldy, herm, scratch);
   else k_dots_partial<<<g, kThreads, 0, L.s>>>(n, x, ldx, y, ldy, herm, scratch);
   CCLR_CK(cudaGetLastError());
   bump(L, "k_dots");
   kbeg(L);
-  k_sum_partials<<<nvec, kThreads, 0, L.s>>>(scratch, kReduceBlocks, out_dev);
+  k_sum_partials<<<nvec, kThreads, 0, L.s>>>(scratch, reduce_blocks(), out_dev);
   CCLR_CK(cudaGetLastError());
   bump(L, "k_sum_partials");
 }

@@ -21,6 +21,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <functional>
+#include <memory>
 
 namespace cclr {
 
@@ -57,7 +58,7 @@ namespace {
 struct Fast32 {
   Ctx& c;
   bool old;
-  explicit Fast32(Ctx& cc) : c(cc), old(cc.L.fast32) { c.L.fast32 = c.opt.precision != CCLR_FP64; }
+  explicit Fast32(Ctx& cc) : c(cc), old(cc.L.fast32) { c.L.fast32 = mixed_precision(c.opt.precision); }
   ~Fast32() { c.L.fast32 = old; }
 };
 
@@ -152,9 +153,19 @@ void combine(Ctx& c, const Rows& X, int m, const std::vector<zc>& W, cplx* Y) {
 }  // namespace
 
 // ------------------------------------------------------------------------------ ground state
+// Jacobi + DIIS.  In the mixed modes the residuals are first evaluated with split-BF16 tensor-core
+// contractions until the residual falls to mixed_floor() of the first one (or stagnates within
+// 10x of it); with refinement the iteration then continues, DIIS restarted, with FP64-class
+// residuals to ground_tol.
 int solve_ground(Ctx& c) {
   const int64_t N = c.N;
   const int kDiis = 8;
+  const bool mixed = mixed_precision(c.opt.precision);
+  const bool refine = refining(c);
+  int phase = mixed ? 1 : 2;
+  std::unique_ptr<PrecisionScope> exact;   // the FP64-class arithmetic of the refinement phase
+  double t_ref = 0.0;
+  long v_ref = 0;
   fill_zero(c.L, c.t, N);
   fill_zero(c.L, c.t2, (int64_t)c.o * c.o * c.v * c.v);
   ++data_generation();
@@ -173,25 +184,44 @@ int solve_ground(Ctx& c) {
   double rn = 0.0, tol_eff = c.opt.ground_tol, rn0 = 0.0, best = 1e300;
   int best_it = 0;
   Phases ph("ground");
+  int it_ref0 = 0;
   try {
-    for (it = 1; it <= c.opt.maxit * 2; ++it) {
+    for (it = 1; it <= c.opt.maxit * 2 + (phase == 2 && mixed ? it_ref0 : 0); ++it) {
       ph.mark(c, "residual");
+      if (phase == 2 && mixed) { ++v_ref; }
+      const double t0 = now();
       ccsd_residual(c, R);
       ph.mark(c, "diis");
       zc h;
       dots(c.L, N, 1, R, 0, R, 0, true, dd, scr);
       to_host(c, dd, &h, 1);
+      if (phase == 2 && mixed) t_ref += now() - t0;
       rn = std::sqrt(h.real());
       c.stats.max_residual = rn;
-      // tensor-core modes: the sigma-type products carry ~1e-5 relative error (split-BF16
-      // operands, FP32 accumulation; the Fock diagonal is exact), so the target is 1e-5 of the
-      // starting residual, with a stop at a stagnating residual below 1e-4 of it (8 iterations
-      // without a 20% gain)
-      if (it == 1) tol_eff = c.opt.precision == CCLR_FP64 ? c.opt.ground_tol : std::max(c.opt.ground_tol, 1e-5 * rn);
+      // mixed modes: the residual carries ~1e-5 relative error (split-BF16 operands, FP32
+      // accumulation; the Fock diagonal is exact), so the mixed phase ends at mixed_floor() of the
+      // starting residual, or at a stagnating residual below 10x that (8 iterations without a
+      // 20% gain)
+      if (it == 1) tol_eff = mixed ? std::max(c.opt.ground_tol, mixed_floor(c) * rn) : c.opt.ground_tol;
       if (it == 1) rn0 = rn;
-      if (rn < tol_eff) { ok = true; break; }
-      if (rn < 0.8 * best) { best = rn; best_it = it; }
-      if (c.opt.precision != CCLR_FP64 && it - best_it >= 8 && best < 1e-4 * rn0) { ok = true; break; }
+      if (phase == 1) {
+        if (rn < 0.8 * best) { best = rn; best_it = it; }
+        const bool floor = rn < tol_eff || (it - best_it >= 8 && best < 10.0 * mixed_floor(c) * rn0);
+        if (floor && (!refine || rn < c.opt.ground_tol)) { ok = true; break; }
+        if (floor) {
+          // refinement: the same amplitudes, FP64-class residuals, DIIS restarted
+          phase = 2;
+          it_ref0 = it;
+          exact.reset(new PrecisionScope(c, CCLR_TC_F64));
+          nh = 0;
+          head = 0;
+          std::fill(Bm.begin(), Bm.end(), zc(0));
+          continue;
+        }
+      } else if (rn < c.opt.ground_tol) {
+        ok = true;
+        break;
+      }
       // new error vector e = -R/D and new amplitudes t + e into the ring buffer slot
       cplx* e = hist_e + (int64_t)head * N;
       cplx* tn = hist_t + (int64_t)head * N;
@@ -238,6 +268,8 @@ int solve_ground(Ctx& c) {
     throw;
   }
   c.dfree(R); c.dfree(hist_t); c.dfree(hist_e);
+  c.stats.refine_vectors += v_ref;
+  c.stats.refine_seconds += t_ref;
   c.e_corr = ccsd_energy(c);
   c.have_t = true;
   if (!ok) throw Error(CCLR_E_NOCONV, "CCSD did not converge: |Omega| = " + std::to_string(rn));
@@ -265,11 +297,10 @@ struct System {            // one right-hand side with its shared trial space
   int best_it = 0;
 };
 
-// Thick restart: compress the trial space onto the span of the current solutions of all shifts
-// (QR with column pivoting of the coefficient matrix [beta_1 ... beta_ns], at most kmax columns).
-// Sigma vectors transform with the basis (S' = S Q), so no sigma is recomputed.
-void restart(Ctx& c, System& s, int maxL, int kmax) {
-  const int64_t N = c.N;
+// Orthonormal directions (in the coefficient space of the trial vectors) spanning the solutions
+// [beta_1 ... beta_ns] of all shifts: Gram-Schmidt with column pivoting, stopping at kmax columns
+// or when the largest remaining column is below cut times the first.
+std::vector<std::vector<zc>> solution_directions(const System& s, double cut, int kmax) {
   const int L = s.L, ns = (int)s.z.size();
   std::vector<std::vector<zc>> cols(ns, std::vector<zc>(L));
   for (int q = 0; q < ns; ++q)
@@ -289,7 +320,7 @@ void restart(Ctx& c, System& s, int maxL, int kmax) {
     if (best < 0) break;
     const double nrm = std::sqrt(bn);
     if (first < 0) first = nrm;
-    if (nrm <= 1e-13 * first) break;
+    if (nrm <= cut * first) break;
     used[best] = 1;
     std::vector<zc> qv(L);
     for (int i = 0; i < L; ++i) qv[i] = cols[best][i] / nrm;
@@ -301,6 +332,16 @@ void restart(Ctx& c, System& s, int maxL, int kmax) {
     }
     Q.push_back(qv);
   }
+  return Q;
+}
+
+// Thick restart: compress the trial space onto the span of the current solutions of all shifts
+// (QR with column pivoting of the coefficient matrix [beta_1 ... beta_ns], at most kmax columns).
+// Sigma vectors transform with the basis (S' = S Q), so no sigma is recomputed.
+void restart(Ctx& c, System& s, int maxL, int kmax) {
+  const int64_t N = c.N;
+  const int L = s.L, ns = (int)s.z.size();
+  const std::vector<std::vector<zc>> Q = solution_directions(s, 1e-13, kmax);
   const int kk = (int)Q.size();
   CCLR_REQUIRE(kk >= 1, CCLR_E_NOCONV, "Davidson restart: empty solution space");
   {
@@ -411,6 +452,8 @@ int add_corrections(Ctx& c, cplx* B, int L, cplx* R, int nt, const double* pre2,
 }
 
 // Solve (Op - z) x = -b for every system and shift.  Op(nvec, in, out) acts on N-vectors.
+// A system that enters with L > 0 starts from its first L trial vectors (their sigma vectors are
+// formed in the first iteration); otherwise from the preconditioned right-hand side.
 //
 // Per iteration and right-hand side, every pass over the N-vectors is one multi-output kernel:
 //   Gram:      B^H [S_new | B_new | b] and S_old^H B_new (the Galerkin matrices B^H S, B^H B)
@@ -423,6 +466,7 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
               int maxL, double tol) {
   static const bool verbose = std::getenv("CCLR_VERBOSE") != nullptr;
   Fast32 f32(c);
+  const bool mixed = mixed_precision(c.opt.precision);
   const int64_t N = c.N;
   const int kMaxNew = 4;   // new trial vectors per right-hand side and iteration (worst shifts first)
   const int kTry = 8;      // candidate corrections formed per right-hand side and iteration
@@ -497,16 +541,21 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
     s.rnorm.assign(s.z.size(), 1e300);
     s.conv.assign(s.z.size(), 0);
     s.done = false;
-    s.L = 0;
-    // start: b / D, normalized (preconditioned right-hand side at z = 0)
-    div_shift(c.L, N, s.rhs, c.Dpre ? c.Dpre : c.D, cx(0), cx(1), s.B);
-    const double nb = std::sqrt(norm2(c, s.B));
-    CCLR_REQUIRE(nb > 0.0, CCLR_E_ARG, "zero right-hand side");
-    scale_vec(c.L, N, cx(1.0 / nb), s.B);
-    mirror(s.B, s.Bf, 0, 1);
-    s.L = 1;
+    s.best = 1e300;
+    s.best_it = 0;
+    CCLR_REQUIRE(s.L >= 0 && s.L <= maxL, CCLR_E_ARG, "Davidson: starting space larger than max_subspace");
+    if (s.L == 0) {
+      // start: b / D, normalized (preconditioned right-hand side at z = 0)
+      div_shift(c.L, N, s.rhs, c.Dpre ? c.Dpre : c.D, cx(0), cx(1), s.B);
+      const double nb = std::sqrt(norm2(c, s.B));
+      CCLR_REQUIRE(nb > 0.0, CCLR_E_ARG, "zero right-hand side");
+      scale_vec(c.L, N, cx(1.0 / nb), s.B);
+      s.L = 1;
+    }
+    mirror(s.B, s.Bf, 0, s.L);
   }
-  std::vector<int> fresh(sys.size(), 1);   // new vectors at the end of each basis
+  std::vector<int> fresh(sys.size());   // new vectors at the end of each basis
+  for (size_t k = 0; k < sys.size(); ++k) fresh[k] = sys[k].L;
   Phases ph("davidson");
   for (int it = 1; it <= c.opt.maxit; ++it) {
     ph.mark(c, "sigma");
@@ -580,9 +629,10 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
       }
       fresh[k] = 0;
       const int L = s.L;
-      // tensor-core modes: sigma carries ~1e-5 relative error at long K (FP32 accumulation), so
-      // the target is raised to 2e-5 of |b| (alpha stays within ~3e-7 of the FP64 result)
-      const double tol_s = c.opt.precision == CCLR_FP64 ? tol : std::max(tol, 2e-5 * std::sqrt(s.xx));
+      // mixed modes: sigma carries ~1e-5 relative error at long K (FP32 accumulation), so the
+      // mixed phase stops at mixed_floor() of |b| (the refinement phase, or the caller with
+      // refine = 0, takes it from there)
+      const double tol_s = mixed ? std::max(tol, mixed_floor(c) * std::sqrt(s.xx)) : tol;
       // ---- subspace solves (B^H S - z B^H B) beta = -B^H b for every shift
       ph.mark(c, "subspace");
       for (size_t q = 0; q < s.z.size(); ++q) {
@@ -594,16 +644,34 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
         for (int i = 0; i < L; ++i) s.beta[q][i] = rhs[i];
       }
       // ---- residual norms of the open shifts; once all are below the target, the shifts
-      // locked earlier are checked again at the final trial space
+      // locked earlier are checked again at the final trial space.  With FP64 vector arithmetic
+      // (FP64 mode, refinement) a pass costs about one DFMA per complex element and output row,
+      // so only the kTry open shifts with the largest last norm are recomputed each iteration;
+      // every open shift is checked once those are below the target.
       std::vector<int> open, locked;
       for (size_t q = 0; q < s.z.size(); ++q) (s.conv[q] ? locked : open).push_back((int)q);
       std::vector<std::pair<double, int>> order;
       ph.mark(c, "norms");
-      residual_norms(s, open);
-      for (int q : open) {
-        s.conv[q] = s.rnorm[q] < tol_s;
-        if (!s.conv[q]) order.push_back({s.rnorm[q], q});
+      std::vector<int> check = open;
+      if (!mixed && (int)open.size() > kTry && it > 1) {
+        std::vector<std::pair<double, int>> last;
+        for (int q : open) last.push_back({s.rnorm[q], q});
+        std::partial_sort(last.begin(), last.begin() + kTry, last.end(), [](auto& a, auto& b) { return a.first > b.first; });
+        check.clear();
+        for (int t = 0; t < kTry; ++t) check.push_back(last[t].second);
+        residual_norms(s, check);
+        bool tracked_done = true;
+        for (int q : check) tracked_done = tracked_done && s.rnorm[q] < tol_s;
+        if (tracked_done) {
+          check = open;
+          residual_norms(s, check);
+        }
+      } else {
+        residual_norms(s, check);
       }
+      for (int q : check) s.conv[q] = s.rnorm[q] < tol_s;
+      for (int q : open)
+        if (!s.conv[q]) order.push_back({s.rnorm[q], q});
       if (order.empty() && !locked.empty()) {
         residual_norms(s, locked);
         for (int q : locked) {
@@ -611,14 +679,13 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
           if (!s.conv[q]) order.push_back({s.rnorm[q], q});
         }
       }
-      for (size_t q = 0; q < s.z.size(); ++q) c.stats.max_residual = std::max(c.stats.max_residual, s.rnorm[q]);
       s.iters = it;
       if (verbose)
         std::fprintf(stderr, "[cclr] davidson it %d rhs %zu L %d unconverged %zu/%zu max|r| %.3e tol %.1e\n", it, k, L,
                      order.size(), s.z.size(), order.empty() ? 0.0 : std::max_element(order.begin(), order.end())->first,
                      tol_s);
-      if (!order.empty() && c.opt.precision != CCLR_FP64) {
-        // tensor-core modes: accept a stagnating solve whose residuals are all within 5x the floor
+      if (!order.empty() && mixed) {
+        // mixed modes: accept a stagnating solve whose residuals are all within 5x the floor
         double mx = 0.0;
         for (auto& pr : order) mx = std::max(mx, pr.first);
         if (mx < 0.8 * s.best) { s.best = mx; s.best_it = it; }
@@ -673,9 +740,50 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
       fresh[k] = kk;
     }
     ph.mark(c, "other");
+    // the largest current residual over all systems and shifts (the final one at exit)
+    c.stats.max_residual = 0.0;
+    for (auto& s : sys)
+      for (double r : s.rnorm) c.stats.max_residual = std::max(c.stats.max_residual, r);
     if (all_done) return;
   }
   throw Error(CCLR_E_NOCONV, "Davidson did not converge within maxit iterations");
+}
+
+// FP64 iterative refinement of systems solved in a mixed mode (cclr_options.refine): every system
+// restarts from the compressed span of its mixed-precision solutions, U = B Q (directions above
+// 1e-10 of the largest, at most 16), whose sigma vectors are formed again in
+// the FP64-class tensor-core mode, and the Davidson iteration continues there with FP64-class
+// sigma products and FP64 residuals, norms and projections until every residual is below tol.
+// The phase-1 arrays of each system (B, S) are freed and replaced; bases[k] / sigs[k] (when not
+// null) are updated to the new arrays.
+void refine_systems(Ctx& c, std::vector<System>& sys, const std::function<void(int, const cplx*, cplx*)>& Op, int maxL,
+                    double tol, std::vector<cplx*>* bases, std::vector<cplx*>* sigs) {
+  PrecisionScope exact(c, CCLR_TC_F64);
+  const int64_t N = c.N;
+  const double t0 = now();
+  const long v0 = c.stats.sigma_vectors;
+  for (size_t k = 0; k < sys.size(); ++k) {
+    System& s = sys[k];
+    const std::vector<std::vector<zc>> Q = solution_directions(s, 1e-10, std::max(1, std::min(16, maxL / 2)));
+    const int r = (int)Q.size();
+    CCLR_REQUIRE(r >= 1, CCLR_E_NOCONV, "refinement: empty solution space");
+    std::vector<zc> W((size_t)s.L * r);
+    for (int j = 0; j < s.L; ++j)
+      for (int a = 0; a < r; ++a) W[(size_t)j * r + a] = Q[a][j];
+    cplx* B2 = c.dalloc((int64_t)maxL * N);
+    combine(c, rows(c, s.B, s.L), r, W, B2);
+    c.dfree(s.B);
+    c.dfree(s.S);
+    cplx* S2 = c.dalloc((int64_t)maxL * N);
+    s.B = B2;
+    s.S = S2;
+    s.L = r;
+    if (bases) (*bases)[k] = B2;
+    if (sigs) (*sigs)[k] = S2;
+  }
+  davidson(c, sys, Op, maxL, tol);
+  c.stats.refine_vectors += c.stats.sigma_vectors - v0;
+  c.stats.refine_seconds += now() - t0;
 }
 
 // ------------------------------------------------------------------------------ Lambda
@@ -691,8 +799,15 @@ int solve_lambda(Ctx& c) {
   s.S = c.dalloc((int64_t)maxL * N);
   std::vector<System> sys{s};
   auto cleanup = [&]() { c.dfree(sys[0].B); c.dfree(sys[0].S); c.dfree(eta); };
+  int its = 0;
   try {
-    davidson(c, sys, [&](int nv, const cplx* in, cplx* out) { sigma_left(c, nv, in, out); }, maxL, c.opt.ground_tol);
+    auto op = [&](int nv, const cplx* in, cplx* out) { sigma_left(c, nv, in, out); };
+    davidson(c, sys, op, maxL, c.opt.ground_tol);
+    its = sys[0].iters;
+    if (refining(c)) {
+      refine_systems(c, sys, op, maxL, c.opt.ground_tol, nullptr, nullptr);
+      its += sys[0].iters;
+    }
   } catch (...) {
     cleanup();
     throw;
@@ -703,7 +818,6 @@ int solve_lambda(Ctx& c) {
   to_dev(c, sys[0].beta[0].data(), bd, sys[0].L);
   lincomb(c.L, N, sys[0].L, sys[0].B, N, bd, c.lam, false);
   expand_t2(c, c.lam + c.Ns, c.l2, 1);
-  const int its = sys[0].iters;
   cleanup();
   c.have_lambda = true;
   c.named.erase("F.ready");
@@ -751,6 +865,7 @@ void lr_solve(Ctx& c, int n_ops, const cplx* ops_host, int n_freq, const double*
     cplx* X = c.dalloc(n * n);
     CCLR_CK(cudaMemcpyAsync(X, ops_host + (int64_t)k * n * n, sizeof(cplx) * n * n, cudaMemcpyHostToDevice, c.stream));
     rd.ops_dev.push_back(X);
+    PrecisionScope exact(c, exact_precision(c));   // the right-hand sides define the answer
     cplx* xi = c.dalloc(N);
     xi_vec(c, X, xi);
     rd.xi.push_back(xi);
@@ -765,7 +880,16 @@ void lr_solve(Ctx& c, int n_ops, const cplx* ops_host, int n_freq, const double*
     sys[k].S = rd.sig[k];
   }
   ph.mark(c, "davidson");
-  davidson(c, sys, [&](int nv, const cplx* in, cplx* out) { sigma_right(c, nv, in, out); }, maxL, c.opt.tol);
+  auto op = [&](int nv, const cplx* in, cplx* out) { sigma_right(c, nv, in, out); };
+  davidson(c, sys, op, maxL, c.opt.tol);
+  std::vector<int> its1(n_ops);
+  for (int k = 0; k < n_ops; ++k) its1[k] = sys[k].iters;
+  rd.refined = refining(c);
+  if (rd.refined) {
+    ph.mark(c, "refine");
+    refine_systems(c, sys, op, maxL, c.opt.tol, &rd.basis, &rd.sig);
+    for (int k = 0; k < n_ops; ++k) sys[k].iters += its1[k];
+  }
   ph.mark(c, "finish");
   rd.nb.resize(n_ops);
   rd.beta.resize(n_ops);
@@ -789,6 +913,10 @@ void lr_solve(Ctx& c, int n_ops, const cplx* ops_host, int n_freq, const double*
 void response_function(Ctx& c, cplx* out_host) {
   ResponseData& rd = c.rd;
   CCLR_REQUIRE(rd.solved, CCLR_E_STATE, "cc_response_function before cc_lr_solve");
+  // refined solutions: FP64 vector arithmetic and all Hessian directions above 1e-12; the Hessian
+  // products in the FP32-class tensor-core mode (the F term is quadratic in the solutions and
+  // carries a small part of <<X;Y>>, so its ~1e-6 relative error stays far below the target)
+  PrecisionScope exact(c, rd.refined ? CCLR_TC_F64 : c.opt.precision);
   Fast32 f32(c);
   const int64_t N = c.N;
   const int nop = rd.n_ops, maxL = std::max(8, c.opt.max_subspace);
@@ -826,7 +954,7 @@ void response_function(Ctx& c, cplx* out_host) {
       if (best < 0) break;
       const double nrm = std::sqrt(bn);
       if (first < 0) first = nrm;
-      if (nrm <= (c.opt.precision == CCLR_FP64 ? 1e-12 : 1e-7) * first) break;
+      if (nrm <= (mixed_precision(c.opt.precision) ? 1e-7 : 1e-12) * first) break;
       used[best] = 1;
       std::vector<zc> qv(Lx);
       for (int i = 0; i < Lx; ++i) qv[i] = cols[best][i] / nrm;
@@ -852,7 +980,10 @@ void response_function(Ctx& c, cplx* out_host) {
       ph.mark(c, "combine");
       combine(c, rows(c, rd.basis[x], Lx), nb, W, yv);
       ph.mark(c, "hessian");
-      hessian_right(c, nb, yv, fb);
+      {
+        PrecisionScope hp(c, rd.refined ? CCLR_TC_BF16X6 : c.opt.precision);
+        hessian_right(c, nb, yv, fb);
+      }
       ph.mark(c, "gram");
       for (int y = 0; y < nop; ++y) {
         std::vector<zc> g;
@@ -899,6 +1030,7 @@ void response_function_ci(Ctx& c, cplx* out_host) {
   ResponseData& rd = c.rd;
   CCLR_REQUIRE(rd.solved, CCLR_E_STATE, "cc_response_function_ci before cc_lr_solve");
   CCLR_REQUIRE(c.have_lambda, CCLR_E_STATE, "cc_response_function_ci needs Lambda");
+  PrecisionScope exact(c, rd.refined ? CCLR_TC_F64 : c.opt.precision);
   Fast32 f32(c);
   const int64_t N = c.N;
   const int nop = rd.n_ops, maxL = std::max(8, c.opt.max_subspace);
@@ -1108,14 +1240,14 @@ int eom_ee(Ctx& c, int nroots, std::vector<zc>& w_out) {
       double mx = 0.0;
       for (int q = 0; q < nroots; ++q) {
         const double tol_q =
-            c.opt.precision == CCLR_FP64 ? c.opt.tol : std::max(c.opt.tol, 1e-5 * std::max(1.0, std::abs(theta[q])));
+            mixed_precision(c.opt.precision) ? std::max(c.opt.tol, 1e-5 * std::max(1.0, std::abs(theta[q]))) : c.opt.tol;
         if (rn[q] >= tol_q) open.push_back(q);
         mx = std::max(mx, rn[q] / tol_q);
       }
       if (verbose)
         std::fprintf(stderr, "[cclr] eom it %d L %d open %zu/%d max|r|/tol %.3e lowest %.10f\n", it, L, open.size(),
                      nroots, mx, theta[0].real());
-      if (!open.empty() && c.opt.precision != CCLR_FP64) {   // stagnation within 5x the floor
+      if (!open.empty() && mixed_precision(c.opt.precision)) {   // stagnation within 5x the floor
         if (mx < 0.8 * best) { best = mx; best_it = it; }
         if (it - best_it >= 4 && mx < 5.0) open.clear();
       }

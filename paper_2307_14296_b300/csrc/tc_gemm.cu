@@ -21,6 +21,7 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <algorithm>
+#include <cmath>
 #include <cstdlib>
 #include <map>
 
@@ -83,9 +84,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* b, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// bounded wait: ~2^22 polls with back-off (about a second); false on expiry
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
-  for (uint32_t i = 0; i < (1u << 22); ++i) {
+// bounded wait: ~2^22 polls with back-off (about a second) unless a limit is given; false on expiry
+constexpr uint32_t kWaitPolls = 1u << 22;
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, uint32_t polls = kWaitPolls) {
+  for (uint32_t i = 0; i < polls; ++i) {
     if (mbar_try_wait(b, parity)) return true;
     if (i > 64) __nanosleep(256);
   }
@@ -172,7 +174,8 @@ constexpr int TC_THREADS = 64 + EPI_THREADS;
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_tc_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int n_rows, int m_rows,
                int kblocks, int kb_per, Pairs pairs, double2 alpha, double2 beta, double2* __restrict__ C, int64_t ldc,
-               int64_t cz, int* __restrict__ err, int xtiles, int ytiles, int nsplit, const OutMap om, bool strided) {
+               int64_t cz, int* __restrict__ err, int xtiles, int ytiles, int nsplit, const OutMap om, bool strided,
+               uint32_t polls, int expire_first) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
@@ -221,7 +224,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         for (int it = 0; it < iters; ++it, ++g) {
           const int s = g % STAGES;
           const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
-          if (!mbar_wait(&empty[s], ph ^ 1u)) { atomicExch(err, 1); *abort_flag = 1; break; }
+          // expire_first (tests of the expiry path): the first wait is for a phase that nothing
+          // completes, so it runs out before any copy or MMA is issued
+          const uint32_t par = (g == 0 && expire_first) ? ph : (ph ^ 1u);
+          if (!mbar_wait(&empty[s], par, polls)) { atomicExch(err, 1); *abort_flag = 1; break; }
           if (*abort_flag) break;
           const int kb = kb0 + it / pairs.n, p = it % pairs.n;
           uint8_t* st = smem + s * STAGE_BYTES;
@@ -243,14 +249,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int kb0 = z * kb_per, kb1 = min(kblocks, kb0 + kb_per);
         const int iters = (kb1 - kb0) * pairs.n;
         const int b = tl & 1;
-        if (!mbar_wait(&tempty[b], (((uint32_t)tl >> 1) & 1u) ^ 1u)) { atomicExch(err, 4); *abort_flag = 1; break; }
+        if (!mbar_wait(&tempty[b], (((uint32_t)tl >> 1) & 1u) ^ 1u, polls)) { atomicExch(err, 4); *abort_flag = 1; break; }
         fence_after();
         const uint32_t cr = tmem + b * TMEM_COLS, ci = cr + BN;
         bool ok = true;
         for (int it = 0; it < iters; ++it, ++g) {
           const int s = g % STAGES;
           const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
-          if (!mbar_wait(&full[s], ph)) { atomicExch(err, 2); *abort_flag = 1; ok = false; break; }
+          if (!mbar_wait(&full[s], ph, polls)) { atomicExch(err, 2); *abort_flag = 1; ok = false; break; }
           fence_after();
           const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
           const uint32_t ar = base, ai = base + A_PLANE, br = base + 2 * A_PLANE, bi = br + B_PLANE;
@@ -301,7 +307,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       if (group_any(*abort_flag != 0)) break;   // also publishes this tile's offsets to the group
       const int n = n0 + lg * 32 + lane;
       const int64_t noff = (strided && n < n_rows) ? out_off((uint32_t)n, om.nn, om.ndim, om.nstr, om.nmul, om.nshr) : 0;
-      const bool ready = mbar_wait(&tfull[b], ((uint32_t)tl >> 1) & 1u);
+      const bool ready = mbar_wait(&tfull[b], ((uint32_t)tl >> 1) & 1u, polls);
       if (group_any(!ready)) {
         if (et == 0) atomicExch(err, 3);
         *abort_flag = 1;
@@ -355,8 +361,391 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   if (warp == 2) {
     fence_after();
     // the MMAs may still run if a role gave up early: wait (bounded) for all of them first
-    if (!mbar_wait(done, 0) && lane == 0) atomicExch(err, 5);
+    if (!mbar_wait(done, 0, polls) && lane == 0) atomicExch(err, 5);
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TMEM_COLS));
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// FP64-class mode (CCLR_TC_F64): the Ozaki splitting (Ozaki, Ogita, Oishi, Rump, "Error-free
+// transformations of matrix multiplication by using fast routines of matrix multiplication and
+// its applications", Numer. Algorithms 59, 2012) on BF16 tensor cores.  Every operand row r gets
+// the exponent e_r with |x| < 2^e_r for all its elements, and each element is written as five
+// signed base-256 digits on the row's grid:
+//     x = sum_{s<5} d_s 2^(e_r - 7 - 8 s) + O(2^(e_r - 40)),   |d_s| <= 128,
+// each digit stored exactly as a BF16 value.  A digit product d_i d_j (|.| <= 2^14) lies on the
+// grid 2^(e_m + e_n - 14 - 8(i + j)) of the output element, so the products of one "group"
+// (i + j = g) summed over a chunk of 256 k values stay exact in FP32 for g = 0 (2 real products
+// per k: <= 2^23) and g = 1 (4 per k: <= 2^24).  Group 2 (3 pairs, 2^-16 of the result) and
+// groups 3..4 (9 pairs, 2^-24) have accumulators of their own: the tensor cores align the
+// products of an MMA to the largest term and drop the bits below its window, so small products
+// must not share an accumulator with large ones.  Digit pairs with i + j >= 5 (below 2^-40) are
+// dropped.  Chunk sums are added into a float-float (hi, lo) running sum per output element, so
+// the result carries ~2^-40 relative to the product of the row maxima, like an FP64 GEMM whose
+// inputs were rounded to 40 bits.
+//
+// Kernel k_tc_zgemm_x: tile 128 (n, TMEM lanes) x 64 (m, TMEM columns), pair-major order inside
+// each 256-deep chunk, groups in order: each group's accumulator is drained by the epilogue while
+// the later groups of the chunk run, and the last group (9 pairs) while the next chunk's first
+// three groups run.  TMEM: g0 | g1 | g2 | g34, each Cr (64) | Ci (64) = 512 columns.
+// Warp 0: TMA producer; warp 1: MMA issuer; warps 2..17: epilogue (TMEM lane quarter warp % 4,
+// 16 columns each), keeping the float-float sums of their elements in a per-CTA global buffer
+// (L2-resident) between chunks and writing C (alpha, beta in FP64) after the last chunk.
+namespace x {
+constexpr int NS = 5;                             // digits (slices) per operand
+constexpr int BN = 64;                            // MMA N = m rows per tile
+constexpr int STAGES = 4;
+constexpr int A_PLANE = BM * BK * 2;              // 16 KB
+constexpr int B_PLANE = BN * BK * 2;              // 8 KB
+constexpr int STAGE_BYTES = 2 * A_PLANE + 2 * B_PLANE;
+constexpr int CK = 4;                             // k-blocks per chunk (256 K values)
+constexpr int EPI_WARPS = 16;
+constexpr int EPI_THREADS = 32 * EPI_WARPS;
+constexpr int THREADS = 64 + EPI_THREADS;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/ + BN * 8 /*row offsets*/;
+constexpr int TMEM_COLS = 512;
+constexpr int MAX_PAIRS = 15;
+constexpr int NG = 4;                             // accumulator groups
+}  // namespace x
+
+struct PairsX {
+  int n;
+  int sa[x::MAX_PAIRS], sb[x::MAX_PAIRS], grp[x::MAX_PAIRS];
+  int first[x::NG], last[x::NG];   // first / last pair index of each group (pairs sorted by group)
+};
+
+// OR of q over the epilogue threads of k_tc_zgemm_x (named barrier 1)
+__device__ __forceinline__ bool group_any_x(bool q) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 q, %1, 0;\n bar.red.or.pred p, 1, 512, q;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)q)
+      : "memory");
+  return r != 0;
+}
+static_assert(x::EPI_THREADS == 512, "group_any_x counts 512 epilogue threads");
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// s + e = a + b exactly (Knuth's TwoSum; round-to-nearest FP32)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float v = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, v)), __fsub_rn(b, v));
+}
+// (H, L) += (h, l), float-float addition with renormalisation
+__device__ __forceinline__ void ff_add(float& H, float& L, float h, float l) {
+  float s, e;
+  two_sum(H, h, s, e);
+  e = __fadd_rn(e, __fadd_rn(L, l));
+  H = __fadd_rn(s, e);
+  L = __fsub_rn(e, __fsub_rn(H, s));
+}
+
+__global__ void __launch_bounds__(x::THREADS, 1)
+    k_tc_zgemm_x(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int n_rows, int m_rows,
+                 int kblocks, int kb_per, PairsX pairs, double2 alpha, float alpha_pow2, double2 beta,
+                 double2* __restrict__ C, int64_t ldc, int64_t cz, int* __restrict__ err, int xtiles, int ytiles,
+                 int nsplit, const OutMap om, bool strided, float4* __restrict__ fstate) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(smem + x::STAGES * x::STAGE_BYTES);
+  uint64_t* empty = full + x::STAGES;
+  uint64_t* gfull = empty + x::STAGES;   // chunk sums of group g ready (MMA commit)
+  uint64_t* gempty = gfull + x::NG;      // the same accumulators drained (all epilogue threads)
+  uint64_t* done = gempty + x::NG;
+  uint32_t* tmem_slot = (uint32_t*)(done + 1);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+  int64_t* moff = (int64_t*)(smem + x::STAGES * x::STAGE_BYTES + 256);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < x::STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < x::NG; ++b) {
+      mbar_init(&gfull[b], 1);
+      mbar_init(&gempty[b], x::EPI_THREADS);
+    }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 2) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(x::TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int xy = xtiles * ytiles;
+  const int ntiles = xy * nsplit;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer: per chunk, the pairs in order, each over the chunk's k-blocks
+      int g = 0;
+      bool stop = false;
+      for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
+        const int z = t / xy, r = t - z * xy, y = r / xtiles, xx = r - y * xtiles;
+        const int kb0 = z * kb_per, kb1 = min(kblocks, kb0 + kb_per);
+        const int n0 = y * BM, m0 = xx * x::BN;
+        for (int c0 = kb0; c0 < kb1 && !stop; c0 += x::CK) {
+          const int c1 = min(kb1, c0 + x::CK);
+          for (int p = 0; p < pairs.n && !stop; ++p)
+            for (int kb = c0; kb < c1; ++kb, ++g) {
+              const int s = g % x::STAGES;
+              const uint32_t ph = (uint32_t)(g / x::STAGES) & 1u;
+              if (!mbar_wait(&empty[s], ph ^ 1u)) { atomicExch(err, 11); *abort_flag = 1; stop = true; break; }
+              if (*abort_flag) { stop = true; break; }
+              uint8_t* st = smem + s * x::STAGE_BYTES;
+              mbar_expect_tx(&full[s], x::STAGE_BYTES);
+              tma_load_3d(st, &tmA, kb * BK, n0, 2 * pairs.sa[p] + 0, &full[s]);
+              tma_load_3d(st + x::A_PLANE, &tmA, kb * BK, n0, 2 * pairs.sa[p] + 1, &full[s]);
+              tma_load_3d(st + 2 * x::A_PLANE, &tmB, kb * BK, m0, 2 * pairs.sb[p] + 0, &full[s]);
+              tma_load_3d(st + 2 * x::A_PLANE + x::B_PLANE, &tmB, kb * BK, m0, 2 * pairs.sb[p] + 1, &full[s]);
+            }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer (single thread)
+      constexpr uint32_t ID = idesc_bf16(BM, x::BN, false), IDN = idesc_bf16(BM, x::BN, true);
+      int g = 0, cc = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok && !*abort_flag; t += gridDim.x) {
+        const int z = t / xy;
+        const int kb0 = z * kb_per, kb1 = min(kblocks, kb0 + kb_per);
+        for (int c0 = kb0; c0 < kb1 && ok; c0 += x::CK, ++cc) {
+          const int c1 = min(kb1, c0 + x::CK);
+          for (int p = 0; p < pairs.n && ok; ++p) {
+            const int grp = pairs.grp[p];
+            const int slot = grp;   // accumulator of this pair
+            if (p == pairs.first[grp]) {
+              // the accumulator of this group must have been drained (previous chunk)
+              if (!mbar_wait(&gempty[slot], ((uint32_t)cc & 1u) ^ 1u)) { atomicExch(err, 14); *abort_flag = 1; ok = false; break; }
+              fence_after();
+            }
+            const uint32_t cr = tmem + (uint32_t)slot * 2 * x::BN, ci = cr + x::BN;
+            for (int kb = c0; kb < c1; ++kb, ++g) {
+              const int s = g % x::STAGES;
+              const uint32_t ph = (uint32_t)(g / x::STAGES) & 1u;
+              if (!mbar_wait(&full[s], ph)) { atomicExch(err, 12); *abort_flag = 1; ok = false; break; }
+              fence_after();
+              const uint32_t base = smem_u32(smem + s * x::STAGE_BYTES);
+              const uint32_t ar = base, ai = base + x::A_PLANE, br = base + 2 * x::A_PLANE, bi = br + x::B_PLANE;
+#pragma unroll
+              for (int ks = 0; ks < BK / 16; ++ks) {
+                const uint32_t off = ks * 32;
+                const uint64_t dar = desc_sw128(ar + off), dai = desc_sw128(ai + off);
+                const uint64_t dbr = desc_sw128(br + off), dbi = desc_sw128(bi + off);
+                const uint32_t first = (kb == c0 && ks == 0 && p == pairs.first[grp]) ? 0u : 1u;
+                mma_bf16(cr, dar, dbr, ID, first);
+                mma_bf16(cr, dai, dbi, IDN, 1u);
+                mma_bf16(ci, dar, dbi, ID, first);
+                mma_bf16(ci, dai, dbr, ID, 1u);
+              }
+              mma_commit(&empty[s]);
+            }
+            if (ok && p == pairs.last[grp]) mma_commit(&gfull[slot]);
+          }
+        }
+      }
+      mma_commit(done);
+    }
+  } else {
+    // ---------------- epilogue warps 2..17: TMEM lane quarter warp % 4, columns 16 ch .. 16 ch + 15
+    const int et = threadIdx.x - 64;
+    const int lg = warp & 3;
+    const int ch = (warp - 2) >> 2;
+    const int row = lg * 32 + lane;                       // TMEM lane = n - n0
+    const uint32_t lane_base = (uint32_t)(lg * 32) << 16;
+    const bool use_beta = (beta.x != 0.0 || beta.y != 0.0);
+    const bool beta_one = (beta.x == 1.0 && beta.y == 0.0);
+    float4* st = fstate + (size_t)blockIdx.x * BM * x::BN;   // [col][row] float-float sums (re hi, re lo, im hi, im lo)
+    int cc = 0;
+    bool stop = false;
+    for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
+      const int z = t / xy, r = t - z * xy, y = r / xtiles, xx = r - y * xtiles;
+      const int kb0 = z * kb_per, kb1 = min(kblocks, kb0 + kb_per);
+      const int n0 = y * BM, m0 = xx * x::BN;
+      const int nch = (kb1 - kb0 + x::CK - 1) / x::CK;
+      double2* Cz = C + (int64_t)z * cz;
+      if (group_any_x(false)) break;   // the previous tile's row offsets are no longer read
+      if (strided && et < x::BN) {
+        const int m = m0 + et;
+        moff[et] = m < m_rows ? out_off((uint32_t)m, om.nm, om.mdim, om.mstr, om.mmul, om.mshr) : 0;
+      }
+      if (group_any_x(*abort_flag != 0)) break;   // also publishes this tile's offsets
+      const int n = n0 + row;
+      const int64_t noff = (strided && n < n_rows) ? out_off((uint32_t)n, om.nn, om.ndim, om.nstr, om.nmul, om.nshr) : 0;
+      for (int ci = 0; ci < nch; ++ci, ++cc) {
+        const uint32_t cpar = (uint32_t)cc & 1u;
+        // group 0 (exact chunk sum)
+        bool ready = mbar_wait(&gfull[0], cpar);
+        if (group_any_x(!ready)) { if (et == 0) atomicExch(err, 13); *abort_flag = 1; stop = true; break; }
+        fence_after();
+        uint32_t a_re[16], a_im[16], b_re[16], b_im[16];
+        tmem_ld16(tmem + lane_base + 16 * ch, a_re);
+        tmem_ld16(tmem + lane_base + x::BN + 16 * ch, a_im);
+        fence_before();
+        mbar_arrive(&gempty[0]);
+        // group 1 (exact chunk sum)
+        ready = mbar_wait(&gfull[1], cpar);
+        if (group_any_x(!ready)) { if (et == 0) atomicExch(err, 13); *abort_flag = 1; stop = true; break; }
+        fence_after();
+        tmem_ld16(tmem + lane_base + 2 * x::BN + 16 * ch, b_re);
+        tmem_ld16(tmem + lane_base + 3 * x::BN + 16 * ch, b_im);
+        fence_before();
+        mbar_arrive(&gempty[1]);
+        float hr[16], lr[16], hi[16], li[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          two_sum(__uint_as_float(a_re[j]), __uint_as_float(b_re[j]), hr[j], lr[j]);
+          two_sum(__uint_as_float(a_im[j]), __uint_as_float(b_im[j]), hi[j], li[j]);
+        }
+        // groups 2 and 3..4 (FP32 sums, 2^-16 and 2^-24 of the result) in 8-column halves
+        for (int gq = 2; gq < x::NG; ++gq) {
+          ready = mbar_wait(&gfull[gq], cpar);
+          if (group_any_x(!ready)) { if (et == 0) atomicExch(err, 13); *abort_flag = 1; stop = true; break; }
+          fence_after();
+          const uint32_t gbase = tmem + lane_base + (uint32_t)gq * 2 * x::BN + 16 * ch;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            uint32_t q_re[8], q_im[8];
+            tmem_ld8(gbase + 8 * h, q_re);
+            tmem_ld8(gbase + x::BN + 8 * h, q_im);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              lr[8 * h + j] = __fadd_rn(lr[8 * h + j], __uint_as_float(q_re[j]));
+              li[8 * h + j] = __fadd_rn(li[8 * h + j], __uint_as_float(q_im[j]));
+            }
+          }
+          fence_before();
+          mbar_arrive(&gempty[gq]);
+        }
+        if (stop) break;
+        // running float-float sums
+        const bool firstc = ci == 0, lastc = ci == nch - 1;
+#pragma unroll 4
+        for (int j = 0; j < 16; ++j) {
+          const int col = 16 * ch + j;
+          float Hr = hr[j], Lr = lr[j], Hi = hi[j], Li = li[j];
+          if (firstc) {
+            const float sr = __fadd_rn(Hr, Lr), si = __fadd_rn(Hi, Li);   // renormalise
+            Lr = __fsub_rn(Lr, __fsub_rn(sr, Hr));
+            Li = __fsub_rn(Li, __fsub_rn(si, Hi));
+            Hr = sr;
+            Hi = si;
+          } else {
+            const float4 s = st[(size_t)col * BM + row];
+            float Sr = s.x, Sl = s.y, Ti = s.z, Tl = s.w;
+            ff_add(Sr, Sl, Hr, Lr);
+            ff_add(Ti, Tl, Hi, Li);
+            Hr = Sr; Lr = Sl; Hi = Ti; Li = Tl;
+          }
+          if (!lastc) {
+            st[(size_t)col * BM + row] = make_float4(Hr, Lr, Hi, Li);
+          } else {
+            const int m = m0 + col;
+            if (n < n_rows && m < m_rows) {
+              double2 v;
+              if (alpha_pow2 != 0.0f) {   // real power-of-two alpha: exact FP32 scaling
+                v = make_double2(epi_f2d(Hr * alpha_pow2) + epi_f2d(Lr * alpha_pow2),
+                                 epi_f2d(Hi * alpha_pow2) + epi_f2d(Li * alpha_pow2));
+              } else {
+                const double cr_ = epi_f2d(Hr) + epi_f2d(Lr), ci_ = epi_f2d(Hi) + epi_f2d(Li);
+                v = make_double2(alpha.x * cr_ - alpha.y * ci_, alpha.x * ci_ + alpha.y * cr_);
+              }
+              double2* dst = strided ? Cz + moff[col] + noff : Cz + (int64_t)m * ldc + n;
+              if (use_beta) {
+                const double2 o = *dst;
+                if (beta_one) {
+                  v.x += o.x;
+                  v.y += o.y;
+                } else {
+                  v.x += beta.x * o.x - beta.y * o.y;
+                  v.y += beta.x * o.y + beta.y * o.x;
+                }
+              }
+              *dst = v;
+            }
+          }
+        }
+      }
+    }
+  }
+  __syncwarp();
+  fence_before();
+  __syncthreads();
+  if (warp == 2) {
+    fence_after();
+    if (!mbar_wait(done, 0) && lane == 0) atomicExch(err, 15);
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(x::TMEM_COLS));
+  }
+}
+
+// Largest biased binary64 exponent of |re| and |im| over each operand row (the row exponent of
+// the fixed-point digits is that value - 1022, so that |x| < 2^e).  rexp is zeroed beforehand.
+__device__ __forceinline__ uint32_t bexp64(double v) { return (uint32_t)((uint64_t)__double_as_longlong(v) >> 52) & 0x7ffu; }
+
+// Signed base-256 digits of x on the grid of a row whose largest biased exponent is eb_row:
+// x = sum_s d_s 2^(eb_row - 1029 - 8 s) (rounded at the last digit), |d_s| <= 128, integer pipe
+// only.  Subnormal x counts as 0.
+__device__ __forceinline__ void ozaki_digits(double v, uint32_t eb_row, int (&d)[x::NS]) {
+  const uint64_t b = (uint64_t)__double_as_longlong(v);
+  const uint32_t eb = (uint32_t)(b >> 52) & 0x7ffu;
+  int64_t X = 0;
+  if (eb != 0u) {
+    const uint64_t M = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const int rs = (int)eb_row - (int)eb + 14;   // >= 14: x / 2^(e - 39) = M 2^-rs
+    if (rs < 64) X = (int64_t)((M + (1ull << (rs - 1))) >> rs);
+    if (b >> 63) X = -X;
+  }
+  d[0] = (int)((X + (1ll << 31)) >> 32); X -= (int64_t)d[0] << 32;
+  d[1] = (int)((X + (1ll << 23)) >> 24); X -= (int64_t)d[1] << 24;
+  d[2] = (int)((X + (1ll << 15)) >> 16); X -= (int64_t)d[2] << 16;
+  d[3] = (int)((X + (1ll << 7)) >> 8);   X -= (int64_t)d[3] << 8;
+  d[4] = (int)X;
+}
+// BF16 bits of d 2^p (|d| <= 256, exact); values below the BF16 normal range flush to zero
+__device__ __forceinline__ uint32_t bf16_digit(int d, int p) {
+  if (d == 0) return 0u;
+  const uint32_t a = (uint32_t)(d < 0 ? -d : d);
+  const int msb = 31 - __clz(a);
+  const int be = msb + p + 127;
+  if (be <= 0) return 0u;
+  const uint32_t sign = d < 0 ? 0x8000u : 0u;
+  if (be >= 255) return sign | 0x7f80u;   // beyond the binary32 range: infinity
+  const uint32_t frac = (a << (7 - msb)) & 0x7fu;
+  return sign | ((uint32_t)be << 7) | frac;
+}
+// the digit planes of one element pair (k, k+1) of a row: out32[plane] = bf16(k) | bf16(k+1) << 16
+__device__ __forceinline__ void ozaki_pair(const double2 (&xv)[2], uint32_t eb_row, uint32_t (&out)[2 * x::NS]) {
+  if (eb_row == 0x7ffu) {   // infinity or NaN in the row: propagate NaN
+#pragma unroll
+    for (int q = 0; q < 2 * x::NS; ++q) out[q] = 0x7fc07fc0u;
+    return;
+  }
+  int dr[2][x::NS], di[2][x::NS];
+  ozaki_digits(xv[0].x, eb_row, dr[0]);
+  ozaki_digits(xv[0].y, eb_row, di[0]);
+  ozaki_digits(xv[1].x, eb_row, dr[1]);
+  ozaki_digits(xv[1].y, eb_row, di[1]);
+#pragma unroll
+  for (int s = 0; s < x::NS; ++s) {
+    const int p = (int)eb_row - 1029 - 8 * s;
+    out[2 * s + 0] = bf16_digit(dr[0][s], p) | (bf16_digit(dr[1][s], p) << 16);
+    out[2 * s + 1] = bf16_digit(di[0][s], p) | (bf16_digit(di[1][s], p) << 16);
   }
 }
 
@@ -409,9 +798,11 @@ __device__ __forceinline__ uint32_t bf16_bits(float f) {
 // pairs of consecutive K elements and stores them as packed bf16x2.  x is rounded to FP32
 // (24 bits) and cut into slices s_0 + s_1 + s_2 in FP32 arithmetic (each difference is exact).
 constexpr int kSplitPairs = 64;
+// With rexp (the FP64-class mode) each pair is written as the row's five fixed-point digits instead.
 __global__ void __launch_bounds__(256) k_split_view(const double2* __restrict__ X, ViewArgs v, int64_t rows, int64_t K,
                                                     bool conj, int nsl, __nv_bfloat16* __restrict__ out, int64_t Kpad,
-                                                    uint32_t nchunk, uint32_t chunk_mul, int chunk_shr) {
+                                                    uint32_t nchunk, uint32_t chunk_mul, int chunk_shr,
+                                                    const uint32_t* __restrict__ rexp) {
   const int64_t plane = rows * Kpad;
   const int lane = threadIdx.x & 31;
   const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -428,6 +819,22 @@ __global__ void __launch_bounds__(256) k_split_view(const double2* __restrict__ 
     for (int h = 0; h < kSplitPairs / 32; ++h) {
       const int64_t p = (int64_t)c * kSplitPairs + h * 32 + lane;
       if (p >= pairs) break;
+      const int64_t e2 = (int64_t)r * (Kpad / 2) + p;   // index of the bf16 pair within a plane
+      if (rexp) {
+        double2 xv[2];
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+          const int64_t k = 2 * p + t;
+          xv[t] = make_double2(0.0, 0.0);
+          if (k < K) xv[t] = X[roff + view_off(v, v.nr, v.rank, (uint32_t)k)];
+          if (conj) xv[t].y = -xv[t].y;
+        }
+        uint32_t o[2 * x::NS];
+        ozaki_pair(xv, rexp[r], o);
+#pragma unroll
+        for (int q = 0; q < 2 * x::NS; ++q) o32[(q * plane) / 2 + e2] = o[q];
+        continue;
+      }
       float re[2], im[2];
 #pragma unroll
       for (int t = 0; t < 2; ++t) {
@@ -437,7 +844,6 @@ __global__ void __launch_bounds__(256) k_split_view(const double2* __restrict__ 
         re[t] = split_d2f(x.x);
         im[t] = split_d2f(conj ? -x.y : x.y);
       }
-      const int64_t e2 = (int64_t)r * (Kpad / 2) + p;   // index of the bf16 pair within a plane
 #pragma unroll
       for (int s = 0; s < 3; ++s) {
         if (s >= nsl) break;
@@ -471,7 +877,8 @@ struct SplitT {
 
 __global__ void __launch_bounds__(256) k_split_view_t(const double2* __restrict__ X, ViewArgs v, SplitT s,
                                                       int64_t rows, int64_t K, bool conj, int nsl,
-                                                      __nv_bfloat16* __restrict__ out, int64_t Kpad, int64_t ntiles) {
+                                                      __nv_bfloat16* __restrict__ out, int64_t Kpad, int64_t ntiles,
+                                                      const uint32_t* __restrict__ rexp) {
   __shared__ double2 tile[64][33];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t plane = rows * Kpad;
@@ -507,6 +914,16 @@ __global__ void __launch_bounds__(256) k_split_view_t(const double2* __restrict_
     for (int j = warp; j < 32; j += 8) {
       if (u0 + j >= dimU) continue;
       const int64_t row = rbase + (u0 + j) * s.rstride[s.u];
+      if (rexp) {
+        double2 xv[2] = {tile[2 * lane][j], tile[2 * lane + 1][j]};
+        if (conj) { xv[0].y = -xv[0].y; xv[1].y = -xv[1].y; }
+        uint32_t o[2 * x::NS];
+        ozaki_pair(xv, rexp[row], o);
+        const int64_t e2 = row * (Kpad / 2) + (k0 / 2) + lane;
+#pragma unroll
+        for (int q = 0; q < 2 * x::NS; ++q) o32[(q * plane) / 2 + e2] = o[q];
+        continue;
+      }
       float re[2], im[2];
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
@@ -530,6 +947,76 @@ __global__ void __launch_bounds__(256) k_split_view_t(const double2* __restrict_
         o32[((2 * sl + 1) * plane) / 2 + e2] = bi[0] | (bi[1] << 16);
       }
     }
+    __syncthreads();
+  }
+}
+
+// Row exponents of the FP64-class digits: rexp[r] = largest biased binary64 exponent of |re| and
+// |im| over row r of the view (rexp zeroed beforehand; atomicMax per warp).  Same work items as
+// k_split_view.
+__global__ void __launch_bounds__(256) k_rowexp(const double2* __restrict__ X, ViewArgs v, int64_t rows, int64_t K,
+                                                uint32_t nchunk, uint32_t chunk_mul, int chunk_shr,
+                                                uint32_t* __restrict__ rexp) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t items = rows * (int64_t)nchunk;
+  for (int64_t w = warp0; w < items; w += nwarps) {
+    const uint32_t wi = (uint32_t)w;
+    const uint32_t r = (uint32_t)(((uint64_t)__umulhi(wi, chunk_mul) + wi) >> chunk_shr);
+    const uint32_t c = wi - r * nchunk;
+    const int64_t roff = view_off(v, 0, v.nr, r);
+    uint32_t m = 0;
+    for (int h = 0; h < 2 * kSplitPairs / 32; ++h) {
+      const int64_t k = (int64_t)c * 2 * kSplitPairs + h * 32 + lane;
+      if (k < K) {
+        const double2 xv = X[roff + view_off(v, v.nr, v.rank, (uint32_t)k)];
+        m = max(m, max(bexp64(xv.x), bexp64(xv.y)));
+      }
+    }
+    m = __reduce_max_sync(0xffffffffu, m);
+    if (lane == 0 && m) atomicMax(&rexp[r], m);
+  }
+}
+
+// Row exponents for the transposing split's views (same tiles as k_split_view_t).
+__global__ void __launch_bounds__(256) k_rowexp_t(const double2* __restrict__ X, ViewArgs v, SplitT s, int64_t K,
+                                                  int64_t ntiles, uint32_t* __restrict__ rexp) {
+  __shared__ uint32_t red[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t dimU = v.dim[s.u];
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    uint32_t r = (uint32_t)t;
+    const uint32_t q1 = (uint32_t)(((uint64_t)__umulhi(r, s.mul_ck) + r) >> s.shr_ck);
+    const uint32_t ck = r - q1 * s.n_ck;
+    const uint32_t q2 = (uint32_t)(((uint64_t)__umulhi(q1, s.mul_cu) + q1) >> s.shr_cu);
+    const uint32_t cu = q1 - q2 * s.n_cu;
+    uint32_t o = q2;
+    int64_t soff = 0, rbase = 0;
+#pragma unroll
+    for (int a = kMaxRank - 1; a >= 0; --a) {
+      if (a >= v.nr || a == s.u) continue;
+      const uint32_t q = (uint32_t)(((uint64_t)__umulhi(o, v.mul[a]) + o) >> v.shr[a]);
+      const int64_t idx = (int64_t)(o - q * (uint32_t)v.dim[a]);
+      soff += idx * v.str[a];
+      rbase += idx * s.rstride[a];
+      o = q;
+    }
+    const int64_t u0 = (int64_t)cu * 32, k0 = (int64_t)ck * 64;
+    if (threadIdx.x < 32) red[threadIdx.x] = 0;
+    __syncthreads();
+    uint32_t m = 0;
+    for (int kk = warp; kk < 64; kk += 8) {
+      const int64_t k = k0 + kk;
+      if (k < K && u0 + lane < dimU) {
+        const double2 xv = X[soff + (u0 + lane) + view_off(v, v.nr, v.rank, (uint32_t)k)];
+        m = max(m, max(bexp64(xv.x), bexp64(xv.y)));
+      }
+    }
+    if (m) atomicMax(&red[lane], m);
+    __syncthreads();
+    if (threadIdx.x < 32 && u0 + threadIdx.x < dimU && red[threadIdx.x])
+      atomicMax(&rexp[rbase + (u0 + threadIdx.x) * s.rstride[s.u]], red[threadIdx.x]);
     __syncthreads();
   }
 }
@@ -627,10 +1114,14 @@ tc::ViewArgs view_args(const Tensor& v, int nr) {
   return a;
 }
 
+// rexp != nullptr: the FP64-class digits (nsl = 5); rexp holds `rows` words of scratch on the stream's device
 void launch_split(const Tensor& v, int nr, int64_t rows, int64_t K, int64_t Kpad, int nsl, __nv_bfloat16* dst,
-                  cudaStream_t stream) {
+                  cudaStream_t stream, uint32_t* rexp = nullptr) {
   CCLR_REQUIRE(rows < (int64_t(1) << 31) && K < (int64_t(1) << 31), CCLR_E_ARG, "tensor-core split: operand too large");
+  CCLR_REQUIRE(!rexp || nsl == tc::x::NS, CCLR_E_ARG, "tensor-core split: digit count");
   const tc::ViewArgs a = view_args(v, nr);
+  const int sms = num_sms();
+  if (rexp) CCLR_CK(cudaMemsetAsync(rexp, 0, sizeof(uint32_t) * (size_t)rows, stream));
   // transposing variant: a row axis has unit stride while the innermost K axis does not
   int u = -1;
   for (int i = 0; i < a.nr; ++i)
@@ -657,8 +1148,9 @@ void launch_split(const Tensor& v, int nr, int64_t rows, int64_t K, int64_t Kpad
     st.n_ck = (uint32_t)n_ck;
     magic(n_cu, st.mul_cu, st.shr_cu);
     magic(n_ck, st.mul_ck, st.shr_ck);
-    const int g = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, 148 * 8));
-    tc::k_split_view_t<<<g, 256, 0, stream>>>(v.p, a, st, rows, K, v.conj, nsl, dst, Kpad, ntiles);
+    const int g = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)sms * 8));
+    if (rexp) tc::k_rowexp_t<<<g, 256, 0, stream>>>(v.p, a, st, K, ntiles, rexp);
+    tc::k_split_view_t<<<g, 256, 0, stream>>>(v.p, a, st, rows, K, v.conj, nsl, dst, Kpad, ntiles, rexp);
     return;
   }
   const int64_t nchunk = (Kpad / 2 + tc::kSplitPairs - 1) / tc::kSplitPairs;
@@ -666,8 +1158,9 @@ void launch_split(const Tensor& v, int nr, int64_t rows, int64_t K, int64_t Kpad
   int l = 0;
   while ((int64_t(1) << l) < nchunk) ++l;
   const uint32_t mul = (uint32_t)(((unsigned __int128)1 << 32) * (((uint64_t)1 << l) - (uint64_t)nchunk) / (uint64_t)nchunk + 1);
-  const int g = (int)std::max<int64_t>(1, std::min<int64_t>((rows * nchunk + 7) / 8, 148 * 16));
-  tc::k_split_view<<<g, 256, 0, stream>>>(v.p, a, rows, K, v.conj, nsl, dst, Kpad, (uint32_t)nchunk, mul, l);
+  const int g = (int)std::max<int64_t>(1, std::min<int64_t>((rows * nchunk + 7) / 8, (int64_t)sms * 16));
+  if (rexp) tc::k_rowexp<<<g, 256, 0, stream>>>(v.p, a, rows, K, (uint32_t)nchunk, mul, l, rexp);
+  tc::k_split_view<<<g, 256, 0, stream>>>(v.p, a, rows, K, v.conj, nsl, dst, Kpad, (uint32_t)nchunk, mul, l, rexp);
 }
 
 void make_slices(Ctx& c, const Tensor& v, int nr, int nsl, Slices& s, __nv_bfloat16* dst) {
@@ -678,11 +1171,13 @@ void make_slices(Ctx& c, const Tensor& v, int nr, int nsl, Slices& s, __nv_bfloa
   s.Kpad = (K + tc::BK - 1) / tc::BK * tc::BK;
   s.nsl = nsl;
   s.p = dst;
+  Scope sc(c.ws);
+  uint32_t* rexp = nsl == tc::x::NS ? (uint32_t*)c.ws.alloc(sizeof(uint32_t) * (size_t)rows) : nullptr;
   c.kt.begin(c.stream);
-  launch_split(v, nr, rows, K, s.Kpad, nsl, dst, c.stream);
+  launch_split(v, nr, rows, K, s.Kpad, nsl, dst, c.stream, rexp);
   CCLR_CK(cudaGetLastError());
-  c.kt.end(c.stream, "k_split_view");
-  ++c.launches;
+  c.kt.end(c.stream, rexp ? "k_split_view(f64 digits)" : "k_split_view");
+  c.launches += rexp ? 2 : 1;
   s.tm = make_map(dst, rows, s.Kpad, 2 * nsl, 128);
 }
 
@@ -813,6 +1308,28 @@ SliceMemo::~SliceMemo() {
 
 namespace {
 
+// Digit pairs (i, j) with i + j < 5 sorted by group: group i + j for i + j < 3, group 3 otherwise
+tc::PairsX pairs_x() {
+  tc::PairsX p{};
+  p.n = 0;
+  for (int g = 0; g < tc::x::NS; ++g)
+    for (int i = 0; i <= g; ++i) {
+      p.sa[p.n] = i;
+      p.sb[p.n] = g - i;
+      p.grp[p.n] = std::min(g, tc::x::NG - 1);
+      ++p.n;
+    }
+  for (int q = 0; q < tc::x::NG; ++q) {
+    p.first[q] = -1;
+    p.last[q] = -1;
+  }
+  for (int k = 0; k < p.n; ++k) {
+    if (p.first[p.grp[k]] < 0) p.first[p.grp[k]] = k;
+    p.last[p.grp[k]] = k;
+  }
+  return p;
+}
+
 tc::Pairs pairs_for(int nsl) {
   tc::Pairs pairs{};
   if (nsl == 2) {
@@ -847,7 +1364,9 @@ size_t tc_cache_bytes() {
   return t;
 }
 
-int tc_slices(int precision) { return precision == CCLR_TC_BF16X3 ? 2 : 3; }
+int tc_slices(int precision) {
+  return precision == CCLR_TC_BF16X3 ? 2 : precision == CCLR_TC_F64 ? tc::x::NS : 3;
+}
 
 bool tc_eligible(int64_t M, int64_t N, int64_t K) {
   // below ~2^18 complex multiply-adds the FP64 kernel is as fast as a tensor-core launch (a few
@@ -861,20 +1380,22 @@ bool tc_eligible(int64_t M, int64_t N, int64_t K) {
 // rows (m resp. n) and whose remaining axes are K (same order in both).
 // split-K slices for an output of M x N with K (1 = none): when the output has fewer tiles than
 // SMs, each slice >= 4 k-blocks
-void tc_split_plan(int64_t M, int64_t N, int64_t K, int& S, int& kb_per) {
+// (bn: the m-rows of a tile, tc::BN or tc::x::BN)
+void tc_split_plan(int64_t M, int64_t N, int64_t K, int& S, int& kb_per, int bn = tc::BN) {
   const int kblocks = (int)((K + tc::BK - 1) / tc::BK);
-  const int64_t tiles = ((M + tc::BN - 1) / tc::BN) * ((N + tc::BM - 1) / tc::BM);
+  const int64_t tiles = ((M + bn - 1) / bn) * ((N + tc::BM - 1) / tc::BM);
+  const int sms = num_sms();
   S = 1;
   kb_per = kblocks;
-  if (tiles < 148 && kblocks >= 8) {
-    S = (int)std::min<int64_t>((148 + tiles - 1) / tiles, kblocks / 4);
+  if (tiles < sms && kblocks >= 8) {
+    S = (int)std::min<int64_t>((sms + tiles - 1) / tiles, kblocks / 4);
     kb_per = (kblocks + S - 1) / S;
     S = (kblocks + kb_per - 1) / kb_per;   // no empty slice
   }
 }
-int tc_splits(int64_t M, int64_t N, int64_t K) {
+int tc_splits(int64_t M, int64_t N, int64_t K, int precision) {
   int S, kb;
-  tc_split_plan(M, N, K, S, kb);
+  tc_split_plan(M, N, K, S, kb, precision == CCLR_TC_F64 ? tc::x::BN : tc::BN);
   return S;
 }
 
@@ -901,24 +1422,79 @@ tc::OutMap out_map(const OutAxes& a) {
 }
 }  // namespace
 
+// FP64-class GEMM (CCLR_TC_F64) on the digit slices sn (n rows) and sm (m rows): k_tc_zgemm_x.
+void tc_gemm_x(Ctx& c, const Slices& sn, const Slices& sm, cplx alpha, cplx beta, cplx* C, int64_t ldc,
+               const OutAxes* oa) {
+  const int64_t M = sm.rows, N = sn.rows;
+  static bool attr[64] = {};
+  if (once_per_device(attr))
+    CCLR_CK(cudaFuncSetAttribute(tc::k_tc_zgemm_x, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::x::SMEM_BYTES));
+  const int kblocks = (int)(sn.Kpad / tc::BK);
+  int S = 1, kb_per = kblocks;
+  tc_split_plan(M, N, sn.Kpad, S, kb_per, tc::x::BN);
+  CCLR_REQUIRE(!oa || S == 1, CCLR_E_ARG, "tc_gemm: strided output with split-K");
+  const tc::OutMap om = oa ? out_map(*oa) : tc::OutMap();
+  cplx* P = S > 1 ? c.ws.cplxs((int64_t)S * M * N) : nullptr;
+  const int64_t ytiles = (N + tc::BM - 1) / tc::BM, xtiles = (M + tc::x::BN - 1) / tc::x::BN;
+  CCLR_REQUIRE(xtiles * ytiles * S < (int64_t)INT32_MAX, CCLR_E_ARG, "tc_gemm: too many tiles");
+  const int grid = (int)std::min<int64_t>(xtiles * ytiles * S, num_sms());
+  float4* fstate = (float4*)c.ws.alloc(sizeof(float4) * (size_t)grid * tc::BM * tc::x::BN);
+  // the B-side map with the 64-row box of this kernel (the cached map has 128-row boxes)
+  const CUtensorMap tmB = make_map(sm.p, sm.rows, sm.Kpad, 2 * sm.nsl, tc::x::BN);
+  const tc::PairsX pairs = pairs_x();
+  // a real power-of-two alpha is applied exactly to the float-float sums (no FP64 multiply)
+  float apow2 = 0.0f;
+  if (S == 1 && alpha.y == 0.0 && alpha.x != 0.0) {
+    int e = 0;
+    const double f = std::frexp(std::fabs(alpha.x), &e);
+    if (f == 0.5 && e > -100 && e < 100) apow2 = (float)alpha.x;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (c.prof) c.prof_events(e0, e1, 1);
+  if (e0) CCLR_CK(cudaEventRecord(e0, c.stream));
+  c.kt.begin(c.stream);
+  if (S > 1)
+    tc::k_tc_zgemm_x<<<grid, tc::x::THREADS, tc::x::SMEM_BYTES, c.stream>>>(
+        sn.tm, tmB, (int)N, (int)M, kblocks, kb_per, pairs, make_double2(1.0, 0.0), 1.0f, make_double2(0.0, 0.0), P, N,
+        M * N, c.tc_err, (int)xtiles, (int)ytiles, S, om, false, fstate);
+  else
+    tc::k_tc_zgemm_x<<<grid, tc::x::THREADS, tc::x::SMEM_BYTES, c.stream>>>(
+        sn.tm, tmB, (int)N, (int)M, kblocks, kb_per, pairs, alpha, apow2, beta, C, ldc, 0, c.tc_err, (int)xtiles,
+        (int)ytiles, 1, om, oa != nullptr, fstate);
+  const cudaError_t le = cudaGetLastError();
+  CCLR_REQUIRE(le == cudaSuccess, CCLR_E_CUDA,
+               std::string("FP64-class tensor-core GEMM launch failed (") + cudaGetErrorString(le) + ") M=" +
+                   std::to_string(M) + " N=" + std::to_string(N) + " K=" + std::to_string(sn.K));
+  c.kt.end(c.stream, "k_tc_zgemm_x");
+  if (e1) {
+    CCLR_CK(cudaEventRecord(e1, c.stream));
+    c.prof_flops_exec[1] += 8.0 * (double)M * N * sn.K * pairs.n;
+    c.prof_flops_useful[1] += 8.0 * (double)M * N * sn.K;
+  }
+  ++c.launches;
+  if (S > 1) splitk_reduce(c.L, P, S, M, N, alpha, beta, C, ldc);
+}
+
 void tc_gemm_views(Ctx& c, const Tensor& vm, int nrm, const Tensor& vn, int nrn, cplx alpha, cplx beta, cplx* C,
                    int64_t ldc, const OutAxes* oa) {
   const int nsl = tc_slices(c.opt.precision);
-  const tc::Pairs pairs = pairs_for(nsl);
   Scope sc(c.ws);
   const Slices sn = get_slices(c, vn, nrn, nsl);   // MMA A-side: rows = n (TMEM lanes)
   const Slices sm = get_slices(c, vm, nrm, nsl);   // MMA B-side: rows = m
   CCLR_REQUIRE(sn.K == sm.K, CCLR_E_ARG, "tc_gemm: K mismatch");
-  const int64_t M = sm.rows, N = sn.rows;
-  static bool attr = false;
-  if (!attr) {
-    CCLR_CK(cudaFuncSetAttribute(tc::k_tc_zgemm, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES));
-    attr = true;
-  }
   if (!c.tc_err) {  // device status word, checked by the API layer at the end of every call
     CCLR_CK(cudaMalloc((void**)&c.tc_err, sizeof(int)));
     CCLR_CK(cudaMemsetAsync(c.tc_err, 0, sizeof(int), c.stream));
   }
+  if (c.opt.precision == CCLR_TC_F64) {
+    tc_gemm_x(c, sn, sm, alpha, beta, C, ldc, oa);
+    return;
+  }
+  const tc::Pairs pairs = pairs_for(nsl);
+  const int64_t M = sm.rows, N = sn.rows;
+  static bool attr[64] = {};
+  if (once_per_device(attr))
+    CCLR_CK(cudaFuncSetAttribute(tc::k_tc_zgemm, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES));
   const int kblocks = (int)(sn.Kpad / tc::BK);
   int S = 1, kb_per = kblocks;
   tc_split_plan(M, N, sn.Kpad, S, kb_per);
@@ -930,20 +1506,25 @@ void tc_gemm_views(Ctx& c, const Tensor& vm, int nrm, const Tensor& vn, int nrn,
   const int64_t ytiles = (N + tc::BM - 1) / tc::BM, xtiles = (M + tc::BN - 1) / tc::BN;
   CCLR_REQUIRE(xtiles * ytiles * S < (int64_t)INT32_MAX, CCLR_E_ARG, "tc_gemm: too many tiles");
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (c.prof) c.prof_events(e0, e1);
+  if (c.prof) c.prof_events(e0, e1, 0);
   if (e0) CCLR_CK(cudaEventRecord(e0, c.stream));
   {
     // persistent: one CTA per SM (or per tile when there are fewer)
-    const int grid = (int)std::min<int64_t>(xtiles * ytiles * S, 148);
+    const int grid = (int)std::min<int64_t>(xtiles * ytiles * S, num_sms());
+    // a pending expiry test (cclr_debug_expire_next_wait) applies to this launch only
+    const uint32_t polls = c.dbg_wait_polls ? c.dbg_wait_polls : tc::kWaitPolls;
+    const int expire = c.dbg_wait_polls ? 1 : 0;
+    c.dbg_wait_polls = 0;
     c.kt.begin(c.stream);
     if (S > 1)
       tc::k_tc_zgemm<<<grid, tc::TC_THREADS, tc::SMEM_BYTES, c.stream>>>(sn.tm, sm.tm, (int)N, (int)M, kblocks, kb_per, pairs,
                                                               make_double2(1.0, 0.0), make_double2(0.0, 0.0), P, N,
-                                                              M * N, c.tc_err, (int)xtiles, (int)ytiles, S, om, false);
+                                                              M * N, c.tc_err, (int)xtiles, (int)ytiles, S, om, false,
+                                                              polls, expire);
     else
       tc::k_tc_zgemm<<<grid, tc::TC_THREADS, tc::SMEM_BYTES, c.stream>>>(sn.tm, sm.tm, (int)N, (int)M, kblocks, kb_per, pairs,
                                                               alpha, beta, C, ldc, 0, c.tc_err, (int)xtiles, (int)ytiles,
-                                                              1, om, strided);
+                                                              1, om, strided, polls, expire);
     const cudaError_t le = cudaGetLastError();
     CCLR_REQUIRE(le == cudaSuccess, CCLR_E_CUDA,
                  std::string("tensor-core GEMM launch failed (") + cudaGetErrorString(le) + ") M=" + std::to_string(M) +
@@ -952,8 +1533,8 @@ void tc_gemm_views(Ctx& c, const Tensor& vm, int nrm, const Tensor& vn, int nrn,
   }
   if (e1) {
     CCLR_CK(cudaEventRecord(e1, c.stream));
-    c.prof_flops_exec += 8.0 * (double)M * N * sn.K * pairs.n;
-    c.prof_flops_useful += 8.0 * (double)M * N * sn.K;
+    c.prof_flops_exec[0] += 8.0 * (double)M * N * sn.K * pairs.n;
+    c.prof_flops_useful[0] += 8.0 * (double)M * N * sn.K;
   }
   ++c.launches;
   if (S > 1) splitk_reduce(c.L, P, S, M, N, alpha, beta, C, ldc);
@@ -986,14 +1567,7 @@ RawPlan raw_plan(int nsl, int64_t M, int64_t N, int64_t K) {
   p.bytes_sn = (int64_t)sizeof(__nv_bfloat16) * 2 * nsl * N * p.Kpad;
   p.bytes_sm = (int64_t)sizeof(__nv_bfloat16) * 2 * nsl * M * p.Kpad;
   p.kblocks = (int)(p.Kpad / tc::BK);
-  const int64_t tiles = ((M + tc::BN - 1) / tc::BN) * ((N + tc::BM - 1) / tc::BM);
-  p.S = 1;
-  p.kb_per = p.kblocks;
-  if (tiles < 148 && p.kblocks >= 8) {
-    p.S = (int)std::min<int64_t>((148 + tiles - 1) / tiles, p.kblocks / 4);
-    p.kb_per = (p.kblocks + p.S - 1) / p.S;
-    p.S = (p.kblocks + p.kb_per - 1) / p.kb_per;
-  }
+  tc_split_plan(M, N, p.Kpad, p.S, p.kb_per);   // the same split-K choice as the context's GEMMs
   p.bytes_p = p.S > 1 ? (int64_t)sizeof(cplx) * p.S * M * N : 0;
   return p;
 }
@@ -1023,25 +1597,23 @@ int tc_raw_gemm_nt(int precision, int64_t M, int64_t N, int64_t K, const cplx* A
   split(B, N, sn);
   split(A, M, sm);
   const CUtensorMap tn = make_map(sn, N, p.Kpad, 2 * nsl, 128), tm = make_map(sm, M, p.Kpad, 2 * nsl, 128);
-  static bool attr = false;
-  if (!attr) {
+  static bool attr[64] = {};
+  if (once_per_device(attr))   // per device: a call on another device needs its own attribute
     CCLR_CK(cudaFuncSetAttribute(tc::k_tc_zgemm, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES));
-    attr = true;
-  }
   const tc::Pairs pairs = pairs_for(nsl);
   const int64_t ytiles = (N + tc::BM - 1) / tc::BM, xtiles = (M + tc::BN - 1) / tc::BN;
   const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
   CCLR_REQUIRE(xtiles * ytiles * p.S < (int64_t)INT32_MAX, CCLR_E_ARG, "tc_gemm: too many tiles");
   {
-    const int grid = (int)std::min<int64_t>(xtiles * ytiles * p.S, 148);
+    const int grid = (int)std::min<int64_t>(xtiles * ytiles * p.S, num_sms());
     if (p.S > 1)
       tc::k_tc_zgemm<<<grid, tc::TC_THREADS, tc::SMEM_BYTES, stream>>>(tn, tm, (int)N, (int)M, p.kblocks, p.kb_per, pairs, one,
                                                             zero, P, N, M * N, err, (int)xtiles, (int)ytiles, p.S,
-                                                            tc::OutMap(), false);
+                                                            tc::OutMap(), false, tc::kWaitPolls, 0);
     else
       tc::k_tc_zgemm<<<grid, tc::TC_THREADS, tc::SMEM_BYTES, stream>>>(tn, tm, (int)N, (int)M, p.kblocks, p.kb_per, pairs, one,
                                                             zero, C, N, 0, err, (int)xtiles, (int)ytiles, 1,
-                                                            tc::OutMap(), false);
+                                                            tc::OutMap(), false, tc::kWaitPolls, 0);
     CCLR_CK(cudaGetLastError());
   }
   if (p.S > 1) {

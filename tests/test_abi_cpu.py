@@ -51,3 +51,33 @@ def test_layout_roundtrip():
     t2 = antisym(synth.random_vector((3, 3, 5, 5), 1, 2))
     a, b = from_amp(to_amp(t1, t2), 3, 5)
     assert np.abs(a - t1).max() == 0 and np.abs(b - t2).max() < 1e-14
+
+
+def test_noalloc_wrapper_rejects_bad_tensors_before_any_gpu_work():
+    """cclr_zgemm_nt_noalloc's argument checks run on the host: a wrong dtype, a non-contiguous
+    view, a host tensor or mismatched shapes raise ValueError without reaching the library."""
+    import torch
+    import paper_2307_14296_b300 as pk
+
+    class Fake:   # stands in for a CUDA tensor (attributes only; no GPU here)
+        def __init__(self, shape, dtype=torch.complex128, contiguous=True):
+            self.shape, self.dtype, self._c, self.is_cuda = tuple(shape), dtype, contiguous, True
+
+        def is_contiguous(self):
+            return self._c
+
+        def dim(self):
+            return len(self.shape)
+
+    good = dict(A=Fake((8, 5)), B=Fake((6, 5)), C=Fake((8, 6)))
+    cases = [
+        dict(good, A=torch.zeros((8, 5), dtype=torch.complex128)),   # host tensor
+        dict(good, B=Fake((6, 5), dtype=torch.complex64)),            # wrong dtype
+        dict(good, C=Fake((8, 6), contiguous=False)),                 # non-contiguous
+        dict(good, B=Fake((6, 4))),                                   # K mismatch
+        dict(good, C=Fake((8, 5))),                                   # short C
+        dict(good, A=Fake((8, 5, 1))),                                # not a matrix
+    ]
+    for cs in cases:
+        with pytest.raises(ValueError):
+            pk.cclr_zgemm_nt_noalloc(cs["A"], cs["B"], cs["C"])

@@ -1,0 +1,133 @@
+"""Mixed precision with FP64 iterative refinement, against the FP64 oracle.
+
+The split-BF16 mode with refinement (cclr_options.refine = 1, the default) runs every iterative
+solve on the tensor cores in split BF16 until the mixed floor, then continues with FP64-class
+tensor-core sigma products and FP64 vector arithmetic to the requested tolerance.  The result
+must therefore match the oracle like an FP64 run does: alpha within 1e-6 relative per component
+(the stated target), and in practice far closer; the true residual of the returned response
+vectors, recomputed by the oracle, must be below the requested tolerance.
+"""
+import numpy as np
+import pytest
+
+import synth
+from layout import from_amp, rel
+from oracle import response as R
+from oracle.deriv import pack
+from oracle.ints import Ints
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pk():
+    import os
+    os.environ.setdefault("CCLR_WORKSPACE_GB", "4")
+    import paper_2307_14296_b300 as pk
+    return pk
+
+
+def make_ctx(pk, inst, **opt):
+    ctx = pk.Context(0, **opt)
+    ctx.cclr_set_hamiltonian(inst.n_occ, inst.n_vir, inst.fock, [inst.blocks[k] for k in synth.CLASSES])
+    return ctx
+
+
+def per_component(got, ref):
+    """max over the components of |got - ref| / |ref| (components that vanish are skipped)"""
+    big = np.abs(ref) > 1e-12 * np.abs(ref).max()
+    return float((np.abs(got - ref)[big] / np.abs(ref)[big]).max())
+
+
+def solve(pk, inst, omegas, gamma, **opt):
+    ctx = make_ctx(pk, inst, **opt)
+    ctx.cc_ground()
+    ctx.cc_lambda()
+    ctx.cc_lr_solve(inst.ops, omegas, gamma)
+    return ctx, ctx.cc_response_function()
+
+
+@pytest.mark.parametrize("prec", [2, 3])
+def test_refined_alpha_matches_oracle_4x20(pk, prec):
+    """(4,20): static, dynamic and damped frequencies, split BF16 (2) and the FP32-class mode (3)
+    with refinement; the tensor-core path engages (batched ladder and ring above 2^18 complex
+    multiply-adds)."""
+    inst = synth.make_instance(4, 20)
+    omegas, gamma = [0.0, 0.077, 0.2], 0.01
+    ctx, got = solve(pk, inst, omegas, gamma, precision=prec, tol=1e-9, ground_tol=1e-10, batch=8)
+    ref = R.CCSystem(Ints.from_instance(inst)).response(inst.ops, [w + 1j * gamma for w in omegas], tol=1e-12)
+    assert per_component(got, ref) < 1e-6
+    assert rel(got, ref) < 1e-9
+    ctx.close()
+
+
+def test_refined_residual_below_tolerance_4x20(pk):
+    """The true residual xi + (A - z) t of returned response vectors, recomputed by the oracle,
+    is below the requested 1e-8 (plus the oracle/GPU difference of A and xi, ~1e-13)."""
+    inst = synth.make_instance(4, 20)
+    o, v = 4, 20
+    omegas, gamma = [0.05, 0.3], 0.01
+    ctx, _ = solve(pk, inst, omegas, gamma, precision=pk.TC_BF16X3, tol=1e-8, ground_tol=1e-10, batch=8)
+    s = R.CCSystem(Ints.from_instance(inst))
+    shifts = [complex(w, gamma) for w in omegas]
+    for k in range(3):
+        xi = s.xi(inst.ops[k])
+        for f, z in enumerate(shifts):
+            t = pack(*from_amp(ctx.cclr_get_response_vector(k, f, 0), o, v))   # oracle element order
+            r = xi + s.sigma_r(t) - z * t
+            assert np.linalg.norm(r) < 1.5e-8, (k, f, np.linalg.norm(r))
+    ctx.close()
+
+
+def test_refined_alpha_strong_coupling_8x40(pk):
+    """(8,40) with integrals of sd 0.015 (1.5x the coupling of the scaled statistics, so that the
+    tensor-core error would show at the 1e-6 level without refinement): split BF16 + refinement
+    against the oracle at 1e-6 per component, and the unrefined mixed solve for contrast."""
+    inst = synth.make_instance(8, 40, sd=0.015)
+    omegas, gamma = [0.05, 0.3], 0.01
+    ref = R.CCSystem(Ints.from_instance(inst)).response(inst.ops, [w + 1j * gamma for w in omegas], tol=1e-11)
+    ctx, got = solve(pk, inst, omegas, gamma, precision=pk.TC_BF16X3, tol=1e-9, ground_tol=1e-10, batch=8,
+                     max_subspace=64)
+    ctx.close()
+    assert per_component(got, ref) < 1e-6, per_component(got, ref)
+    ctx, raw = solve(pk, inst, omegas, gamma, precision=pk.TC_BF16X3, tol=1e-9, ground_tol=1e-10, batch=8,
+                     max_subspace=64, refine=0)
+    ctx.close()
+    assert per_component(got, ref) < per_component(raw, ref)
+
+
+def test_unrefined_mixed_solve_reports_its_floor(pk):
+    """refine = 0: the mixed solve stops at its floor (above the requested tol) and says so in
+    the statistics; with refinement the same call meets tol."""
+    inst = synth.make_instance(4, 20)
+    ctx = make_ctx(pk, inst, precision=pk.TC_BF16X3, tol=1e-10, ground_tol=1e-10, batch=8, refine=0)
+    ctx.cc_ground()
+    ctx.cc_lambda()
+    ctx.cc_lr_solve(inst.ops, [0.1], 0.01)
+    floor = ctx.cclr_get_stats()["max_residual"]
+    assert floor > 1e-10
+    ctx.close()
+    ctx = make_ctx(pk, inst, precision=pk.TC_BF16X3, tol=1e-10, ground_tol=1e-10, batch=8)
+    ctx.cc_ground()
+    ctx.cc_lambda()
+    ctx.cc_lr_solve(inst.ops, [0.1], 0.01)
+    st = ctx.cclr_get_stats()
+    assert st["max_residual"] < 1e-10 and st["refine_vectors"] > 0
+    ctx.close()
+
+
+def test_refinement_without_iterations_left_is_noconv(pk):
+    """A solve that cannot reach its tolerance within maxit returns CCLR_E_NOCONV (not CCLR_OK),
+    and the best iterate stays readable (the CCSD amplitudes after maxit = 2); the same context
+    settings with enough iterations converge."""
+    inst = synth.make_instance(4, 20)
+    ctx = make_ctx(pk, inst, precision=pk.TC_BF16X3, ground_tol=1e-12, batch=8, maxit=2)
+    with pytest.raises(pk.CCLRError) as e:
+        ctx.cc_ground()
+    assert e.value.status == pk.CCLR_E_NOCONV
+    t = ctx.cclr_get_amplitudes(pk.AMP_T)
+    assert np.all(np.isfinite(t)) and np.abs(t).max() > 0
+    ctx.close()
+    ctx = make_ctx(pk, inst, precision=pk.TC_BF16X3, ground_tol=1e-10, batch=8)
+    ctx.cc_ground()
+    ctx.close()
