@@ -34,6 +34,10 @@ WORKLOADS = {
     "30x200": dict(n_occ=30, n_vir=200, n_freq=16, w_min=0.05, w_max=0.30, gamma=0.005, n_ops=3, tol=1e-8),
     # smaller replica of the same path (profiling captures that must stay small)
     "12x90": dict(n_occ=12, n_vir=90, n_freq=4, w_min=0.05, w_max=0.30, gamma=0.005, n_ops=3, tol=1e-8),
+    # mixed precision at scale: 4 frequencies, gamma 0.01, refined to a residual of 1e-8
+    "40x260": dict(n_occ=40, n_vir=260, n_freq=4, w_min=0.05, w_max=0.30, gamma=0.01, n_ops=3, tol=1e-8),
+    # adjoint gradients of alpha(0.1 + 0.005i) (operator elements and a static field)
+    "20x150": dict(n_occ=20, n_vir=150, n_freq=1, w_min=0.1, w_max=0.1, gamma=0.005, n_ops=3, tol=1e-10),
 }
 WORKLOAD = WORKLOADS["30x200"]
 METRIC = "CC-LR sigma TFLOP/s and s per converged α(ω) at 1e-6; mixed/batched vs FP64"
@@ -155,7 +159,26 @@ def oracle_sample(budget_s: float = 20.0):
     n_sig += calls["n"]
     flops = 8 * sigma_cmac(o, v) * n_sig
     return flops / dt / 1e12, dt, (f"oracle (NumPy FP64) full path at n_occ={o}, n_vir={v}: CCSD + Lambda + "
-                                    f"one damped frequency x 3 operators ({n_sig} sigma-type products, {dt:.1f} s)")
+                                    f"one damped frequency x 3 operators ({n_sig} sigma-type products, {dt:.1f} s); "
+                                    f"the oracle's v^4 tensors (25.6 GB at 200 virtuals) rule out a 30/200 sample")
+
+
+def oracle_sigma_one_thread(o: int = 8, v: int = 60):
+    """One right sigma product of the oracle with the BLAS limited to one thread (the paper's CPU
+    timings use one OpenMP thread): seconds and TFLOP/s by the sigma-count rule."""
+    import synth
+    from threadpoolctl import threadpool_limits
+    from oracle.ints import Ints
+    from oracle import response as R
+    inst = synth.make_instance(o, v)
+    s = R.CCSystem(Ints.from_instance(inst), tol=1e-8)
+    x = synth.random_vector((s.D.size,), 5, 5, 1e-2)
+    with threadpool_limits(limits=1):
+        s.sigma_r(x)
+        t0 = time.perf_counter()
+        s.sigma_r(x)
+        dt = time.perf_counter() - t0
+    return dt, 8 * sigma_cmac(o, v) / dt / 1e12
 
 
 def run_reference(args, world, rank):
@@ -171,7 +194,9 @@ def run_reference(args, world, rank):
     value = statistics.mean(vals)
     line = dict(metric=METRIC, value=value, unit="TFLOP/s", n_gpus=world, steps=args.steps, warmup=args.warmup,
                 ms_per_step=1e3 * statistics.mean(times), higher_is_better=True, scaling="weak", vs_baseline=None,
-                dtype="f64", data="synthetic", impl="reference", config=config_dict(args),
+                dtype="f64", data="synthetic", impl="reference",
+                config=dict(config_dict(args), reference_sample="each step: the oracle's full path on the 8/60 "
+                            "member of the same system family (the 30/200 system does not fit the oracle)"),
                 cpu_baseline=dict(value=value, unit="TFLOP/s", cores=cores, kind="oracle", sample=desc),
                 e2e=dict(value=value, unit="TFLOP/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line), flush=True)
@@ -256,6 +281,121 @@ def eom_replica(pk, synth):
     b = np.array([complex(*r) for r in out["fp64"]["roots"]])
     out["max_rel_diff_bf16x3_vs_fp64"] = float(np.abs(a - b).max() / np.abs(b).max())
     return out
+
+
+def run_accuracy_at_scale(args):
+    """The workload of --workload solved twice from the same Hamiltonian: split BF16 with FP64
+    refinement (the requested tolerance) and the FP64-class tensor-core mode throughout (every
+    contraction on the five-digit path, FP64 vector arithmetic, no mixed phase; the FP64 DFMA
+    path would take ~45 min at 40/260), each timed end to end; prints the per-frequency,
+    per-component relative error of alpha and both times as one JSON line."""
+    import paper_2307_14296_b300 as pk
+    import synth
+    w = WORKLOAD
+    o, v = w["n_occ"], w["n_vir"]
+    inst = synth.make_instance(o, v)
+    om = np.linspace(w["w_min"], w["w_max"], w["n_freq"])
+    out, alpha = dict(mode="accuracy_at_scale", workload=config_dict(args)["workload"]), {}
+    for name, prec in (("reference_f64tc", pk.TC_F64), ("bf16x3_refined", pk.TC_BF16X3)):
+        ctx = pk.Context(0, precision=prec, tol=w["tol"], ground_tol=1e-9, max_subspace=args.max_subspace,
+                         batch=8, maxit=100)
+        t0 = time.perf_counter()
+        ctx.cclr_set_hamiltonian(o, v, inst.fock, [inst.blocks[k] for k in synth.CLASSES])
+        ctx.cc_ground()
+        ctx.cc_lambda()
+        ctx.cc_lr_solve(inst.ops, om, w["gamma"])
+        st = ctx.cclr_get_stats()
+        alpha[name] = -ctx.cc_response_function()
+        out[name] = dict(seconds=time.perf_counter() - t0, final_response_residual=st["max_residual"],
+                         refine_sigma_products=st["refine_vectors"])
+        ctx.close()
+    a, b = alpha["bf16x3_refined"], alpha["reference_f64tc"]
+    out["per_frequency"] = [dict(omega=float(om[f]), max_rel_per_component=float((np.abs(a[f] - b[f]) / np.abs(b[f])).max()),
+                                 max_rel_to_largest=float(np.abs(a[f] - b[f]).max() / np.abs(b[f]).max()),
+                                 mean_alpha=[float(np.trace(b[f]).real / 3), float(np.trace(b[f]).imag / 3)])
+                            for f in range(len(om))]
+    print(json.dumps(out), flush=True)
+
+
+def run_adjoint(args):
+    """Gradients of alpha on the workload of --workload (20/150 at w = 0.1, gamma = 0.005 by
+    default): forward solve, then d Re and d Im of all nine components with respect to every
+    real parameter of the three Hermitian dipole operators through the autograd backward (one
+    set of 4 n_ops left solves, reused for the 18 Jacobian rows), checked against a central
+    difference (h = 1e-4) of two further solves along one random Hermitian direction; and the
+    static-field derivative d alpha / d eps for a field along operator 2 by finite field
+    (h = 1e-4).  One JSON line."""
+    import torch
+    import paper_2307_14296_b300 as pk
+    from paper_2307_14296_b300 import autograd as ag
+    import synth
+    w = WORKLOAD
+    o, v = w["n_occ"], w["n_vir"]
+    inst = synth.make_instance(o, v)
+    n = inst.n
+    om = list(np.linspace(w["w_min"], w["w_max"], w["n_freq"]))
+    prec = prec_of(pk, args.precision)
+    blocks = [inst.blocks[k] for k in synth.CLASSES]
+
+    def new_context():
+        return pk.Context(0, precision=prec, tol=w["tol"], ground_tol=1e-10, max_subspace=args.max_subspace,
+                          batch=8, maxit=100)
+    dev = torch.device("cuda", 0)
+    out = dict(mode="adjoint", workload=config_dict(args)["workload"], precision=args.precision, omega=om,
+               gamma=w["gamma"])
+    ctx = new_context()
+    t0 = time.perf_counter()
+    ctx.cclr_set_hamiltonian(o, v, inst.fock, blocks)
+    ctx.cc_ground()
+    ctx.cc_lambda()
+    out["ground_lambda_seconds"] = time.perf_counter() - t0
+    th0 = np.stack([ag.hermitian_params(inst.ops[k]) for k in range(3)])
+    th = torch.tensor(th0, device=dev, requires_grad=True)
+    ops = torch.stack([ag.hermitian_from_params(th[k], n) for k in range(3)])
+    t0 = time.perf_counter()
+    alpha = ag.polarizability(ops, ctx, om, w["gamma"])
+    torch.cuda.synchronize()
+    out["forward_seconds"] = time.perf_counter() - t0
+    jac = np.zeros((2, 3, 3) + th0.shape)
+    t0 = time.perf_counter()
+    for x in range(3):
+        for y in range(3):
+            for part, gv in enumerate((1.0, 1j)):
+                g = torch.zeros_like(alpha)
+                g[0, x, y] = gv
+                (gt,) = torch.autograd.grad(alpha, th, grad_outputs=g, retain_graph=True)
+                jac[part, x, y] = gt.cpu().numpy()
+    torch.cuda.synchronize()
+    out["backward_seconds_18_rows"] = time.perf_counter() - t0
+    out["left_solves"] = 4 * 3
+    a0 = alpha.detach().cpu().numpy()[0]
+    out["alpha"] = [[[float(a0[x, y].real), float(a0[x, y].imag)] for y in range(3)] for x in range(3)]
+    out["grad_norm_re"] = float(np.linalg.norm(jac[0]))
+    out["grad_norm_im"] = float(np.linalg.norm(jac[1]))
+    # central difference along one random direction of all operator parameters
+    rng = np.random.default_rng(23)
+    d = rng.standard_normal(th0.shape)
+    h = 1e-4
+
+    def alpha_at(t):
+        o3 = np.stack([ag.hermitian_from_params(torch.from_numpy(t[k]), n).numpy() for k in range(3)])
+        ctx.cc_lr_solve(o3, om, w["gamma"])
+        return -ctx.cc_response_function()[0]
+    t0 = time.perf_counter()
+    fd = (alpha_at(th0 + h * d) - alpha_at(th0 - h * d)) / (2 * h)
+    out["fd_seconds"] = time.perf_counter() - t0
+    got = np.einsum("rxyk,k->rxy", jac.reshape(2, 3, 3, -1), d.ravel())
+    err = max(np.abs(got[0] - fd.real).max(), np.abs(got[1] - fd.imag).max())
+    out["fd_check"] = dict(h=h, max_abs_diff=float(err), max_abs_fd=float(np.abs(fd).max()),
+                           max_rel=float(err / np.abs(fd).max()))
+    ctx.close()
+    t0 = time.perf_counter()
+    dfield, _, _ = ag.alpha_field_derivative(new_context, o, v, inst.fock, blocks, inst.ops[2], inst.ops, om,
+                                             w["gamma"], h=1e-4)
+    out["field"] = dict(operator=2, h=1e-4, seconds=time.perf_counter() - t0,
+                        d_alpha_d_eps=[[[float(dfield[0, x, y].real), float(dfield[0, x, y].imag)] for y in range(3)]
+                                       for x in range(3)])
+    print(json.dumps(out), flush=True)
 
 
 def run_gemm(args):
@@ -361,6 +501,11 @@ def main():
                     help="time only the solver's Gram and vecmat kernels on synthetic vectors (kernel profiling)")
     ap.add_argument("--sigma", default=None, metavar="O,V[,SIDE]",
                     help="time only one batched sigma product of 8 vectors on an O/V system (kernel profiling)")
+    ap.add_argument("--accuracy-at-scale", action="store_true",
+                    help="solve the workload refined and in the FP64-class mode; per-frequency alpha errors")
+    ap.add_argument("--max-subspace", type=int, default=64, help="Davidson trial-space limit")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="gradients of alpha w.r.t. the operators and a static field (use --workload 20x150)")
     args = ap.parse_args()
     global WORKLOAD
     WORKLOAD = WORKLOADS[args.workload]
@@ -372,6 +517,12 @@ def main():
         return
     if args.vector_kernels:
         run_vector_kernels(args)
+        return
+    if args.accuracy_at_scale:
+        run_accuracy_at_scale(args)
+        return
+    if args.adjoint:
+        run_adjoint(args)
         return
     world, rank, local = dist_init()
     if args.impl == "reference":
@@ -387,7 +538,8 @@ def main():
     inst = synth.make_instance(o, v, seed=synth.DEFAULT_SEED + rank)
     omegas = np.linspace(w["w_min"], w["w_max"], w["n_freq"])
     prec = prec_of(pk, args.precision)
-    ctx = pk.Context(local, precision=prec, tol=w["tol"], ground_tol=1e-8, max_subspace=64, batch=8, maxit=80)
+    ctx = pk.Context(local, precision=prec, tol=w["tol"], ground_tol=1e-8, max_subspace=args.max_subspace, batch=8,
+                     maxit=80)
     blocks = [inst.blocks[k] for k in synth.CLASSES]
     # pinned host copies of the inputs (for the end-to-end measurement)
     pinned = [torch.from_numpy(np.ascontiguousarray(b)).pin_memory() for b in [inst.fock] + blocks + [inst.ops]]
@@ -512,7 +664,10 @@ def main():
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         tf, dt, desc = oracle_sample()
-        cpu = dict(value=tf, unit="TFLOP/s", cores=len(os.sched_getaffinity(0)), kind="oracle", sample=desc)
+        t1, tf1 = oracle_sigma_one_thread()
+        cpu = dict(value=tf, unit="TFLOP/s", cores=len(os.sched_getaffinity(0)), kind="oracle", sample=desc,
+                   one_thread_sigma=dict(seconds=t1, tflops=tf1, sample="one oracle right sigma at n_occ=8, n_vir=60, "
+                                                                        "BLAS limited to 1 thread"))
 
     if rank != 0:
         return

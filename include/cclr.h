@@ -87,6 +87,11 @@ typedef struct {
    * reached is in cclr_stats.max_residual. */
   int refine;
   double refine_tol;   /* mixed-phase floor relative to the right-hand side, 0 = 2e-5         */
+  /* Tile autotuning of the split-BF16 GEMM kernel (default 1): the first two launches of every
+   * GEMM shape try a 128-row and a 64-row tile (timed with CUDA events on the context's stream),
+   * later launches use the faster.  With the environment variable CCLR_AUTOTUNE_CACHE naming a
+   * file, decisions are read from it at first use and appended to it.  0: 128-row tiles. */
+  int autotune;
 } cclr_options;
 
 /* Fill *opt with the defaults listed above. */
@@ -139,6 +144,33 @@ cclr_status cc_lr_solve(cclr_ctx *ctx, int n_ops, const cclr_c128 *ops, int n_fr
  * n_freq*n_ops*n_ops values.  The polarizability is alpha = -<<mu;mu>>.  Requires cc_lr_solve. */
 cclr_status cc_response_function(cclr_ctx *ctx, cclr_c128 *out);
 
+/* Gradient of the CC-CC response function with respect to the property operators, by the adjoint
+ * method (Sec. 2.3: the response function is linear in each operator through xi^X and eta^X; the
+ * multipliers l of t-bar A-type left equations carry the dependence of t^X on xi^X).  For
+ * frequency index f of the last cc_lr_solve and every operator k, four n x n matrices G[k][s],
+ * s over the shifts (0: w+ig, 1: -w+ig, 2: w-ig, 3: -w-ig), with
+ *   G[k][s] = 1/2 [ eta-density(t^k(w_s)) + xi-density(l) ],  l (A + w_s) = -(eta^k + F t^k(w_s)),
+ * where the densities D are the matrices with eta^X . v = sum_pq D_pq X_pq and
+ * l . xi^X = sum_pq D_pq X_pq.  For perturbations dX_x and dX_y of operators x and y:
+ *   d<<X_x;X_y>>_{w+ig} = sum G[y][0] o dX_x + conj(sum G[y][1] o dX_x)
+ *                       + sum G[x][3] o dX_y + conj(sum G[x][2] o dX_y)
+ * (o: element-wise product summed over all p, q).  out: n_ops*4*n*n values, [k][s][p][q]
+ * row-major.  Costs 4 n_ops left solves and Hessian products.  Requires cc_lr_solve. */
+cclr_status cclr_response_gradient(cclr_ctx *ctx, int f, cclr_c128 *out);
+
+/* eta of the CC energy at the current T: the derivative dE/dt in the amplitude layout (the Lambda
+ * equations read t-bar A = -eta; Sec. 2.3 and the SI ground-state Lambda equations).  N values. */
+cclr_status cclr_eta_ground(cclr_ctx *ctx, cclr_c128 *out);
+
+/* Left (adjoint) linear systems  l_k (A + w) = -b_k  for nrhs right-hand sides b (nrhs x N, amplitude
+ * layout) at the current T, with the shift w = w_re + i w_im (SI left sigma equations
+ * sigma_sin-ee-left / sigma_double-ee-left).  b = eta of the energy and w = 0 give Lambda; the
+ * response-function gradient uses b = eta^X + F t^X(w).  Solved to cclr_options.tol by the same
+ * Davidson and refinement as the Lambda equations; out: nrhs x N.  CCLR_E_NOCONV if the solve
+ * does not converge within maxit (out is then not written), CCLR_E_ARG on non-finite input. */
+cclr_status cclr_left_solve(cclr_ctx *ctx, int nrhs, const cclr_c128 *rhs, double w_re, double w_im,
+                            cclr_c128 *out);
+
 /* The CC-CI response function (Sec. 2.3 Eq. CC-CI response function; EOM-eta of the SI "Linear
  * response" section): the same symmetrization and layout as cc_response_function, from the
  * solutions of the last cc_lr_solve, without the Hessian term.  Requires cc_lr_solve (after
@@ -164,6 +196,13 @@ cclr_status cclr_get_eom_vector(cclr_ctx *ctx, int root, cclr_c128 *dst, size_t 
 /* Which amplitude set: ground T, Lambda, or a response solution. */
 enum { CCLR_AMP_T = 0, CCLR_AMP_LAMBDA = 1 };
 
+/* Caller arrays of amplitudes, operators, right-hand sides and gradients (cclr_get/set_amplitudes,
+ * cclr_get_response_vector, cclr_residual, cclr_xi, cclr_eta, cclr_eta_ground, cc_lr_solve's ops,
+ * cclr_left_solve, cclr_response_gradient, cclr_get_eom_vector) may be host memory or device
+ * memory: with unified addressing the copy direction follows from the pointer.  The calls return
+ * after their copies complete; the caller orders device inputs before the call (e.g. by
+ * synchronizing the stream that wrote them). */
+
 /* Copy amplitudes out in the amplitude layout (n must be o*v + Po*Pv). */
 cclr_status cclr_get_amplitudes(cclr_ctx *ctx, int which, cclr_c128 *dst, size_t n);
 
@@ -187,7 +226,9 @@ cclr_status cclr_sigma(cclr_ctx *ctx, int side, int nvec, const cclr_c128 *in, c
 cclr_status cclr_residual(cclr_ctx *ctx, cclr_c128 *out, cclr_c128 *e_corr_out);
 
 /* xi^X (SI Eq. xi-equation), eta^X (SI Eq. eta-equation) and, with eom != 0, the EOM eta^X of
- * the SI, for one Hermitian operator X (host (o+v)^2).  eta needs Lambda. */
+ * the SI, for one Hermitian operator X (host (o+v)^2).  eta needs Lambda.  These and
+ * cclr_hessian compute in the precision of the response results: FP64-class tensor cores
+ * (CCLR_TC_F64) on a split-BF16 context that refines, the context's precision otherwise. */
 cclr_status cclr_xi(cclr_ctx *ctx, const cclr_c128 *op, cclr_c128 *out);
 cclr_status cclr_eta(cclr_ctx *ctx, const cclr_c128 *op, int eom, cclr_c128 *out);
 
@@ -262,6 +303,23 @@ cclr_status cclr_kernel_breakdown(cclr_ctx *ctx, char *buf, int cap);
  * expiry, every role exits, TMEM is freed, and the call that launched it returns CCLR_E_TIMEOUT.
  * The context stays usable.  CCLR_E_ARG for polls = 0. */
 cclr_status cclr_debug_expire_next_wait(cclr_ctx *ctx, unsigned polls);
+
+/* Several systems of uneven size solved as one batch: for every k < n, context ctxs[k] (its own
+ * Hamiltonian, set by cclr_set_hamiltonian, and its own stream) runs cc_ground, cc_lambda,
+ * cc_lr_solve(n_ops operators ops[k], the n_freq frequencies omegas, gamma) and
+ * cc_response_function into out[k] (n_freq*n_ops*n_ops values), each system on its own host
+ * thread, so that the kernels of the systems overlap on the GPU (the GEMMs of a small system
+ * occupy few SMs).  The contexts must be distinct; each call is as documented for one context.
+ * status (may be NULL) receives each system's status; the return value is the first non-OK
+ * status in system order, CCLR_OK if all succeeded, CCLR_E_ARG for bad arguments. */
+cclr_status cclr_response_batch(cclr_ctx *const *ctxs, int n, int n_ops, const cclr_c128 *const *ops, int n_freq,
+                                const double *omegas, double gamma, cclr_c128 *const *out, cclr_status *status);
+
+/* The tile autotuner's decisions so far, one text line per GEMM shape: "MxNxK/slices/c|s/SMs rows
+ * stages ms_128 ms_64" (the shape key, the chosen tile rows and pipeline stages, and the timed
+ * milliseconds of the two candidates), into buf (cap bytes including the terminating NUL; longer
+ * text is truncated).  CCLR_E_ARG if buf is NULL or cap < 1. */
+cclr_status cclr_autotune_report(cclr_ctx *ctx, char *buf, int cap);
 
 /* Per-call statistics of the last cc_* call: sigma launches and vectors, seconds spent;
  * refine_vectors / refine_seconds: the FP64-class sigma products (CCSD residuals) and the

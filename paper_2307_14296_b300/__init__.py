@@ -37,14 +37,15 @@ EXPORTS = (
     "cclr_set_amplitudes", "cclr_get_response_vector", "cclr_sigma", "cclr_residual", "cclr_xi",
     "cclr_eta", "cclr_hessian", "cclr_zgemm_nt", "cclr_kernel_profile", "cclr_get_stats",
     "cclr_zgemm_nt_noalloc", "cclr_kernel_breakdown", "cclr_bench_vector_kernels", "cclr_gram",
-    "cclr_debug_expire_next_wait",
+    "cclr_debug_expire_next_wait", "cclr_autotune_report", "cclr_response_batch", "cclr_response_gradient",
+    "cclr_eta_ground", "cclr_left_solve",
 )
 
 
 class Options(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("ground_tol", ctypes.c_double), ("maxit", ctypes.c_int),
                 ("max_subspace", ctypes.c_int), ("precision", ctypes.c_int), ("batch", ctypes.c_int),
-                ("refine", ctypes.c_int), ("refine_tol", ctypes.c_double)]
+                ("refine", ctypes.c_int), ("refine_tol", ctypes.c_double), ("autotune", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -84,6 +85,12 @@ _sig = {
     "cclr_bench_vector_kernels": (_i, [_vp, _i, ctypes.c_int64, _i, _i, _i, _i, _vp]),
     "cclr_gram": (_i, [_vp, _i, ctypes.c_int64, _i, _i, _vp, _vp, _vp]),
     "cclr_debug_expire_next_wait": (_i, [_vp, ctypes.c_uint]),
+    "cclr_autotune_report": (_i, [_vp, ctypes.c_char_p, _i]),
+    "cclr_response_gradient": (_i, [_vp, _i, _vp]),
+    "cclr_eta_ground": (_i, [_vp, _vp]),
+    "cclr_left_solve": (_i, [_vp, _i, _vp, _d, _d, _vp]),
+    "cclr_response_batch": (_i, [ctypes.POINTER(_vp), _i, _i, ctypes.POINTER(_vp), _i, _vp, _d, ctypes.POINTER(_vp),
+                                 _vp]),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(_lib, _name)
@@ -115,6 +122,41 @@ def _ptr(a: np.ndarray):
 
 def _is_torch_cuda(x) -> bool:
     return hasattr(x, "is_cuda") and x.is_cuda
+
+
+def _in(x):
+    """(pointer, keep-alive) for an input array: a contiguous complex128 CUDA tensor is passed as
+    its device pointer after the stream that produced it has finished; anything else as a host
+    complex128 array."""
+    if _is_torch_cuda(x):
+        import torch
+        if x.dtype != torch.complex128 or not x.is_contiguous():
+            raise ValueError("device arrays must be contiguous complex128 tensors")
+        torch.cuda.current_stream(x.device).synchronize()
+        return _vp(x.data_ptr()), x
+    a = _c128(x)
+    return _ptr(a), a
+
+
+def _out(shape, like=None, out=None):
+    """Output array: `out` if given (host or CUDA), else a CUDA tensor on `like`'s device when
+    `like` is a CUDA tensor, else a host array."""
+    if out is None:
+        if _is_torch_cuda(like):
+            import torch
+            out = torch.empty(shape, dtype=torch.complex128, device=like.device)
+        else:
+            out = np.zeros(shape, np.complex128)
+    if _is_torch_cuda(out):
+        import torch
+        if out.dtype != torch.complex128 or not out.is_contiguous() or tuple(out.shape) != tuple(shape):
+            raise ValueError(f"output must be a contiguous complex128 tensor of shape {tuple(shape)}")
+        torch.cuda.current_stream(out.device).synchronize()
+        return _vp(out.data_ptr()), out
+    if not (isinstance(out, np.ndarray) and out.dtype == np.complex128 and out.flags.c_contiguous
+            and out.shape == tuple(shape)):
+        raise ValueError(f"output must be a C-contiguous complex128 array of shape {tuple(shape)}")
+    return _ptr(out), out
 
 
 class Context:
@@ -169,16 +211,42 @@ class Context:
         return it.value
 
     def cc_lr_solve(self, ops, omegas, gamma):
-        ops = _c128(ops)
+        """ops: (n_ops, n, n) host array or complex128 CUDA tensor."""
+        p, ops = _in(ops)
         om = np.ascontiguousarray(omegas, dtype=np.float64)
         its = np.zeros(ops.shape[0] * om.size, np.int32)
-        self._check(_lib.cc_lr_solve(self._h, ops.shape[0], _ptr(ops), om.size, _ptr(om), float(gamma), _ptr(its)))
+        self._check(_lib.cc_lr_solve(self._h, ops.shape[0], p, om.size, _ptr(om), float(gamma), _ptr(its)))
         self._nops, self._nfreq = ops.shape[0], om.size
+        self.lr_serial = getattr(self, "lr_serial", 0) + 1
         return its.reshape(ops.shape[0], om.size)
 
     def cc_response_function(self):
         out = np.zeros((self._nfreq, self._nops, self._nops), np.complex128)
         self._check(_lib.cc_response_function(self._h, _ptr(out)))
+        return out
+
+    def cclr_response_gradient(self, f: int, out=None, like=None):
+        """Operator gradient of the response function at frequency index f: G[k][s] (n_ops, 4, n, n)
+        with d<<X_x;X_y>> = sum G[y,0] dX_x + conj(sum G[y,1] dX_x) + sum G[x,3] dX_y
+        + conj(sum G[x,2] dX_y).  Written to `out` (host or CUDA), else to a new array on `like`'s
+        device."""
+        n = self.n_occ + self.n_vir
+        p, out = _out((self._nops, 4, n, n), like, out)
+        self._check(_lib.cclr_response_gradient(self._h, int(f), p))
+        return out
+
+    def cclr_eta_ground(self, out=None, like=None):
+        """dE/dt at the current T (the right-hand side of the Lambda equations)."""
+        p, out = _out((self.N,), like, out)
+        self._check(_lib.cclr_eta_ground(self._h, p))
+        return out
+
+    def cclr_left_solve(self, rhs, w=0.0, out=None):
+        """l (A + w) = -b for each row b of rhs ([nrhs, N] or [N]; host or CUDA)."""
+        p, b = _in(rhs)
+        nrhs = b.shape[0] if b.ndim == 2 else 1
+        po, out = _out(tuple(b.shape), b, out)
+        self._check(_lib.cclr_left_solve(self._h, nrhs, p, float(complex(w).real), float(complex(w).imag), po))
         return out
 
     def cc_response_function_ci(self):
@@ -201,14 +269,16 @@ class Context:
         return out
 
     # ---- components
-    def cclr_get_amplitudes(self, which=AMP_T):
-        out = np.zeros(self.N, np.complex128)
-        self._check(_lib.cclr_get_amplitudes(self._h, which, _ptr(out), out.size))
+    def cclr_get_amplitudes(self, which=AMP_T, out=None, like=None):
+        p, out = _out((self.N,), like, out)
+        self._check(_lib.cclr_get_amplitudes(self._h, which, p, self.N))
         return out
 
     def cclr_set_amplitudes(self, which, vec):
-        vec = _c128(vec)
-        self._check(_lib.cclr_set_amplitudes(self._h, which, _ptr(vec), vec.size))
+        """vec: host array or complex128 CUDA tensor (amplitude layout)."""
+        p, vec = _in(vec)
+        n = vec.numel() if _is_torch_cuda(vec) else vec.size
+        self._check(_lib.cclr_set_amplitudes(self._h, which, p, n))
 
     def cclr_get_response_vector(self, k, f, s):
         out = np.zeros(self.N, np.complex128)
@@ -231,10 +301,11 @@ class Context:
         self._check(_lib.cclr_sigma(self._h, side, nvec, _ptr(v), _ptr(res), 0, precision))
         return res
 
-    def cclr_residual(self):
-        out = np.zeros(self.N, np.complex128)
+    def cclr_residual(self, out=None, like=None):
+        """(Omega(T), E_corr); Omega written to `out` (host or CUDA) or a new array on `like`'s device."""
+        p, out = _out((self.N,), like, out)
         e = np.zeros(1, np.complex128)
-        self._check(_lib.cclr_residual(self._h, _ptr(out), _ptr(e)))
+        self._check(_lib.cclr_residual(self._h, p, _ptr(e)))
         return out, complex(e[0])
 
     def cclr_xi(self, op):
@@ -311,6 +382,16 @@ class Context:
         nothing completes, with `polls` polls per wait (test of the CCLR_E_TIMEOUT path)."""
         self._check(_lib.cclr_debug_expire_next_wait(self._h, int(polls)))
 
+    def cclr_autotune_report(self) -> dict:
+        """{shape key: (tile rows, stages, ms of the 128-row tile, ms of the 64-row tile)} decided so far."""
+        buf = ctypes.create_string_buffer(1 << 20)
+        self._check(_lib.cclr_autotune_report(self._h, buf, len(buf)))
+        out = {}
+        for line in buf.value.decode().splitlines():
+            k, bn, st, m0, m1 = line.split()
+            out[k] = (int(bn), int(st), float(m0), float(m1))
+        return out
+
     def cclr_get_stats(self) -> dict:
         s = Stats()
         self._check(_lib.cclr_get_stats(self._h, ctypes.byref(s)))
@@ -385,6 +466,28 @@ def cclr_zgemm_nt_noalloc(A, B, C, precision=TC_BF16X3, stream=None) -> int:
     N = B.shape[0]
     s = _vp(stream.cuda_stream) if stream is not None else _vp()
     return _lib.cclr_zgemm_nt_noalloc(precision, M, N, K, _vp(A.data_ptr()), _vp(B.data_ptr()), _vp(C.data_ptr()), s)
+
+
+def cclr_response_batch(contexts, ops, omegas, gamma):
+    """Several systems (contexts with their Hamiltonians set) solved as one batch, one host thread
+    per system so that their kernels overlap on the GPU: the response function of each system
+    (list of [n_freq, n_ops, n_ops] arrays).  ops: one [n_ops, n, n] array per system."""
+    n = len(contexts)
+    ops = [_c128(o) for o in ops]
+    n_ops = ops[0].shape[0]
+    om = np.ascontiguousarray(omegas, dtype=np.float64)
+    outs = [np.zeros((om.size, n_ops, n_ops), np.complex128) for _ in range(n)]
+    st = np.zeros(n, np.int32)
+    h = (_vp * n)(*[c._h for c in contexts])
+    po = (_vp * n)(*[o.ctypes.data for o in ops])
+    pout = (_vp * n)(*[o.ctypes.data for o in outs])
+    r = _lib.cclr_response_batch(h, n, n_ops, po, om.size, _ptr(om), float(gamma), pout, _ptr(st))
+    if r != CCLR_OK:
+        bad = int(np.flatnonzero(st)[0])
+        raise CCLRError(int(st[bad]), f"system {bad}: " + _lib.cclr_last_error(contexts[bad]._h).decode())
+    for c in contexts:
+        c._nops, c._nfreq = n_ops, om.size
+    return outs
 
 
 def library_path() -> str:

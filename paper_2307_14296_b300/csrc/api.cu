@@ -5,6 +5,7 @@
 #include <chrono>
 #include <cstdlib>
 #include <cmath>
+#include <thread>
 
 using namespace cclr;
 
@@ -35,6 +36,7 @@ cclr_status guard(cclr_ctx* h, F&& fn) {
     CCLR_CK(cudaSetDevice(c.device));
     fn(c);
     CCLR_CK(cudaStreamSynchronize(c.stream));
+    tc_tune_collect(c);
     if (c.prof) c.prof_collect();
     if (c.kt.on) c.kt.collect();
     static const bool verbose = std::getenv("CCLR_VERBOSE") != nullptr;
@@ -42,7 +44,7 @@ cclr_status guard(cclr_ctx* h, F&& fn) {
       size_t fr = 0, tot = 0;
       cudaMemGetInfo(&fr, &tot);
       std::fprintf(stderr, "[cclr] memory: arrays %.2f GiB (%zu), slice cache %.2f GiB, workspace peak %.2f of %.2f GiB, free %.2f GiB\n",
-                   c.persistent_total() / 1073741824.0, c.persistent.size(), tc_cache_bytes() / 1073741824.0,
+                   c.persistent_total() / 1073741824.0, c.persistent.size(), tc_cache_bytes(c) / 1073741824.0,
                    c.ws.peak / 1073741824.0, c.ws.cap / 1073741824.0, fr / 1073741824.0);
     }
     if (c.tc_err) {
@@ -67,8 +69,8 @@ cclr_status guard(cclr_ctx* h, F&& fn) {
 }
 
 void free_all(Ctx& c) {
-  tc_release_cache();
-  ++hbar_generation();
+  tc_release_cache_for(c);
+  ++c.data_gen;
   for (void* p : c.persistent) cudaFree(p);
   c.persistent.clear();
   c.persistent_bytes.clear();
@@ -88,8 +90,42 @@ void free_all(Ctx& c) {
   if (c.ws.base) { cudaFree(c.ws.base); c.ws = Arena(); }
 }
 
+// Copies between the library's device arrays and caller memory use cudaMemcpyDefault: with unified
+// addressing the runtime reads from the pointer whether it is host (pageable or pinned) or device
+// memory, so the amplitude, operator and gradient entry points take either without a flag.
 void upload(Ctx& c, cplx* dst, const void* src, int64_t n) {
-  CCLR_CK(cudaMemcpyAsync(dst, src, sizeof(cplx) * n, cudaMemcpyHostToDevice, c.stream));
+  CCLR_CK(cudaMemcpyAsync(dst, src, sizeof(cplx) * n, cudaMemcpyDefault, c.stream));
+}
+void download(Ctx& c, void* dst, const cplx* src, int64_t n) {
+  CCLR_CK(cudaMemcpyAsync(dst, src, sizeof(cplx) * n, cudaMemcpyDefault, c.stream));
+}
+
+// true when p is device (or managed) memory, false for host memory
+bool device_pointer(const void* p) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// rejects infinities and NaN in n complex values at p (host loop, or a device scan for device p)
+void require_finite(Ctx& c, const cplx* p, int64_t n, const char* what) {
+  bool ok = true;
+  if (device_pointer(p)) {
+    Scope sc(c.ws);
+    int* bad = (int*)c.ws.alloc(sizeof(int));
+    CCLR_CK(cudaMemsetAsync(bad, 0, sizeof(int), c.stream));
+    flag_nonfinite(c.L, p, n, bad);
+    int h = 0;
+    CCLR_CK(cudaMemcpyAsync(&h, bad, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+    c.sync();
+    ok = h == 0;
+  } else {
+    for (int64_t i = 0; i < n && ok; ++i) ok = std::isfinite(p[i].x) && std::isfinite(p[i].y);
+  }
+  if (!ok) throw Error(CCLR_E_ARG, std::string(what) + ": an element is an infinity or NaN");
 }
 
 // copy in/out helpers for entry points that accept host or device pointers
@@ -135,6 +171,7 @@ void cclr_default_options(cclr_options* opt) {
   opt->batch = 0;
   opt->refine = 1;
   opt->refine_tol = 0.0;
+  opt->autotune = 1;
 }
 
 cclr_status cclr_create(cclr_ctx** out, int device, const cclr_options* opt) {
@@ -171,6 +208,7 @@ void cclr_destroy(cclr_ctx* h) {
   if (!h) return;
   cudaSetDevice(h->c.device);
   free_all(h->c);
+  tc_state_free(h->c);
   if (h->c.tc_err) cudaFree(h->c.tc_err);
   for (auto& e : h->c.ev_pool) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
   if (h->c.stream) cudaStreamDestroy(h->c.stream);
@@ -327,9 +365,7 @@ cclr_status cc_lr_solve(cclr_ctx* h, int n_ops, const cclr_c128* ops, int n_freq
     CCLR_REQUIRE(std::isfinite(gamma), CCLR_E_ARG, "cc_lr_solve: gamma must be finite");
     for (int f = 0; f < n_freq; ++f)
       CCLR_REQUIRE(std::isfinite(omegas[f]), CCLR_E_ARG, "cc_lr_solve: a frequency is an infinity or NaN");
-    for (int64_t i = 0; i < (int64_t)n_ops * c.n * c.n; ++i)
-      CCLR_REQUIRE(std::isfinite(ops[i].re) && std::isfinite(ops[i].im), CCLR_E_ARG,
-                   "cc_lr_solve: an operator element is an infinity or NaN");
+    require_finite(c, (const cplx*)ops, (int64_t)n_ops * c.n * c.n, "cc_lr_solve: operator");
     lr_solve(c, n_ops, (const cplx*)ops, n_freq, omegas, gamma, iters_out);
   });
 }
@@ -338,6 +374,35 @@ cclr_status cc_response_function(cclr_ctx* h, cclr_c128* out) {
   return guard(h, [&](Ctx& c) {
     CCLR_REQUIRE(out, CCLR_E_ARG, "null output");
     response_function(c, (cplx*)out);
+  });
+}
+
+cclr_status cclr_response_gradient(cclr_ctx* h, int f, cclr_c128* out) {
+  return guard(h, [&](Ctx& c) {
+    CCLR_REQUIRE(out, CCLR_E_ARG, "null output");
+    response_gradient(c, f, (cplx*)out);
+  });
+}
+
+cclr_status cclr_eta_ground(cclr_ctx* h, cclr_c128* out) {
+  return guard(h, [&](Ctx& c) {
+    CCLR_REQUIRE(c.have_hbar && out, CCLR_E_STATE, "cclr_eta_ground needs T");
+    PrecisionScope exact(c, exact_precision(c));
+    Scope sc(c.ws);
+    cplx* r = c.ws.cplxs(c.N);
+    eta_ground(c, r);
+    download(c, out, r, c.N);
+    c.sync();
+  });
+}
+
+cclr_status cclr_left_solve(cclr_ctx* h, int nrhs, const cclr_c128* rhs, double w_re, double w_im, cclr_c128* out) {
+  return guard(h, [&](Ctx& c) {
+    CCLR_REQUIRE(c.have_hbar, CCLR_E_STATE, "cclr_left_solve needs T");
+    CCLR_REQUIRE(nrhs >= 1 && rhs && out && std::isfinite(w_re) && std::isfinite(w_im), CCLR_E_ARG,
+                 "bad cclr_left_solve arguments");
+    require_finite(c, (const cplx*)rhs, (int64_t)nrhs * c.N, "cclr_left_solve: right-hand side");
+    left_solve(c, nrhs, (const cplx*)rhs, zc(w_re, w_im), (cplx*)out);
   });
 }
 
@@ -362,7 +427,7 @@ cclr_status cclr_get_eom_vector(cclr_ctx* h, int root, cclr_c128* dst, size_t n)
   return guard(h, [&](Ctx& c) {
     CCLR_REQUIRE(dst && (int64_t)n == c.N, CCLR_E_ARG, "vector buffer length must be o*v + Po*Pv");
     CCLR_REQUIRE(root >= 0 && root < (int)c.eom_vecs.size(), CCLR_E_STATE, "no such EOM root (call cc_eom_ee)");
-    CCLR_CK(cudaMemcpyAsync(dst, c.eom_vecs[root], sizeof(cplx) * n, cudaMemcpyDeviceToHost, c.stream));
+    download(c, dst, c.eom_vecs[root], (int64_t)n);
   });
 }
 
@@ -372,7 +437,7 @@ cclr_status cclr_get_amplitudes(cclr_ctx* h, int which, cclr_c128* dst, size_t n
     const cplx* src = which == CCLR_AMP_T ? c.t : which == CCLR_AMP_LAMBDA ? c.lam : nullptr;
     CCLR_REQUIRE(src, CCLR_E_ARG, "unknown amplitude set");
     CCLR_REQUIRE(which == CCLR_AMP_T ? c.have_t : c.have_lambda, CCLR_E_STATE, "amplitudes not available");
-    CCLR_CK(cudaMemcpyAsync(dst, src, sizeof(cplx) * n, cudaMemcpyDeviceToHost, c.stream));
+    download(c, dst, src, (int64_t)n);
   });
 }
 
@@ -414,7 +479,7 @@ cclr_status cclr_get_response_vector(cclr_ctx* h, int k, int f, int s, cclr_c128
     const zc* beta = &rd.beta[k][(size_t)rd.shift_of[(size_t)f * 4 + s] * maxL];
     CCLR_CK(cudaMemcpyAsync(b, beta, sizeof(cplx) * rd.nb[k], cudaMemcpyHostToDevice, c.stream));
     lincomb(c.L, c.N, rd.nb[k], rd.basis[k], c.N, b, t, false);
-    CCLR_CK(cudaMemcpyAsync(dst, t, sizeof(cplx) * n, cudaMemcpyDeviceToHost, c.stream));
+    download(c, dst, t, (int64_t)n);
     c.sync();
   });
 }
@@ -450,7 +515,7 @@ cclr_status cclr_residual(cclr_ctx* h, cclr_c128* out, cclr_c128* e_corr_out) {
     Scope sc(c.ws);
     cplx* R = c.ws.cplxs(c.N);
     ccsd_residual(c, R);
-    CCLR_CK(cudaMemcpyAsync(out, R, sizeof(cplx) * c.N, cudaMemcpyDeviceToHost, c.stream));
+    download(c, out, R, c.N);
     c.sync();
     if (e_corr_out) { zc e = ccsd_energy(c); e_corr_out->re = e.real(); e_corr_out->im = e.imag(); }
   });
@@ -459,12 +524,13 @@ cclr_status cclr_residual(cclr_ctx* h, cclr_c128* out, cclr_c128* e_corr_out) {
 cclr_status cclr_xi(cclr_ctx* h, const cclr_c128* op, cclr_c128* out) {
   return guard(h, [&](Ctx& c) {
     CCLR_REQUIRE(c.have_t && op && out, CCLR_E_STATE, "xi needs T");
+    PrecisionScope exact(c, exact_precision(c));
     Scope sc(c.ws);
     cplx* X = c.ws.cplxs((int64_t)c.n * c.n);
     upload(c, X, op, (int64_t)c.n * c.n);
     cplx* r = c.ws.cplxs(c.N);
     xi_vec(c, X, r);
-    CCLR_CK(cudaMemcpyAsync(out, r, sizeof(cplx) * c.N, cudaMemcpyDeviceToHost, c.stream));
+    download(c, out, r, c.N);
     c.sync();
   });
 }
@@ -472,12 +538,13 @@ cclr_status cclr_xi(cclr_ctx* h, const cclr_c128* op, cclr_c128* out) {
 cclr_status cclr_eta(cclr_ctx* h, const cclr_c128* op, int eom, cclr_c128* out) {
   return guard(h, [&](Ctx& c) {
     CCLR_REQUIRE(c.have_lambda && op && out, CCLR_E_STATE, "eta needs Lambda");
+    PrecisionScope exact(c, exact_precision(c));
     Scope sc(c.ws);
     cplx* X = c.ws.cplxs((int64_t)c.n * c.n);
     upload(c, X, op, (int64_t)c.n * c.n);
     cplx* r = c.ws.cplxs(c.N);
     eta_vec(c, X, eom != 0, r);
-    CCLR_CK(cudaMemcpyAsync(out, r, sizeof(cplx) * c.N, cudaMemcpyDeviceToHost, c.stream));
+    download(c, out, r, c.N);
     c.sync();
   });
 }
@@ -485,6 +552,7 @@ cclr_status cclr_eta(cclr_ctx* h, const cclr_c128* op, int eom, cclr_c128* out) 
 cclr_status cclr_hessian(cclr_ctx* h, int nvec, const cclr_c128* u, cclr_c128* out, int on_device) {
   return guard(h, [&](Ctx& c) {
     CCLR_REQUIRE(c.have_lambda && u && out && nvec >= 1, CCLR_E_STATE, "hessian needs Lambda");
+    PrecisionScope exact(c, exact_precision(c));
     Scope sc(c.ws);
     IO io(c, u, out, (int64_t)nvec * c.N, (int64_t)nvec * c.N, on_device != 0);
     hessian_right(c, nvec, io.in, io.dout);
@@ -662,6 +730,46 @@ cclr_status cclr_kernel_breakdown(cclr_ctx* h, char* buf, int cap) {
 cclr_status cclr_debug_expire_next_wait(cclr_ctx* h, unsigned polls) {
   if (!h || polls == 0) return CCLR_E_ARG;
   h->c.dbg_wait_polls = polls;
+  return CCLR_OK;
+}
+
+cclr_status cclr_response_batch(cclr_ctx* const* ctxs, int n, int n_ops, const cclr_c128* const* ops, int n_freq,
+                                const double* omegas, double gamma, cclr_c128* const* out, cclr_status* status) {
+  if (!ctxs || n < 1 || !ops || !out || !omegas) return CCLR_E_ARG;
+  for (int k = 0; k < n; ++k)
+    if (!ctxs[k] || !ops[k] || !out[k]) return CCLR_E_ARG;
+  std::vector<cclr_status> st(n, CCLR_OK);
+  auto one = [&](int k) {   // the whole response path of system k on its context's stream
+    cclr_ctx* h = ctxs[k];
+    cclr_status r = cc_ground(h, nullptr, nullptr);
+    if (r == CCLR_OK) r = cc_lambda(h, nullptr);
+    if (r == CCLR_OK) r = cc_lr_solve(h, n_ops, ops[k], n_freq, omegas, gamma, nullptr);
+    if (r == CCLR_OK) r = cc_response_function(h, out[k]);
+    st[k] = r;
+  };
+  std::vector<std::thread> th;
+  try {
+    for (int k = 1; k < n; ++k) th.emplace_back(one, k);
+  } catch (...) {
+    for (auto& t : th) t.join();
+    return CCLR_E_ARG;
+  }
+  one(0);
+  for (auto& t : th) t.join();
+  cclr_status first = CCLR_OK;
+  for (int k = 0; k < n; ++k) {
+    if (status) status[k] = st[k];
+    if (first == CCLR_OK) first = st[k];
+  }
+  return first;
+}
+
+cclr_status cclr_autotune_report(cclr_ctx* h, char* buf, int cap) {
+  if (!h || !buf || cap < 1) return CCLR_E_ARG;
+  const std::string out = tc_tune_report();
+  const size_t n = std::min<size_t>(out.size(), (size_t)cap - 1);
+  std::memcpy(buf, out.data(), n);
+  buf[n] = 0;
   return CCLR_OK;
 }
 

@@ -52,7 +52,7 @@ void expand_t2(Ctx& c, const cplx* packed, cplx* full, int64_t nvec) {
   // packed: nvec contiguous blocks of Po*Pv; full: nvec x (o,o,v,v)
   Tensor X = Tensor::make(full, {nvec, (int64_t)c.o, (int64_t)c.o, (int64_t)c.v, (int64_t)c.v});
   unpack_doubles(c.L, packed, c.Po * c.Pv, X, c.o, c.v);
-  if (full == c.t2 || full == c.l2) ++data_generation();   // cached tensor-core slices are stale
+  if (full == c.t2 || full == c.l2) ++c.data_gen;   // cached tensor-core slices are stale
 }
 
 void pack_anti(Ctx& c, const Tensor& X, cplx* D, int64_t nvec, cplx alpha, bool anti, bool acc) {

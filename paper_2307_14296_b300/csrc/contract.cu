@@ -154,7 +154,7 @@ void einsum_impl(Ctx& c, const char* spec, cplx alpha, const Tensor& A, const Te
         fl.erase(fl.find(unit), 1);
         fl += unit;
       }
-      if (tc_splits(M, N, K, c.opt.precision) == 1 && !fl.empty() && !fr.empty() && fl.size() <= 4 && fr.size() <= 4) {
+      if (tc_splits(c, M, N, K, true) == 1 && !fl.empty() && !fr.empty() && fl.size() <= 4 && fr.size() <= 4) {
         const Tensor vl = lane_b ? reorder(B, s.b, fl + korder) : reorder(A, s.a, fl + korder);
         const Tensor vr = lane_b ? reorder(A, s.a, fr + korder) : reorder(B, s.b, fr + korder);
         OutAxes oa;

@@ -37,14 +37,28 @@ int tc_slices(int precision);        // BF16 slices per operand in a tensor-core
 // views is reserved from the context's arena at construction (declare it after the Scope that
 // should release that space).  No effect in the FP64 mode.
 struct SliceMemo {
+  Ctx& c;
   bool active = false;
   SliceMemo(Ctx& c, const void* src, int64_t elems, int views);
   ~SliceMemo();
   SliceMemo(const SliceMemo&) = delete;
   SliceMemo& operator=(const SliceMemo&) = delete;
 };
+// While alive, the listed device ranges (pointer, bytes) hold values on a grid of 2^(e - 14), e the
+// exponent with |x| < 2^e of the largest element: exactly two FP64-class digits in every operand
+// view, so the FP64-class GEMMs skip the digit products that involve their lower digits.
+struct CoarseOperands {
+  Ctx& c;
+  int n = 0;
+  CoarseOperands(Ctx& c, std::initializer_list<std::pair<const void*, size_t>> ranges);
+  ~CoarseOperands();
+  CoarseOperands(const CoarseOperands&) = delete;
+  CoarseOperands& operator=(const CoarseOperands&) = delete;
+};
+struct TcState;                      // per-context state of the tensor-core path (tc_gemm.cu)
 void tc_release_cache_for(Ctx& c);   // frees the cached BF16 slices of persistent operands
-size_t tc_cache_bytes();             // bytes held by that cache
+size_t tc_cache_bytes(Ctx& c);       // bytes held by that cache
+void tc_state_free(Ctx& c);          // frees all of it
 
 struct Ctx {
   int device = 0;
@@ -98,6 +112,11 @@ struct Ctx {
   // test of the expiry path: the next tensor-core GEMM launch gets this poll limit and a first
   // wait that nothing completes (0 = no test pending)
   uint32_t dbg_wait_polls = 0;
+  // sigma inputs rounded to the coarse grid (round_coarse): the sigma products mark their
+  // gathered copies as CoarseOperands
+  bool coarse_sigma = false;
+  TcState* tcs = nullptr;      // slice cache, memos, coarse ranges, autotuner launches
+  uint64_t data_gen = 1;       // bumped whenever integrals, T, Lambda or Hbar change
   KernelTimer kt;   // per-kernel timing (switched on with the tensor-core timing)
   bool prof = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
@@ -182,11 +201,7 @@ inline double mixed_floor(const Ctx& c) { return c.opt.refine_tol > 0.0 ? c.opt.
 void gemm_dispatch(Ctx& c, bool ta, bool tb, int64_t M, int64_t N, int64_t K, cplx alpha, const cplx* A,
                    int64_t lda, const cplx* B, int64_t ldb, cplx beta, cplx* C, int64_t ldc);
 
-// tensor-core backend state (tc_gemm.cu): cached BF16 slices of static operands are valid for one
-// Hbar generation
-uint64_t& hbar_generation();
-uint64_t& data_generation();   // bumped whenever integrals, T, Lambda or Hbar change
-void tc_release_cache();
+
 bool tc_eligible(int64_t M, int64_t N, int64_t K);
 // C[m*ldc + n] = alpha sum_k vm[m,k] vn[n,k] + beta C on the tensor cores; the first nrm / nrn
 // axes of the views are the rows, the remaining axes K (in the same order in both views)
@@ -198,7 +213,10 @@ struct OutAxes {
 };
 void tc_gemm_views(Ctx& c, const Tensor& vm, int nrm, const Tensor& vn, int nrn, cplx alpha, cplx beta, cplx* C,
                    int64_t ldc, const OutAxes* oa = nullptr);
-int tc_splits(int64_t M, int64_t N, int64_t K, int precision);   // split-K slices the tensor-core GEMM would use
+// split-K slices the tensor-core GEMM would use for this shape (strided: output through a row map)
+int tc_splits(const Ctx& c, int64_t M, int64_t N, int64_t K, bool strided);
+void tc_tune_collect(Ctx& c);    // resolves the tile autotuner's timed launches (after a stream sync)
+std::string tc_tune_report();    // decided tile shapes, one line per GEMM shape
 
 // equations (ccsd.cu, sigma.cu, props.cu)
 void build_denominators(Ctx& c);
@@ -210,6 +228,8 @@ void sigma_left(Ctx& c, int nvec, const cplx* in, cplx* out);
 void xi_vec(Ctx& c, const cplx* X, cplx* out);
 void eta_vec(Ctx& c, const cplx* X, bool eom, cplx* out);
 void hessian_right(Ctx& c, int nvec, const cplx* in, cplx* out);
+void xi_density(Ctx& c, const cplx* l, cplx* D);     // D: l . xi^X = sum D[p,q] X[p,q]
+void eta_density(Ctx& c, const cplx* v, cplx* D);    // D: eta^X . v = sum D[p,q] X[p,q]
 void eta_ground(Ctx& c, cplx* out);
 void expand_t2(Ctx& c, const cplx* packed, cplx* full, int64_t nvec);   // packed doubles -> o,o,v,v
 void pack_anti(Ctx& c, const Tensor& X, cplx* D, int64_t nvec, cplx alpha, bool anti, bool acc);
@@ -222,6 +242,8 @@ void lr_solve(Ctx& c, int n_ops, const cplx* ops_host, int n_freq, const double*
               int* iters_out);
 void response_function(Ctx& c, cplx* out_host);
 void response_function_ci(Ctx& c, cplx* out_host);
+void response_gradient(Ctx& c, int f, cplx* out_host);   // operator gradient of <<X;Y>> (adjoint)
+void left_solve(Ctx& c, int nrhs, const cplx* rhs, zc w, cplx* out);   // l (A + w) = -b
 int eom_ee(Ctx& c, int nroots, std::vector<zc>& w_out);
 
 // small dense complex linear algebra on the host

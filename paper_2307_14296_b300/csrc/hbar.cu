@@ -10,7 +10,7 @@ namespace cclr {
 static inline Tensor T(cplx* p, std::initializer_list<int64_t> d) { return Tensor::make(p, d); }
 
 void build_hbar(Ctx& c) {
-  ++hbar_generation();
+  ++c.data_gen;
   const int64_t o = c.o, v = c.v, Po = c.Po, Pv = c.Pv;
   auto ensure = [&](cplx*& p, int64_t n) { if (!p) p = c.dalloc(n); };
   ensure(c.Fae, v * v);

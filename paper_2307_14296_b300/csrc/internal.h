@@ -177,6 +177,9 @@ struct Launch {  // stream + launch counter shared by all kernels of one context
 void permute(const Launch& L, const Tensor& src, const Tensor& dst, cplx alpha, bool accumulate);
 void fill_zero(const Launch& L, cplx* p, int64_t n);
 void flag_nonfinite(const Launch& L, const cplx* p, int64_t n, int* flag);   // *flag = 1 on inf / NaN
+// x <- x rounded to the grid 2^(e - 14) of its largest element (|x| < 2^e): 15 significant bits
+// relative to that element, exactly two FP64-class digits in any view (scratch: one word)
+void round_coarse(const Launch& L, cplx* x, int64_t n, unsigned* scratch);
 void fill_hash(const Launch& L, cplx* p, int64_t n, uint64_t seed);   // deterministic values in [-1, 1)^2
 
 // Row-major complex FP64 GEMM: C[MxN] = alpha op(A) op(B) + beta C; op(A)[m,k] = ta ? A[k*lda+m]

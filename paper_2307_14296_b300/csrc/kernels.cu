@@ -182,6 +182,30 @@ __global__ void k_fill_hash(cplx* p, int64_t n, uint64_t seed) {
   }
 }
 
+// *out = largest biased binary64 exponent of the real and imaginary parts (out zeroed beforehand)
+__global__ void k_max_bexp(const cplx* __restrict__ x, int64_t n, unsigned* out) {
+  unsigned m = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const cplx v = x[i];
+    m = max(m, max((unsigned)((uint64_t)__double_as_longlong(v.x) >> 52) & 0x7ffu,
+                   (unsigned)((uint64_t)__double_as_longlong(v.y) >> 52) & 0x7ffu));
+  }
+  m = __reduce_max_sync(0xffffffffu, m);
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
+}
+// x <- x rounded to the nearest multiple of 2^(e - 14), e = *bexp - 1022 (|x| < 2^e for all x)
+__global__ void k_round_grid(cplx* x, int64_t n, const unsigned* bexp) {
+  const unsigned b = *bexp;
+  if (b == 0u || b == 0x7ffu) return;
+  const int k = (int)b - 1036;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    cplx v = x[i];
+    v.x = scalbn(rint(scalbn(v.x, -k)), k);
+    v.y = scalbn(rint(scalbn(v.y, -k)), k);
+    x[i] = v;
+  }
+}
+
 // *flag = 1 if any real or imaginary part is an infinity or a NaN
 __global__ void k_nonfinite(const cplx* __restrict__ p, int64_t n, int* flag) {
   bool bad = false;
@@ -569,21 +593,91 @@ template <> struct Arith<true> {
   }
   __device__ static X opnd(cplx v) { return opnd(d2f2(v)); }
   __device__ static Acc zero() { return 0ull; }
+  __device__ static X zero_x() { return X{0ull, 0ull}; }
+  __device__ static C zero_c() { return C{0ull, 0ull}; }
   __device__ static void mac(Acc& acc, const C& c, const X& x) {
     acc = ffma2(c.re, x.a, acc);
     acc = ffma2(c.im, x.b, acc);
   }
 };
+// Float-float (double-FP32) complex numbers: value = (rh + rl) + i (ih + il), |rl| <= ulp(rh)/2.
+struct __align__(16) FF2 {
+  float rh, rl, ih, il;
+};
+// x = h + l: h = x rounded to binary32, l = the exact remainder x - h rounded to binary32 (about
+// 48 significant bits in all), on the integer pipe.  Remainders below the binary32 normal range
+// are dropped, so |x| below ~2^-90 (1e-27) keeps fewer bits, down to 24 (checked against binary64
+// on 2e4 values spanning 1e-30..1e30: h + l within 2^-47 of x for |x| above that).
+__device__ __forceinline__ void split_ff(double x, float& h, float& l) {
+  h = d2f(x);
+  l = 0.f;
+  const uint64_t bx = (uint64_t)__double_as_longlong(x);
+  const int e = (int)((bx >> 52) & 0x7ffu);
+  const uint32_t uh = __float_as_uint(h), eh = (uh >> 23) & 0xffu;
+  if (e == 0 || e == 0x7ff || eh == 0u || eh == 0xffu) return;
+  // |x| = M 2^(e - 1075), |h| = Mh 2^(eh - 150) = (Mh << sh) 2^(e - 1075)
+  const int64_t M = (int64_t)((bx & 0xFFFFFFFFFFFFFull) | (1ull << 52));
+  const int64_t Mh = (int64_t)((uh & 0x7fffffu) | 0x800000u);
+  const int sh = (int)eh - e + 925;   // 29, or 30 when rounding carried into the next binade
+  const int64_t k = M - (Mh << sh);   // |k| < 2^29
+  if (k == 0) return;
+  const uint32_t a = (uint32_t)(k < 0 ? -k : k);
+  const int msb = 31 - __clz(a);
+  uint32_t m;
+  int p = msb;
+  if (msb > 23) {
+    m = (a + (1u << (msb - 24))) >> (msb - 23);   // round half up to 24 bits
+    if (m >> 24) { m >>= 1; ++p; }
+  } else {
+    m = a << (23 - msb);
+  }
+  const int be = p + e - 948;   // binary32 biased exponent of |k| 2^(e - 1075)
+  if (be <= 0) return;
+  const uint32_t sx = (uint32_t)(bx >> 63) ^ (k < 0 ? 1u : 0u);
+  l = __uint_as_float((sx << 31) | ((uint32_t)be << 23) | (m & 0x7fffffu));
+}
+// (H, L) += s (ah + al)(bh + bl) with the products of the high parts exact (FMA) and the sum
+// compensated (TwoSum); s = +1 or -1.  Round-to-nearest intrinsics keep the compiler from
+// contracting or reassociating the error terms.
+__device__ __forceinline__ void ff_prod_acc(float& H, float& L, float ah, float al, float bh, float bl, float s) {
+  const float p = __fmul_rn(ah, bh);
+  float e = __fmaf_rn(ah, bh, -p);
+  e = __fmaf_rn(ah, bl, e);
+  e = __fmaf_rn(al, bh, e);
+  const float ps = s * p, es = s * e;
+  const float t = __fadd_rn(H, ps);
+  const float v = __fsub_rn(t, H);
+  const float err = __fadd_rn(__fsub_rn(H, __fsub_rn(t, v)), __fsub_rn(ps, v));
+  H = t;
+  L = __fadd_rn(L, __fadd_rn(err, es));
+}
+// The "FP64" arithmetic of the solver's vector kernels: float-float on the FP32 pipe (~2^-46
+// relative per operation).  B300's FP64 pipe issues at 1/64 of the FP32 rate, so a complex
+// multiply-add in FP64 (4 DFMA) costs as much as ~256 FP32 operations; in float-float it is
+// about 48, with the inputs split once per element.
 template <> struct Arith<false> {
-  typedef cplx C;
-  typedef cplx X;
-  typedef cplx Acc;
-  __device__ static C coef(cplx c) { return c; }
-  __device__ static X opnd(cplx v) { return v; }
-  __device__ static Acc zero() { return make_double2(0.0, 0.0); }
+  typedef FF2 C;
+  typedef FF2 X;
+  typedef FF2 Acc;
+  __device__ static FF2 split(cplx v) {
+    FF2 r;
+    split_ff(v.x, r.rh, r.rl);
+    split_ff(v.y, r.ih, r.il);
+    return r;
+  }
+  __device__ static C coef(cplx c) { return split(c); }
+  __device__ static X opnd(cplx v) { return split(v); }
+  __device__ static Acc zero() { return FF2{0.f, 0.f, 0.f, 0.f}; }
+  __device__ static X zero_x() { return zero(); }
+  __device__ static C zero_c() { return zero(); }
   __device__ static void mac(Acc& acc, const C& c, const X& x) {
-    acc.x = fma(c.x, x.x, fma(-c.y, x.y, acc.x));
-    acc.y = fma(c.x, x.y, fma(c.y, x.x, acc.y));
+    ff_prod_acc(acc.rh, acc.rl, c.rh, c.rl, x.rh, x.rl, 1.f);
+    ff_prod_acc(acc.rh, acc.rl, c.ih, c.il, x.ih, x.il, -1.f);
+    ff_prod_acc(acc.ih, acc.il, c.rh, c.rl, x.ih, x.il, 1.f);
+    ff_prod_acc(acc.ih, acc.il, c.ih, c.il, x.rh, x.rl, 1.f);
+  }
+  __device__ static cplx to_cplx(const Acc& a) {
+    return make_double2(f2d(a.rh) + f2d(a.rl), f2d(a.ih) + f2d(a.il));
   }
 };
 
@@ -680,7 +774,8 @@ __global__ void __launch_bounds__(kThreads, F32 ? 2 : 1)
             const float2 v = upk2(a[e][q]);
             r = make_float2(v.x + b.x, v.y + b.y);
           } else {
-            r = make_double2(a[e][q].x + b.x, a[e][q].y + b.y);
+            const cplx v = A::to_cplx(a[e][q]);
+            r = make_double2(v.x + b.x, v.y + b.y);
           }
           if (!norm_y) nn[q] += r.x * r.x + r.y * r.y;
           if (D) {
@@ -893,8 +988,7 @@ __global__ void __launch_bounds__(kGramWarps * 32, 1)
 #pragma unroll
     for (int j = 0; j < NY; ++j) {
       if constexpr (X32) yv[j] = A::opnd(j < ny ? st[(nx + j) * pitch + k] : make_float2(0.f, 0.f));
-      else if constexpr (F32) yv[j] = j < ny ? reinterpret_cast<const PX*>(st)[(nx + j) * pitch + k] : PX{0ull, 0ull};
-      else yv[j] = A::opnd(j < ny ? st[(nx + j) * pitch + k] : make_double2(0.0, 0.0));
+      else yv[j] = j < ny ? reinterpret_cast<const PX*>(st)[(nx + j) * pitch + k] : A::zero_x();
     }
 #pragma unroll
     for (int a = 0; a < RL; ++a) {
@@ -904,12 +998,8 @@ __global__ void __launch_bounds__(kGramWarps * 32, 1)
         float2 xv = r < nx ? st[r * pitch + k] : make_float2(0.f, 0.f);
         if (herm) xv.y = -xv.y;
         xc = A::coef(xv);
-      } else if constexpr (F32) {
-        xc = r < nx ? reinterpret_cast<const PC*>(st)[r * pitch + k] : PC{0ull, 0ull};
       } else {
-        cplx xv = r < nx ? st[r * pitch + k] : make_double2(0.0, 0.0);
-        if (herm) xv.y = -xv.y;
-        xc = A::coef(xv);
+        xc = r < nx ? reinterpret_cast<const PC*>(st)[r * pitch + k] : A::zero_c();
       }
 #pragma unroll
       for (int j = 0; j < NY; ++j) A::mac(acc[a][j], xc, yv[j]);
@@ -936,17 +1026,24 @@ __global__ void __launch_bounds__(kGramWarps * 32, 1)
     SE* st = s ? st1 : st0;
     const int64_t base = ch << lc;
     const int lim = (int)min((int64_t)CH, n - base);
-    if constexpr (F32 && !X32) {
-      // in place: each FP64 element becomes its 16-byte FP32 packed form; a warp per row when
-      // there are enough rows, else all threads over the rows x chunk elements
+    if constexpr (!X32) {
+      // in place: each FP64 element becomes its 16-byte packed form (FP32 pairs, or the
+      // float-float split); a warp per row when there are enough rows, else all threads over the
+      // rows x chunk elements
       const float sg = herm ? -1.f : 1.f;   // coefficient of conj(x) for the Hermitian product
       auto pack = [&](cplx* p, bool xrow) {
-        const float2 v = d2f2(*p);
-        if (xrow) {
-          const float ci = sg * v.y;
-          *reinterpret_cast<PC*>(p) = PC{pk2(v.x, v.x), pk2(-ci, ci)};
+        if constexpr (F32) {
+          const float2 v = d2f2(*p);
+          if (xrow) {
+            const float ci = sg * v.y;
+            *reinterpret_cast<PC*>(p) = PC{pk2(v.x, v.x), pk2(-ci, ci)};
+          } else {
+            *reinterpret_cast<PX*>(p) = PX{pk2(v.x, v.y), pk2(v.y, v.x)};
+          }
         } else {
-          *reinterpret_cast<PX*>(p) = PX{pk2(v.x, v.y), pk2(v.y, v.x)};
+          cplx v = *p;
+          if (xrow && herm) v.y = -v.y;
+          *reinterpret_cast<FF2*>(p) = A::split(v);
         }
       };
       if (nr >= kGramWarps) {
@@ -989,7 +1086,7 @@ __global__ void __launch_bounds__(kGramWarps * 32, 1)
       if constexpr (F32) {
         v = make_double2((double)hi[a][j][0] + (double)lo[a][j][0], (double)hi[a][j][1] + (double)lo[a][j][1]);
       } else {
-        v = acc[a][j];
+        v = A::to_cplx(acc[a][j]);
       }
       red[((warp * RL + a) * NY + j) * 32 + lane] = v;
     }
@@ -1328,6 +1425,19 @@ void fill_hash(const Launch& L, cplx* p, int64_t n, uint64_t seed) {
   k_fill_hash<<<grid_for(n), kThreads, 0, L.s>>>(p, n, seed);
   CCLR_CK(cudaGetLastError());
   bump(L, "k_fill_hash");
+}
+
+void round_coarse(const Launch& L, cplx* x, int64_t n, unsigned* scratch) {
+  if (n <= 0) return;
+  CCLR_CK(cudaMemsetAsync(scratch, 0, sizeof(unsigned), L.s));
+  kbeg(L);
+  k_max_bexp<<<grid_for(n), kThreads, 0, L.s>>>(x, n, scratch);
+  CCLR_CK(cudaGetLastError());
+  bump(L, "k_max_bexp");
+  kbeg(L);
+  k_round_grid<<<grid_for(n), kThreads, 0, L.s>>>(x, n, scratch);
+  CCLR_CK(cudaGetLastError());
+  bump(L, "k_round_grid");
 }
 
 void flag_nonfinite(const Launch& L, const cplx* p, int64_t n, int* flag) {

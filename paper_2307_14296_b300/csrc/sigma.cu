@@ -70,6 +70,8 @@ void sigma_right(Ctx& c, int nvec, const cplx* in, cplx* out) {
   Scope sc(c.ws);
   const int64_t Z = nvec, o = c.o, v = c.v, Po = c.Po, Pv = c.Pv;
   Batch r = gather(c, Z, in, true);
+  const size_t cb = c.coarse_sigma ? sizeof(cplx) : 0;   // inputs on the coarse grid (refinement)
+  CoarseOperands coarse(c, {{r.s1, cb * Z * o * v}, {r.d2, cb * Z * c.Nd}, {r.full, cb * Z * o * o * v * v}});
   SliceMemo memo(c, r.full, Z * o * o * v * v, 3);   // r_ij^ab is read in three layouts
   Tensor t2 = T(c.t2, {o, o, v, v});
   Tensor Fae = T(c.Fae, {v, v}), Fmi = T(c.Fmi, {o, o}), Fme = T(c.Fme, {o, v});
@@ -125,6 +127,8 @@ void sigma_left(Ctx& c, int nvec, const cplx* in, cplx* out) {
   Scope sc(c.ws);
   const int64_t Z = nvec, o = c.o, v = c.v, Po = c.Po, Pv = c.Pv;
   Batch l = gather(c, Z, in, true);
+  const size_t cb = c.coarse_sigma ? sizeof(cplx) : 0;   // inputs on the coarse grid (refinement)
+  CoarseOperands coarse(c, {{l.s1, cb * Z * o * v}, {l.d2, cb * Z * c.Nd}, {l.full, cb * Z * o * o * v * v}});
   SliceMemo memo(c, l.full, Z * o * o * v * v, 3);   // l_ij^ab is read in three layouts
   Tensor t2 = T(c.t2, {o, o, v, v});
   Tensor Fae = T(c.Fae, {v, v}), Fmi = T(c.Fmi, {o, o}), Fme = T(c.Fme, {o, v});
@@ -256,6 +260,93 @@ void eta_vec(Ctx& c, const cplx* Xd, bool eom, cplx* out) {
     xi_vec(c, Xd, xi);
     einsum(c, "ijab,jb->ia", cx(1), l2, T(xi, {o, v}), 1.0, S1);
   }
+}
+
+// Operator densities: the n x n matrices D with l . xi^X = sum_pq D[p,q] X[p,q] (xi_density) and
+// eta^X . v = sum_pq D[p,q] X[p,q] (eta_density), the transposes of the xi and eta formulas above
+// (both are linear in X; bilinear products over unique excitations, doubles with the weights of
+// the antisymmetrizers).  l, v in the amplitude layout; D (device, n x n row-major) is written.
+namespace {
+struct Blocks {   // the oo, ov, vo, vv views of an n x n matrix
+  Tensor oo, ov, vo, vv;
+};
+Blocks blocks_of(cplx* D, int64_t o, int64_t v) {
+  const int64_t n = o + v;
+  auto blk = [&](bool ro, bool co) {
+    Tensor t = Tensor::make(D, {n, n});
+    t.dim[0] = ro ? o : v;
+    t.dim[1] = co ? o : v;
+    t.p = D + (ro ? 0 : o * n) + (co ? 0 : o);
+    return t;
+  };
+  return Blocks{blk(true, true), blk(true, false), blk(false, true), blk(false, false)};
+}
+}  // namespace
+
+void xi_density(Ctx& c, const cplx* l, cplx* D) {
+  Scope sc(c.ws);
+  const int64_t o = c.o, v = c.v, n = c.n;
+  fill_zero(c.L, D, n * n);
+  Blocks d = blocks_of(D, o, v);
+  Tensor t1 = T(c.t, {o, v}), t2 = T(c.t2, {o, o, v, v});
+  Tensor l1 = T((cplx*)l, {o, v});
+  cplx* l2f = c.ws.cplxs(o * o * v * v);
+  expand_t2(c, l + c.Ns, l2f, 1);
+  Tensor l2 = T(l2f, {o, o, v, v});
+  permute(c.L, l1.perm({1, 0}), d.vo, cx(1), false);                        // X_ai
+  einsum(c, "ia,ie->ae", cx(1), l1, t1, 1.0, d.vv);                          // X_ae t_i^e
+  einsum(c, "ia,ma->mi", cx(-1), l1, t1, 1.0, d.oo);                         // -X_mi t_m^a
+  cplx* k = c.ws.cplxs(o * o);
+  Tensor K = T(k, {o, o});
+  einsum(c, "ia,ma->im", cx(1), l1, t1, 0.0, K);
+  einsum(c, "ie,im->me", cx(-1), t1, K, 1.0, d.ov);                          // -X_me t_i^e t_m^a
+  einsum(c, "ia,imae->me", cx(1), l1, t2, 1.0, d.ov);                        // X_me t_im^ae
+  einsum(c, "ijab,ijaf->bf", cx(0.5), l2, t2, 1.0, d.vv);                    // P(ab) X_bf t_ij^af
+  einsum(c, "ijab,imab->mj", cx(-0.5), l2, t2, 1.0, d.oo);                   // -P(ij) X_mj t_im^ab
+  cplx* pim = c.ws.cplxs(o * o);
+  einsum(c, "ijab,mjab->im", cx(1), l2, t2, 0.0, T(pim, {o, o}));
+  einsum(c, "ie,im->me", cx(-0.5), t1, T(pim, {o, o}), 1.0, d.ov);           // -P(ij) X_me t_i^e t_mj^ab
+  cplx* qaf = c.ws.cplxs(v * v);
+  einsum(c, "ijab,ijfb->af", cx(1), l2, t2, 0.0, T(qaf, {v, v}));
+  einsum(c, "ma,af->mf", cx(-0.5), t1, T(qaf, {v, v}), 1.0, d.ov);           // -P(ab) X_mf t_m^a t_ij^fb
+}
+
+void eta_density(Ctx& c, const cplx* vv, cplx* D) {
+  CCLR_REQUIRE(c.have_lambda, CCLR_E_STATE, "eta density: Lambda not available");
+  Scope sc(c.ws);
+  const int64_t o = c.o, v = c.v, n = c.n;
+  fill_zero(c.L, D, n * n);
+  Blocks d = blocks_of(D, o, v);
+  Tensor t1 = T(c.t, {o, v}), t2 = T(c.t2, {o, o, v, v});
+  Tensor l1 = T(c.lam, {o, v}), l2 = T(c.l2, {o, o, v, v});
+  Tensor v1 = T((cplx*)vv, {o, v});
+  cplx* v2f = c.ws.cplxs(o * o * v * v);
+  expand_t2(c, vv + c.Ns, v2f, 1);
+  Tensor v2 = T(v2f, {o, o, v, v});
+  permute(c.L, v1, d.ov, cx(1), true);                                       // X_ia
+  einsum(c, "ie,ia->ea", cx(1), l1, v1, 1.0, d.vv);                          // X_ea l_i^e
+  einsum(c, "ia,ma->im", cx(-1), v1, l1, 1.0, d.oo);                         // -X_im l_m^a
+  cplx* ea = c.ws.cplxs(v * v);
+  einsum(c, "ie,ia->ea", cx(1), l1, v1, 0.0, T(ea, {v, v}));
+  einsum(c, "me,ea->ma", cx(-1), t1, T(ea, {v, v}), 1.0, d.ov);              // -X_ma t_m^e l_i^e
+  cplx* im = c.ws.cplxs(o * o);
+  einsum(c, "ia,ma->im", cx(1), v1, l1, 0.0, T(im, {o, o}));
+  einsum(c, "im,me->ie", cx(-1), T(im, {o, o}), t1, 1.0, d.ov);              // -X_ie t_m^e l_m^a
+  cplx* g = c.ws.cplxs(o * o);
+  einsum(c, "mnfe,mife->ni", cx(1), t2, l2, 0.0, T(g, {o, o}));
+  einsum(c, "ni,ia->na", cx(-0.5), T(g, {o, o}), v1, 1.0, d.ov);             // -1/2 G_ni X_na
+  cplx* h = c.ws.cplxs(v * v);
+  einsum(c, "nmfe,nmfa->ea", cx(1), t2, l2, 0.0, T(h, {v, v}));
+  einsum(c, "ea,ia->ie", cx(-0.5), T(h, {v, v}), v1, 1.0, d.ov);             // -1/2 H_ea X_ie
+  einsum(c, "ijab,ia->jb", cx(1), v2, l1, 1.0, d.ov);                        // P(ij)P(ab) l_i^a X_jb
+  cplx* kk = c.ws.cplxs(v * v);
+  einsum(c, "ijae,ijab->eb", cx(1), l2, v2, 0.0, T(kk, {v, v}));
+  permute(c.L, T(kk, {v, v}), d.vv, cx(0.5), true);                          // P(ab) l_ij^ae X_eb
+  einsum(c, "me,eb->mb", cx(-0.5), t1, T(kk, {v, v}), 1.0, d.ov);            // -P(ab) t_m^e l_ij^ae X_mb
+  cplx* jj = c.ws.cplxs(o * o);
+  einsum(c, "ijab,imab->jm", cx(1), v2, l2, 0.0, T(jj, {o, o}));
+  permute(c.L, T(jj, {o, o}), d.oo, cx(-0.5), true);                         // -P(ij) l_im^ab X_jm
+  einsum(c, "jm,me->je", cx(-0.5), T(jj, {o, o}), t1, 1.0, d.ov);            // -P(ij) t_m^e l_im^ab X_je
 }
 
 // eta of the Lambda equations: dE/dt = (F_me, <ij||ab>) in the amplitude layout

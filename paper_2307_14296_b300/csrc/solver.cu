@@ -168,7 +168,7 @@ int solve_ground(Ctx& c) {
   long v_ref = 0;
   fill_zero(c.L, c.t, N);
   fill_zero(c.L, c.t2, (int64_t)c.o * c.o * c.v * c.v);
-  ++data_generation();
+  ++c.data_gen;
   cplx* R = c.dalloc(N);
   cplx* hist_t = c.dalloc(kDiis * N);
   cplx* hist_e = c.dalloc(kDiis * N);
@@ -278,7 +278,7 @@ int solve_ground(Ctx& c) {
 
 // ------------------------------------------------------------------------------ Davidson
 struct System {            // one right-hand side with its shared trial space
-  const cplx* rhs;         // b (device, N)
+  const cplx* rhs = nullptr;   // b (device, N)
   std::vector<zc> z;       // shifts
   cplx *B = nullptr, *S = nullptr;
   // FP32 mirrors of B and S (tensor-core modes): the passes whose arithmetic is FP32 anyway
@@ -297,42 +297,62 @@ struct System {            // one right-hand side with its shared trial space
   int best_it = 0;
 };
 
-// Orthonormal directions (in the coefficient space of the trial vectors) spanning the solutions
-// [beta_1 ... beta_ns] of all shifts: Gram-Schmidt with column pivoting, stopping at kmax columns
-// or when the largest remaining column is below cut times the first.
-std::vector<std::vector<zc>> solution_directions(const System& s, double cut, int kmax) {
-  const int L = s.L, ns = (int)s.z.size();
-  std::vector<std::vector<zc>> cols(ns, std::vector<zc>(L));
-  for (int q = 0; q < ns; ++q)
-    for (int i = 0; i < L; ++i) cols[q][i] = s.beta[q][i];
+// Orthonormal vectors spanning the columns cols (each of length L): Gram-Schmidt with column
+// pivoting, stopping at kmax vectors or when the largest remaining column is below cut times the
+// first.  Each new vector is orthogonalised against the ones before it again (two passes): the
+// last directions come from columns reduced to ~cut of their size, whose one-pass projections
+// would lose orthogonality at eps / cut.  cols is overwritten.
+std::vector<std::vector<zc>> pivoted_orthonormal(std::vector<std::vector<zc>>& cols, int L, double cut, int kmax) {
+  const int ns = (int)cols.size();
   std::vector<std::vector<zc>> Q;
   std::vector<char> used(ns, 0);
   double first = -1.0;
+  auto dot = [&](const std::vector<zc>& a, const std::vector<zc>& b) {
+    zc d(0);
+    for (int i = 0; i < L; ++i) d += std::conj(a[i]) * b[i];
+    return d;
+  };
   while ((int)Q.size() < kmax) {
     int best = -1;
     double bn = 0.0;
     for (int q = 0; q < ns; ++q) {
       if (used[q]) continue;
       double nn = 0.0;
-      for (auto& x : cols[q]) nn += std::norm(x);
+      for (int i = 0; i < L; ++i) nn += std::norm(cols[q][i]);
       if (nn > bn) { bn = nn; best = q; }
     }
     if (best < 0) break;
-    const double nrm = std::sqrt(bn);
-    if (first < 0) first = nrm;
-    if (nrm <= cut * first) break;
+    if (first < 0) first = std::sqrt(bn);
+    if (std::sqrt(bn) <= cut * first) break;
     used[best] = 1;
-    std::vector<zc> qv(L);
-    for (int i = 0; i < L; ++i) qv[i] = cols[best][i] / nrm;
+    std::vector<zc> qv = cols[best];
+    for (auto& u : Q) {   // second pass against the earlier vectors
+      const zc d = dot(u, qv);
+      for (int i = 0; i < L; ++i) qv[i] -= d * u[i];
+    }
+    double nrm = 0.0;
+    for (int i = 0; i < L; ++i) nrm += std::norm(qv[i]);
+    nrm = std::sqrt(nrm);
+    if (!(nrm > 0.0)) continue;
+    for (int i = 0; i < L; ++i) qv[i] /= nrm;
     for (int q = 0; q < ns; ++q) {
       if (used[q]) continue;
-      zc d(0);
-      for (int i = 0; i < L; ++i) d += std::conj(qv[i]) * cols[q][i];
+      const zc d = dot(qv, cols[q]);
       for (int i = 0; i < L; ++i) cols[q][i] -= d * qv[i];
     }
     Q.push_back(qv);
   }
   return Q;
+}
+
+// Orthonormal directions (in the coefficient space of the trial vectors) spanning the solutions
+// [beta_1 ... beta_ns] of all shifts (pivoted_orthonormal).
+std::vector<std::vector<zc>> solution_directions(const System& s, double cut, int kmax) {
+  const int L = s.L, ns = (int)s.z.size();
+  std::vector<std::vector<zc>> cols(ns, std::vector<zc>(L));
+  for (int q = 0; q < ns; ++q)
+    for (int i = 0; i < L; ++i) cols[q][i] = s.beta[q][i];
+  return pivoted_orthonormal(cols, L, cut, kmax);
 }
 
 // Thick restart: compress the trial space onto the span of the current solutions of all shifts
@@ -384,16 +404,18 @@ void restart(Ctx& c, System& s, int maxL, int kmax) {
 }
 
 // Projects the nt candidate corrections R (device, nt x N; overwritten) against the trial space
-// B[0..L) with one classical Gram-Schmidt pass (R -= B (B^H R)), then appends up to kmax of them
-// to B[L..]: Gram-Schmidt among the candidates in their own Gram metric, in the given order; a
-// direction is kept only if at least 1% of its norm before projection (pre2: squared norms) lies
-// outside the trial space and the directions kept before it.  Returns the number appended.
-// cdev holds >= L * nt coefficients.
+// B[0..L) with two classical Gram-Schmidt passes (R -= B (B^H R), twice: the basis stays
+// orthonormal to working precision, so that coefficient-space compressions of the solutions are
+// compressions in the vector space), then appends up to kmax of them to B[L..]: Gram-Schmidt
+// among the candidates in their own Gram metric, in the given order; a direction is kept only if
+// at least 1% of its norm before projection (pre2: squared norms) lies outside the trial space
+// and the directions kept before it.  Returns the number appended.  cdev holds >= L * nt
+// coefficients.
 int add_corrections(Ctx& c, cplx* B, int L, cplx* R, int nt, const double* pre2, int kmax, cplx* cdev,
                     double* vscr, const void* Bf = nullptr, void* Rf = nullptr) {
   const int64_t N = c.N, Np = N + (N & 1);
   if (kmax <= 0 || nt <= 0) return 0;
-  if (L > 0) {
+  for (int pass = 0; pass < 2 && L > 0; ++pass) {
     std::vector<zc> g;
     if (Bf && Rf) {   // B^H R from the FP32 mirrors (R mirrored here)
       for (int t = 0; t < nt; ++t) to_f32(c.L, R + (int64_t)t * N, (float2*)Rf + (int64_t)t * Np, N);
@@ -462,8 +484,14 @@ int add_corrections(Ctx& c, cplx* B, int L, cplx* R, int nt, const double* pre2,
 //   projection: delta -= B (B^H delta), one classical Gram-Schmidt pass; the basis need not be
 //              orthonormal to working precision because B^H B enters the Galerkin matrices
 //   selection: Gram-Schmidt among the candidates in their own Gram metric, worst first
+//
+// coarse: every trial vector is rounded to the coarse grid of its largest element (round_coarse)
+// before its sigma vector is formed, and the sigma products treat their inputs as such (the
+// FP64-class contractions then need 9 instead of 15 digit products on the trial-vector operands).
+// The rounding only changes which trial vectors span the space; every sigma vector is the exact
+// product of the stored vector.
 void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, const cplx*, cplx*)>& Op,
-              int maxL, double tol) {
+              int maxL, double tol, bool coarse = false) {
   static const bool verbose = std::getenv("CCLR_VERBOSE") != nullptr;
   Fast32 f32(c);
   const bool mixed = mixed_precision(c.opt.precision);
@@ -477,6 +505,11 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
   cplx* zdev = c.ws.cplxs(kVecMatOut);
   double* n2dev = (double*)c.ws.alloc(sizeof(double) * kVecMatOut);
   cplx* R = c.ws.cplxs((int64_t)kTry * N);
+  unsigned* rscr = (unsigned*)c.ws.alloc(sizeof(unsigned));
+  auto round_rows = [&](cplx* X, int r0, int nr) {
+    if (coarse)
+      for (int r = r0; r < r0 + nr; ++r) round_coarse(c.L, X + (int64_t)r * N, N, rscr);
+  };
   // coefficients of r_q = S beta_q - z_q B beta_q over the rows [S | B]
   auto resid_coef = [&](const System& s, const std::vector<int>& qs, size_t g0, int m) {
     const int L = s.L;
@@ -552,6 +585,7 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
       scale_vec(c.L, N, cx(1.0 / nb), s.B);
       s.L = 1;
     }
+    round_rows(s.B, 0, s.L);
     mirror(s.B, s.Bf, 0, s.L);
   }
   std::vector<int> fresh(sys.size());   // new vectors at the end of each basis
@@ -573,6 +607,12 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
           copy_vec(c.L, N, sys[k].B + (int64_t)(sys[k].L - fresh[k] + j) * N, in + (int64_t)q * N);
       const int bmax = c.opt.batch > 0 ? c.opt.batch : total;
       double t0 = now();
+      struct CoarseFlag {   // the sigma products see coarse inputs while this is alive
+        Ctx& c;
+        bool old;
+        CoarseFlag(Ctx& cc, bool on) : c(cc), old(cc.coarse_sigma) { c.coarse_sigma = on; }
+        ~CoarseFlag() { c.coarse_sigma = old; }
+      } cf(c, coarse);
       for (int q0 = 0; q0 < total; q0 += bmax) {
         const int nb = std::min(bmax, total - q0);
         Op(nb, in + (int64_t)q0 * N, out + (int64_t)q0 * N);
@@ -732,6 +772,7 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
       // ---- project out the trial space and append the new directions
       ph.mark(c, "project");
       const int kk = add_corrections(c, s.B, s.L, R, nt, pre2, std::min(kMaxNew, maxL - s.L), cdev, vscr, s.Bf, Rf);
+      round_rows(s.B, s.L, kk);
       mirror(s.B, s.Bf, s.L, kk);
       if (kk == 0)
         throw Error(CCLR_E_NOCONV, "Davidson stagnated: residual " + std::to_string(order.front().first) +
@@ -781,7 +822,7 @@ void refine_systems(Ctx& c, std::vector<System>& sys, const std::function<void(i
     if (bases) (*bases)[k] = B2;
     if (sigs) (*sigs)[k] = S2;
   }
-  davidson(c, sys, Op, maxL, tol);
+  davidson(c, sys, Op, maxL, tol, true);
   c.stats.refine_vectors += c.stats.sigma_vectors - v0;
   c.stats.refine_seconds += now() - t0;
 }
@@ -863,7 +904,7 @@ void lr_solve(Ctx& c, int n_ops, const cplx* ops_host, int n_freq, const double*
   std::vector<System> sys(n_ops);
   for (int k = 0; k < n_ops; ++k) {
     cplx* X = c.dalloc(n * n);
-    CCLR_CK(cudaMemcpyAsync(X, ops_host + (int64_t)k * n * n, sizeof(cplx) * n * n, cudaMemcpyHostToDevice, c.stream));
+    CCLR_CK(cudaMemcpyAsync(X, ops_host + (int64_t)k * n * n, sizeof(cplx) * n * n, cudaMemcpyDefault, c.stream));
     rd.ops_dev.push_back(X);
     PrecisionScope exact(c, exact_precision(c));   // the right-hand sides define the answer
     cplx* xi = c.dalloc(N);
@@ -913,9 +954,8 @@ void lr_solve(Ctx& c, int n_ops, const cplx* ops_host, int n_freq, const double*
 void response_function(Ctx& c, cplx* out_host) {
   ResponseData& rd = c.rd;
   CCLR_REQUIRE(rd.solved, CCLR_E_STATE, "cc_response_function before cc_lr_solve");
-  // refined solutions: FP64 vector arithmetic and all Hessian directions above 1e-12; the Hessian
-  // products in the FP32-class tensor-core mode (the F term is quadratic in the solutions and
-  // carries a small part of <<X;Y>>, so its ~1e-6 relative error stays far below the target)
+  // refined solutions: the Hessian products in the FP64-class mode, FP64 vector arithmetic (the
+  // F term enters small components of <<X;Y>> at the 1e-6 level if formed in FP32 class)
   PrecisionScope exact(c, rd.refined ? CCLR_TC_F64 : c.opt.precision);
   Fast32 f32(c);
   const int64_t N = c.N;
@@ -931,8 +971,9 @@ void response_function(Ctx& c, cplx* out_host) {
   auto beta = [&](int k, int f, int s) { return &rd.beta[k][(size_t)rd.shift_of[(size_t)f * 4 + s] * maxL]; };
   // The Hessian acts only on the solutions t^X(-z) and t^X(z*) of every frequency.  Their
   // coefficient vectors span few directions: compress them (QR with column pivoting, cutoff
-  // 1e-12 of the largest in FP64 mode; 1e-7 in the tensor-core modes, whose sigma products carry
-  // ~1e-5 relative error) to Q_x, form the products F (B^x Q_x) in batches and contract them at once:
+  // 1e-12 of the largest in FP64 mode, 1e-10 for refined solutions; 1e-7 in the unrefined mixed
+  // modes, whose sigma products carry ~1e-5 relative error) to Q_x, form the products
+  // F (B^x Q_x) in batches and contract them at once:
   //   M^{xy} = (B^x Q_x F) . B^y,  (t^X F) . t^Y = gamma^T M^{xy} beta^Y,  gamma = Q_x^H beta^X.
   std::vector<std::vector<std::vector<zc>>> Q(nop);
   for (int x = 0; x < nop; ++x) {
@@ -940,32 +981,7 @@ void response_function(Ctx& c, cplx* out_host) {
     std::vector<std::vector<zc>> cols;
     for (int f = 0; f < rd.n_freq; ++f)
       for (int s : {3, 2}) cols.emplace_back(beta(x, f, s), beta(x, f, s) + Lx);
-    std::vector<char> used(cols.size(), 0);
-    double first = -1.0;
-    while ((int)Q[x].size() < Lx) {
-      int best = -1;
-      double bn = 0.0;
-      for (size_t q = 0; q < cols.size(); ++q) {
-        if (used[q]) continue;
-        double nn = 0.0;
-        for (auto& v : cols[q]) nn += std::norm(v);
-        if (nn > bn) { bn = nn; best = (int)q; }
-      }
-      if (best < 0) break;
-      const double nrm = std::sqrt(bn);
-      if (first < 0) first = nrm;
-      if (nrm <= (mixed_precision(c.opt.precision) ? 1e-7 : 1e-12) * first) break;
-      used[best] = 1;
-      std::vector<zc> qv(Lx);
-      for (int i = 0; i < Lx; ++i) qv[i] = cols[best][i] / nrm;
-      for (size_t q = 0; q < cols.size(); ++q) {
-        if (used[q]) continue;
-        zc d(0);
-        for (int i = 0; i < Lx; ++i) d += std::conj(qv[i]) * cols[q][i];
-        for (int i = 0; i < Lx; ++i) cols[q][i] -= d * qv[i];
-      }
-      Q[x].push_back(qv);
-    }
+    Q[x] = pivoted_orthonormal(cols, Lx, mixed_precision(c.opt.precision) ? 1e-7 : rd.refined ? 1e-10 : 1e-12, Lx);
     const int rx = (int)Q[x].size();
     for (int y = 0; y < nop; ++y) M[(size_t)x * nop + y].assign((size_t)rx * rd.nb[y], zc(0));
     const int bmax = std::max(1, std::min(c.opt.batch > 0 ? c.opt.batch : 8, rx));
@@ -980,10 +996,7 @@ void response_function(Ctx& c, cplx* out_host) {
       ph.mark(c, "combine");
       combine(c, rows(c, rd.basis[x], Lx), nb, W, yv);
       ph.mark(c, "hessian");
-      {
-        PrecisionScope hp(c, rd.refined ? CCLR_TC_BF16X6 : c.opt.precision);
-        hessian_right(c, nb, yv, fb);
-      }
+      hessian_right(c, nb, yv, fb);
       ph.mark(c, "gram");
       for (int y = 0; y < nop; ++y) {
         std::vector<zc> g;
@@ -1019,6 +1032,129 @@ void response_function(Ctx& c, cplx* out_host) {
         const zc val = half(f, x, y, 0, 3) + std::conj(half(f, x, y, 1, 2));
         out_host[((size_t)f * nop + x) * nop + y] = make_double2(val.real(), val.imag());
       }
+}
+
+// Gradient of the CC-CC response function with respect to the operators (adjoint method).
+// <<X;Y>>_z = f(z) + conj(f(-z*)), f(w) = 1/2 [eta^X t^Y(w) + eta^Y t^X(-w) + (t^X(-w) F) t^Y(w)],
+// t^X(w) = -(A - w)^{-1} xi^X, is linear in X and in Y through xi and eta.  Differentiating in
+// X at fixed Y (F is symmetric):
+//   d f(w) = 1/2 [eta^{dX} t^Y(w) + l^Y(w) xi^{dX}],  l^Y(w) (A + w) = -(eta^Y + F t^Y(w)),
+// one left solve (SI left sigma equations) per operator and shift, and the densities of
+// xi_density / eta_density turn the products into matrices over X's elements:
+//   G[k][s] = 1/2 [eta_density(t^k(w_s)) + xi_density(l^k(w_s))],  w_s the shift s of frequency f
+//   (0: w+ig, 1: -w+ig, 2: w-ig, 3: -w-ig), so that for operator perturbations dX_x, dX_y
+//   d<<X_x;X_y>> = sum G[y][0] o dX_x + conj(sum G[y][1] o dX_x) + sum G[x][3] o dX_y
+//                  + conj(sum G[x][2] o dX_y)        (o: element-wise product, sum over p, q).
+// out_host: n_ops x 4 matrices n x n.  Requires cc_lr_solve.
+void response_gradient(Ctx& c, int f, cplx* out_host) {
+  ResponseData& rd = c.rd;
+  CCLR_REQUIRE(rd.solved, CCLR_E_STATE, "cclr_response_gradient before cc_lr_solve");
+  CCLR_REQUIRE(f >= 0 && f < rd.n_freq, CCLR_E_ARG, "cclr_response_gradient: frequency index");
+  const int64_t N = c.N, n = c.n;
+  const int nop = rd.n_ops, maxL = std::max(8, c.opt.max_subspace);
+  // solution vectors t^k(w_s) and right-hand sides eta^k + F t^k(w_s) (FP64-class when refined)
+  std::vector<cplx*> tv, rhs, Bs, Ss;
+  auto cleanup = [&]() {
+    for (auto p : tv) c.dfree(p);
+    for (auto p : rhs) c.dfree(p);
+    for (auto p : Bs) c.dfree(p);
+    for (auto p : Ss) c.dfree(p);
+  };
+  try {
+    std::vector<System> sys(4 * nop);
+    {
+      PrecisionScope exact(c, rd.refined ? CCLR_TC_F64 : c.opt.precision);
+      Scope sc(c.ws);
+      cplx* bd = c.ws.cplxs(maxL);
+      for (int k = 0; k < nop; ++k)
+        for (int q = 0; q < 4; ++q) {
+          cplx* t = c.dalloc(N);
+          tv.push_back(t);
+          const zc* beta = &rd.beta[k][(size_t)rd.shift_of[(size_t)f * 4 + q] * maxL];
+          to_dev(c, beta, bd, rd.nb[k]);
+          lincomb(c.L, N, rd.nb[k], rd.basis[k], N, bd, t, false);
+          cplx* b = c.dalloc(N);
+          rhs.push_back(b);
+          hessian_right(c, 1, t, b);
+          axpy(c.L, N, cx(1), rd.eta[k], b);
+          System& s = sys[(size_t)4 * k + q];
+          s.rhs = b;
+          s.z = {-rd.shifts[rd.shift_of[(size_t)f * 4 + q]]};   // l (A - w_l) = -b with w_l = -w_s
+          s.B = c.dalloc((int64_t)maxL * N);
+          s.S = c.dalloc((int64_t)maxL * N);
+          Bs.push_back(s.B);
+          Ss.push_back(s.S);
+        }
+    }
+    auto op = [&](int nv, const cplx* in, cplx* out) { sigma_left(c, nv, in, out); };
+    davidson(c, sys, op, maxL, c.opt.tol);
+    if (refining(c)) refine_systems(c, sys, op, maxL, c.opt.tol, &Bs, &Ss);
+    PrecisionScope exact(c, rd.refined ? CCLR_TC_F64 : c.opt.precision);
+    Scope sc(c.ws);
+    cplx* l = c.ws.cplxs(N);
+    cplx* bd = c.ws.cplxs(maxL);
+    cplx* D1 = c.ws.cplxs(n * n);
+    cplx* D2 = c.ws.cplxs(n * n);
+    for (int k = 0; k < nop; ++k)
+      for (int q = 0; q < 4; ++q) {
+        const System& s = sys[(size_t)4 * k + q];
+        to_dev(c, s.beta[0].data(), bd, s.L);
+        lincomb(c.L, N, s.L, s.B, N, bd, l, false);
+        eta_density(c, tv[(size_t)4 * k + q], D1);
+        xi_density(c, l, D2);
+        axpy(c.L, n * n, cx(1), D2, D1);
+        scale_vec(c.L, n * n, cx(0.5), D1);
+        CCLR_CK(cudaMemcpyAsync(out_host + ((size_t)4 * k + q) * n * n, D1, sizeof(cplx) * n * n, cudaMemcpyDefault,
+                                c.stream));
+        c.sync();
+      }
+  } catch (...) {
+    cleanup();
+    throw;
+  }
+  cleanup();
+}
+
+// Left (adjoint) linear systems l_k (A + w) = -b_k for nrhs right-hand sides (host or device
+// memory, cudaMemcpyDefault) with one shift; the Lambda equations are the case b = eta of the
+// energy, w = 0.  The same Davidson (and refinement) as the Lambda solve.
+void left_solve(Ctx& c, int nrhs, const cplx* rhs, zc w, cplx* out) {
+  const int64_t N = c.N;
+  const int maxL = std::max(8, c.opt.max_subspace);
+  std::vector<System> sys(nrhs);   // refinement replaces B and S: free what the systems hold
+  auto cleanup = [&]() {
+    for (auto& s : sys) {
+      if (s.rhs) c.dfree(const_cast<cplx*>(s.rhs));
+      if (s.B) c.dfree(s.B);
+      if (s.S) c.dfree(s.S);
+    }
+  };
+  try {
+    for (int k = 0; k < nrhs; ++k) {
+      cplx* b = c.dalloc(N);
+      sys[k].rhs = b;
+      CCLR_CK(cudaMemcpyAsync(b, rhs + (int64_t)k * N, sizeof(cplx) * N, cudaMemcpyDefault, c.stream));
+      sys[k].z = {-w};
+      sys[k].B = c.dalloc((int64_t)maxL * N);
+      sys[k].S = c.dalloc((int64_t)maxL * N);
+    }
+    auto op = [&](int nv, const cplx* in, cplx* o) { sigma_left(c, nv, in, o); };
+    davidson(c, sys, op, maxL, c.opt.tol);
+    if (refining(c)) refine_systems(c, sys, op, maxL, c.opt.tol, nullptr, nullptr);
+    Scope sc(c.ws);
+    cplx* bd = c.ws.cplxs(maxL);
+    cplx* l = c.ws.cplxs(N);
+    for (int k = 0; k < nrhs; ++k) {
+      to_dev(c, sys[k].beta[0].data(), bd, sys[k].L);
+      lincomb(c.L, N, sys[k].L, sys[k].B, N, bd, l, false);
+      CCLR_CK(cudaMemcpyAsync(out + (int64_t)k * N, l, sizeof(cplx) * N, cudaMemcpyDefault, c.stream));
+      c.sync();
+    }
+  } catch (...) {
+    cleanup();
+    throw;
+  }
+  cleanup();
 }
 
 // CC-CI response function (Eq. CC-CI response function): no Hessian term; EOM-eta of the SI

@@ -24,6 +24,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <map>
+#include <mutex>
 
 namespace cclr {
 
@@ -170,25 +171,33 @@ __device__ __forceinline__ bool group_any(bool q) {
 constexpr int EPI_WARPS = 12;
 constexpr int EPI_THREADS = 32 * EPI_WARPS;
 constexpr int TC_THREADS = 64 + EPI_THREADS;
+// dynamic shared memory of k_tc_zgemm<BN, STAGES>
+constexpr int smem_bytes(int bn, int stages) {
+  return stages * (2 * A_PLANE + 2 * bn * BK * 2) + 1024 /*align*/ + 256 /*barriers*/ + 2 * bn * 8 /*row offsets*/;
+}
 
+template <int BN_, int ST_>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_tc_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int n_rows, int m_rows,
                int kblocks, int kb_per, Pairs pairs, double2 alpha, double2 beta, double2* __restrict__ C, int64_t ldc,
                int64_t cz, int* __restrict__ err, int xtiles, int ytiles, int nsplit, const OutMap om, bool strided,
                uint32_t polls, int expire_first) {
+  constexpr int BP_ = BN_ * BK * 2;            // bytes of one B-side BF16 plane tile
+  constexpr int SB_ = 2 * A_PLANE + 2 * BP_;     // bytes of one pipeline stage
+  constexpr int TC_ = 2 * BN_;                   // TMEM columns of one accumulator (Cr | Ci)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
-  uint64_t* empty = full + STAGES;
-  uint64_t* tfull = empty + STAGES;    // accumulator b holds a finished tile (MMA commit)
+  uint64_t* full = (uint64_t*)(smem + ST_ * SB_);
+  uint64_t* empty = full + ST_;
+  uint64_t* tfull = empty + ST_;    // accumulator b holds a finished tile (MMA commit)
   uint64_t* tempty = tfull + 2;        // accumulator b drained (all epilogue threads)
   uint64_t* done = tempty + 2;         // every MMA of this CTA has completed
   uint32_t* tmem_slot = (uint32_t*)(done + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
-  int64_t* moff = (int64_t*)(smem + STAGES * STAGE_BYTES + 256);   // [2][BN] strided row offsets
+  int64_t* moff = (int64_t*)(smem + ST_ * SB_ + 256);   // [2][BN_] strided row offsets
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
+    for (int s = 0; s < ST_; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
@@ -202,7 +211,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   }
   if (warp == 2) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(2 * TMEM_COLS));
+                 "r"(2 * TC_));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   fence_before();
@@ -219,30 +228,30 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
         const int z = t / xy, r = t - z * xy, y = r / xtiles, x = r - y * xtiles;
         const int kb0 = z * kb_per, kb1 = min(kblocks, kb0 + kb_per);
-        const int n0 = y * BM, m0 = x * BN;
+        const int n0 = y * BM, m0 = x * BN_;
         const int iters = (kb1 - kb0) * pairs.n;
         for (int it = 0; it < iters; ++it, ++g) {
-          const int s = g % STAGES;
-          const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
+          const int s = g % ST_;
+          const uint32_t ph = (uint32_t)(g / ST_) & 1u;
           // expire_first (tests of the expiry path): the first wait is for a phase that nothing
           // completes, so it runs out before any copy or MMA is issued
           const uint32_t par = (g == 0 && expire_first) ? ph : (ph ^ 1u);
           if (!mbar_wait(&empty[s], par, polls)) { atomicExch(err, 1); *abort_flag = 1; break; }
           if (*abort_flag) break;
           const int kb = kb0 + it / pairs.n, p = it % pairs.n;
-          uint8_t* st = smem + s * STAGE_BYTES;
-          mbar_expect_tx(&full[s], STAGE_BYTES);
+          uint8_t* st = smem + s * SB_;
+          mbar_expect_tx(&full[s], SB_);
           tma_load_3d(st, &tmA, kb * BK, n0, 2 * pairs.sa[p] + 0, &full[s]);
           tma_load_3d(st + A_PLANE, &tmA, kb * BK, n0, 2 * pairs.sa[p] + 1, &full[s]);
           tma_load_3d(st + 2 * A_PLANE, &tmB, kb * BK, m0, 2 * pairs.sb[p] + 0, &full[s]);
-          tma_load_3d(st + 2 * A_PLANE + B_PLANE, &tmB, kb * BK, m0, 2 * pairs.sb[p] + 1, &full[s]);
+          tma_load_3d(st + 2 * A_PLANE + BP_, &tmB, kb * BK, m0, 2 * pairs.sb[p] + 1, &full[s]);
         }
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
       // ---------------- MMA issuer (single thread)
-      constexpr uint32_t ID = idesc_bf16(BM, BN, false), IDN = idesc_bf16(BM, BN, true);
+      constexpr uint32_t ID = idesc_bf16(BM, BN_, false), IDN = idesc_bf16(BM, BN_, true);
       int g = 0, tl = 0;
       for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x, ++tl) {
         const int z = t / xy;
@@ -251,15 +260,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int b = tl & 1;
         if (!mbar_wait(&tempty[b], (((uint32_t)tl >> 1) & 1u) ^ 1u, polls)) { atomicExch(err, 4); *abort_flag = 1; break; }
         fence_after();
-        const uint32_t cr = tmem + b * TMEM_COLS, ci = cr + BN;
+        const uint32_t cr = tmem + b * TC_, ci = cr + BN_;
         bool ok = true;
         for (int it = 0; it < iters; ++it, ++g) {
-          const int s = g % STAGES;
-          const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
+          const int s = g % ST_;
+          const uint32_t ph = (uint32_t)(g / ST_) & 1u;
           if (!mbar_wait(&full[s], ph, polls)) { atomicExch(err, 2); *abort_flag = 1; ok = false; break; }
           fence_after();
-          const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
-          const uint32_t ar = base, ai = base + A_PLANE, br = base + 2 * A_PLANE, bi = br + B_PLANE;
+          const uint32_t base = smem_u32(smem + s * SB_);
+          const uint32_t ar = base, ai = base + A_PLANE, br = base + 2 * A_PLANE, bi = br + BP_;
 #pragma unroll
           for (int ks = 0; ks < BK / 16; ++ks) {
             const uint32_t off = ks * 32;  // 16 BF16 = 32 bytes along K inside the swizzle row
@@ -296,11 +305,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     int tl = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++tl) {
       const int z = t / xy, r = t - z * xy, y = r / xtiles, x = r - y * xtiles;
-      const int n0 = y * BM, m0 = x * BN;
+      const int n0 = y * BM, m0 = x * BN_;
       const int b = tl & 1;
       double2* Cz = C + (int64_t)z * cz;
-      int64_t* mo = moff + b * BN;
-      if (strided && et < BN) {
+      int64_t* mo = moff + b * BN_;
+      if (strided && et < BN_) {
         const int m = m0 + et;
         mo[et] = m < m_rows ? out_off((uint32_t)m, om.nm, om.mdim, om.mstr, om.mmul, om.mshr) : 0;
       }
@@ -314,12 +323,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         break;
       }
       fence_after();
-      const uint32_t acc = tmem + b * TMEM_COLS + lane_base;
+      const uint32_t acc = tmem + b * TC_ + lane_base;
 #pragma unroll 1
-      for (int c0 = 16 * ch; c0 < BN; c0 += 16 * (EPI_WARPS / 4)) {
+      for (int c0 = 16 * ch; c0 < BN_; c0 += 16 * (EPI_WARPS / 4)) {
         uint32_t rr[16], ri[16];
         tmem_ld16(acc + c0, rr);
-        tmem_ld16(acc + BN + c0, ri);
+        tmem_ld16(acc + BN_ + c0, ri);
         if (n < n_rows) {
           // the beta operands of the chunk are all loaded before any is used
           double2 old[16];
@@ -362,7 +371,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     fence_after();
     // the MMAs may still run if a role gave up early: wait (bounded) for all of them first
     if (!mbar_wait(done, 0, polls) && lane == 0) atomicExch(err, 5);
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TMEM_COLS));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TC_));
   }
 }
 
@@ -1061,24 +1070,58 @@ struct Slices {
   __nv_bfloat16* p = nullptr;
   int64_t rows = 0, K = 0, Kpad = 0;
   int nsl = 0;
+  int ndig = 0;   // FP64-class digits that can be nonzero (2 for operands on a coarse grid)
   CUtensorMap tm;
 };
 
-// Slices of persistent operands (integrals, Hbar, amplitudes) are kept keyed by pointer and view
-// layout.  Those of the integrals live until the Hamiltonian changes; the others for one
-// generation of the context's data (bumped whenever amplitudes, Lambda or Hbar change).  When the
-// cache is full, integral slices not read in the current generation are evicted, largest first.
+}  // namespace
+
+// Per-context state of the tensor-core path: the slice cache of persistent operands, the memos of
+// transient operands, the coarse operand ranges and the autotuner's timed launches.
 struct CacheEntry {
   Slices s;
   uint64_t gen = 0;    // data generation of the last use
   bool integral = false;
 };
-size_t entry_bytes(const CacheEntry& e) { return sizeof(__nv_bfloat16) * 2 * e.s.nsl * e.s.rows * e.s.Kpad; }
-std::map<std::string, CacheEntry>& cache() {
-  static std::map<std::string, CacheEntry> m;
-  return m;
+struct Memo {
+  const void* src = nullptr;
+  char* base = nullptr;
+  size_t cap = 0, used = 0;
+  std::vector<std::pair<std::string, Slices>> entries;
+};
+struct TunePending {
+  std::string key;
+  int cfg;
+  cudaEvent_t a, b;
+};
+struct TcState {
+  std::map<std::string, CacheEntry> cache;
+  uint64_t cache_gen = 0;
+  std::vector<Memo> memos;
+  std::vector<std::pair<const char*, const char*>> coarse;   // device ranges on a coarse grid
+  std::vector<TunePending> pending;
+};
+TcState& tcs(Ctx& c) {
+  if (!c.tcs) c.tcs = new TcState();
+  return *c.tcs;
 }
-uint64_t g_cache_gen = 0;
+
+namespace {
+
+// Device ranges whose values lie on a coarse fixed-point grid (CoarseOperands): their FP64-class
+// digits beyond the second are zero.
+bool is_coarse(Ctx& c, const void* p) {
+  const char* q = (const char*)p;
+  for (auto& r : tcs(c).coarse)
+    if (q >= r.first && q < r.second) return true;
+  return false;
+}
+
+// Slices of persistent operands (integrals, Hbar, amplitudes) are kept keyed by pointer and view
+// layout.  Those of the integrals live until the Hamiltonian changes; the others for one
+// generation of the context's data (bumped whenever amplitudes, Lambda or Hbar change).  When the
+// cache is full, integral slices not read in the current generation are evicted, largest first.
+size_t entry_bytes(const CacheEntry& e) { return sizeof(__nv_bfloat16) * 2 * e.s.nsl * e.s.rows * e.s.Kpad; }
 
 // View arguments of the split kernel: axes of extent 1 dropped, neighbours that are contiguous
 // in memory merged (within the row group and within the K group), division multipliers set.
@@ -1203,30 +1246,28 @@ bool is_persistent(const Ctx& c, const void* p) {
 // (the unpacked trial vectors of a sigma product: e.g. r_mn^ea over (m, n, e) for two singles
 // terms) are split once.  A SliceMemo names the operand, which must not change while it is
 // alive, and reserves workspace for its slices; memos nest.
-struct Memo {
-  const void* src = nullptr;
-  char* base = nullptr;
-  size_t cap = 0, used = 0;
-  std::vector<std::pair<std::string, Slices>> entries;
-};
-std::vector<Memo>& memos() {
-  static std::vector<Memo> m;
-  return m;
-}
 
 // Slices of view v (first nr axes = rows): from the cache for persistent operands, from the memo
 // of a transient operand named by a SliceMemo, else into the workspace.
+Slices get_slices_any(Ctx& c, const Tensor& v, int nr, int nsl);
 Slices get_slices(Ctx& c, const Tensor& v, int nr, int nsl) {
-  if (g_cache_gen != data_generation()) {
-    for (auto it = cache().begin(); it != cache().end();) {
+  Slices s = get_slices_any(c, v, nr, nsl);
+  s.ndig = (nsl == tc::x::NS && is_coarse(c, v.p)) ? 2 : nsl;
+  return s;
+}
+Slices get_slices_any(Ctx& c, const Tensor& v, int nr, int nsl) {
+  TcState& T = tcs(c);
+  auto& cache = T.cache;
+  if (T.cache_gen != c.data_gen) {
+    for (auto it = cache.begin(); it != cache.end();) {
       if (it->second.integral) {
         ++it;
         continue;
       }
       cudaFree(it->second.s.p);
-      it = cache().erase(it);
+      it = cache.erase(it);
     }
-    g_cache_gen = data_generation();
+    T.cache_gen = c.data_gen;
   }
   int64_t elems = 1;
   for (int i = 0; i < v.rank; ++i) elems *= v.dim[i];
@@ -1240,33 +1281,33 @@ Slices get_slices(Ctx& c, const Tensor& v, int nr, int nsl) {
     std::string key = std::to_string((uintptr_t)v.p) + "|" + std::to_string(nr) + "|" + std::to_string(nsl) + "|" +
                       std::to_string((int)v.conj);
     for (int i = 0; i < v.rank; ++i) key += "|" + std::to_string(v.dim[i]) + ":" + std::to_string(v.str[i]);
-    auto it = cache().find(key);
-    if (it != cache().end()) {
-      it->second.gen = data_generation();
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      it->second.gen = c.data_gen;
       return it->second.s;
     }
     const double cap = cap_gb * (double)(1ull << 30);
-    size_t cached = tc_cache_bytes();
+    size_t cached = tc_cache_bytes(c);
     while ((double)(cached + bytes) > cap) {   // evict the largest integral entry idle this generation
-      auto victim = cache().end();
-      for (auto e = cache().begin(); e != cache().end(); ++e)
-        if (e->second.integral && e->second.gen != data_generation() &&
-            (victim == cache().end() || entry_bytes(e->second) > entry_bytes(victim->second)))
+      auto victim = cache.end();
+      for (auto e = cache.begin(); e != cache.end(); ++e)
+        if (e->second.integral && e->second.gen != c.data_gen &&
+            (victim == cache.end() || entry_bytes(e->second) > entry_bytes(victim->second)))
           victim = e;
-      if (victim == cache().end()) break;
+      if (victim == cache.end()) break;
       cached -= entry_bytes(victim->second);
       cudaFree(victim->second.s.p);
-      cache().erase(victim);
+      cache.erase(victim);
     }
     __nv_bfloat16* dst = nullptr;
     if ((double)(cached + bytes) <= cap && cudaMalloc((void**)&dst, bytes) == cudaSuccess) {
       make_slices(c, v, nr, nsl, s, dst);
-      cache()[key] = CacheEntry{s, data_generation(), is_integral(c, v.p)};
+      cache[key] = CacheEntry{s, c.data_gen, is_integral(c, v.p)};
       return s;
     }
     cudaGetLastError();  // out of memory for the cache: fall through to a workspace copy
   }
-  for (auto it = memos().rbegin(); it != memos().rend(); ++it) {
+  for (auto it = T.memos.rbegin(); it != T.memos.rend(); ++it) {
     if (it->src != v.p) continue;
     std::string key = std::to_string(nr) + "|" + std::to_string(nsl) + "|" + std::to_string((int)v.conj);
     for (int i = 0; i < v.rank; ++i) key += "|" + std::to_string(v.dim[i]) + ":" + std::to_string(v.str[i]);
@@ -1287,7 +1328,18 @@ Slices get_slices(Ctx& c, const Tensor& v, int nr, int nsl) {
 
 }  // namespace
 
-SliceMemo::SliceMemo(Ctx& c, const void* src, int64_t elems, int views) {
+CoarseOperands::CoarseOperands(Ctx& cc, std::initializer_list<std::pair<const void*, size_t>> ranges) : c(cc) {
+  for (auto& r : ranges)
+    if (r.first && r.second) {
+      tcs(c).coarse.push_back({(const char*)r.first, (const char*)r.first + r.second});
+      ++n;
+    }
+}
+CoarseOperands::~CoarseOperands() {
+  for (int i = 0; i < n; ++i) tcs(c).coarse.pop_back();
+}
+
+SliceMemo::SliceMemo(Ctx& cc, const void* src, int64_t elems, int views) : c(cc) {
   if (c.opt.precision == CCLR_FP64 || src == nullptr) return;
   // each view: nsl slices x (re, im) BF16 planes, K padded to a multiple of BK per row
   const size_t want = (size_t)views * 2 * sizeof(__nv_bfloat16) * (size_t)tc_slices(c.opt.precision) *
@@ -1299,21 +1351,23 @@ SliceMemo::SliceMemo(Ctx& c, const void* src, int64_t elems, int views) {
   m.src = src;
   m.base = (char*)c.ws.alloc(cap);
   m.cap = cap;
-  memos().push_back(std::move(m));
+  tcs(c).memos.push_back(std::move(m));
   active = true;
 }
 SliceMemo::~SliceMemo() {
-  if (active) memos().pop_back();
+  if (active) tcs(c).memos.pop_back();
 }
 
 namespace {
 
-// Digit pairs (i, j) with i + j < 5 sorted by group: group i + j for i + j < 3, group 3 otherwise
-tc::PairsX pairs_x() {
+// Digit pairs (i, j) with i + j < 5, i < nda (A-side digits), j < ndb (B-side digits), sorted by
+// group: group i + j for i + j < 3, group 3 otherwise
+tc::PairsX pairs_x(int nda = tc::x::NS, int ndb = tc::x::NS) {
   tc::PairsX p{};
   p.n = 0;
   for (int g = 0; g < tc::x::NS; ++g)
     for (int i = 0; i <= g; ++i) {
+      if (i >= nda || g - i >= ndb) continue;
       p.sa[p.n] = i;
       p.sb[p.n] = g - i;
       p.grp[p.n] = std::min(g, tc::x::NG - 1);
@@ -1346,22 +1400,26 @@ tc::Pairs pairs_for(int nsl) {
 
 }  // namespace
 
-uint64_t& data_generation() {
-  static uint64_t g = 1;
-  return g;
+void tc_release_cache_for(Ctx& c) {   // cudaFree waits for the kernels still reading the slices
+  if (!c.tcs) return;
+  for (auto& kv : c.tcs->cache) cudaFree(kv.second.s.p);
+  c.tcs->cache.clear();
 }
-
-uint64_t& hbar_generation() { return data_generation(); }
-
-void tc_release_cache() {   // cudaFree waits for the kernels still reading the slices
-  for (auto& kv : cache()) cudaFree(kv.second.s.p);
-  cache().clear();
-}
-void tc_release_cache_for(Ctx&) { tc_release_cache(); }
-size_t tc_cache_bytes() {
+size_t tc_cache_bytes(Ctx& c) {
   size_t t = 0;
-  for (auto& kv : cache()) t += entry_bytes(kv.second);
+  if (c.tcs)
+    for (auto& kv : c.tcs->cache) t += entry_bytes(kv.second);
   return t;
+}
+void tc_state_free(Ctx& c) {
+  if (!c.tcs) return;
+  tc_release_cache_for(c);
+  for (auto& p : c.tcs->pending) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  delete c.tcs;
+  c.tcs = nullptr;
 }
 
 int tc_slices(int precision) {
@@ -1380,6 +1438,107 @@ bool tc_eligible(int64_t M, int64_t N, int64_t K) {
 // rows (m resp. n) and whose remaining axes are K (same order in both).
 // split-K slices for an output of M x N with K (1 = none): when the output has fewer tiles than
 // SMs, each slice >= 4 k-blocks
+namespace {
+
+// ---- tile autotuner of the split-BF16 kernel (cclr_options.autotune).  Two tile shapes:
+// 128 m-rows with 3 pipeline stages and 64 m-rows with 4 stages (the narrower tile gives more
+// CTAs and less padding on small or skinny outputs; the wider one halves the A-side reloads).
+// Tuning is online: the first launch of a GEMM shape (M, N, K, slice count, output map, SM
+// count) uses the first shape and the second launch the second, each timed with CUDA events on
+// the context's stream; later launches of that shape use the faster one.  No extra work is run.
+// With CCLR_AUTOTUNE_CACHE set, decisions are read from and appended to that file.
+struct TileCfg {
+  int bn, stages;
+};
+constexpr TileCfg kTileCfgs[2] = {{128, 3}, {64, 4}};
+struct TuneState {
+  int best = -1;           // decided configuration
+  int launched[2] = {};    // timed launches issued per configuration
+  float ms[2] = {-1.f, -1.f};
+};
+// decisions are shared by all contexts of the process (guarded by tune_mutex)
+std::map<std::string, TuneState>& tune_table() {
+  static std::map<std::string, TuneState> t;
+  return t;
+}
+std::mutex& tune_mutex() {
+  static std::mutex m;
+  return m;
+}
+std::string tune_key(int64_t M, int64_t N, int64_t K, int nsl, bool strided) {
+  return std::to_string(M) + "x" + std::to_string(N) + "x" + std::to_string(K) + "/" + std::to_string(nsl) + "/" +
+         (strided ? "s" : "c") + "/" + std::to_string(num_sms());
+}
+const char* tune_cache_path() { return std::getenv("CCLR_AUTOTUNE_CACHE"); }
+void tune_load() {
+  static bool loaded = false;
+  if (loaded) return;
+  loaded = true;
+  const char* path = tune_cache_path();
+  if (!path) return;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return;
+  char key[256];
+  int best = 0;
+  while (std::fscanf(f, "%255s %d", key, &best) == 2)
+    if (best == 0 || best == 1) tune_table()[key].best = best;
+  std::fclose(f);
+}
+// the configuration the next launch of this shape uses (no state change)
+int tune_peek(const Ctx& c, const std::string& key) {
+  if (!c.opt.autotune) return 0;
+  std::lock_guard<std::mutex> lk(tune_mutex());
+  tune_load();
+  auto it = tune_table().find(key);
+  if (it == tune_table().end()) return 0;
+  const TuneState& t = it->second;
+  if (t.best >= 0) return t.best;
+  return t.launched[0] == 0 ? 0 : (t.launched[1] == 0 ? 1 : 0);
+}
+
+}  // namespace
+
+// Resolves the timed launches of the tile autotuner on this context (after a stream synchronize).
+void tc_tune_collect(Ctx& c) {
+  if (!c.tcs) return;
+  std::lock_guard<std::mutex> lk(tune_mutex());
+  for (auto& p : c.tcs->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      TuneState& t = tune_table()[p.key];
+      t.ms[p.cfg] = ms;
+      if (t.best < 0 && t.ms[0] >= 0.f && t.ms[1] >= 0.f) {
+        t.best = t.ms[1] < t.ms[0] ? 1 : 0;
+        if (const char* path = tune_cache_path())
+          if (FILE* f = std::fopen(path, "a")) {
+            std::fprintf(f, "%s %d\n", p.key.c_str(), t.best);
+            std::fclose(f);
+          }
+      }
+    }
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  c.tcs->pending.clear();
+}
+
+// Decided tile shapes of the autotuner as text, "key bn stages ms0 ms1" per line.
+std::string tc_tune_report() {
+  std::lock_guard<std::mutex> lk(tune_mutex());
+  std::string out;
+  for (auto& kv : tune_table()) {
+    const TuneState& t = kv.second;
+    if (t.best < 0) continue;
+    char line[320];
+    std::snprintf(line, sizeof line, "%s %d %d %.4f %.4f\n", kv.first.c_str(), kTileCfgs[t.best].bn,
+                  kTileCfgs[t.best].stages, t.ms[0], t.ms[1]);
+    out += line;
+  }
+  return out;
+}
+
+namespace {
+
 // (bn: the m-rows of a tile, tc::BN or tc::x::BN)
 void tc_split_plan(int64_t M, int64_t N, int64_t K, int& S, int& kb_per, int bn = tc::BN) {
   const int kblocks = (int)((K + tc::BK - 1) / tc::BK);
@@ -1393,9 +1552,16 @@ void tc_split_plan(int64_t M, int64_t N, int64_t K, int& S, int& kb_per, int bn 
     S = (kblocks + kb_per - 1) / kb_per;   // no empty slice
   }
 }
-int tc_splits(int64_t M, int64_t N, int64_t K, int precision) {
+}  // namespace
+
+int tc_splits(const Ctx& c, int64_t M, int64_t N, int64_t K, bool strided) {
   int S, kb;
-  tc_split_plan(M, N, K, S, kb, precision == CCLR_TC_F64 ? tc::x::BN : tc::BN);
+  int bn = tc::x::BN;
+  if (c.opt.precision != CCLR_TC_F64) {
+    const int64_t Kpad = (K + tc::BK - 1) / tc::BK * tc::BK;
+    bn = kTileCfgs[tune_peek(c, tune_key(M, N, Kpad, tc_slices(c.opt.precision), strided))].bn;
+  }
+  tc_split_plan(M, N, K, S, kb, bn);
   return S;
 }
 
@@ -1441,7 +1607,7 @@ void tc_gemm_x(Ctx& c, const Slices& sn, const Slices& sm, cplx alpha, cplx beta
   float4* fstate = (float4*)c.ws.alloc(sizeof(float4) * (size_t)grid * tc::BM * tc::x::BN);
   // the B-side map with the 64-row box of this kernel (the cached map has 128-row boxes)
   const CUtensorMap tmB = make_map(sm.p, sm.rows, sm.Kpad, 2 * sm.nsl, tc::x::BN);
-  const tc::PairsX pairs = pairs_x();
+  const tc::PairsX pairs = pairs_x(sn.ndig, sm.ndig);
   // a real power-of-two alpha is applied exactly to the float-float sums (no FP64 multiply)
   float apow2 = 0.0f;
   if (S == 1 && alpha.y == 0.0 && alpha.x != 0.0) {
@@ -1492,22 +1658,38 @@ void tc_gemm_views(Ctx& c, const Tensor& vm, int nrm, const Tensor& vn, int nrn,
   }
   const tc::Pairs pairs = pairs_for(nsl);
   const int64_t M = sm.rows, N = sn.rows;
-  static bool attr[64] = {};
-  if (once_per_device(attr))
-    CCLR_CK(cudaFuncSetAttribute(tc::k_tc_zgemm, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES));
+  const bool strided = oa != nullptr;
+  const std::string key = tune_key(M, N, sn.Kpad, nsl, strided);
+  const int cfg = tune_peek(c, key);
+  const int bn = kTileCfgs[cfg].bn;
   const int kblocks = (int)(sn.Kpad / tc::BK);
   int S = 1, kb_per = kblocks;
-  tc_split_plan(M, N, sn.Kpad, S, kb_per);
+  tc_split_plan(M, N, sn.Kpad, S, kb_per, bn);
   CCLR_REQUIRE(!oa || S == 1, CCLR_E_ARG, "tc_gemm: strided output with split-K");
   const tc::OutMap om = oa ? out_map(*oa) : tc::OutMap();
-  const bool strided = oa != nullptr;
   cplx* P = nullptr;
   if (S > 1) P = c.ws.cplxs((int64_t)S * M * N);
-  const int64_t ytiles = (N + tc::BM - 1) / tc::BM, xtiles = (M + tc::BN - 1) / tc::BN;
+  const int64_t ytiles = (N + tc::BM - 1) / tc::BM, xtiles = (M + bn - 1) / bn;
   CCLR_REQUIRE(xtiles * ytiles * S < (int64_t)INT32_MAX, CCLR_E_ARG, "tc_gemm: too many tiles");
+  // the B-side map with this tile's box (the cached maps have 128-row boxes)
+  const CUtensorMap tmB = bn == 128 ? sm.tm : make_map(sm.p, sm.rows, sm.Kpad, 2 * sm.nsl, bn);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (c.prof) c.prof_events(e0, e1, 0);
   if (e0) CCLR_CK(cudaEventRecord(e0, c.stream));
+  // a launch of an undecided shape is timed for the autotuner
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  bool timed = false;
+  if (c.opt.autotune) {
+    std::lock_guard<std::mutex> lk(tune_mutex());
+    TuneState& t = tune_table()[key];
+    timed = t.best < 0 && t.launched[cfg] == 0;
+    if (timed) t.launched[cfg] = 1;
+  }
+  if (timed) {
+    CCLR_CK(cudaEventCreate(&t0));
+    CCLR_CK(cudaEventCreate(&t1));
+    CCLR_CK(cudaEventRecord(t0, c.stream));
+  }
   {
     // persistent: one CTA per SM (or per tile when there are fewer)
     const int grid = (int)std::min<int64_t>(xtiles * ytiles * S, num_sms());
@@ -1516,20 +1698,30 @@ void tc_gemm_views(Ctx& c, const Tensor& vm, int nrm, const Tensor& vn, int nrn,
     const int expire = c.dbg_wait_polls ? 1 : 0;
     c.dbg_wait_polls = 0;
     c.kt.begin(c.stream);
-    if (S > 1)
-      tc::k_tc_zgemm<<<grid, tc::TC_THREADS, tc::SMEM_BYTES, c.stream>>>(sn.tm, sm.tm, (int)N, (int)M, kblocks, kb_per, pairs,
-                                                              make_double2(1.0, 0.0), make_double2(0.0, 0.0), P, N,
-                                                              M * N, c.tc_err, (int)xtiles, (int)ytiles, S, om, false,
-                                                              polls, expire);
-    else
-      tc::k_tc_zgemm<<<grid, tc::TC_THREADS, tc::SMEM_BYTES, c.stream>>>(sn.tm, sm.tm, (int)N, (int)M, kblocks, kb_per, pairs,
-                                                              alpha, beta, C, ldc, 0, c.tc_err, (int)xtiles, (int)ytiles,
-                                                              1, om, strided, polls, expire);
+    auto launch = [&](auto kernel, int smem, bool* attr) {
+      if (once_per_device(attr))
+        CCLR_CK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+      if (S > 1)
+        kernel<<<grid, tc::TC_THREADS, smem, c.stream>>>(sn.tm, tmB, (int)N, (int)M, kblocks, kb_per, pairs,
+                                                         make_double2(1.0, 0.0), make_double2(0.0, 0.0), P, N, M * N,
+                                                         c.tc_err, (int)xtiles, (int)ytiles, S, om, false, polls, expire);
+      else
+        kernel<<<grid, tc::TC_THREADS, smem, c.stream>>>(sn.tm, tmB, (int)N, (int)M, kblocks, kb_per, pairs, alpha, beta,
+                                                         C, ldc, 0, c.tc_err, (int)xtiles, (int)ytiles, 1, om, strided,
+                                                         polls, expire);
+    };
+    static bool attr128[64] = {}, attr64[64] = {};
+    if (bn == 128) launch(tc::k_tc_zgemm<128, 3>, tc::smem_bytes(128, 3), attr128);
+    else launch(tc::k_tc_zgemm<64, 4>, tc::smem_bytes(64, 4), attr64);
     const cudaError_t le = cudaGetLastError();
     CCLR_REQUIRE(le == cudaSuccess, CCLR_E_CUDA,
                  std::string("tensor-core GEMM launch failed (") + cudaGetErrorString(le) + ") M=" + std::to_string(M) +
                      " N=" + std::to_string(N) + " K=" + std::to_string(sn.K) + " S=" + std::to_string(S));
-    c.kt.end(c.stream, "k_tc_zgemm");
+    c.kt.end(c.stream, bn == 128 ? "k_tc_zgemm" : "k_tc_zgemm<64>");
+  }
+  if (t0) {
+    CCLR_CK(cudaEventRecord(t1, c.stream));
+    tcs(c).pending.push_back({key, cfg, t0, t1});
   }
   if (e1) {
     CCLR_CK(cudaEventRecord(e1, c.stream));
@@ -1599,7 +1791,8 @@ int tc_raw_gemm_nt(int precision, int64_t M, int64_t N, int64_t K, const cplx* A
   const CUtensorMap tn = make_map(sn, N, p.Kpad, 2 * nsl, 128), tm = make_map(sm, M, p.Kpad, 2 * nsl, 128);
   static bool attr[64] = {};
   if (once_per_device(attr))   // per device: a call on another device needs its own attribute
-    CCLR_CK(cudaFuncSetAttribute(tc::k_tc_zgemm, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES));
+    CCLR_CK(cudaFuncSetAttribute(tc::k_tc_zgemm<tc::BN, tc::STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 tc::SMEM_BYTES));
   const tc::Pairs pairs = pairs_for(nsl);
   const int64_t ytiles = (N + tc::BM - 1) / tc::BM, xtiles = (M + tc::BN - 1) / tc::BN;
   const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
@@ -1607,11 +1800,11 @@ int tc_raw_gemm_nt(int precision, int64_t M, int64_t N, int64_t K, const cplx* A
   {
     const int grid = (int)std::min<int64_t>(xtiles * ytiles * p.S, num_sms());
     if (p.S > 1)
-      tc::k_tc_zgemm<<<grid, tc::TC_THREADS, tc::SMEM_BYTES, stream>>>(tn, tm, (int)N, (int)M, p.kblocks, p.kb_per, pairs, one,
+      tc::k_tc_zgemm<tc::BN, tc::STAGES><<<grid, tc::TC_THREADS, tc::SMEM_BYTES, stream>>>(tn, tm, (int)N, (int)M, p.kblocks, p.kb_per, pairs, one,
                                                             zero, P, N, M * N, err, (int)xtiles, (int)ytiles, p.S,
                                                             tc::OutMap(), false, tc::kWaitPolls, 0);
     else
-      tc::k_tc_zgemm<<<grid, tc::TC_THREADS, tc::SMEM_BYTES, stream>>>(tn, tm, (int)N, (int)M, p.kblocks, p.kb_per, pairs, one,
+      tc::k_tc_zgemm<tc::BN, tc::STAGES><<<grid, tc::TC_THREADS, tc::SMEM_BYTES, stream>>>(tn, tm, (int)N, (int)M, p.kblocks, p.kb_per, pairs, one,
                                                             zero, C, N, 0, err, (int)xtiles, (int)ytiles, 1,
                                                             tc::OutMap(), false, tc::kWaitPolls, 0);
     CCLR_CK(cudaGetLastError());

@@ -131,3 +131,47 @@ def test_refinement_without_iterations_left_is_noconv(pk):
     ctx = make_ctx(pk, inst, precision=pk.TC_BF16X3, ground_tol=1e-10, batch=8)
     ctx.cc_ground()
     ctx.close()
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+def test_response_function_matches_direct_evaluation(pk, prec):
+    """The response function evaluated in the trial spaces (compressed Hessian directions) equals
+    its definition evaluated from the full solution vectors, eta and Hessian products returned by
+    the library: f(z) = 1/2 [eta^X t^Y(z) + eta^Y t^X(-z) + (t^X(-z) F) t^Y(z)], <<X;Y>> = f(z) +
+    conj(f(-z*)).  16 damped frequencies (64 shifts per operator) grow trial spaces of ~60 vectors,
+    where a non-orthonormal basis made the coefficient-space compression drop vector-space
+    directions at the 1e-6 level.  FP64 mode and split BF16 with refinement."""
+    inst = synth.make_instance(8, 40)
+    om, gamma = np.linspace(0.05, 0.3, 16), 0.005
+    ctx, lib = solve(pk, inst, om, gamma, precision=prec, tol=1e-10, ground_tol=1e-11, batch=8, max_subspace=64)
+    eta = [ctx.cclr_eta(inst.ops[k]) for k in range(3)]
+    for f in (0, 15):
+        t = {(k, s): ctx.cclr_get_response_vector(k, f, s) for k in range(3) for s in range(4)}
+        Ft = {(k, s): ctx.cclr_hessian(t[(k, s)][None])[0] for k in range(3) for s in (2, 3)}
+
+        def half(x, y, sz, smz):
+            return 0.5 * (eta[x] @ t[(y, sz)] + eta[y] @ t[(x, smz)] + Ft[(x, smz)] @ t[(y, sz)])
+
+        direct = np.array([[half(x, y, 0, 3) + np.conj(half(x, y, 1, 2)) for y in range(3)] for x in range(3)])
+        assert np.abs(lib[f] - direct).max() < 1e-10 * np.abs(direct).max(), np.abs(lib[f] - direct).max()
+    ctx.close()
+
+
+def test_batch_of_uneven_systems_matches_single_solves(pk):
+    """cclr_response_batch: three systems of uneven size solved concurrently (one host thread and
+    stream each) give the response functions of the same systems solved one by one, and the
+    smallest matches the oracle."""
+    sizes = [(3, 8), (4, 12), (5, 14)]
+    insts = [synth.make_instance(o, v, seed=31 + k) for k, (o, v) in enumerate(sizes)]
+    om, gamma = [0.05, 0.3], 0.01
+    opt = dict(tol=1e-10, ground_tol=1e-11)
+    ctxs = [make_ctx(pk, inst, **opt) for inst in insts]
+    batch = pk.cclr_response_batch(ctxs, [inst.ops for inst in insts], om, gamma)
+    for c in ctxs:
+        c.close()
+    for k, inst in enumerate(insts):
+        ctx, single = solve(pk, inst, om, gamma, **opt)
+        ctx.close()
+        assert rel(batch[k], single) < 1e-12
+    ref = R.CCSystem(Ints.from_instance(insts[0])).response(insts[0].ops, [w + 1j * gamma for w in om], tol=1e-12)
+    assert rel(batch[0], ref) < 1e-9

@@ -134,3 +134,21 @@ def test_solver_gram_block(ctx, n, nx, ny, mirror):
     got = ctx.cclr_gram(X, Y, mirror=mirror)
     ref = np.conj(X) @ Y.T
     assert np.abs(got - ref).max() < 1e-6 * np.abs(ref).max()
+
+
+def test_tile_autotuner_decides_and_stays_correct(ctx):
+    """The first two launches of a GEMM shape run the 128-row and the 64-row tile (timed); the
+    third uses the faster.  All three results must be correct, and the report lists the shape with
+    both timings."""
+    M, N, K = 200, 900, 2000
+    A = synth.random_vector((M, K), 9, 1)
+    B = synth.random_vector((N, K), 9, 2)
+    ref = A @ B.T
+    for _ in range(3):
+        assert rel(ctx.cclr_zgemm_nt(A, B, precision=2), ref) < BOUND[2]
+    rep = ctx.cclr_autotune_report()
+    key = [k for k in rep if k.startswith(f"{M}x{N}x{(K + 63) // 64 * 64}/2/")]
+    assert key, rep
+    bn, stages, ms128, ms64 = rep[key[0]]
+    assert bn in (64, 128) and ms128 > 0 and ms64 > 0
+    assert (bn == 64) == (ms64 < ms128)
