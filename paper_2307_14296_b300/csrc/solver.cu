@@ -301,8 +301,11 @@ struct System {            // one right-hand side with its shared trial space
 // pivoting, stopping at kmax vectors or when the largest remaining column is below cut times the
 // first.  Each new vector is orthogonalised against the ones before it again (two passes): the
 // last directions come from columns reduced to ~cut of their size, whose one-pass projections
-// would lose orthogonality at eps / cut.  cols is overwritten.
-std::vector<std::vector<zc>> pivoted_orthonormal(std::vector<std::vector<zc>>& cols, int L, double cut, int kmax) {
+// would lose orthogonality at eps / cut.  cols is overwritten.  weights (when not null) receives,
+// per vector, the norm of its pivot column relative to the first: a bound on the component of any
+// column along that vector relative to the largest column.
+std::vector<std::vector<zc>> pivoted_orthonormal(std::vector<std::vector<zc>>& cols, int L, double cut, int kmax,
+                                                 std::vector<double>* weights = nullptr) {
   const int ns = (int)cols.size();
   std::vector<std::vector<zc>> Q;
   std::vector<char> used(ns, 0);
@@ -341,6 +344,7 @@ std::vector<std::vector<zc>> pivoted_orthonormal(std::vector<std::vector<zc>>& c
       for (int i = 0; i < L; ++i) cols[q][i] -= d * qv[i];
     }
     Q.push_back(qv);
+    if (weights) weights->push_back(std::sqrt(bn) / first);
   }
   return Q;
 }
@@ -490,11 +494,16 @@ int add_corrections(Ctx& c, cplx* B, int L, cplx* R, int nt, const double* pre2,
 // FP64-class contractions then need 9 instead of 15 digit products on the trial-vector operands).
 // The rounding only changes which trial vectors span the space; every sigma vector is the exact
 // product of the stored vector.
+// corr_prec >= 0: the sigma products of the vectors added after the first iteration run in that
+// (mixed) precision while the starting space keeps the ambient one; the residuals are then exact
+// only up to the mixed error of the added vectors' (small) components, a stagnating solve is
+// accepted, and the caller verifies (refine_systems).
 void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, const cplx*, cplx*)>& Op,
-              int maxL, double tol, bool coarse = false) {
+              int maxL, double tol, bool coarse = false, int corr_prec = -1) {
   static const bool verbose = std::getenv("CCLR_VERBOSE") != nullptr;
   Fast32 f32(c);
   const bool mixed = mixed_precision(c.opt.precision);
+  const bool approx = corr_prec >= 0;
   const int64_t N = c.N;
   const int kMaxNew = 4;   // new trial vectors per right-hand side and iteration (worst shifts first)
   const int kTry = 8;      // candidate corrections formed per right-hand side and iteration
@@ -612,7 +621,9 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
         bool old;
         CoarseFlag(Ctx& cc, bool on) : c(cc), old(cc.coarse_sigma) { c.coarse_sigma = on; }
         ~CoarseFlag() { c.coarse_sigma = old; }
-      } cf(c, coarse);
+      } cf(c, coarse && !(approx && it > 1));
+      std::unique_ptr<PrecisionScope> corr;
+      if (approx && it > 1) corr.reset(new PrecisionScope(c, corr_prec));
       for (int q0 = 0; q0 < total; q0 += bmax) {
         const int nb = std::min(bmax, total - q0);
         Op(nb, in + (int64_t)q0 * N, out + (int64_t)q0 * N);
@@ -724,12 +735,13 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
         std::fprintf(stderr, "[cclr] davidson it %d rhs %zu L %d unconverged %zu/%zu max|r| %.3e tol %.1e\n", it, k, L,
                      order.size(), s.z.size(), order.empty() ? 0.0 : std::max_element(order.begin(), order.end())->first,
                      tol_s);
-      if (!order.empty() && mixed) {
-        // mixed modes: accept a stagnating solve whose residuals are all within 5x the floor
+      if (!order.empty() && (mixed || approx)) {
+        // mixed modes: accept a stagnating solve whose residuals are all within 5x the floor;
+        // mixed corrections: accept any stagnating solve (the caller verifies it exactly)
         double mx = 0.0;
         for (auto& pr : order) mx = std::max(mx, pr.first);
         if (mx < 0.8 * s.best) { s.best = mx; s.best_it = it; }
-        if (it - s.best_it >= 4 && mx < 5.0 * tol_s) order.clear();
+        if (it - s.best_it >= 4 && (approx || mx < 5.0 * tol_s)) order.clear();
       }
       if (order.empty()) {
         s.done = true;
@@ -774,6 +786,10 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
       const int kk = add_corrections(c, s.B, s.L, R, nt, pre2, std::min(kMaxNew, maxL - s.L), cdev, vscr, s.Bf, Rf);
       round_rows(s.B, s.L, kk);
       mirror(s.B, s.Bf, s.L, kk);
+      if (kk == 0 && approx) {   // no new direction: hand the solve to the caller's verification
+        s.done = true;
+        continue;
+      }
       if (kk == 0)
         throw Error(CCLR_E_NOCONV, "Davidson stagnated: residual " + std::to_string(order.front().first) +
                                        " above tolerance " + std::to_string(tol_s) + " with no new direction");
@@ -781,6 +797,10 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
       fresh[k] = kk;
     }
     ph.mark(c, "other");
+    if (!all_done) {
+      all_done = true;
+      for (auto& s : sys) all_done = all_done && s.done;
+    }
     // the largest current residual over all systems and shifts (the final one at exit)
     c.stats.max_residual = 0.0;
     for (auto& s : sys)
@@ -790,19 +810,42 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
   throw Error(CCLR_E_NOCONV, "Davidson did not converge within maxit iterations");
 }
 
-// FP64 iterative refinement of systems solved in a mixed mode (cclr_options.refine): every system
-// restarts from the compressed span of its mixed-precision solutions, U = B Q (directions above
-// 1e-10 of the largest, at most 16), whose sigma vectors are formed again in
-// the FP64-class tensor-core mode, and the Davidson iteration continues there with FP64-class
-// sigma products and FP64 residuals, norms and projections until every residual is below tol.
-// The phase-1 arrays of each system (B, S) are freed and replaced; bases[k] / sigs[k] (when not
-// null) are updated to the new arrays.
+void restart_from_solutions(Ctx& c, std::vector<System>& sys, int maxL, std::vector<cplx*>* bases,
+                            std::vector<cplx*>* sigs);
+
+// FP64 iterative refinement of systems solved in a mixed mode (cclr_options.refine).  Each round
+// restarts every system from the compressed span of its current solutions, U = B Q (directions
+// above 1e-10 of the largest, at most 16), whose sigma vectors are formed in the FP64-class
+// tensor-core mode, so the first Davidson iteration of a round sees exact residuals.  The
+// corrections added after it have small coefficients (the mixed phase left a relative residual
+// of ~2e-5), so their sigma products run in the caller's mixed mode: their ~1e-5 relative error
+// enters the solution at ~1e-10.  A round that converges in its first iteration is verified and
+// ends the refinement; after two mixed rounds the corrections use the FP64-class mode as well.
+// Residuals, norms and projections are FP64 throughout.  The phase-1 arrays of each system (B, S)
+// are freed and replaced; bases[k] / sigs[k] (when not null) are updated to the new arrays.
 void refine_systems(Ctx& c, std::vector<System>& sys, const std::function<void(int, const cplx*, cplx*)>& Op, int maxL,
                     double tol, std::vector<cplx*>* bases, std::vector<cplx*>* sigs) {
+  const int corr_prec = c.opt.precision;   // the mixed mode of the first phase
   PrecisionScope exact(c, CCLR_TC_F64);
-  const int64_t N = c.N;
   const double t0 = now();
   const long v0 = c.stats.sigma_vectors;
+  for (int round = 0;; ++round) {
+    const bool exact_corr = round >= 2;
+    restart_from_solutions(c, sys, maxL, bases, sigs);
+    davidson(c, sys, Op, maxL, tol, exact_corr, exact_corr ? -1 : corr_prec);
+    bool verified = true;
+    for (auto& s : sys) verified = verified && s.iters == 1;
+    if (verified || exact_corr) break;
+  }
+  c.stats.refine_vectors += c.stats.sigma_vectors - v0;
+  c.stats.refine_seconds += now() - t0;
+}
+
+// Replaces every system's trial space by the compressed span of its solutions (see
+// refine_systems); the sigma vectors of the new space are formed by the next Davidson call.
+void restart_from_solutions(Ctx& c, std::vector<System>& sys, int maxL, std::vector<cplx*>* bases,
+                            std::vector<cplx*>* sigs) {
+  const int64_t N = c.N;
   for (size_t k = 0; k < sys.size(); ++k) {
     System& s = sys[k];
     const std::vector<std::vector<zc>> Q = solution_directions(s, 1e-10, std::max(1, std::min(16, maxL / 2)));
@@ -822,9 +865,6 @@ void refine_systems(Ctx& c, std::vector<System>& sys, const std::function<void(i
     if (bases) (*bases)[k] = B2;
     if (sigs) (*sigs)[k] = S2;
   }
-  davidson(c, sys, Op, maxL, tol, true);
-  c.stats.refine_vectors += c.stats.sigma_vectors - v0;
-  c.stats.refine_seconds += now() - t0;
 }
 
 // ------------------------------------------------------------------------------ Lambda
@@ -975,18 +1015,33 @@ void response_function(Ctx& c, cplx* out_host) {
   // modes, whose sigma products carry ~1e-5 relative error) to Q_x, form the products
   // F (B^x Q_x) in batches and contract them at once:
   //   M^{xy} = (B^x Q_x F) . B^y,  (t^X F) . t^Y = gamma^T M^{xy} beta^Y,  gamma = Q_x^H beta^X.
+  // Refined solutions: direction j carries at most a fraction w_j (its pivot weight) of any
+  // solution, so a product error eps_p enters the F term at <= w_j eps_p of its size.  Directions
+  // with w_j > 1e-4 use the FP64-class mode, 1e-6 < w_j <= 1e-4 the FP32-class split (eps ~1e-7),
+  // the rest the three-product split (eps ~2e-5): every contribution stays below ~2e-11.
+  const int base_prec = c.opt.precision;   // FP64-class when refined, else the solve's mode
+  auto dir_prec = [&](double w) {
+    if (!rd.refined) return base_prec;
+    return w > 1e-4 ? (int)CCLR_TC_F64 : w > 1e-6 ? (int)CCLR_TC_BF16X6 : (int)CCLR_TC_BF16X3;
+  };
   std::vector<std::vector<std::vector<zc>>> Q(nop);
   for (int x = 0; x < nop; ++x) {
     const int Lx = rd.nb[x];
     std::vector<std::vector<zc>> cols;
     for (int f = 0; f < rd.n_freq; ++f)
       for (int s : {3, 2}) cols.emplace_back(beta(x, f, s), beta(x, f, s) + Lx);
-    Q[x] = pivoted_orthonormal(cols, Lx, mixed_precision(c.opt.precision) ? 1e-7 : rd.refined ? 1e-10 : 1e-12, Lx);
+    std::vector<double> wts;
+    Q[x] = pivoted_orthonormal(cols, Lx, mixed_precision(c.opt.precision) ? 1e-7 : rd.refined ? 1e-10 : 1e-12, Lx,
+                               &wts);
     const int rx = (int)Q[x].size();
     for (int y = 0; y < nop; ++y) M[(size_t)x * nop + y].assign((size_t)rx * rd.nb[y], zc(0));
     const int bmax = std::max(1, std::min(c.opt.batch > 0 ? c.opt.batch : 8, rx));
-    for (int q0 = 0; q0 < rx; q0 += bmax) {
-      const int nb = std::min(bmax, rx - q0);
+    for (int q0 = 0; q0 < rx;) {
+      // one batch: up to bmax consecutive directions of the same precision
+      const int p = dir_prec(wts[q0]);
+      int nb = 1;
+      while (nb < bmax && q0 + nb < rx && dir_prec(wts[q0 + nb]) == p) ++nb;
+      PrecisionScope dp(c, p);
       Scope sc(c.ws);
       cplx* yv = c.ws.cplxs((int64_t)nb * N);
       cplx* fb = c.ws.cplxs((int64_t)nb * N);
@@ -1005,6 +1060,14 @@ void response_function(Ctx& c, cplx* out_host) {
         for (int i = 0; i < nb; ++i)
           for (int j = 0; j < rd.nb[y]; ++j) Mxy[(size_t)(q0 + i) * rd.nb[y] + j] = g[(size_t)i * rd.nb[y] + j];
       }
+      q0 += nb;
+    }
+    static const bool verbose = std::getenv("CCLR_VERBOSE") != nullptr;
+    if (verbose) {
+      int cnt[5] = {0, 0, 0, 0, 0};
+      for (double w : wts) cnt[dir_prec(w)]++;
+      std::fprintf(stderr, "[cclr] response_function op %d: %d Hessian directions (F64 %d, BF16X6 %d, BF16X3 %d)\n", x,
+                   rx, cnt[CCLR_TC_F64], cnt[CCLR_TC_BF16X6], cnt[CCLR_TC_BF16X3]);
     }
   }
   ph.mark(c, "forms");

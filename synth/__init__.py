@@ -13,7 +13,7 @@ Instance recipe (all complex128):
   * property operators X_k (dipole components) are Hermitian n x n, strict upper triangle
     Re, Im ~ N(0, dip_sd^2), real diagonal N(0, dip_sd^2).
 
-Random streams: numpy's Philox4x32 counter-based generator keyed by (seed, stream):
+Random streams: numpy's Philox (4x64, 10 rounds) counter-based generator keyed by (seed, stream):
   stream 0 orbital energies, 1..6 the six integral classes, 100+k property operator k.
 
 Storage of the six integral classes (the layout the C ABI takes; pair index of p<q within one

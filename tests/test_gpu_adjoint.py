@@ -6,7 +6,7 @@ import pytest
 import torch
 
 import synth
-from layout import rel
+from layout import from_amp, rel, to_amp
 from oracle import response as R
 from oracle.deriv import pack
 from oracle.ints import Ints
@@ -144,7 +144,7 @@ def test_energy_adjoint_is_eta_and_lambda_is_its_left_solve_4x20(pk):
     assert lam.is_cuda
     lam = lam.cpu().numpy()
     S = R.CCSystem(Ints.from_instance(inst))
-    assert rel(lam, pack(S.l1, S.l2)) < 1e-8
+    assert rel(lam, to_amp(S.l1, S.l2)) < 1e-8    # the library's amplitude layout
     ctx.cc_lambda()
     assert rel(lam, ctx.cclr_get_amplitudes(pk.AMP_LAMBDA)) < 1e-9
     ctx.close()
@@ -166,12 +166,12 @@ def test_left_solve_residual_by_oracle_4x20(pk):
     l = lt.cpu().numpy()
     lh = ctx.cclr_left_solve(b, w)
     assert rel(lh, l) < 1e-12
-    from oracle.deriv import unpack
     o, v = inst.n_occ, inst.n_vir
-    S = R.CCSystem(Ints.from_instance(inst), t=unpack(t, o, v), lam=(np.zeros((o, v)), np.zeros((o, o, v, v))))
+    S = R.CCSystem(Ints.from_instance(inst), t=from_amp(t, o, v), lam=(np.zeros((o, v)), np.zeros((o, o, v, v))))
     for k in range(2):
-        r = S.sigma_l(l[k]) + w * l[k] + b[k]
-        assert np.linalg.norm(r) < 2e-9 * np.linalg.norm(b[k]), np.linalg.norm(r) / np.linalg.norm(b[k])
+        lk, bk = pack(*from_amp(l[k], o, v)), pack(*from_amp(b[k], o, v))   # oracle element order
+        r = S.sigma_l(lk) + w * lk + bk
+        assert np.linalg.norm(r) < 2e-9 * np.linalg.norm(bk), np.linalg.norm(r) / np.linalg.norm(bk)
     ctx.close()
 
 
