@@ -166,18 +166,14 @@ def oracle_sample(budget_s: float = 20.0):
 def oracle_sigma_one_thread(o: int = 8, v: int = 60):
     """One right sigma product of the oracle with the BLAS limited to one thread (the paper's CPU
     timings use one OpenMP thread): seconds and TFLOP/s by the sigma-count rule."""
-    import synth
-    from threadpoolctl import threadpool_limits
-    from oracle.ints import Ints
-    from oracle import response as R
-    inst = synth.make_instance(o, v)
-    s = R.CCSystem(Ints.from_instance(inst), tol=1e-8)
-    x = synth.random_vector((s.D.size,), 5, 5, 1e-2)
-    with threadpool_limits(limits=1):
-        s.sigma_r(x)
-        t0 = time.perf_counter()
-        s.sigma_r(x)
-        dt = time.perf_counter() - t0
+    # a fresh interpreter whose BLAS starts with one thread (the variables are read at load time)
+    code = ("import sys, time; sys.path.insert(0, %r); import synth; from oracle.ints import Ints; "
+            "from oracle import response as R; inst = synth.make_instance(%d, %d); "
+            "s = R.CCSystem(Ints.from_instance(inst), tol=1e-8); x = synth.random_vector((s.D.size,), 5, 5, 1e-2); "
+            "s.sigma_r(x); t0 = time.perf_counter(); s.sigma_r(x); print(time.perf_counter() - t0)") % (ROOT, o, v)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=1200)
+    dt = float(r.stdout.strip().splitlines()[-1])
     return dt, 8 * sigma_cmac(o, v) / dt / 1e12
 
 
@@ -398,6 +394,71 @@ def run_adjoint(args):
     print(json.dumps(out), flush=True)
 
 
+C2_SYSTEMS = [(8, 60), (12, 90), (18, 120)]
+
+
+def run_batch(args):
+    """Three uneven systems, (8,60), (12,90) and (18,120), x 3 dipole operators x 16 frequencies on
+    [0.05, 0.30] (gamma 0.005), each from Hamiltonian to alpha in the FP32-class tensor-core mode
+    with FP64 refinement to 1e-8: once as one batch (cclr_response_batch: one host thread and
+    stream per system, kernels overlapping on the GPU) and once one system after another.  Also
+    the FP64-class mode throughout for the largest system as the accuracy reference.  One JSON
+    line."""
+    import paper_2307_14296_b300 as pk
+    import synth
+    om = np.linspace(0.05, 0.30, 16)
+    gamma = 0.005
+    insts = [synth.make_instance(o, v, seed=synth.DEFAULT_SEED + 7 + k) for k, (o, v) in enumerate(C2_SYSTEMS)]
+    prec = prec_of(pk, args.precision) if args.precision != "bf16x3" else pk.TC_BF16X6
+
+    def contexts(p):
+        cs = []
+        for inst in insts:
+            c = pk.Context(0, precision=p, tol=1e-8, ground_tol=1e-9, max_subspace=args.max_subspace, batch=8,
+                           maxit=100)
+            c.cclr_set_hamiltonian(inst.n_occ, inst.n_vir, inst.fock, [inst.blocks[k] for k in synth.CLASSES])
+            cs.append(c)
+        return cs
+    out = dict(mode="batch", workload="three uneven systems " + ", ".join(f"{o}/{v}" for o, v in C2_SYSTEMS) +
+               ": 3 operators x 16 frequencies on [0.05,0.30], gamma 0.005, residual 1e-8", precision=prec)
+    cs = contexts(prec)
+    pk.cclr_response_batch(cs, [i.ops for i in insts], om[:2], gamma)   # warm-up (autotuner, caches)
+    for c in cs:
+        c.close()
+    cs = contexts(prec)
+    t0 = time.perf_counter()
+    batched = pk.cclr_response_batch(cs, [i.ops for i in insts], om, gamma)
+    out["batched_seconds"] = time.perf_counter() - t0
+    out["sigma_products"] = [c.cclr_get_stats()["sigma_vectors"] for c in cs]
+    for c in cs:
+        c.close()
+    seq = []
+    t0 = time.perf_counter()
+    for inst, c in zip(insts, contexts(prec)):
+        c.cc_ground()
+        c.cc_lambda()
+        c.cc_lr_solve(inst.ops, om, gamma)
+        seq.append(-c.cc_response_function())
+        c.close()
+    out["sequential_seconds"] = time.perf_counter() - t0
+    out["batch_speedup"] = out["sequential_seconds"] / out["batched_seconds"]
+    out["batch_vs_sequential_max_rel"] = max(float(np.abs(-b - s).max() / np.abs(s).max()) for b, s in zip(batched, seq))
+    ref = []
+    t0 = time.perf_counter()
+    for inst, c in zip(insts, contexts(pk.TC_F64)):
+        c.cc_ground()
+        c.cc_lambda()
+        c.cc_lr_solve(inst.ops, om, gamma)
+        ref.append(-c.cc_response_function())
+        c.close()
+    out["f64tc_seconds"] = time.perf_counter() - t0
+    out["per_system"] = [dict(system=f"{o}/{v}",
+                              max_rel_per_component_vs_f64tc=float((np.abs(-b - r) / np.abs(r)).max()),
+                              max_rel_to_largest_vs_f64tc=float(np.abs(-b - r).max() / np.abs(r).max()))
+                         for (o, v), b, r in zip(C2_SYSTEMS, batched, ref)]
+    print(json.dumps(out), flush=True)
+
+
 def run_gemm(args):
     """Tensor-core GEMM alone on one shape (A: M x K, B: N x K, complex), e.g. the packed ladder
     contraction of eight trial vectors (M = 8 Po, K = Pv): a small case for kernel captures."""
@@ -504,6 +565,8 @@ def main():
     ap.add_argument("--accuracy-at-scale", action="store_true",
                     help="solve the workload refined and in the FP64-class mode; per-frequency alpha errors")
     ap.add_argument("--max-subspace", type=int, default=64, help="Davidson trial-space limit")
+    ap.add_argument("--batch", action="store_true",
+                    help="three uneven systems (8/60, 12/90, 18/120) solved as one batch and one by one")
     ap.add_argument("--adjoint", action="store_true",
                     help="gradients of alpha w.r.t. the operators and a static field (use --workload 20x150)")
     args = ap.parse_args()
@@ -523,6 +586,9 @@ def main():
         return
     if args.adjoint:
         run_adjoint(args)
+        return
+    if args.batch:
+        run_batch(args)
         return
     world, rank, local = dist_init()
     if args.impl == "reference":

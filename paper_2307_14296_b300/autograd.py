@@ -58,7 +58,7 @@ class CCSDResidual(torch.autograd.Function):
         cc = ctx.cc
         cc.cclr_set_amplitudes(AMP_T, _lib_arg(t))   # the left sigma is the Jacobian at this t
         lg = cc.cclr_sigma(_lib_arg(g.conj()).reshape(1, -1), side=1)
-        return _as_tensor(lg, g).reshape(g.shape).conj(), None
+        return _as_tensor(lg, g).reshape(g.shape).conj().resolve_conj(), None
 
 
 def ccsd_residual(t, cc):

@@ -494,16 +494,15 @@ int add_corrections(Ctx& c, cplx* B, int L, cplx* R, int nt, const double* pre2,
 // FP64-class contractions then need 9 instead of 15 digit products on the trial-vector operands).
 // The rounding only changes which trial vectors span the space; every sigma vector is the exact
 // product of the stored vector.
-// corr_prec >= 0: the sigma products of the vectors added after the first iteration run in that
-// (mixed) precision while the starting space keeps the ambient one; the residuals are then exact
-// only up to the mixed error of the added vectors' (small) components, a stagnating solve is
-// accepted, and the caller verifies (refine_systems).
+// coarse: the corrections added after the first iteration are rounded to the coarse grid (two
+// digits in every view), so their FP64-class sigma products need 9 instead of 15 digit pairs; the
+// starting space keeps every digit (rounding a restart space would throw away the accuracy it
+// carries).
 void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, const cplx*, cplx*)>& Op,
-              int maxL, double tol, bool coarse = false, int corr_prec = -1) {
+              int maxL, double tol, bool coarse = false) {
   static const bool verbose = std::getenv("CCLR_VERBOSE") != nullptr;
   Fast32 f32(c);
   const bool mixed = mixed_precision(c.opt.precision);
-  const bool approx = corr_prec >= 0;
   const int64_t N = c.N;
   const int kMaxNew = 4;   // new trial vectors per right-hand side and iteration (worst shifts first)
   const int kTry = 8;      // candidate corrections formed per right-hand side and iteration
@@ -594,7 +593,6 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
       scale_vec(c.L, N, cx(1.0 / nb), s.B);
       s.L = 1;
     }
-    round_rows(s.B, 0, s.L);
     mirror(s.B, s.Bf, 0, s.L);
   }
   std::vector<int> fresh(sys.size());   // new vectors at the end of each basis
@@ -621,9 +619,7 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
         bool old;
         CoarseFlag(Ctx& cc, bool on) : c(cc), old(cc.coarse_sigma) { c.coarse_sigma = on; }
         ~CoarseFlag() { c.coarse_sigma = old; }
-      } cf(c, coarse && !(approx && it > 1));
-      std::unique_ptr<PrecisionScope> corr;
-      if (approx && it > 1) corr.reset(new PrecisionScope(c, corr_prec));
+      } cf(c, coarse && it > 1);
       for (int q0 = 0; q0 < total; q0 += bmax) {
         const int nb = std::min(bmax, total - q0);
         Op(nb, in + (int64_t)q0 * N, out + (int64_t)q0 * N);
@@ -735,13 +731,12 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
         std::fprintf(stderr, "[cclr] davidson it %d rhs %zu L %d unconverged %zu/%zu max|r| %.3e tol %.1e\n", it, k, L,
                      order.size(), s.z.size(), order.empty() ? 0.0 : std::max_element(order.begin(), order.end())->first,
                      tol_s);
-      if (!order.empty() && (mixed || approx)) {
-        // mixed modes: accept a stagnating solve whose residuals are all within 5x the floor;
-        // mixed corrections: accept any stagnating solve (the caller verifies it exactly)
+      if (!order.empty() && mixed) {
+        // mixed modes: accept a stagnating solve whose residuals are all within 5x the floor
         double mx = 0.0;
         for (auto& pr : order) mx = std::max(mx, pr.first);
         if (mx < 0.8 * s.best) { s.best = mx; s.best_it = it; }
-        if (it - s.best_it >= 4 && (approx || mx < 5.0 * tol_s)) order.clear();
+        if (it - s.best_it >= 4 && mx < 5.0 * tol_s) order.clear();
       }
       if (order.empty()) {
         s.done = true;
@@ -786,10 +781,6 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
       const int kk = add_corrections(c, s.B, s.L, R, nt, pre2, std::min(kMaxNew, maxL - s.L), cdev, vscr, s.Bf, Rf);
       round_rows(s.B, s.L, kk);
       mirror(s.B, s.Bf, s.L, kk);
-      if (kk == 0 && approx) {   // no new direction: hand the solve to the caller's verification
-        s.done = true;
-        continue;
-      }
       if (kk == 0)
         throw Error(CCLR_E_NOCONV, "Davidson stagnated: residual " + std::to_string(order.front().first) +
                                        " above tolerance " + std::to_string(tol_s) + " with no new direction");
@@ -797,10 +788,6 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
       fresh[k] = kk;
     }
     ph.mark(c, "other");
-    if (!all_done) {
-      all_done = true;
-      for (auto& s : sys) all_done = all_done && s.done;
-    }
     // the largest current residual over all systems and shifts (the final one at exit)
     c.stats.max_residual = 0.0;
     for (auto& s : sys)
@@ -813,30 +800,20 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
 void restart_from_solutions(Ctx& c, std::vector<System>& sys, int maxL, std::vector<cplx*>* bases,
                             std::vector<cplx*>* sigs);
 
-// FP64 iterative refinement of systems solved in a mixed mode (cclr_options.refine).  Each round
-// restarts every system from the compressed span of its current solutions, U = B Q (directions
-// above 1e-10 of the largest, at most 16), whose sigma vectors are formed in the FP64-class
-// tensor-core mode, so the first Davidson iteration of a round sees exact residuals.  The
-// corrections added after it have small coefficients (the mixed phase left a relative residual
-// of ~2e-5), so their sigma products run in the caller's mixed mode: their ~1e-5 relative error
-// enters the solution at ~1e-10.  A round that converges in its first iteration is verified and
-// ends the refinement; after two mixed rounds the corrections use the FP64-class mode as well.
-// Residuals, norms and projections are FP64 throughout.  The phase-1 arrays of each system (B, S)
-// are freed and replaced; bases[k] / sigs[k] (when not null) are updated to the new arrays.
+// FP64 iterative refinement of systems solved in a mixed mode (cclr_options.refine): every system
+// restarts from the compressed span of its mixed-precision solutions, U = B Q (directions above
+// 1e-10 of the largest, at most 16), whose sigma vectors are formed again in the FP64-class
+// tensor-core mode from every digit, and the Davidson iteration continues there with FP64-class
+// sigma products of coarse corrections and FP64 residuals, norms and projections until every
+// residual is below tol.  The phase-1 arrays of each system (B, S) are freed and replaced;
+// bases[k] / sigs[k] (when not null) are updated to the new arrays.
 void refine_systems(Ctx& c, std::vector<System>& sys, const std::function<void(int, const cplx*, cplx*)>& Op, int maxL,
                     double tol, std::vector<cplx*>* bases, std::vector<cplx*>* sigs) {
-  const int corr_prec = c.opt.precision;   // the mixed mode of the first phase
   PrecisionScope exact(c, CCLR_TC_F64);
   const double t0 = now();
   const long v0 = c.stats.sigma_vectors;
-  for (int round = 0;; ++round) {
-    const bool exact_corr = round >= 2;
-    restart_from_solutions(c, sys, maxL, bases, sigs);
-    davidson(c, sys, Op, maxL, tol, exact_corr, exact_corr ? -1 : corr_prec);
-    bool verified = true;
-    for (auto& s : sys) verified = verified && s.iters == 1;
-    if (verified || exact_corr) break;
-  }
+  restart_from_solutions(c, sys, maxL, bases, sigs);
+  davidson(c, sys, Op, maxL, tol, true);
   c.stats.refine_vectors += c.stats.sigma_vectors - v0;
   c.stats.refine_seconds += now() - t0;
 }
