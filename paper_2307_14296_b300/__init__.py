@@ -3,7 +3,7 @@
 Thin ctypes layer over the C ABI in include/cclr.h: it converts numpy arrays (host) or torch CUDA
 tensors (device) into pointers and sizes and turns status codes into exceptions.  Every step of
 the computation runs in the CUDA library; there is no Python or CPU fallback, and importing this
-package fails if libcclr.so has not been built (python -m paper_2307_14296_b300.build).
+package fails if libcclr.so has not been built (python paper_2307_14296_b300/build.py).
 
 Vector layout ("amplitude layout"): [singles t_i^a at i*v + a | doubles t_ij^ab at
 P(i,j)*Pv + P(a,b)] with P(p,q) = q*(q-1)/2 + p for p < q; unique elements only.
@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libcclr.so")
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(
-        "libcclr.so is missing: build the CUDA library with `python -m paper_2307_14296_b300.build` "
+        "libcclr.so is missing: build the CUDA library with `python paper_2307_14296_b300/build.py` "
         "(there is no CPU fallback)")
 
 _lib = ctypes.CDLL(LIB_PATH)

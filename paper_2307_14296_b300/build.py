@@ -1,5 +1,5 @@
 """Build libcclr.so in-tree for sm_103a with nvcc (no JIT cache, so the library travels with the
-source tree).  Usage: python -m paper_2307_14296_b300.build [--force]"""
+source tree).  Usage: python paper_2307_14296_b300/build.py [--force] (run as a script: importing the package needs the built library)"""
 from __future__ import annotations
 import glob
 import os

@@ -489,15 +489,12 @@ int add_corrections(Ctx& c, cplx* B, int L, cplx* R, int nt, const double* pre2,
 //              orthonormal to working precision because B^H B enters the Galerkin matrices
 //   selection: Gram-Schmidt among the candidates in their own Gram metric, worst first
 //
-// coarse: every trial vector is rounded to the coarse grid of its largest element (round_coarse)
-// before its sigma vector is formed, and the sigma products treat their inputs as such (the
-// FP64-class contractions then need 9 instead of 15 digit products on the trial-vector operands).
-// The rounding only changes which trial vectors span the space; every sigma vector is the exact
-// product of the stored vector.
-// coarse: the corrections added after the first iteration are rounded to the coarse grid (two
-// digits in every view), so their FP64-class sigma products need 9 instead of 15 digit pairs; the
-// starting space keeps every digit (rounding a restart space would throw away the accuracy it
-// carries).
+// coarse: the corrections added after the first iteration are rounded to the coarse grid of their
+// largest element (round_coarse: two digits in every view), and the sigma products treat them as
+// such (the FP64-class contractions then need 9 instead of 15 digit products on the trial-vector
+// operands).  The rounding only changes which vectors span the space; every sigma vector is the
+// exact product of the stored vector.  The starting space keeps every digit: rounding a restart
+// space would throw away the accuracy it carries.
 void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, const cplx*, cplx*)>& Op,
               int maxL, double tol, bool coarse = false) {
   static const bool verbose = std::getenv("CCLR_VERBOSE") != nullptr;
