@@ -419,7 +419,17 @@ int add_corrections(Ctx& c, cplx* B, int L, cplx* R, int nt, const double* pre2,
                     double* vscr, const void* Bf = nullptr, void* Rf = nullptr) {
   const int64_t N = c.N, Np = N + (N & 1);
   if (kmax <= 0 || nt <= 0) return 0;
+  // With mirrors the projection runs in FP32 arithmetic whatever the solve's vector arithmetic:
+  // the corrections are only directions (B^H B enters the Galerkin matrices exactly, so a basis
+  // orthogonal to FP32 level is enough).
+  struct Arith32 {
+    Ctx& c;
+    bool old;
+    Arith32(Ctx& cc, bool on) : c(cc), old(cc.L.fast32) { if (on) c.L.fast32 = true; }
+    ~Arith32() { c.L.fast32 = old; }
+  };
   for (int pass = 0; pass < 2 && L > 0; ++pass) {
+    Arith32 a32(c, Bf && Rf);
     std::vector<zc> g;
     if (Bf && Rf) {   // B^H R from the FP32 mirrors (R mirrored here)
       for (int t = 0; t < nt; ++t) to_f32(c.L, R + (int64_t)t * N, (float2*)Rf + (int64_t)t * Np, N);
@@ -540,14 +550,17 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
     return s.Sf ? m32(s.Sf, 0, s.L).add(reinterpret_cast<const cplx*>(s.Bf), s.L, Np)
                 : Rows().add(s.S, s.L, N).add(s.B, s.L, N);
   };
+  // Mixed modes mirror B, S and b (every FP32-arithmetic pass reads them); FP64-arithmetic solves
+  // mirror B alone, for the FP32 projection of new corrections (residuals, candidates and
+  // Galerkin blocks stay on the FP64 rows).
   const bool mirrors = c.L.fast32;
   for (auto& s : sys) {
-    s.Bf = mirrors ? c.ws.alloc(sizeof(float2) * (size_t)maxL * (size_t)Np) : nullptr;
+    s.Bf = c.ws.alloc(sizeof(float2) * (size_t)maxL * (size_t)Np);
     s.Sf = mirrors ? c.ws.alloc(sizeof(float2) * (size_t)maxL * (size_t)Np) : nullptr;
     s.bf = mirrors ? c.ws.alloc(sizeof(float2) * (size_t)Np) : nullptr;
     if (s.bf) to_f32(c.L, s.rhs, s.bf, N);
   }
-  void* Rf = mirrors ? c.ws.alloc(sizeof(float2) * (size_t)kTry * (size_t)Np) : nullptr;
+  void* Rf = c.ws.alloc(sizeof(float2) * (size_t)kTry * (size_t)Np);
   auto mirror = [&](const cplx* X, void* Xf, int r0, int nr) {   // rows [r0, r0 + nr) of B or S
     if (Xf)
       for (int r = r0; r < r0 + nr; ++r) to_f32(c.L, X + (int64_t)r * N, (float2*)Xf + (int64_t)r * Np, N);

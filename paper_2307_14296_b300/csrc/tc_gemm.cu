@@ -398,20 +398,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // the later groups of the chunk run, and the last group (9 pairs) while the next chunk's first
 // three groups run.  TMEM: g0 | g1 | g2 | g34, each Cr (64) | Ci (64) = 512 columns.
 // Warp 0: TMA producer; warp 1: MMA issuer; warps 2..17: epilogue (TMEM lane quarter warp % 4,
-// 16 columns each), keeping the float-float sums of their elements in a per-CTA global buffer
-// (L2-resident) between chunks and writing C (alpha, beta in FP64) after the last chunk.
+// 16 columns each), keeping the float-float sums of their 16 elements across the chunks of a tile
+// (high words in registers, low words in shared memory: 18 warps leave 96 registers a thread) and
+// writing C (alpha, beta in FP64) after the last chunk.
 namespace x {
 constexpr int NS = 5;                             // digits (slices) per operand
 constexpr int BN = 64;                            // MMA N = m rows per tile
-constexpr int STAGES = 4;
+constexpr int STAGES = 3;
 constexpr int A_PLANE = BM * BK * 2;              // 16 KB
 constexpr int B_PLANE = BN * BK * 2;              // 8 KB
 constexpr int STAGE_BYTES = 2 * A_PLANE + 2 * B_PLANE;
+constexpr int RING_BYTES = STAGES * STAGE_BYTES;
 constexpr int CK = 4;                             // k-blocks per chunk (256 K values)
 constexpr int EPI_WARPS = 16;
 constexpr int EPI_THREADS = 32 * EPI_WARPS;
 constexpr int THREADS = 64 + EPI_THREADS;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/ + BN * 8 /*row offsets*/;
+constexpr int LO_OFFSET = RING_BYTES + 256 /*barriers*/ + BN * 8 /*row offsets*/;
+constexpr int LO_BYTES = BM * BN * 8;             // low words of the float-float sums (re, im)
+constexpr int SMEM_BYTES = LO_OFFSET + LO_BYTES + 1024 /*align*/;
 constexpr int TMEM_COLS = 512;
 constexpr int MAX_PAIRS = 15;
 constexpr int NG = 4;                             // accumulator groups
@@ -442,6 +446,13 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&r)[4]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 // s + e = a + b exactly (Knuth's TwoSum; round-to-nearest FP32)
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = __fadd_rn(a, b);
@@ -461,17 +472,18 @@ __global__ void __launch_bounds__(x::THREADS, 1)
     k_tc_zgemm_x(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int n_rows, int m_rows,
                  int kblocks, int kb_per, PairsX pairs, double2 alpha, float alpha_pow2, double2 beta,
                  double2* __restrict__ C, int64_t ldc, int64_t cz, int* __restrict__ err, int xtiles, int ytiles,
-                 int nsplit, const OutMap om, bool strided, float4* __restrict__ fstate) {
+                 int nsplit, const OutMap om, bool strided) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* full = (uint64_t*)(smem + x::STAGES * x::STAGE_BYTES);
+  uint64_t* full = (uint64_t*)(smem + x::RING_BYTES);
   uint64_t* empty = full + x::STAGES;
   uint64_t* gfull = empty + x::STAGES;   // chunk sums of group g ready (MMA commit)
   uint64_t* gempty = gfull + x::NG;      // the same accumulators drained (all epilogue threads)
   uint64_t* done = gempty + x::NG;
   uint32_t* tmem_slot = (uint32_t*)(done + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
-  int64_t* moff = (int64_t*)(smem + x::STAGES * x::STAGE_BYTES + 256);
+  int64_t* moff = (int64_t*)(smem + x::RING_BYTES + 256);
+  float2* lo = (float2*)(smem + x::LO_OFFSET);   // [col][row] low words (re, im)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < x::STAGES; ++s) {
@@ -580,7 +592,6 @@ __global__ void __launch_bounds__(x::THREADS, 1)
     const uint32_t lane_base = (uint32_t)(lg * 32) << 16;
     const bool use_beta = (beta.x != 0.0 || beta.y != 0.0);
     const bool beta_one = (beta.x == 1.0 && beta.y == 0.0);
-    float4* st = fstate + (size_t)blockIdx.x * BM * x::BN;   // [col][row] float-float sums (re hi, re lo, im hi, im lo)
     int cc = 0;
     bool stop = false;
     for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
@@ -597,32 +608,50 @@ __global__ void __launch_bounds__(x::THREADS, 1)
       if (group_any_x(*abort_flag != 0)) break;   // also publishes this tile's offsets
       const int n = n0 + row;
       const int64_t noff = (strided && n < n_rows) ? out_off((uint32_t)n, om.nn, om.ndim, om.nstr, om.nmul, om.nshr) : 0;
+      // running float-float sums of this thread's 16 elements: high words in registers, low
+      // words in shared memory ([col][row]: a warp's 32 rows are contiguous)
+      float Hr[16], Hi[16];
+      float2* lrow = lo + row;
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        Hr[k] = 0.0f;
+        Hi[k] = 0.0f;
+        lrow[(16 * ch + k) * BM] = make_float2(0.0f, 0.0f);
+      }
       for (int ci = 0; ci < nch; ++ci, ++cc) {
         const uint32_t cpar = (uint32_t)cc & 1u;
-        // group 0 (exact chunk sum)
+        // groups 0 and 1: exact chunk sums, folded 4 columns at a time (two_sum of the pair is exact)
         bool ready = mbar_wait(&gfull[0], cpar);
         if (group_any_x(!ready)) { if (et == 0) atomicExch(err, 13); *abort_flag = 1; stop = true; break; }
-        fence_after();
-        uint32_t a_re[16], a_im[16], b_re[16], b_im[16];
-        tmem_ld16(tmem + lane_base + 16 * ch, a_re);
-        tmem_ld16(tmem + lane_base + x::BN + 16 * ch, a_im);
-        fence_before();
-        mbar_arrive(&gempty[0]);
-        // group 1 (exact chunk sum)
         ready = mbar_wait(&gfull[1], cpar);
         if (group_any_x(!ready)) { if (et == 0) atomicExch(err, 13); *abort_flag = 1; stop = true; break; }
         fence_after();
-        tmem_ld16(tmem + lane_base + 2 * x::BN + 16 * ch, b_re);
-        tmem_ld16(tmem + lane_base + 3 * x::BN + 16 * ch, b_im);
-        fence_before();
-        mbar_arrive(&gempty[1]);
-        float hr[16], lr[16], hi[16], li[16];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          two_sum(__uint_as_float(a_re[j]), __uint_as_float(b_re[j]), hr[j], lr[j]);
-          two_sum(__uint_as_float(a_im[j]), __uint_as_float(b_im[j]), hi[j], li[j]);
+        for (int h = 0; h < 4; ++h) {
+          uint32_t a_re[4], a_im[4], b_re[4], b_im[4];
+          tmem_ld4(tmem + lane_base + 16 * ch + 4 * h, a_re);
+          tmem_ld4(tmem + lane_base + x::BN + 16 * ch + 4 * h, a_im);
+          tmem_ld4(tmem + lane_base + 2 * x::BN + 16 * ch + 4 * h, b_re);
+          tmem_ld4(tmem + lane_base + 3 * x::BN + 16 * ch + 4 * h, b_im);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int k = 4 * h + j;
+            float2* lp = lrow + (16 * ch + k) * BM;
+            float sr, er, si, ei;
+            two_sum(__uint_as_float(a_re[j]), __uint_as_float(b_re[j]), sr, er);
+            two_sum(__uint_as_float(a_im[j]), __uint_as_float(b_im[j]), si, ei);
+            float2 l = *lp;
+            ff_add(Hr[k], l.x, sr, er);
+            ff_add(Hi[k], l.y, si, ei);
+            *lp = l;
+          }
         }
-        // groups 2 and 3..4 (FP32 sums, 2^-16 and 2^-24 of the result) in 8-column halves
+        fence_before();
+        mbar_arrive(&gempty[0]);
+        mbar_arrive(&gempty[1]);
+        // groups 2 and 3..4 (FP32 sums, ~2^-16 and ~2^-24 of the result) into the low parts; the
+        // next float-float addition renormalises
+#pragma unroll
         for (int gq = 2; gq < x::NG; ++gq) {
           ready = mbar_wait(&gfull[gq], cpar);
           if (group_any_x(!ready)) { if (et == 0) atomicExch(err, 13); *abort_flag = 1; stop = true; break; }
@@ -635,59 +664,47 @@ __global__ void __launch_bounds__(x::THREADS, 1)
             tmem_ld8(gbase + x::BN + 8 * h, q_im);
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-              lr[8 * h + j] = __fadd_rn(lr[8 * h + j], __uint_as_float(q_re[j]));
-              li[8 * h + j] = __fadd_rn(li[8 * h + j], __uint_as_float(q_im[j]));
+              float2* lp = lrow + (16 * ch + 8 * h + j) * BM;
+              float2 l = *lp;
+              l.x = __fadd_rn(l.x, __uint_as_float(q_re[j]));
+              l.y = __fadd_rn(l.y, __uint_as_float(q_im[j]));
+              *lp = l;
             }
           }
           fence_before();
           mbar_arrive(&gempty[gq]);
         }
         if (stop) break;
-        // running float-float sums
-        const bool firstc = ci == 0, lastc = ci == nch - 1;
-#pragma unroll 4
+      }
+      if (stop) break;
+      {
+        // C = alpha (hi + lo) + beta C in FP64 (fully unrolled: the sums stay in registers)
+#pragma unroll
         for (int j = 0; j < 16; ++j) {
           const int col = 16 * ch + j;
-          float Hr = hr[j], Lr = lr[j], Hi = hi[j], Li = li[j];
-          if (firstc) {
-            const float sr = __fadd_rn(Hr, Lr), si = __fadd_rn(Hi, Li);   // renormalise
-            Lr = __fsub_rn(Lr, __fsub_rn(sr, Hr));
-            Li = __fsub_rn(Li, __fsub_rn(si, Hi));
-            Hr = sr;
-            Hi = si;
-          } else {
-            const float4 s = st[(size_t)col * BM + row];
-            float Sr = s.x, Sl = s.y, Ti = s.z, Tl = s.w;
-            ff_add(Sr, Sl, Hr, Lr);
-            ff_add(Ti, Tl, Hi, Li);
-            Hr = Sr; Lr = Sl; Hi = Ti; Li = Tl;
-          }
-          if (!lastc) {
-            st[(size_t)col * BM + row] = make_float4(Hr, Lr, Hi, Li);
-          } else {
-            const int m = m0 + col;
-            if (n < n_rows && m < m_rows) {
-              double2 v;
-              if (alpha_pow2 != 0.0f) {   // real power-of-two alpha: exact FP32 scaling
-                v = make_double2(epi_f2d(Hr * alpha_pow2) + epi_f2d(Lr * alpha_pow2),
-                                 epi_f2d(Hi * alpha_pow2) + epi_f2d(Li * alpha_pow2));
-              } else {
-                const double cr_ = epi_f2d(Hr) + epi_f2d(Lr), ci_ = epi_f2d(Hi) + epi_f2d(Li);
-                v = make_double2(alpha.x * cr_ - alpha.y * ci_, alpha.x * ci_ + alpha.y * cr_);
-              }
-              double2* dst = strided ? Cz + moff[col] + noff : Cz + (int64_t)m * ldc + n;
-              if (use_beta) {
-                const double2 o = *dst;
-                if (beta_one) {
-                  v.x += o.x;
-                  v.y += o.y;
-                } else {
-                  v.x += beta.x * o.x - beta.y * o.y;
-                  v.y += beta.x * o.y + beta.y * o.x;
-                }
-              }
-              *dst = v;
+          const int m = m0 + col;
+          if (n < n_rows && m < m_rows) {
+            const float2 l = lrow[col * BM];
+            double2 v;
+            if (alpha_pow2 != 0.0f) {   // real power-of-two alpha: exact FP32 scaling
+              v = make_double2(epi_f2d(Hr[j] * alpha_pow2) + epi_f2d(l.x * alpha_pow2),
+                               epi_f2d(Hi[j] * alpha_pow2) + epi_f2d(l.y * alpha_pow2));
+            } else {
+              const double cr_ = epi_f2d(Hr[j]) + epi_f2d(l.x), ci_ = epi_f2d(Hi[j]) + epi_f2d(l.y);
+              v = make_double2(alpha.x * cr_ - alpha.y * ci_, alpha.x * ci_ + alpha.y * cr_);
             }
+            double2* dst = strided ? Cz + moff[col] + noff : Cz + (int64_t)m * ldc + n;
+            if (use_beta) {
+              const double2 o = *dst;
+              if (beta_one) {
+                v.x += o.x;
+                v.y += o.y;
+              } else {
+                v.x += beta.x * o.x - beta.y * o.y;
+                v.y += beta.x * o.y + beta.y * o.x;
+              }
+            }
+            *dst = v;
           }
         }
       }
@@ -1604,7 +1621,6 @@ void tc_gemm_x(Ctx& c, const Slices& sn, const Slices& sm, cplx alpha, cplx beta
   const int64_t ytiles = (N + tc::BM - 1) / tc::BM, xtiles = (M + tc::x::BN - 1) / tc::x::BN;
   CCLR_REQUIRE(xtiles * ytiles * S < (int64_t)INT32_MAX, CCLR_E_ARG, "tc_gemm: too many tiles");
   const int grid = (int)std::min<int64_t>(xtiles * ytiles * S, num_sms());
-  float4* fstate = (float4*)c.ws.alloc(sizeof(float4) * (size_t)grid * tc::BM * tc::x::BN);
   // the B-side map with the 64-row box of this kernel (the cached map has 128-row boxes)
   const CUtensorMap tmB = make_map(sm.p, sm.rows, sm.Kpad, 2 * sm.nsl, tc::x::BN);
   const tc::PairsX pairs = pairs_x(sn.ndig, sm.ndig);
@@ -1622,11 +1638,11 @@ void tc_gemm_x(Ctx& c, const Slices& sn, const Slices& sm, cplx alpha, cplx beta
   if (S > 1)
     tc::k_tc_zgemm_x<<<grid, tc::x::THREADS, tc::x::SMEM_BYTES, c.stream>>>(
         sn.tm, tmB, (int)N, (int)M, kblocks, kb_per, pairs, make_double2(1.0, 0.0), 1.0f, make_double2(0.0, 0.0), P, N,
-        M * N, c.tc_err, (int)xtiles, (int)ytiles, S, om, false, fstate);
+        M * N, c.tc_err, (int)xtiles, (int)ytiles, S, om, false);
   else
     tc::k_tc_zgemm_x<<<grid, tc::x::THREADS, tc::x::SMEM_BYTES, c.stream>>>(
         sn.tm, tmB, (int)N, (int)M, kblocks, kb_per, pairs, alpha, apow2, beta, C, ldc, 0, c.tc_err, (int)xtiles,
-        (int)ytiles, 1, om, oa != nullptr, fstate);
+        (int)ytiles, 1, om, oa != nullptr);
   const cudaError_t le = cudaGetLastError();
   CCLR_REQUIRE(le == cudaSuccess, CCLR_E_CUDA,
                std::string("FP64-class tensor-core GEMM launch failed (") + cudaGetErrorString(le) + ") M=" +
