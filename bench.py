@@ -50,6 +50,33 @@ def sigma_cmac(o: int, v: int) -> float:
     return Po * Pv * Pv + o**3 * v**3 + 5.5 * o**2 * v**3 + 6 * o**3 * v**2 + o**4 * v**2 / 4
 
 
+# The per-vector contractions of the CC Hessian product (u F) as the library runs them (SI working
+# equations for (t^X F), unpacked tensors); z is the batch index.
+HESSIAN_TERMS = (
+    "kica,zia->zkc ka,zia->zik ic,zik->zkc ic,zia->zca ka,zca->zkc eica,zia->zec ke,zec->zkc kima,zia->zkm "
+    "mc,zkm->zkc ma,zia->zim ikmc,zim->zkc ie,zia->zea ekac,zea->zkc kjab,zijab->zki ic,zki->zkc "
+    "ijcb,zijab->zca ka,zca->zkc ia,zijab->zjb jkbc,zjb->zkc mkae,zia->zmkei zmkei,iecm->zkc keam,zia->zekmi "
+    "imec,zekmi->zkc kifa,zia->zkf fc,zkf->zkc nica,zia->znc kn,znc->zkc fa,zia->zif ikfc,zif->zkc "
+    "in,zia->zna nkac,zna->zkc ijac,zijab->zcb kb,zcb->zkc ikab,zijab->zkj jc,zkj->zkc ikeb,zijab->zkeja "
+    "zkeja,ejac->zkc ikmb,zijab->zkmja mjac,zkmja->zkc ekab,zijab->zekij ijec,zekij->zkc mkab,zijab->zmkij "
+    "ijmc,zmkij->zkc ijae,zijab->zeb ekbc,zeb->zkc imab,zijab->zmj jkmc,zmj->zkc lida,zia->zld kc,zld->zklcd "
+    "ka,zia->zki ikab,zijab->zkj zki,ilcd->zklcd ic,zia->zca ijac,zijab->zcb zca,klad->zklcd la,zia->zli "
+    "lima,zia->zlm ljab,zijab->zli kicd,zli->zklcd id,zia->zda eida,zia->zde ijdb,zijab->zda "
+    "klca,zda->zklcd klma,zia->zklmi klab,zijab->zklij micd,zklmi->zklcd kimd,zia->zkmda lida,zijab->zljdb "
+    "ekdf,zif->zkide mlca,zkmda->zklcd klea,zia->zklei zklei,eicd->zklcd klab,zijab->zklij zklij,ijcd->zklcd"
+).split()
+
+
+def hessian_cmac(o: int, v: int) -> float:
+    """Complex MACs of one Hessian product: per contraction, the product of the index ranges
+    over both operands' indices (occupied i..n -> o, virtual a..f -> v)."""
+    tot = 0.0
+    for t in HESSIAN_TERMS:
+        idx = set(t.split("->")[0].replace(",", "")) - {"z"}
+        tot += float(np.prod([o if ch in "ijklmn" else v for ch in idx]))
+    return tot
+
+
 def prec_of(pk, name: str) -> int:
     return {"bf16x3": pk.TC_BF16X3, "bf16x6": pk.TC_BF16X6, "f64tc": pk.TC_F64, "fp64": pk.FP64}[name]
 
@@ -429,7 +456,6 @@ def run_batch(args):
     t0 = time.perf_counter()
     batched = pk.cclr_response_batch(cs, [i.ops for i in insts], om, gamma)
     out["batched_seconds"] = time.perf_counter() - t0
-    out["sigma_products"] = [c.cclr_get_stats()["sigma_vectors"] for c in cs]
     for c in cs:
         c.close()
     seq = []
@@ -663,7 +689,11 @@ def main():
     t_local = ev0.elapsed_time(ev1) / 1e3 / args.steps
     t_step = allreduce(t_local, world, "max")
     n_prod = statistics.mean(s["ground_iters"] + s["lambda_sigma"] + s["lr_sigma"] + s["hessian"] for s in stats)
-    flops = 8 * sigma_cmac(o, v) * n_prod
+
+    def step_cmac(st):   # sigma-type products at the sigma count, Hessian products at their own
+        return (sigma_cmac(o, v) * (st["ground_iters"] + st["lambda_sigma"] + st["lr_sigma"])
+                + hessian_cmac(o, v) * st["hessian"])
+    flops = 8 * statistics.mean(step_cmac(s) for s in stats)
     value = allreduce(flops / t_step / 1e12, world, "sum")
 
     # end to end through the C ABI: pinned host inputs copied in, response function copied out
@@ -674,8 +704,7 @@ def main():
         ctx.cclr_set_hamiltonian(o, v, host[0], host[1:7])
         st = step()
         t_e2e = allreduce(time.perf_counter() - t0, world, "max")
-        n_e2e = st["ground_iters"] + st["lambda_sigma"] + st["lr_sigma"] + st["hessian"]
-        e2e = dict(value=allreduce(8 * sigma_cmac(o, v) * n_e2e / t_e2e / 1e12, world, "sum"), unit="TFLOP/s",
+        e2e = dict(value=allreduce(8 * step_cmac(st) / t_e2e / 1e12, world, "sum"), unit="TFLOP/s",
                    h2d_bytes_per_step=int(h2d), d2h_bytes_per_step=int(st["resp"].nbytes), seconds=t_e2e)
 
     # plain-FP64 comparison at full size: one FP64 right sigma vector timed alone (outside the
@@ -688,8 +717,10 @@ def main():
         t0 = time.perf_counter()
         ctx.cclr_sigma(x, side=0, precision=pk.FP64)
         fp64_sigma = time.perf_counter() - t0
-        fp64 = dict(sigma_seconds=fp64_sigma, step_seconds_extrapolated=fp64_sigma * n_prod,
-                    note="extrapolated, not measured: sigma-type products of this step x one FP64 sigma")
+        fp64 = dict(sigma_seconds=fp64_sigma,
+                    step_seconds_extrapolated=fp64_sigma * statistics.mean(step_cmac(s) for s in stats) / sigma_cmac(o, v),
+                    note="extrapolated, not measured: this step's work (Hessian products at their own cost) in "
+                         "units of one FP64 sigma")
     # per-kernel shares: one extra untimed step with CUDA events around every launch
     breakdown = None
     if rank == 0 and not args.no_breakdown:
@@ -740,28 +771,19 @@ def main():
     pk_, src = peaks()
     peak = pk_.get("bf16_tflops_sustained", pk_["bf16_tflops"])
     alpha = -stats[-1]["resp"]
-    # Roofline of the tensor-core kernels.  Split BF16 (k_tc_zgemm): algorithmic work by the
-    # sigma-count rule, 3 slice products x 8 BF16 flops per complex MAC of every mixed-phase
-    # sigma-type product.  FP64-class (k_tc_zgemm_x): the BF16 flops of the digit products the
-    # method needs for the operands it is given, counted by the library per launch (8 per complex
-    # MAC and digit pair: 15 pairs for full operands, 9 for coarse corrections); beside it the
-    # FP64-equivalent rate (8 flops per complex MAC of the emulated FP64 product).
-    n_ref = statistics.mean(s["refine_products"] for s in stats)
+    # Roofline of the tensor-core kernels on the BF16 flops of the slice or digit products the
+    # method needs for the operands of each launch, counted by the library (8 per complex MAC and
+    # product: 3 slice products in split BF16, 6 in the FP32-class split, 15 digit pairs for full
+    # FP64-class operands and 9 for coarse corrections); beside it the rate of the complex
+    # products themselves (8 flops per complex MAC: FP64-equivalent for the FP64-class kernel).
     per_kernel = {}
-    pr = prof
-    ms = pr["ms"] / args.steps
-    per_kernel["k_tc_zgemm"] = dict(
-        kernel_ms_per_step=ms, launches_per_step=pr["launches"] / args.steps,
-        achieved_tflops=(24.0 * sigma_cmac(o, v) * (n_prod - n_ref) / (ms * 1e-3) / 1e12 if ms > 0 else None),
-        achieved_rule="24 BF16 flops x sigma complex MACs x mixed-phase sigma-type products",
-        executed_tflops=(pr["flops_exec"] / args.steps / (ms * 1e-3) / 1e12 if ms > 0 else None))
-    pr = prof["f64"]
-    ms = pr["ms"] / args.steps
-    per_kernel["k_tc_zgemm_x"] = dict(
-        kernel_ms_per_step=ms, launches_per_step=pr["launches"] / args.steps,
-        achieved_tflops=(pr["flops_exec"] / args.steps / (ms * 1e-3) / 1e12 if ms > 0 else None),
-        achieved_rule="8 BF16 flops x complex MACs x digit pairs of each launch (library count)",
-        fp64_equivalent_tflops=(pr["flops_useful"] / args.steps / (ms * 1e-3) / 1e12 if ms > 0 else None))
+    for name, pr in (("k_tc_zgemm", prof), ("k_tc_zgemm_x", prof["f64"])):
+        ms = pr["ms"] / args.steps
+        per_kernel[name] = dict(
+            kernel_ms_per_step=ms, launches_per_step=pr["launches"] / args.steps,
+            achieved_tflops=(pr["flops_exec"] / args.steps / (ms * 1e-3) / 1e12 if ms > 0 else None),
+            achieved_rule="8 BF16 flops x complex MACs x slice or digit products of each launch (library count)",
+            complex_product_tflops=(pr["flops_useful"] / args.steps / (ms * 1e-3) / 1e12 if ms > 0 else None))
     dom = max(per_kernel, key=lambda k: per_kernel[k]["kernel_ms_per_step"])
     achieved = per_kernel[dom]["achieved_tflops"]
     line = dict(

@@ -397,34 +397,42 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // each 256-deep chunk, groups in order: each group's accumulator is drained by the epilogue while
 // the later groups of the chunk run, and the last group (9 pairs) while the next chunk's first
 // three groups run.  TMEM: g0 | g1 | g2 | g34, each Cr (64) | Ci (64) = 512 columns.
-// Warp 0: TMA producer; warp 1: MMA issuer; warps 2..17: epilogue (TMEM lane quarter warp % 4,
-// 16 columns each), keeping the float-float sums of their 16 elements across the chunks of a tile
-// (high words in registers, low words in shared memory: 18 warps leave 96 registers a thread) and
+// Tiles of 128 x 128 (MMA N = 128: 64-wide tiles run the tensor pipe at about half rate).  The
+// four accumulator groups share two TMEM slots of (re, im) x 128 columns in turn.  Warp 0: TMA
+// producer; warp 1: MMA issuer; warps 2..17: epilogue (TMEM lane quarter warp % 4, 32 columns
+// each), keeping the float-float sums of the tile in a per-CTA global buffer between chunks and
 // writing C (alpha, beta in FP64) after the last chunk.
 namespace x {
 constexpr int NS = 5;                             // digits (slices) per operand
-constexpr int BN = 64;                            // MMA N = m rows per tile
+constexpr int BN = 128;                           // MMA N = m rows per tile
 constexpr int STAGES = 3;
 constexpr int A_PLANE = BM * BK * 2;              // 16 KB
-constexpr int B_PLANE = BN * BK * 2;              // 8 KB
+constexpr int B_PLANE = BN * BK * 2;              // 16 KB
 constexpr int STAGE_BYTES = 2 * A_PLANE + 2 * B_PLANE;
 constexpr int RING_BYTES = STAGES * STAGE_BYTES;
 constexpr int CK = 4;                             // k-blocks per chunk (256 K values)
 constexpr int EPI_WARPS = 16;
 constexpr int EPI_THREADS = 32 * EPI_WARPS;
 constexpr int THREADS = 64 + EPI_THREADS;
-constexpr int LO_OFFSET = RING_BYTES + 256 /*barriers*/ + BN * 8 /*row offsets*/;
-constexpr int LO_BYTES = BM * BN * 8;             // low words of the float-float sums (re, im)
-constexpr int SMEM_BYTES = LO_OFFSET + LO_BYTES + 1024 /*align*/;
-constexpr int TMEM_COLS = 512;
+constexpr int COLS = BN / 4;                      // columns of one epilogue thread
+constexpr int SMEM_BYTES = RING_BYTES + 256 /*barriers*/ + BN * 8 /*row offsets*/ + 1024 /*align*/;
+constexpr int NSLOT = 2;                          // TMEM accumulator slots, (re, im) x BN columns each
+constexpr int TMEM_COLS = NSLOT * 2 * BN;
 constexpr int MAX_PAIRS = 15;
 constexpr int NG = 4;                             // accumulator groups
 }  // namespace x
 
+// Digit pairs sorted by accumulator group, and the schedule of the two TMEM slots: the groups
+// present take the slots in turn (group order), so before its first pair of a chunk a group waits
+// for the drain of the slot's previous user: the group two places earlier in the same chunk, or
+// the slot's last user in the previous chunk.
 struct PairsX {
   int n;
   int sa[x::MAX_PAIRS], sb[x::MAX_PAIRS], grp[x::MAX_PAIRS];
-  int first[x::NG], last[x::NG];   // first / last pair index of each group (pairs sorted by group)
+  int first[x::NG], last[x::NG];   // first / last pair index of each group (-1: group absent)
+  int slot[x::NG];                 // TMEM slot of each present group
+  int wait_grp[x::NG];             // group whose drain frees the slot
+  int wait_same[x::NG];            // 1: that drain belongs to the same chunk, 0: to the previous one
 };
 
 // OR of q over the epilogue threads of k_tc_zgemm_x (named barrier 1)
@@ -472,18 +480,17 @@ __global__ void __launch_bounds__(x::THREADS, 1)
     k_tc_zgemm_x(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int n_rows, int m_rows,
                  int kblocks, int kb_per, PairsX pairs, double2 alpha, float alpha_pow2, double2 beta,
                  double2* __restrict__ C, int64_t ldc, int64_t cz, int* __restrict__ err, int xtiles, int ytiles,
-                 int nsplit, const OutMap om, bool strided) {
+                 int nsplit, const OutMap om, bool strided, float2* __restrict__ fstate) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = (uint64_t*)(smem + x::RING_BYTES);
   uint64_t* empty = full + x::STAGES;
   uint64_t* gfull = empty + x::STAGES;   // chunk sums of group g ready (MMA commit)
-  uint64_t* gempty = gfull + x::NG;      // the same accumulators drained (all epilogue threads)
+  uint64_t* gempty = gfull + x::NG;      // the slot of group g drained (all epilogue threads)
   uint64_t* done = gempty + x::NG;
   uint32_t* tmem_slot = (uint32_t*)(done + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
   int64_t* moff = (int64_t*)(smem + x::RING_BYTES + 256);
-  float2* lo = (float2*)(smem + x::LO_OFFSET);   // [col][row] low words (re, im)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < x::STAGES; ++s) {
@@ -550,13 +557,13 @@ __global__ void __launch_bounds__(x::THREADS, 1)
           const int c1 = min(kb1, c0 + x::CK);
           for (int p = 0; p < pairs.n && ok; ++p) {
             const int grp = pairs.grp[p];
-            const int slot = grp;   // accumulator of this pair
             if (p == pairs.first[grp]) {
-              // the accumulator of this group must have been drained (previous chunk)
-              if (!mbar_wait(&gempty[slot], ((uint32_t)cc & 1u) ^ 1u)) { atomicExch(err, 14); *abort_flag = 1; ok = false; break; }
+              // the slot of this group must have been drained by its previous user
+              const uint32_t par = ((uint32_t)cc & 1u) ^ (pairs.wait_same[grp] ? 0u : 1u);
+              if (!mbar_wait(&gempty[pairs.wait_grp[grp]], par)) { atomicExch(err, 14); *abort_flag = 1; ok = false; break; }
               fence_after();
             }
-            const uint32_t cr = tmem + (uint32_t)slot * 2 * x::BN, ci = cr + x::BN;
+            const uint32_t cr = tmem + (uint32_t)pairs.slot[grp] * 2 * x::BN, ci = cr + x::BN;
             for (int kb = c0; kb < c1; ++kb, ++g) {
               const int s = g % x::STAGES;
               const uint32_t ph = (uint32_t)(g / x::STAGES) & 1u;
@@ -577,14 +584,20 @@ __global__ void __launch_bounds__(x::THREADS, 1)
               }
               mma_commit(&empty[s]);
             }
-            if (ok && p == pairs.last[grp]) mma_commit(&gfull[slot]);
+            if (ok && p == pairs.last[grp]) mma_commit(&gfull[grp]);
           }
         }
       }
       mma_commit(done);
     }
   } else {
-    // ---------------- epilogue warps 2..17: TMEM lane quarter warp % 4, columns 16 ch .. 16 ch + 15
+    // ---------------- epilogue warps 2..17: TMEM lane quarter warp % 4 (rows n0 + 32 (warp % 4) ..),
+    // columns COLS ch .. COLS ch + COLS - 1, ch = (warp - 2) / 4.  Per chunk the exact sums of
+    // groups 0 and 1 (drained together; two_sum of the pair is exact) are added to the running
+    // float-float sums, and the FP32 sums of groups 2 and 3..4 (~2^-16 and ~2^-24 of the result)
+    // to their low words.  The running sums of the CTA's tile live in its slice of fstate,
+    // [hi | lo][col][row] float2 (re, im): a warp's 32 rows are contiguous, and every element is
+    // touched by one thread only.
     const int et = threadIdx.x - 64;
     const int lg = warp & 3;
     const int ch = (warp - 2) >> 2;
@@ -592,6 +605,11 @@ __global__ void __launch_bounds__(x::THREADS, 1)
     const uint32_t lane_base = (uint32_t)(lg * 32) << 16;
     const bool use_beta = (beta.x != 0.0 || beta.y != 0.0);
     const bool beta_one = (beta.x == 1.0 && beta.y == 0.0);
+    float2* hi = fstate + (size_t)blockIdx.x * 2 * BM * x::BN + row;   // element (col, row) at hi[col * BM]
+    float2* lo = hi + BM * x::BN;
+    const bool has1 = pairs.first[1] >= 0;
+    const uint32_t s0 = tmem + lane_base + (uint32_t)pairs.slot[0] * 2 * x::BN + x::COLS * ch;
+    const uint32_t s1 = tmem + lane_base + (uint32_t)(has1 ? pairs.slot[1] : 0) * 2 * x::BN + x::COLS * ch;
     int cc = 0;
     bool stop = false;
     for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
@@ -608,67 +626,64 @@ __global__ void __launch_bounds__(x::THREADS, 1)
       if (group_any_x(*abort_flag != 0)) break;   // also publishes this tile's offsets
       const int n = n0 + row;
       const int64_t noff = (strided && n < n_rows) ? out_off((uint32_t)n, om.nn, om.ndim, om.nstr, om.nmul, om.nshr) : 0;
-      // running float-float sums of this thread's 16 elements: high words in registers, low
-      // words in shared memory ([col][row]: a warp's 32 rows are contiguous)
-      float Hr[16], Hi[16];
-      float2* lrow = lo + row;
-#pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        Hr[k] = 0.0f;
-        Hi[k] = 0.0f;
-        lrow[(16 * ch + k) * BM] = make_float2(0.0f, 0.0f);
-      }
       for (int ci = 0; ci < nch; ++ci, ++cc) {
         const uint32_t cpar = (uint32_t)cc & 1u;
-        // groups 0 and 1: exact chunk sums, folded 4 columns at a time (two_sum of the pair is exact)
+        const bool firstc = ci == 0;
         bool ready = mbar_wait(&gfull[0], cpar);
         if (group_any_x(!ready)) { if (et == 0) atomicExch(err, 13); *abort_flag = 1; stop = true; break; }
-        ready = mbar_wait(&gfull[1], cpar);
-        if (group_any_x(!ready)) { if (et == 0) atomicExch(err, 13); *abort_flag = 1; stop = true; break; }
+        if (has1) {
+          ready = mbar_wait(&gfull[1], cpar);
+          if (group_any_x(!ready)) { if (et == 0) atomicExch(err, 13); *abort_flag = 1; stop = true; break; }
+        }
         fence_after();
-#pragma unroll
-        for (int h = 0; h < 4; ++h) {
-          uint32_t a_re[4], a_im[4], b_re[4], b_im[4];
-          tmem_ld4(tmem + lane_base + 16 * ch + 4 * h, a_re);
-          tmem_ld4(tmem + lane_base + x::BN + 16 * ch + 4 * h, a_im);
-          tmem_ld4(tmem + lane_base + 2 * x::BN + 16 * ch + 4 * h, b_re);
-          tmem_ld4(tmem + lane_base + 3 * x::BN + 16 * ch + 4 * h, b_im);
+#pragma unroll 2
+        for (int q = 0; q < x::COLS / 4; ++q) {
+          uint32_t a_re[4], a_im[4], b_re[4] = {0u, 0u, 0u, 0u}, b_im[4] = {0u, 0u, 0u, 0u};
+          tmem_ld4(s0 + 4 * q, a_re);
+          tmem_ld4(s0 + x::BN + 4 * q, a_im);
+          if (has1) {
+            tmem_ld4(s1 + 4 * q, b_re);
+            tmem_ld4(s1 + x::BN + 4 * q, b_im);
+          }
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
-            const int k = 4 * h + j;
-            float2* lp = lrow + (16 * ch + k) * BM;
+            const int col = x::COLS * ch + 4 * q + j;
             float sr, er, si, ei;
             two_sum(__uint_as_float(a_re[j]), __uint_as_float(b_re[j]), sr, er);
             two_sum(__uint_as_float(a_im[j]), __uint_as_float(b_im[j]), si, ei);
-            float2 l = *lp;
-            ff_add(Hr[k], l.x, sr, er);
-            ff_add(Hi[k], l.y, si, ei);
-            *lp = l;
+            if (firstc) {
+              hi[col * BM] = make_float2(sr, si);
+              lo[col * BM] = make_float2(er, ei);
+            } else {
+              float2 h = hi[col * BM], l = lo[col * BM];
+              ff_add(h.x, l.x, sr, er);
+              ff_add(h.y, l.y, si, ei);
+              hi[col * BM] = h;
+              lo[col * BM] = l;
+            }
           }
         }
         fence_before();
         mbar_arrive(&gempty[0]);
-        mbar_arrive(&gempty[1]);
-        // groups 2 and 3..4 (FP32 sums, ~2^-16 and ~2^-24 of the result) into the low parts; the
-        // next float-float addition renormalises
-#pragma unroll
+        if (has1) mbar_arrive(&gempty[1]);
         for (int gq = 2; gq < x::NG; ++gq) {
+          if (pairs.first[gq] < 0) continue;   // group absent (same for every thread)
           ready = mbar_wait(&gfull[gq], cpar);
           if (group_any_x(!ready)) { if (et == 0) atomicExch(err, 13); *abort_flag = 1; stop = true; break; }
           fence_after();
-          const uint32_t gbase = tmem + lane_base + (uint32_t)gq * 2 * x::BN + 16 * ch;
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
+          const uint32_t gbase = tmem + lane_base + (uint32_t)pairs.slot[gq] * 2 * x::BN + x::COLS * ch;
+#pragma unroll 2
+          for (int q = 0; q < x::COLS / 8; ++q) {
             uint32_t q_re[8], q_im[8];
-            tmem_ld8(gbase + 8 * h, q_re);
-            tmem_ld8(gbase + x::BN + 8 * h, q_im);
+            tmem_ld8(gbase + 8 * q, q_re);
+            tmem_ld8(gbase + x::BN + 8 * q, q_im);
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-              float2* lp = lrow + (16 * ch + 8 * h + j) * BM;
-              float2 l = *lp;
+              const int col = x::COLS * ch + 8 * q + j;
+              float2 l = lo[col * BM];
               l.x = __fadd_rn(l.x, __uint_as_float(q_re[j]));
               l.y = __fadd_rn(l.y, __uint_as_float(q_im[j]));
-              *lp = l;
+              lo[col * BM] = l;
             }
           }
           fence_before();
@@ -677,35 +692,34 @@ __global__ void __launch_bounds__(x::THREADS, 1)
         if (stop) break;
       }
       if (stop) break;
-      {
-        // C = alpha (hi + lo) + beta C in FP64 (fully unrolled: the sums stay in registers)
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int col = 16 * ch + j;
-          const int m = m0 + col;
-          if (n < n_rows && m < m_rows) {
-            const float2 l = lrow[col * BM];
-            double2 v;
-            if (alpha_pow2 != 0.0f) {   // real power-of-two alpha: exact FP32 scaling
-              v = make_double2(epi_f2d(Hr[j] * alpha_pow2) + epi_f2d(l.x * alpha_pow2),
-                               epi_f2d(Hi[j] * alpha_pow2) + epi_f2d(l.y * alpha_pow2));
-            } else {
-              const double cr_ = epi_f2d(Hr[j]) + epi_f2d(l.x), ci_ = epi_f2d(Hi[j]) + epi_f2d(l.y);
-              v = make_double2(alpha.x * cr_ - alpha.y * ci_, alpha.x * ci_ + alpha.y * cr_);
-            }
-            double2* dst = strided ? Cz + moff[col] + noff : Cz + (int64_t)m * ldc + n;
-            if (use_beta) {
-              const double2 o = *dst;
-              if (beta_one) {
-                v.x += o.x;
-                v.y += o.y;
-              } else {
-                v.x += beta.x * o.x - beta.y * o.y;
-                v.y += beta.x * o.y + beta.y * o.x;
-              }
-            }
-            *dst = v;
+      // C = alpha (hi + lo) + beta C in FP64 (a split without k-blocks contributes zero)
+#pragma unroll 4
+      for (int j = 0; j < x::COLS; ++j) {
+        const int col = x::COLS * ch + j;
+        const int m = m0 + col;
+        if (n < n_rows && m < m_rows) {
+          const float2 h = nch > 0 ? hi[col * BM] : make_float2(0.0f, 0.0f);
+          const float2 l = nch > 0 ? lo[col * BM] : make_float2(0.0f, 0.0f);
+          double2 v;
+          if (alpha_pow2 != 0.0f) {   // real power-of-two alpha: exact FP32 scaling
+            v = make_double2(epi_f2d(h.x * alpha_pow2) + epi_f2d(l.x * alpha_pow2),
+                             epi_f2d(h.y * alpha_pow2) + epi_f2d(l.y * alpha_pow2));
+          } else {
+            const double cr_ = epi_f2d(h.x) + epi_f2d(l.x), ci_ = epi_f2d(h.y) + epi_f2d(l.y);
+            v = make_double2(alpha.x * cr_ - alpha.y * ci_, alpha.x * ci_ + alpha.y * cr_);
           }
+          double2* dst = strided ? Cz + moff[col] + noff : Cz + (int64_t)m * ldc + n;
+          if (use_beta) {
+            const double2 o = *dst;
+            if (beta_one) {
+              v.x += o.x;
+              v.y += o.y;
+            } else {
+              v.x += beta.x * o.x - beta.y * o.y;
+              v.y += beta.x * o.y + beta.y * o.x;
+            }
+          }
+          *dst = v;
         }
       }
     }
@@ -1398,6 +1412,30 @@ tc::PairsX pairs_x(int nda = tc::x::NS, int ndb = tc::x::NS) {
     if (p.first[p.grp[k]] < 0) p.first[p.grp[k]] = k;
     p.last[p.grp[k]] = k;
   }
+  // TMEM slots: the groups present take slots 0, 1, 0, 1 in group order; a group waits for the
+  // drain of the slot's previous user (two groups earlier in the chunk, else the slot's last user
+  // in the previous chunk)
+  std::vector<int> present;
+  for (int q = 0; q < tc::x::NG; ++q) {
+    p.slot[q] = 0;
+    p.wait_grp[q] = q;
+    p.wait_same[q] = 0;
+    if (p.first[q] >= 0) present.push_back(q);
+  }
+  const int np = (int)present.size();
+  for (int k = 0; k < np; ++k) {
+    const int q = present[k];
+    p.slot[q] = k & 1;
+    if (k >= 2) {
+      p.wait_grp[q] = present[k - 2];
+      p.wait_same[q] = 1;
+    } else {
+      int m = np - 1;
+      while ((m & 1) != (k & 1)) --m;
+      p.wait_grp[q] = present[m];
+      p.wait_same[q] = 0;
+    }
+  }
   return p;
 }
 
@@ -1621,7 +1659,7 @@ void tc_gemm_x(Ctx& c, const Slices& sn, const Slices& sm, cplx alpha, cplx beta
   const int64_t ytiles = (N + tc::BM - 1) / tc::BM, xtiles = (M + tc::x::BN - 1) / tc::x::BN;
   CCLR_REQUIRE(xtiles * ytiles * S < (int64_t)INT32_MAX, CCLR_E_ARG, "tc_gemm: too many tiles");
   const int grid = (int)std::min<int64_t>(xtiles * ytiles * S, num_sms());
-  // the B-side map with the 64-row box of this kernel (the cached map has 128-row boxes)
+  float2* fstate = (float2*)c.ws.alloc(sizeof(float2) * 2 * (size_t)grid * tc::BM * tc::x::BN);
   const CUtensorMap tmB = make_map(sm.p, sm.rows, sm.Kpad, 2 * sm.nsl, tc::x::BN);
   const tc::PairsX pairs = pairs_x(sn.ndig, sm.ndig);
   // a real power-of-two alpha is applied exactly to the float-float sums (no FP64 multiply)
@@ -1638,11 +1676,11 @@ void tc_gemm_x(Ctx& c, const Slices& sn, const Slices& sm, cplx alpha, cplx beta
   if (S > 1)
     tc::k_tc_zgemm_x<<<grid, tc::x::THREADS, tc::x::SMEM_BYTES, c.stream>>>(
         sn.tm, tmB, (int)N, (int)M, kblocks, kb_per, pairs, make_double2(1.0, 0.0), 1.0f, make_double2(0.0, 0.0), P, N,
-        M * N, c.tc_err, (int)xtiles, (int)ytiles, S, om, false);
+        M * N, c.tc_err, (int)xtiles, (int)ytiles, S, om, false, fstate);
   else
     tc::k_tc_zgemm_x<<<grid, tc::x::THREADS, tc::x::SMEM_BYTES, c.stream>>>(
         sn.tm, tmB, (int)N, (int)M, kblocks, kb_per, pairs, alpha, apow2, beta, C, ldc, 0, c.tc_err, (int)xtiles,
-        (int)ytiles, 1, om, oa != nullptr);
+        (int)ytiles, 1, om, oa != nullptr, fstate);
   const cudaError_t le = cudaGetLastError();
   CCLR_REQUIRE(le == cudaSuccess, CCLR_E_CUDA,
                std::string("FP64-class tensor-core GEMM launch failed (") + cudaGetErrorString(le) + ") M=" +
