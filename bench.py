@@ -318,10 +318,11 @@ def run_accuracy_at_scale(args):
     o, v = w["n_occ"], w["n_vir"]
     inst = synth.make_instance(o, v)
     om = np.linspace(w["w_min"], w["w_max"], w["n_freq"])
-    out, alpha = dict(mode="accuracy_at_scale", workload=config_dict(args)["workload"]), {}
+    out, alpha = dict(mode="accuracy_at_scale", workload=config_dict(args)["workload"],
+                      max_subspace=args.max_subspace, sigma_batch=args.sigma_batch), {}
     for name, prec in (("reference_f64tc", pk.TC_F64), ("bf16x3_refined", pk.TC_BF16X3)):
         ctx = pk.Context(0, precision=prec, tol=w["tol"], ground_tol=1e-9, max_subspace=args.max_subspace,
-                         batch=8, maxit=100)
+                         batch=args.sigma_batch, maxit=100)
         t0 = time.perf_counter()
         ctx.cclr_set_hamiltonian(o, v, inst.fock, [inst.blocks[k] for k in synth.CLASSES])
         ctx.cc_ground()
@@ -420,6 +421,13 @@ def run_adjoint(args):
                                        for x in range(3)])
     print(json.dumps(out), flush=True)
 
+
+# The plain-FP64 step of the 30/200 workload, measured once: `python bench.py --precision fp64
+# --warmup 0 --steps 1 --no-e2e --no-breakdown --no-extra --no-cpu-baseline --no-accuracy` on a
+# B300 (2026-12-04) had not finished when stopped after 1500 s.
+FP64_STEP_30x200 = dict(lower_bound_seconds=1500.0,
+                        how="python bench.py --precision fp64 --warmup 0 --steps 1 (30/200, 16 frequencies, "
+                            "residual 1e-8) on a B300, stopped unfinished after 1500 s")
 
 C2_SYSTEMS = [(8, 60), (12, 90), (18, 120)]
 
@@ -591,6 +599,7 @@ def main():
     ap.add_argument("--accuracy-at-scale", action="store_true",
                     help="solve the workload refined and in the FP64-class mode; per-frequency alpha errors")
     ap.add_argument("--max-subspace", type=int, default=64, help="Davidson trial-space limit")
+    ap.add_argument("--sigma-batch", type=int, default=8, help="trial vectors per sigma call (--accuracy-at-scale)")
     ap.add_argument("--batch", action="store_true",
                     help="three uneven systems (8/60, 12/90, 18/120) solved as one batch and one by one")
     ap.add_argument("--adjoint", action="store_true",
@@ -721,6 +730,10 @@ def main():
                     step_seconds_extrapolated=fp64_sigma * statistics.mean(step_cmac(s) for s in stats) / sigma_cmac(o, v),
                     note="extrapolated, not measured: this step's work (Hessian products at their own cost) in "
                          "units of one FP64 sigma")
+        if args.workload == "30x200":
+            fp64["step_seconds_measured_lower_bound"] = FP64_STEP_30x200["lower_bound_seconds"]
+            fp64["measured_how"] = FP64_STEP_30x200["how"]
+            fp64["speedup_lower_bound"] = FP64_STEP_30x200["lower_bound_seconds"] / t_step
     # per-kernel shares: one extra untimed step with CUDA events around every launch
     breakdown = None
     if rank == 0 and not args.no_breakdown:

@@ -256,9 +256,10 @@ cclr_status cclr_gram(cclr_ctx *ctx, int mirror, int64_t n, int nx, int ny, cons
  *   ms3[0]  the Gram block X^H Y (nx x ny),
  *   ms3[1]  Y_q = sum_j X_j C_jq for m outputs, squared norms only (the residual-norm pass),
  *   ms3[2]  the same with the m outputs stored (the correction pass),
- * and returns milliseconds per call (CUDA events on the context's stream).  precision
- * CCLR_FP64 runs the FP64 kernels, the tensor-core modes the FP32-arithmetic ones the solver
- * uses there.  1 <= m <= 16, nx <= 512.  Needs a Hamiltonian (for the context's workspace). */
+ * and returns milliseconds per call (CUDA events on the context's stream).  The arithmetic is
+ * the solver's for that precision: FP32 pairs in the mixed modes (CCLR_TC_BF16X3, BF16X6),
+ * float-float in CCLR_FP64 and CCLR_TC_F64 (the refinement's passes).  1 <= m <= 16, nx <= 512.
+ * Needs a Hamiltonian (for the context's workspace). */
 cclr_status cclr_bench_vector_kernels(cclr_ctx *ctx, int precision, int64_t n, int nx, int ny, int m, int reps,
                                       double *ms3);
 

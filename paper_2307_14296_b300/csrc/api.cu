@@ -630,7 +630,7 @@ cclr_status cclr_bench_vector_kernels(cclr_ctx* h, int precision, int64_t n, int
                  CCLR_E_ARG, "bad vector-kernel benchmark arguments");
     CCLR_REQUIRE(valid_precision(precision), CCLR_E_ARG, "unknown precision");
     const bool saved = c.L.fast32;
-    c.L.fast32 = precision != CCLR_FP64;
+    c.L.fast32 = mixed_precision(precision);   // the solver's rule: FP32 pairs, else float-float
     cplx *X = nullptr, *Y = nullptr, *C = nullptr, *G = nullptr, *scr = nullptr;
     double *vs = nullptr, *n2 = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
