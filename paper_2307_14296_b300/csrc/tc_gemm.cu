@@ -593,9 +593,9 @@ __global__ void __launch_bounds__(x::THREADS, 1)
   } else {
     // ---------------- epilogue warps 2..17: TMEM lane quarter warp % 4 (rows n0 + 32 (warp % 4) ..),
     // columns COLS ch .. COLS ch + COLS - 1, ch = (warp - 2) / 4.  Per chunk the exact sums of
-    // groups 0 and 1 (drained together; two_sum of the pair is exact) are added to the running
-    // float-float sums, and the FP32 sums of groups 2 and 3..4 (~2^-16 and ~2^-24 of the result)
-    // to their low words.  The running sums of the CTA's tile live in its slice of fstate,
+    // groups 0 and 1 are added to the running float-float sums (each drained as soon as it is
+    // complete), and the FP32 sums of groups 2 and 3..4 (~2^-16 and ~2^-24 of the result) to
+    // their low words.  The running sums of the CTA's tile live in its slice of fstate,
     // [hi | lo][col][row] float2 (re, im): a warp's 32 rows are contiguous, and every element is
     // touched by one thread only.
     const int et = threadIdx.x - 64;
@@ -629,46 +629,42 @@ __global__ void __launch_bounds__(x::THREADS, 1)
       for (int ci = 0; ci < nch; ++ci, ++cc) {
         const uint32_t cpar = (uint32_t)cc & 1u;
         const bool firstc = ci == 0;
-        bool ready = mbar_wait(&gfull[0], cpar);
-        if (group_any_x(!ready)) { if (et == 0) atomicExch(err, 13); *abort_flag = 1; stop = true; break; }
-        if (has1) {
-          ready = mbar_wait(&gfull[1], cpar);
+        // groups 0 and 1 one after the other, each an exact chunk sum added to the float-float
+        // sums (group 0's slot is free for group 2 while group 1 still runs)
+        for (int gx = 0; gx < 2; ++gx) {
+          if (gx == 1 && !has1) break;   // same for every thread
+          const bool ready = mbar_wait(&gfull[gx], cpar);
           if (group_any_x(!ready)) { if (et == 0) atomicExch(err, 13); *abort_flag = 1; stop = true; break; }
-        }
-        fence_after();
+          fence_after();
+          const uint32_t sb = gx == 0 ? s0 : s1;
 #pragma unroll 2
-        for (int q = 0; q < x::COLS / 4; ++q) {
-          uint32_t a_re[4], a_im[4], b_re[4] = {0u, 0u, 0u, 0u}, b_im[4] = {0u, 0u, 0u, 0u};
-          tmem_ld4(s0 + 4 * q, a_re);
-          tmem_ld4(s0 + x::BN + 4 * q, a_im);
-          if (has1) {
-            tmem_ld4(s1 + 4 * q, b_re);
-            tmem_ld4(s1 + x::BN + 4 * q, b_im);
-          }
+          for (int q = 0; q < x::COLS / 8; ++q) {
+            uint32_t a_re[8], a_im[8];
+            tmem_ld8(sb + 8 * q, a_re);
+            tmem_ld8(sb + x::BN + 8 * q, a_im);
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const int col = x::COLS * ch + 4 * q + j;
-            float sr, er, si, ei;
-            two_sum(__uint_as_float(a_re[j]), __uint_as_float(b_re[j]), sr, er);
-            two_sum(__uint_as_float(a_im[j]), __uint_as_float(b_im[j]), si, ei);
-            if (firstc) {
-              hi[col * BM] = make_float2(sr, si);
-              lo[col * BM] = make_float2(er, ei);
-            } else {
-              float2 h = hi[col * BM], l = lo[col * BM];
-              ff_add(h.x, l.x, sr, er);
-              ff_add(h.y, l.y, si, ei);
-              hi[col * BM] = h;
-              lo[col * BM] = l;
+            for (int j = 0; j < 8; ++j) {
+              const int col = x::COLS * ch + 8 * q + j;
+              const float xr = __uint_as_float(a_re[j]), xi = __uint_as_float(a_im[j]);
+              if (firstc && gx == 0) {
+                hi[col * BM] = make_float2(xr, xi);
+                lo[col * BM] = make_float2(0.0f, 0.0f);
+              } else {
+                float2 h = hi[col * BM], l = lo[col * BM];
+                ff_add(h.x, l.x, xr, 0.0f);
+                ff_add(h.y, l.y, xi, 0.0f);
+                hi[col * BM] = h;
+                lo[col * BM] = l;
+              }
             }
           }
+          fence_before();
+          mbar_arrive(&gempty[gx]);
         }
-        fence_before();
-        mbar_arrive(&gempty[0]);
-        if (has1) mbar_arrive(&gempty[1]);
+        if (stop) break;
         for (int gq = 2; gq < x::NG; ++gq) {
           if (pairs.first[gq] < 0) continue;   // group absent (same for every thread)
-          ready = mbar_wait(&gfull[gq], cpar);
+          const bool ready = mbar_wait(&gfull[gq], cpar);
           if (group_any_x(!ready)) { if (et == 0) atomicExch(err, 13); *abort_flag = 1; stop = true; break; }
           fence_after();
           const uint32_t gbase = tmem + lane_base + (uint32_t)pairs.slot[gq] * 2 * x::BN + x::COLS * ch;
