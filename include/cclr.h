@@ -158,6 +158,22 @@ cclr_status cc_response_function(cclr_ctx *ctx, cclr_c128 *out);
  * row-major.  Costs 4 n_ops left solves and Hessian products.  Requires cc_lr_solve. */
 cclr_status cclr_response_gradient(cclr_ctx *ctx, int f, cclr_c128 *out);
 
+/* A synthetic instance generated on the device and installed as the Hamiltonian (as
+ * cclr_set_hamiltonian with it), for measurements without host generation and host-to-device
+ * copies.  Recipe (the counter-based one of the Python package's synth.counter, bit for bit):
+ * Philox4x32-10 (Salmon et al., SC'11), counter (element index lo, hi, stream, 0), key (seed lo,
+ * hi); per element a Box-Muller pair from two 53-bit uniforms with logarithm and sine / cosine
+ * from fixed-order series in explicitly rounded FP64.  Orbital energies occupied U[-2, -0.5],
+ * virtual U[0.3, 4] (stream 0, each range sorted); the six antisymmetrized classes in the packed
+ * layouts of cclr_set_hamiltonian with Re, Im ~ N(0, sd^2) per canonical element (streams 1..6;
+ * the Hermitian classes real on their diagonal); n_ops Hermitian operators with entries
+ * N(0, dip_sd^2) (streams 100 + k) written to ops_out (n_ops x n x n, host or device memory;
+ * may be null when n_ops = 0).  Temporary device arrays of the packed class sizes are allocated
+ * and freed inside the call.  Errors as cclr_set_hamiltonian; CCLR_E_OOM if the temporaries do not
+ * fit. */
+cclr_status cclr_set_synthetic(cclr_ctx *ctx, int n_occ, int n_vir, uint64_t seed, double sd, double dip_sd,
+                               int n_ops, cclr_c128 *ops_out);
+
 /* eta of the CC energy at the current T: the derivative dE/dt in the amplitude layout (the Lambda
  * equations read t-bar A = -eta; Sec. 2.3 and the SI ground-state Lambda equations).  N values. */
 cclr_status cclr_eta_ground(cclr_ctx *ctx, cclr_c128 *out);

@@ -38,7 +38,7 @@ EXPORTS = (
     "cclr_eta", "cclr_hessian", "cclr_zgemm_nt", "cclr_kernel_profile", "cclr_get_stats",
     "cclr_zgemm_nt_noalloc", "cclr_kernel_breakdown", "cclr_bench_vector_kernels", "cclr_gram",
     "cclr_debug_expire_next_wait", "cclr_autotune_report", "cclr_response_batch", "cclr_response_gradient",
-    "cclr_eta_ground", "cclr_left_solve",
+    "cclr_eta_ground", "cclr_left_solve", "cclr_set_synthetic",
 )
 
 
@@ -88,6 +88,7 @@ _sig = {
     "cclr_autotune_report": (_i, [_vp, ctypes.c_char_p, _i]),
     "cclr_response_gradient": (_i, [_vp, _i, _vp]),
     "cclr_eta_ground": (_i, [_vp, _vp]),
+    "cclr_set_synthetic": (_i, [_vp, _i, _i, ctypes.c_uint64, _d, _d, _i, _vp]),
     "cclr_left_solve": (_i, [_vp, _i, _vp, _d, _d, _vp]),
     "cclr_response_batch": (_i, [ctypes.POINTER(_vp), _i, _i, ctypes.POINTER(_vp), _i, _vp, _d, ctypes.POINTER(_vp),
                                  _vp]),
@@ -198,6 +199,16 @@ class Context:
         arr = (_vp * 6)(*[b.ctypes.data for b in bl])
         self._check(_lib.cclr_set_hamiltonian(self._h, n_occ, n_vir, _ptr(fock), arr))
         self.n_occ, self.n_vir = n_occ, n_vir
+
+    def cclr_set_synthetic(self, n_occ, n_vir, seed, sd, dip_sd=0.1, n_ops=3):
+        """Generate the counter-based synthetic instance on the device and install it (see
+        cclr_set_synthetic in cclr.h); returns the operators (n_ops, n, n) as a host array."""
+        n = n_occ + n_vir
+        ops = np.zeros((n_ops, n, n), np.complex128)
+        self._check(_lib.cclr_set_synthetic(self._h, int(n_occ), int(n_vir), int(seed), float(sd), float(dip_sd),
+                                            int(n_ops), _ptr(ops) if n_ops else _vp()))
+        self.n_occ, self.n_vir = n_occ, n_vir
+        return ops
 
     def cc_ground(self):
         e = np.zeros(1, np.complex128)

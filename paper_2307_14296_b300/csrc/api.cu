@@ -384,6 +384,55 @@ cclr_status cclr_response_gradient(cclr_ctx* h, int f, cclr_c128* out) {
   });
 }
 
+cclr_status cclr_set_synthetic(cclr_ctx* h, int n_occ, int n_vir, uint64_t seed, double sd, double dip_sd,
+                               int n_ops, cclr_c128* ops_out) {
+  if (!h) return CCLR_E_ARG;
+  const int64_t o = n_occ, v = n_vir, n = o + v, Po = o * (o - 1) / 2, Pv = v * (v - 1) / 2;
+  const int64_t sizes[6] = {Po * Po, Po * o * v, Po * Pv, o * v * o * v, o * v * Pv, Pv * Pv};
+  cplx* blocks[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  double* eps_u = nullptr;
+  cplx* ops = nullptr;
+  std::vector<cclr_c128> fock((size_t)(n > 0 ? n * n : 0));
+  auto release = [&]() {
+    for (auto& b : blocks) { if (b) cudaFree(b); b = nullptr; }
+    if (eps_u) cudaFree(eps_u);
+    if (ops) cudaFree(ops);
+    eps_u = nullptr;
+    ops = nullptr;
+  };
+  // generation into temporary device arrays (not the context's workspace: the Hamiltonian setter
+  // below releases and re-creates it)
+  cclr_status st = guard(h, [&](Ctx& c) {
+    CCLR_REQUIRE(n_occ >= 2 && n_vir >= 2, CCLR_E_ARG, "need n_occ >= 2 and n_vir >= 2");
+    CCLR_REQUIRE(std::isfinite(sd) && sd >= 0.0 && std::isfinite(dip_sd) && dip_sd >= 0.0 && n_ops >= 0 &&
+                     (n_ops == 0 || ops_out),
+                 CCLR_E_ARG, "bad cclr_set_synthetic arguments");
+    for (int k = 0; k < 6; ++k) CCLR_CK(cudaMalloc((void**)&blocks[k], sizeof(cplx) * (size_t)std::max<int64_t>(1, sizes[k])));
+    CCLR_CK(cudaMalloc((void**)&eps_u, sizeof(double) * (size_t)n));
+    if (n_ops > 0) CCLR_CK(cudaMalloc((void**)&ops, sizeof(cplx) * (size_t)(n_ops * n * n)));
+    synthetic_instance(c, n_occ, n_vir, seed, sd, dip_sd, n_ops, blocks, eps_u, ops);
+    std::vector<double> u((size_t)n);
+    CCLR_CK(cudaMemcpyAsync(u.data(), eps_u, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, c.stream));
+    if (n_ops > 0)
+      CCLR_CK(cudaMemcpyAsync(ops_out, ops, sizeof(cplx) * (size_t)(n_ops * n * n), cudaMemcpyDefault, c.stream));
+    c.sync();
+    // orbital energies: occupied U[-2, -0.5], virtual U[0.3, 4], each range sorted
+    std::vector<double> eo((size_t)o), ev((size_t)v);
+    for (int64_t p = 0; p < o; ++p) eo[p] = -2.0 + (-0.5 - -2.0) * u[p];
+    for (int64_t p = 0; p < v; ++p) ev[p] = 0.3 + (4.0 - 0.3) * u[o + p];
+    std::sort(eo.begin(), eo.end());
+    std::sort(ev.begin(), ev.end());
+    for (int64_t p = 0; p < n; ++p) fock[(size_t)(p * n + p)].re = p < o ? eo[p] : ev[p - o];
+  });
+  if (st == CCLR_OK) {
+    const cclr_c128* bl[6];
+    for (int k = 0; k < 6; ++k) bl[k] = (const cclr_c128*)blocks[k];
+    st = cclr_set_hamiltonian(h, n_occ, n_vir, fock.data(), bl);
+  }
+  release();
+  return st;
+}
+
 cclr_status cclr_eta_ground(cclr_ctx* h, cclr_c128* out) {
   return guard(h, [&](Ctx& c) {
     CCLR_REQUIRE(c.have_hbar && out, CCLR_E_STATE, "cclr_eta_ground needs T");

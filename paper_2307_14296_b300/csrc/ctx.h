@@ -244,6 +244,8 @@ void response_function(Ctx& c, cplx* out_host);
 void response_function_ci(Ctx& c, cplx* out_host);
 void response_gradient(Ctx& c, int f, cplx* out_host);   // operator gradient of <<X;Y>> (adjoint)
 void left_solve(Ctx& c, int nrhs, const cplx* rhs, zc w, cplx* out);   // l (A + w) = -b
+void synthetic_instance(Ctx& c, int n_occ, int n_vir, uint64_t seed, double sd, double dip_sd, int n_ops,
+                        cplx* const blocks[6], double* eps_u, cplx* ops);   // counter-based instance
 int eom_ee(Ctx& c, int nroots, std::vector<zc>& w_out);
 
 // small dense complex linear algebra on the host
