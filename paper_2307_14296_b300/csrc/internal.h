@@ -250,6 +250,11 @@ struct VecMat {
   // X rows hold FP32 complex values (float2; row pointers cast to cplx*, strides in float2
   // elements): the FP32 mirrors of the solver's trial vectors.  Needs Launch::fast32.
   bool x32 = false;
+  // optional per-output additive rows (FP32 complex, float2 elements): r_q += addq[arow[q] * ldadd + i]
+  // (the stored anchor residuals of the refinement).  Needs Launch::fast32.
+  const void* addq = nullptr;
+  int64_t ldadd = 0;
+  int arow[16] = {};
 };
 // y[i] = x[i] rounded to FP32 (float2), n complex values (the solver's FP32 mirrors)
 void to_f32(const Launch& L, const cplx* x, void* y, int64_t n);

@@ -688,10 +688,14 @@ inline int vecmat_blocks() { return 4 * num_sms(); }
 // zero and never stored); each thread takes E elements per step so that every coefficient read
 // from shared memory serves E elements.  With F32 the whole element pipeline (products, sums,
 // preconditioner, accumulation into Y) runs in FP32 and only loads and stores touch FP64.
+struct AddRows {   // row index of each output's additive row (VecMat::arow)
+  int r[kVecMatOut];
+};
 template <bool F32, int Q, int E, int U, bool X32>
 __global__ void __launch_bounds__(kThreads, F32 ? 2 : 1)
     k_vecmat(int64_t n, Rows X, int m, const cplx* __restrict__ C, const cplx* __restrict__ add, cplx* Y, int64_t ldy,
-             bool acc, const double* __restrict__ D, const cplx* __restrict__ z, bool norm_y, double* part) {
+             bool acc, const double* __restrict__ D, const cplx* __restrict__ z, bool norm_y, double* part,
+             const float2* __restrict__ addq, int64_t ldadd, AddRows arow) {
   typedef Arith<F32> A;
   typedef typename A::C Cf;
   typedef typename std::conditional<F32, float, double>::type R;
@@ -773,6 +777,11 @@ __global__ void __launch_bounds__(kThreads, F32 ? 2 : 1)
           if constexpr (F32) {
             const float2 v = upk2(a[e][q]);
             r = make_float2(v.x + b.x, v.y + b.y);
+            if (addq) {
+              const float2 t = addq[(int64_t)arow.r[q] * ldadd + i];
+              r.x += t.x;
+              r.y += t.y;
+            }
           } else {
             const cplx v = A::to_cplx(a[e][q]);
             r = make_double2(v.x + b.x, v.y + b.y);
@@ -1288,8 +1297,10 @@ void launch_vecmat(const Launch& L, int64_t n, const VecMat& a, double* part) {
   static bool attr[64] = {};
   if (once_per_device(attr))   // kVecMatMaxRows x 16 coefficients (16 B each) + row table: 132 KiB
     CCLR_CK(cudaFuncSetAttribute(k_vecmat<F32, Q, E, U, X32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 136 << 10));
+  AddRows ar;
+  for (int q = 0; q < kVecMatOut; ++q) ar.r[q] = a.arow[q];
   k_vecmat<F32, Q, E, U, X32><<<vecmat_blocks(), kThreads, smem, L.s>>>(n, a.X, a.m, a.C, a.add, a.Y, a.ldy, a.acc, a.D, a.z,
-                                                              a.norm_y, part);
+                                                              a.norm_y, part, (const float2*)a.addq, a.ldadd, ar);
 }
 }  // namespace
 
@@ -1303,6 +1314,7 @@ void vecmat(const Launch& L, int64_t n, const VecMat& a, double* scratch) {
   double* part = a.norm2 ? scratch : nullptr;
   kbeg(L);
   CCLR_REQUIRE(!a.x32 || L.fast32, CCLR_E_ARG, "vecmat: FP32 rows need the FP32 arithmetic");
+  CCLR_REQUIRE(!a.addq || L.fast32, CCLR_E_ARG, "vecmat: additive FP32 rows need the FP32 arithmetic");
   if (a.x32) {
     if (a.m == 1) launch_vecmat<true, 1, true>(L, n, a, part);
     else if (a.m <= 4) launch_vecmat<true, 4, true>(L, n, a, part);

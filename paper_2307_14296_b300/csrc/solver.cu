@@ -295,6 +295,10 @@ struct System {            // one right-hand side with its shared trial space
   int iters = 0;
   double best = 1e300;     // best max-residual so far and its iteration (stagnation test)
   int best_it = 0;
+  // anchored residuals (refinement): r0_q (FP32 rows, one per shift) at the coefficients beta0
+  void* R0 = nullptr;
+  std::vector<std::vector<zc>> beta0;
+  bool anchor_ok = false;
 };
 
 // Orthonormal vectors spanning the columns cols (each of length L): Gram-Schmidt with column
@@ -505,8 +509,15 @@ int add_corrections(Ctx& c, cplx* B, int L, cplx* R, int nt, const double* pre2,
 // operands).  The rounding only changes which vectors span the space; every sigma vector is the
 // exact product of the stored vector.  The starting space keeps every digit: rounding a restart
 // space would throw away the accuracy it carries.
+// anchored (FP64-arithmetic solves that start from an accurate space, i.e. the refinement): the
+// residuals of later iterations are r_q = r0_q + (S - z_q B)(beta_q - beta0_q).  The anchor r0_q is
+// formed once in float-float after the first subspace solve (and again after a thick restart) and
+// kept as FP32 rows (|r0| is near the mixed phase's floor, so FP32 storage errs at ~1e-11 of the
+// right-hand side); the increment has coefficients of the size of the corrections and is formed in
+// FP32 arithmetic from the FP64 rows (HBM-bound instead of float-float compute-bound).  Without
+// device memory for the anchors the float-float passes are kept.
 void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, const cplx*, cplx*)>& Op,
-              int maxL, double tol, bool coarse = false) {
+              int maxL, double tol, bool coarse = false, bool anchored = false) {
   static const bool verbose = std::getenv("CCLR_VERBOSE") != nullptr;
   Fast32 f32(c);
   const bool mixed = mixed_precision(c.opt.precision);
@@ -565,16 +576,102 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
     if (Xf)
       for (int r = r0; r < r0 + nr; ++r) to_f32(c.L, X + (int64_t)r * N, (float2*)Xf + (int64_t)r * Np, N);
   };
-  auto residual_norms = [&](System& s, const std::vector<int>& qs) {
-    for (size_t g0 = 0; g0 < qs.size(); g0 += kVecMatOut) {
-      const int m = (int)std::min<size_t>(kVecMatOut, qs.size() - g0);
-      resid_coef(s, qs, g0, m);
+  // anchors
+  struct AnchorMem {
+    std::vector<System>& sys;
+    ~AnchorMem() {
+      for (auto& s : sys)
+        if (s.R0) { cudaFree(s.R0); s.R0 = nullptr; }
+    }
+  } anchor_mem{sys};
+  struct Arith32Scope {   // FP32 arithmetic for the anchored passes
+    Ctx& c;
+    bool old;
+    explicit Arith32Scope(Ctx& cc) : c(cc), old(cc.L.fast32) { c.L.fast32 = true; }
+    ~Arith32Scope() { c.L.fast32 = old; }
+  };
+  for (auto& s : sys) {
+    s.anchor_ok = false;
+    s.R0 = nullptr;
+    if (anchored && !mixed) {
+      if (cudaMalloc(&s.R0, sizeof(float2) * (size_t)Np * s.z.size()) != cudaSuccess) {
+        cudaGetLastError();
+        s.R0 = nullptr;   // float-float passes
+      }
+    }
+  }
+  // coefficients of the increment (beta_q - beta0_q) over the rows [S | B]
+  auto anchored_coef = [&](const System& s, const std::vector<int>& qs, size_t g0, int m) {
+    const int L = s.L;
+    std::vector<zc> C((size_t)2 * L * m);
+    for (int t = 0; t < m; ++t) {
+      const int q = qs[g0 + t];
+      for (int j = 0; j < L; ++j) {
+        const zc d = s.beta[q][j] - s.beta0[q][j];
+        C[(size_t)j * m + t] = d;
+        C[(size_t)(L + j) * m + t] = -s.z[q] * d;
+      }
+    }
+    to_dev(c, C.data(), cdev, (int64_t)2 * L * m);
+  };
+  auto anchored_args = [&](const System& s, const std::vector<int>& qs, size_t g0, int m, VecMat& a) {
+    anchored_coef(s, qs, g0, m);
+    a.X = Rows().add(s.S, s.L, N).add(s.B, s.L, N);
+    a.x32 = false;
+    a.m = m;
+    a.C = cdev;
+    a.add = nullptr;
+    a.addq = s.R0;
+    a.ldadd = Np;
+    for (int t = 0; t < m; ++t) a.arow[t] = qs[g0 + t];
+  };
+  // the anchor of every shift (float-float pass; also this iteration's residual norms)
+  auto compute_anchor = [&](System& s) {
+    std::vector<int> all(s.z.size());
+    for (size_t q = 0; q < all.size(); ++q) all[q] = (int)q;
+    Scope s3(c.ws);
+    cplx* Yt = c.ws.cplxs((int64_t)kVecMatOut * N);
+    for (size_t g0 = 0; g0 < all.size(); g0 += kVecMatOut) {
+      const int m = (int)std::min<size_t>(kVecMatOut, all.size() - g0);
+      resid_coef(s, all, g0, m);
       VecMat a;
       a.X = SB(s);
       a.x32 = s.Sf != nullptr;
       a.m = m;
       a.C = cdev;
       a.add = s.rhs;
+      a.Y = Yt;
+      a.ldy = N;
+      a.norm2 = n2dev;
+      vecmat(c.L, N, a, vscr);
+      double h[kVecMatOut];
+      CCLR_CK(cudaMemcpyAsync(h, n2dev, sizeof(double) * m, cudaMemcpyDeviceToHost, c.stream));
+      for (int t = 0; t < m; ++t)
+        to_f32(c.L, Yt + (int64_t)t * N, (float2*)s.R0 + (int64_t)all[g0 + t] * Np, N);
+      c.sync();
+      for (int t = 0; t < m; ++t) s.rnorm[all[g0 + t]] = std::sqrt(std::max(0.0, h[t]));
+    }
+    s.beta0 = s.beta;
+    for (auto& b0 : s.beta0)   // coefficients of later vectors start from zero
+      for (int j = s.L; j < (int)b0.size(); ++j) b0[j] = zc(0);
+    s.anchor_ok = true;
+  };
+  auto residual_norms = [&](System& s, const std::vector<int>& qs) {
+    for (size_t g0 = 0; g0 < qs.size(); g0 += kVecMatOut) {
+      const int m = (int)std::min<size_t>(kVecMatOut, qs.size() - g0);
+      VecMat a;
+      std::unique_ptr<Arith32Scope> a32;
+      if (s.anchor_ok) {
+        anchored_args(s, qs, g0, m, a);
+        a32.reset(new Arith32Scope(c));
+      } else {
+        resid_coef(s, qs, g0, m);
+        a.X = SB(s);
+        a.x32 = s.Sf != nullptr;
+        a.m = m;
+        a.C = cdev;
+        a.add = s.rhs;
+      }
       a.norm2 = n2dev;
       vecmat(c.L, N, a, vscr);
       double h[kVecMatOut];
@@ -700,6 +797,12 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
         zsolve(L, G, rhs);
         for (int i = 0; i < L; ++i) s.beta[q][i] = rhs[i];
       }
+      bool have_all = false;   // the anchor pass gave every shift's norm at this iteration
+      if (s.R0 && !s.anchor_ok) {
+        ph.mark(c, "anchor");
+        compute_anchor(s);
+        have_all = true;
+      }
       // ---- residual norms of the open shifts; once all are below the target, the shifts
       // locked earlier are checked again at the final trial space.  With FP64 vector arithmetic
       // (FP64 mode, refinement) a pass costs about one DFMA per complex element and output row,
@@ -710,7 +813,9 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
       std::vector<std::pair<double, int>> order;
       ph.mark(c, "norms");
       std::vector<int> check = open;
-      if (!mixed && (int)open.size() > kTry && it > 1) {
+      if (have_all) {
+        // norms already fresh
+      } else if (!mixed && (int)open.size() > kTry && it > 1) {
         std::vector<std::pair<double, int>> last;
         for (int q : open) last.push_back({s.rnorm[q], q});
         std::partial_sort(last.begin(), last.begin() + kTry, last.end(), [](auto& a, auto& b) { return a.first > b.first; });
@@ -730,7 +835,7 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
       for (int q : open)
         if (!s.conv[q]) order.push_back({s.rnorm[q], q});
       if (order.empty() && !locked.empty()) {
-        residual_norms(s, locked);
+        if (!have_all) residual_norms(s, locked);
         for (int q : locked) {
           s.conv[q] = s.rnorm[q] < tol_s;
           if (!s.conv[q]) order.push_back({s.rnorm[q], q});
@@ -759,6 +864,7 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
         restart(c, s, maxL, maxL - 2 * kMaxNew);
         mirror(s.B, s.Bf, 0, s.L);
         mirror(s.S, s.Sf, 0, s.L);
+        s.anchor_ok = false;   // new basis: anchored again after the next subspace solve
       }
       // ---- preconditioned residuals of the worst shifts, one pass
       ph.mark(c, "candidates");
@@ -766,16 +872,22 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
       std::vector<int> qs(nt);
       std::vector<zc> zq(nt);
       for (int t = 0; t < nt; ++t) { qs[t] = order[t].second; zq[t] = s.z[qs[t]]; }
-      resid_coef(s, qs, 0, nt);
       to_dev(c, zq.data(), zdev, nt);
       double pre2[kVecMatOut];
       {
         VecMat a;
-        a.X = SB(s);
-        a.x32 = s.Sf != nullptr;
-        a.m = nt;
-        a.C = cdev;
-        a.add = s.rhs;
+        std::unique_ptr<Arith32Scope> a32;
+        if (s.anchor_ok) {
+          anchored_args(s, qs, 0, nt, a);
+          a32.reset(new Arith32Scope(c));
+        } else {
+          resid_coef(s, qs, 0, nt);
+          a.X = SB(s);
+          a.x32 = s.Sf != nullptr;
+          a.m = nt;
+          a.C = cdev;
+          a.add = s.rhs;
+        }
         a.Y = R;
         a.ldy = N;
         a.D = c.Dpre ? c.Dpre : c.D;
@@ -823,7 +935,7 @@ void refine_systems(Ctx& c, std::vector<System>& sys, const std::function<void(i
   const double t0 = now();
   const long v0 = c.stats.sigma_vectors;
   restart_from_solutions(c, sys, maxL, bases, sigs);
-  davidson(c, sys, Op, maxL, tol, true);
+  davidson(c, sys, Op, maxL, tol, true, true);
   c.stats.refine_vectors += c.stats.sigma_vectors - v0;
   c.stats.refine_seconds += now() - t0;
 }

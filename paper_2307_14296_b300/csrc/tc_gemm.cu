@@ -838,7 +838,7 @@ constexpr int kSplitPairs = 64;
 __global__ void __launch_bounds__(256) k_split_view(const double2* __restrict__ X, ViewArgs v, int64_t rows, int64_t K,
                                                     bool conj, int nsl, __nv_bfloat16* __restrict__ out, int64_t Kpad,
                                                     uint32_t nchunk, uint32_t chunk_mul, int chunk_shr,
-                                                    const uint32_t* __restrict__ rexp) {
+                                                    const uint32_t* __restrict__ rexp, int nd) {
   const int64_t plane = rows * Kpad;
   const int lane = threadIdx.x & 31;
   const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -868,7 +868,7 @@ __global__ void __launch_bounds__(256) k_split_view(const double2* __restrict__ 
         uint32_t o[2 * x::NS];
         ozaki_pair(xv, rexp[r], o);
 #pragma unroll
-        for (int q = 0; q < 2 * x::NS; ++q) o32[(q * plane) / 2 + e2] = o[q];
+        for (int q = 0; q < 2 * nd; ++q) o32[(q * plane) / 2 + e2] = o[q];   // zero digit planes are not read
         continue;
       }
       float re[2], im[2];
@@ -914,7 +914,7 @@ struct SplitT {
 __global__ void __launch_bounds__(256) k_split_view_t(const double2* __restrict__ X, ViewArgs v, SplitT s,
                                                       int64_t rows, int64_t K, bool conj, int nsl,
                                                       __nv_bfloat16* __restrict__ out, int64_t Kpad, int64_t ntiles,
-                                                      const uint32_t* __restrict__ rexp) {
+                                                      const uint32_t* __restrict__ rexp, int nd) {
   __shared__ double2 tile[64][33];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t plane = rows * Kpad;
@@ -957,7 +957,7 @@ __global__ void __launch_bounds__(256) k_split_view_t(const double2* __restrict_
         ozaki_pair(xv, rexp[row], o);
         const int64_t e2 = row * (Kpad / 2) + (k0 / 2) + lane;
 #pragma unroll
-        for (int q = 0; q < 2 * x::NS; ++q) o32[(q * plane) / 2 + e2] = o[q];
+        for (int q = 0; q < 2 * nd; ++q) o32[(q * plane) / 2 + e2] = o[q];   // zero digit planes are not read
         continue;
       }
       float re[2], im[2];
@@ -1185,8 +1185,10 @@ tc::ViewArgs view_args(const Tensor& v, int nr) {
 }
 
 // rexp != nullptr: the FP64-class digits (nsl = 5); rexp holds `rows` words of scratch on the stream's device
+// nd: digit planes written in digit mode (2 for operands on the coarse grid, whose higher digits
+// are zero and never read; else all five)
 void launch_split(const Tensor& v, int nr, int64_t rows, int64_t K, int64_t Kpad, int nsl, __nv_bfloat16* dst,
-                  cudaStream_t stream, uint32_t* rexp = nullptr) {
+                  cudaStream_t stream, uint32_t* rexp = nullptr, int nd = tc::x::NS) {
   CCLR_REQUIRE(rows < (int64_t(1) << 31) && K < (int64_t(1) << 31), CCLR_E_ARG, "tensor-core split: operand too large");
   CCLR_REQUIRE(!rexp || nsl == tc::x::NS, CCLR_E_ARG, "tensor-core split: digit count");
   const tc::ViewArgs a = view_args(v, nr);
@@ -1220,7 +1222,7 @@ void launch_split(const Tensor& v, int nr, int64_t rows, int64_t K, int64_t Kpad
     magic(n_ck, st.mul_ck, st.shr_ck);
     const int g = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)sms * 8));
     if (rexp) tc::k_rowexp_t<<<g, 256, 0, stream>>>(v.p, a, st, K, ntiles, rexp);
-    tc::k_split_view_t<<<g, 256, 0, stream>>>(v.p, a, st, rows, K, v.conj, nsl, dst, Kpad, ntiles, rexp);
+    tc::k_split_view_t<<<g, 256, 0, stream>>>(v.p, a, st, rows, K, v.conj, nsl, dst, Kpad, ntiles, rexp, nd);
     return;
   }
   const int64_t nchunk = (Kpad / 2 + tc::kSplitPairs - 1) / tc::kSplitPairs;
@@ -1230,10 +1232,10 @@ void launch_split(const Tensor& v, int nr, int64_t rows, int64_t K, int64_t Kpad
   const uint32_t mul = (uint32_t)(((unsigned __int128)1 << 32) * (((uint64_t)1 << l) - (uint64_t)nchunk) / (uint64_t)nchunk + 1);
   const int g = (int)std::max<int64_t>(1, std::min<int64_t>((rows * nchunk + 7) / 8, (int64_t)sms * 16));
   if (rexp) tc::k_rowexp<<<g, 256, 0, stream>>>(v.p, a, rows, K, (uint32_t)nchunk, mul, l, rexp);
-  tc::k_split_view<<<g, 256, 0, stream>>>(v.p, a, rows, K, v.conj, nsl, dst, Kpad, (uint32_t)nchunk, mul, l, rexp);
+  tc::k_split_view<<<g, 256, 0, stream>>>(v.p, a, rows, K, v.conj, nsl, dst, Kpad, (uint32_t)nchunk, mul, l, rexp, nd);
 }
 
-void make_slices(Ctx& c, const Tensor& v, int nr, int nsl, Slices& s, __nv_bfloat16* dst) {
+void make_slices(Ctx& c, const Tensor& v, int nr, int nsl, Slices& s, __nv_bfloat16* dst, int nd = tc::x::NS) {
   int64_t rows = 1, K = 1;
   for (int i = 0; i < v.rank; ++i) (i < nr ? rows : K) *= v.dim[i];
   s.rows = rows;
@@ -1244,7 +1246,7 @@ void make_slices(Ctx& c, const Tensor& v, int nr, int nsl, Slices& s, __nv_bfloa
   Scope sc(c.ws);
   uint32_t* rexp = nsl == tc::x::NS ? (uint32_t*)c.ws.alloc(sizeof(uint32_t) * (size_t)rows) : nullptr;
   c.kt.begin(c.stream);
-  launch_split(v, nr, rows, K, s.Kpad, nsl, dst, c.stream, rexp);
+  launch_split(v, nr, rows, K, s.Kpad, nsl, dst, c.stream, rexp, nd);
   CCLR_CK(cudaGetLastError());
   c.kt.end(c.stream, rexp ? "k_split_view(f64 digits)" : "k_split_view");
   c.launches += rexp ? 2 : 1;
@@ -1283,6 +1285,9 @@ Slices get_slices(Ctx& c, const Tensor& v, int nr, int nsl) {
   return s;
 }
 Slices get_slices_any(Ctx& c, const Tensor& v, int nr, int nsl) {
+  // transient operands on the coarse grid get only their two nonzero digit planes written (the
+  // persistent cache always holds all five)
+  const int nd = (nsl == tc::x::NS && is_coarse(c, v.p)) ? 2 : tc::x::NS;
   TcState& T = tcs(c);
   auto& cache = T.cache;
   if (T.cache_gen != c.data_gen) {
@@ -1342,14 +1347,14 @@ Slices get_slices_any(Ctx& c, const Tensor& v, int nr, int nsl) {
       if (e.first == key) return e.second;
     const size_t at = (it->used + 255) & ~size_t(255);
     if (at + bytes <= it->cap) {
-      make_slices(c, v, nr, nsl, s, (__nv_bfloat16*)(it->base + at));
+      make_slices(c, v, nr, nsl, s, (__nv_bfloat16*)(it->base + at), nd);
       it->used = at + bytes;
       it->entries.push_back({key, s});
       return s;
     }
     break;
   }
-  make_slices(c, v, nr, nsl, s, (__nv_bfloat16*)c.ws.alloc(bytes));
+  make_slices(c, v, nr, nsl, s, (__nv_bfloat16*)c.ws.alloc(bytes), nd);
   return s;
 }
 
