@@ -14,6 +14,10 @@ TEST INFRASTRUCTURE ONLY.
                    (Eq. CC-CC response function with C^{+-w} and P(X,Y) written out; the
                    conjugation flips the real frequency and keeps the damping, which is the
                    reading that reproduces the exact sum over states);
+  * asymmetric form: f(z) = 1/2 [eta^X t^Y(z) + t-bar^Y(z) xi^X], symmetrized the same way, with
+                   the first-order multipliers t-bar^Y(z) (A + z) = -(eta^Y + F t^Y(z)) from left
+                   sigma products (Sec. 2.3, the asymmetric CC-CC form; the printed form omits the
+                   C^{+-w} symmetrizer, which the stated equality with the symmetric form needs);
   * polarizability alpha_xy(z) = -<<mu_x; mu_y>>_z, mean alpha, anisotropy, and the absorption
     cross section sigma(w) = 4 pi w / c Im mean-alpha (Eq. abs_cpp; Sec. 5 definitions).
 All products in the response function are bilinear (no conjugation) over unique excitations.
@@ -125,8 +129,10 @@ class CCSystem:
     def solve_dense(self, A, xi, z):
         return -np.linalg.solve(A - z * np.eye(A.shape[0]), xi)
 
-    def davidson(self, xi, z, tol=1e-10, maxit=200, start="pivot"):
-        """Davidson solve of (A - z) t = -xi (SI Davidson scheme, steps 1-5)."""
+    def davidson(self, xi, z, tol=1e-10, maxit=200, start="pivot", op=None):
+        """Davidson solve of (A - z) t = -xi (SI Davidson scheme, steps 1-5).  With op =
+        self.sigma_l (v -> v A, i.e. A^T v) it solves the left system t (A - z) = -xi instead."""
+        op = self.sigma_r if op is None else op
         D = self.D
         if start == "pivot":
             b0 = np.zeros_like(xi)
@@ -134,7 +140,7 @@ class CCSystem:
         else:
             b0 = -xi / (D - z)
         B = [b0 / np.linalg.norm(b0)]
-        S = [self.sigma_r(B[0])]
+        S = [op(B[0])]
         for it in range(1, maxit + 1):
             Bm, Sm = np.array(B), np.array(S)
             G = Bm.conj() @ (Sm - z * Bm).T
@@ -153,7 +159,7 @@ class CCSystem:
             if cn < 1e-14:
                 return t, it, rn
             B.append(c / cn)
-            S.append(self.sigma_r(B[-1]))
+            S.append(op(B[-1]))
         raise RuntimeError(f"Davidson did not converge (|r|={rn:.3e})")
 
     def response(self, ops, zs, solver="davidson", tol=1e-11, A=None, half=False, form="cc"):
@@ -166,13 +172,16 @@ class CCSystem:
             f(z) = 1/2 [eometa^a t^b(z) - (lam.t^a(-z))(lam.xi^b)
                         + eometa^b t^a(-z) - (lam.t^b(z))(lam.xi^a)],
             lam the ground-state multipliers; P swaps (a, -z) with (b, z).
-        Both are symmetrized as f(z) + conj(f(-z*)).  With half=True return the unsymmetrized
+        form="asym": the asymmetric CC-CC form (Sec. 2.3),
+            f(z) = 1/2 [eta^a t^b(z) + tbar^b(z) xi^a],  tbar^b(z) (A + z) = -(eta^b + F t^b(z)),
+            which needs solves for operator b only (right and left).
+        All three are symmetrized as f(z) + conj(f(-z*)).  With half=True return the unsymmetrized
         f(z) instead (2 f(0) of the CC-CC form is the second derivative of the CC energy with
         respect to static fields).
         """
-        assert form in ("cc", "ci")
+        assert form in ("cc", "ci", "asym")
         nops = len(ops)
-        eta = [self.eta(X) if form == "cc" else self.eta_eom(X) for X in ops]
+        eta = [self.eta_eom(X) if form == "ci" else self.eta(X) for X in ops]
         xis = [self.xi(X) for X in ops]
         lam = pack(self.l1, self.l2)
         lam_xi = [self.bdot(lam, x) for x in xis]
@@ -187,7 +196,20 @@ class CCSystem:
                     cache[key] = self.davidson(xis[k], w, tol=tol)[0]
             return cache[key]
 
+        def tbar_of(k, w):
+            """First-order multipliers: tbar (A + w) = -(eta^k + F t^k(w))."""
+            key = ("left", k, complex(w))
+            if key not in cache:
+                rhs = eta[k] + self.hessian(t_of(k, w))
+                if solver == "dense":
+                    cache[key] = -np.linalg.solve(A.T + w * np.eye(A.shape[0]), rhs)
+                else:
+                    cache[key] = self.davidson(rhs, -w, tol=tol, op=self.sigma_l)[0]
+            return cache[key]
+
         def f(z, a, b):
+            if form == "asym":
+                return 0.5 * (self.bdot(eta[a], t_of(b, z)) + self.bdot(tbar_of(b, z), xis[a]))
             tx = t_of(a, -z)
             ty = t_of(b, z)
             if form == "ci":

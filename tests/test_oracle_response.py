@@ -151,3 +151,52 @@ def test_derived_quantities():
     assert R.anisotropy(alpha)[0] == 4.5
     alpha = alpha + 1j * np.eye(3)[None]
     assert abs(R.cross_section([0.1], alpha)[0] - 4 * np.pi * 0.1 / 137.035999084) < 1e-15
+
+
+def test_asymmetric_form_two_electron_sum_over_states(two_electron):
+    """The asymmetric CC-CC form (first-order multipliers from left solves) is exact for two
+    electrons too."""
+    inst, s, sos = two_electron
+    got = s.response(inst.ops, ZS, solver="dense", A=s.dense_A(), form="asym")
+    assert np.abs(got - sos).max() < 1e-11 * np.abs(sos).max()
+
+
+@pytest.fixture(scope="module")
+def four_electron():
+    inst = synth.make_instance(4, 8, seed=5, sd=0.05)
+    s = R.CCSystem(Ints.from_instance(inst))
+    return inst, s, s.dense_A()
+
+
+def test_asymmetric_form_equals_symmetric_form(four_electron):
+    """Beyond two electrons the asymmetric and symmetric CC-CC forms still agree (Sec. 2.3): the
+    identity tbar^Y(z) xi^X = eta^Y t^X(-z) + t^X(-z) F t^Y(z) holds for the exact solutions.
+    Dense and Davidson solves, static and damped shifts."""
+    inst, s, A = four_electron
+    zs = [0.0, 0.1 + 0.01j, -0.07 + 0.02j]
+    cc = s.response(inst.ops, zs, solver="dense", A=A)
+    asym = s.response(inst.ops, zs, solver="dense", A=A, form="asym")
+    assert np.abs(asym - cc).max() < 1e-11 * np.abs(cc).max()
+    dav = s.response(inst.ops, zs[1:], tol=1e-12, form="asym")
+    assert np.abs(dav - cc[1:]).max() < 1e-9 * np.abs(cc).max()
+
+
+def test_first_order_multipliers_solve_the_left_equation(four_electron):
+    """The left Davidson (op = left sigma) against the dense transpose: tbar (A + w) = -b."""
+    inst, s, A = four_electron
+    rng = np.random.default_rng(2)
+    b = rng.normal(size=A.shape[0]) + 1j * rng.normal(size=A.shape[0])
+    w = 0.12 + 0.01j
+    tb = s.davidson(b, -w, tol=1e-12, op=s.sigma_l)[0]
+    assert np.abs(tb @ (A + w * np.eye(A.shape[0])) + b).max() < 1e-10 * np.abs(b).max()
+
+
+def test_asymmetric_form_needs_the_hessian_term(four_electron, monkeypatch):
+    """Planted mistake: without F t^Y in the multiplier right-hand side the two forms disagree, so
+    the equality above does check that term."""
+    inst, s, A = four_electron
+    zs = [0.1 + 0.01j]
+    cc = s.response(inst.ops, zs, solver="dense", A=A)
+    monkeypatch.setattr(s, "hessian", lambda u: np.zeros_like(u))
+    bad = s.response(inst.ops, zs, solver="dense", A=A, form="asym")
+    assert np.abs(bad - cc).max() > 1e-4 * np.abs(cc).max()
