@@ -193,6 +193,17 @@ cclr_status cclr_left_solve(cclr_ctx *ctx, int nrhs, const cclr_c128 *rhs, doubl
  * cc_lambda); CCLR_E_STATE otherwise. */
 cclr_status cc_response_function_ci(cclr_ctx *ctx, cclr_c128 *out);
 
+/* The asymmetric CC-CC response function (Sec. 2.3, the asymmetric form beside Eq. CC-CC
+ * response function): with the first-order multipliers of each operator Y,
+ *   tbar^Y(z) (A + z) = -(eta^Y + F t^Y(z))   (left sigma products, solved to cclr_options.tol),
+ *   f(z) = 1/2 [eta^X t^Y(z) + tbar^Y(z) xi^X],   out[f][x][y] = f(z) + conj(f(-z*)),
+ * z = w_f + i gamma, from the solutions t^Y(z), t^Y(-z*) of the last cc_lr_solve.  Same layout
+ * as cc_response_function and equal to it for exact solutions (its error is first order in the
+ * solution errors, the symmetric form's second order).  Costs 2 n_ops left solves and Hessian
+ * products per frequency.  Requires cc_lr_solve; CCLR_E_STATE otherwise, CCLR_E_NOCONV if a
+ * multiplier solve does not converge within maxit (out is then not written). */
+cclr_status cc_response_function_asym(cclr_ctx *ctx, cclr_c128 *out);
+
 /* EOM-CCSD excitation energies (SI "EOM-EE sigma-vectors and intermediates"; the Davidson scheme
  * applied to the eigenproblem): the n_roots (1..16) eigenvalues of the CC Jacobian A with the
  * smallest real part, from a non-Hermitian Davidson iteration on right sigma products with the

@@ -31,7 +31,8 @@ TC_FP32 = TC_BF16X6   # the FP32-class tensor-core mode
 AMP_T, AMP_LAMBDA = 0, 1
 EXPORTS = (
     "cclr_default_options", "cclr_create", "cclr_destroy", "cclr_last_error", "cclr_set_hamiltonian",
-    "cc_ground", "cc_lambda", "cc_lr_solve", "cc_response_function", "cc_response_function_ci", "cc_eom_ee",
+    "cc_ground", "cc_lambda", "cc_lr_solve", "cc_response_function", "cc_response_function_ci", "cc_response_function_asym",
+    "cc_eom_ee",
     "cclr_get_eom_vector",
     "cclr_get_amplitudes",
     "cclr_set_amplitudes", "cclr_get_response_vector", "cclr_sigma", "cclr_residual", "cclr_xi",
@@ -67,6 +68,7 @@ _sig = {
     "cc_lr_solve": (_i, [_vp, _i, _vp, _i, _vp, _d, _vp]),
     "cc_response_function": (_i, [_vp, _vp]),
     "cc_response_function_ci": (_i, [_vp, _vp]),
+    "cc_response_function_asym": (_i, [_vp, _vp]),
     "cc_eom_ee": (_i, [_vp, _i, _vp, _vp]),
     "cclr_get_eom_vector": (_i, [_vp, _i, _vp, ctypes.c_size_t]),
     "cclr_get_amplitudes": (_i, [_vp, _i, _vp, _sz]),
@@ -266,6 +268,13 @@ class Context:
         self._check(_lib.cc_response_function_ci(self._h, _ptr(out)))
         return out
 
+    def cc_response_function_asym(self):
+        """The asymmetric CC-CC form (first-order multipliers from left solves) from the same
+        solutions."""
+        out = np.zeros((self._nfreq, self._nops, self._nops), np.complex128)
+        self._check(_lib.cc_response_function_asym(self._h, _ptr(out)))
+        return out
+
     def cc_eom_ee(self, n_roots):
         """Lowest n_roots EOM-CCSD excitation energies (complex, ordered by real part) and the
         iteration count."""
@@ -436,6 +445,10 @@ def cc_response_function(ctx):
 
 def cc_response_function_ci(ctx):
     return ctx.cc_response_function_ci()
+
+
+def cc_response_function_asym(ctx):
+    return ctx.cc_response_function_asym()
 
 
 def cc_eom_ee(ctx, n_roots):

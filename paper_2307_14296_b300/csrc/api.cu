@@ -462,6 +462,13 @@ cclr_status cc_response_function_ci(cclr_ctx* h, cclr_c128* out) {
   });
 }
 
+cclr_status cc_response_function_asym(cclr_ctx* h, cclr_c128* out) {
+  return guard(h, [&](Ctx& c) {
+    CCLR_REQUIRE(out, CCLR_E_ARG, "null output");
+    response_function_asym(c, (cplx*)out);
+  });
+}
+
 cclr_status cc_eom_ee(cclr_ctx* h, int n_roots, cclr_c128* energies_out, int* iters_out) {
   return guard(h, [&](Ctx& c) {
     CCLR_REQUIRE(energies_out, CCLR_E_ARG, "null output");

@@ -1370,6 +1370,100 @@ void response_function_ci(Ctx& c, cplx* out_host) {
       }
 }
 
+// Asymmetric CC-CC response function (Sec. 2.3): with the first-order multipliers of operator Y,
+//   tbar^Y(z) (A + z) = -(eta^Y + F t^Y(z))          (left sigma products, as the Lambda solve),
+//   f(z) = 1/2 [eta^X t^Y(z) + tbar^Y(z) xi^X],   <<X;Y>>_z = f(z) + conj(f(-z*)).
+// It equals the symmetric form for exact solutions; its error is first order in the solution
+// errors (the symmetric form's is second order).  Only the shifts z = w + ig and -z* = -w + ig of
+// cc_lr_solve are read; per frequency the 2 n_ops multiplier systems share one Davidson run.
+void response_function_asym(Ctx& c, cplx* out_host) {
+  ResponseData& rd = c.rd;
+  CCLR_REQUIRE(rd.solved, CCLR_E_STATE, "cc_response_function_asym before cc_lr_solve");
+  const int64_t N = c.N;
+  const int nop = rd.n_ops, maxL = std::max(8, c.opt.max_subspace);
+  const int prec = rd.refined ? CCLR_TC_F64 : c.opt.precision;
+  auto beta = [&](int k, int f, int s) { return &rd.beta[k][(size_t)rd.shift_of[(size_t)f * 4 + s] * maxL]; };
+  auto dotL = [&](const std::vector<zc>& a, const zc* b, int L) {
+    zc acc(0);
+    for (int i = 0; i < L; ++i) acc += a[i] * b[i];
+    return acc;
+  };
+  // eta^X . t^Y(z) = (eta^X . B^Y) beta^Y(z)
+  std::vector<std::vector<zc>> E((size_t)nop * nop);
+  {
+    PrecisionScope exact(c, prec);
+    Fast32 f32(c);
+    for (int x = 0; x < nop; ++x)
+      for (int y = 0; y < nop; ++y)
+        gram_host(c, rows(c, rd.eta[x], 1), rows(c, rd.basis[y], rd.nb[y]), false, E[(size_t)x * nop + y]);
+  }
+  std::vector<zc> half((size_t)rd.n_freq * nop * nop * 2);   // [f][x][y][s], s: 0 z, 1 -z*
+  for (int f = 0; f < rd.n_freq; ++f) {
+    std::vector<System> sys((size_t)2 * nop);   // [y][s]
+    auto cleanup = [&]() {
+      for (auto& s : sys) {
+        if (s.rhs) c.dfree(const_cast<cplx*>(s.rhs));
+        if (s.B) c.dfree(s.B);
+        if (s.S) c.dfree(s.S);
+        s.rhs = nullptr;
+        s.B = s.S = nullptr;
+      }
+    };
+    try {
+      {
+        PrecisionScope exact(c, prec);
+        Scope sc(c.ws);
+        cplx* bd = c.ws.cplxs(maxL);
+        cplx* t = c.ws.cplxs(N);
+        for (int y = 0; y < nop; ++y)
+          for (int q = 0; q < 2; ++q) {
+            System& s = sys[(size_t)2 * y + q];
+            to_dev(c, beta(y, f, q), bd, rd.nb[y]);
+            lincomb(c.L, N, rd.nb[y], rd.basis[y], N, bd, t, false);
+            cplx* b = c.dalloc(N);
+            s.rhs = b;
+            hessian_right(c, 1, t, b);
+            axpy(c.L, N, cx(1), rd.eta[y], b);
+            s.z = {-rd.shifts[rd.shift_of[(size_t)f * 4 + q]]};   // tbar (A - w_l) = -b, w_l = -z
+            s.B = c.dalloc((int64_t)maxL * N);
+            s.S = c.dalloc((int64_t)maxL * N);
+          }
+      }
+      auto op = [&](int nv, const cplx* in, cplx* o) { sigma_left(c, nv, in, o); };
+      davidson(c, sys, op, maxL, c.opt.tol);
+      if (refining(c)) refine_systems(c, sys, op, maxL, c.opt.tol, nullptr, nullptr);
+      PrecisionScope exact(c, prec);
+      Fast32 f32(c);
+      Scope sc(c.ws);
+      cplx* bd = c.ws.cplxs(maxL);
+      cplx* l = c.ws.cplxs(N);
+      for (int y = 0; y < nop; ++y)
+        for (int q = 0; q < 2; ++q) {
+          const System& s = sys[(size_t)2 * y + q];
+          to_dev(c, s.beta[0].data(), bd, s.L);
+          lincomb(c.L, N, s.L, s.B, N, bd, l, false);
+          for (int x = 0; x < nop; ++x) {
+            std::vector<zc> g;
+            gram_host(c, rows(c, l, 1), rows(c, rd.xi[x], 1), false, g);
+            const zc et = dotL(E[(size_t)x * nop + y], beta(y, f, q), rd.nb[y]);
+            half[(((size_t)f * nop + x) * nop + y) * 2 + q] = 0.5 * (et + g[0]);
+          }
+        }
+    } catch (...) {
+      cleanup();
+      throw;
+    }
+    cleanup();
+  }
+  for (int f = 0; f < rd.n_freq; ++f)
+    for (int x = 0; x < nop; ++x)
+      for (int y = 0; y < nop; ++y) {
+        const size_t i = (((size_t)f * nop + x) * nop + y) * 2;
+        const zc val = half[i] + std::conj(half[i + 1]);
+        out_host[((size_t)f * nop + x) * nop + y] = make_double2(val.real(), val.imag());
+      }
+}
+
 // ------------------------------------------------------------------------------ EOM-EE
 // Lowest roots of the right eigenproblem A r = w r (EOM-CCSD excitation energies; SI "EOM-EE
 // sigma-vectors and intermediates", with the Davidson scheme used for eigenvalues): a

@@ -135,6 +135,7 @@ def test_two_electron_exact_sum_over_states(pk):
     ctx.cc_lr_solve(inst.ops, [0.1, 0.25], 0.01)
     assert rel(ctx.cc_response_function(), sos) < TOL
     assert rel(ctx.cc_response_function_ci(), sos) < TOL   # both forms are exact for two electrons
+    assert rel(ctx.cc_response_function_asym(), sos) < TOL
     ctx.close()
 
 
@@ -150,6 +151,23 @@ def test_cc_ci_response_function(pk):
     got = ctx.cc_response_function_ci()
     ref = s.response(inst.ops, [w + 1j * gamma for w in omegas], tol=1e-11, form="ci")
     assert rel(got, ref) < TOL
+    ctx.close()
+
+
+def test_asymmetric_response_function(pk):
+    """Asymmetric CC-CC form (first-order multipliers from left solves on the device) against the
+    oracle's asymmetric form and against the symmetric form, (3,8), static and damped."""
+    inst = synth.make_instance(3, 8, seed=21, sd=0.05)
+    s = R.CCSystem(Ints.from_instance(inst))
+    omegas, gamma = [0.0, 0.05, 0.3], 0.01
+    ctx = make_ctx(pk, inst, tol=1e-11, ground_tol=1e-12)
+    ctx.cc_ground()
+    ctx.cc_lambda()
+    ctx.cc_lr_solve(inst.ops, omegas, gamma)
+    got = ctx.cc_response_function_asym()
+    ref = s.response(inst.ops, [w + 1j * gamma for w in omegas], tol=1e-12, form="asym")
+    assert rel(got, ref) < TOL
+    assert rel(got, ctx.cc_response_function()) < TOL
     ctx.close()
 
 
@@ -195,7 +213,7 @@ def test_eom_ee_tensor_cores_match_fp64(pk):
 
 def test_mixed_electric_magnetic_operators(pk):
     """Optical-rotation operator pair (real symmetric mu, imaginary antisymmetric m) through the
-    same path: both response forms against the oracle at (3,8), damped frequencies."""
+    same path: the three response forms against the oracle at (3,8), damped frequencies."""
     from test_oracle_response import mixed_operators
     inst = synth.make_instance(3, 8, seed=21, sd=0.05)
     ops = mixed_operators(inst.n_occ + inst.n_vir, 4)
@@ -208,6 +226,7 @@ def test_mixed_electric_magnetic_operators(pk):
     ctx.cc_lr_solve(ops, omegas, gamma)
     assert rel(ctx.cc_response_function(), s.response(ops, zs, tol=1e-11)) < TOL
     assert rel(ctx.cc_response_function_ci(), s.response(ops, zs, tol=1e-11, form="ci")) < TOL
+    assert rel(ctx.cc_response_function_asym(), s.response(ops, zs, tol=1e-11, form="asym")) < TOL
     ctx.close()
 
 

@@ -61,6 +61,20 @@ def test_refined_alpha_matches_oracle_4x20(pk, prec):
     ctx.close()
 
 
+def test_refined_asymmetric_form_4x20(pk):
+    """The asymmetric form in split BF16 with refinement (right and multiplier solves refined to
+    1e-10; its error is first order in theirs) against the oracle's symmetric form at 1e-6 per
+    component."""
+    inst = synth.make_instance(4, 20)
+    omegas, gamma = [0.0, 0.2], 0.01
+    ctx, sym = solve(pk, inst, omegas, gamma, precision=pk.TC_BF16X3, tol=1e-10, ground_tol=1e-11, batch=8)
+    got = ctx.cc_response_function_asym()
+    ctx.close()
+    ref = R.CCSystem(Ints.from_instance(inst)).response(inst.ops, [w + 1j * gamma for w in omegas], tol=1e-12)
+    assert per_component(got, ref) < 1e-6, per_component(got, ref)
+    assert rel(got, sym) < 1e-8
+
+
 def test_refined_residual_below_tolerance_4x20(pk):
     """The true residual xi + (A - z) t of returned response vectors, recomputed by the oracle,
     is below the requested 1e-8 (plus the oracle/GPU difference of A and xi, ~1e-13)."""
