@@ -297,6 +297,7 @@ struct System {            // one right-hand side with its shared trial space
   int best_it = 0;
   // anchored residuals (refinement): r0_q (FP32 rows, one per shift) at the coefficients beta0
   void* R0 = nullptr;
+  void* Sa = nullptr;      // FP32 mirror of S for the anchored passes (null: they read the FP64 rows)
   std::vector<std::vector<zc>> beta0;
   bool anchor_ok = false;
 };
@@ -580,8 +581,10 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
   struct AnchorMem {
     std::vector<System>& sys;
     ~AnchorMem() {
-      for (auto& s : sys)
+      for (auto& s : sys) {
         if (s.R0) { cudaFree(s.R0); s.R0 = nullptr; }
+        if (s.Sa) { cudaFree(s.Sa); s.Sa = nullptr; }
+      }
     }
   } anchor_mem{sys};
   struct Arith32Scope {   // FP32 arithmetic for the anchored passes
@@ -590,13 +593,23 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
     explicit Arith32Scope(Ctx& cc) : c(cc), old(cc.L.fast32) { c.L.fast32 = true; }
     ~Arith32Scope() { c.L.fast32 = old; }
   };
+  // Both are taken from free device memory, not the workspace (the sigma products' temporaries
+  // live there); the S mirror only while ample memory stays free for the tensor-core slice cache.
   for (auto& s : sys) {
     s.anchor_ok = false;
-    s.R0 = nullptr;
+    s.R0 = s.Sa = nullptr;
     if (anchored && !mixed) {
       if (cudaMalloc(&s.R0, sizeof(float2) * (size_t)Np * s.z.size()) != cudaSuccess) {
         cudaGetLastError();
         s.R0 = nullptr;   // float-float passes
+        continue;
+      }
+      const size_t sa_bytes = sizeof(float2) * (size_t)maxL * (size_t)Np;
+      size_t fr = 0, tot = 0;
+      if (cudaMemGetInfo(&fr, &tot) == cudaSuccess && fr > sa_bytes + ((size_t)16 << 30) &&
+          cudaMalloc(&s.Sa, sa_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        s.Sa = nullptr;
       }
     }
   }
@@ -616,8 +629,13 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
   };
   auto anchored_args = [&](const System& s, const std::vector<int>& qs, size_t g0, int m, VecMat& a) {
     anchored_coef(s, qs, g0, m);
-    a.X = Rows().add(s.S, s.L, N).add(s.B, s.L, N);
-    a.x32 = false;
+    if (s.Sa) {
+      a.X = m32(s.Sa, 0, s.L).add(reinterpret_cast<const cplx*>(s.Bf), s.L, Np);
+      a.x32 = true;
+    } else {
+      a.X = Rows().add(s.S, s.L, N).add(s.B, s.L, N);
+      a.x32 = false;
+    }
     a.m = m;
     a.C = cdev;
     a.add = nullptr;
@@ -738,6 +756,7 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
         for (int j = 0; j < fresh[k]; ++j, ++q)
           copy_vec(c.L, N, out + (int64_t)q * N, sys[k].S + (int64_t)(sys[k].L - fresh[k] + j) * N);
         mirror(sys[k].S, sys[k].Sf, sys[k].L - fresh[k], fresh[k]);
+        mirror(sys[k].S, sys[k].Sa, sys[k].L - fresh[k], fresh[k]);
       }
     }
     bool all_done = true;
@@ -807,7 +826,8 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
       // locked earlier are checked again at the final trial space.  With FP64 vector arithmetic
       // (FP64 mode, refinement) a pass costs about one DFMA per complex element and output row,
       // so only the kTry open shifts with the largest last norm are recomputed each iteration;
-      // every open shift is checked once those are below the target.
+      // every open shift is checked once those are below the target.  Anchored residuals (FP32
+      // passes) are cheap enough to refresh every open shift's norm each iteration.
       std::vector<int> open, locked;
       for (size_t q = 0; q < s.z.size(); ++q) (s.conv[q] ? locked : open).push_back((int)q);
       std::vector<std::pair<double, int>> order;
@@ -815,7 +835,7 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
       std::vector<int> check = open;
       if (have_all) {
         // norms already fresh
-      } else if (!mixed && (int)open.size() > kTry && it > 1) {
+      } else if (!mixed && !s.anchor_ok && (int)open.size() > kTry && it > 1) {
         std::vector<std::pair<double, int>> last;
         for (int q : open) last.push_back({s.rnorm[q], q});
         std::partial_sort(last.begin(), last.begin() + kTry, last.end(), [](auto& a, auto& b) { return a.first > b.first; });
@@ -864,14 +884,34 @@ void davidson(Ctx& c, std::vector<System>& sys, const std::function<void(int, co
         restart(c, s, maxL, maxL - 2 * kMaxNew);
         mirror(s.B, s.Bf, 0, s.L);
         mirror(s.S, s.Sf, 0, s.L);
+        mirror(s.S, s.Sa, 0, s.L);
         s.anchor_ok = false;   // new basis: anchored again after the next subspace solve
       }
-      // ---- preconditioned residuals of the worst shifts, one pass
+      // ---- preconditioned residuals of kTry shifts, one pass.  The worst shift first, then
+      // greedily the shift whose norm times its distance (in z) to the shifts taken is largest:
+      // the solutions vary smoothly with z, so corrections of neighbouring shifts are nearly
+      // parallel, and spreading them over the shift set spans more of all shifts' errors.
       ph.mark(c, "candidates");
       const int nt = std::min<int>(kTry, (int)order.size());
       std::vector<int> qs(nt);
       std::vector<zc> zq(nt);
-      for (int t = 0; t < nt; ++t) { qs[t] = order[t].second; zq[t] = s.z[qs[t]]; }
+      {
+        std::vector<char> taken(order.size(), 0);
+        for (int t = 0; t < nt; ++t) {
+          int bi = 0;
+          double bv = -1.0;
+          for (size_t i = 0; i < order.size() && t > 0; ++i) {
+            if (taken[i]) continue;
+            double dmin = 1e300;
+            for (int p = 0; p < t; ++p) dmin = std::min(dmin, std::abs(s.z[order[i].second] - s.z[qs[p]]));
+            const double v = order[i].first * dmin;
+            if (v > bv) { bv = v; bi = (int)i; }
+          }
+          taken[bi] = 1;
+          qs[t] = order[bi].second;
+          zq[t] = s.z[qs[t]];
+        }
+      }
       to_dev(c, zq.data(), zdev, nt);
       double pre2[kVecMatOut];
       {
