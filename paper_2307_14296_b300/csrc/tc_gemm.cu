@@ -734,10 +734,14 @@ __global__ void __launch_bounds__(x::THREADS, 1)
 // the fixed-point digits is that value - 1022, so that |x| < 2^e).  rexp is zeroed beforehand.
 __device__ __forceinline__ uint32_t bexp64(double v) { return (uint32_t)((uint64_t)__double_as_longlong(v) >> 52) & 0x7ffu; }
 
-// Signed base-256 digits of x on the grid of a row whose largest biased exponent is eb_row:
-// x = sum_s d_s 2^(eb_row - 1029 - 8 s) (rounded at the last digit), |d_s| <= 128, integer pipe
-// only.  Subnormal x counts as 0.
-__device__ __forceinline__ void ozaki_digits(double v, uint32_t eb_row, int (&d)[x::NS]) {
+// Signed base-256 digits of x on the grid of a row whose largest biased exponent is eb_row: the
+// fixed-point integer X = round(x / 2^(eb_row - 1061)) (|X| <= 2^39; subnormal x counts as 0)
+// is written as X = sum_s d_s 2^(32 - 8 s) with d_0 in [-128, 128] and d_1..d_4 in [-128, 127],
+// read from the bytes of U = X + kDigitOffset (>= 0): kDigitOffset holds 128 in each of the five
+// digit positions, so the low four bytes of U are d_4..d_1 + 128 and U >> 32 is d_0 + 128.
+// Returns U (integer pipe only).
+constexpr int64_t kDigitOffset = 0x8080808080ll;
+__device__ __forceinline__ uint64_t ozaki_offset(double v, uint32_t eb_row) {
   const uint64_t b = (uint64_t)__double_as_longlong(v);
   const uint32_t eb = (uint32_t)(b >> 52) & 0x7ffu;
   int64_t X = 0;
@@ -747,11 +751,11 @@ __device__ __forceinline__ void ozaki_digits(double v, uint32_t eb_row, int (&d)
     if (rs < 64) X = (int64_t)((M + (1ull << (rs - 1))) >> rs);
     if (b >> 63) X = -X;
   }
-  d[0] = (int)((X + (1ll << 31)) >> 32); X -= (int64_t)d[0] << 32;
-  d[1] = (int)((X + (1ll << 23)) >> 24); X -= (int64_t)d[1] << 24;
-  d[2] = (int)((X + (1ll << 15)) >> 16); X -= (int64_t)d[2] << 16;
-  d[3] = (int)((X + (1ll << 7)) >> 8);   X -= (int64_t)d[3] << 8;
-  d[4] = (int)X;
+  return (uint64_t)(X + kDigitOffset);
+}
+// d_s + 128 from U
+__device__ __forceinline__ uint32_t ozaki_byte(uint64_t U, int s) {
+  return s == 0 ? (uint32_t)(U >> 32) : ((uint32_t)U >> (32 - 8 * s)) & 0xffu;
 }
 // BF16 bits of d 2^p (|d| <= 256, exact); values below the BF16 normal range flush to zero
 __device__ __forceinline__ uint32_t bf16_digit(int d, int p) {
@@ -765,23 +769,45 @@ __device__ __forceinline__ uint32_t bf16_digit(int d, int p) {
   const uint32_t frac = (a << (7 - msb)) & 0x7fu;
   return sign | ((uint32_t)be << 7) | frac;
 }
+// binary32 bits of (byte - 128) 2^p for a row whose digit scales are normal binary32 numbers:
+// 2^23 + byte is exact in binary32 (exponent-bias construction), the subtraction of 2^23 + 128 is
+// exact, and so is the power-of-two scaling (overflow gives infinity, as bf16_digit).  Its top
+// 16 bits are the BF16 digit (at most 8 significant bits).
+__device__ __forceinline__ uint32_t digit_f32_bits(uint32_t byte, float scale) {
+  return __float_as_uint(__fmul_rn(__fsub_rn(__uint_as_float(0x4B000000u | byte), 8388736.0f), scale));
+}
 // the digit planes of one element pair (k, k+1) of a row: out32[plane] = bf16(k) | bf16(k+1) << 16
-__device__ __forceinline__ void ozaki_pair(const double2 (&xv)[2], uint32_t eb_row, uint32_t (&out)[2 * x::NS]) {
+// (only the first nd digit planes are formed: the rest are zero on coarse operands and never read)
+__device__ __forceinline__ void ozaki_pair(const double2 (&xv)[2], uint32_t eb_row, uint32_t (&out)[2 * x::NS], int nd) {
   if (eb_row == 0x7ffu) {   // infinity or NaN in the row: propagate NaN
 #pragma unroll
     for (int q = 0; q < 2 * x::NS; ++q) out[q] = 0x7fc07fc0u;
     return;
   }
-  int dr[2][x::NS], di[2][x::NS];
-  ozaki_digits(xv[0].x, eb_row, dr[0]);
-  ozaki_digits(xv[0].y, eb_row, di[0]);
-  ozaki_digits(xv[1].x, eb_row, dr[1]);
-  ozaki_digits(xv[1].y, eb_row, di[1]);
+  const uint64_t u[4] = {ozaki_offset(xv[0].x, eb_row), ozaki_offset(xv[0].y, eb_row),
+                         ozaki_offset(xv[1].x, eb_row), ozaki_offset(xv[1].y, eb_row)};
+  if (eb_row >= 935u && eb_row <= 1156u) {   // every 2^p_s, p_s = eb_row - 1029 - 8 s, a normal binary32
+#pragma unroll
+    for (int s = 0; s < x::NS; ++s) {
+      if (s >= nd) break;
+      const float scale = __uint_as_float((uint32_t)((int)eb_row - 1029 - 8 * s + 127) << 23);
+      uint32_t f[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) f[t] = digit_f32_bits(ozaki_byte(u[t], s), scale);
+      out[2 * s + 0] = __byte_perm(f[0], f[2], 0x7632);   // top halves: bf16(k) | bf16(k+1) << 16
+      out[2 * s + 1] = __byte_perm(f[1], f[3], 0x7632);
+    }
+    return;
+  }
 #pragma unroll
   for (int s = 0; s < x::NS; ++s) {
+    if (s >= nd) break;
     const int p = (int)eb_row - 1029 - 8 * s;
-    out[2 * s + 0] = bf16_digit(dr[0][s], p) | (bf16_digit(dr[1][s], p) << 16);
-    out[2 * s + 1] = bf16_digit(di[0][s], p) | (bf16_digit(di[1][s], p) << 16);
+    uint32_t h[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) h[t] = bf16_digit((int)ozaki_byte(u[t], s) - 128, p);
+    out[2 * s + 0] = h[0] | (h[2] << 16);
+    out[2 * s + 1] = h[1] | (h[3] << 16);
   }
 }
 
@@ -866,9 +892,10 @@ __global__ void __launch_bounds__(256) k_split_view(const double2* __restrict__ 
           if (conj) xv[t].y = -xv[t].y;
         }
         uint32_t o[2 * x::NS];
-        ozaki_pair(xv, rexp[r], o);
+        ozaki_pair(xv, rexp[r], o, nd);
 #pragma unroll
-        for (int q = 0; q < 2 * nd; ++q) o32[(q * plane) / 2 + e2] = o[q];   // zero digit planes are not read
+        for (int q = 0; q < 2 * x::NS; ++q)
+          if (q < 2 * nd) o32[(q * plane) / 2 + e2] = o[q];   // zero digit planes are not read
         continue;
       }
       float re[2], im[2];
@@ -954,10 +981,11 @@ __global__ void __launch_bounds__(256) k_split_view_t(const double2* __restrict_
         double2 xv[2] = {tile[2 * lane][j], tile[2 * lane + 1][j]};
         if (conj) { xv[0].y = -xv[0].y; xv[1].y = -xv[1].y; }
         uint32_t o[2 * x::NS];
-        ozaki_pair(xv, rexp[row], o);
+        ozaki_pair(xv, rexp[row], o, nd);
         const int64_t e2 = row * (Kpad / 2) + (k0 / 2) + lane;
 #pragma unroll
-        for (int q = 0; q < 2 * nd; ++q) o32[(q * plane) / 2 + e2] = o[q];   // zero digit planes are not read
+        for (int q = 0; q < 2 * x::NS; ++q)
+          if (q < 2 * nd) o32[(q * plane) / 2 + e2] = o[q];   // zero digit planes are not read
         continue;
       }
       float re[2], im[2];
