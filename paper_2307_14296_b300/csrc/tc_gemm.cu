@@ -645,16 +645,28 @@ __global__ void __launch_bounds__(x::THREADS, 1)
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
               const int col = x::COLS * ch + 8 * q + j;
-              const float xr = __uint_as_float(a_re[j]), xi = __uint_as_float(a_im[j]);
               if (firstc && gx == 0) {
-                hi[col * BM] = make_float2(xr, xi);
+                hi[col * BM] = make_float2(__uint_as_float(a_re[j]), __uint_as_float(a_im[j]));
                 lo[col * BM] = make_float2(0.0f, 0.0f);
-              } else {
-                float2 h = hi[col * BM], l = lo[col * BM];
-                ff_add(h.x, l.x, xr, 0.0f);
-                ff_add(h.y, l.y, xi, 0.0f);
-                hi[col * BM] = h;
-                lo[col * BM] = l;
+              }
+            }
+            if (!(firstc && gx == 0)) {
+              // all eight columns' running sums are loaded before any is stored, so that the
+              // loads (L2 hits) overlap instead of waiting behind the stores of earlier columns
+              float2 h[8], l[8];
+#pragma unroll
+              for (int j = 0; j < 8; ++j) {
+                const int col = x::COLS * ch + 8 * q + j;
+                h[j] = hi[col * BM];
+                l[j] = lo[col * BM];
+              }
+#pragma unroll
+              for (int j = 0; j < 8; ++j) {
+                const int col = x::COLS * ch + 8 * q + j;
+                ff_add(h[j].x, l[j].x, __uint_as_float(a_re[j]), 0.0f);
+                ff_add(h[j].y, l[j].y, __uint_as_float(a_im[j]), 0.0f);
+                hi[col * BM] = h[j];
+                lo[col * BM] = l[j];
               }
             }
           }
@@ -671,15 +683,20 @@ __global__ void __launch_bounds__(x::THREADS, 1)
 #pragma unroll 2
           for (int q = 0; q < x::COLS / 8; ++q) {
             uint32_t q_re[8], q_im[8];
+            float2 l8[8];
             tmem_ld8(gbase + 8 * q, q_re);
             tmem_ld8(gbase + x::BN + 8 * q, q_im);
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
               const int col = x::COLS * ch + 8 * q + j;
-              float2 l = lo[col * BM];
-              l.x = __fadd_rn(l.x, __uint_as_float(q_re[j]));
-              l.y = __fadd_rn(l.y, __uint_as_float(q_im[j]));
-              lo[col * BM] = l;
+              l8[j] = lo[col * BM];
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const int col = x::COLS * ch + 8 * q + j;
+              l8[j].x = __fadd_rn(l8[j].x, __uint_as_float(q_re[j]));
+              l8[j].y = __fadd_rn(l8[j].y, __uint_as_float(q_im[j]));
+              lo[col * BM] = l8[j];
             }
           }
           fence_before();
