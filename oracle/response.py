@@ -225,6 +225,100 @@ class CCSystem:
         return out
 
 
+    # -- static-field derivative of the response function
+    def at(self, t=None, lam=None):
+        """The same Hamiltonian at other amplitudes and/or multipliers (packed vectors; default the
+        converged ones): Hbar rebuilt at t, nothing solved."""
+        t = pack(self.t1, self.t2) if t is None else t
+        lam = pack(self.l1, self.l2) if lam is None else lam
+        return CCSystem(self.I, t=unpack(t, self.o, self.v), lam=unpack(lam, self.o, self.v))
+
+    def field_derivative(self, ops, V, zs, solver="dense", tol=1e-12, A=None):
+        """d<<X_a; X_b>>_z / d eps for the field H + eps V (V added to the Fock matrix, orbitals
+        unrelaxed), operators fixed: array [len(zs), nops, nops], symmetrized as f'(z) +
+        conj(f'(-z*)).  The CC-CC response function (Sec. 2.3) differentiated by the chain rule
+        through the ground amplitudes, the multipliers and the response amplitudes; the
+        derivatives of the response amplitudes are eliminated with the first-order multipliers
+        tbar^k(w) (A + w) = -(eta^k + F t^k(w)):
+          f'(w) = 1/2 [eta^a' t^b + eta^b' t^a + t^a F' t^b
+                       + tbar^a(-w) (A' t^b + xi^b') + tbar^b(w) (A' t^a + xi^a')],
+          t^b = t^b(w), t^a = t^a(-w).
+        The field enters as Omega + eps xi^V(t) and E + eps <HF|e^-T V e^T|HF>, so
+          t^V = d t0/d eps = -A^-1 xi^V,   lam^V A = -(eta^V + F t^V),
+          A' u = D^2 Omega[t^V, u] + D xi^V[u],   xi^k' = D xi^k[t^V],
+          eta^k' = D_t eta^k[t^V] + eta^k(lam^V) - eta^k(lam = 0),
+          F' u = D_t (F u)[t^V] + F(lam^V) u - F(lam = 0) u + D_t eta^V[u],
+        D the directional derivative in the amplitudes.  Every differentiated quantity is a
+        polynomial in the amplitudes of degree <= 3 (sigma, Omega), 2 (xi, F) or 1 (eta), so the
+        five-point stencil used here is exact up to rounding; eta and F are linear in lambda."""
+        nops = len(ops)
+        n = self.D.size
+        t0 = pack(self.t1, self.t2)
+        if solver == "dense" and A is None:
+            A = self.dense_A()
+        eye = np.eye(n)
+
+        def solve_r(rhs, w):     # (A - w) t = -rhs
+            if solver == "dense":
+                return -np.linalg.solve(A - w * eye, rhs)
+            return self.davidson(rhs, w, tol=tol)[0]
+
+        def solve_l(rhs, w):     # tbar (A + w) = -rhs
+            if solver == "dense":
+                return -np.linalg.solve(A.T + w * eye, rhs)
+            return self.davidson(rhs, -w, tol=tol, op=self.sigma_l)[0]
+
+        def ddir(g, u):
+            """d/ds g(t0 + s u) at s = 0 for g a polynomial of degree <= 4 in s (exact stencil)."""
+            h = 0.05 / max(np.abs(u).max(), 1e-300)
+            vals = {s: g(self.at(t=t0 + s * h * u)) for s in (-2, -1, 1, 2)}
+            return (vals[-2] - 8 * vals[-1] + 8 * vals[1] - vals[2]) / (12 * h)
+
+        tV = solve_r(self.xi(V), 0.0)
+        lamV = solve_l(self.eta(V) + self.hessian(tV), 0.0)
+        sys_l, sys_0 = self.at(lam=lamV), self.at(lam=np.zeros(n, dtype=np.complex128))
+        shifted = {s: self.at(t=t0 + s * (0.05 / max(np.abs(tV).max(), 1e-300)) * tV) for s in (-2, -1, 1, 2)}
+        hV = 0.05 / max(np.abs(tV).max(), 1e-300)
+
+        def along_tV(g):         # D_t g[t^V] from the four shifted systems
+            return (g(shifted[-2]) - 8 * g(shifted[-1]) + 8 * g(shifted[1]) - g(shifted[2])) / (12 * hV)
+
+        eta_p = [along_tV(lambda S, X=X: S.eta(X)) + sys_l.eta(X) - sys_0.eta(X) for X in ops]
+        xi_p = [along_tV(lambda S, X=X: S.xi(X)) for X in ops]
+        eta = [self.eta(X) for X in ops]
+        cache = {}
+
+        def t_of(k, w):
+            key = ("r", k, complex(w))
+            if key not in cache:
+                cache[key] = solve_r(self.xi(ops[k]), w)
+            return cache[key]
+
+        def tbar_of(k, w):
+            key = ("l", k, complex(w))
+            if key not in cache:
+                cache[key] = solve_l(eta[k] + self.hessian(t_of(k, w)), w)
+            return cache[key]
+
+        def a_prime(u):          # A' u
+            return along_tV(lambda S: S.sigma_r(u)) + ddir(lambda S: S.xi(V), u)
+
+        def f_prime(w, a, b):
+            tb, ta = t_of(b, w), t_of(a, -w)
+            Fp_tb = (along_tV(lambda S: S.hessian(tb)) + sys_l.hessian(tb) - sys_0.hessian(tb)
+                     + ddir(lambda S: S.eta(V), tb))
+            return 0.5 * (self.bdot(eta_p[a], tb) + self.bdot(eta_p[b], ta) + self.bdot(ta, Fp_tb)
+                          + self.bdot(tbar_of(a, -w), a_prime(tb) + xi_p[b])
+                          + self.bdot(tbar_of(b, w), a_prime(ta) + xi_p[a]))
+
+        out = np.zeros((len(zs), nops, nops), dtype=np.complex128)
+        for k, z in enumerate(zs):
+            for a in range(nops):
+                for b in range(nops):
+                    out[k, a, b] = f_prime(z, a, b) + np.conj(f_prime(-np.conj(z), a, b))
+        return out
+
+
 def polarizability(resp):
     """alpha_xy = -<<mu_x; mu_y>>."""
     return -resp

@@ -200,3 +200,58 @@ def test_asymmetric_form_needs_the_hessian_term(four_electron, monkeypatch):
     monkeypatch.setattr(s, "hessian", lambda u: np.zeros_like(u))
     bad = s.response(inst.ops, zs, solver="dense", A=A, form="asym")
     assert np.abs(bad - cc).max() > 1e-4 * np.abs(cc).max()
+
+
+def _herm(n, seed, scale):
+    rng = np.random.default_rng(seed)
+    a = rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n))
+    return scale * (a + a.conj().T) / 2
+
+
+def _richardson(fun, h=1e-3):
+    """d/d eps at 0 by central differences at h and h/2 with one Richardson step (error O(h^4))."""
+    d1 = (fun(h) - fun(-h)) / (2 * h)
+    d2 = (fun(h / 2) - fun(-h / 2)) / h
+    return (4 * d2 - d1) / 3
+
+
+ZF = [0.0, 0.1 + 0.01j]
+
+
+def test_field_derivative_two_electron_matches_fci_finite_field():
+    """The analytic static-field derivative of <<X;Y>> (field V on the Fock matrix) against the
+    finite-field derivative of the exact sum over states (FCI) for two electrons."""
+    inst = synth.make_instance(2, 6, seed=11, sd=0.05)
+    V = _herm(8, 3, 0.05)
+    got = R.CCSystem(Ints.from_instance(inst)).field_derivative(inst.ops, V, ZF)
+    eri = synth.full_eri(inst)
+    ref = _richardson(lambda e: det.fci_response(inst.fock + e * V, eri, 2, inst.ops, ZF)[0])
+    assert np.abs(got - ref).max() < 1e-8 * np.abs(ref).max()
+
+
+def test_field_derivative_matches_cc_finite_field(four_electron):
+    """Four electrons: against the finite-field derivative of the CC-CC response function itself
+    (CCSD, Lambda and the response solved again at eps = +-h, +-h/2); dense and Davidson solves."""
+    inst, s, A = four_electron
+    V = _herm(12, 4, 0.05)
+    got = s.field_derivative(inst.ops, V, ZF, A=A)
+
+    def resp(e):
+        se = R.CCSystem(s.I.with_fock(inst.fock + e * V), tol=1e-13)
+        return se.response(inst.ops, ZF, solver="dense", A=se.dense_A())
+    ref = _richardson(resp)
+    assert np.abs(got - ref).max() < 1e-8 * np.abs(ref).max()
+    dav = s.field_derivative(inst.ops, V, ZF[1:], solver="davidson", tol=1e-12)
+    assert np.abs(dav - got[1:]).max() < 1e-8 * np.abs(ref).max()
+
+
+def test_field_derivative_needs_the_multiplier_response(four_electron, monkeypatch):
+    """Planted mistake: with the multipliers held at lambda0 in every shifted system (the
+    lambda^V terms dropped) the derivative no longer matches, so the pin above checks them."""
+    inst, s, A = four_electron
+    V = _herm(12, 4, 0.05)
+    good = s.field_derivative(inst.ops, V, ZF[1:], A=A)
+    orig = R.CCSystem.at
+    monkeypatch.setattr(R.CCSystem, "at", lambda self, t=None, lam=None: orig(self, t=t))
+    bad = s.field_derivative(inst.ops, V, ZF[1:], A=A)
+    assert np.abs(bad - good).max() > 1e-4 * np.abs(good).max()
