@@ -204,6 +204,21 @@ cclr_status cc_response_function_ci(cclr_ctx *ctx, cclr_c128 *out);
  * multiplier solve does not converge within maxit (out is then not written). */
 cclr_status cc_response_function_asym(cclr_ctx *ctx, cclr_c128 *out);
 
+/* Static-field derivative of the CC-CC response function (Sec. 2.3 Eq. CC-CC response function
+ * differentiated): out[f][x][y] = d<<X_x;X_y>>_{w_f + i gamma} / d eps for the Hamiltonian with
+ * eps V added to its Fock matrix (orbitals unrelaxed, as the response functions), at the
+ * operators and frequencies of the last cc_lr_solve; d alpha / d eps = -out.  V: an n x n matrix,
+ * row-major, host or device memory.  The derivative follows from the chain rule through the
+ * ground amplitudes (t^V = -A^-1 xi^V), the multipliers (lam^V A = -(eta^V + F t^V)) and the
+ * response amplitudes, whose derivatives are eliminated with the first-order multipliers
+ * tbar^k(w) (A + w) = -(eta^k + F t^k(w)); the amplitude derivatives of sigma, xi, eta and F are
+ * taken from the library's products at shifted amplitudes by stencils that are exact for their
+ * polynomial degree.  Costs one right and one left static solve, 4 n_ops left solves per
+ * frequency, and per frequency four Hbar builds with batched sigma and Hessian products.
+ * Requires cc_lr_solve; CCLR_E_ARG on non-finite V; CCLR_E_NOCONV if a solve does not converge
+ * (the context's amplitudes and multipliers are restored in every case). */
+cclr_status cclr_field_derivative(cclr_ctx *ctx, const cclr_c128 *V, cclr_c128 *out);
+
 /* EOM-CCSD excitation energies (SI "EOM-EE sigma-vectors and intermediates"; the Davidson scheme
  * applied to the eigenproblem): the n_roots (1..16) eigenvalues of the CC Jacobian A with the
  * smallest real part, from a non-Hermitian Davidson iteration on right sigma products with the

@@ -32,7 +32,7 @@ AMP_T, AMP_LAMBDA = 0, 1
 EXPORTS = (
     "cclr_default_options", "cclr_create", "cclr_destroy", "cclr_last_error", "cclr_set_hamiltonian",
     "cc_ground", "cc_lambda", "cc_lr_solve", "cc_response_function", "cc_response_function_ci", "cc_response_function_asym",
-    "cc_eom_ee",
+    "cclr_field_derivative", "cc_eom_ee",
     "cclr_get_eom_vector",
     "cclr_get_amplitudes",
     "cclr_set_amplitudes", "cclr_get_response_vector", "cclr_sigma", "cclr_residual", "cclr_xi",
@@ -69,6 +69,7 @@ _sig = {
     "cc_response_function": (_i, [_vp, _vp]),
     "cc_response_function_ci": (_i, [_vp, _vp]),
     "cc_response_function_asym": (_i, [_vp, _vp]),
+    "cclr_field_derivative": (_i, [_vp, _vp, _vp]),
     "cc_eom_ee": (_i, [_vp, _i, _vp, _vp]),
     "cclr_get_eom_vector": (_i, [_vp, _i, _vp, ctypes.c_size_t]),
     "cclr_get_amplitudes": (_i, [_vp, _i, _vp, _sz]),
@@ -229,7 +230,7 @@ class Context:
         om = np.ascontiguousarray(omegas, dtype=np.float64)
         its = np.zeros(ops.shape[0] * om.size, np.int32)
         self._check(_lib.cc_lr_solve(self._h, ops.shape[0], p, om.size, _ptr(om), float(gamma), _ptr(its)))
-        self._nops, self._nfreq = ops.shape[0], om.size
+        self._nops, self._nfreq, self._norb = ops.shape[0], om.size, ops.shape[-1]
         self.lr_serial = getattr(self, "lr_serial", 0) + 1
         return its.reshape(ops.shape[0], om.size)
 
@@ -273,6 +274,16 @@ class Context:
         solutions."""
         out = np.zeros((self._nfreq, self._nops, self._nops), np.complex128)
         self._check(_lib.cc_response_function_asym(self._h, _ptr(out)))
+        return out
+
+    def cclr_field_derivative(self, V):
+        """d<<X_x;X_y>>/d eps [n_freq, n_ops, n_ops] for the field eps V on the Fock matrix (V: n x n,
+        host or CUDA); d alpha / d eps is its negative."""
+        p, keep = _in(V)
+        if tuple(keep.shape) != (self._norb, self._norb):
+            raise ValueError("V must be an n x n matrix of the operators' size")
+        out = np.zeros((self._nfreq, self._nops, self._nops), np.complex128)
+        self._check(_lib.cclr_field_derivative(self._h, p, _ptr(out)))
         return out
 
     def cc_eom_ee(self, n_roots):

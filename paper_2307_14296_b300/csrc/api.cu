@@ -469,6 +469,14 @@ cclr_status cc_response_function_asym(cclr_ctx* h, cclr_c128* out) {
   });
 }
 
+cclr_status cclr_field_derivative(cclr_ctx* h, const cclr_c128* V, cclr_c128* out) {
+  return guard(h, [&](Ctx& c) {
+    CCLR_REQUIRE(V && out, CCLR_E_ARG, "null argument");
+    require_finite(c, (const cplx*)V, c.n * c.n, "cclr_field_derivative: field operator");
+    field_derivative(c, (const cplx*)V, (cplx*)out);
+  });
+}
+
 cclr_status cc_eom_ee(cclr_ctx* h, int n_roots, cclr_c128* energies_out, int* iters_out) {
   return guard(h, [&](Ctx& c) {
     CCLR_REQUIRE(energies_out, CCLR_E_ARG, "null output");

@@ -243,6 +243,7 @@ void lr_solve(Ctx& c, int n_ops, const cplx* ops_host, int n_freq, const double*
 void response_function(Ctx& c, cplx* out_host);
 void response_function_ci(Ctx& c, cplx* out_host);
 void response_function_asym(Ctx& c, cplx* out_host);
+void field_derivative(Ctx& c, const cplx* V, cplx* out_host);   // d<<X;Y>>/d eps, field V on the Fock matrix
 void response_gradient(Ctx& c, int f, cplx* out_host);   // operator gradient of <<X;Y>> (adjoint)
 void left_solve(Ctx& c, int nrhs, const cplx* rhs, zc w, cplx* out);   // l (A + w) = -b
 void synthetic_instance(Ctx& c, int n_occ, int n_vir, uint64_t seed, double sd, double dip_sd, int n_ops,

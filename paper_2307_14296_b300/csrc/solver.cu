@@ -1504,6 +1504,281 @@ void response_function_asym(Ctx& c, cplx* out_host) {
       }
 }
 
+// Static-field derivative of the CC-CC response function (Sec. 2.3 differentiated): d<<X_a;X_b>>_z
+// / d eps for H + eps V (V added to the Fock matrix, orbitals unrelaxed), operators fixed, from the
+// solutions of the last cc_lr_solve.  The derivatives of the response amplitudes are eliminated
+// with the first-order multipliers tbar^k(w) (A + w) = -(eta^k + F t^k(w)):
+//   f'(w) = 1/2 [eta^a' t^b + eta^b' t^a + t^a F' t^b + tbar^a(-w) (A' t^b + xi^b')
+//                + tbar^b(w) (A' t^a + xi^a')],   t^b = t^b(w), t^a = t^a(-w),
+//   <<X_a;X_b>>'_z = f'(z) + conj(f'(-z*)).
+// The field enters as Omega + eps xi^V(t) and E + eps <HF|e^-T V e^T|HF>, so with
+// t^V = -A^-1 xi^V (ground amplitudes) and lam^V A = -(eta^V + F t^V) (multipliers):
+//   A' u = D^2 Omega[t^V, u] + D xi^V[u],   xi^k' = D xi^k[t^V],
+//   eta^k' = D_t eta^k[t^V] + eta^k(lam^V) - eta^k(lam = 0),
+//   F' u = D_t (F u)[t^V] + F(lam^V) u - F(lam = 0) u + D_t eta^V[u].
+// D is the directional derivative in the amplitudes, taken from the library's own products at
+// shifted amplitudes: sigma is a cubic in the amplitudes (five-point stencil, exact for degree
+// 4), xi and F are quadratics and eta is linear (central differences, exact); eta and F are
+// linear in the multipliers.  Products run in the exact mode of the context (FP64, or the
+// FP64-class mode of refined solves); the solves are those of cc_lr_solve (refined likewise).
+void field_derivative(Ctx& c, const cplx* V_in, cplx* out_host) {
+  ResponseData& rd = c.rd;
+  CCLR_REQUIRE(rd.solved, CCLR_E_STATE, "cclr_field_derivative before cc_lr_solve");
+  CCLR_REQUIRE(c.have_lambda && c.have_hbar, CCLR_E_STATE, "cclr_field_derivative needs T and Lambda");
+  const int64_t N = c.N, n = c.n;
+  const int nop = rd.n_ops, nv = 4 * nop, maxL = std::max(8, c.opt.max_subspace);
+  const int prec = rd.refined ? (int)CCLR_TC_F64 : exact_precision(c);
+  const int bmax = c.opt.batch > 0 ? c.opt.batch : nv;
+  std::vector<cplx*> owned;
+  auto alloc = [&](int64_t m) { cplx* p = c.dalloc(m); owned.push_back(p); return p; };
+  cplx* Vd = alloc(n * n);
+  cplx* t0 = alloc(N);
+  cplx* l0 = alloc(N);
+  cplx* tmp = alloc(N);
+  cplx* xiV = alloc(N);
+  cplx* etaV = alloc(N);
+  cplx* tV = alloc(N);
+  cplx* lamV = alloc(N);
+  cplx* Tv = alloc((int64_t)nv * N);    // t^k(z_s), [k][s]
+  cplx* Lv = alloc((int64_t)nv * N);    // tbar^k(z_s)
+  cplx* Ap = alloc((int64_t)nv * N);    // A' t^k(z_s)
+  cplx* Fp = alloc((int64_t)nv * N);    // F' t^k(z_s)
+  cplx* Pv = alloc((int64_t)nv * N);    // products of one batched call
+  cplx* etap = alloc((int64_t)nop * N); // eta^k'
+  cplx* xip = alloc((int64_t)nop * N);  // xi^k'
+  bool moved = false;                   // amplitudes or multipliers differ from the converged ones
+  auto set_amps = [&](const cplx* t) {
+    copy_vec(c.L, N, t, c.t);
+    expand_t2(c, c.t + c.Ns, c.t2, 1);
+  };
+  auto set_lam = [&](const cplx* l) {
+    copy_vec(c.L, N, l, c.lam);
+    expand_t2(c, c.lam + c.Ns, c.l2, 1);
+    c.named.erase("F.ready");
+  };
+  auto rebuild = [&]() {
+    build_hbar(c);
+    c.named.erase("F.ready");
+  };
+  auto shift_amps = [&](const cplx* u, double h) {   // amplitudes t0 + h u
+    copy_vec(c.L, N, t0, tmp);
+    axpy(c.L, N, cx(h), u, tmp);
+    set_amps(tmp);
+  };
+  auto restore = [&]() {
+    if (!moved) return;
+    PrecisionScope exact(c, prec);
+    set_amps(t0);
+    rebuild();
+    set_lam(l0);
+    moved = false;
+  };
+  auto step_for = [&](const cplx* u) {   // stencil step: at most 0.05 per element of h u
+    const double nu = std::sqrt(norm2(c, u));
+    return nu > 0.0 ? 0.05 / nu : 1.0;
+  };
+  // batched products of the nv vectors Tv into Pv, then dst += a Pv
+  auto batched = [&](void (*fn)(Ctx&, int, const cplx*, cplx*), cplx* dst, cplx a) {
+    for (int q0 = 0; q0 < nv; q0 += bmax) {
+      const int nb = std::min(bmax, nv - q0);
+      fn(c, nb, Tv + (int64_t)q0 * N, Pv + (int64_t)q0 * N);
+    }
+    axpy(c.L, (int64_t)nv * N, a, Pv, dst);
+  };
+  auto dot = [&](const cplx* x, const cplx* y) {
+    std::vector<zc> g;
+    gram_host(c, rows(c, x, 1), rows(c, y, 1), false, g);
+    return g[0];
+  };
+  auto vec = [&](cplx* base, int k, int sidx) { return base + ((int64_t)k * 4 + sidx) * N; };
+  try {
+    CCLR_CK(cudaMemcpyAsync(Vd, V_in, sizeof(cplx) * n * n, cudaMemcpyDefault, c.stream));
+    copy_vec(c.L, N, c.t, t0);
+    copy_vec(c.L, N, c.lam, l0);
+    {
+      PrecisionScope exact(c, prec);
+      xi_vec(c, Vd, xiV);
+      eta_vec(c, Vd, false, etaV);
+    }
+    // t^V: (A - 0) t = -xi^V
+    {
+      std::vector<System> sys(1);
+      sys[0].rhs = xiV;
+      sys[0].z = {zc(0.0)};
+      sys[0].B = c.dalloc((int64_t)maxL * N);
+      sys[0].S = c.dalloc((int64_t)maxL * N);
+      auto free_sys = [&]() {
+        if (sys[0].B) c.dfree(sys[0].B);
+        if (sys[0].S) c.dfree(sys[0].S);
+        sys[0].B = sys[0].S = nullptr;
+      };
+      try {
+        auto op = [&](int m, const cplx* in, cplx* o) { sigma_right(c, m, in, o); };
+        davidson(c, sys, op, maxL, c.opt.tol);
+        if (refining(c)) refine_systems(c, sys, op, maxL, c.opt.tol, nullptr, nullptr);
+        Scope sc(c.ws);
+        cplx* bd = c.ws.cplxs(maxL);
+        to_dev(c, sys[0].beta[0].data(), bd, sys[0].L);
+        lincomb(c.L, N, sys[0].L, sys[0].B, N, bd, tV, false);
+      } catch (...) {
+        free_sys();
+        throw;
+      }
+      free_sys();
+    }
+    // lam^V: lam (A + 0) = -(eta^V + F t^V)
+    {
+      PrecisionScope exact(c, prec);
+      hessian_right(c, 1, tV, tmp);
+      axpy(c.L, N, cx(1), etaV, tmp);
+    }
+    left_solve(c, 1, tmp, zc(0.0), lamV);
+    const double hV = step_for(tV);
+    fill_zero(c.L, etap, (int64_t)nop * N);
+    fill_zero(c.L, xip, (int64_t)nop * N);
+    std::vector<zc> half((size_t)rd.n_freq * nop * nop * 2);   // [f][a][b][w], w: 0 z, 1 -z*
+    for (int f = 0; f < rd.n_freq; ++f) {
+      // response amplitudes t^k(z_s) and first-order multipliers tbar^k(z_s)
+      {
+        PrecisionScope exact(c, prec);
+        Scope sc(c.ws);
+        cplx* bd = c.ws.cplxs(maxL);
+        for (int k = 0; k < nop; ++k)
+          for (int q = 0; q < 4; ++q) {
+            to_dev(c, &rd.beta[k][(size_t)rd.shift_of[(size_t)f * 4 + q] * maxL], bd, rd.nb[k]);
+            lincomb(c.L, N, rd.nb[k], rd.basis[k], N, bd, vec(Tv, k, q), false);
+          }
+      }
+      {
+        std::vector<System> sys((size_t)nv);
+        auto free_sys = [&]() {
+          for (auto& sy : sys) {
+            if (sy.rhs) c.dfree(const_cast<cplx*>(sy.rhs));
+            if (sy.B) c.dfree(sy.B);
+            if (sy.S) c.dfree(sy.S);
+            sy.rhs = nullptr;
+            sy.B = sy.S = nullptr;
+          }
+        };
+        try {
+          {
+            PrecisionScope exact(c, prec);
+            for (int k = 0; k < nop; ++k)
+              for (int q = 0; q < 4; ++q) {
+                System& sy = sys[(size_t)4 * k + q];
+                cplx* b = c.dalloc(N);
+                sy.rhs = b;
+                hessian_right(c, 1, vec(Tv, k, q), b);
+                axpy(c.L, N, cx(1), rd.eta[k], b);
+                sy.z = {-rd.shifts[rd.shift_of[(size_t)f * 4 + q]]};
+                sy.B = c.dalloc((int64_t)maxL * N);
+                sy.S = c.dalloc((int64_t)maxL * N);
+              }
+          }
+          auto op = [&](int m, const cplx* in, cplx* o) { sigma_left(c, m, in, o); };
+          davidson(c, sys, op, maxL, c.opt.tol);
+          if (refining(c)) refine_systems(c, sys, op, maxL, c.opt.tol, nullptr, nullptr);
+          Scope sc(c.ws);
+          cplx* bd = c.ws.cplxs(maxL);
+          for (int i = 0; i < nv; ++i) {
+            to_dev(c, sys[i].beta[0].data(), bd, sys[i].L);
+            lincomb(c.L, N, sys[i].L, sys[i].B, N, bd, Lv + (int64_t)i * N, false);
+          }
+        } catch (...) {
+          free_sys();
+          throw;
+        }
+        free_sys();
+      }
+      PrecisionScope exact(c, prec);
+      fill_zero(c.L, Ap, (int64_t)nv * N);
+      fill_zero(c.L, Fp, (int64_t)nv * N);
+      moved = true;
+      // multipliers lam^V and 0 at t0: (F(lam^V) - F(0)) u and eta^k(lam^V) - eta^k(0)
+      for (int side = 0; side < 2; ++side) {
+        const cplx sg = side == 0 ? cx(1) : cx(-1);
+        if (side == 0) {
+          set_lam(lamV);
+        } else {
+          fill_zero(c.L, tmp, N);
+          set_lam(tmp);
+        }
+        batched(hessian_right, Fp, sg);
+        if (f == 0)
+          for (int k = 0; k < nop; ++k) {
+            eta_vec(c, rd.ops_dev[k], false, tmp);
+            axpy(c.L, N, sg, tmp, etap + (int64_t)k * N);
+          }
+      }
+      set_lam(l0);
+      // amplitudes t0 + s hV t^V: D^2 Omega[t^V, u] (five-point), D_t (F u)[t^V], D xi^k[t^V] and
+      // D_t eta^k[t^V] (central)
+      const int sv[4] = {-2, -1, 1, 2};
+      const double c5[4] = {1.0 / 12, -8.0 / 12, 8.0 / 12, -1.0 / 12};
+      for (int i = 0; i < 4; ++i) {
+        shift_amps(tV, sv[i] * hV);
+        rebuild();
+        batched(sigma_right, Ap, cx(c5[i] / hV));
+        if (sv[i] == -1 || sv[i] == 1) {
+          const double w = sv[i] / (2.0 * hV);
+          batched(hessian_right, Fp, cx(w));
+          if (f == 0)
+            for (int k = 0; k < nop; ++k) {
+              xi_vec(c, rd.ops_dev[k], tmp);
+              axpy(c.L, N, cx(w), tmp, xip + (int64_t)k * N);
+              eta_vec(c, rd.ops_dev[k], false, tmp);
+              axpy(c.L, N, cx(w), tmp, etap + (int64_t)k * N);
+            }
+        }
+      }
+      set_amps(t0);
+      rebuild();
+      // amplitudes t0 +- h u for every response vector u: D xi^V[u] into A' u, D_t eta^V[u] into F' u
+      // (xi and eta read the amplitudes only; the Hbar of t0 stays valid)
+      for (int i = 0; i < nv; ++i) {
+        const cplx* u = Tv + (int64_t)i * N;
+        const double hu = step_for(u);
+        for (int sg = -1; sg <= 1; sg += 2) {
+          shift_amps(u, sg * hu);
+          xi_vec(c, Vd, tmp);
+          axpy(c.L, N, cx(sg / (2.0 * hu)), tmp, Ap + (int64_t)i * N);
+          eta_vec(c, Vd, false, tmp);
+          axpy(c.L, N, cx(sg / (2.0 * hu)), tmp, Fp + (int64_t)i * N);
+        }
+      }
+      set_amps(t0);
+      moved = false;
+      // f'(w) for w = z (t^b(z), t^a(-z)) and w = -z* (t^b(-z*), t^a(z*))
+      for (int a = 0; a < nop; ++a)
+        for (int b = 0; b < nop; ++b)
+          for (int w = 0; w < 2; ++w) {
+            const int sb = w == 0 ? 0 : 1, sa = w == 0 ? 3 : 2;
+            const cplx *tb = vec(Tv, b, sb), *ta = vec(Tv, a, sa);
+            zc val = dot(etap + (int64_t)a * N, tb) + dot(etap + (int64_t)b * N, ta) + dot(ta, vec(Fp, b, sb));
+            copy_vec(c.L, N, vec(Ap, b, sb), tmp);
+            axpy(c.L, N, cx(1), xip + (int64_t)b * N, tmp);
+            val += dot(vec(Lv, a, sa), tmp);
+            copy_vec(c.L, N, vec(Ap, a, sa), tmp);
+            axpy(c.L, N, cx(1), xip + (int64_t)a * N, tmp);
+            val += dot(vec(Lv, b, sb), tmp);
+            half[(((size_t)f * nop + a) * nop + b) * 2 + w] = 0.5 * val;
+          }
+    }
+    for (int f = 0; f < rd.n_freq; ++f)
+      for (int a = 0; a < nop; ++a)
+        for (int b = 0; b < nop; ++b) {
+          const size_t i = (((size_t)f * nop + a) * nop + b) * 2;
+          const zc val = half[i] + std::conj(half[i + 1]);
+          out_host[((size_t)f * nop + a) * nop + b] = make_double2(val.real(), val.imag());
+        }
+  } catch (...) {
+    try { restore(); } catch (...) {}
+    for (auto p : owned) c.dfree(p);
+    throw;
+  }
+  for (auto p : owned) c.dfree(p);
+}
+
 // ------------------------------------------------------------------------------ EOM-EE
 // Lowest roots of the right eigenproblem A r = w r (EOM-CCSD excitation energies; SI "EOM-EE
 // sigma-vectors and intermediates", with the Davidson scheme used for eigenvalues): a

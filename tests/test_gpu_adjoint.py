@@ -206,3 +206,51 @@ def test_static_field_derivative_3x8(pk):
                                                                            tol=1e-12))
     ref = (ref[0] - ref[1]) / (2 * h)
     assert np.abs(got - ref).max() < 1e-7 * np.abs(ref).max(), np.abs(got - ref).max() / np.abs(ref).max()
+
+
+def _herm(n, seed, scale):
+    rng = np.random.default_rng(seed)
+    a = rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n))
+    return scale * (a + a.conj().T) / 2
+
+
+def test_analytic_field_derivative_matches_oracle_3x8(pk):
+    """cclr_field_derivative (the CC-CC response function differentiated through t0, lambda0 and
+    the response amplitudes, with first-order multipliers and exact stencils of the device's own
+    products) against the oracle's analytic derivative, FP64, static and damped frequencies, and
+    against the device's own finite field (central difference of two complete solves)."""
+    from paper_2307_14296_b300 import autograd as ag
+    inst = synth.make_instance(3, 8, seed=21, sd=0.05)
+    V = _herm(inst.n, 7, 0.05)
+    om, gamma = [0.0, 0.2], 0.01
+    ctx = make_ctx(pk, inst, tol=1e-11, ground_tol=1e-12)
+    ctx.cc_ground()
+    ctx.cc_lambda()
+    ctx.cc_lr_solve(inst.ops, om, gamma)
+    before = ctx.cc_response_function()
+    got = ctx.cclr_field_derivative(V)
+    after = ctx.cc_response_function()
+    ref = R.CCSystem(Ints.from_instance(inst), tol=1e-12).field_derivative(inst.ops, V, [w + 1j * gamma for w in om])
+    assert rel(got, ref) < 1e-8, rel(got, ref)
+    assert np.array_equal(before, after)   # amplitudes and multipliers restored
+    blocks = [inst.blocks[k] for k in synth.CLASSES]
+    fd = ag.alpha_field_derivative(lambda: pk.Context(0, tol=1e-11, ground_tol=1e-12), 3, 8, inst.fock, blocks, V,
+                                   inst.ops, om, gamma, h=1e-3)[0]
+    assert rel(-got, fd) < 1e-6, rel(-got, fd)
+    ctx.close()
+
+
+def test_analytic_field_derivative_refined_split_bf16_4x20(pk):
+    """The same derivative from split-BF16 solves refined to 1e-10 (products in the FP64-class
+    mode) against the oracle at (4,20)."""
+    inst = synth.make_instance(4, 20)
+    V = _herm(inst.n, 8, 0.05)
+    om, gamma = [0.1], 0.01
+    ctx = make_ctx(pk, inst, precision=pk.TC_BF16X3, tol=1e-10, ground_tol=1e-11, batch=8)
+    ctx.cc_ground()
+    ctx.cc_lambda()
+    ctx.cc_lr_solve(inst.ops, om, gamma)
+    got = ctx.cclr_field_derivative(V)
+    ctx.close()
+    ref = R.CCSystem(Ints.from_instance(inst), tol=1e-12).field_derivative(inst.ops, V, [w + 1j * gamma for w in om])
+    assert rel(got, ref) < 1e-6, rel(got, ref)
