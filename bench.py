@@ -357,7 +357,8 @@ def run_adjoint(args):
     real parameter of the three Hermitian dipole operators through the autograd backward (one
     set of 4 n_ops left solves, reused for the 18 Jacobian rows), checked against a central
     difference (h = 1e-4) of two further solves along one random Hermitian direction; and the
-    static-field derivative d alpha / d eps for a field along operator 2 by finite field
+    static-field derivative d alpha / d eps for a field along operator 2 analytically
+    (cclr_field_derivative) and by finite field
     (h = 1e-4).  One JSON line."""
     import torch
     import paper_2307_14296_b300 as pk
@@ -422,13 +423,20 @@ def run_adjoint(args):
     err = max(np.abs(got[0] - fd.real).max(), np.abs(got[1] - fd.imag).max())
     out["fd_check"] = dict(h=h, max_abs_diff=float(err), max_abs_fd=float(np.abs(fd).max()),
                            max_rel=float(err / np.abs(fd).max()))
+    # the static-field derivative analytically (cclr_field_derivative on the converged state)
+    ctx.cc_lr_solve(inst.ops, om, w["gamma"])
+    t0 = time.perf_counter()
+    danal = -ctx.cclr_field_derivative(inst.ops[2])
+    t_anal = time.perf_counter() - t0
     ctx.close()
     t0 = time.perf_counter()
     dfield, _, _ = ag.alpha_field_derivative(new_context, o, v, inst.fock, blocks, inst.ops[2], inst.ops, om,
                                              w["gamma"], h=1e-4)
     out["field"] = dict(operator=2, h=1e-4, seconds=time.perf_counter() - t0,
                         d_alpha_d_eps=[[[float(dfield[0, x, y].real), float(dfield[0, x, y].imag)] for y in range(3)]
-                                       for x in range(3)])
+                                       for x in range(3)],
+                        analytic_seconds=t_anal,
+                        analytic_vs_finite_field_max_rel=float(np.abs(danal - dfield).max() / np.abs(dfield).max()))
     print(json.dumps(out), flush=True)
 
 
