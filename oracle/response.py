@@ -18,6 +18,8 @@ TEST INFRASTRUCTURE ONLY.
                    the first-order multipliers t-bar^Y(z) (A + z) = -(eta^Y + F t^Y(z)) from left
                    sigma products (Sec. 2.3, the asymmetric CC-CC form; the printed form omits the
                    C^{+-w} symmetrizer, which the stated equality with the symmetric form needs);
+  * static-field derivative d<<X;Y>>_z / d eps for H + eps V on the Fock matrix: the response
+                   function above differentiated by the chain rule (field_derivative);
   * polarizability alpha_xy(z) = -<<mu_x; mu_y>>_z, mean alpha, anisotropy, and the absorption
     cross section sigma(w) = 4 pi w / c Im mean-alpha (Eq. abs_cpp; Sec. 5 definitions).
 All products in the response function are bilinear (no conjugation) over unique excitations.
