@@ -67,7 +67,14 @@ typedef enum {
  *  In the BF16X3/BF16X6 modes the solvers' vector passes run in FP32 arithmetic and the iterations
  *  stop at floors relative to the right-hand side (see cclr_options.refine); small solves and the
  *  response-function contraction stay in FP64 in every mode. */
-typedef enum { CCLR_FP64 = 0, CCLR_TC_BF16X3 = 2, CCLR_TC_BF16X6 = 3, CCLR_TC_F64 = 4 } cclr_precision;
+typedef enum {
+  CCLR_FP64 = 0,
+  CCLR_TC_BF16X3 = 2,
+  CCLR_TC_BF16X6 = 3,
+  CCLR_TC_F64 = 4,
+  CCLR_BF16X2_TC = CCLR_TC_BF16X3, /* other names: split BF16 (two slices per operand) */
+  CCLR_FP32_TC = CCLR_TC_BF16X6    /*              the FP32-class tensor-core mode */
+} cclr_precision;
 
 typedef struct {
   double tol;          /* residual 2-norm target of the response solves (default 1e-8)        */
@@ -255,6 +262,11 @@ cclr_status cclr_set_amplitudes(cclr_ctx *ctx, int which, const cclr_c128 *src, 
 /* Response solution t^X(z) for operator k, frequency f and shift s (0: w+ig, 1: -w+ig,
  * 2: w-ig, 3: -w-ig) after cc_lr_solve, in the amplitude layout. */
 cclr_status cclr_get_response_vector(cclr_ctx *ctx, int k, int f, int s, cclr_c128 *dst, size_t n);
+
+/* One export call for every amplitude set: which = 0 the ground amplitudes T, 1 the multipliers
+ * Lambda (idx ignored; as cclr_get_amplitudes), 2 a response solution t^X(z) with
+ * idx = (k * n_freq + f) * 4 + s (as cclr_get_response_vector).  n must be o*v + Po*Pv. */
+cclr_status cclr_export_amplitudes(cclr_ctx *ctx, int which, int idx, cclr_c128 *dst, size_t n);
 
 /* Sigma vectors for nvec vectors in the amplitude layout (side 0: right, A r, SI Eqs.
  * sigma_sin-ee / sigma_double-ee; side 1: left, l A, SI Eqs. sigma_sin-ee-left /

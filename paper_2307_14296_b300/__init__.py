@@ -32,7 +32,7 @@ AMP_T, AMP_LAMBDA = 0, 1
 EXPORTS = (
     "cclr_default_options", "cclr_create", "cclr_destroy", "cclr_last_error", "cclr_set_hamiltonian",
     "cc_ground", "cc_lambda", "cc_lr_solve", "cc_response_function", "cc_response_function_ci", "cc_response_function_asym",
-    "cclr_field_derivative", "cc_eom_ee",
+    "cclr_field_derivative", "cclr_export_amplitudes", "cc_eom_ee",
     "cclr_get_eom_vector",
     "cclr_get_amplitudes",
     "cclr_set_amplitudes", "cclr_get_response_vector", "cclr_sigma", "cclr_residual", "cclr_xi",
@@ -70,6 +70,7 @@ _sig = {
     "cc_response_function_ci": (_i, [_vp, _vp]),
     "cc_response_function_asym": (_i, [_vp, _vp]),
     "cclr_field_derivative": (_i, [_vp, _vp, _vp]),
+    "cclr_export_amplitudes": (_i, [_vp, _i, _i, _vp, _sz]),
     "cc_eom_ee": (_i, [_vp, _i, _vp, _vp]),
     "cclr_get_eom_vector": (_i, [_vp, _i, _vp, ctypes.c_size_t]),
     "cclr_get_amplitudes": (_i, [_vp, _i, _vp, _sz]),
@@ -274,6 +275,12 @@ class Context:
         solutions."""
         out = np.zeros((self._nfreq, self._nops, self._nops), np.complex128)
         self._check(_lib.cc_response_function_asym(self._h, _ptr(out)))
+        return out
+
+    def cclr_export_amplitudes(self, which, idx=0):
+        """T (which 0), Lambda (1) or the response solution idx = (k n_freq + f) 4 + s (2)."""
+        out = np.zeros(self.N, np.complex128)
+        self._check(_lib.cclr_export_amplitudes(self._h, int(which), int(idx), _ptr(out), out.size))
         return out
 
     def cclr_field_derivative(self, V):

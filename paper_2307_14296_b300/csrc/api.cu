@@ -548,6 +548,18 @@ cclr_status cclr_get_response_vector(cclr_ctx* h, int k, int f, int s, cclr_c128
   });
 }
 
+cclr_status cclr_export_amplitudes(cclr_ctx* h, int which, int idx, cclr_c128* dst, size_t n) {
+  if (which == 0 || which == 1) return cclr_get_amplitudes(h, which, dst, n);
+  if (which == 2) {
+    if (!h) return CCLR_E_ARG;
+    const ResponseData& rd = h->c.rd;
+    const int nf = std::max(1, rd.n_freq);
+    const int s = idx & 3, q = idx >> 2;
+    return cclr_get_response_vector(h, idx < 0 ? -1 : q / nf, q % nf, s, dst, n);
+  }
+  return guard(h, [&](Ctx&) { throw Error(CCLR_E_ARG, "cclr_export_amplitudes: unknown amplitude set"); });
+}
+
 cclr_status cclr_sigma(cclr_ctx* h, int side, int nvec, const cclr_c128* in, cclr_c128* out, int on_device,
                        int precision) {
   return guard(h, [&](Ctx& c) {

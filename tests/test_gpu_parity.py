@@ -297,3 +297,20 @@ def test_tensor_core_response_matches_fp64(pk):
         ctx.close()
     ref = alpha[pk.FP64]
     assert np.abs(alpha[pk.TC_BF16X3] - ref).max() < 2e-5 * np.abs(ref).max()
+
+
+def test_export_amplitudes_matches_the_getters(pk):
+    """cclr_export_amplitudes (the single export call) returns the same bits as
+    cclr_get_amplitudes and cclr_get_response_vector for every amplitude set."""
+    inst = synth.make_instance(3, 8, seed=21, sd=0.05)
+    ctx = make_ctx(pk, inst, tol=1e-10, ground_tol=1e-11)
+    ctx.cc_ground()
+    ctx.cc_lambda()
+    ctx.cc_lr_solve(inst.ops, [0.05, 0.3], 0.01)
+    assert np.array_equal(ctx.cclr_export_amplitudes(0), ctx.cclr_get_amplitudes(pk.AMP_T))
+    assert np.array_equal(ctx.cclr_export_amplitudes(1), ctx.cclr_get_amplitudes(pk.AMP_LAMBDA))
+    for k, f, s in [(0, 0, 0), (1, 1, 2), (2, 0, 3)]:
+        assert np.array_equal(ctx.cclr_export_amplitudes(2, (k * 2 + f) * 4 + s), ctx.cclr_get_response_vector(k, f, s))
+    with pytest.raises(pk.CCLRError):
+        ctx.cclr_export_amplitudes(2, 3 * 2 * 4)
+    ctx.close()
