@@ -287,9 +287,11 @@ class Context:
         """d<<X_x;X_y>>/d eps [n_freq, n_ops, n_ops] for the field eps V on the Fock matrix (V: n x n,
         host or CUDA); d alpha / d eps is its negative."""
         p, keep = _in(V)
-        if tuple(keep.shape) != (self._norb, self._norb):
+        norb = getattr(self, "_norb", None)   # None before cc_lr_solve: the library reports the state
+        if norb is not None and tuple(keep.shape) != (norb, norb):
             raise ValueError("V must be an n x n matrix of the operators' size")
-        out = np.zeros((self._nfreq, self._nops, self._nops), np.complex128)
+        nf, no = getattr(self, "_nfreq", 0), getattr(self, "_nops", 0)
+        out = np.zeros((nf, no, no), np.complex128)
         self._check(_lib.cclr_field_derivative(self._h, p, _ptr(out)))
         return out
 

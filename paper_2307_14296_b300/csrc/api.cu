@@ -472,6 +472,7 @@ cclr_status cc_response_function_asym(cclr_ctx* h, cclr_c128* out) {
 cclr_status cclr_field_derivative(cclr_ctx* h, const cclr_c128* V, cclr_c128* out) {
   return guard(h, [&](Ctx& c) {
     CCLR_REQUIRE(V && out, CCLR_E_ARG, "null argument");
+    CCLR_REQUIRE(c.rd.solved, CCLR_E_STATE, "cclr_field_derivative before cc_lr_solve");
     require_finite(c, (const cplx*)V, c.n * c.n, "cclr_field_derivative: field operator");
     field_derivative(c, (const cplx*)V, (cplx*)out);
   });

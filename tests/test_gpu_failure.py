@@ -106,6 +106,10 @@ def test_call_order_violations_are_state_errors(pk):
     with pytest.raises(pk.CCLRError) as e:
         ctx.cc_response_function()           # before cc_lr_solve
     assert e.value.status == pk.CCLR_E_STATE
+    for call in (ctx.cc_response_function_asym, lambda: ctx.cclr_field_derivative(np.zeros((2, 2), complex))):
+        with pytest.raises(pk.CCLRError) as e:
+            call()                           # before cc_lr_solve (V is not read)
+        assert e.value.status == pk.CCLR_E_STATE
     ctx.close()
 
 
