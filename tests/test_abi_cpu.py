@@ -81,3 +81,24 @@ def test_noalloc_wrapper_rejects_bad_tensors_before_any_gpu_work():
     for cs in cases:
         with pytest.raises(ValueError):
             pk.cclr_zgemm_nt_noalloc(cs["A"], cs["B"], cs["C"])
+
+
+def test_header_is_plain_c_and_links_against_the_library(tmp_path):
+    """include/cclr.h compiles as C99 without warnings, and a C program that takes the address of
+    every declared entry point links against the built library (no call is made)."""
+    import shutil
+    import subprocess
+    import paper_2307_14296_b300 as pk
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    names = header_functions()
+    src = tmp_path / "abi.c"
+    src.write_text('#include "cclr.h"\n#include <stdio.h>\nint main(void) {\n  const void *f[] = {'
+                   + ", ".join("(const void *)&" + n for n in names) + "};\n"
+                   "  printf(\"%d\\n\", (int)(sizeof f / sizeof f[0]));\n  return CCLR_FP32_TC == CCLR_TC_BF16X6 ? 0 : 1;\n}\n")
+    lib = pk.library_path()
+    out = subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-Wno-pedantic", "-I", os.path.join(ROOT, "include"),
+                          str(src), lib, "-Wl,-rpath," + os.path.dirname(lib), "-o", str(tmp_path / "abi")],
+                         capture_output=True, text=True)
+    assert out.returncode == 0, out.stderr
