@@ -255,3 +255,17 @@ def test_field_derivative_needs_the_multiplier_response(four_electron, monkeypat
     monkeypatch.setattr(R.CCSystem, "at", lambda self, t=None, lam=None: orig(self, t=t))
     bad = s.field_derivative(inst.ops, V, ZF[1:], A=A)
     assert np.abs(bad - good).max() > 1e-4 * np.abs(good).max()
+
+
+def test_static_field_derivative_is_a_symmetric_third_derivative(four_electron):
+    """At w = 0 and gamma = 0 the CC-CC response function is the second derivative of the CC
+    energy, so its field derivative along X_z is the third derivative: d<<X_x;X_y>>/d eps_z is
+    symmetric in x, y and z."""
+    inst, s, A = four_electron
+    D = [s.field_derivative(inst.ops, inst.ops[z], [0.0], A=A)[0] for z in range(3)]
+    scale = max(np.abs(d).max() for d in D)
+    for x in range(3):
+        for y in range(3):
+            for z in range(3):
+                assert abs(D[z][x, y] - D[y][x, z]) < 1e-10 * scale
+                assert abs(D[z][x, y] - D[x][z, y]) < 1e-10 * scale
