@@ -378,6 +378,20 @@ def run_adjoint(args):
     dev = torch.device("cuda", 0)
     out = dict(mode="adjoint", workload=config_dict(args)["workload"], precision=args.precision, omega=om,
                gamma=w["gamma"])
+    # warm-up of the PyTorch side of the backward (its kernels load and compile for this GPU at
+    # first use, ~10 s once per process) on a small system, so that the timed rows are steady state
+    wi = synth.make_instance(3, 8)
+    wctx = new_context()
+    wctx.cclr_set_hamiltonian(3, 8, wi.fock, [wi.blocks[k] for k in synth.CLASSES])
+    wctx.cc_ground()
+    wctx.cc_lambda()
+    wth = torch.tensor(np.stack([ag.hermitian_params(wi.ops[k]) for k in range(3)]), device=dev, requires_grad=True)
+    wal = ag.polarizability(torch.stack([ag.hermitian_from_params(wth[k], wi.n) for k in range(3)]), wctx, om,
+                            w["gamma"])
+    wg = torch.zeros_like(wal)
+    wg[0, 0, 0] = 1.0
+    torch.autograd.grad(wal, wth, grad_outputs=wg)
+    wctx.close()
     ctx = new_context()
     t0 = time.perf_counter()
     ctx.cclr_set_hamiltonian(o, v, inst.fock, blocks)
