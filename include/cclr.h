@@ -162,7 +162,9 @@ cclr_status cc_response_function(cclr_ctx *ctx, cclr_c128 *out);
  *   d<<X_x;X_y>>_{w+ig} = sum G[y][0] o dX_x + conj(sum G[y][1] o dX_x)
  *                       + sum G[x][3] o dX_y + conj(sum G[x][2] o dX_y)
  * (o: element-wise product summed over all p, q).  out: n_ops*4*n*n values, [k][s][p][q]
- * row-major.  Costs 4 n_ops left solves and Hessian products.  Requires cc_lr_solve. */
+ * row-major.  Costs 4 n_ops left solves and Hessian products; the 4 n_ops left systems are solved
+ * together, each holding 2 max_subspace vectors of N complex values (CCLR_E_OOM if they do not
+ * fit).  Requires cc_lr_solve. */
 cclr_status cclr_response_gradient(cclr_ctx *ctx, int f, cclr_c128 *out);
 
 /* A synthetic instance generated on the device and installed as the Hamiltonian (as
@@ -207,7 +209,8 @@ cclr_status cc_response_function_ci(cclr_ctx *ctx, cclr_c128 *out);
  * z = w_f + i gamma, from the solutions t^Y(z), t^Y(-z*) of the last cc_lr_solve.  Same layout
  * as cc_response_function and equal to it for exact solutions (its error is first order in the
  * solution errors, the symmetric form's second order).  Costs 2 n_ops left solves and Hessian
- * products per frequency.  Requires cc_lr_solve; CCLR_E_STATE otherwise, CCLR_E_NOCONV if a
+ * products per frequency; the 2 n_ops left systems of a frequency are solved together, each
+ * holding 2 max_subspace vectors of N complex values (CCLR_E_OOM if they do not fit).  Requires cc_lr_solve; CCLR_E_STATE otherwise, CCLR_E_NOCONV if a
  * multiplier solve does not converge within maxit (out is then not written). */
 cclr_status cc_response_function_asym(cclr_ctx *ctx, cclr_c128 *out);
 
