@@ -209,8 +209,8 @@ cclr_status cc_response_function_ci(cclr_ctx *ctx, cclr_c128 *out);
  * z = w_f + i gamma, from the solutions t^Y(z), t^Y(-z*) of the last cc_lr_solve.  Same layout
  * as cc_response_function and equal to it for exact solutions (its error is first order in the
  * solution errors, the symmetric form's second order).  Costs 2 n_ops left solves and Hessian
- * products per frequency; the 2 n_ops left systems of a frequency are solved together, each
- * holding 2 max_subspace vectors of N complex values (CCLR_E_OOM if they do not fit).  Requires cc_lr_solve; CCLR_E_STATE otherwise, CCLR_E_NOCONV if a
+ * products per frequency; the two left systems of one operator and frequency are solved together,
+ * each holding 2 max_subspace vectors of N complex values (CCLR_E_OOM if they do not fit).  Requires cc_lr_solve; CCLR_E_STATE otherwise, CCLR_E_NOCONV if a
  * multiplier solve does not converge within maxit (out is then not written). */
 cclr_status cc_response_function_asym(cclr_ctx *ctx, cclr_c128 *out);
 

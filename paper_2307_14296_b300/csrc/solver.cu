@@ -1415,7 +1415,8 @@ void response_function_ci(Ctx& c, cplx* out_host) {
 //   f(z) = 1/2 [eta^X t^Y(z) + tbar^Y(z) xi^X],   <<X;Y>>_z = f(z) + conj(f(-z*)).
 // It equals the symmetric form for exact solutions; its error is first order in the solution
 // errors (the symmetric form's is second order).  Only the shifts z = w + ig and -z* = -w + ig of
-// cc_lr_solve are read; per frequency the 2 n_ops multiplier systems share one Davidson run.
+// cc_lr_solve are read; the two multiplier systems of one operator and frequency share a Davidson
+// run (their trial spaces are the memory of the call).
 void response_function_asym(Ctx& c, cplx* out_host) {
   ResponseData& rd = c.rd;
   CCLR_REQUIRE(rd.solved, CCLR_E_STATE, "cc_response_function_asym before cc_lr_solve");
@@ -1438,8 +1439,9 @@ void response_function_asym(Ctx& c, cplx* out_host) {
         gram_host(c, rows(c, rd.eta[x], 1), rows(c, rd.basis[y], rd.nb[y]), false, E[(size_t)x * nop + y]);
   }
   std::vector<zc> half((size_t)rd.n_freq * nop * nop * 2);   // [f][x][y][s], s: 0 z, 1 -z*
-  for (int f = 0; f < rd.n_freq; ++f) {
-    std::vector<System> sys((size_t)2 * nop);   // [y][s]
+  for (int f = 0; f < rd.n_freq; ++f)
+    for (int y = 0; y < nop; ++y) {   // one operator's two multiplier systems at a time
+    std::vector<System> sys(2);   // s: 0 z, 1 -z*
     auto cleanup = [&]() {
       for (auto& s : sys) {
         if (s.rhs) c.dfree(const_cast<cplx*>(s.rhs));
@@ -1455,9 +1457,8 @@ void response_function_asym(Ctx& c, cplx* out_host) {
         Scope sc(c.ws);
         cplx* bd = c.ws.cplxs(maxL);
         cplx* t = c.ws.cplxs(N);
-        for (int y = 0; y < nop; ++y)
-          for (int q = 0; q < 2; ++q) {
-            System& s = sys[(size_t)2 * y + q];
+        for (int q = 0; q < 2; ++q) {
+            System& s = sys[q];
             to_dev(c, beta(y, f, q), bd, rd.nb[y]);
             lincomb(c.L, N, rd.nb[y], rd.basis[y], N, bd, t, false);
             cplx* b = c.dalloc(N);
@@ -1477,9 +1478,8 @@ void response_function_asym(Ctx& c, cplx* out_host) {
       Scope sc(c.ws);
       cplx* bd = c.ws.cplxs(maxL);
       cplx* l = c.ws.cplxs(N);
-      for (int y = 0; y < nop; ++y)
-        for (int q = 0; q < 2; ++q) {
-          const System& s = sys[(size_t)2 * y + q];
+      for (int q = 0; q < 2; ++q) {
+          const System& s = sys[q];
           to_dev(c, s.beta[0].data(), bd, s.L);
           lincomb(c.L, N, s.L, s.B, N, bd, l, false);
           for (int x = 0; x < nop; ++x) {
