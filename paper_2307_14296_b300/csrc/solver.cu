@@ -1441,60 +1441,60 @@ void response_function_asym(Ctx& c, cplx* out_host) {
   std::vector<zc> half((size_t)rd.n_freq * nop * nop * 2);   // [f][x][y][s], s: 0 z, 1 -z*
   for (int f = 0; f < rd.n_freq; ++f)
     for (int y = 0; y < nop; ++y) {   // one operator's two multiplier systems at a time
-    std::vector<System> sys(2);   // s: 0 z, 1 -z*
-    auto cleanup = [&]() {
-      for (auto& s : sys) {
-        if (s.rhs) c.dfree(const_cast<cplx*>(s.rhs));
-        if (s.B) c.dfree(s.B);
-        if (s.S) c.dfree(s.S);
-        s.rhs = nullptr;
-        s.B = s.S = nullptr;
-      }
-    };
-    try {
-      {
+      std::vector<System> sys(2);   // s: 0 z, 1 -z*
+      auto cleanup = [&]() {
+        for (auto& s : sys) {
+          if (s.rhs) c.dfree(const_cast<cplx*>(s.rhs));
+          if (s.B) c.dfree(s.B);
+          if (s.S) c.dfree(s.S);
+          s.rhs = nullptr;
+          s.B = s.S = nullptr;
+        }
+      };
+      try {
+        {
+          PrecisionScope exact(c, prec);
+          Scope sc(c.ws);
+          cplx* bd = c.ws.cplxs(maxL);
+          cplx* t = c.ws.cplxs(N);
+          for (int q = 0; q < 2; ++q) {
+              System& s = sys[q];
+              to_dev(c, beta(y, f, q), bd, rd.nb[y]);
+              lincomb(c.L, N, rd.nb[y], rd.basis[y], N, bd, t, false);
+              cplx* b = c.dalloc(N);
+              s.rhs = b;
+              hessian_right(c, 1, t, b);
+              axpy(c.L, N, cx(1), rd.eta[y], b);
+              s.z = {-rd.shifts[rd.shift_of[(size_t)f * 4 + q]]};   // tbar (A - w_l) = -b, w_l = -z
+              s.B = c.dalloc((int64_t)maxL * N);
+              s.S = c.dalloc((int64_t)maxL * N);
+            }
+        }
+        auto op = [&](int nv, const cplx* in, cplx* o) { sigma_left(c, nv, in, o); };
+        davidson(c, sys, op, maxL, c.opt.tol);
+        if (refining(c)) refine_systems(c, sys, op, maxL, c.opt.tol, nullptr, nullptr);
         PrecisionScope exact(c, prec);
+        Fast32 f32(c);
         Scope sc(c.ws);
         cplx* bd = c.ws.cplxs(maxL);
-        cplx* t = c.ws.cplxs(N);
+        cplx* l = c.ws.cplxs(N);
         for (int q = 0; q < 2; ++q) {
-            System& s = sys[q];
-            to_dev(c, beta(y, f, q), bd, rd.nb[y]);
-            lincomb(c.L, N, rd.nb[y], rd.basis[y], N, bd, t, false);
-            cplx* b = c.dalloc(N);
-            s.rhs = b;
-            hessian_right(c, 1, t, b);
-            axpy(c.L, N, cx(1), rd.eta[y], b);
-            s.z = {-rd.shifts[rd.shift_of[(size_t)f * 4 + q]]};   // tbar (A - w_l) = -b, w_l = -z
-            s.B = c.dalloc((int64_t)maxL * N);
-            s.S = c.dalloc((int64_t)maxL * N);
+            const System& s = sys[q];
+            to_dev(c, s.beta[0].data(), bd, s.L);
+            lincomb(c.L, N, s.L, s.B, N, bd, l, false);
+            for (int x = 0; x < nop; ++x) {
+              std::vector<zc> g;
+              gram_host(c, rows(c, l, 1), rows(c, rd.xi[x], 1), false, g);
+              const zc et = dotL(E[(size_t)x * nop + y], beta(y, f, q), rd.nb[y]);
+              half[(((size_t)f * nop + x) * nop + y) * 2 + q] = 0.5 * (et + g[0]);
+            }
           }
+      } catch (...) {
+        cleanup();
+        throw;
       }
-      auto op = [&](int nv, const cplx* in, cplx* o) { sigma_left(c, nv, in, o); };
-      davidson(c, sys, op, maxL, c.opt.tol);
-      if (refining(c)) refine_systems(c, sys, op, maxL, c.opt.tol, nullptr, nullptr);
-      PrecisionScope exact(c, prec);
-      Fast32 f32(c);
-      Scope sc(c.ws);
-      cplx* bd = c.ws.cplxs(maxL);
-      cplx* l = c.ws.cplxs(N);
-      for (int q = 0; q < 2; ++q) {
-          const System& s = sys[q];
-          to_dev(c, s.beta[0].data(), bd, s.L);
-          lincomb(c.L, N, s.L, s.B, N, bd, l, false);
-          for (int x = 0; x < nop; ++x) {
-            std::vector<zc> g;
-            gram_host(c, rows(c, l, 1), rows(c, rd.xi[x], 1), false, g);
-            const zc et = dotL(E[(size_t)x * nop + y], beta(y, f, q), rd.nb[y]);
-            half[(((size_t)f * nop + x) * nop + y) * 2 + q] = 0.5 * (et + g[0]);
-          }
-        }
-    } catch (...) {
       cleanup();
-      throw;
     }
-    cleanup();
-  }
   for (int f = 0; f < rd.n_freq; ++f)
     for (int x = 0; x < nop; ++x)
       for (int y = 0; y < nop; ++y) {
