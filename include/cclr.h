@@ -162,9 +162,9 @@ cclr_status cc_response_function(cclr_ctx *ctx, cclr_c128 *out);
  *   d<<X_x;X_y>>_{w+ig} = sum G[y][0] o dX_x + conj(sum G[y][1] o dX_x)
  *                       + sum G[x][3] o dX_y + conj(sum G[x][2] o dX_y)
  * (o: element-wise product summed over all p, q).  out: n_ops*4*n*n values, [k][s][p][q]
- * row-major.  Costs 4 n_ops left solves and Hessian products; the 4 n_ops left systems are solved
- * together, each holding 2 max_subspace vectors of N complex values (CCLR_E_OOM if they do not
- * fit).  Requires cc_lr_solve. */
+ * row-major.  Costs 4 n_ops left solves and Hessian products; the four left systems of one
+ * operator are solved together, each holding 2 max_subspace vectors of N complex values
+ * (CCLR_E_OOM if they do not fit).  Requires cc_lr_solve. */
 cclr_status cclr_response_gradient(cclr_ctx *ctx, int f, cclr_c128 *out);
 
 /* A synthetic instance generated on the device and installed as the Hamiltonian (as

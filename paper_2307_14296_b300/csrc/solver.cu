@@ -1254,21 +1254,26 @@ void response_gradient(Ctx& c, int f, cplx* out_host) {
   CCLR_REQUIRE(f >= 0 && f < rd.n_freq, CCLR_E_ARG, "cclr_response_gradient: frequency index");
   const int64_t N = c.N, n = c.n;
   const int nop = rd.n_ops, maxL = std::max(8, c.opt.max_subspace);
-  // solution vectors t^k(w_s) and right-hand sides eta^k + F t^k(w_s) (FP64-class when refined)
+  // per operator (its four shifts share one Davidson run): solution vectors t^k(w_s) and
+  // right-hand sides eta^k + F t^k(w_s) (FP64-class when refined)
   std::vector<cplx*> tv, rhs, Bs, Ss;
   auto cleanup = [&]() {
     for (auto p : tv) c.dfree(p);
     for (auto p : rhs) c.dfree(p);
     for (auto p : Bs) c.dfree(p);
     for (auto p : Ss) c.dfree(p);
+    tv.clear();
+    rhs.clear();
+    Bs.clear();
+    Ss.clear();
   };
   try {
-    std::vector<System> sys(4 * nop);
-    {
-      PrecisionScope exact(c, rd.refined ? CCLR_TC_F64 : c.opt.precision);
-      Scope sc(c.ws);
-      cplx* bd = c.ws.cplxs(maxL);
-      for (int k = 0; k < nop; ++k)
+    for (int k = 0; k < nop; ++k) {
+      std::vector<System> sys(4);
+      {
+        PrecisionScope exact(c, rd.refined ? CCLR_TC_F64 : c.opt.precision);
+        Scope sc(c.ws);
+        cplx* bd = c.ws.cplxs(maxL);
         for (int q = 0; q < 4; ++q) {
           cplx* t = c.dalloc(N);
           tv.push_back(t);
@@ -1279,7 +1284,7 @@ void response_gradient(Ctx& c, int f, cplx* out_host) {
           rhs.push_back(b);
           hessian_right(c, 1, t, b);
           axpy(c.L, N, cx(1), rd.eta[k], b);
-          System& s = sys[(size_t)4 * k + q];
+          System& s = sys[q];
           s.rhs = b;
           s.z = {-rd.shifts[rd.shift_of[(size_t)f * 4 + q]]};   // l (A - w_l) = -b with w_l = -w_s
           s.B = c.dalloc((int64_t)maxL * N);
@@ -1287,34 +1292,36 @@ void response_gradient(Ctx& c, int f, cplx* out_host) {
           Bs.push_back(s.B);
           Ss.push_back(s.S);
         }
-    }
-    auto op = [&](int nv, const cplx* in, cplx* out) { sigma_left(c, nv, in, out); };
-    davidson(c, sys, op, maxL, c.opt.tol);
-    if (refining(c)) refine_systems(c, sys, op, maxL, c.opt.tol, &Bs, &Ss);
-    PrecisionScope exact(c, rd.refined ? CCLR_TC_F64 : c.opt.precision);
-    Scope sc(c.ws);
-    cplx* l = c.ws.cplxs(N);
-    cplx* bd = c.ws.cplxs(maxL);
-    cplx* D1 = c.ws.cplxs(n * n);
-    cplx* D2 = c.ws.cplxs(n * n);
-    for (int k = 0; k < nop; ++k)
-      for (int q = 0; q < 4; ++q) {
-        const System& s = sys[(size_t)4 * k + q];
-        to_dev(c, s.beta[0].data(), bd, s.L);
-        lincomb(c.L, N, s.L, s.B, N, bd, l, false);
-        eta_density(c, tv[(size_t)4 * k + q], D1);
-        xi_density(c, l, D2);
-        axpy(c.L, n * n, cx(1), D2, D1);
-        scale_vec(c.L, n * n, cx(0.5), D1);
-        CCLR_CK(cudaMemcpyAsync(out_host + ((size_t)4 * k + q) * n * n, D1, sizeof(cplx) * n * n, cudaMemcpyDefault,
-                                c.stream));
-        c.sync();
       }
+      auto op = [&](int nv, const cplx* in, cplx* out) { sigma_left(c, nv, in, out); };
+      davidson(c, sys, op, maxL, c.opt.tol);
+      if (refining(c)) refine_systems(c, sys, op, maxL, c.opt.tol, &Bs, &Ss);
+      {
+        PrecisionScope exact(c, rd.refined ? CCLR_TC_F64 : c.opt.precision);
+        Scope sc(c.ws);
+        cplx* l = c.ws.cplxs(N);
+        cplx* bd = c.ws.cplxs(maxL);
+        cplx* D1 = c.ws.cplxs(n * n);
+        cplx* D2 = c.ws.cplxs(n * n);
+        for (int q = 0; q < 4; ++q) {
+          const System& s = sys[q];
+          to_dev(c, s.beta[0].data(), bd, s.L);
+          lincomb(c.L, N, s.L, s.B, N, bd, l, false);
+          eta_density(c, tv[q], D1);
+          xi_density(c, l, D2);
+          axpy(c.L, n * n, cx(1), D2, D1);
+          scale_vec(c.L, n * n, cx(0.5), D1);
+          CCLR_CK(cudaMemcpyAsync(out_host + ((size_t)4 * k + q) * n * n, D1, sizeof(cplx) * n * n,
+                                  cudaMemcpyDefault, c.stream));
+          c.sync();
+        }
+      }
+      cleanup();
+    }
   } catch (...) {
     cleanup();
     throw;
   }
-  cleanup();
 }
 
 // Left (adjoint) linear systems l_k (A + w) = -b_k for nrhs right-hand sides (host or device
