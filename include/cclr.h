@@ -224,7 +224,8 @@ cclr_status cc_response_function_asym(cclr_ctx *ctx, cclr_c128 *out);
  * tbar^k(w) (A + w) = -(eta^k + F t^k(w)); the amplitude derivatives of sigma, xi, eta and F are
  * taken from the library's products at shifted amplitudes by stencils that are exact for their
  * polynomial degree.  Costs one right and one left static solve, 4 n_ops left solves per
- * frequency, and per frequency four Hbar builds with batched sigma and Hessian products.
+ * frequency (solved together, each system holding 2 max_subspace vectors of N complex values),
+ * and per frequency four Hbar builds with batched sigma and Hessian products.
  * Requires cc_lr_solve; CCLR_E_ARG on non-finite V; CCLR_E_NOCONV if a solve does not converge
  * (the context's amplitudes and multipliers are restored in every case). */
 cclr_status cclr_field_derivative(cclr_ctx *ctx, const cclr_c128 *V, cclr_c128 *out);
